@@ -1,0 +1,198 @@
+"""ctypes front end of the plain FP64 CPU oracle (``dgsem_oracle.c``).
+
+TEST INFRASTRUCTURE ONLY: the oracle is imported by ``tests/``,
+``__graft_entry__.smoke()`` and the cpu_baseline / reference legs of
+``bench.py``, never by the product package. It shares no code with the CUDA
+library. Every function here only marshals numpy arrays to the C routines;
+the arithmetic (and its citations) lives in ``dgsem_oracle.c``.
+
+All arrays use the state layout u[e][v][k][j][i] (element-major, variable,
+then nodes with x fastest), float64, C-contiguous.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "dgsem_oracle.c")
+_SO = os.path.join(_HERE, "liboracle.so")
+_lib = None
+
+_dp = ctypes.POINTER(ctypes.c_double)
+_ip = ctypes.POINTER(ctypes.c_int)
+_llp = ctypes.POINTER(ctypes.c_longlong)
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (-O2 -ffp-contract=off, OpenMP): once with
+    double, once with double complex for the complex-step JVP."""
+    if not force and os.path.exists(_SO) and os.path.getmtime(_SO) >= os.path.getmtime(_SRC):
+        return _SO
+    bdir = os.path.join(_HERE, "_build")
+    os.makedirs(bdir, exist_ok=True)
+    flags = ["-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-fopenmp", "-std=c11"]
+    o1 = os.path.join(bdir, "or_real.o")
+    o2 = os.path.join(bdir, "or_cstep.o")
+    tmp = _SO + f".tmp{os.getpid()}"
+    subprocess.check_call(["gcc", *flags, "-c", _SRC, "-o", o1])
+    subprocess.check_call(["gcc", *flags, "-DOR_CSTEP", "-c", _SRC, "-o", o2])
+    subprocess.check_call(["gcc", "-shared", "-fopenmp", o1, o2, "-o", tmp, "-lm"])
+    os.replace(tmp, _SO)
+    return _SO
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = ctypes.CDLL(_SO)
+        L.or_lgl.argtypes = [ctypes.c_int, _dp, _dp]
+        L.or_diff_matrix.argtypes = [ctypes.c_int, _dp, _dp]
+        L.or_lsrk_coefficients.argtypes = [_dp, _dp, _dp]
+        L.or_ln_mean.argtypes = [ctypes.c_double, ctypes.c_double]
+        L.or_ln_mean.restype = ctypes.c_double
+        L.or_two_point.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                   _dp, _dp, _dp]
+        rhs_args = [ctypes.c_int, ctypes.c_int, _ip, _dp, ctypes.c_double, ctypes.c_int,
+                    ctypes.c_int]
+        L.or_rhs.argtypes = rhs_args + [_dp, _dp, _llp, ctypes.c_longlong, ctypes.c_int]
+        L.or_rhs_jvp.argtypes = rhs_args + [_dp, _dp, _dp, _llp, ctypes.c_longlong,
+                                            ctypes.c_int]
+        L.or_rk_stage.argtypes = [ctypes.c_longlong, _dp, _dp, _dp, ctypes.c_double,
+                                  ctypes.c_double, ctypes.c_double]
+        L.or_max_dt.argtypes = [ctypes.c_int, ctypes.c_int, _ip, _dp, ctypes.c_double,
+                                ctypes.c_double, _dp]
+        L.or_max_dt.restype = ctypes.c_double
+        L.or_integrals.argtypes = [ctypes.c_int, ctypes.c_int, _ip, _dp, ctypes.c_double, _dp,
+                                   _dp]
+        _lib = L
+    return _lib
+
+
+def _d(a):
+    return a.ctypes.data_as(_dp)
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def lgl(N: int):
+    """LGL nodes and weights (xi, w), each of length N+1."""
+    xi = np.zeros(N + 1)
+    w = np.zeros(N + 1)
+    if lib().or_lgl(N, _d(xi), _d(w)) != 0:
+        raise ValueError("bad N")
+    return xi, w
+
+
+def diff_matrix(N: int, xi=None):
+    """Nodal differentiation matrix D[i, j] = l_j'(xi_i)."""
+    if xi is None:
+        xi, _ = lgl(N)
+    xi = _f64(xi)
+    D = np.zeros((N + 1, N + 1))
+    lib().or_diff_matrix(N, _d(xi), _d(D))
+    return D
+
+
+def lsrk_coefficients():
+    """Carpenter-Kennedy 5-stage 4th-order 2N-storage coefficients (A, B, c)."""
+    A, B, c = np.zeros(5), np.zeros(5), np.zeros(5)
+    lib().or_lsrk_coefficients(_d(A), _d(B), _d(c))
+    return A, B, c
+
+
+def ln_mean(x: float, y: float) -> float:
+    return lib().or_ln_mean(float(x), float(y))
+
+
+# two_point kinds: volume fluxes 0 Ranocha, 1 Chandrashekar, 2 central;
+# surface fluxes 10 LLF, 11 Ranocha, 12 HLL, 13 Chandrashekar; 20 physical f(u_L)
+RANOCHA, CHANDRASHEKAR, CENTRAL = 0, 1, 2
+S_LLF, S_RANOCHA, S_HLL, S_CHANDRASHEKAR = 0, 1, 2, 3
+PHYSICAL = 20
+
+
+def two_point(kind: int, d: int, n: int, uL, uR, gamma: float = 1.4):
+    uL, uR = _f64(uL), _f64(uR)
+    f = np.zeros(d + 2)
+    if lib().or_two_point(kind, d, n, gamma, _d(uL), _d(uR), _d(f)) != 0:
+        raise ValueError("bad flux kind")
+    return f
+
+
+def _mesh_args(d, n, dom):
+    n_arr = (ctypes.c_int * 3)(*(list(n) + [1] * (3 - len(n))))
+    dom = _f64(dom)
+    return n_arr, dom
+
+
+def _elems(elems):
+    if elems is None:
+        return None, 0, None
+    e = np.ascontiguousarray(elems, dtype=np.int64)
+    return e.ctypes.data_as(_llp), len(e), e
+
+
+def rhs(d, N, n, dom, u, gamma=1.4, vflux=RANOCHA, sflux=S_LLF, elems=None, nthreads=0):
+    """du = rhs(u) (all elements, or only `elems`; other entries of du are 0)."""
+    n_arr, dom = _mesh_args(d, n, dom)
+    u = _f64(u)
+    du = np.zeros_like(u)
+    ep, ne, keep = _elems(elems)
+    rc = lib().or_rhs(d, N, n_arr, _d(dom), gamma, vflux, sflux, _d(u), _d(du), ep, ne,
+                      nthreads)
+    if rc != 0:
+        raise ValueError("or_rhs: bad arguments")
+    return du
+
+
+def rhs_jvp(d, N, n, dom, u, v, gamma=1.4, vflux=RANOCHA, sflux=S_LLF, elems=None, nthreads=0):
+    """J(u) v of the rhs by complex-step differentiation."""
+    n_arr, dom = _mesh_args(d, n, dom)
+    u, v = _f64(u), _f64(v)
+    jv = np.zeros_like(u)
+    ep, ne, keep = _elems(elems)
+    rc = lib().or_rhs_jvp(d, N, n_arr, _d(dom), gamma, vflux, sflux, _d(u), _d(v), _d(jv), ep,
+                          ne, nthreads)
+    if rc != 0:
+        raise ValueError("or_rhs_jvp failed")
+    return jv
+
+
+def rk_stage(u, k, du, a, b, dt):
+    """In place: k <- a k + dt du; u <- u + b k (float64 contiguous arrays)."""
+    for x in (u, k, du):
+        assert x.dtype == np.float64 and x.flags.c_contiguous
+    lib().or_rk_stage(u.size, _d(u), _d(k), _d(du), a, b, dt)
+
+
+def max_dt(d, N, n, dom, u, cfl=0.5, gamma=1.4):
+    n_arr, dom = _mesh_args(d, n, dom)
+    u = _f64(u)
+    return lib().or_max_dt(d, N, n_arr, _d(dom), gamma, cfl, _d(u))
+
+
+def integrals(d, N, n, dom, u, gamma=1.4):
+    """[rho, rho v_1..rho v_d, E, entropy S, kinetic energy] integrated."""
+    n_arr, dom = _mesh_args(d, n, dom)
+    u = _f64(u)
+    out = np.zeros(d + 4)
+    if lib().or_integrals(d, N, n_arr, _d(dom), gamma, _d(u), _d(out)) != 0:
+        raise ValueError("bad mesh")
+    return out
+
+
+def lsrk_step(d, N, n, dom, u, dt, gamma=1.4, vflux=RANOCHA, sflux=S_LLF, nthreads=0):
+    """One full Carpenter-Kennedy step (5 stages) on a copy of u."""
+    A, B, _ = lsrk_coefficients()
+    u = _f64(u).copy()
+    k = np.zeros_like(u)
+    for s in range(5):
+        du = rhs(d, N, n, dom, u, gamma, vflux, sflux, nthreads=nthreads)
+        rk_stage(u, k, du, A[s], B[s], dt)
+    return u

@@ -1,0 +1,132 @@
+"""Seeded synthetic inputs shared by the CUDA path's tests, the oracle's
+tests and the benchmark.
+
+This module holds no arithmetic of the method itself: it evaluates initial
+states (density waves, seeded noise, cotangents) at node coordinates that the
+caller supplies from the 1D node positions of whichever side it is testing,
+and it draws the seeded ensemble descriptions. All states are float64 in the
+layout u[e][v][k][j][i] (element-major; within an element, variable, then
+nodes with x fastest; elements lexicographic with x fastest).
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+import numpy as np
+
+
+def node_coordinates(d, N, n, dom, xi):
+    """Physical coordinates of every node, shape (d, n_elem, (N+1)^d).
+
+    Element (ex, ey[, ez]) covers [lo + ex h, lo + (ex+1) h] per direction;
+    reference node xi in [-1, 1] maps to lo + (ex + (xi + 1)/2) h."""
+    xi = np.asarray(xi, dtype=np.float64)
+    np1 = N + 1
+    n = list(n)
+    h = [(dom[2 * k + 1] - dom[2 * k]) / n[k] for k in range(d)]
+    # element coordinate grids, x fastest
+    eidx = np.indices(n[::-1]).reshape(d, -1)[::-1]  # eidx[k] = element index along k
+    nidx = np.indices([np1] * d).reshape(d, -1)[::-1]  # node index along k, x fastest
+    X = np.empty((d, eidx.shape[1], nidx.shape[1]))
+    for k in range(d):
+        X[k] = dom[2 * k] + (eidx[k][:, None] + 0.5 * (xi[nidx[k]][None, :] + 1.0)) * h[k]
+    return X
+
+
+def prim_to_cons(rho, v, p, gamma=1.4):
+    """Conserved state (rho, rho v, E) from primitives; the ideal-gas energy
+    E = p/(gamma-1) + rho |v|^2 / 2 defines the initial condition."""
+    d = len(v)
+    v2 = sum(vk * vk for vk in v)
+    out = [rho] + [rho * vk for vk in v] + [p / (gamma - 1.0) + 0.5 * rho * v2]
+    return np.stack(out, axis=1).reshape(rho.shape[0], d + 2, -1)
+
+
+def density_wave(d, N, n, dom, xi, amplitude=0.98, velocity=None, pressure=20.0, gamma=1.4,
+                 t=0.0):
+    """rho = 1 + A sin(pi (sum_k x_k - t sum_k v_k)), constant v and p: an exact
+    solution of the Euler equations on a periodic [-1, 1]^d box."""
+    if velocity is None:
+        velocity = (0.1, 0.2, 0.3)[:d]
+    X = node_coordinates(d, N, n, dom, xi)
+    phase = X.sum(axis=0) - t * float(np.sum(velocity))
+    rho = 1.0 + amplitude * np.sin(np.pi * phase)
+    v = [np.full_like(rho, velocity[k]) for k in range(d)]
+    p = np.full_like(rho, pressure)
+    return np.ascontiguousarray(prim_to_cons(rho, v, p, gamma).reshape(-1))
+
+
+def noisy_density_wave(d, N, n, dom, xi, seed=0, noise=1.0e-2, amplitude=0.98, velocity=None,
+                       pressure=20.0, gamma=1.4):
+    """Density wave plus independent uniform noise of the given amplitude on
+    rho, every v_k and p at every node (drawn in layout order from
+    numpy default_rng(seed))."""
+    if velocity is None:
+        velocity = (0.1, 0.2, 0.3)[:d]
+    X = node_coordinates(d, N, n, dom, xi)
+    rho = 1.0 + amplitude * np.sin(np.pi * X.sum(axis=0))
+    rng = np.random.default_rng(seed)
+    r = rng.uniform(-1.0, 1.0, size=(rho.shape[0], d + 2, rho.shape[1])) * noise
+    rho = rho + r[:, 0]
+    v = [velocity[k] + r[:, 1 + k] for k in range(d)]
+    p = pressure + r[:, d + 1]
+    return np.ascontiguousarray(prim_to_cons(rho, v, p, gamma).reshape(-1))
+
+
+def uniform_state(d, N, n, rho=1.3, velocity=None, pressure=7.0, gamma=1.4):
+    """A constant state (free stream)."""
+    if velocity is None:
+        velocity = (0.3, -0.2, 0.1)[:d]
+    ne = int(np.prod(n))
+    P = (N + 1) ** d
+    r = np.full((ne, P), rho)
+    v = [np.full((ne, P), velocity[k]) for k in range(d)]
+    p = np.full((ne, P), pressure)
+    return np.ascontiguousarray(prim_to_cons(r, v, p, gamma).reshape(-1))
+
+
+def random_state(d, N, n, seed=0, gamma=1.4):
+    """Seeded random but physical state: rho in [0.5, 2], v in [-0.5, 0.5]^d,
+    p in [0.5, 3], independent per node."""
+    rng = np.random.default_rng(seed)
+    ne = int(np.prod(n))
+    P = (N + 1) ** d
+    rho = rng.uniform(0.5, 2.0, size=(ne, P))
+    v = [rng.uniform(-0.5, 0.5, size=(ne, P)) for _ in range(d)]
+    p = rng.uniform(0.5, 3.0, size=(ne, P))
+    return np.ascontiguousarray(prim_to_cons(rho, v, p, gamma).reshape(-1))
+
+
+def gaussian(size, seed=0):
+    """i.i.d. N(0, 1) entries (cotangents, random directions)."""
+    return np.random.default_rng(seed).standard_normal(size)
+
+
+@dataclass
+class EnsembleMember:
+    d: int
+    N: int
+    n: tuple
+    amplitude: float
+    velocity: tuple
+    pressure: float
+
+
+def ensemble(n_sims=48, seed=0, n_range=(8, 24), degrees=(3, 4, 5), pressure=20.0):
+    """Seeded ensemble of independent periodic 3D density-wave simulations on
+    [-1, 1]^3: per member (generator default_rng([seed, member])) elements per
+    dimension uniform in n_range, N from degrees, amplitude in [0.1, 0.98],
+    velocity in [-0.3, 0.3]^3."""
+    out = []
+    for s in range(n_sims):
+        rng = np.random.default_rng([seed, s])
+        ne = int(rng.integers(n_range[0], n_range[1] + 1))
+        N = int(rng.choice(degrees))
+        A = float(rng.uniform(0.1, 0.98))
+        v = tuple(float(x) for x in rng.uniform(-0.3, 0.3, size=3))
+        out.append(EnsembleMember(3, N, (ne, ne, ne), A, v, pressure))
+    return out
+
+
+def box(d, lo=-1.0, hi=1.0):
+    """Domain [lo, hi]^d as [lo0, hi0, lo1, hi1, ...]."""
+    return np.array([lo, hi] * d, dtype=np.float64)

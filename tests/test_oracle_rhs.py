@@ -1,0 +1,323 @@
+"""Pins of the oracle's semidiscrete operator rhs(u), its time stepping and
+its integrals against what the method fixes: free-stream preservation,
+discrete conservation, entropy conservation / dissipation, equivalence of the
+central-flux split form with the weak-form DGSEM written here with matrices,
+equivariance under axis permutations, convergence to the exact time
+derivative and to the exact solution, and the complex-step JVP against
+finite differences (CPU only)."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2108_06476_gb300 import workloads as W
+
+GAMMA = 1.4
+
+
+def quad_weights(orc, d, N, n, dom):
+    """Quadrature weight of every value (element Jacobian times LGL weights)."""
+    _, w = orc.lgl(N)
+    wq = w
+    for _ in range(d - 1):
+        wq = np.multiply.outer(w, wq).reshape(-1)  # x fastest
+    jac = np.prod([(dom[2 * k + 1] - dom[2 * k]) / n[k] / 2 for k in range(d)])
+    ne = int(np.prod(n))
+    return np.broadcast_to(jac * wq, (ne, d + 2, len(wq))).reshape(-1)
+
+
+def theta(u, d, nelem):
+    U = u.reshape(nelem, d + 2, -1)
+    rho, m, E = U[:, 0], U[:, 1:1 + d], U[:, d + 1]
+    v = m / rho[:, None]
+    v2 = (v * v).sum(axis=1)
+    p = (GAMMA - 1) * (E - 0.5 * rho * v2)
+    s = np.log(p) - GAMMA * np.log(rho)
+    b = rho / p
+    out = np.empty_like(U)
+    out[:, 0] = (GAMMA - s) / (GAMMA - 1) - 0.5 * b * v2
+    out[:, 1:1 + d] = b[:, None] * v
+    out[:, d + 1] = -b
+    return out.reshape(-1)
+
+
+CASES = [(2, 1, (2, 3)), (2, 3, (4, 3)), (2, 4, (3, 3)), (3, 2, (2, 3, 2)), (3, 3, (2, 2, 3))]
+
+
+@pytest.mark.parametrize("d,N,n", CASES)
+@pytest.mark.parametrize("vf,sf", [(0, 0), (0, 1), (1, 3), (2, 2)])
+def test_free_stream(orc, d, N, n, vf, sf):
+    dom = np.array([-1.0, 1.0, -0.5, 1.5, 0.0, 3.0][:2 * d])
+    u = W.uniform_state(d, N, n)
+    du = orc.rhs(d, N, n, dom, u, vflux=vf, sflux=sf)
+    fmax = 10.0
+    hmin = min((dom[2 * k + 1] - dom[2 * k]) / n[k] for k in range(d))
+    assert np.max(np.abs(du)) < 1e-13 * fmax * (2 / hmin) * (N + 1) ** 2
+
+
+@pytest.mark.parametrize("d,N,n", CASES)
+@pytest.mark.parametrize("vf,sf", [(0, 0), (0, 1), (1, 3), (2, 2), (1, 0)])
+def test_conservation(orc, d, N, n, vf, sf):
+    dom = np.array([-1.0, 1.0, -0.5, 1.5, 0.0, 3.0][:2 * d])
+    u = W.random_state(d, N, n, seed=7)
+    du = orc.rhs(d, N, n, dom, u, vflux=vf, sflux=sf)
+    wq = quad_weights(orc, d, N, n, dom)
+    tot = (wq * du).reshape(-1, d + 2, (N + 1) ** d).sum(axis=(0, 2))
+    scale = (wq * np.abs(du)).reshape(-1, d + 2, (N + 1) ** d).sum(axis=(0, 2))
+    assert np.all(np.abs(tot) <= 1e-14 * scale.max())
+
+
+@pytest.mark.parametrize("d,N,n", CASES)
+@pytest.mark.parametrize("vf,sf", [(0, 1), (1, 3)])
+def test_entropy_conservation_ec(orc, d, N, n, vf, sf):
+    dom = W.box(d)
+    u = W.random_state(d, N, n, seed=8)
+    du = orc.rhs(d, N, n, dom, u, vflux=vf, sflux=sf)
+    wq = quad_weights(orc, d, N, n, dom)
+    t = wq * theta(u, d, int(np.prod(n))) * du
+    assert abs(t.sum()) < 1e-13 * np.abs(t).sum()
+
+
+@pytest.mark.parametrize("d,N,n", CASES)
+def test_entropy_dissipation_llf(orc, d, N, n):
+    dom = W.box(d)
+    u = W.random_state(d, N, n, seed=9)
+    du = orc.rhs(d, N, n, dom, u, vflux=0, sflux=0)
+    wq = quad_weights(orc, d, N, n, dom)
+    t = wq * theta(u, d, int(np.prod(n))) * du
+    assert t.sum() < -1e-3 * np.abs(t).sum()
+
+
+def _weak_form_rhs(orc, d, N, n, dom, u, sflux_kind):
+    """Standard weak-form DGSEM with matrices: per direction
+    du = -(2/h) W^-1 (-D^T W f + B F*) applied along the axis."""
+    xi, w = orc.lgl(N)
+    D = orc.diff_matrix(N)
+    np1 = N + 1
+    ne = int(np.prod(n))
+    U = u.reshape(ne, d + 2, *([np1] * d))  # axes: e, v, (z), y, x
+    Ug = U.reshape(*n[::-1], d + 2, *([np1] * d))
+    du = np.zeros_like(U)
+    Kw = np.diag(1 / w) @ (-D.T @ np.diag(w))
+    for dirn in range(d):
+        h = (dom[2 * dirn + 1] - dom[2 * dirn]) / n[dirn]
+        ax_node = 2 + (d - 1 - dirn)   # node axis of this direction in U
+        ax_elem = d - 1 - dirn         # element axis in Ug
+        # nodal fluxes
+        F = np.zeros_like(U)
+        Fs_R = np.zeros_like(U)
+        for e in range(ne):
+            for idx in np.ndindex(*([np1] * d)):
+                F[(e, slice(None)) + idx] = orc.two_point(20, d, dirn, U[(e, slice(None)) + idx],
+                                                           U[(e, slice(None)) + idx])
+        vol = np.moveaxis(np.tensordot(Kw, np.moveaxis(F, ax_node, 0), axes=(1, 0)), 0, ax_node)
+        # surface: right trace of e and left trace of e+1 along this direction
+        Fg = np.zeros_like(Ug)
+        sl_N = [slice(None)] * Ug.ndim
+        sl_0 = [slice(None)] * Ug.ndim
+        node_ax_g = d + 1 + (d - 1 - dirn)
+        sl_N[node_ax_g] = N
+        sl_0[node_ax_g] = 0
+        uL = Ug[tuple(sl_N)]
+        uR = np.roll(Ug, -1, axis=ax_elem)[tuple(sl_0)]
+        FS = np.zeros_like(uL)
+        vax = d  # variable axis in the traces
+        uLm = np.moveaxis(uL, vax, -1).reshape(-1, d + 2)
+        uRm = np.moveaxis(uR, vax, -1).reshape(-1, d + 2)
+        FSm = np.stack([orc.two_point(10 + sflux_kind, d, dirn, a, b) for a, b in zip(uLm, uRm)])
+        FS = np.moveaxis(FSm.reshape(np.moveaxis(uL, vax, -1).shape), -1, vax)
+        surf = np.zeros_like(Ug)
+        surf[tuple(sl_N)] += FS / w[N]
+        surf[tuple(sl_0)] -= np.roll(FS, 1, axis=ax_elem) / w[0]
+        du += -(2 / h) * (vol + surf.reshape(U.shape))
+    return du.reshape(-1)
+
+
+@pytest.mark.parametrize("d,N,n", [(2, 2, (3, 2)), (2, 3, (2, 2)), (3, 2, (2, 2, 2))])
+@pytest.mark.parametrize("sf", [0, 2])
+def test_central_volume_flux_is_weak_form(orc, d, N, n, sf):
+    dom = np.array([-1.0, 1.0, -0.5, 1.5, 0.0, 3.0][:2 * d])
+    u = W.random_state(d, N, n, seed=11)
+    du = orc.rhs(d, N, n, dom, u, vflux=2, sflux=sf)
+    ref = _weak_form_rhs(orc, d, N, n, dom, u, sf)
+    assert np.max(np.abs(du - ref)) < 1e-12 * np.max(np.abs(ref))
+
+
+def _permute_state(u, d, N, n, perm):
+    """Relabel coordinate axes: new axis k is old axis perm[k] (elements,
+    nodes and momentum components)."""
+    np1 = N + 1
+    U = u.reshape(*n[::-1], d + 2, *([np1] * d))
+    # array axes: elements (z, y, x), variable, nodes (z, y, x); direction k
+    # sits at element position d-1-k and node position 2d-k
+    eperm = [d - 1 - perm[d - 1 - q] for q in range(d)]
+    nperm = [d + 1 + (d - 1 - perm[d - 1 - q]) for q in range(d)]
+    V = np.transpose(U, eperm + [d] + nperm).copy()
+    mom = V[(slice(None),) * d + (slice(1, 1 + d),)].copy()
+    V[(slice(None),) * d + (slice(1, 1 + d),)] = mom[(slice(None),) * d + (list(perm),)]
+    return V.reshape(-1)
+
+
+@pytest.mark.parametrize("d,N", [(2, 3), (3, 2)])
+def test_axis_permutation_equivariance(orc, d, N):
+    n = (2, 3, 4)[:d]
+    perm = (1, 0) if d == 2 else (2, 0, 1)
+    dom = W.box(d)
+    u = W.random_state(d, N, n, seed=12)
+    du = orc.rhs(d, N, n, dom, u, vflux=0, sflux=0)
+    n_new = tuple(n[perm[k]] for k in range(d))
+    u2 = _permute_state(u, d, N, n, perm)
+    du2 = orc.rhs(d, N, n_new, dom, u2, vflux=0, sflux=0)
+    assert np.max(np.abs(du2 - _permute_state(du, d, N, n, perm))) < 1e-12 * np.max(np.abs(du))
+
+
+@pytest.mark.parametrize("d,N", [(2, 3), (3, 2)])
+def test_rhs_converges_to_exact_time_derivative(orc, d, N):
+    # density wave: d_t rho = -pi A (sum v) cos(pi sum x); rhs -> exact at order ~N
+    xi, _ = orc.lgl(N)
+    errs = []
+    sizes = (4, 8, 16) if d == 2 else (2, 4, 8)
+    for ne in sizes:
+        n = (ne,) * d
+        dom = W.box(d)
+        u = W.density_wave(d, N, n, dom, xi, amplitude=0.5)
+        du = orc.rhs(d, N, n, dom, u, vflux=0, sflux=0).reshape(-1, d + 2, (N + 1) ** d)
+        X = W.node_coordinates(d, N, n, dom, xi)
+        vs = (0.1, 0.2, 0.3)[:d]
+        exact = -np.pi * 0.5 * sum(vs) * np.cos(np.pi * X.sum(axis=0))
+        errs.append(np.max(np.abs(du[:, 0] - exact)))
+    rates = [math.log2(errs[i] / errs[i + 1]) for i in range(len(errs) - 1)]
+    assert rates[-1] > N - 0.7, (errs, rates)
+
+
+def _l2_density_error(orc, d, N, n, dom, u, t, **wave):
+    xi, w = orc.lgl(N)
+    ex = W.density_wave(d, N, n, dom, xi, t=t, **wave).reshape(-1, d + 2, (N + 1) ** d)[:, 0]
+    got = u.reshape(-1, d + 2, (N + 1) ** d)[:, 0]
+    wq = quad_weights(orc, d, N, n, dom).reshape(-1, d + 2, (N + 1) ** d)[:, 0]
+    return math.sqrt(np.sum(wq * (got - ex) ** 2))
+
+
+# Observed orders to T = 1 on 4^2, 8^2, 16^2 elements: LLF gives about N+1 for
+# odd N (4.4 at N=3) and somewhat above N for even N; the EC surface flux
+# gives about N at odd N (the known odd/even behaviour).
+@pytest.mark.parametrize("N,sf,minrate", [(2, 0, 1.9), (3, 0, 3.6), (3, 1, 2.8)])
+def test_eoc_density_wave_2d(orc, N, sf, minrate):
+    d = 2
+    T = 1.0
+    wave = dict(amplitude=0.5, velocity=(0.1, 0.2), pressure=1.0)
+    errs = []
+    for ne in (4, 8, 16):
+        n = (ne, ne)
+        dom = W.box(d)
+        xi, _ = orc.lgl(N)
+        u = W.density_wave(d, N, n, dom, xi, **wave)
+        nsteps = int(math.ceil(T / orc.max_dt(d, N, n, dom, u, cfl=0.5)))
+        dt = T / nsteps
+        for _ in range(nsteps):
+            u = orc.lsrk_step(d, N, n, dom, u, dt, vflux=0, sflux=sf)
+        errs.append(_l2_density_error(orc, d, N, n, dom, u, T, **wave))
+    rates = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert rates[-1] > minrate, (errs, rates)
+
+
+@pytest.mark.parametrize("d,N,n,vf,sf", [(2, 2, (2, 3), 0, 0), (3, 1, (2, 2, 2), 0, 1),
+                                         (2, 3, (2, 2), 1, 2)])
+def test_complex_step_jvp_matches_finite_differences(orc, d, N, n, vf, sf):
+    dom = W.box(d)
+    u = W.random_state(d, N, n, seed=13)
+    v = W.gaussian(u.size, seed=14)
+    jv = orc.rhs_jvp(d, N, n, dom, u, v, vflux=vf, sflux=sf)
+    eps = 1e-6
+    fd = (orc.rhs(d, N, n, dom, u + eps * v, vflux=vf, sflux=sf)
+          - orc.rhs(d, N, n, dom, u - eps * v, vflux=vf, sflux=sf)) / (2 * eps)
+    assert np.linalg.norm(jv - fd) < 1e-6 * np.linalg.norm(jv)
+    # complex step of a linear-in-u quantity is exact: J u for the mass flux
+    # is not linear, so instead check the real part is untouched
+    du = orc.rhs(d, N, n, dom, u, vflux=vf, sflux=sf)
+    assert np.all(np.isfinite(jv)) and np.linalg.norm(du) > 0
+
+
+def test_element_subset_matches_full(orc):
+    d, N, n = 3, 3, (3, 2, 2)
+    dom = W.box(d)
+    u = W.random_state(d, N, n, seed=15)
+    full = orc.rhs(d, N, n, dom, u).reshape(-1, d + 2, (N + 1) ** d)
+    sub = orc.rhs(d, N, n, dom, u, elems=[5, 0, 7]).reshape(-1, d + 2, (N + 1) ** d)
+    for e in (5, 0, 7):
+        assert np.array_equal(sub[e], full[e])
+    assert np.all(sub[1] == 0)
+
+
+def test_max_dt_uniform_state(orc):
+    d, N, n = 3, 3, (4, 5, 6)
+    dom = np.array([-1.0, 1.0, 0.0, 1.0, 0.0, 3.0])
+    u = W.uniform_state(d, N, n, rho=1.3, velocity=(0.3, -0.2, 0.1), pressure=7.0)
+    c = math.sqrt(GAMMA * 7.0 / 1.3)
+    lam = sum((2 / ((dom[2 * k + 1] - dom[2 * k]) / n[k])) * (abs(v) + c)
+              for k, v in enumerate((0.3, -0.2, 0.1)))
+    assert orc.max_dt(d, N, n, dom, u, cfl=0.5) == pytest.approx(0.5 * 2 / ((N + 1) * lam),
+                                                                  rel=1e-14)
+
+
+def test_max_dt_takes_worst_element(orc):
+    d, N, n = 2, 2, (3, 3)
+    dom = W.box(d)
+    u = W.uniform_state(d, N, n).reshape(9, 4, 9)
+    base = orc.max_dt(d, N, n, dom, u.reshape(-1))
+    u2 = u.copy()
+    u2[4, 1, 3] *= 3.0  # faster x-velocity at one node of element 4
+    assert orc.max_dt(d, N, n, dom, u2.reshape(-1)) < base
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_integrals_density_wave(orc, d):
+    # exact integrals over [-1,1]^d: mass 2^d (the sine integrates to zero),
+    # momentum 2^d v, energy 2^d (p/(gamma-1) + |v|^2/2); the LGL residual of
+    # the sine term decays quickly with resolution
+    N = 3
+    vs = (0.1, 0.2, 0.3)[:d]
+    errs = []
+    for ne in (2, 4, 8):
+        n = (ne,) * d
+        dom = W.box(d)
+        xi, _ = orc.lgl(N)
+        u = W.density_wave(d, N, n, dom, xi, velocity=vs)
+        I = orc.integrals(d, N, n, dom, u)
+        vol = 2.0 ** d
+        exact = [vol] + [vol * v for v in vs] + [vol * (20.0 / 0.4 + 0.5 * sum(v * v for v in vs))]
+        errs.append(max(abs(I[k] - exact[k]) for k in range(d + 2)))
+        assert I[d + 3] == pytest.approx(0.5 * vol * sum(v * v for v in vs), rel=1e-12)
+    assert errs[-1] < 1e-12
+
+
+def test_integrals_entropy_against_scipy(orc):
+    # 2D: S = -rho (ln p - gamma ln rho)/(gamma-1) integrated by scipy
+    from scipy import integrate
+    d, N = 2, 4
+    n = (16, 16)
+    dom = W.box(d)
+    xi, _ = orc.lgl(N)
+    u = W.density_wave(d, N, n, dom, xi, amplitude=0.5, velocity=(0.1, 0.2))
+    I = orc.integrals(d, N, n, dom, u)
+
+    def S(y, x):
+        rho = 1 + 0.5 * math.sin(math.pi * (x + y))
+        return -rho * (math.log(20.0) - GAMMA * math.log(rho)) / (GAMMA - 1)
+
+    ref, _ = integrate.dblquad(S, -1, 1, -1, 1, epsabs=1e-13, epsrel=1e-13)
+    assert I[d + 2] == pytest.approx(ref, rel=1e-9)
+
+
+def test_conserved_integrals_constant_in_time(orc):
+    d, N, n = 2, 3, (4, 4)
+    dom = W.box(d)
+    xi, _ = orc.lgl(N)
+    u = W.noisy_density_wave(d, N, n, dom, xi, seed=3, velocity=(0.1, 0.2))
+    I0 = orc.integrals(d, N, n, dom, u)
+    dt = orc.max_dt(d, N, n, dom, u)
+    for _ in range(5):
+        u = orc.lsrk_step(d, N, n, dom, u, dt)
+    I1 = orc.integrals(d, N, n, dom, u)
+    np.testing.assert_allclose(I1[:d + 2], I0[:d + 2], rtol=1e-13, atol=1e-13)
+    assert I1[d + 2] < I0[d + 2]  # LLF dissipates the (mathematical) entropy
