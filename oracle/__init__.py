@@ -51,6 +51,7 @@ def lib():
         L = ctypes.CDLL(_SO)
         L.or_lgl.argtypes = [ctypes.c_int, _dp, _dp]
         L.or_diff_matrix.argtypes = [ctypes.c_int, _dp, _dp]
+        L.or_dtilde.argtypes = [ctypes.c_int, _dp, _dp]
         L.or_lsrk_coefficients.argtypes = [_dp, _dp, _dp]
         L.or_ln_mean.argtypes = [ctypes.c_double, ctypes.c_double]
         L.or_ln_mean.restype = ctypes.c_double
@@ -97,6 +98,15 @@ def diff_matrix(N: int, xi=None):
     D = np.zeros((N + 1, N + 1))
     lib().or_diff_matrix(N, _d(xi), _d(D))
     return D
+
+
+def dtilde(N: int):
+    """Split-form volume matrix Dt = 2 D - W^-1 B (long double, rounded once)."""
+    Dt = np.zeros((N + 1, N + 1))
+    w = np.zeros(N + 1)
+    if lib().or_dtilde(N, _d(Dt), _d(w)) != 0:
+        raise ValueError("bad N")
+    return Dt
 
 
 def lsrk_coefficients():

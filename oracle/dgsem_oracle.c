@@ -27,11 +27,16 @@
  * the published method it cites. Readings of open points are listed in the
  * repository's design notes.
  *
- * Structure: the rhs is evaluated as the textbook split form
+ * Structure: the rhs is the split form of the DGSEM (Fisher-Carpenter;
+ * Gassner-Winters-Kopriva), per node and per coordinate direction,
  *     du_i = -(2/h) [ sum_m 2 D_im f#(u_i, u_m)
- *                     + (delta_iN (F*_R - f(u_i)) - delta_i0 (F*_L - f(u_i))) / w_i ]
- * per node and per coordinate direction, evaluating every two-point flux
- * (both orders, including m = i) and every surface flux once per adjacent
+ *                     + (delta_iN (F*_R - f(u_i)) - delta_i0 (F*_L - f(u_i))) / w_i ],
+ * evaluated in the algebraically identical form
+ *     du_i = -(2/h) [ sum_m Dt_im f#(u_i, u_m) + delta_iN F*_R / w_N - delta_i0 F*_L / w_0 ]
+ * with Dt = 2 D - W^-1 B formed in long double (see or_dtilde): the first
+ * form cancels 2 D_00 f(u_0) against f(u_0)/w_0 in floating point at every
+ * boundary node. Every two-point flux is evaluated for the node it updates
+ * (both orders of each pair, and m = i), every surface flux once per adjacent
  * element. No pair halving, no blocking, no reordering.
  *
  * The file is compiled twice: once with real = double (names or_*), once with
@@ -87,10 +92,10 @@ static void legendre(int N, long double x, long double *p, long double *dp) {
 }
 
 /* Legendre-Gauss-Lobatto nodes xi_0 = -1 < ... < xi_N = 1 (the interior ones
- * are the roots of P_N') and weights w_i = 2 / (N (N+1) P_N(xi_i)^2).
- * Newton iteration on P_N' from Chebyshev-Gauss-Lobatto guesses; P_N'' from
- * Legendre's equation (1-x^2) P'' = 2x P' - N(N+1) P. Returns 0 on success. */
-int or_lgl(int N, double *xi, double *w) {
+ * are the roots of P_N') and weights w_i = 2 / (N (N+1) P_N(xi_i)^2), in long
+ * double. Newton iteration on P_N' from Chebyshev-Gauss-Lobatto guesses;
+ * P_N'' from Legendre's equation (1-x^2) P'' = 2x P' - N(N+1) P. */
+static int lgl_ld(int N, long double *xi, long double *w) {
   if (N < 1 || N > 32) return -1;
   const long double pi = 3.141592653589793238462643383279502884L;
   for (int j = 0; j <= N; ++j) {
@@ -110,33 +115,72 @@ int or_lgl(int N, double *xi, double *w) {
     }
     long double p, dp;
     legendre(N, x, &p, &dp);
-    xi[j] = (double)x;
-    w[j] = (double)(2.0L / ((long double)N * (N + 1) * p * p));
+    xi[j] = x;
+    w[j] = 2.0L / ((long double)N * (N + 1) * p * p);
   }
   return 0;
 }
 
-/* Nodal differentiation matrix D_ij = l_j'(xi_i), row-major D[i*(N+1)+j],
- * from barycentric weights (long double); D_ii = -sum_{j != i} D_ij. */
-int or_diff_matrix(int N, const double *xi, double *D) {
+int or_lgl(int N, double *xi, double *w) {
+  long double x[33], ww[33];
+  if (lgl_ld(N, x, ww)) return -1;
+  for (int j = 0; j <= N; ++j) { xi[j] = (double)x[j]; w[j] = (double)ww[j]; }
+  return 0;
+}
+
+/* Nodal differentiation matrix D_ij = l_j'(xi_i) (row-major, long double) from
+ * barycentric weights; D_ii = -sum_{j != i} D_ij. */
+static int dmat_ld(int N, const long double *xi, long double *D) {
   int np = N + 1;
   long double lam[64];
   if (np > 64) return -1;
   for (int j = 0; j < np; ++j) {
     long double prod = 1.0L;
     for (int k = 0; k < np; ++k)
-      if (k != j) prod *= ((long double)xi[j] - (long double)xi[k]);
+      if (k != j) prod *= (xi[j] - xi[k]);
     lam[j] = 1.0L / prod;
   }
   for (int i = 0; i < np; ++i) {
     long double diag = 0.0L;
     for (int j = 0; j < np; ++j) {
       if (j == i) continue;
-      long double v = (lam[j] / lam[i]) / ((long double)xi[i] - (long double)xi[j]);
-      D[i * np + j] = (double)v;
+      long double v = (lam[j] / lam[i]) / (xi[i] - xi[j]);
+      D[i * np + j] = v;
       diag -= v;
     }
-    D[i * np + i] = (double)diag;
+    D[i * np + i] = diag;
+  }
+  return 0;
+}
+
+/* D as doubles, from the double nodes xi (used by the basis pins). */
+int or_diff_matrix(int N, const double *xi, double *D) {
+  long double x[64], Dl[64 * 64];
+  if (N < 1 || N > 63) return -1;
+  for (int j = 0; j <= N; ++j) x[j] = xi[j];
+  dmat_ld(N, x, Dl);
+  for (int t = 0; t < (N + 1) * (N + 1); ++t) D[t] = (double)Dl[t];
+  return 0;
+}
+
+/* Split-form volume matrix Dt = 2 D - W^-1 B with B = diag(-1, 0, ..., 0, 1),
+ * formed in long double from the long double basis and rounded once. By the
+ * summation-by-parts property W D + (W D)^T = B its diagonal vanishes, and
+ *   sum_m 2 D_im f#(u_i,u_m) - (B_ii / w_i) f(u_i) = sum_m Dt_im f#(u_i,u_m)
+ * since f#(u,u) = f(u); also returns the weights. */
+int or_dtilde(int N, double *Dt, double *w) {
+  long double x[33], ww[33], Dl[33 * 33];
+  if (lgl_ld(N, x, ww)) return -1;
+  dmat_ld(N, x, Dl);
+  int np = N + 1;
+  for (int i = 0; i < np; ++i) {
+    for (int j = 0; j < np; ++j) {
+      long double v = 2.0L * Dl[i * np + j];
+      if (i == j && i == 0) v += 1.0L / ww[0];
+      if (i == j && i == N) v -= 1.0L / ww[N];
+      Dt[i * np + j] = (double)v;
+    }
+    w[i] = (double)ww[i];
   }
   return 0;
 }
@@ -162,7 +206,7 @@ void or_lsrk_coefficients(double *A, double *B, double *c) {
 }
 #else
 int or_lgl(int N, double *xi, double *w);
-int or_diff_matrix(int N, const double *xi, double *D);
+int or_dtilde(int N, double *Dt, double *w);
 #endif
 
 /* ------------------------------------------------------------------------ */
@@ -396,9 +440,8 @@ int OR(rhs)(int d, int N, const int *n, const double *dom, double gamma, int vfl
   if (mesh_init(&m, d, N, n, dom)) return -1;
   two_point_flux fvol = volume_flux_by_id(vflux), fsurf = surface_flux_by_id(sflux);
   if (!fvol || !fsurf) return -1;
-  double xi[16], w[16], D[256];
-  or_lgl(N, xi, w);
-  or_diff_matrix(N, xi, D);
+  double w[16], Dt[256];
+  or_dtilde(N, Dt, w);
   long long count = elems ? n_elems : m.nelem;
 #ifdef _OPENMP
   if (nthreads > 0) omp_set_num_threads(nthreads);
@@ -414,26 +457,24 @@ int OR(rhs)(int d, int N, const int *n, const double *dom, double gamma, int vfl
         int i = node_coord(&m, node, dir);
         real vol[MAXV], f[MAXV], um[MAXV];
         for (int v = 0; v < m.nv; ++v) vol[v] = 0.0;
-        /* volume: sum_m 2 D_im f#(u_i, u_m) along the line */
+        /* volume: sum_m Dt_im f#(u_i, u_m) along the line */
         for (int a = 0; a <= N; ++a) {
           load_node(&m, u, e, node_with(&m, node, dir, a), um);
           fvol(d, dir, gamma, ui, um, f);
-          for (int v = 0; v < m.nv; ++v) vol[v] += 2.0 * D[i * m.np + a] * f[v];
+          for (int v = 0; v < m.nv; ++v) vol[v] += Dt[i * m.np + a] * f[v];
         }
-        /* surface: (F* - f(u_i)) / w_i at the right face, minus at the left */
-        if (i == N || i == 0) {
-          real fi[MAXV], fs[MAXV], uo[MAXV];
-          OR(euler_flux)(d, dir, gamma, ui, fi);
-          if (i == N) {
-            load_node(&m, u, neighbour(&m, e, dir, +1), node_with(&m, node, dir, 0), uo);
-            fsurf(d, dir, gamma, ui, uo, fs);
-            for (int v = 0; v < m.nv; ++v) vol[v] += (fs[v] - fi[v]) / w[N];
-          }
-          if (i == 0) {
-            load_node(&m, u, neighbour(&m, e, dir, -1), node_with(&m, node, dir, N), uo);
-            fsurf(d, dir, gamma, uo, ui, fs);
-            for (int v = 0; v < m.nv; ++v) vol[v] -= (fs[v] - fi[v]) / w[0];
-          }
+        /* surface: + F*_R / w_N at the right face, - F*_L / w_0 at the left */
+        if (i == N) {
+          real fs[MAXV], uo[MAXV];
+          load_node(&m, u, neighbour(&m, e, dir, +1), node_with(&m, node, dir, 0), uo);
+          fsurf(d, dir, gamma, ui, uo, fs);
+          for (int v = 0; v < m.nv; ++v) vol[v] += fs[v] / w[N];
+        }
+        if (i == 0) {
+          real fs[MAXV], uo[MAXV];
+          load_node(&m, u, neighbour(&m, e, dir, -1), node_with(&m, node, dir, N), uo);
+          fsurf(d, dir, gamma, uo, ui, fs);
+          for (int v = 0; v < m.nv; ++v) vol[v] -= fs[v] / w[0];
         }
         for (int v = 0; v < m.nv; ++v) acc[v] -= (2.0 / m.h[dir]) * vol[v];
       }

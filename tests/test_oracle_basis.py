@@ -83,6 +83,21 @@ def test_sbp_property(orc, N):
     assert np.max(np.abs(S + S.T)) < 1e-13 * max(1, N)
 
 
+@pytest.mark.parametrize("N", range(1, 9))
+def test_dtilde(orc, N):
+    # the long double Dt agrees with 2 D - W^-1 B from the double basis, has a
+    # zero diagonal to long double accuracy and W Dt is skew-symmetric
+    xi, w = orc.lgl(N)
+    D = orc.diff_matrix(N)
+    B = np.zeros((N + 1, N + 1))
+    B[0, 0], B[N, N] = -1.0, 1.0
+    Dt = orc.dtilde(N)
+    assert np.max(np.abs(Dt - (2 * D - np.diag(1 / w) @ B))) < 1e-13 * max(1, N * N)
+    assert np.max(np.abs(np.diag(Dt))) < 1e-17 * max(1, N * N)
+    S = np.diag(w) @ Dt
+    assert np.max(np.abs(S + S.T)) < 4e-15 * max(1, N)
+
+
 def _golden_ck():
     A, B, c = [], [], []
     with open(os.path.join(GOLDEN, "carpenter_kennedy_1994.txt")) as fh:
