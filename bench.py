@@ -1,0 +1,419 @@
+#!/usr/bin/env python3
+"""Benchmark of the DGSEM hot path: rhs DOF-evaluations per second (1/PID).
+
+One step = one Carpenter-Kennedy LSRK time step of the 3D compressible Euler
+DGSEM: the CFL time step (one reduction, read back to the host) and five
+stages of rhs (surface-flux kernel + flux-differencing volume kernel with
+lifting) followed by the stage update. The metric counts (N+1)^3 nodes x
+elements x 5 rhs evaluations per step over the wall time (the paper's
+performance index PID = time / (steps 5 elements (N+1)^3), inverted).
+
+Default workload: 3D Euler, N=3, 64^3 periodic elements on [-1,1]^3, density
+wave rho = 1 + 0.98 sin(pi(x+y+z)), v = (0.1,0.2,0.3), p = 20, plus seeded
+uniform 1e-2 noise on rho, v and p (seed 0); Ranocha EC volume flux, LLF
+surface flux. The FP64 path gives `value`; the FP32 kernels (FP64 state and
+RK accumulation) are timed on the same state and reported under "fp32".
+
+`--impl reference` times the plain CPU oracle on a bounded sample of the
+same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "rhs DOF-evals/s (1/PID) 3D Euler N=3, FP32 vs FP64 at stated error; % of FP64 peak"
+UNIT = "DOF-rhs-evals/s"
+
+WORKLOADS = {
+    "euler3d_n3_64cubed_noisy_wave": dict(d=3, N=3, ne=64, noise=1e-2),
+    "euler3d_n3_32cubed_wave": dict(d=3, N=3, ne=32, noise=0.0),
+    "euler3d_n7_24cubed_noisy_wave": dict(d=3, N=7, ne=24, noise=1e-2),
+}
+DEFAULT_WORKLOAD = "euler3d_n3_64cubed_noisy_wave"
+
+# FP64 vector peak derived from the nominal 1.25 TFLOP/s of the part: 2 DFMA
+# per clock per SM x 152 SMs x 2 flops x 2070 MHz. FP32: 128 FMA lanes/SM.
+SMS, SM_MAX_MHZ = 152, 2070.0
+FP64_PEAK_TFLOPS = SMS * 2 * 2 * SM_MAX_MHZ * 1e6 / 1e12
+FP32_PEAK_TFLOPS = SMS * 128 * 2 * SM_MAX_MHZ * 1e6 / 1e12
+
+
+def volume_flops_per_node(d, N):
+    """Algorithmic flops per node of the volume kernel (Ranocha flux; log,
+    division and square root count as one flop each): pairs per node d N / 2,
+    each 46 + 5d flops of flux and 4 (d+2) of accumulation; prologue 3d + 3;
+    lifting 4 d (d+2) / (N+1)."""
+    pair = 46 + 5 * d + 4 * (d + 2)
+    return d * N / 2 * pair + 3 * d + 3 + 4 * d * (d + 2) / (N + 1)
+
+
+def source_sha():
+    h = hashlib.sha1()
+    csrc = os.path.join(ROOT, "paper_2108_06476_gb300", "csrc")
+    for fn in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, fn), "rb") as fh:
+            h.update(fn.encode() + fh.read())
+    return h.hexdigest()[:12]
+
+
+def ncu_traffic(key):
+    """DRAM bytes per node of a kernel from a committed ncu summary, or None
+    when the kernels changed since that capture."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic.json")
+    try:
+        with open(path) as fh:
+            rec = json.load(fh).get(key)
+    except (OSError, ValueError):
+        return None
+    if not rec or rec.get("src_sha") != source_sha():
+        return None
+    return rec.get("bytes_per_node")
+
+
+class ClockSampler:
+    """Samples nvidia-smi SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.lines = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[4:8]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def make_state(spec, xi, seed=0):
+    from paper_2108_06476_gb300 import workloads as W
+    d, N, ne = spec["d"], spec["N"], spec["ne"]
+    n = (ne,) * d
+    dom = W.box(d)
+    if spec["noise"] > 0:
+        return W.noisy_density_wave(d, N, n, dom, xi, seed=seed, noise=spec["noise"])
+    return W.density_wave(d, N, n, dom, xi)
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def run_reference(args, spec, world, rank):
+    """The plain CPU oracle on a bounded sample of the workload's elements:
+    each step = 5 x (oracle rhs on the sample + oracle stage update of the
+    sample's values)."""
+    if rank != 0:
+        return
+    import numpy as np
+    import oracle
+    oracle.build()
+    d, N, ne = spec["d"], spec["N"], spec["ne"]
+    n = (ne,) * d
+    from paper_2108_06476_gb300 import workloads as W
+    dom = W.box(d)
+    xi, _ = oracle.lgl(N)
+    u = make_state(spec, xi)
+    P, nv = (N + 1) ** d, d + 2
+    nelem = ne ** d
+    cores = os.cpu_count() or 1
+    # size the sample: about 1.5 s of oracle work per step
+    probe = np.arange(0, nelem, max(1, nelem // 256))[:256]
+    du = np.zeros_like(u)
+    t = time.perf_counter()
+    oracle.rhs(d, N, n, dom, u, elems=probe, out=du)
+    per_elem = (time.perf_counter() - t) / len(probe)
+    count = int(min(nelem, max(64, 0.3 / max(per_elem, 1e-9))))
+    rng = np.random.default_rng(1)
+    elems = np.sort(rng.choice(nelem, size=count, replace=False))
+    A, B, _ = oracle.lsrk_coefficients()
+    uu = u.reshape(nelem, nv * P)
+    k = np.zeros((count, nv * P))
+    dt = 1e-5
+
+    def step():
+        for s in range(5):
+            oracle.rhs(d, N, n, dom, u, elems=elems, out=du)
+            us = np.ascontiguousarray(uu[elems])
+            ds = np.ascontiguousarray(du.reshape(nelem, nv * P)[elems])
+            oracle.rk_stage(us, k, ds, A[s], B[s], dt)
+            uu[elems] = us
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    el = time.perf_counter() - t0
+    value = count * P * 5 * args.steps / el
+    sample = (f"{count} of {nelem} elements ({count * P} of {nelem * P} nodes) of {args.workload}, "
+              f"5 rhs + 5 stage updates per step")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": el / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "d": d, "N": N, "elements_per_dim": ne,
+                       "volume_flux": "ranocha", "surface_flux": "llf"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline(spec, xi, u):
+    """The oracle's rhs on a bounded sample of the workload (about 10 s with
+    all host cores)."""
+    import numpy as np
+    import oracle
+    oracle.build()
+    d, N, ne = spec["d"], spec["N"], spec["ne"]
+    n = (ne,) * d
+    from paper_2108_06476_gb300 import workloads as W
+    dom = W.box(d)
+    nelem = ne ** d
+    P = (N + 1) ** d
+    du = np.zeros_like(u)
+    probe = np.arange(0, nelem, max(1, nelem // 512))[:512]
+    t = time.perf_counter()
+    oracle.rhs(d, N, n, dom, u, elems=probe, out=du)
+    per_elem = (time.perf_counter() - t) / len(probe)
+    count = int(min(nelem, max(512, 10.0 / max(per_elem, 1e-9))))
+    elems = np.sort(np.random.default_rng(2).choice(nelem, size=count, replace=False))
+    t = time.perf_counter()
+    oracle.rhs(d, N, n, dom, u, elems=elems, out=du)
+    el = time.perf_counter() - t
+    return {"value": count * P / el, "unit": UNIT, "cores": os.cpu_count() or 1,
+            "kind": "oracle",
+            "sample": f"one oracle rhs over {count} of {nelem} elements ({count * P} nodes), "
+                      f"{el:.1f} s, OpenMP on all host cores"}
+
+
+def run_ours(args, spec, world, rank, local):
+    import numpy as np
+    import torch
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    from paper_2108_06476_gb300 import Mesh, lgl_nodes, build as dgbuild
+    dgbuild.build()
+    d, N, ne = spec["d"], spec["N"], spec["ne"]
+    n = (ne,) * d
+    xi, _ = lgl_nodes(N)
+    u_host = make_state(spec, xi, seed=rank)
+    M = ne ** d * (N + 1) ** d
+    mesh = Mesh(d, N, n, precision="fp64")
+    u0 = torch.from_numpy(u_host).cuda()
+    u = u0.clone()
+    du = mesh.empty_rhs()
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+
+    def run_steps(m, uu, dd, k):
+        for _ in range(k):
+            dt = m.max_dt(uu, cfl=0.5)
+            m.step(uu, dt, dd)
+
+    def timed(fn):
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        barrier()
+        ms = e0.elapsed_time(e1)
+        if dist is not None:
+            t = torch.tensor([ms], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms
+
+    # ---- FP64: headline ----
+    run_steps(mesh, u, du, args.warmup)
+    with ClockSampler(local) as clk:
+        ms = timed(lambda: run_steps(mesh, u, du, args.steps))
+    mesh.check()
+    value = M * 5 * args.steps * world / (ms / 1e3)
+    launches_per_step = 1 + 5 * 3
+
+    # ---- kernel timings (dominant kernel: volume) ----
+    def kernel_ms(m, uu, dd, part, reps=10):
+        m.rhs_part(uu, dd, 1)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            m.rhs_part(uu, dd, part)
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    u.copy_(u0)
+    vol_ms = kernel_ms(mesh, u, du, 2)
+    surf_ms = kernel_ms(mesh, u, du, 1)
+    flops_node = volume_flops_per_node(d, N)
+    achieved = flops_node * M / (vol_ms / 1e3) / 1e12
+    traffic = ncu_traffic(f"fp64_volume_{d}d_n{N}")
+
+    # ---- FP32 kernels with FP64 state and RK accumulation ----
+    fp32 = None
+    if not args.no_fp32:
+        mesh32 = Mesh(d, N, n, precision="fp32")
+        u32 = u0.clone()
+        du32 = mesh32.empty_rhs()
+        ref64 = mesh.rhs(u0).double()
+        r32 = mesh32.rhs(u0, du32).double()
+        err32 = float(torch.linalg.norm(r32 - ref64) / torch.linalg.norm(ref64))
+        run_steps(mesh32, u32, du32, args.warmup)
+        ms32 = timed(lambda: run_steps(mesh32, u32, du32, args.steps))
+        mesh32.check()
+        u32.copy_(u0)
+        vol32 = kernel_ms(mesh32, u32, du32, 2)
+        fp32 = {"value": M * 5 * args.steps * world / (ms32 / 1e3), "unit": UNIT,
+                "ms_per_step": ms32 / args.steps, "speedup_vs_fp64": ms / ms32,
+                "rhs_rel_l2_vs_fp64": err32,
+                "volume_kernel_ms": vol32,
+                "volume_tflops": flops_node * M / (vol32 / 1e3) / 1e12,
+                "volume_frac_of_fp32_peak": flops_node * M / (vol32 / 1e3) / 1e12
+                / FP32_PEAK_TFLOPS}
+        del mesh32, u32, du32
+
+    # ---- end to end through the public API with host buffers ----
+    e2e = None
+    if not args.no_e2e:
+        uh = torch.empty(u0.numel(), dtype=torch.float64, pin_memory=True)
+        uh.copy_(u0.cpu())
+        ud = torch.empty_like(u0)
+
+        def e2e_steps(k):
+            for _ in range(k):
+                ud.copy_(uh, non_blocking=True)
+                dt = mesh.max_dt(ud, cfl=0.5)
+                mesh.step(ud, dt, du)
+                uh.copy_(ud, non_blocking=True)
+
+        e2e_steps(1)
+        ms_e = timed(lambda: e2e_steps(args.steps))
+        nbytes = u0.numel() * 8
+        e2e = {"value": M * 5 * args.steps * world / (ms_e / 1e3), "unit": UNIT,
+               "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "d": d, "N": N, "elements_per_dim": ne,
+                   "nodes": M, "volume_flux": "ranocha", "surface_flux": "llf", "cfl": 0.5,
+                   "parallelism": f"replicas{world}" if world > 1 else "single",
+                   "l2": "inputs larger than L2 (state alone is "
+                         f"{M * (d + 2) * 8 / 1e6:.0f} MB per buffer)"},
+        "gpu_launches": launches_per_step * args.steps,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+                     "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+                     "traffic": None if traffic is None else traffic * M,
+                     "kernel": "volume_kernel (FP64)",
+                     "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz "
+                                    "(nominal 1.25 TFLOP/s FP64)",
+                     "flops_per_node": flops_node, "kernel_ms": vol_ms},
+        "kernels_ms": {"volume": vol_ms, "surface": surf_ms},
+        "fp32": fp32,
+        "e2e": e2e,
+        "clocks": clk.summary(),
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(spec, xi, u_host)
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default=DEFAULT_WORKLOAD)
+    ap.add_argument("--no-fp32", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    spec = WORKLOADS[args.workload]
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, spec, world, rank)
+    else:
+        run_ours(args, spec, world, rank, local)
+
+
+if __name__ == "__main__":
+    main()

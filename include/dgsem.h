@@ -1,0 +1,144 @@
+/*
+ * dgsem.h - C ABI of the GB300 (sm_103a) DGSEM library: the right-hand side
+ * du/dt = rhs(u) of the discontinuous Galerkin spectral element method for the
+ * 2D/3D compressible Euler equations (ideal gas) on a uniform periodic
+ * Cartesian mesh, and the low-storage Runge-Kutta stage that consumes it.
+ *
+ * Paper: H. Ranocha et al., "Adaptive numerical simulations with Trixi.jl: A
+ * case study of Julia for scientific computing" (2021).
+ *   - conservation law d_t u + sum_j d_xj f^j(u) = 0: Sec. 2, Eq. (1);
+ *   - DGSEM on LGL nodes, entropy-conservative flux differencing with the
+ *     Ranocha EC/KEP two-point flux: Sec. 2.1 and Sec. 3.1;
+ *   - surface fluxes (local Lax-Friedrichs, EC, HLL): Sec. 2.2, Sec. 3.1;
+ *   - Carpenter-Kennedy 5-stage 4th-order low-storage RK and the CFL time
+ *     step: Sec. 3.1; performance index PID: Sec. 3.1, Eq. (3);
+ *   - analysis integrals: Sec. 2.2.
+ *
+ * Conventions shared by every entry point:
+ *   - State layout u[e][v][k][j][i]: element-major; inside an element the
+ *     d+2 conserved variables (rho, rho v_1..rho v_d, E) one after another,
+ *     each as (N+1)^d nodal values with i (x) fastest. Elements are ordered
+ *     lexicographically with x fastest: e = ex + n0 (ey + n1 ez). Element
+ *     (ex, ey, ez) covers [lo + ex h, lo + (ex+1) h] in each direction.
+ *   - Buffers passed to compute calls are DEVICE pointers owned by the caller
+ *     (the library never frees them), at least 16-byte aligned. The state u
+ *     is always float64. The rhs output du is float64 in DG_FP64 precision and
+ *     float32 in DG_FP32 precision.
+ *   - The library owns the mesh object and its device scratch: the RK
+ *     register k, the surface-flux buffer, the reduction partials and a
+ *     device error word.
+ *   - Compute calls are asynchronous on the mesh's CUDA stream unless they
+ *     return host values (dg_max_dt, dg_integrals, dg_mesh_check), which
+ *     synchronise that stream.
+ *   - Every call returns a dg_status; nothing is thrown or aborted across the
+ *     ABI. dg_last_error() gives a thread-local message for the last failure.
+ */
+#ifndef DGSEM_H
+#define DGSEM_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dg_mesh dg_mesh; /* opaque, library-owned */
+
+typedef enum {
+  DG_OK = 0,
+  DG_ERR_ARG = -1,         /* invalid argument: handle, size, pointer, option */
+  DG_ERR_CUDA = -2,        /* a CUDA runtime call failed */
+  DG_ERR_OOM = -3,         /* device allocation failed */
+  DG_ERR_NONPHYSICAL = -4, /* rho <= 0, p <= 0 or a non-finite value was met */
+  DG_ERR_TIMEOUT = -5      /* a bounded device wait gave up */
+} dg_status;
+
+/* Two-point volume fluxes (flux differencing, Sec. 2.1/3.1). */
+enum { DG_VFLUX_RANOCHA = 0, DG_VFLUX_CHANDRASHEKAR = 1, DG_VFLUX_CENTRAL = 2 };
+/* Surface fluxes. LLF wave speed: max(|v_n,L|, |v_n,R|) + max(c_L, c_R). */
+enum { DG_SFLUX_LLF = 0, DG_SFLUX_RANOCHA = 1, DG_SFLUX_HLL = 2, DG_SFLUX_CHANDRASHEKAR = 3 };
+/* Arithmetic of the rhs kernels. RK accumulation and reductions are FP64. */
+enum { DG_FP64 = 0, DG_FP32 = 1 };
+
+typedef struct {
+  double gamma;     /* ratio of specific heats, > 1 */
+  int volume_flux;  /* DG_VFLUX_* */
+  int surface_flux; /* DG_SFLUX_* */
+  int precision;    /* DG_FP64 or DG_FP32 */
+} dg_options;
+
+/* Create a uniform periodic Cartesian mesh of elements_per_dim[0] x ... x
+ * elements_per_dim[d-1] elements of polynomial degree N on the box
+ * domain = {lo_0, hi_0, lo_1, hi_1[, lo_2, hi_2]}.
+ * d in {2, 3}; 1 <= N <= 7; every elements_per_dim[k] >= 1; lo_k < hi_k.
+ * opt NULL selects gamma = 1.4, Ranocha volume flux, LLF surface flux, FP64.
+ * cuda_stream is a cudaStream_t (NULL = legacy default stream).
+ * Allocates the library-owned device buffers. Errors: DG_ERR_ARG, DG_ERR_OOM,
+ * DG_ERR_CUDA; *out is NULL on failure. */
+int dg_mesh_create(int d, int N, const int *elements_per_dim, const double *domain,
+                   const dg_options *opt, void *cuda_stream, dg_mesh **out);
+
+/* Free the mesh and its device buffers (after synchronising its stream).
+ * NULL is accepted. */
+int dg_mesh_destroy(dg_mesh *mesh);
+
+/* Sizes: nodes M = n_elem (N+1)^d, variables d+2, values (d+2) M. */
+int dg_mesh_info(const dg_mesh *mesh, long long *n_nodes, int *n_vars, long long *n_values);
+
+/* Change the CUDA stream used by subsequent calls on this mesh. */
+int dg_mesh_set_stream(dg_mesh *mesh, void *cuda_stream);
+
+/* The library's own LGL nodes xi[N+1] and weights w[N+1] (host arrays),
+ * computed in long double and rounded (basis of Sec. 2.1's DGSEM). */
+int dg_lgl_nodes(int N, double *xi, double *w);
+
+/* du = rhs(u) (Sec. 2.1 DGSEM, Eq. (1) with s = 0): split-form flux
+ * differencing in the volume, surface flux at every interface, lifting and
+ * inverse-Jacobian scaling. u: device float64[n_values]; du: device
+ * float64 (DG_FP64) or float32 (DG_FP32) [n_values]. Asynchronous.
+ * Non-physical states set the device error word (see dg_mesh_check). */
+int dg_rhs(dg_mesh *mesh, const double *u, void *du);
+
+/* One kernel of dg_rhs, for timing the two kernels separately: parts = 1
+ * launches only the surface-flux kernel (fills the library's face buffer),
+ * parts = 2 only the volume kernel with lifting (reads the face buffer of the
+ * previous part-1 call on the same u), parts = 3 both (same as dg_rhs).
+ * Asynchronous. */
+int dg_rhs_part(dg_mesh *mesh, const double *u, void *du, int parts);
+
+/* One stage of the Carpenter-Kennedy 2N-storage scheme (Sec. 3.1):
+ * k <- a k + dt du; u <- u + b k, with the library-owned register k
+ * (zeroed at creation and by dg_rk_reset). du has the rhs dtype of the mesh.
+ * Asynchronous. */
+int dg_rk_stage(dg_mesh *mesh, double *u, const void *du, double a, double b, double dt);
+
+/* Zero the RK register k (start of a new integration). Asynchronous. */
+int dg_rk_reset(dg_mesh *mesh);
+
+/* One full LSRK step (5 stages of dg_rhs + dg_rk_stage with the published
+ * Carpenter-Kennedy coefficients) using the caller's du buffer as scratch.
+ * Asynchronous. */
+int dg_step(dg_mesh *mesh, double *u, void *du, double dt);
+
+/* CFL time step (Sec. 3.1): dt = cfl * 2 / ((N+1) max_e sum_k (2/h_k)
+ * max_nodes(|v_k| + c)), c = sqrt(gamma p / rho). Synchronises the stream;
+ * returns DG_ERR_NONPHYSICAL if the state is not physical. */
+int dg_max_dt(dg_mesh *mesh, const double *u, double cfl, double *dt_out);
+
+/* Integrals over the domain by each element's LGL quadrature (Sec. 2.2
+ * analysis quantities): out[d+4] (host) = rho, rho v_1..rho v_d, E,
+ * entropy S = -rho (ln p - gamma ln rho)/(gamma-1), kinetic energy
+ * rho |v|^2 / 2. Compensated (double-double) reductions in FP64.
+ * Synchronises the stream. */
+int dg_integrals(dg_mesh *mesh, const double *u, double *out);
+
+/* Synchronise the mesh's stream and report the device error word:
+ * *flags (may be NULL) receives its bits (1 = rho <= 0, 2 = p <= 0,
+ * 4 = non-finite); returns DG_ERR_NONPHYSICAL if any is set, and clears it. */
+int dg_mesh_check(dg_mesh *mesh, int *flags);
+
+/* Thread-local description of the last failed call ("" if none). */
+const char *dg_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DGSEM_H */

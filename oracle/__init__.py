@@ -148,11 +148,17 @@ def _elems(elems):
     return e.ctypes.data_as(_llp), len(e), e
 
 
-def rhs(d, N, n, dom, u, gamma=1.4, vflux=RANOCHA, sflux=S_LLF, elems=None, nthreads=0):
-    """du = rhs(u) (all elements, or only `elems`; other entries of du are 0)."""
+def rhs(d, N, n, dom, u, gamma=1.4, vflux=RANOCHA, sflux=S_LLF, elems=None, nthreads=0,
+        out=None):
+    """du = rhs(u) (all elements, or only `elems`; other entries of du are 0,
+    or left as they are in `out` when an output buffer is given)."""
     n_arr, dom = _mesh_args(d, n, dom)
     u = _f64(u)
-    du = np.zeros_like(u)
+    if out is not None:
+        assert out.dtype == np.float64 and out.flags.c_contiguous and out.shape == u.shape
+        du = out
+    else:
+        du = np.zeros_like(u)
     ep, ne, keep = _elems(elems)
     rc = lib().or_rhs(d, N, n_arr, _d(dom), gamma, vflux, sflux, _d(u), _d(du), ep, ne,
                       nthreads)

@@ -1,0 +1,593 @@
+// C ABI of the DGSEM library (declared in include/dgsem.h): mesh set-up with
+// the LGL basis, rhs dispatch, the Carpenter-Kennedy stage update, the CFL
+// time step and the compensated integrals.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include "dgsem.h"
+#include "dg_device.cuh"
+
+namespace dg {
+cudaError_t rhs_launch_double_2(int, const double*, double*, double*, const Geom&,
+                                const Tables<double>&, int, int, unsigned*, cudaStream_t, int);
+cudaError_t rhs_launch_double_3(int, const double*, double*, double*, const Geom&,
+                                const Tables<double>&, int, int, unsigned*, cudaStream_t, int);
+cudaError_t rhs_launch_float_2(int, const double*, float*, float*, const Geom&,
+                               const Tables<float>&, int, int, unsigned*, cudaStream_t, int);
+cudaError_t rhs_launch_float_3(int, const double*, float*, float*, const Geom&,
+                               const Tables<float>&, int, int, unsigned*, cudaStream_t, int);
+}  // namespace dg
+
+using dg::Geom;
+using dg::Tables;
+
+struct dg_mesh {
+  int d, N, np, nv;
+  int n[3];
+  double dom[6];
+  double h[3];
+  long long nelem, P, nnodes, nvalues;
+  dg_options opt;
+  cudaStream_t stream;
+  Geom geom;
+  Tables<double> t64;
+  Tables<float> t32;
+  double w[dg::kNPMax];
+  double* k;           // RK register, nvalues doubles
+  void* fs;            // face-flux buffer, d * nv * nelem * (N+1)^(d-1) values
+  double* wq;          // quadrature weight of each node of an element, P doubles
+  double* partials;    // integral partials, kRedBlocks * 7 * 2 doubles
+  double* red_out;     // 7 * 2 doubles
+  unsigned long long* speed;  // max wave-speed sum (as ordered bits)
+  unsigned* err;       // device error word
+};
+
+namespace {
+
+thread_local char g_last_error[512] = "";
+
+int fail(int code, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_last_error, sizeof(g_last_error), fmt, ap);
+  va_end(ap);
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+  return fail(e == cudaErrorMemoryAllocation ? DG_ERR_OOM : DG_ERR_CUDA, "%s: %s", what,
+              cudaGetErrorString(e));
+}
+
+#define DG_CUDA(call, what)                     \
+  do {                                          \
+    cudaError_t e_ = (call);                    \
+    if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+  } while (0)
+
+constexpr int kRedBlocks = 608;  // 4 x 152 SMs
+constexpr int kRedThreads = 256;
+
+// ---- LGL basis in long double ----
+// Legendre P_n(x) by the three-term recurrence.
+long double legendre_p(int n, long double x) {
+  if (n == 0) return 1.0L;
+  long double a = 1.0L, b = x;
+  for (int k = 1; k < n; ++k) {
+    long double c = ((2.0L * k + 1.0L) * x * b - k * a) / (k + 1.0L);
+    a = b;
+    b = c;
+  }
+  return b;
+}
+
+// LGL nodes are the zeros of q(x) = P_{N+1}(x) - P_{N-1}(x) = (2N+1) int P_N,
+// with q'(x) = (2N+1) P_N(x); Newton from Chebyshev-Gauss-Lobatto guesses.
+// Weights w_j = 2 / (N (N+1) P_N(x_j)^2).
+void lgl_basis(int N, long double* x, long double* w) {
+  const long double pi = 3.14159265358979323846264338327950288L;
+  for (int j = 0; j <= N; ++j) {
+    long double t = -cosl(pi * j / N);
+    if (j > 0 && j < N) {
+      for (int it = 0; it < 200; ++it) {
+        long double q = legendre_p(N + 1, t) - legendre_p(N - 1, t);
+        long double dq = (2.0L * N + 1.0L) * legendre_p(N, t);
+        long double step = q / dq;
+        t -= step;
+        if (fabsl(step) <= 1e-32L) break;
+      }
+    }
+    x[j] = t;
+    long double pn = legendre_p(N, t);
+    w[j] = 2.0L / ((long double)N * (N + 1) * pn * pn);
+  }
+  x[0] = -1.0L;
+  x[N] = 1.0L;
+}
+
+// Split-form matrix Dt = 2 D - W^-1 B from the closed-form LGL
+// differentiation matrix D_ij = P_N(x_i) / (P_N(x_j) (x_i - x_j)) (i != j),
+// D_00 = -N(N+1)/4, D_NN = N(N+1)/4, other diagonal entries 0.
+void split_matrix(int N, const long double* x, const long double* w, long double Dt[8][8]) {
+  for (int i = 0; i <= N; ++i) {
+    for (int j = 0; j <= N; ++j) {
+      long double dij;
+      if (i != j) dij = legendre_p(N, x[i]) / (legendre_p(N, x[j]) * (x[i] - x[j]));
+      else if (i == 0) dij = -(long double)N * (N + 1) / 4.0L;
+      else if (i == N) dij = (long double)N * (N + 1) / 4.0L;
+      else dij = 0.0L;
+      long double b = (i == j && i == 0) ? -1.0L : (i == j && i == N) ? 1.0L : 0.0L;
+      Dt[i][j] = 2.0L * dij - b / w[i];
+    }
+  }
+}
+
+// Carpenter & Kennedy (1994) five-stage fourth-order 2N-storage scheme.
+const double kRkA[5] = {0.0, -567301805773.0 / 1357537059087.0,
+                        -2404267990393.0 / 2016746695238.0,
+                        -3550918686646.0 / 2091501179385.0,
+                        -1275806237668.0 / 842570457699.0};
+const double kRkB[5] = {1432997174477.0 / 9575080441755.0, 5161836677717.0 / 13612068292357.0,
+                        1720146321549.0 / 2090206949498.0, 3134564353537.0 / 4481467310338.0,
+                        2277821191437.0 / 14882151754819.0};
+
+// ---- kernels ----
+template <typename RD>
+__global__ void rk_stage_kernel(double* __restrict__ u, double* __restrict__ k,
+                                const RD* __restrict__ du, double a, double b, double dt,
+                                long long n) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  const long long n2 = n / 2;
+  double2* u2 = reinterpret_cast<double2*>(u);
+  double2* k2 = reinterpret_cast<double2*>(k);
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += stride) {
+    double2 kk = k2[i], uu = u2[i];
+    double d0, d1;
+    if (sizeof(RD) == 8) {
+      const double2 dd = reinterpret_cast<const double2*>(du)[i];
+      d0 = dd.x;
+      d1 = dd.y;
+    } else {
+      const float2 dd = reinterpret_cast<const float2*>(du)[i];
+      d0 = dd.x;
+      d1 = dd.y;
+    }
+    kk.x = a * kk.x + dt * d0;
+    kk.y = a * kk.y + dt * d1;
+    uu.x = uu.x + b * kk.x;
+    uu.y = uu.y + b * kk.y;
+    k2[i] = kk;
+    u2[i] = uu;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0 && (n & 1)) {
+    const long long i = n - 1;
+    const double kk = a * k[i] + dt * (double)du[i];
+    k[i] = kk;
+    u[i] = u[i] + b * kk;
+  }
+}
+
+// Max over elements of sum_k (2/h_k) max_nodes(|v_k| + c); one warp per
+// element, one atomic per block on the ordered bit pattern of the result.
+template <int D>
+__global__ void speed_kernel(const double* __restrict__ u, Geom g, int P, double s0, double s1,
+                             double s2, unsigned long long* out, unsigned* err) {
+  constexpr int NV = D + 2;
+  const int lane = threadIdx.x & 31;
+  const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  const double gm1 = g.gamma - 1.0;
+  double best = 0.0;
+  unsigned bad = 0;
+  for (long long e = warp; e < g.nelem; e += nwarps) {
+    double lam[3] = {0.0, 0.0, 0.0};
+    for (int node = lane; node < P; node += 32) {
+      double c[NV];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) c[v] = u[(e * NV + v) * P + node];
+      const dg::Prim<double, D> q = dg::cons2prim<double, D>(c, gm1);
+      bad |= dg::prim_check(q);
+      const double cs = sqrt(g.gamma * q.p / q.rho);
+#pragma unroll
+      for (int k = 0; k < D; ++k) lam[k] = fmax(lam[k], fabs(q.v[k]) + cs);
+    }
+#pragma unroll
+    for (int k = 0; k < D; ++k)
+      for (int off = 16; off > 0; off >>= 1)
+        lam[k] = fmax(lam[k], __shfl_xor_sync(0xffffffffu, lam[k], off));
+    double s = s0 * lam[0];
+    s = s + s1 * lam[1];
+    if (D == 3) s = s + s2 * lam[2];
+    best = fmax(best, s);
+  }
+  __shared__ double sb[32];
+  if (lane == 0) sb[threadIdx.x >> 5] = best;
+  if (bad) atomicOr(err, bad);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double m = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmax(m, sb[w]);
+    atomicMax(out, (unsigned long long)__double_as_longlong(m));
+  }
+}
+
+// double-double accumulation (Knuth two-sum)
+struct dd {
+  double hi, lo;
+};
+__device__ __forceinline__ dd dd_add(dd a, dd b) {
+  const double s = a.hi + b.hi;
+  const double bb = s - a.hi;
+  const double err = (a.hi - (s - bb)) + (b.hi - bb);
+  const double lo = a.lo + b.lo + err;
+  const double hi = s + lo;
+  return dd{hi, lo - (hi - s)};
+}
+__device__ __forceinline__ dd dd_add1(dd a, double x) { return dd_add(a, dd{x, 0.0}); }
+
+template <int D>
+__global__ void integrals_kernel(const double* __restrict__ u, Geom g, int P,
+                                 const double* __restrict__ wq, double* __restrict__ partials,
+                                 unsigned* err) {
+  constexpr int NV = D + 2, NQ = D + 4;
+  dd acc[NQ];
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) acc[q] = dd{0.0, 0.0};
+  const long long total = g.nelem * P;
+  const double gm1 = g.gamma - 1.0;
+  unsigned bad = 0;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const long long e = t / P;
+    const int node = (int)(t % P);
+    double c[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) c[v] = u[(e * NV + v) * P + node];
+    const dg::Prim<double, D> q = dg::cons2prim<double, D>(c, gm1);
+    bad |= dg::prim_check(q);
+    const double w = wq[node];
+    double v2 = 0.0;
+#pragma unroll
+    for (int k = 0; k < D; ++k) v2 += q.v[k] * q.v[k];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) acc[v] = dd_add1(acc[v], w * c[v]);
+    acc[NV] = dd_add1(acc[NV], w * (-q.rho * (log(q.p) - g.gamma * log(q.rho)) / gm1));
+    acc[NV + 1] = dd_add1(acc[NV + 1], w * (0.5 * q.rho * v2));
+  }
+  if (bad) atomicOr(err, bad);
+  __shared__ double sh[kRedThreads][2];
+  for (int q = 0; q < NQ; ++q) {
+    sh[threadIdx.x][0] = acc[q].hi;
+    sh[threadIdx.x][1] = acc[q].lo;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+      if ((int)threadIdx.x < s) {
+        dd r = dd_add(dd{sh[threadIdx.x][0], sh[threadIdx.x][1]},
+                      dd{sh[threadIdx.x + s][0], sh[threadIdx.x + s][1]});
+        sh[threadIdx.x][0] = r.hi;
+        sh[threadIdx.x][1] = r.lo;
+      }
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+      partials[(blockIdx.x * 7 + q) * 2 + 0] = sh[0][0];
+      partials[(blockIdx.x * 7 + q) * 2 + 1] = sh[0][1];
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void integrals_final_kernel(const double* __restrict__ partials, int nblocks, int nq,
+                                       double* __restrict__ out) {
+  __shared__ double sh[kRedThreads][2];
+  for (int q = 0; q < nq; ++q) {
+    dd a{0.0, 0.0};
+    for (int b = threadIdx.x; b < nblocks; b += blockDim.x)
+      a = dd_add(a, dd{partials[(b * 7 + q) * 2], partials[(b * 7 + q) * 2 + 1]});
+    sh[threadIdx.x][0] = a.hi;
+    sh[threadIdx.x][1] = a.lo;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+      if ((int)threadIdx.x < s) {
+        dd r = dd_add(dd{sh[threadIdx.x][0], sh[threadIdx.x][1]},
+                      dd{sh[threadIdx.x + s][0], sh[threadIdx.x + s][1]});
+        sh[threadIdx.x][0] = r.hi;
+        sh[threadIdx.x][1] = r.lo;
+      }
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+      out[2 * q] = sh[0][0];
+      out[2 * q + 1] = sh[0][1];
+    }
+    __syncthreads();
+  }
+}
+
+bool valid_mesh(const dg_mesh* m) { return m != nullptr && m->k != nullptr; }
+
+int grid_for(long long work, int threads) {
+  long long b = (work + threads - 1) / threads;
+  if (b > 152LL * 32) b = 152LL * 32;
+  if (b < 1) b = 1;
+  return (int)b;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* dg_last_error(void) { return g_last_error; }
+
+int dg_lgl_nodes(int N, double* xi, double* w) {
+  if (N < 1 || N > 7 || !xi || !w) return fail(DG_ERR_ARG, "dg_lgl_nodes: N must be in [1, 7]");
+  long double x[8], ww[8];
+  lgl_basis(N, x, ww);
+  for (int j = 0; j <= N; ++j) {
+    xi[j] = (double)x[j];
+    w[j] = (double)ww[j];
+  }
+  return DG_OK;
+}
+
+int dg_mesh_create(int d, int N, const int* epd, const double* domain, const dg_options* opt,
+                   void* cuda_stream, dg_mesh** out) {
+  if (out) *out = nullptr;
+  if (!out || !epd || !domain) return fail(DG_ERR_ARG, "dg_mesh_create: null argument");
+  if (d < 2 || d > 3) return fail(DG_ERR_ARG, "dg_mesh_create: d must be 2 or 3 (got %d)", d);
+  if (N < 1 || N > 7) return fail(DG_ERR_ARG, "dg_mesh_create: N must be in [1, 7] (got %d)", N);
+  dg_options o = {1.4, DG_VFLUX_RANOCHA, DG_SFLUX_LLF, DG_FP64};
+  if (opt) o = *opt;
+  if (!(o.gamma > 1.0) || o.volume_flux < 0 || o.volume_flux > 2 || o.surface_flux < 0 ||
+      o.surface_flux > 3 || (o.precision != DG_FP64 && o.precision != DG_FP32))
+    return fail(DG_ERR_ARG, "dg_mesh_create: invalid options");
+  dg_mesh* m = new dg_mesh();
+  memset(m, 0, sizeof(*m));
+  m->d = d;
+  m->N = N;
+  m->np = N + 1;
+  m->nv = d + 2;
+  m->opt = o;
+  m->stream = (cudaStream_t)cuda_stream;
+  m->nelem = 1;
+  m->P = 1;
+  for (int k = 0; k < 3; ++k) {
+    m->n[k] = 1;
+    m->h[k] = 1.0;
+  }
+  for (int k = 0; k < d; ++k) {
+    if (epd[k] < 1 || !(domain[2 * k + 1] > domain[2 * k])) {
+      delete m;
+      return fail(DG_ERR_ARG, "dg_mesh_create: bad elements_per_dim or domain in direction %d", k);
+    }
+    m->n[k] = epd[k];
+    m->dom[2 * k] = domain[2 * k];
+    m->dom[2 * k + 1] = domain[2 * k + 1];
+    m->h[k] = (domain[2 * k + 1] - domain[2 * k]) / epd[k];
+    m->nelem *= epd[k];
+    m->P *= m->np;
+  }
+  if (m->nelem > (1LL << 31)) {
+    delete m;
+    return fail(DG_ERR_ARG, "dg_mesh_create: too many elements");
+  }
+  m->nnodes = m->nelem * m->P;
+  m->nvalues = m->nnodes * m->nv;
+  m->geom.n[0] = m->n[0];
+  m->geom.n[1] = m->n[1];
+  m->geom.n[2] = m->n[2];
+  m->geom.nelem = m->nelem;
+  m->geom.gamma = o.gamma;
+
+  // basis and scaled split-form tables
+  long double x[8], w[8], Dt[8][8];
+  lgl_basis(N, x, w);
+  split_matrix(N, x, w, Dt);
+  memset(&m->t64, 0, sizeof(m->t64));
+  memset(&m->t32, 0, sizeof(m->t32));
+  for (int k = 0; k < d; ++k) {
+    const long double s = -2.0L / (long double)m->h[k];
+    for (int a = 0; a <= N; ++a)
+      for (int b = 0; b <= N; ++b) {
+        m->t64.Ds[k][a][b] = (double)(s * Dt[a][b]);
+        m->t32.Ds[k][a][b] = (float)(s * Dt[a][b]);
+      }
+    m->t64.liftR[k] = (double)(s / w[N]);
+    m->t64.liftL[k] = (double)(-s / w[0]);
+    m->t32.liftR[k] = (float)(s / w[N]);
+    m->t32.liftL[k] = (float)(-s / w[0]);
+  }
+  for (int j = 0; j <= N; ++j) m->w[j] = (double)w[j];
+
+  // node quadrature weights jac * w_i * w_j (* w_k)
+  double jac = 1.0;
+  for (int k = 0; k < d; ++k) jac *= 0.5 * m->h[k];
+  double wq_host[512];
+  for (long long node = 0; node < m->P; ++node) {
+    double wqv = jac;
+    long long r = node;
+    for (int k = 0; k < d; ++k) {
+      wqv *= m->w[r % m->np];
+      r /= m->np;
+    }
+    wq_host[node] = wqv;
+  }
+
+  const size_t rsize = (o.precision == DG_FP64) ? sizeof(double) : sizeof(float);
+  const long long nfaces_vals = (long long)d * m->nv * m->nelem * (m->P / m->np);
+  cudaError_t e;
+  if ((e = cudaMalloc(&m->k, m->nvalues * sizeof(double))) != cudaSuccess ||
+      (e = cudaMalloc(&m->fs, nfaces_vals * rsize)) != cudaSuccess ||
+      (e = cudaMalloc(&m->wq, m->P * sizeof(double))) != cudaSuccess ||
+      (e = cudaMalloc(&m->partials, kRedBlocks * 7 * 2 * sizeof(double))) != cudaSuccess ||
+      (e = cudaMalloc(&m->red_out, 7 * 2 * sizeof(double))) != cudaSuccess ||
+      (e = cudaMalloc(&m->speed, sizeof(unsigned long long))) != cudaSuccess ||
+      (e = cudaMalloc(&m->err, sizeof(unsigned))) != cudaSuccess) {
+    int rc = cuda_fail(e, "dg_mesh_create: cudaMalloc");
+    cudaFree(m->k);
+    cudaFree(m->fs);
+    cudaFree(m->wq);
+    cudaFree(m->partials);
+    cudaFree(m->red_out);
+    cudaFree(m->speed);
+    cudaFree(m->err);
+    delete m;
+    return rc;
+  }
+  if ((e = cudaMemcpyAsync(m->wq, wq_host, m->P * sizeof(double), cudaMemcpyHostToDevice,
+                           m->stream)) != cudaSuccess ||
+      (e = cudaMemsetAsync(m->k, 0, m->nvalues * sizeof(double), m->stream)) != cudaSuccess ||
+      (e = cudaMemsetAsync(m->err, 0, sizeof(unsigned), m->stream)) != cudaSuccess ||
+      (e = cudaStreamSynchronize(m->stream)) != cudaSuccess) {
+    int rc = cuda_fail(e, "dg_mesh_create: initialisation");
+    dg_mesh_destroy(m);
+    return rc;
+  }
+  *out = m;
+  return DG_OK;
+}
+
+int dg_mesh_destroy(dg_mesh* m) {
+  if (!m) return DG_OK;
+  cudaStreamSynchronize(m->stream);
+  cudaFree(m->k);
+  cudaFree(m->fs);
+  cudaFree(m->wq);
+  cudaFree(m->partials);
+  cudaFree(m->red_out);
+  cudaFree(m->speed);
+  cudaFree(m->err);
+  delete m;
+  return DG_OK;
+}
+
+int dg_mesh_info(const dg_mesh* m, long long* n_nodes, int* n_vars, long long* n_values) {
+  if (!valid_mesh(m)) return fail(DG_ERR_ARG, "dg_mesh_info: invalid mesh");
+  if (n_nodes) *n_nodes = m->nnodes;
+  if (n_vars) *n_vars = m->nv;
+  if (n_values) *n_values = m->nvalues;
+  return DG_OK;
+}
+
+int dg_mesh_set_stream(dg_mesh* m, void* cuda_stream) {
+  if (!valid_mesh(m)) return fail(DG_ERR_ARG, "dg_mesh_set_stream: invalid mesh");
+  m->stream = (cudaStream_t)cuda_stream;
+  return DG_OK;
+}
+
+int dg_rhs(dg_mesh* m, const double* u, void* du) { return dg_rhs_part(m, u, du, 3); }
+
+int dg_rhs_part(dg_mesh* m, const double* u, void* du, int parts) {
+  if (!valid_mesh(m) || !u || !du) return fail(DG_ERR_ARG, "dg_rhs: null argument");
+  if (parts < 1 || parts > 3) return fail(DG_ERR_ARG, "dg_rhs_part: parts must be 1, 2 or 3");
+  cudaError_t e;
+  if (m->opt.precision == DG_FP64) {
+    e = (m->d == 2 ? dg::rhs_launch_double_2 : dg::rhs_launch_double_3)(
+        m->N, u, (double*)du, (double*)m->fs, m->geom, m->t64, m->opt.volume_flux,
+        m->opt.surface_flux, m->err, m->stream, parts);
+  } else {
+    e = (m->d == 2 ? dg::rhs_launch_float_2 : dg::rhs_launch_float_3)(
+        m->N, u, (float*)du, (float*)m->fs, m->geom, m->t32, m->opt.volume_flux,
+        m->opt.surface_flux, m->err, m->stream, parts);
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "dg_rhs: launch");
+  return DG_OK;
+}
+
+int dg_rk_stage(dg_mesh* m, double* u, const void* du, double a, double b, double dt) {
+  if (!valid_mesh(m) || !u || !du) return fail(DG_ERR_ARG, "dg_rk_stage: null argument");
+  const int grid = grid_for((m->nvalues + 1) / 2, 256);
+  if (m->opt.precision == DG_FP64)
+    rk_stage_kernel<double><<<grid, 256, 0, m->stream>>>(u, m->k, (const double*)du, a, b, dt,
+                                                         m->nvalues);
+  else
+    rk_stage_kernel<float><<<grid, 256, 0, m->stream>>>(u, m->k, (const float*)du, a, b, dt,
+                                                        m->nvalues);
+  DG_CUDA(cudaGetLastError(), "dg_rk_stage: launch");
+  return DG_OK;
+}
+
+int dg_rk_reset(dg_mesh* m) {
+  if (!valid_mesh(m)) return fail(DG_ERR_ARG, "dg_rk_reset: invalid mesh");
+  DG_CUDA(cudaMemsetAsync(m->k, 0, m->nvalues * sizeof(double), m->stream), "dg_rk_reset");
+  return DG_OK;
+}
+
+int dg_step(dg_mesh* m, double* u, void* du, double dt) {
+  if (!valid_mesh(m) || !u || !du) return fail(DG_ERR_ARG, "dg_step: null argument");
+  for (int s = 0; s < 5; ++s) {
+    int rc = dg_rhs(m, u, du);
+    if (rc != DG_OK) return rc;
+    rc = dg_rk_stage(m, u, du, kRkA[s], kRkB[s], dt);
+    if (rc != DG_OK) return rc;
+  }
+  return DG_OK;
+}
+
+int dg_mesh_check(dg_mesh* m, int* flags) {
+  if (!valid_mesh(m)) return fail(DG_ERR_ARG, "dg_mesh_check: invalid mesh");
+  unsigned h = 0;
+  DG_CUDA(cudaMemcpyAsync(&h, m->err, sizeof(unsigned), cudaMemcpyDeviceToHost, m->stream),
+          "dg_mesh_check: copy");
+  DG_CUDA(cudaStreamSynchronize(m->stream), "dg_mesh_check: sync");
+  if (flags) *flags = (int)h;
+  if (h) {
+    DG_CUDA(cudaMemsetAsync(m->err, 0, sizeof(unsigned), m->stream), "dg_mesh_check: clear");
+    return fail(DG_ERR_NONPHYSICAL, "non-physical state met (flags %u: 1 rho<=0, 2 p<=0, 4 NaN)", h);
+  }
+  return DG_OK;
+}
+
+int dg_max_dt(dg_mesh* m, const double* u, double cfl, double* dt_out) {
+  if (!valid_mesh(m) || !u || !dt_out || !(cfl > 0.0))
+    return fail(DG_ERR_ARG, "dg_max_dt: bad argument");
+  DG_CUDA(cudaMemsetAsync(m->speed, 0, sizeof(unsigned long long), m->stream), "dg_max_dt: clear");
+  const int threads = 256;
+  const int grid = grid_for(m->nelem * 32, threads);
+  const double s0 = 2.0 / m->h[0], s1 = 2.0 / m->h[1], s2 = 2.0 / m->h[2];
+  if (m->d == 2)
+    speed_kernel<2><<<grid, threads, 0, m->stream>>>(u, m->geom, (int)m->P, s0, s1, s2, m->speed,
+                                                     m->err);
+  else
+    speed_kernel<3><<<grid, threads, 0, m->stream>>>(u, m->geom, (int)m->P, s0, s1, s2, m->speed,
+                                                     m->err);
+  DG_CUDA(cudaGetLastError(), "dg_max_dt: launch");
+  unsigned long long bits = 0;
+  DG_CUDA(cudaMemcpyAsync(&bits, m->speed, sizeof(bits), cudaMemcpyDeviceToHost, m->stream),
+          "dg_max_dt: copy");
+  int rc = dg_mesh_check(m, nullptr);
+  if (rc != DG_OK) return rc;
+  double worst;
+  memcpy(&worst, &bits, sizeof(worst));
+  if (!(worst > 0.0)) return fail(DG_ERR_NONPHYSICAL, "dg_max_dt: zero or invalid wave speed");
+  *dt_out = cfl * 2.0 / ((m->N + 1) * worst);
+  return DG_OK;
+}
+
+int dg_integrals(dg_mesh* m, const double* u, double* out) {
+  if (!valid_mesh(m) || !u || !out) return fail(DG_ERR_ARG, "dg_integrals: null argument");
+  const int nq = m->d + 4;
+  if (m->d == 2)
+    integrals_kernel<2><<<kRedBlocks, kRedThreads, 0, m->stream>>>(u, m->geom, (int)m->P, m->wq,
+                                                                   m->partials, m->err);
+  else
+    integrals_kernel<3><<<kRedBlocks, kRedThreads, 0, m->stream>>>(u, m->geom, (int)m->P, m->wq,
+                                                                   m->partials, m->err);
+  DG_CUDA(cudaGetLastError(), "dg_integrals: launch");
+  integrals_final_kernel<<<1, kRedThreads, 0, m->stream>>>(m->partials, kRedBlocks, nq,
+                                                           m->red_out);
+  DG_CUDA(cudaGetLastError(), "dg_integrals: final launch");
+  double host[14];
+  DG_CUDA(cudaMemcpyAsync(host, m->red_out, 2 * nq * sizeof(double), cudaMemcpyDeviceToHost,
+                          m->stream),
+          "dg_integrals: copy");
+  int rc = dg_mesh_check(m, nullptr);
+  if (rc != DG_OK) return rc;
+  for (int q = 0; q < nq; ++q) out[q] = host[2 * q] + host[2 * q + 1];
+  return DG_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,272 @@
+// Device-side building blocks of the DGSEM rhs: mesh/basis parameters, the
+// conserved-to-primitive prologue, the logarithmic mean, the two-point volume
+// fluxes and the surface fluxes, all templated on the arithmetic type R
+// (double or float). Kernels live in dg_rhs_kernels.cuh.
+//
+// Formulas (paper: Ranocha et al., "Adaptive numerical simulations with
+// Trixi.jl", Sec. 2.1 and 3.1, which cite them):
+//   Euler flux     f_n(u) = (rho v_n, rho v_n v + p e_n, (E + p) v_n),
+//                  p = (gamma - 1)(E - rho |v|^2 / 2)
+//   log mean       ln_mean(x, y) = (y - x) / ln(y / x), evaluated with the
+//                  truncated atanh series for ((x-y)/(x+y))^2 < threshold
+//                  (ranocha2021efficient)
+//   Ranocha EC/KEP flux (ranocha2020icosahom), Chandrashekar EC flux,
+//   central flux (weak form, gassner2016split), local Lax-Friedrichs and HLL.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace dg {
+
+constexpr int kNPMax = 8;  // N <= 7
+
+// error-word bits
+constexpr unsigned kErrRho = 1u, kErrP = 2u, kErrNaN = 4u;
+
+struct Geom {
+  int n[3];         // elements per direction (1 for unused)
+  long long nelem;  // total elements
+  double gamma;
+};
+
+// Per-direction split-form tables, scaled by the inverse Jacobian:
+//   Ds[k][a][b] = -(2/h_k) Dt[a][b], Dt = 2 D - W^-1 B (zero diagonal)
+//   liftR[k] = -(2/h_k)/w_N (right face), liftL[k] = +(2/h_k)/w_0 (left face)
+template <typename R>
+struct Tables {
+  R Ds[3][kNPMax][kNPMax];
+  R liftR[3];
+  R liftL[3];
+};
+
+template <int D, int N>
+struct Shape {
+  static constexpr int NP = N + 1;
+  static constexpr int P = (D == 2) ? NP * NP : NP * NP * NP;  // nodes per element
+  static constexpr int NV = D + 2;                              // conserved variables
+  static constexpr int LINES = P / NP;                          // lines per direction
+};
+
+// Node index of position a along direction DIR on line l (l enumerates the
+// remaining coordinates in ascending order, first one fastest). The same l
+// enumerates the face nodes of the two faces normal to DIR.
+template <int D, int N, int DIR>
+__device__ __forceinline__ int line_node(int l, int a) {
+  constexpr int NP = N + 1;
+  if (DIR == 0) return a + NP * l;
+  if (DIR == 1) return (D == 2) ? l + NP * a : (l % NP) + NP * a + NP * NP * (l / NP);
+  return l + NP * NP * a;
+}
+
+template <int D, int N>
+__device__ __forceinline__ int line_node_rt(int dir, int l, int a) {
+  if (dir == 0) return line_node<D, N, 0>(l, a);
+  if (dir == 1) return line_node<D, N, 1>(l, a);
+  return line_node<D, N, 2>(l, a);
+}
+
+// Neighbour of element e at offset +-1 in direction dir (periodic).
+__device__ __forceinline__ long long neighbour(const Geom& g, long long e, int dir, int s) {
+  long long ex = e % g.n[0];
+  long long r = e / g.n[0];
+  long long ey = r % g.n[1];
+  long long ez = r / g.n[1];
+  if (dir == 0) ex = (ex + s + g.n[0]) % g.n[0];
+  else if (dir == 1) ey = (ey + s + g.n[1]) % g.n[1];
+  else ez = (ez + s + g.n[2]) % g.n[2];
+  return ex + (long long)g.n[0] * (ey + (long long)g.n[1] * ez);
+}
+
+// ---- rounding-explicit scalar ops (used where both sides of a comparison
+// or a cancellation must round identically to a plain IEEE evaluation) ----
+__device__ __forceinline__ double rn_mul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double rn_add(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double rn_sub(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ double rn_div(double a, double b) { return __ddiv_rn(a, b); }
+__device__ __forceinline__ float rn_mul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float rn_add(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float rn_sub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float rn_div(float a, float b) { return __fdiv_rn(a, b); }
+
+template <typename R, int D>
+struct Prim {
+  R rho, v[D], p;
+};
+
+// Primitive variables from conserved ones, rounded as the plain left-to-right
+// IEEE evaluation of v_k = m_k / rho, p = (gamma-1) (E - (rho/2) |v|^2).
+template <typename R, int D>
+__device__ __forceinline__ Prim<R, D> cons2prim(const R* c, R gm1) {
+  Prim<R, D> q;
+  q.rho = c[0];
+  R v2 = R(0);
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    q.v[k] = rn_div(c[1 + k], c[0]);
+    v2 = (k == 0) ? rn_mul(q.v[0], q.v[0]) : rn_add(v2, rn_mul(q.v[k], q.v[k]));
+  }
+  q.p = rn_mul(gm1, rn_sub(c[D + 1], rn_mul(rn_mul(R(0.5), c[0]), v2)));
+  return q;
+}
+
+template <typename R, int D>
+__device__ __forceinline__ unsigned prim_check(const Prim<R, D>& q) {
+  unsigned bad = 0;
+  if (!(q.rho > R(0))) bad |= kErrRho;
+  if (!(q.p > R(0))) bad |= kErrP;
+  if (!isfinite(q.rho) || !isfinite(q.p)) bad |= kErrNaN;
+  return bad;
+}
+
+// ---- logarithmic mean ----
+// FP64: threshold 1e-4 and series through f2^3 (series truncation ~ 2e-17);
+// the switch quantity f2 = (x(x-2y)+y^2)/(x(x+2y)+y^2) is rounded as a plain
+// IEEE evaluation so that the branch taken is reproducible.
+__device__ __forceinline__ double ln_mean(double x, double y) {
+  const double y2 = rn_mul(y, y);
+  const double num = rn_add(rn_mul(x, rn_sub(x, rn_mul(2.0, y))), y2);
+  const double den = rn_add(rn_mul(x, rn_add(x, rn_mul(2.0, y))), y2);
+  const double f2 = rn_div(num, den);
+  if (f2 < 1.0e-4)
+    return (x + y) / (2.0 + f2 * (2.0 / 3.0 + f2 * (2.0 / 5.0 + f2 * (2.0 / 7.0))));
+  return (y - x) / log(y / x);
+}
+
+// FP32: the direct quotient loses ~eps/|ln(y/x)| relative accuracy, so the
+// series covers f2 < 1e-2 (|ln(y/x)| > 0.2 otherwise); terms through f2^4
+// leave a truncation of 2 f2^5/11 < 2e-11, below float rounding.
+__device__ __forceinline__ float ln_mean(float x, float y) {
+  const float s = x + y, dd = y - x;
+  const float r = dd / s;
+  const float f2 = r * r;
+  if (f2 < 1.0e-2f)
+    return s / (2.0f + f2 * (2.0f / 3.0f + f2 * (2.0f / 5.0f + f2 * (2.0f / 7.0f + f2 * (2.0f / 9.0f)))));
+  return dd / logf(y / x);
+}
+
+// ---- two-point volume fluxes f#(L, R) in direction DIR ----
+enum { kVRanocha = 0, kVChandrashekar = 1, kVCentral = 2 };
+
+template <typename R, int D, int DIR>
+__device__ __forceinline__ void flux_ranocha(const Prim<R, D>& L, const Prim<R, D>& Rt, R gm1inv,
+                                             R f[D + 2]) {
+  const R rho_mean = ln_mean(L.rho, Rt.rho);
+  const R inv_rho_p_mean = L.p * Rt.p / ln_mean(L.rho * Rt.p, Rt.rho * L.p);
+  R v_dot = L.v[0] * Rt.v[0];
+#pragma unroll
+  for (int k = 1; k < D; ++k) v_dot += L.v[k] * Rt.v[k];
+  const R p_avg = R(0.5) * (L.p + Rt.p);
+  f[0] = rho_mean * R(0.5) * (L.v[DIR] + Rt.v[DIR]);
+#pragma unroll
+  for (int k = 0; k < D; ++k) f[1 + k] = f[0] * R(0.5) * (L.v[k] + Rt.v[k]);
+  f[1 + DIR] += p_avg;
+  f[D + 1] = f[0] * (R(0.5) * v_dot + inv_rho_p_mean * gm1inv) +
+             R(0.5) * (L.p * Rt.v[DIR] + Rt.p * L.v[DIR]);
+}
+
+template <typename R, int D, int DIR>
+__device__ __forceinline__ void flux_chandrashekar(const Prim<R, D>& L, const Prim<R, D>& Rt,
+                                                   R gm1inv, R f[D + 2]) {
+  const R bL = R(0.5) * L.rho / L.p, bR = R(0.5) * Rt.rho / Rt.p;
+  const R rho_ln = ln_mean(L.rho, Rt.rho), beta_ln = ln_mean(bL, bR);
+  const R rho_avg = R(0.5) * (L.rho + Rt.rho), beta_avg = R(0.5) * (bL + bR);
+  R v2L = R(0), v2R = R(0), va[D];
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    v2L += L.v[k] * L.v[k];
+    v2R += Rt.v[k] * Rt.v[k];
+    va[k] = R(0.5) * (L.v[k] + Rt.v[k]);
+  }
+  const R p_mean = R(0.5) * rho_avg / beta_avg;
+  f[0] = rho_ln * va[DIR];
+#pragma unroll
+  for (int k = 0; k < D; ++k) f[1 + k] = f[0] * va[k];
+  f[1 + DIR] += p_mean;
+  R fe = f[0] * R(0.5) * (gm1inv / beta_ln - R(0.5) * (v2L + v2R));
+#pragma unroll
+  for (int k = 0; k < D; ++k) fe += f[1 + k] * va[k];
+  f[D + 1] = fe;
+}
+
+// physical flux from primitives (volume kernels keep only primitives)
+template <typename R, int D, int DIR>
+__device__ __forceinline__ void euler_flux_prim(const Prim<R, D>& q, R gm1inv, R f[D + 2]) {
+  const R m = q.rho * q.v[DIR];
+  R v2 = R(0);
+#pragma unroll
+  for (int k = 0; k < D; ++k) v2 += q.v[k] * q.v[k];
+  f[0] = m;
+#pragma unroll
+  for (int k = 0; k < D; ++k) f[1 + k] = m * q.v[k];
+  f[1 + DIR] += q.p;
+  const R E = q.p * gm1inv + R(0.5) * q.rho * v2;
+  f[D + 1] = (E + q.p) * q.v[DIR];
+}
+
+template <typename R, int D, int DIR>
+__device__ __forceinline__ void flux_central(const Prim<R, D>& L, const Prim<R, D>& Rt, R gm1inv,
+                                             R f[D + 2]) {
+  R fl[D + 2], fr[D + 2];
+  euler_flux_prim<R, D, DIR>(L, gm1inv, fl);
+  euler_flux_prim<R, D, DIR>(Rt, gm1inv, fr);
+#pragma unroll
+  for (int v = 0; v < D + 2; ++v) f[v] = R(0.5) * (fl[v] + fr[v]);
+}
+
+template <int VF, typename R, int D, int DIR>
+__device__ __forceinline__ void volume_flux(const Prim<R, D>& L, const Prim<R, D>& Rt, R gm1inv,
+                                            R f[D + 2]) {
+  if (VF == kVRanocha) flux_ranocha<R, D, DIR>(L, Rt, gm1inv, f);
+  else if (VF == kVChandrashekar) flux_chandrashekar<R, D, DIR>(L, Rt, gm1inv, f);
+  else flux_central<R, D, DIR>(L, Rt, gm1inv, f);
+}
+
+// ---- surface fluxes F*(u_L, u_R) in direction dir (runtime) ----
+enum { kSLLF = 0, kSRanocha = 1, kSHLL = 2, kSChandrashekar = 3 };
+
+// physical flux from the conserved state and its primitives
+template <typename R, int D>
+__device__ __forceinline__ void euler_flux_cons(const R* c, const Prim<R, D>& q, int dir,
+                                                R f[D + 2]) {
+  const R m = c[1 + dir];
+  f[0] = m;
+#pragma unroll
+  for (int k = 0; k < D; ++k) f[1 + k] = m * q.v[k];
+  f[1 + dir] += q.p;
+  f[D + 1] = (c[D + 1] + q.p) * q.v[dir];
+}
+
+template <typename R, int D, int DIR>
+__device__ __forceinline__ void surface_flux_dir(int sf, const R* cL, const R* cR,
+                                                 const Prim<R, D>& L, const Prim<R, D>& Rt,
+                                                 R gamma, R gm1inv, R f[D + 2]) {
+  if (sf == kSRanocha) {
+    flux_ranocha<R, D, DIR>(L, Rt, gm1inv, f);
+    return;
+  }
+  if (sf == kSChandrashekar) {
+    flux_chandrashekar<R, D, DIR>(L, Rt, gm1inv, f);
+    return;
+  }
+  R fl[D + 2], fr[D + 2];
+  euler_flux_cons<R, D>(cL, L, DIR, fl);
+  euler_flux_cons<R, D>(cR, Rt, DIR, fr);
+  const R cl = sqrt(gamma * L.p / L.rho), cr = sqrt(gamma * Rt.p / Rt.rho);
+  if (sf == kSLLF) {
+    const R lam = fmax(fabs(L.v[DIR]), fabs(Rt.v[DIR])) + fmax(cl, cr);
+#pragma unroll
+    for (int v = 0; v < D + 2; ++v) f[v] = R(0.5) * (fl[v] + fr[v]) - R(0.5) * lam * (cR[v] - cL[v]);
+    return;
+  }
+  // HLL
+  const R sL = fmin(L.v[DIR] - cl, Rt.v[DIR] - cr);
+  const R sR = fmax(L.v[DIR] + cl, Rt.v[DIR] + cr);
+#pragma unroll
+  for (int v = 0; v < D + 2; ++v) {
+    if (sL >= R(0)) f[v] = fl[v];
+    else if (sR <= R(0)) f[v] = fr[v];
+    else f[v] = (sR * fl[v] - sL * fr[v] + sL * sR * (cR[v] - cL[v])) / (sR - sL);
+  }
+}
+
+}  // namespace dg

@@ -1,0 +1,233 @@
+"""Python binding of libdgsem.so: argument marshalling only.
+
+Every step of the rhs, the RK stage, the time step and the integrals runs in
+the library's CUDA kernels; torch provides device memory and streams. There
+is no CPU fallback: if the shared library is missing or cannot be loaded,
+every entry point raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+SO_PATH = os.path.join(_HERE, "libdgsem.so")
+
+VFLUX = {"ranocha": 0, "chandrashekar": 1, "central": 2}
+SFLUX = {"llf": 0, "ranocha": 1, "hll": 2, "chandrashekar": 3}
+PRECISION = {"fp64": 0, "fp32": 1}
+
+# Carpenter-Kennedy (1994) five-stage fourth-order 2N-storage coefficients
+RK_A = (0.0, -567301805773.0 / 1357537059087.0, -2404267990393.0 / 2016746695238.0,
+        -3550918686646.0 / 2091501179385.0, -1275806237668.0 / 842570457699.0)
+RK_B = (1432997174477.0 / 9575080441755.0, 5161836677717.0 / 13612068292357.0,
+        1720146321549.0 / 2090206949498.0, 3134564353537.0 / 4481467310338.0,
+        2277821191437.0 / 14882151754819.0)
+
+EXPORTS = ("dg_mesh_create", "dg_mesh_destroy", "dg_mesh_info", "dg_mesh_set_stream",
+           "dg_lgl_nodes", "dg_rhs", "dg_rhs_part", "dg_rk_stage", "dg_rk_reset", "dg_step", "dg_max_dt",
+           "dg_integrals", "dg_mesh_check", "dg_last_error")
+
+
+class DGError(RuntimeError):
+    pass
+
+
+class _Options(ctypes.Structure):
+    _fields_ = [("gamma", ctypes.c_double), ("volume_flux", ctypes.c_int),
+                ("surface_flux", ctypes.c_int), ("precision", ctypes.c_int)]
+
+
+_lib = None
+
+
+def load(path: str = SO_PATH):
+    """Load the shared library (raises if it is missing: no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise DGError(f"libdgsem.so not built ({path}); run paper_2108_06476_gb300.build.build()")
+    L = ctypes.CDLL(path)
+    vp, dp, ip, llp = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), \
+        ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_longlong)
+    L.dg_mesh_create.argtypes = [ctypes.c_int, ctypes.c_int, ip, dp, ctypes.POINTER(_Options), vp,
+                                 ctypes.POINTER(vp)]
+    L.dg_mesh_destroy.argtypes = [vp]
+    L.dg_mesh_info.argtypes = [vp, llp, ip, llp]
+    L.dg_mesh_set_stream.argtypes = [vp, vp]
+    L.dg_lgl_nodes.argtypes = [ctypes.c_int, dp, dp]
+    L.dg_rhs.argtypes = [vp, vp, vp]
+    L.dg_rhs_part.argtypes = [vp, vp, vp, ctypes.c_int]
+    L.dg_rk_stage.argtypes = [vp, vp, vp, ctypes.c_double, ctypes.c_double, ctypes.c_double]
+    L.dg_rk_reset.argtypes = [vp]
+    L.dg_step.argtypes = [vp, vp, vp, ctypes.c_double]
+    L.dg_max_dt.argtypes = [vp, vp, ctypes.c_double, dp]
+    L.dg_integrals.argtypes = [vp, vp, dp]
+    L.dg_mesh_check.argtypes = [vp, ip]
+    L.dg_last_error.restype = ctypes.c_char_p
+    L.dg_last_error.argtypes = []
+    for name in EXPORTS:
+        getattr(L, name).restype = ctypes.c_char_p if name == "dg_last_error" else ctypes.c_int
+    _lib = L
+    return L
+
+
+def _check(rc: int, what: str):
+    if rc != 0:
+        msg = load().dg_last_error().decode(errors="replace")
+        raise DGError(f"{what} failed ({rc}): {msg}")
+
+
+def lgl_nodes(N: int):
+    """The library's LGL nodes and weights (host numpy arrays)."""
+    xi = np.zeros(N + 1)
+    w = np.zeros(N + 1)
+    dp = ctypes.POINTER(ctypes.c_double)
+    _check(load().dg_lgl_nodes(N, xi.ctypes.data_as(dp), w.ctypes.data_as(dp)), "dg_lgl_nodes")
+    return xi, w
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+@dataclass
+class MeshSpec:
+    d: int
+    N: int
+    n: tuple
+    domain: tuple
+    gamma: float = 1.4
+    volume_flux: str = "ranocha"
+    surface_flux: str = "llf"
+    precision: str = "fp64"
+
+
+class Mesh:
+    """A uniform periodic Cartesian DGSEM mesh on the current CUDA device.
+
+    State tensors are float64 CUDA tensors of n_values entries in the layout
+    u[e][v][k][j][i]; rhs outputs are float64 (fp64) or float32 (fp32)."""
+
+    def __init__(self, d, N, n, domain=None, gamma=1.4, volume_flux="ranocha",
+                 surface_flux="llf", precision="fp64", stream=None):
+        import torch
+        self._torch = torch
+        L = load()
+        if domain is None:
+            domain = (-1.0, 1.0) * d
+        self.d, self.N, self.n = int(d), int(N), tuple(int(x) for x in n)
+        self.domain = tuple(float(x) for x in domain)
+        self.precision = precision
+        self.rhs_dtype = torch.float64 if precision == "fp64" else torch.float32
+        opt = _Options(gamma, VFLUX[volume_flux], SFLUX[surface_flux], PRECISION[precision])
+        n_arr = (ctypes.c_int * 3)(*(list(self.n) + [1] * (3 - len(self.n))))
+        dom = (ctypes.c_double * 6)(*(list(self.domain) + [0.0] * (6 - len(self.domain))))
+        h = ctypes.c_void_p()
+        st = stream if stream is not None else torch.cuda.current_stream()
+        self._stream = st
+        _check(L.dg_mesh_create(self.d, self.N, n_arr, dom, ctypes.byref(opt),
+                                ctypes.c_void_p(st.cuda_stream), ctypes.byref(h)),
+               "dg_mesh_create")
+        self._h = h
+        nn, nv, nvals = ctypes.c_longlong(), ctypes.c_int(), ctypes.c_longlong()
+        _check(L.dg_mesh_info(h, ctypes.byref(nn), ctypes.byref(nv), ctypes.byref(nvals)),
+               "dg_mesh_info")
+        self.n_nodes, self.n_vars, self.n_values = nn.value, nv.value, nvals.value
+
+    # -- lifetime --
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load().dg_mesh_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self):
+        return self._h
+
+    def _sync_stream(self):
+        st = self._torch.cuda.current_stream()
+        if st.cuda_stream != self._stream.cuda_stream:
+            _check(load().dg_mesh_set_stream(self._h, ctypes.c_void_p(st.cuda_stream)),
+                   "dg_mesh_set_stream")
+            self._stream = st
+
+    def _check_state(self, u):
+        t = self._torch
+        if not (u.is_cuda and u.dtype == t.float64 and u.is_contiguous()
+                and u.numel() == self.n_values):
+            raise DGError("u must be a contiguous float64 CUDA tensor of n_values entries")
+
+    def empty_rhs(self):
+        return self._torch.empty(self.n_values, dtype=self.rhs_dtype, device="cuda")
+
+    # -- compute --
+    def rhs(self, u, du=None):
+        self._check_state(u)
+        if du is None:
+            du = self.empty_rhs()
+        if not (du.is_cuda and du.dtype == self.rhs_dtype and du.is_contiguous()
+                and du.numel() == self.n_values):
+            raise DGError("du has the wrong dtype, size or layout")
+        self._sync_stream()
+        _check(load().dg_rhs(self._h, _ptr(u), _ptr(du)), "dg_rhs")
+        return du
+
+    def rhs_part(self, u, du, parts):
+        """Launch only the surface kernel (parts=1), only the volume kernel
+        (parts=2) or both (3); used to time the kernels separately."""
+        self._sync_stream()
+        _check(load().dg_rhs_part(self._h, _ptr(u), _ptr(du), int(parts)), "dg_rhs_part")
+
+    def rk_stage(self, u, du, a, b, dt):
+        self._check_state(u)
+        self._sync_stream()
+        _check(load().dg_rk_stage(self._h, _ptr(u), _ptr(du), float(a), float(b), float(dt)),
+               "dg_rk_stage")
+
+    def rk_reset(self):
+        self._sync_stream()
+        _check(load().dg_rk_reset(self._h), "dg_rk_reset")
+
+    def step(self, u, dt, du=None):
+        self._check_state(u)
+        if du is None:
+            du = self.empty_rhs()
+        self._sync_stream()
+        _check(load().dg_step(self._h, _ptr(u), _ptr(du), float(dt)), "dg_step")
+        return du
+
+    def max_dt(self, u, cfl=0.5):
+        self._check_state(u)
+        self._sync_stream()
+        out = ctypes.c_double()
+        _check(load().dg_max_dt(self._h, _ptr(u), float(cfl), ctypes.byref(out)), "dg_max_dt")
+        return out.value
+
+    def integrals(self, u):
+        self._check_state(u)
+        self._sync_stream()
+        out = np.zeros(self.d + 4)
+        _check(load().dg_integrals(self._h, _ptr(u),
+                                   out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))),
+               "dg_integrals")
+        return out
+
+    def check(self):
+        """Synchronise and raise DGError if a non-physical state was met."""
+        self._sync_stream()
+        flags = ctypes.c_int()
+        rc = load().dg_mesh_check(self._h, ctypes.byref(flags))
+        if rc != 0:
+            _check(rc, "dg_mesh_check")
+        return flags.value
