@@ -57,13 +57,13 @@
 typedef double complex real;
 #define OR(name) orc_##name
 #define RE(x) creal(x)
-#define RLOG(x) clog(x)
+#define RLOG1P(x) clog(1.0 + (x))
 #define RSQRT(x) csqrt(x)
 #else
 typedef double real;
 #define OR(name) or_##name
 #define RE(x) (x)
-#define RLOG(x) log(x)
+#define RLOG1P(x) log1p(x)
 #define RSQRT(x) sqrt(x)
 #endif
 
@@ -237,12 +237,14 @@ void OR(euler_flux)(int d, int n, double gamma, const real *u, real *f) {
 /* Logarithmic mean (y - x) / ln(y / x) in the form of ranocha2021efficient:
  * with f2 = ((x - y) / (x + y))^2, a truncated series of the identity
  * ln(y/x) = 2 atanh((y - x)/(y + x)) for f2 < 1e-4, the direct quotient
- * otherwise. */
+ * otherwise. In the direct quotient ln(y/x) is evaluated as log1p((y-x)/x):
+ * log(fl(y/x)) would carry the rounding of y/x divided by ln(y/x), up to
+ * ~50 ulps just above the switch. */
 real OR(ln_mean)(real x, real y) {
   real f2 = (x * (x - 2.0 * y) + y * y) / (x * (x + 2.0 * y) + y * y);
   if (RE(f2) < 1.0e-4)
     return (x + y) / (2.0 + f2 * (2.0 / 3.0 + f2 * (2.0 / 5.0 + f2 * (2.0 / 7.0))));
-  return (y - x) / RLOG(y / x);
+  return (y - x) / RLOG1P((y - x) / x);
 }
 
 /* Ranocha's entropy-conserving and kinetic-energy-preserving two-point flux,
