@@ -7,9 +7,8 @@
 // Trixi.jl", Sec. 2.1 and 3.1, which cite them):
 //   Euler flux     f_n(u) = (rho v_n, rho v_n v + p e_n, (E + p) v_n),
 //                  p = (gamma - 1)(E - rho |v|^2 / 2)
-//   log mean       ln_mean(x, y) = (y - x) / ln(y / x), evaluated with the
-//                  truncated atanh series for ((x-y)/(x+y))^2 < threshold
-//                  (ranocha2021efficient)
+//   log mean       ln_mean(x, y) = (y - x) / ln(y / x) (ranocha2021efficient's
+//                  atanh-series idea, with a longer series and log1p)
 //   Ranocha EC/KEP flux (ranocha2020icosahom), Chandrashekar EC flux,
 //   central flux (weak form, gassner2016split), local Lax-Friedrichs and HLL.
 #pragma once
@@ -119,29 +118,56 @@ __device__ __forceinline__ unsigned prim_check(const Prim<R, D>& q) {
 }
 
 // ---- logarithmic mean ----
-// FP64: threshold 1e-4 and series through f2^3 (series truncation ~ 2e-17);
-// the switch quantity f2 = (x(x-2y)+y^2)/(x(x+2y)+y^2) is rounded as a plain
-// IEEE evaluation so that the branch taken is reproducible.
-__device__ __forceinline__ double ln_mean(double x, double y) {
-  const double y2 = rn_mul(y, y);
-  const double num = rn_add(rn_mul(x, rn_sub(x, rn_mul(2.0, y))), y2);
-  const double den = rn_add(rn_mul(x, rn_add(x, rn_mul(2.0, y))), y2);
-  const double f2 = rn_div(num, den);
-  if (f2 < 1.0e-4)
-    return (x + y) / (2.0 + f2 * (2.0 / 3.0 + f2 * (2.0 / 5.0 + f2 * (2.0 / 7.0))));
-  return (y - x) / log(y / x);
+// ln_mean(x, y) = (y - x) / ln(y / x). With t = (y - x)/(y + x), f2 = t^2,
+// ln(y/x) = 2 atanh(t) = 2 t (1 + f2/3 + f2^2/5 + ...), so
+//   ln_mean = (x + y) / S(f2),  1 / ln_mean = S(f2) / (x + y),
+//   S(f2) = 2 (1 + f2/3 + f2^2/5 + f2^3/7 + ...).
+// In the series branch y - x is exact (Sterbenz) and every rounding is
+// relative to the result; outside it ln(y/x) = log1p((y - x)/x). Neither
+// branch divides a rounding error by ln(y/x), which the flux differencing
+// would amplify by (2/h)|Dt| |f| / |du|.
+// FP64: f2 < 1e-2 with terms through f2^7 (truncation f2^8/17 < 1e-17).
+__device__ __forceinline__ double series_s(double f2) {
+  double S = 2.0 / 15.0;
+  S = fma(f2, S, 2.0 / 13.0);
+  S = fma(f2, S, 2.0 / 11.0);
+  S = fma(f2, S, 2.0 / 9.0);
+  S = fma(f2, S, 2.0 / 7.0);
+  S = fma(f2, S, 2.0 / 5.0);
+  S = fma(f2, S, 2.0 / 3.0);
+  return fma(f2, S, 2.0);
+}
+// FP32: f2 < 4e-2 with terms through f2^5 (truncation f2^6/13 < 4e-10).
+__device__ __forceinline__ float series_s(float f2) {
+  float S = 2.0f / 11.0f;
+  S = fmaf(f2, S, 2.0f / 9.0f);
+  S = fmaf(f2, S, 2.0f / 7.0f);
+  S = fmaf(f2, S, 2.0f / 5.0f);
+  S = fmaf(f2, S, 2.0f / 3.0f);
+  return fmaf(f2, S, 2.0f);
+}
+__device__ __forceinline__ double series_limit(double) { return 1.0e-2; }
+__device__ __forceinline__ float series_limit(float) { return 4.0e-2f; }
+__device__ __forceinline__ double log1p_(double z) { return log1p(z); }
+__device__ __forceinline__ float log1p_(float z) { return log1pf(z); }
+
+template <typename R>
+__device__ __forceinline__ R ln_mean(R x, R y) {
+  const R s = x + y, d = y - x;
+  const R t = d / s;
+  const R f2 = t * t;
+  if (f2 < series_limit(R(0))) return s / series_s(f2);
+  return d / log1p_(d / x);
 }
 
-// FP32: the direct quotient loses ~eps/|ln(y/x)| relative accuracy, so the
-// series covers f2 < 1e-2 (|ln(y/x)| > 0.2 otherwise); terms through f2^4
-// leave a truncation of 2 f2^5/11 < 2e-11, below float rounding.
-__device__ __forceinline__ float ln_mean(float x, float y) {
-  const float s = x + y, dd = y - x;
-  const float r = dd / s;
-  const float f2 = r * r;
-  if (f2 < 1.0e-2f)
-    return s / (2.0f + f2 * (2.0f / 3.0f + f2 * (2.0f / 5.0f + f2 * (2.0f / 7.0f + f2 * (2.0f / 9.0f)))));
-  return dd / logf(y / x);
+template <typename R>
+__device__ __forceinline__ R inv_ln_mean(R x, R y) {
+  const R s = x + y, d = y - x;
+  const R rs = R(1) / s;
+  const R t = d * rs;
+  const R f2 = t * t;
+  if (f2 < series_limit(R(0))) return series_s(f2) * rs;
+  return log1p_(d / x) / d;
 }
 
 // ---- two-point volume fluxes f#(L, R) in direction DIR ----
@@ -151,7 +177,7 @@ template <typename R, int D, int DIR>
 __device__ __forceinline__ void flux_ranocha(const Prim<R, D>& L, const Prim<R, D>& Rt, R gm1inv,
                                              R f[D + 2]) {
   const R rho_mean = ln_mean(L.rho, Rt.rho);
-  const R inv_rho_p_mean = L.p * Rt.p / ln_mean(L.rho * Rt.p, Rt.rho * L.p);
+  const R inv_rho_p_mean = L.p * Rt.p * inv_ln_mean(L.rho * Rt.p, Rt.rho * L.p);
   R v_dot = L.v[0] * Rt.v[0];
 #pragma unroll
   for (int k = 1; k < D; ++k) v_dot += L.v[k] * Rt.v[k];
@@ -168,7 +194,7 @@ template <typename R, int D, int DIR>
 __device__ __forceinline__ void flux_chandrashekar(const Prim<R, D>& L, const Prim<R, D>& Rt,
                                                    R gm1inv, R f[D + 2]) {
   const R bL = R(0.5) * L.rho / L.p, bR = R(0.5) * Rt.rho / Rt.p;
-  const R rho_ln = ln_mean(L.rho, Rt.rho), beta_ln = ln_mean(bL, bR);
+  const R rho_ln = ln_mean(L.rho, Rt.rho), inv_beta_ln = inv_ln_mean(bL, bR);
   const R rho_avg = R(0.5) * (L.rho + Rt.rho), beta_avg = R(0.5) * (bL + bR);
   R v2L = R(0), v2R = R(0), va[D];
 #pragma unroll
@@ -182,7 +208,7 @@ __device__ __forceinline__ void flux_chandrashekar(const Prim<R, D>& L, const Pr
 #pragma unroll
   for (int k = 0; k < D; ++k) f[1 + k] = f[0] * va[k];
   f[1 + DIR] += p_mean;
-  R fe = f[0] * R(0.5) * (gm1inv / beta_ln - R(0.5) * (v2L + v2R));
+  R fe = f[0] * R(0.5) * (gm1inv * inv_beta_ln - R(0.5) * (v2L + v2R));
 #pragma unroll
   for (int k = 0; k < D; ++k) fe += f[1 + k] * va[k];
   f[D + 1] = fe;

@@ -222,3 +222,31 @@ def test_nonphysical_state_is_reported():
     assert m.check() == 0  # the word was cleared
     with pytest.raises(DGError):
         m.max_dt(ut)
+
+
+# ---- FP32 kernels (FP64 state, FP32 volume/surface arithmetic) ----
+TOL32 = 1e-5  # the FP32 target's relative L2 rhs error
+
+
+@pytest.mark.parametrize("N,ne,count", [(3, 64, 400), (7, 24, 60)])
+def test_rhs_fp32_full_size_sampled(orc, N, ne, count):
+    d, n = 3, (ne, ne, ne)
+    dom = W.box(d)
+    xi, _ = orc.lgl(N)
+    u = W.noisy_density_wave(d, N, n, dom, xi, seed=0)
+    elems = _sample_elements(n, count, seed=N + 10)
+    ref = oracle_rhs(orc, d, N, n, dom, u, elems=elems).reshape(-1, d + 2, (N + 1) ** d)[elems]
+    got = gpu_rhs(d, N, n, dom, u, precision="fp32").reshape(-1, d + 2, (N + 1) ** d)[elems]
+    err = rel_l2(got, ref)
+    print(f"{ne}^3 N={N} FP32 sampled rel L2 = {err:.3e}")
+    assert err <= TOL32
+
+
+@pytest.mark.parametrize("d,N,n", [(3, 3, (4, 3, 2)), (2, 4, (5, 3)), (3, 5, (2, 2, 2))])
+@pytest.mark.parametrize("vf,sf", [(0, 0), (1, 1), (2, 2), (0, 3)])
+def test_rhs_fp32_small(orc, d, N, n, vf, sf):
+    dom = W.box(d)
+    u = W.random_state(d, N, n, seed=40 + N)
+    ref = oracle_rhs(orc, d, N, n, dom, u, vf, sf)
+    got = gpu_rhs(d, N, n, dom, u, vf, sf, precision="fp32")
+    assert rel_l2(got, ref) <= TOL32, rel_l2(got, ref)
