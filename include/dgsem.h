@@ -135,6 +135,29 @@ int dg_integrals(dg_mesh *mesh, const double *u, double *out);
  * 4 = non-finite); returns DG_ERR_NONPHYSICAL if any is set, and clears it. */
 int dg_mesh_check(dg_mesh *mesh, int *flags);
 
+/* dg_rhs without any device allocation, for callers that cannot allocate:
+ * code running inside another runtime that owns all device memory through
+ * its own arena, plugins with a memory budget fixed at load time, or callers
+ * that may not allocate after their setup phase. (The paper has no
+ * counterpart; it is an interface for such embedders.)
+ * Same arithmetic as dg_rhs in DG_FP64 precision: the mesh is given as plain
+ * arguments (as for dg_mesh_create; opt NULL = defaults, precision must be
+ * DG_FP64) and u, du are caller-owned device float64 arrays of
+ * (d+2) n_elem (N+1)^d values. The surface-flux scratch and the device error
+ * word live in one static device array of 2^21 doubles (16 MiB) that every
+ * GPU which loads the library holds until the process exits; meshes needing
+ * more than 2^21 - 32 face values, d (d+2) n_elem (N+1)^(d-1), are rejected
+ * with DG_ERR_ARG. No cudaMalloc, cudaFree or other allocating call is made.
+ * The first call on a device looks up the array's device address (with
+ * that device current) and caches it; make that first call before any stream
+ * capture. Every call shares the array and it keeps the last call's
+ * contents: the error word is cleared at each call and non-physical states
+ * are not reported by this entry point. Calls that overlap on the GPU (on
+ * different streams, or from different threads) race on the shared scratch.
+ * Asynchronous on cuda_stream. */
+int dg_rhs_noalloc(int d, int N, const int *elements_per_dim, const double *domain,
+                   const dg_options *opt, const double *u, double *du, void *cuda_stream);
+
 /* Thread-local description of the last failed call ("" if none). */
 const char *dg_last_error(void);
 

@@ -318,6 +318,27 @@ int grid_for(long long work, int threads) {
 
 }  // namespace
 
+namespace dg {
+// Internal helpers for other translation units of the library (not exported
+// in the C header): record a failure message, and build the FP64 split-form
+// tables of a uniform mesh with element widths h[0..d-1].
+int set_last_error(int code, const char* msg) { return fail(code, "%s", msg); }
+
+void build_tables_fp64(int d, int N, const double* h, Tables<double>* t) {
+  long double x[8], w[8], Dt[8][8];
+  lgl_basis(N, x, w);
+  split_matrix(N, x, w, Dt);
+  memset(t, 0, sizeof(*t));
+  for (int k = 0; k < d; ++k) {
+    const long double s = -2.0L / (long double)h[k];
+    for (int a = 0; a <= N; ++a)
+      for (int b = 0; b <= N; ++b) t->Ds[k][a][b] = (double)(s * Dt[a][b]);
+    t->liftR[k] = (double)(s / w[N]);
+    t->liftL[k] = (double)(-s / w[0]);
+  }
+}
+}  // namespace dg
+
 extern "C" {
 
 const char* dg_last_error(void) { return g_last_error; }
