@@ -402,6 +402,8 @@ int dg_mesh_create(int d, int N, const int* epd, const double* domain, const dg_
   m->geom.n[2] = m->n[2];
   m->geom.nelem = m->nelem;
   m->geom.gamma = o.gamma;
+  m->geom.gm1 = o.gamma - 1.0;
+  m->geom.gm1inv = 1.0 / (o.gamma - 1.0);
 
   // basis and scaled split-form tables
   long double x[8], w[8], Dt[8][8];

@@ -24,8 +24,10 @@ constexpr unsigned kErrRho = 1u, kErrP = 2u, kErrNaN = 4u;
 
 struct Geom {
   int n[3];         // elements per direction (1 for unused)
-  long long nelem;  // total elements
+  long long nelem;  // total elements (< 2^31)
   double gamma;
+  double gm1;       // gamma - 1
+  double gm1inv;    // 1 / (gamma - 1)
 };
 
 // Per-direction split-form tables, scaled by the inverse Jacobian:
@@ -117,16 +119,48 @@ __device__ __forceinline__ unsigned prim_check(const Prim<R, D>& q) {
   return bad;
 }
 
+// ---- reciprocals ----
+// FP64: hardware approximation (rcp.approx.ftz.f64) refined by two
+// Newton-Raphson steps r <- r + r (1 - x r), each doubling the correct bits;
+// the result is within about one ulp of 1/x for normal x.
+__device__ __forceinline__ double rcp(double x) {
+  double r;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
+  double e = fma(-x, r, 1.0);
+  r = fma(r, e, r);
+  e = fma(-x, r, 1.0);
+  return fma(r, e, r);
+}
+// FP32: the hardware approximation (rcp.approx.ftz.f32, within 1 ulp).
+__device__ __forceinline__ float rcp(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
 // ---- logarithmic mean ----
-// ln_mean(x, y) = (y - x) / ln(y / x). With t = (y - x)/(y + x), f2 = t^2,
-// ln(y/x) = 2 atanh(t) = 2 t (1 + f2/3 + f2^2/5 + ...), so
-//   ln_mean = (x + y) / S(f2),  1 / ln_mean = S(f2) / (x + y),
-//   S(f2) = 2 (1 + f2/3 + f2^2/5 + f2^3/7 + ...).
+// ln_mean(x, y) = (y - x) / ln(y / x). With s = x + y, t = (y - x)/s and
+// f2 = t^2, ln(y/x) = 2 atanh(t), so
+//   ln_mean(x, y)   = (s/2) Q(f2),   Q(f2) = t / atanh(t),
+//   1/ln_mean(x, y) = S(f2) / s,     S(f2) = 2 atanh(t) / t = 2 sum_k f2^k/(2k+1).
+// Q's coefficients are those of the reciprocal power series of
+// atanh(t)/t = sum_k f2^k/(2k+1): 1, -1/3, -4/45, -44/945, -428/14175,
+// -10196/467775, -10719068/638512875, -25865068/1915538625, ...
 // In the series branch y - x is exact (Sterbenz) and every rounding is
 // relative to the result; outside it ln(y/x) = log1p((y - x)/x). Neither
 // branch divides a rounding error by ln(y/x), which the flux differencing
-// would amplify by (2/h)|Dt| |f| / |du|.
-// FP64: f2 < 1e-2 with terms through f2^7 (truncation f2^8/17 < 1e-17).
+// would amplify by (2/h)|Dt||f|/|du|, and the series branch divides nothing.
+// FP64: series for f2 < 1e-2, Q and S through f2^7 (truncation < 2e-18).
+__device__ __forceinline__ double series_q(double f2) {
+  double q = -25865068.0 / 1915538625.0;
+  q = fma(f2, q, -10719068.0 / 638512875.0);
+  q = fma(f2, q, -10196.0 / 467775.0);
+  q = fma(f2, q, -428.0 / 14175.0);
+  q = fma(f2, q, -44.0 / 945.0);
+  q = fma(f2, q, -4.0 / 45.0);
+  q = fma(f2, q, -1.0 / 3.0);
+  return fma(f2, q, 1.0);
+}
 __device__ __forceinline__ double series_s(double f2) {
   double S = 2.0 / 15.0;
   S = fma(f2, S, 2.0 / 13.0);
@@ -137,7 +171,15 @@ __device__ __forceinline__ double series_s(double f2) {
   S = fma(f2, S, 2.0 / 3.0);
   return fma(f2, S, 2.0);
 }
-// FP32: f2 < 4e-2 with terms through f2^5 (truncation f2^6/13 < 4e-10).
+// FP32: series for f2 < 4e-2, Q and S through f2^5 (truncation < 1e-9).
+__device__ __forceinline__ float series_q(float f2) {
+  float q = -10196.0f / 467775.0f;
+  q = fmaf(f2, q, -428.0f / 14175.0f);
+  q = fmaf(f2, q, -44.0f / 945.0f);
+  q = fmaf(f2, q, -4.0f / 45.0f);
+  q = fmaf(f2, q, -1.0f / 3.0f);
+  return fmaf(f2, q, 1.0f);
+}
 __device__ __forceinline__ float series_s(float f2) {
   float S = 2.0f / 11.0f;
   S = fmaf(f2, S, 2.0f / 9.0f);
@@ -148,26 +190,29 @@ __device__ __forceinline__ float series_s(float f2) {
 }
 __device__ __forceinline__ double series_limit(double) { return 1.0e-2; }
 __device__ __forceinline__ float series_limit(float) { return 4.0e-2f; }
-__device__ __forceinline__ double log1p_(double z) { return log1p(z); }
-__device__ __forceinline__ float log1p_(float z) { return log1pf(z); }
+
+// far from x = y: the direct forms (rare on smooth data; kept out of line)
+static __device__ __noinline__ double ln_mean_far(double x, double y) { return (y - x) / log1p((y - x) / x); }
+static __device__ __noinline__ float ln_mean_far(float x, float y) { return (y - x) / log1pf((y - x) / x); }
+static __device__ __noinline__ double inv_ln_mean_far(double x, double y) { return log1p((y - x) / x) / (y - x); }
+static __device__ __noinline__ float inv_ln_mean_far(float x, float y) { return log1pf((y - x) / x) / (y - x); }
 
 template <typename R>
 __device__ __forceinline__ R ln_mean(R x, R y) {
-  const R s = x + y, d = y - x;
-  const R t = d / s;
+  const R s = x + y;
+  const R t = (y - x) * rcp(s);
   const R f2 = t * t;
-  if (f2 < series_limit(R(0))) return s / series_s(f2);
-  return d / log1p_(d / x);
+  if (f2 < series_limit(R(0))) return R(0.5) * s * series_q(f2);
+  return ln_mean_far(x, y);
 }
 
 template <typename R>
 __device__ __forceinline__ R inv_ln_mean(R x, R y) {
-  const R s = x + y, d = y - x;
-  const R rs = R(1) / s;
-  const R t = d * rs;
+  const R rs = rcp(x + y);
+  const R t = (y - x) * rs;
   const R f2 = t * t;
   if (f2 < series_limit(R(0))) return series_s(f2) * rs;
-  return log1p_(d / x) / d;
+  return inv_ln_mean_far(x, y);
 }
 
 // ---- two-point volume fluxes f#(L, R) in direction DIR ----

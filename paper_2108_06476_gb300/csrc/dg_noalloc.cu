@@ -94,6 +94,8 @@ extern "C" int dg_rhs_noalloc(int d, int N, const int* elements_per_dim, const d
     if (g.nelem > kFaceValues) break;
   }
   g.gamma = o.gamma;
+  g.gm1 = o.gamma - 1.0;
+  g.gm1inv = 1.0 / (o.gamma - 1.0);
   const long long face_values = (long long)d * (d + 2) * g.nelem * lines;
   if (g.nelem > kFaceValues || face_values > kFaceValues)
     return fail(DG_ERR_ARG,

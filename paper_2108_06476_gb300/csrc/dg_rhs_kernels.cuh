@@ -7,88 +7,187 @@
 //
 //  volume_kernel: one CTA per EPB elements, one thread per element line.
 //    Prologue: conserved -> primitive at every node into shared memory.
-//    Per direction: each thread walks its line's N(N+1)/2 node pairs once,
-//    evaluating f#(u_a, u_b) a single time for both nodes, since f# is
-//    symmetric and the split-form matrix has a zero diagonal:
+//    Per direction (a runtime loop; the flux is written with the direction's
+//    normal component first, so one code body serves every direction): each
+//    thread walks its line's N(N+1)/2 node pairs once, evaluating f#(u_a, u_b)
+//    a single time for both nodes, since f# is symmetric and the split-form
+//    matrix has a zero diagonal:
 //      du_a += Ds[a][b] f#(u_a, u_b),  du_b += Ds[b][a] f#(u_a, u_b).
 //    Epilogue: lifting of the face fluxes at the element's boundary nodes,
 //    du += liftR F*_R (node N) + liftL F*_L (node 0) per direction, and one
 //    coalesced store of du.
+//
+// FP32 kernels keep the pressure relative to a per-element reference P_e
+// (P_e = fl32((gamma-1) E at the element's first node); p' = p - P_e is formed
+// from the FP64 energy difference E - E_ref). Because the rows of Ds sum to
+// -lift at the boundary nodes and to zero inside, the constant P_e in the
+// normal-momentum flux and the term P_e avg(v_n) in the energy flux cancel
+// analytically against the lifting: the kernels accumulate only p' parts,
+// add P_e sum_b Ds_ab avg(v_n) to the energy once per node, and store the
+// normal-momentum surface flux relative to the left element's P_e.
 #pragma once
 #include "dg_device.cuh"
 
 namespace dg {
 
-template <int D, int N, typename R>
-__global__ void surface_kernel(const double* __restrict__ u, R* __restrict__ fs, Geom g, int sf) {
-  using S = Shape<D, N>;
-  constexpr int NV = S::NV, P = S::P, NF = S::LINES;
-  const int dir = blockIdx.y;
-  const long long total = g.nelem * NF;
-  const R gamma = R(g.gamma), gm1 = R(g.gamma - 1.0), gm1inv = R(1.0 / (g.gamma - 1.0));
-  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
-       t += (long long)gridDim.x * blockDim.x) {
-    const long long e = t / NF;
-    const int l = (int)(t % NF);
-    const long long er = neighbour(g, e, dir, +1);
-    const int nl = line_node_rt<D, N>(dir, l, N), nr = line_node_rt<D, N>(dir, l, 0);
-    R cl[NV], cr[NV];
-#pragma unroll
-    for (int v = 0; v < NV; ++v) {
-      cl[v] = R(u[(e * NV + v) * P + nl]);
-      cr[v] = R(u[(er * NV + v) * P + nr]);
-    }
-    const Prim<R, D> ql = cons2prim<R, D>(cl, gm1), qr = cons2prim<R, D>(cr, gm1);
-    R f[NV];
-    if (dir == 0) surface_flux_dir<R, D, 0>(sf, cl, cr, ql, qr, gamma, gm1inv, f);
-    else if (dir == 1) surface_flux_dir<R, D, 1>(sf, cl, cr, ql, qr, gamma, gm1inv, f);
-    else surface_flux_dir<R, D, (D == 3 ? 2 : 1)>(sf, cl, cr, ql, qr, gamma, gm1inv, f);
-#pragma unroll
-    for (int v = 0; v < NV; ++v) fs[((long long)(dir * NV + v) * g.nelem + e) * NF + l] = f[v];
-  }
+__device__ __forceinline__ int elem_index(const Geom& g, int x, int y, int z) {
+  return x + g.n[0] * (y + g.n[1] * z);
 }
 
-// One direction of the flux-differencing volume term for the line owned by
-// this thread; adds the line's contributions into the shared accumulators.
-template <int D, int N, typename R, int VF, int DIR, int EPB>
-__device__ __forceinline__ void volume_direction(R (*sp)[D + 2][Shape<D, N>::P],
-                                                 R (*sa)[D + 2][Shape<D, N>::P], int el, int l,
-                                                 const Tables<R>& tb, R gm1inv) {
+// periodic neighbour of element e at offset s = +-1 in direction dir (32-bit)
+__device__ __forceinline__ int neighbour32(const Geom& g, int e, int dir, int s) {
+  int x = e % g.n[0];
+  const int r = e / g.n[0];
+  int y = r % g.n[1];
+  int z = r / g.n[1];
+  if (dir == 0) x = (x + s + g.n[0]) % g.n[0];
+  else if (dir == 1) y = (y + s + g.n[1]) % g.n[1];
+  else z = (z + s + g.n[2]) % g.n[2];
+  return elem_index(g, x, y, z);
+}
+
+// FP32 pressure reference of element e: P_e = fl32((gamma-1) E_ref) and the
+// residual c_e = fl32((gamma-1) E_ref - P_e), E_ref = E at the first node.
+__device__ __forceinline__ void pressure_ref(const double* __restrict__ u, int e, int nv, int P,
+                                             double gm1, float& Pe, float& ce, double& Eref) {
+  Eref = u[((long long)e * nv + nv - 1) * P];
+  const double pe = gm1 * Eref;
+  Pe = (float)pe;
+  ce = (float)(pe - (double)Pe);
+}
+
+// FP32 primitives of one node: rho, v, the pressure offset p' = p - P_e
+// (from the FP64 energy difference), and the full pressure P_e + p'.
+template <int D>
+__device__ __forceinline__ void prim_f32(const double* c, float gm1, float Pe, float ce,
+                                         double Eref, float& rho, float* v, float& pp,
+                                         float& p) {
+  rho = (float)c[0];
+  const float rr = rcp(rho);
+  float ke = 0.0f;
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    v[k] = (float)c[1 + k] * rr;
+    ke = fmaf(v[k], v[k], ke);
+  }
+  ke *= 0.5f * rho;
+  const float dE = (float)(c[D + 1] - Eref);
+  pp = fmaf(gm1, dE - ke, ce);
+  p = Pe + pp;
+}
+
+// node primitives as seen by one direction: normal component first
+template <typename R, int D>
+struct LinePrim {
+  R rho, p, hp, pg, vn, hvn;
+  R vt[D - 1], hvt[D - 1];
+};
+
+// Ranocha's EC/KEP flux in normal-first order. hp is p/2 (FP64) or p'/2
+// (FP32, then the P_e parts are handled by the caller); an = avg(v_n).
+template <typename R, int D>
+__device__ __forceinline__ void ranocha_nf(const LinePrim<R, D>& L, const LinePrim<R, D>& Rt,
+                                           R f[D + 2], R& an) {
+  const R rho_ln = ln_mean(L.rho, Rt.rho);
+  const R inv = inv_ln_mean(L.rho * Rt.p, Rt.rho * L.p);
+  an = L.hvn + Rt.hvn;
+  const R f0 = rho_ln * an;
+  f[0] = f0;
+  f[1] = fma(f0, an, L.hp + Rt.hp);
+#pragma unroll
+  for (int j = 0; j < D - 1; ++j) f[2 + j] = f0 * (L.hvt[j] + Rt.hvt[j]);
+  R vd = L.hvn * Rt.vn;
+#pragma unroll
+  for (int j = 0; j < D - 1; ++j) vd = fma(L.hvt[j], Rt.vt[j], vd);
+  const R ee = fma(L.p * Rt.pg, inv, vd);  // v_L.v_R / 2 + p_L p_R / ((gamma-1) ln_mean(rho p))
+  f[D + 1] = fma(f0, ee, fma(L.hp, Rt.vn, Rt.hp * L.vn));
+}
+
+// the other volume fluxes through the generic (Prim) forms, normal first
+template <int VF, typename R, int D>
+__device__ __forceinline__ void generic_nf(const LinePrim<R, D>& L, const LinePrim<R, D>& Rt,
+                                           R gm1inv, R f[D + 2]) {
+  Prim<R, D> a, b;
+  a.rho = L.rho;
+  a.p = L.p;
+  a.v[0] = L.vn;
+  b.rho = Rt.rho;
+  b.p = Rt.p;
+  b.v[0] = Rt.vn;
+#pragma unroll
+  for (int j = 0; j < D - 1; ++j) {
+    a.v[1 + j] = L.vt[j];
+    b.v[1 + j] = Rt.vt[j];
+  }
+  volume_flux<VF, R, D, 0>(a, b, gm1inv, f);
+}
+
+template <int D, int N, typename R, int VF, int EPB>
+__device__ __forceinline__ void volume_direction(int dir, R (*sp)[4 + 2 * D][Shape<D, N>::P],
+                                                 R (*sa)[D + 3][Shape<D, N>::P], int el, int l,
+                                                 const Tables<R>& tb, R gm1inv, R Pe) {
   using S = Shape<D, N>;
   constexpr int NP = S::NP, NV = S::NV;
-  Prim<R, D> q[NP];
+  constexpr bool F32 = sizeof(R) == 4;
+  constexpr bool SHIFT_E = F32 && VF == kVRanocha;  // P_e avg(v_n) accumulated apart
+  constexpr int NA = NV + (SHIFT_E ? 1 : 0);
+  const int t1 = (dir + 1) % D, t2 = (dir + 2) % D;
+  int node[NP];
+  LinePrim<R, D> q[NP];
 #pragma unroll
   for (int a = 0; a < NP; ++a) {
-    const int node = line_node<D, N, DIR>(l, a);
-    q[a].rho = sp[el][0][node];
-#pragma unroll
-    for (int k = 0; k < D; ++k) q[a].v[k] = sp[el][1 + k][node];
-    q[a].p = sp[el][D + 1][node];
+    node[a] = line_node_rt<D, N>(dir, l, a);
+    const int nd = node[a];
+    q[a].rho = sp[el][0][nd];
+    q[a].p = sp[el][1][nd];
+    q[a].hp = sp[el][2][nd];
+    q[a].pg = sp[el][3][nd];
+    q[a].vn = sp[el][4 + dir][nd];
+    q[a].hvn = sp[el][4 + D + dir][nd];
+    q[a].vt[0] = sp[el][4 + t1][nd];
+    q[a].hvt[0] = sp[el][4 + D + t1][nd];
+    if (D == 3) {
+      q[a].vt[D - 2] = sp[el][4 + t2][nd];
+      q[a].hvt[D - 2] = sp[el][4 + D + t2][nd];
+    }
   }
-  R acc[NP][NV];
+  R acc[NP][NA];
 #pragma unroll
   for (int a = 0; a < NP; ++a)
 #pragma unroll
-    for (int v = 0; v < NV; ++v) acc[a][v] = R(0);
+    for (int v = 0; v < NA; ++v) acc[a][v] = R(0);
 #pragma unroll
   for (int a = 0; a < NP; ++a) {
 #pragma unroll
     for (int b = a + 1; b < NP; ++b) {
-      R f[NV];
-      volume_flux<VF, R, D, DIR>(q[a], q[b], gm1inv, f);
-      const R dab = tb.Ds[DIR][a][b], dba = tb.Ds[DIR][b][a];
+      R f[NV], an = R(0);
+      if (VF == kVRanocha) {
+        ranocha_nf<R, D>(q[a], q[b], f, an);
+      } else {
+        generic_nf<VF, R, D>(q[a], q[b], gm1inv, f);
+        if (F32) f[1] -= Pe;
+      }
+      const R dab = tb.Ds[dir][a][b], dba = tb.Ds[dir][b][a];
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
-        acc[a][v] += dab * f[v];
-        acc[b][v] += dba * f[v];
+        acc[a][v] = fma(dab, f[v], acc[a][v]);
+        acc[b][v] = fma(dba, f[v], acc[b][v]);
+      }
+      if (SHIFT_E) {
+        acc[a][NA - 1] = fma(dab, an, acc[a][NA - 1]);
+        acc[b][NA - 1] = fma(dba, an, acc[b][NA - 1]);
       }
     }
   }
 #pragma unroll
   for (int a = 0; a < NP; ++a) {
-    const int node = line_node<D, N, DIR>(l, a);
-#pragma unroll
-    for (int v = 0; v < NV; ++v) sa[el][v][node] += acc[a][v];
+    const int nd = node[a];
+    sa[el][0][nd] += acc[a][0];
+    sa[el][1 + dir][nd] += acc[a][1];
+    sa[el][1 + t1][nd] += acc[a][2];
+    if (D == 3) sa[el][1 + t2][nd] += acc[a][D];
+    sa[el][D + 1][nd] += acc[a][D + 1];
+    if (SHIFT_E) sa[el][D + 2][nd] += acc[a][NA - 1];
   }
 }
 
@@ -98,76 +197,311 @@ __global__ void __launch_bounds__(EPB* Shape<D, N>::LINES)
                   Geom g, Tables<R> tb, unsigned* __restrict__ err) {
   using S = Shape<D, N>;
   constexpr int NP = S::NP, P = S::P, NV = S::NV, LINES = S::LINES;
-  __shared__ R sp[EPB][NV][P];  // primitives rho, v_1..v_d, p
-  __shared__ R sa[EPB][NV][P];  // accumulated volume terms
-  const long long e0 = (long long)blockIdx.x * EPB;
-  const R gm1 = R(g.gamma - 1.0), gm1inv = R(1.0 / (g.gamma - 1.0));
+  constexpr bool F32 = sizeof(R) == 4;
+  constexpr int NC = 4 + 2 * D;  // rho, p, p/2 (or p'/2), p/(gamma-1), v[D], v[D]/2
+  extern __shared__ __align__(16) unsigned char dg_smem[];
+  R(*sp)[NC][P] = reinterpret_cast<R(*)[NC][P]>(dg_smem);
+  R(*sa)[D + 3][P] = reinterpret_cast<R(*)[D + 3][P]>(dg_smem + sizeof(R) * EPB * NC * P);
+  __shared__ int s_left[EPB][3];
+  __shared__ float s_pref[EPB][4];  // FP32: own P_e, then the left neighbours' P
+  __shared__ float s_cref[EPB];
+  __shared__ double s_eref[EPB];
+  const int e0 = blockIdx.x * EPB;
+  const int nelem = (int)g.nelem;
+  const R gm1inv = R(g.gm1inv);
+  if (threadIdx.x < EPB && e0 + (int)threadIdx.x < nelem) {
+    const int el = threadIdx.x, e = e0 + el;
+    const int x = e % g.n[0], r = e / g.n[0], y = r % g.n[1], z = r / g.n[1];
+    s_left[el][0] = elem_index(g, x == 0 ? g.n[0] - 1 : x - 1, y, z);
+    s_left[el][1] = elem_index(g, x, y == 0 ? g.n[1] - 1 : y - 1, z);
+    s_left[el][2] = (D == 3) ? elem_index(g, x, y, z == 0 ? g.n[2] - 1 : z - 1) : 0;
+    if (F32) {
+      float Pe, ce;
+      double Er;
+      pressure_ref(u, e, NV, P, g.gm1, Pe, ce, Er);
+      s_pref[el][0] = Pe;
+      s_cref[el] = ce;
+      s_eref[el] = Er;
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        float Pl, cl;
+        double El;
+        pressure_ref(u, s_left[el][k], NV, P, g.gm1, Pl, cl, El);
+        s_pref[el][1 + k] = Pl;
+      }
+    }
+  }
+  __syncthreads();
   unsigned bad = 0;
   for (int t = threadIdx.x; t < EPB * P; t += blockDim.x) {
     const int el = t / P, node = t % P;
-    const long long e = e0 + el;
-    if (e < g.nelem) {
-      R c[NV];
+    const int e = e0 + el;
+    if (e >= nelem) continue;
+    double c[NV];
 #pragma unroll
-      for (int v = 0; v < NV; ++v) c[v] = R(u[(e * NV + v) * P + node]);
-      const Prim<R, D> q = cons2prim<R, D>(c, gm1);
+    for (int v = 0; v < NV; ++v) c[v] = u[((long long)e * NV + v) * P + node];
+    R rho, p, hp, v[D];
+    if (F32) {
+      float vf[D], pp, pf, rf;
+      prim_f32<D>(c, (float)g.gm1, s_pref[el][0], s_cref[el], s_eref[el], rf, vf, pp, pf);
+      rho = R(rf);
+      p = R(pf);
+      hp = R(0.5f * pp);
+#pragma unroll
+      for (int k = 0; k < D; ++k) v[k] = R(vf[k]);
+      if (!(rf > 0.0f)) bad |= kErrRho;
+      if (!(pf > 0.0f)) bad |= kErrP;
+      if (!isfinite(rf) || !isfinite(pf)) bad |= kErrNaN;
+    } else {
+      const Prim<double, D> q = cons2prim<double, D>(c, g.gm1);
       bad |= prim_check(q);
-      sp[el][0][node] = q.rho;
+      rho = R(q.rho);
+      p = R(q.p);
+      hp = R(0.5) * p;
 #pragma unroll
-      for (int k = 0; k < D; ++k) sp[el][1 + k][node] = q.v[k];
-      sp[el][D + 1][node] = q.p;
-#pragma unroll
-      for (int v = 0; v < NV; ++v) sa[el][v][node] = R(0);
+      for (int k = 0; k < D; ++k) v[k] = R(q.v[k]);
     }
+    sp[el][0][node] = rho;
+    sp[el][1][node] = p;
+    sp[el][2][node] = hp;
+    sp[el][3][node] = p * gm1inv;
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      sp[el][4 + k][node] = v[k];
+      sp[el][4 + D + k][node] = R(0.5) * v[k];
+    }
+#pragma unroll
+    for (int k = 0; k < D + 3; ++k) sa[el][k][node] = R(0);
   }
   if (bad) atomicOr(err, bad);
   __syncthreads();
   const int el = threadIdx.x / LINES, l = threadIdx.x % LINES;
-  const bool active = (e0 + el) < g.nelem;
-  if (active) volume_direction<D, N, R, VF, 0, EPB>(sp, sa, el, l, tb, gm1inv);
-  __syncthreads();
-  if (active) volume_direction<D, N, R, VF, 1, EPB>(sp, sa, el, l, tb, gm1inv);
-  if (D == 3) {
+  const bool active = (e0 + el) < nelem;
+  const R Pe = F32 ? R(s_pref[active ? el : 0][0]) : R(0);
+#pragma unroll 1
+  for (int dir = 0; dir < D; ++dir) {
+    if (active) volume_direction<D, N, R, VF, EPB>(dir, sp, sa, el, l, tb, gm1inv, Pe);
     __syncthreads();
-    if (active) volume_direction<D, N, R, VF, (D == 3 ? 2 : 1), EPB>(sp, sa, el, l, tb, gm1inv);
   }
-  __syncthreads();
   // epilogue: lifting of the surface fluxes, then the store
   for (int t = threadIdx.x; t < EPB * P; t += blockDim.x) {
     const int ell = t / P, node = t % P;
-    const long long e = e0 + ell;
-    if (e >= g.nelem) continue;
-    int c[3] = {node % NP, (node / NP) % NP, node / (NP * NP)};
+    const int e = e0 + ell;
+    if (e >= nelem) continue;
+    const int c[3] = {node % NP, (node / NP) % NP, node / (NP * NP)};
+    const R Pself = F32 ? R(s_pref[ell][0]) : R(0);
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
       R val = sa[ell][v][node];
+      if (F32 && VF == kVRanocha && v == D + 1) val = fma(Pself, sa[ell][D + 2][node], val);
 #pragma unroll
       for (int dir = 0; dir < D; ++dir) {
         // face-node index: the node's other coordinates, first one fastest
-        const int lf = (dir == 0) ? (c[1] + NP * c[2]) : (dir == 1) ? (c[0] + NP * c[2])
-                                                                    : (c[0] + NP * c[1]);
-        const int lf2 = (D == 2) ? ((dir == 0) ? c[1] : c[0]) : lf;
+        const int lf = (D == 2) ? ((dir == 0) ? c[1] : c[0])
+                                : (dir == 0) ? (c[1] + NP * c[2])
+                                : (dir == 1) ? (c[0] + NP * c[2]) : (c[0] + NP * c[1]);
         if (c[dir] == N)
-          val += tb.liftR[dir] * fs[((long long)(dir * NV + v) * g.nelem + e) * LINES + lf2];
+          val = fma(tb.liftR[dir], fs[((long long)(dir * NV + v) * nelem + e) * LINES + lf], val);
         if (c[dir] == 0) {
-          const long long el_ = neighbour(g, e, dir, -1);
-          val += tb.liftL[dir] * fs[((long long)(dir * NV + v) * g.nelem + el_) * LINES + lf2];
+          R F = fs[((long long)(dir * NV + v) * nelem + s_left[ell][dir]) * LINES + lf];
+          if (F32 && v == 1 + dir) F += R(s_pref[ell][1 + dir]) - Pself;
+          val = fma(tb.liftL[dir], F, val);
         }
       }
-      du[(e * NV + v) * P + node] = val;
+      du[((long long)e * NV + v) * P + node] = val;
     }
   }
 }
 
-// elements per CTA: about 128 threads, shared memory <= 40 KB
+// ---- surface ----
+// trace state for the surface flux, normal component first; ps is the
+// pressure in the additive normal-momentum term (p itself in FP64, p minus the
+// left element's P_e in FP32)
+template <typename R, int D>
+struct Trace {
+  R rho, p, ps, vn, vt[D - 1], mn, mt[D - 1], E;
+};
+
+template <typename R, int D>
+__device__ __forceinline__ void surface_nf(int sf, const Trace<R, D>& L, const Trace<R, D>& Rt,
+                                           R dE, R gamma, R gm1inv, R f[D + 2]) {
+  if (sf == kSRanocha) {
+    const R rho_ln = ln_mean(L.rho, Rt.rho);
+    const R inv = inv_ln_mean(L.rho * Rt.p, Rt.rho * L.p);
+    const R an = R(0.5) * (L.vn + Rt.vn);
+    const R f0 = rho_ln * an;
+    f[0] = f0;
+    f[1] = f0 * an + R(0.5) * (L.ps + Rt.ps);
+    R vd = L.vn * Rt.vn;
+#pragma unroll
+    for (int j = 0; j < D - 1; ++j) {
+      f[2 + j] = f0 * R(0.5) * (L.vt[j] + Rt.vt[j]);
+      vd += L.vt[j] * Rt.vt[j];
+    }
+    f[D + 1] = f0 * (R(0.5) * vd + L.p * Rt.p * inv * gm1inv) +
+               R(0.5) * (L.p * Rt.vn + Rt.p * L.vn);
+    return;
+  }
+  if (sf == kSChandrashekar) {
+    Prim<R, D> a, b;
+    a.rho = L.rho;
+    a.p = L.p;
+    a.v[0] = L.vn;
+    b.rho = Rt.rho;
+    b.p = Rt.p;
+    b.v[0] = Rt.vn;
+#pragma unroll
+    for (int j = 0; j < D - 1; ++j) {
+      a.v[1 + j] = L.vt[j];
+      b.v[1 + j] = Rt.vt[j];
+    }
+    flux_chandrashekar<R, D, 0>(a, b, gm1inv, f);
+    f[1] -= L.p - L.ps;
+    return;
+  }
+  R fl[D + 2], fr[D + 2], dq[D + 2];
+  fl[0] = L.mn;
+  fr[0] = Rt.mn;
+  fl[1] = L.mn * L.vn + L.ps;
+  fr[1] = Rt.mn * Rt.vn + Rt.ps;
+#pragma unroll
+  for (int j = 0; j < D - 1; ++j) {
+    fl[2 + j] = L.mn * L.vt[j];
+    fr[2 + j] = Rt.mn * Rt.vt[j];
+    dq[2 + j] = Rt.mt[j] - L.mt[j];
+  }
+  fl[D + 1] = (L.E + L.p) * L.vn;
+  fr[D + 1] = (Rt.E + Rt.p) * Rt.vn;
+  dq[0] = Rt.rho - L.rho;
+  dq[1] = Rt.mn - L.mn;
+  dq[D + 1] = dE;
+  const R cl = sqrt(gamma * L.p / L.rho), cr = sqrt(gamma * Rt.p / Rt.rho);
+  if (sf == kSLLF) {
+    const R lam = fmax(fabs(L.vn), fabs(Rt.vn)) + fmax(cl, cr);
+#pragma unroll
+    for (int v = 0; v < D + 2; ++v) f[v] = R(0.5) * (fl[v] + fr[v]) - R(0.5) * lam * dq[v];
+    return;
+  }
+  const R sL = fmin(L.vn - cl, Rt.vn - cr);
+  const R sR = fmax(L.vn + cl, Rt.vn + cr);
+#pragma unroll
+  for (int v = 0; v < D + 2; ++v) {
+    if (sL >= R(0)) f[v] = fl[v];
+    else if (sR <= R(0)) f[v] = fr[v];
+    else f[v] = (sR * fl[v] - sL * fr[v] + sL * sR * dq[v]) / (sR - sL);
+  }
+}
+
+template <int D, int N, typename R, int dir>
+__device__ __forceinline__ void surface_body(const double* __restrict__ u, R* __restrict__ fs,
+                                             const Geom& g, int sf) {
+  using S = Shape<D, N>;
+  constexpr int NV = S::NV, P = S::P, NF = S::LINES;
+  constexpr bool F32 = sizeof(R) == 4;
+  const int nelem = (int)g.nelem;
+  const long long total = (long long)nelem * NF;
+  const R gamma = R(g.gamma), gm1inv = R(g.gm1inv);
+  constexpr int t1 = (dir + 1) % D, t2 = (dir + 2) % D;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int e = (int)(t / NF);
+    const int l = (int)(t % NF);
+    const int er = neighbour32(g, e, dir, +1);
+    const int nl = line_node<D, N, dir>(l, N), nr = line_node<D, N, dir>(l, 0);
+    double cl[NV], cr[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      cl[v] = u[((long long)e * NV + v) * P + nl];
+      cr[v] = u[((long long)er * NV + v) * P + nr];
+    }
+    Trace<R, D> L, Rt;
+    R dE;
+    if (F32) {
+      float PeL, ceL, PeR, ceR, vL[D], vR[D], ppL, ppR, pL, pR, rL, rR;
+      double ErL, ErR;
+      pressure_ref(u, e, NV, P, g.gm1, PeL, ceL, ErL);
+      pressure_ref(u, er, NV, P, g.gm1, PeR, ceR, ErR);
+      prim_f32<D>(cl, (float)g.gm1, PeL, ceL, ErL, rL, vL, ppL, pL);
+      prim_f32<D>(cr, (float)g.gm1, PeR, ceR, ErR, rR, vR, ppR, pR);
+      L.rho = R(rL);
+      L.p = R(pL);
+      L.ps = R(ppL);
+      Rt.rho = R(rR);
+      Rt.p = R(pR);
+      Rt.ps = R(ppR + (PeR - PeL));
+      L.vn = R(vL[dir]);
+      Rt.vn = R(vR[dir]);
+      L.vt[0] = R(vL[t1]);
+      Rt.vt[0] = R(vR[t1]);
+      if (D == 3) {
+        L.vt[D - 2] = R(vL[t2]);
+        Rt.vt[D - 2] = R(vR[t2]);
+      }
+      dE = R((float)(cr[NV - 1] - cl[NV - 1]));
+    } else {
+      const Prim<double, D> ql = cons2prim<double, D>(cl, g.gm1);
+      const Prim<double, D> qr = cons2prim<double, D>(cr, g.gm1);
+      L.rho = R(ql.rho);
+      L.p = R(ql.p);
+      L.ps = L.p;
+      Rt.rho = R(qr.rho);
+      Rt.p = R(qr.p);
+      Rt.ps = Rt.p;
+      L.vn = R(ql.v[dir]);
+      Rt.vn = R(qr.v[dir]);
+      L.vt[0] = R(ql.v[t1]);
+      Rt.vt[0] = R(qr.v[t1]);
+      if (D == 3) {
+        L.vt[D - 2] = R(ql.v[t2]);
+        Rt.vt[D - 2] = R(qr.v[t2]);
+      }
+      dE = R(cr[NV - 1] - cl[NV - 1]);
+    }
+    L.mn = R(cl[1 + dir]);
+    Rt.mn = R(cr[1 + dir]);
+    L.mt[0] = R(cl[1 + t1]);
+    Rt.mt[0] = R(cr[1 + t1]);
+    if (D == 3) {
+      L.mt[D - 2] = R(cl[1 + t2]);
+      Rt.mt[D - 2] = R(cr[1 + t2]);
+    }
+    L.E = R(cl[NV - 1]);
+    Rt.E = R(cr[NV - 1]);
+    R f[NV];
+    surface_nf<R, D>(sf, L, Rt, dE, gamma, gm1inv, f);
+    const long long base = (long long)nelem * NF;
+    const long long off = (long long)e * NF + l;
+    fs[(long long)(dir * NV + 0) * base + off] = f[0];
+    fs[(long long)(dir * NV + 1 + dir) * base + off] = f[1];
+    fs[(long long)(dir * NV + 1 + t1) * base + off] = f[2];
+    if (D == 3) fs[(long long)(dir * NV + 1 + t2) * base + off] = f[D];
+    fs[(long long)(dir * NV + NV - 1) * base + off] = f[NV - 1];
+  }
+}
+
+template <int D, int N, typename R>
+__global__ void surface_kernel(const double* __restrict__ u, R* __restrict__ fs, Geom g, int sf) {
+  if (blockIdx.y == 0) surface_body<D, N, R, 0>(u, fs, g, sf);
+  else if (blockIdx.y == 1) surface_body<D, N, R, 1>(u, fs, g, sf);
+  else surface_body<D, N, R, (D == 3 ? 2 : 1)>(u, fs, g, sf);
+}
+
+// elements per CTA: about 128 threads, dynamic shared memory <= 96 KB
 template <int D, int N, typename R>
 struct Launch {
   static constexpr int LINES = Shape<D, N>::LINES;
   static constexpr int BY_THREADS = (128 / LINES) > 0 ? (128 / LINES) : 1;
-  static constexpr int PER_ELEM = 2 * Shape<D, N>::NV * Shape<D, N>::P * (int)sizeof(R);
-  static constexpr int BY_SMEM = (40960 / PER_ELEM) > 0 ? (40960 / PER_ELEM) : 1;
+  static constexpr int PER_ELEM = (4 + 2 * D + D + 3) * Shape<D, N>::P * (int)sizeof(R);
+  static constexpr int BY_SMEM = (98304 / PER_ELEM) > 0 ? (98304 / PER_ELEM) : 1;
   static constexpr int EPB = BY_THREADS < BY_SMEM ? BY_THREADS : BY_SMEM;
+  static constexpr int SMEM = EPB * PER_ELEM;
 };
+
+template <typename K>
+cudaError_t allow_smem(K kernel, int bytes) {
+  if (bytes <= 48 * 1024) return cudaSuccess;
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
 
 // parts: bit 0 = surface kernel, bit 1 = volume kernel (both for an rhs)
 template <int D, int N, typename R>
@@ -185,12 +519,18 @@ cudaError_t launch_rhs_dn(const double* u, R* du, R* fs, const Geom& g, const Ta
   if (!(parts & 2)) return cudaGetLastError();
   const long long grid = (g.nelem + EPB - 1) / EPB;
   const int threads = EPB * L::LINES;
-  if (vf == kVRanocha)
-    volume_kernel<D, N, R, kVRanocha, EPB><<<(unsigned)grid, threads, 0, st>>>(u, du, fs, g, tb, err);
-  else if (vf == kVChandrashekar)
-    volume_kernel<D, N, R, kVChandrashekar, EPB><<<(unsigned)grid, threads, 0, st>>>(u, du, fs, g, tb, err);
-  else
-    volume_kernel<D, N, R, kVCentral, EPB><<<(unsigned)grid, threads, 0, st>>>(u, du, fs, g, tb, err);
+  constexpr int SM = L::SMEM;
+  cudaError_t e;
+  if (vf == kVRanocha) {
+    if ((e = allow_smem(volume_kernel<D, N, R, kVRanocha, EPB>, SM)) != cudaSuccess) return e;
+    volume_kernel<D, N, R, kVRanocha, EPB><<<(unsigned)grid, threads, SM, st>>>(u, du, fs, g, tb, err);
+  } else if (vf == kVChandrashekar) {
+    if ((e = allow_smem(volume_kernel<D, N, R, kVChandrashekar, EPB>, SM)) != cudaSuccess) return e;
+    volume_kernel<D, N, R, kVChandrashekar, EPB><<<(unsigned)grid, threads, SM, st>>>(u, du, fs, g, tb, err);
+  } else {
+    if ((e = allow_smem(volume_kernel<D, N, R, kVCentral, EPB>, SM)) != cudaSuccess) return e;
+    volume_kernel<D, N, R, kVCentral, EPB><<<(unsigned)grid, threads, SM, st>>>(u, du, fs, g, tb, err);
+  }
   return cudaGetLastError();
 }
 
