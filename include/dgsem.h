@@ -104,6 +104,16 @@ int dg_rhs(dg_mesh *mesh, const double *u, void *du);
  * Asynchronous. */
 int dg_rhs_part(dg_mesh *mesh, const double *u, void *du, int parts);
 
+/* Vector-Jacobian product of the rhs: ubar = (d rhs/d u)(u)^T w, for
+ * differentiating through simulations (Sec. 2 feature list: automatic
+ * differentiation of the semidiscretisation). u, w, ubar: device float64
+ * [n_values], same layout as u. The two-point and surface-flux Jacobians are
+ * recomputed with forward-mode dual numbers (nothing is kept from dg_rhs);
+ * at non-smooth points max/min take the first argument on ties and
+ * d|x|/dx = sign(x), sign(0) = +1. DG_FP32 meshes evaluate the Jacobians in
+ * float. Allocates the face adjoint buffer on first use. Asynchronous. */
+int dg_rhs_vjp(dg_mesh *mesh, const double *u, const double *w, double *ubar);
+
 /* One stage of the Carpenter-Kennedy 2N-storage scheme (Sec. 3.1):
  * k <- a k + dt du; u <- u + b k, with the library-owned register k
  * (zeroed at creation and by dg_rk_reset). du has the rhs dtype of the mesh.

@@ -19,6 +19,14 @@ cudaError_t rhs_launch_float_2(int, const double*, float*, float*, const Geom&,
                                const Tables<float>&, int, int, unsigned*, cudaStream_t, int);
 cudaError_t rhs_launch_float_3(int, const double*, float*, float*, const Geom&,
                                const Tables<float>&, int, int, unsigned*, cudaStream_t, int);
+cudaError_t vjp_launch_double_2(int, const double*, const double*, double*, double*, const Geom&,
+                                const Tables<double>&, int, int, cudaStream_t);
+cudaError_t vjp_launch_double_3(int, const double*, const double*, double*, double*, const Geom&,
+                                const Tables<double>&, int, int, cudaStream_t);
+cudaError_t vjp_launch_float_2(int, const double*, const double*, double*, double*, const Geom&,
+                               const Tables<double>&, int, int, cudaStream_t);
+cudaError_t vjp_launch_float_3(int, const double*, const double*, double*, double*, const Geom&,
+                               const Tables<double>&, int, int, cudaStream_t);
 }  // namespace dg
 
 using dg::Geom;
@@ -43,6 +51,7 @@ struct dg_mesh {
   double* red_out;     // 7 * 2 doubles
   unsigned long long* speed;  // max wave-speed sum (as ordered bits)
   unsigned* err;       // device error word
+  double* fbar;        // face adjoint buffer of dg_rhs_vjp, allocated on first use
 };
 
 namespace {
@@ -190,7 +199,7 @@ __global__ void speed_kernel(const double* __restrict__ u, Geom g, int P, double
       for (int v = 0; v < NV; ++v) c[v] = u[(e * NV + v) * P + node];
       const dg::Prim<double, D> q = dg::cons2prim<double, D>(c, gm1);
       bad |= dg::prim_check(q);
-      const double cs = sqrt(g.gamma * q.p / q.rho);
+      const double cs = sqrt(g.gamma * q.p * (1.0 / q.rho));
 #pragma unroll
       for (int k = 0; k < D; ++k) lam[k] = fmax(lam[k], fabs(q.v[k]) + cs);
     }
@@ -483,6 +492,7 @@ int dg_mesh_destroy(dg_mesh* m) {
   cudaFree(m->red_out);
   cudaFree(m->speed);
   cudaFree(m->err);
+  cudaFree(m->fbar);
   delete m;
   return DG_OK;
 }
@@ -517,6 +527,25 @@ int dg_rhs_part(dg_mesh* m, const double* u, void* du, int parts) {
         m->opt.surface_flux, m->err, m->stream, parts);
   }
   if (e != cudaSuccess) return cuda_fail(e, "dg_rhs: launch");
+  return DG_OK;
+}
+
+int dg_rhs_vjp(dg_mesh* m, const double* u, const double* w, double* ubar) {
+  if (!valid_mesh(m) || !u || !w || !ubar) return fail(DG_ERR_ARG, "dg_rhs_vjp: null argument");
+  if (!m->fbar) {
+    const long long n = 2LL * m->d * m->nv * m->nelem * (m->P / m->np);
+    DG_CUDA(cudaMalloc(&m->fbar, n * sizeof(double)), "dg_rhs_vjp: cudaMalloc");
+  }
+  cudaError_t e;
+  if (m->opt.precision == DG_FP64)
+    e = (m->d == 2 ? dg::vjp_launch_double_2 : dg::vjp_launch_double_3)(
+        m->N, u, w, ubar, m->fbar, m->geom, m->t64, m->opt.volume_flux, m->opt.surface_flux,
+        m->stream);
+  else
+    e = (m->d == 2 ? dg::vjp_launch_float_2 : dg::vjp_launch_float_3)(
+        m->N, u, w, ubar, m->fbar, m->geom, m->t64, m->opt.volume_flux, m->opt.surface_flux,
+        m->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "dg_rhs_vjp: launch");
   return DG_OK;
 }
 

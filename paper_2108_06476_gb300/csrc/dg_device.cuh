@@ -89,36 +89,6 @@ __device__ __forceinline__ float rn_add(float a, float b) { return __fadd_rn(a, 
 __device__ __forceinline__ float rn_sub(float a, float b) { return __fsub_rn(a, b); }
 __device__ __forceinline__ float rn_div(float a, float b) { return __fdiv_rn(a, b); }
 
-template <typename R, int D>
-struct Prim {
-  R rho, v[D], p;
-};
-
-// Primitive variables from conserved ones, rounded as the plain left-to-right
-// IEEE evaluation of v_k = m_k / rho, p = (gamma-1) (E - (rho/2) |v|^2).
-template <typename R, int D>
-__device__ __forceinline__ Prim<R, D> cons2prim(const R* c, R gm1) {
-  Prim<R, D> q;
-  q.rho = c[0];
-  R v2 = R(0);
-#pragma unroll
-  for (int k = 0; k < D; ++k) {
-    q.v[k] = rn_div(c[1 + k], c[0]);
-    v2 = (k == 0) ? rn_mul(q.v[0], q.v[0]) : rn_add(v2, rn_mul(q.v[k], q.v[k]));
-  }
-  q.p = rn_mul(gm1, rn_sub(c[D + 1], rn_mul(rn_mul(R(0.5), c[0]), v2)));
-  return q;
-}
-
-template <typename R, int D>
-__device__ __forceinline__ unsigned prim_check(const Prim<R, D>& q) {
-  unsigned bad = 0;
-  if (!(q.rho > R(0))) bad |= kErrRho;
-  if (!(q.p > R(0))) bad |= kErrP;
-  if (!isfinite(q.rho) || !isfinite(q.p)) bad |= kErrNaN;
-  return bad;
-}
-
 // ---- reciprocals ----
 // FP64: hardware approximation (rcp.approx.ftz.f64) refined by two
 // Newton-Raphson steps r <- r + r (1 - x r), each doubling the correct bits;
@@ -136,6 +106,40 @@ __device__ __forceinline__ float rcp(float x) {
   float r;
   asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
   return r;
+}
+
+template <typename R, int D>
+struct Prim {
+  R rho, v[D], p;
+};
+
+// Primitive variables from conserved ones, rounded as the plain left-to-right
+// IEEE evaluation of v_k = m_k / rho, p = (gamma-1) (E - (rho/2) |v|^2).
+// The quotients use one reciprocal and a residual correction
+// q = m r + (m - rho (m r)) r, which gives the correctly rounded m / rho.
+template <typename R, int D>
+__device__ __forceinline__ Prim<R, D> cons2prim(const R* c, R gm1) {
+  Prim<R, D> q;
+  q.rho = c[0];
+  const R rr = rcp(c[0]);
+  R v2 = R(0);
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    const R q0 = c[1 + k] * rr;
+    q.v[k] = fma(fma(-c[0], q0, c[1 + k]), rr, q0);
+    v2 = (k == 0) ? rn_mul(q.v[0], q.v[0]) : rn_add(v2, rn_mul(q.v[k], q.v[k]));
+  }
+  q.p = rn_mul(gm1, rn_sub(c[D + 1], rn_mul(rn_mul(R(0.5), c[0]), v2)));
+  return q;
+}
+
+template <typename R, int D>
+__device__ __forceinline__ unsigned prim_check(const Prim<R, D>& q) {
+  unsigned bad = 0;
+  if (!(q.rho > R(0))) bad |= kErrRho;
+  if (!(q.p > R(0))) bad |= kErrP;
+  if (!isfinite(q.rho) || !isfinite(q.p)) bad |= kErrNaN;
+  return bad;
 }
 
 // ---- logarithmic mean ----

@@ -375,7 +375,7 @@ __device__ __forceinline__ void surface_nf(int sf, const Trace<R, D>& L, const T
   dq[0] = Rt.rho - L.rho;
   dq[1] = Rt.mn - L.mn;
   dq[D + 1] = dE;
-  const R cl = sqrt(gamma * L.p / L.rho), cr = sqrt(gamma * Rt.p / Rt.rho);
+  const R cl = sqrt(gamma * L.p * rcp(L.rho)), cr = sqrt(gamma * Rt.p * rcp(Rt.rho));
   if (sf == kSLLF) {
     const R lam = fmax(fabs(L.vn), fabs(Rt.vn)) + fmax(cl, cr);
 #pragma unroll

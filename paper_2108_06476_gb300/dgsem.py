@@ -28,7 +28,7 @@ RK_B = (1432997174477.0 / 9575080441755.0, 5161836677717.0 / 13612068292357.0,
         2277821191437.0 / 14882151754819.0)
 
 EXPORTS = ("dg_mesh_create", "dg_mesh_destroy", "dg_mesh_info", "dg_mesh_set_stream",
-           "dg_lgl_nodes", "dg_rhs", "dg_rhs_part", "dg_rk_stage", "dg_rk_reset", "dg_step", "dg_max_dt",
+           "dg_lgl_nodes", "dg_rhs", "dg_rhs_part", "dg_rhs_vjp", "dg_rk_stage", "dg_rk_reset", "dg_step", "dg_max_dt",
            "dg_integrals", "dg_mesh_check", "dg_last_error")
 
 
@@ -62,6 +62,7 @@ def load(path: str = SO_PATH):
     L.dg_lgl_nodes.argtypes = [ctypes.c_int, dp, dp]
     L.dg_rhs.argtypes = [vp, vp, vp]
     L.dg_rhs_part.argtypes = [vp, vp, vp, ctypes.c_int]
+    L.dg_rhs_vjp.argtypes = [vp, vp, vp, vp]
     L.dg_rk_stage.argtypes = [vp, vp, vp, ctypes.c_double, ctypes.c_double, ctypes.c_double]
     L.dg_rk_reset.argtypes = [vp]
     L.dg_step.argtypes = [vp, vp, vp, ctypes.c_double]
@@ -182,6 +183,17 @@ class Mesh:
         self._sync_stream()
         _check(load().dg_rhs(self._h, _ptr(u), _ptr(du)), "dg_rhs")
         return du
+
+    def rhs_vjp(self, u, w, ubar=None):
+        """ubar = (d rhs / d u)^T w (float64 CUDA tensors of n_values)."""
+        self._check_state(u)
+        self._check_state(w)
+        if ubar is None:
+            ubar = self._torch.empty_like(u)
+        self._check_state(ubar)
+        self._sync_stream()
+        _check(load().dg_rhs_vjp(self._h, _ptr(u), _ptr(w), _ptr(ubar)), "dg_rhs_vjp")
+        return ubar
 
     def rhs_part(self, u, du, parts):
         """Launch only the surface kernel (parts=1), only the volume kernel

@@ -1,0 +1,114 @@
+"""GPU vector-Jacobian product of the rhs (dg_rhs_vjp) against the oracle's
+exact Jacobian-vector products (complex-step differentiation): full
+transposed Jacobians on tiny meshes, the adjoint dot test <w, J v> =
+<J^T w, v> at the N=4, 16^3 size, central finite differences of the GPU rhs,
+and the autograd wrapper."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from paper_2108_06476_gb300 import Mesh, workloads as W  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+VF = {0: "ranocha", 1: "chandrashekar", 2: "central"}
+SF = {0: "llf", 1: "ranocha", 2: "hll", 3: "chandrashekar"}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2108_06476_gb300 import build
+    build.build()
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def gpu_vjp(d, N, n, dom, u, w, vf=0, sf=0, precision="fp64"):
+    m = Mesh(d, N, n, tuple(dom), volume_flux=VF[vf], surface_flux=SF[sf], precision=precision)
+    ub = m.rhs_vjp(torch.from_numpy(u).cuda(), torch.from_numpy(w).cuda())
+    torch.cuda.synchronize()
+    return ub.cpu().numpy()
+
+
+@pytest.mark.parametrize("d,N,n", [(2, 2, (2, 3)), (3, 1, (2, 2, 1)), (2, 3, (1, 2))])
+@pytest.mark.parametrize("vf,sf", [(0, 0), (0, 1), (1, 2), (2, 0), (0, 3)])
+def test_vjp_equals_transposed_oracle_jacobian(orc, d, N, n, vf, sf):
+    dom = W.box(d)
+    u = W.random_state(d, N, n, seed=50 + vf)
+    w = W.gaussian(u.size, seed=51 + sf)
+    # the full Jacobian column by column from the oracle's exact JVP
+    J = np.empty((u.size, u.size))
+    for j in range(u.size):
+        e = np.zeros(u.size)
+        e[j] = 1.0
+        J[:, j] = orc.rhs_jvp(d, N, n, dom, u, e, vflux=vf, sflux=sf)
+    ref = J.T @ w
+    got = gpu_vjp(d, N, n, dom, u, w, vf, sf)
+    err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+    assert err <= 1e-12, err
+
+
+def test_vjp_adjoint_dot_16cubed_n4(orc):
+    # VJP configuration: 3D N=4, 16^3 periodic elements, density wave plus 1e-2
+    # noise, cotangent with i.i.d. N(0,1) entries
+    d, N, n = 3, 4, (16, 16, 16)
+    dom = W.box(d)
+    xi, _ = orc.lgl(N)
+    u = W.noisy_density_wave(d, N, n, dom, xi, seed=0)
+    w = W.gaussian(u.size, seed=1)
+    ub = gpu_vjp(d, N, n, dom, u, w)
+    for s in range(3):
+        v = W.gaussian(u.size, seed=100 + s)
+        jv = orc.rhs_jvp(d, N, n, dom, u, v)
+        lhs, rhs = float(w @ jv), float(ub @ v)
+        scale = float(np.abs(w * jv).sum())
+        assert abs(lhs - rhs) <= 1e-12 * scale, (lhs, rhs, scale)
+
+
+def test_vjp_central_differences():
+    d, N, n = 3, 4, (6, 5, 4)
+    dom = W.box(d)
+    from paper_2108_06476_gb300 import lgl_nodes
+    xi, _ = lgl_nodes(N)
+    u = W.noisy_density_wave(d, N, n, dom, xi, seed=2)
+    w = W.gaussian(u.size, seed=3)
+    m = Mesh(d, N, n)
+    ut, wt = torch.from_numpy(u).cuda(), torch.from_numpy(w).cuda()
+    ub = m.rhs_vjp(ut, wt).cpu().numpy()
+    eps = 1e-6
+    for s in range(4):
+        v = W.gaussian(u.size, seed=10 + s)
+        vt = torch.from_numpy(v).cuda()
+        fd = (m.rhs(ut + eps * vt) - m.rhs(ut - eps * vt)).cpu().numpy() / (2 * eps)
+        a, b = float(w @ fd), float(ub @ v)
+        assert abs(a - b) <= 1e-6 * abs(b), (a, b)
+
+
+def test_autograd_function_uses_the_vjp():
+    from paper_2108_06476_gb300.autograd import rhs as rhs_fn
+    d, N, n = 2, 3, (4, 3)
+    u = W.random_state(d, N, n, seed=5)
+    w = W.gaussian(u.size, seed=6)
+    m = Mesh(d, N, n)
+    ut = torch.from_numpy(u).cuda().requires_grad_(True)
+    wt = torch.from_numpy(w).cuda()
+    du = rhs_fn(m, ut)
+    (du * wt).sum().backward()
+    ref = m.rhs_vjp(ut.detach(), wt)
+    assert torch.allclose(ut.grad, ref, rtol=0, atol=0)
+    assert torch.equal(du.detach(), m.rhs(ut.detach()))
+
+
+def test_vjp_fp32_against_fp64():
+    d, N, n = 3, 4, (16, 16, 16)
+    dom = W.box(d)
+    from paper_2108_06476_gb300 import lgl_nodes
+    xi, _ = lgl_nodes(N)
+    u = W.noisy_density_wave(d, N, n, dom, xi, seed=0)
+    w = W.gaussian(u.size, seed=1)
+    a = gpu_vjp(d, N, n, dom, u, w)
+    b = gpu_vjp(d, N, n, dom, u, w, precision="fp32")
+    err = np.linalg.norm(a - b) / np.linalg.norm(a)
+    print(f"VJP 16^3 N=4 FP32 vs FP64 rel L2 = {err:.3e}")
+    assert err <= 1e-4
