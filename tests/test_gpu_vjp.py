@@ -76,13 +76,21 @@ def test_vjp_central_differences():
     m = Mesh(d, N, n)
     ut, wt = torch.from_numpy(u).cuda(), torch.from_numpy(w).cuda()
     ub = m.rhs_vjp(ut, wt).cpu().numpy()
-    eps = 1e-6
+    # central differences with step 1e-6 differ from the exact product by
+    # their O(eps^2) truncation error (large near the smallest densities of the
+    # noisy state): the gap must be small and shrink ~4x when eps halves
     for s in range(4):
         v = W.gaussian(u.size, seed=10 + s)
         vt = torch.from_numpy(v).cuda()
-        fd = (m.rhs(ut + eps * vt) - m.rhs(ut - eps * vt)).cpu().numpy() / (2 * eps)
-        a, b = float(w @ fd), float(ub @ v)
-        assert abs(a - b) <= 1e-6 * abs(b), (a, b)
+        b = float(ub @ v)
+
+        def fd(eps):
+            d = (m.rhs(ut + eps * vt) - m.rhs(ut - eps * vt)).cpu().numpy() / (2 * eps)
+            return float(w @ d)
+
+        e1, e2 = abs(fd(1e-6) - b), abs(fd(2e-6) - b)
+        assert e1 <= 1e-5 * abs(b), (e1, b)
+        assert e1 <= 1e-9 * abs(b) or 2.5 < e2 / e1 < 5.5, (e1, e2)
 
 
 def test_autograd_function_uses_the_vjp():
@@ -111,4 +119,4 @@ def test_vjp_fp32_against_fp64():
     b = gpu_vjp(d, N, n, dom, u, w, precision="fp32")
     err = np.linalg.norm(a - b) / np.linalg.norm(a)
     print(f"VJP 16^3 N=4 FP32 vs FP64 rel L2 = {err:.3e}")
-    assert err <= 1e-4
+    assert err <= 1e-5
