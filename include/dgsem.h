@@ -168,6 +168,50 @@ int dg_mesh_check(dg_mesh *mesh, int *flags);
 int dg_rhs_noalloc(int d, int N, const int *elements_per_dim, const double *domain,
                    const dg_options *opt, const double *u, double *du, void *cuda_stream);
 
+/* ---- Batched ensemble of independent 3D periodic simulations ----
+ * n_sims meshes of N[s] in {3,4,5} and elements_per_dim[s]^3 elements on
+ * [-1,1]^3 (Sec. 3.1 setup: periodic box, Carpenter-Kennedy LSRK, CFL step),
+ * advanced together. The state of all members is one float64 device array:
+ * member s occupies values [offsets[s], offsets[s+1]) in the layout of u above.
+ * Every Runge-Kutta stage is ONE kernel launch over a work list of
+ * (member, element batch) items that evaluates surface fluxes, the flux-
+ * differencing volume term, lifting and the stage update per element; a
+ * stage reads one state buffer and writes the other. Options: Ranocha volume
+ * flux only; any surface flux; DG_FP64 or DG_FP32 arithmetic (FP64 state). */
+typedef struct dg_ensemble dg_ensemble;
+
+int dg_ensemble_create(int n_sims, const int *N, const int *elements_per_dim,
+                       const dg_options *opt, void *cuda_stream, dg_ensemble **out);
+int dg_ensemble_destroy(dg_ensemble *ens);
+/* total values and nodes; offsets[n_sims+1] (may be NULL) */
+int dg_ensemble_info(const dg_ensemble *ens, long long *n_values, long long *n_nodes,
+                     long long *offsets);
+/* per-member time steps: host arrays of n_sims (set / read back, synchronous) */
+int dg_ensemble_set_dt(dg_ensemble *ens, const double *dt_host);
+int dg_ensemble_get_dt(dg_ensemble *ens, double *dt_host);
+/* per-member CFL time steps computed on the device from u (asynchronous;
+ * the values stay on the device for the next stages) */
+int dg_ensemble_compute_dt(dg_ensemble *ens, const double *u, double cfl);
+/* one stage s in [0,5): u_out = u_in + B_s k, k = A_s k + dt du(u_in);
+ * u_in != u_out. Asynchronous. */
+int dg_ensemble_stage(dg_ensemble *ens, const double *u_in, double *u_out, int stage);
+/* one full step in place on u using u_tmp as the second buffer; when
+ * cfl > 0 the time steps are first recomputed from u on the device. */
+int dg_ensemble_step(dg_ensemble *ens, double *u, double *u_tmp, double cfl);
+/* the same step recorded once as a CUDA graph (for these buffers and cfl)
+ * and replayed on every later call. */
+int dg_ensemble_step_graph(dg_ensemble *ens, double *u, double *u_tmp, double cfl);
+int dg_ensemble_rk_reset(dg_ensemble *ens);
+/* synchronise; DG_ERR_NONPHYSICAL if a non-physical state was met */
+int dg_ensemble_check(dg_ensemble *ens, int *flags);
+/* CTA shape: threads per CTA (multiple of 32) and persistent CTAs per SM;
+ * elements per work item follow as threads / (N+1)^2 for each degree. */
+int dg_ensemble_set_block(dg_ensemble *ens, int threads, int blocks_per_sm);
+/* autotuner: times one stage for each candidate shape on (u, u_tmp), keeps
+ * the fastest and reports it (outputs may be NULL); k is preserved. */
+int dg_ensemble_tune(dg_ensemble *ens, const double *u, double *u_tmp, int *best_threads,
+                     int *best_blocks_per_sm, float *best_ms);
+
 /* Thread-local description of the last failed call ("" if none). */
 const char *dg_last_error(void);
 

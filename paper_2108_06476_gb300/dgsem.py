@@ -29,7 +29,12 @@ RK_B = (1432997174477.0 / 9575080441755.0, 5161836677717.0 / 13612068292357.0,
 
 EXPORTS = ("dg_mesh_create", "dg_mesh_destroy", "dg_mesh_info", "dg_mesh_set_stream",
            "dg_lgl_nodes", "dg_rhs", "dg_rhs_part", "dg_rhs_vjp", "dg_rk_stage", "dg_rk_reset", "dg_step", "dg_max_dt",
-           "dg_integrals", "dg_mesh_check", "dg_last_error")
+           "dg_integrals", "dg_mesh_check", "dg_last_error", "dg_rhs_noalloc",
+           "dg_ensemble_create", "dg_ensemble_destroy", "dg_ensemble_info",
+           "dg_ensemble_set_dt", "dg_ensemble_get_dt", "dg_ensemble_compute_dt",
+           "dg_ensemble_stage", "dg_ensemble_step", "dg_ensemble_step_graph",
+           "dg_ensemble_rk_reset", "dg_ensemble_check", "dg_ensemble_set_block",
+           "dg_ensemble_tune")
 
 
 class DGError(RuntimeError):
@@ -69,6 +74,21 @@ def load(path: str = SO_PATH):
     L.dg_max_dt.argtypes = [vp, vp, ctypes.c_double, dp]
     L.dg_integrals.argtypes = [vp, vp, dp]
     L.dg_mesh_check.argtypes = [vp, ip]
+    L.dg_rhs_noalloc.argtypes = [ctypes.c_int, ctypes.c_int, ip, dp, vp, vp, vp, vp]
+    L.dg_ensemble_create.argtypes = [ctypes.c_int, ip, ip, ctypes.POINTER(_Options), vp,
+                                     ctypes.POINTER(vp)]
+    L.dg_ensemble_destroy.argtypes = [vp]
+    L.dg_ensemble_info.argtypes = [vp, llp, llp, llp]
+    L.dg_ensemble_set_dt.argtypes = [vp, dp]
+    L.dg_ensemble_get_dt.argtypes = [vp, dp]
+    L.dg_ensemble_compute_dt.argtypes = [vp, vp, ctypes.c_double]
+    L.dg_ensemble_stage.argtypes = [vp, vp, vp, ctypes.c_int]
+    L.dg_ensemble_step.argtypes = [vp, vp, vp, ctypes.c_double]
+    L.dg_ensemble_step_graph.argtypes = [vp, vp, vp, ctypes.c_double]
+    L.dg_ensemble_rk_reset.argtypes = [vp]
+    L.dg_ensemble_check.argtypes = [vp, ip]
+    L.dg_ensemble_set_block.argtypes = [vp, ctypes.c_int, ctypes.c_int]
+    L.dg_ensemble_tune.argtypes = [vp, vp, vp, ip, ip, ctypes.POINTER(ctypes.c_float)]
     L.dg_last_error.restype = ctypes.c_char_p
     L.dg_last_error.argtypes = []
     for name in EXPORTS:
@@ -243,3 +263,97 @@ class Mesh:
         if rc != 0:
             _check(rc, "dg_mesh_check")
         return flags.value
+
+
+class Ensemble:
+    """A batch of independent 3D periodic Euler meshes on [-1, 1]^3 with
+    degrees N[s] in {3, 4, 5} and n[s]^3 elements, advanced together (one
+    kernel launch per Runge-Kutta stage). The state of all members is one
+    float64 CUDA tensor; member s is the slice offsets[s]:offsets[s+1]."""
+
+    def __init__(self, N, n, gamma=1.4, surface_flux="llf", precision="fp64", stream=None):
+        import torch
+        self._torch = torch
+        L = load()
+        self.N = [int(x) for x in N]
+        self.n = [int(x) for x in n]
+        self.n_sims = len(self.N)
+        opt = _Options(gamma, VFLUX["ranocha"], SFLUX[surface_flux], PRECISION[precision])
+        Na = (ctypes.c_int * self.n_sims)(*self.N)
+        na = (ctypes.c_int * self.n_sims)(*self.n)
+        st = stream if stream is not None else torch.cuda.current_stream()
+        h = ctypes.c_void_p()
+        _check(L.dg_ensemble_create(self.n_sims, Na, na, ctypes.byref(opt),
+                                    ctypes.c_void_p(st.cuda_stream), ctypes.byref(h)),
+               "dg_ensemble_create")
+        self._h = h
+        nv, nn = ctypes.c_longlong(), ctypes.c_longlong()
+        offs = (ctypes.c_longlong * (self.n_sims + 1))()
+        _check(L.dg_ensemble_info(h, ctypes.byref(nv), ctypes.byref(nn), offs),
+               "dg_ensemble_info")
+        self.n_values, self.n_nodes = nv.value, nn.value
+        self.offsets = [offs[i] for i in range(self.n_sims + 1)]
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load().dg_ensemble_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _chk(self, u):
+        t = self._torch
+        if not (u.is_cuda and u.dtype == t.float64 and u.is_contiguous()
+                and u.numel() == self.n_values):
+            raise DGError("ensemble state must be a contiguous float64 CUDA tensor")
+
+    def set_dt(self, dt):
+        a = np.ascontiguousarray(dt, dtype=np.float64)
+        _check(load().dg_ensemble_set_dt(self._h, a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))),
+               "dg_ensemble_set_dt")
+
+    def get_dt(self):
+        a = np.zeros(self.n_sims)
+        _check(load().dg_ensemble_get_dt(self._h, a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))),
+               "dg_ensemble_get_dt")
+        return a
+
+    def compute_dt(self, u, cfl=0.5):
+        self._chk(u)
+        _check(load().dg_ensemble_compute_dt(self._h, _ptr(u), float(cfl)), "dg_ensemble_compute_dt")
+
+    def stage(self, u_in, u_out, s):
+        self._chk(u_in)
+        self._chk(u_out)
+        _check(load().dg_ensemble_stage(self._h, _ptr(u_in), _ptr(u_out), int(s)), "dg_ensemble_stage")
+
+    def step(self, u, u_tmp, cfl=0.0, graph=False):
+        self._chk(u)
+        self._chk(u_tmp)
+        fn = load().dg_ensemble_step_graph if graph else load().dg_ensemble_step
+        _check(fn(self._h, _ptr(u), _ptr(u_tmp), float(cfl)), "dg_ensemble_step")
+
+    def rk_reset(self):
+        _check(load().dg_ensemble_rk_reset(self._h), "dg_ensemble_rk_reset")
+
+    def check(self):
+        f = ctypes.c_int()
+        _check(load().dg_ensemble_check(self._h, ctypes.byref(f)), "dg_ensemble_check")
+        return f.value
+
+    def set_block(self, threads, blocks_per_sm):
+        _check(load().dg_ensemble_set_block(self._h, int(threads), int(blocks_per_sm)),
+               "dg_ensemble_set_block")
+
+    def tune(self, u, u_tmp):
+        """Autotune the CTA shape; returns (threads, ctas_per_sm, ms_per_stage)."""
+        self._chk(u)
+        self._chk(u_tmp)
+        t, b, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_float()
+        _check(load().dg_ensemble_tune(self._h, _ptr(u), _ptr(u_tmp), ctypes.byref(t),
+                                       ctypes.byref(b), ctypes.byref(ms)), "dg_ensemble_tune")
+        return t.value, b.value, ms.value

@@ -127,6 +127,18 @@ def ensemble(n_sims=48, seed=0, n_range=(8, 24), degrees=(3, 4, 5), pressure=20.
     return out
 
 
+def ensemble_state(members, nodes_of_degree):
+    """Concatenated initial states of ensemble members (density waves with
+    each member's amplitude, velocity and pressure on [-1, 1]^3);
+    nodes_of_degree(N) gives the 1D node positions."""
+    parts = []
+    for m in members:
+        parts.append(density_wave(3, m.N, m.n, box(3), nodes_of_degree(m.N),
+                                  amplitude=m.amplitude, velocity=m.velocity,
+                                  pressure=m.pressure))
+    return np.ascontiguousarray(np.concatenate(parts))
+
+
 def box(d, lo=-1.0, hi=1.0):
     """Domain [lo, hi]^d as [lo0, hi0, lo1, hi1, ...]."""
     return np.array([lo, hi] * d, dtype=np.float64)
