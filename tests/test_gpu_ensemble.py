@@ -51,23 +51,30 @@ def test_ensemble_step_matches_oracle(orc):
     for s, m in enumerate(mem):
         assert dts[s] == pytest.approx(orc.max_dt(3, m.N, m.n, W.box(3), parts0[s], cfl=0.5),
                                        rel=1e-14)
-    # one stage: u1 = u0 + B_0 dt rhs(u0)
-    from paper_2108_06476_gb300 import RK_A, RK_B
+    # one stage u1 = u0 + B_0 dt rhs(u0) with a large dt, so that the increment
+    # dominates u and (u1 - u0) / (B_0 dt) recovers the rhs without the
+    # rounding of u0 + increment
+    from paper_2108_06476_gb300 import RK_B
+    big = 1.0e6
+    E.set_dt(np.full(len(mem), big))
     E.stage(ut, tmp, 0)
     got = split(E, tmp.cpu().numpy())
     for s, m in enumerate(mem):
         du = orc.rhs(3, m.N, m.n, W.box(3), parts0[s])
-        ref = parts0[s] + RK_B[0] * dts[s] * du
-        assert rel(got[s] - parts0[s], ref - parts0[s]) <= 1e-12
-    # a full step from u0 (k reset) against the oracle's five stages
+        assert rel((got[s] - parts0[s]) / (RK_B[0] * big), du) <= 1e-12
+    # a full step from u0 (k reset, CFL time steps) against the oracle's five
+    # stages; the state is rounded to ulp(u) once per stage on both sides
+    E.set_dt(dts)
     E.rk_reset()
     ut.copy_(torch.from_numpy(u0))
-    E.step(ut, tmp, cfl=0.0)  # uses the dt computed above
+    E.step(ut, tmp, cfl=0.0)
     assert E.check() == 0
     got = split(E, ut.cpu().numpy())
     for s, m in enumerate(mem):
         ref = orc.lsrk_step(3, m.N, m.n, W.box(3), parts0[s], dts[s])
-        assert rel(got[s] - parts0[s], ref - parts0[s]) <= 1e-11
+        inc = np.linalg.norm(ref - parts0[s])
+        bound = 1e-11 + 1e-15 * np.linalg.norm(ref) / inc
+        assert rel(got[s] - parts0[s], ref - parts0[s]) <= bound
 
 
 def test_graph_step_and_tuner_are_bitwise_consistent(orc):
@@ -95,27 +102,43 @@ def test_graph_step_and_tuner_are_bitwise_consistent(orc):
     assert torch.equal(a, c)
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32"])
-def test_48_member_configuration(orc, precision):
+# FP32 bars: the FP32 target (1e-5) is stated for density waves with 1e-2
+# noise; on the noise-free waves of the ensemble configuration the energy
+# equation is ~10^4-conditioned ((2/h)|Dt||f_E| against |du_E|), which puts
+# FP32's ~6e-8 rounding at a few 1e-4 (the single-mesh FP32 path measures
+# 3.7e-4 on the 32^3 wave).
+@pytest.mark.parametrize("precision,noisy,tol", [("fp64", False, 1e-12), ("fp32", False, 1e-3),
+                                                 ("fp64", True, 1e-12), ("fp32", True, 1e-5)])
+def test_48_member_configuration(orc, precision, noisy, tol):
     mem = W.ensemble(n_sims=48, seed=0)
-    u0 = W.ensemble_state(mem, lambda N: orc.lgl(N)[0])
+    if noisy:
+        u0 = np.concatenate([W.noisy_density_wave(3, m.N, m.n, W.box(3), orc.lgl(m.N)[0],
+                                                  seed=s, amplitude=m.amplitude,
+                                                  velocity=m.velocity)
+                             for s, m in enumerate(mem)])
+    else:
+        u0 = W.ensemble_state(mem, lambda N: orc.lgl(N)[0])
     E = Ensemble([m.N for m in mem], [m.n[0] for m in mem], precision=precision)
     ut = torch.from_numpy(u0.copy()).cuda()
     tmp = torch.empty_like(ut)
-    E.compute_dt(ut, cfl=0.5)
-    dts = E.get_dt()
+    big = 1.0e6
+    E.set_dt(np.full(len(mem), big))
     E.stage(ut, tmp, 0)
     torch.cuda.synchronize()
     got = split(E, tmp.cpu().numpy())
     parts0 = split(E, u0)
     from paper_2108_06476_gb300 import RK_B
-    # the two smallest members against the oracle
-    order = np.argsort([m.n[0] ** 3 * (m.N + 1) ** 3 for m in mem])[:2]
-    tol = 1e-12 if precision == "fp64" else 1e-5
-    for s in order:
+    # the two smallest members and the largest one against the oracle (on a
+    # sample of its elements)
+    sizes = [m.n[0] ** 3 * (m.N + 1) ** 3 for m in mem]
+    for s in list(np.argsort(sizes)[:2]) + [int(np.argmax(sizes))]:
         m = mem[s]
-        du = orc.rhs(3, m.N, m.n, W.box(3), parts0[s])
-        ref = RK_B[0] * dts[s] * du
-        err = rel(got[s] - parts0[s], ref)
-        print(f"ensemble member {s} (N={m.N}, n={m.n[0]}) {precision} stage rel err {err:.3e}")
+        ne = m.n[0] ** 3
+        elems = np.arange(0, ne, max(1, ne // 300))
+        P = (m.N + 1) ** 3
+        du = orc.rhs(3, m.N, m.n, W.box(3), parts0[s], elems=elems).reshape(ne, 5, P)[elems]
+        gd = ((got[s] - parts0[s]) / (RK_B[0] * big)).reshape(ne, 5, P)[elems]
+        err = rel(gd, du)
+        print(f"ensemble member {s} (N={m.N}, n={m.n[0]}) {precision} noisy={noisy} "
+              f"rel err {err:.3e}")
         assert err <= tol
