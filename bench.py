@@ -218,6 +218,33 @@ def run_reference(args, spec, world, rank):
     print(json.dumps(line), flush=True)
 
 
+def run_ensemble(args, timed, rank):
+    """The seeded 48-member ensemble advanced with one launch per stage and a
+    CUDA-graph step, after the autotuner picked the CTA shape; FP64 and FP32."""
+    import torch
+    from paper_2108_06476_gb300 import Ensemble, lgl_nodes, workloads as W
+    mem = W.ensemble(n_sims=48, seed=rank)
+    u0 = torch.from_numpy(W.ensemble_state(mem, lambda N: lgl_nodes(N)[0])).cuda()
+    out = {"workload": f"48 periodic 3D density waves (seed {rank}), N in {{3,4,5}}, "
+                       "n in [8,24]", "members": len(mem)}
+    k = max(1, min(args.steps, 5))
+    for prec in ("fp64", "fp32"):
+        E = Ensemble([m.N for m in mem], [m.n[0] for m in mem], precision=prec)
+        u = u0.clone()
+        tmp = torch.empty_like(u)
+        threads, per_sm, stage_ms = E.tune(u, tmp)
+        for _ in range(args.warmup):
+            E.step(u, tmp, cfl=0.5, graph=True)
+        ms = timed(lambda: [E.step(u, tmp, cfl=0.5, graph=True) for _ in range(k)])
+        E.check()
+        out[prec] = {"value": E.n_nodes * 5 * k / (ms / 1e3), "unit": UNIT,
+                     "ms_per_step": ms / k, "tuned_threads": threads,
+                     "tuned_ctas_per_sm": per_sm, "tuned_stage_ms": stage_ms}
+        out["nodes"] = E.n_nodes
+        del E, u, tmp
+    return out
+
+
 def cpu_baseline(spec, xi, u):
     """The oracle's rhs on a bounded sample of the workload (about 10 s with
     all host cores)."""
@@ -361,6 +388,11 @@ def run_ours(args, spec, world, rank, local):
         e2e = {"value": M * 5 * args.steps * world / (ms_e / 1e3), "unit": UNIT,
                "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}
 
+    # ---- batched ensemble: 48 members (seed 0), N in {3,4,5}, n in [8,24] ----
+    ensemble = None
+    if not args.no_ensemble:
+        ensemble = run_ensemble(args, timed, rank)
+
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
@@ -384,6 +416,7 @@ def run_ours(args, spec, world, rank, local):
                      "flops_per_node": flops_node, "kernel_ms": vol_ms},
         "kernels_ms": {"volume": vol_ms, "surface": surf_ms},
         "fp32": fp32,
+        "ensemble": ensemble,
         "e2e": e2e,
         "clocks": clk.summary(),
     }
@@ -406,6 +439,7 @@ def main():
     ap.add_argument("--no-fp32", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-ensemble", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
