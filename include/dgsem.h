@@ -128,6 +128,19 @@ int dg_rk_reset(dg_mesh *mesh);
  * Asynchronous. */
 int dg_step(dg_mesh *mesh, double *u, void *du, double dt);
 
+/* One full LSRK step with the CFL time step computed on the device
+ * (Sec. 3.1): a wave-speed reduction and the dt formula below run as kernels,
+ * then five stages whose update k <- A k + dt du, u <- u + B k is fused into
+ * the volume kernel (no du buffer, no host synchronisation). Asynchronous. */
+int dg_step_cfl(dg_mesh *mesh, double *u, double cfl);
+
+/* dg_step_cfl recorded once as a CUDA graph for (u, cfl) and replayed on
+ * later calls with the same arguments. Asynchronous. */
+int dg_step_graph(dg_mesh *mesh, double *u, double cfl);
+
+/* The time step used by the last dg_step_cfl / dg_step_graph (synchronises). */
+int dg_last_dt(dg_mesh *mesh, double *dt_out);
+
 /* CFL time step (Sec. 3.1): dt = cfl * 2 / ((N+1) max_e sum_k (2/h_k)
  * max_nodes(|v_k| + c)), c = sqrt(gamma p / rho). Synchronises the stream;
  * returns DG_ERR_NONPHYSICAL if the state is not physical. */

@@ -12,13 +12,17 @@
 
 namespace dg {
 cudaError_t rhs_launch_double_2(int, const double*, double*, double*, const Geom&,
-                                const Tables<double>&, int, int, unsigned*, cudaStream_t, int);
+                                const Tables<double>&, int, int, unsigned*, cudaStream_t, int,
+                                const StageFuse&);
 cudaError_t rhs_launch_double_3(int, const double*, double*, double*, const Geom&,
-                                const Tables<double>&, int, int, unsigned*, cudaStream_t, int);
+                                const Tables<double>&, int, int, unsigned*, cudaStream_t, int,
+                                const StageFuse&);
 cudaError_t rhs_launch_float_2(int, const double*, float*, float*, const Geom&,
-                               const Tables<float>&, int, int, unsigned*, cudaStream_t, int);
+                               const Tables<float>&, int, int, unsigned*, cudaStream_t, int,
+                               const StageFuse&);
 cudaError_t rhs_launch_float_3(int, const double*, float*, float*, const Geom&,
-                               const Tables<float>&, int, int, unsigned*, cudaStream_t, int);
+                               const Tables<float>&, int, int, unsigned*, cudaStream_t, int,
+                               const StageFuse&);
 cudaError_t vjp_launch_double_2(int, const double*, const double*, double*, double*, const Geom&,
                                 const Tables<double>&, int, int, cudaStream_t);
 cudaError_t vjp_launch_double_3(int, const double*, const double*, double*, double*, const Geom&,
@@ -52,6 +56,11 @@ struct dg_mesh {
   unsigned long long* speed;  // max wave-speed sum (as ordered bits)
   unsigned* err;       // device error word
   double* fbar;        // face adjoint buffer of dg_rhs_vjp, allocated on first use
+  float* pref;         // FP32 meshes: per-element pressure references
+  double* dt_dev;      // time step computed on the device (dg_step_cfl)
+  cudaGraphExec_t graph;
+  const double* graph_u;
+  double graph_cfl;
 };
 
 namespace {
@@ -221,6 +230,20 @@ __global__ void speed_kernel(const double* __restrict__ u, Geom g, int P, double
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmax(m, sb[w]);
     atomicMax(out, (unsigned long long)__double_as_longlong(m));
   }
+}
+
+// dt = cfl 2 / ((N+1) worst) on the device from the wave-speed word, which is
+// cleared for the next reduction
+__global__ void dt_kernel(unsigned long long* speed, int N, double cfl, double* dt,
+                          unsigned* err) {
+  const double worst = __longlong_as_double((long long)*speed);
+  *speed = 0ull;
+  if (!(worst > 0.0)) {
+    atomicOr(err, 4u);
+    *dt = 0.0;
+    return;
+  }
+  *dt = cfl * 2.0 / ((N + 1) * worst);
 }
 
 // double-double accumulation (Knuth two-sum)
@@ -457,7 +480,9 @@ int dg_mesh_create(int d, int N, const int* epd, const double* domain, const dg_
       (e = cudaMalloc(&m->partials, kRedBlocks * 7 * 2 * sizeof(double))) != cudaSuccess ||
       (e = cudaMalloc(&m->red_out, 7 * 2 * sizeof(double))) != cudaSuccess ||
       (e = cudaMalloc(&m->speed, sizeof(unsigned long long))) != cudaSuccess ||
-      (e = cudaMalloc(&m->err, sizeof(unsigned))) != cudaSuccess) {
+      (e = cudaMalloc(&m->err, sizeof(unsigned))) != cudaSuccess ||
+      (e = cudaMalloc(&m->pref, m->nelem * sizeof(float))) != cudaSuccess ||
+      (e = cudaMalloc(&m->dt_dev, sizeof(double))) != cudaSuccess) {
     int rc = cuda_fail(e, "dg_mesh_create: cudaMalloc");
     cudaFree(m->k);
     cudaFree(m->fs);
@@ -466,6 +491,8 @@ int dg_mesh_create(int d, int N, const int* epd, const double* domain, const dg_
     cudaFree(m->red_out);
     cudaFree(m->speed);
     cudaFree(m->err);
+    cudaFree(m->pref);
+    cudaFree(m->dt_dev);
     delete m;
     return rc;
   }
@@ -473,6 +500,8 @@ int dg_mesh_create(int d, int N, const int* epd, const double* domain, const dg_
                            m->stream)) != cudaSuccess ||
       (e = cudaMemsetAsync(m->k, 0, m->nvalues * sizeof(double), m->stream)) != cudaSuccess ||
       (e = cudaMemsetAsync(m->err, 0, sizeof(unsigned), m->stream)) != cudaSuccess ||
+      (e = cudaMemsetAsync(m->speed, 0, sizeof(unsigned long long), m->stream)) != cudaSuccess ||
+      (e = cudaMemsetAsync(m->dt_dev, 0, sizeof(double), m->stream)) != cudaSuccess ||
       (e = cudaStreamSynchronize(m->stream)) != cudaSuccess) {
     int rc = cuda_fail(e, "dg_mesh_create: initialisation");
     dg_mesh_destroy(m);
@@ -493,6 +522,9 @@ int dg_mesh_destroy(dg_mesh* m) {
   cudaFree(m->speed);
   cudaFree(m->err);
   cudaFree(m->fbar);
+  cudaFree(m->pref);
+  cudaFree(m->dt_dev);
+  if (m->graph) cudaGraphExecDestroy(m->graph);
   delete m;
   return DG_OK;
 }
@@ -520,11 +552,11 @@ int dg_rhs_part(dg_mesh* m, const double* u, void* du, int parts) {
   if (m->opt.precision == DG_FP64) {
     e = (m->d == 2 ? dg::rhs_launch_double_2 : dg::rhs_launch_double_3)(
         m->N, u, (double*)du, (double*)m->fs, m->geom, m->t64, m->opt.volume_flux,
-        m->opt.surface_flux, m->err, m->stream, parts);
+        m->opt.surface_flux, m->err, m->stream, parts, dg::StageFuse());
   } else {
     e = (m->d == 2 ? dg::rhs_launch_float_2 : dg::rhs_launch_float_3)(
         m->N, u, (float*)du, (float*)m->fs, m->geom, m->t32, m->opt.volume_flux,
-        m->opt.surface_flux, m->err, m->stream, parts);
+        m->opt.surface_flux, m->err, m->stream, parts, dg::StageFuse());
   }
   if (e != cudaSuccess) return cuda_fail(e, "dg_rhs: launch");
   return DG_OK;
@@ -576,6 +608,95 @@ int dg_step(dg_mesh* m, double* u, void* du, double dt) {
     rc = dg_rk_stage(m, u, du, kRkA[s], kRkB[s], dt);
     if (rc != DG_OK) return rc;
   }
+  return DG_OK;
+}
+
+namespace {
+int launch_speed(dg_mesh* m, const double* u) {
+  const int threads = 256;
+  const int grid = grid_for(m->nelem * 32, threads);
+  const double s0 = 2.0 / m->h[0], s1 = 2.0 / m->h[1], s2 = 2.0 / m->h[2];
+  if (m->d == 2)
+    speed_kernel<2><<<grid, threads, 0, m->stream>>>(u, m->geom, (int)m->P, s0, s1, s2, m->speed,
+                                                     m->err);
+  else
+    speed_kernel<3><<<grid, threads, 0, m->stream>>>(u, m->geom, (int)m->P, s0, s1, s2, m->speed,
+                                                     m->err);
+  DG_CUDA(cudaGetLastError(), "speed kernel launch");
+  return DG_OK;
+}
+
+// dt on the device, then five stages with the update fused into the volume
+// kernel (no du buffer, no host synchronisation)
+int enqueue_fused_step(dg_mesh* m, double* u, double cfl) {
+  int rc = launch_speed(m, u);
+  if (rc) return rc;
+  dt_kernel<<<1, 1, 0, m->stream>>>(m->speed, m->N, cfl, m->dt_dev, m->err);
+  DG_CUDA(cudaGetLastError(), "dt kernel launch");
+  for (int s = 0; s < 5; ++s) {
+    dg::StageFuse fz;
+    fz.k = m->k;
+    fz.dt = m->dt_dev;
+    fz.a = kRkA[s];
+    fz.b = kRkB[s];
+    cudaError_t e;
+    if (m->opt.precision == DG_FP64) {
+      e = (m->d == 2 ? dg::rhs_launch_double_2 : dg::rhs_launch_double_3)(
+          m->N, u, nullptr, (double*)m->fs, m->geom, m->t64, m->opt.volume_flux,
+          m->opt.surface_flux, m->err, m->stream, 3, fz);
+    } else {
+      fz.pref = m->pref;
+      e = (m->d == 2 ? dg::rhs_launch_float_2 : dg::rhs_launch_float_3)(
+          m->N, u, nullptr, (float*)m->fs, m->geom, m->t32, m->opt.volume_flux,
+          m->opt.surface_flux, m->err, m->stream, 3, fz);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "fused stage launch");
+  }
+  return DG_OK;
+}
+}  // namespace
+
+int dg_step_cfl(dg_mesh* m, double* u, double cfl) {
+  if (!valid_mesh(m) || !u || !(cfl > 0.0)) return fail(DG_ERR_ARG, "dg_step_cfl: bad argument");
+  return enqueue_fused_step(m, u, cfl);
+}
+
+int dg_step_graph(dg_mesh* m, double* u, double cfl) {
+  if (!valid_mesh(m) || !u || !(cfl > 0.0)) return fail(DG_ERR_ARG, "dg_step_graph: bad argument");
+  if (!m->graph || m->graph_u != u || m->graph_cfl != cfl) {
+    if (m->graph) {
+      cudaGraphExecDestroy(m->graph);
+      m->graph = nullptr;
+    }
+    cudaStream_t cap;
+    DG_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking), "dg_step_graph: stream");
+    cudaStream_t saved = m->stream;
+    m->stream = cap;
+    cudaGraph_t g = nullptr;
+    cudaError_t ce = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    int rc = (ce == cudaSuccess) ? enqueue_fused_step(m, u, cfl) : DG_ERR_CUDA;
+    if (ce == cudaSuccess) ce = cudaStreamEndCapture(cap, &g);
+    m->stream = saved;
+    cudaStreamDestroy(cap);
+    if (rc != DG_OK || ce != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      return rc != DG_OK ? rc : cuda_fail(ce, "dg_step_graph: capture");
+    }
+    ce = cudaGraphInstantiate(&m->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (ce != cudaSuccess) return cuda_fail(ce, "dg_step_graph: instantiate");
+    m->graph_u = u;
+    m->graph_cfl = cfl;
+  }
+  DG_CUDA(cudaGraphLaunch(m->graph, m->stream), "dg_step_graph: launch");
+  return DG_OK;
+}
+
+int dg_last_dt(dg_mesh* m, double* dt_out) {
+  if (!valid_mesh(m) || !dt_out) return fail(DG_ERR_ARG, "dg_last_dt: bad argument");
+  DG_CUDA(cudaMemcpyAsync(dt_out, m->dt_dev, sizeof(double), cudaMemcpyDeviceToHost, m->stream),
+          "dg_last_dt: copy");
+  DG_CUDA(cudaStreamSynchronize(m->stream), "dg_last_dt: sync");
   return DG_OK;
 }
 

@@ -40,6 +40,19 @@ struct Tables {
   R liftL[3];
 };
 
+// Optional fusion of the Runge-Kutta stage into the volume kernel's
+// epilogue: with k set, du is not stored; instead k <- a k + dt du and
+// u <- u + b k for the element (the surface kernel of the same stage has
+// already read every trace, and no other CTA reads this element's u).
+// pref (FP32 only): per-element pressure references published by the
+// surface kernel, read by the volume kernel for the left neighbours.
+struct StageFuse {
+  double* k = nullptr;
+  const double* dt = nullptr;
+  double a = 0.0, b = 0.0;
+  float* pref = nullptr;
+};
+
 template <int D, int N>
 struct Shape {
   static constexpr int NP = N + 1;

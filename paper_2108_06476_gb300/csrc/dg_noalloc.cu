@@ -19,9 +19,11 @@
 
 namespace dg {
 cudaError_t rhs_launch_double_2(int, const double*, double*, double*, const Geom&,
-                                const Tables<double>&, int, int, unsigned*, cudaStream_t, int);
+                                const Tables<double>&, int, int, unsigned*, cudaStream_t, int,
+                                const StageFuse&);
 cudaError_t rhs_launch_double_3(int, const double*, double*, double*, const Geom&,
-                                const Tables<double>&, int, int, unsigned*, cudaStream_t, int);
+                                const Tables<double>&, int, int, unsigned*, cudaStream_t, int,
+                                const StageFuse&);
 int set_last_error(int code, const char* msg);
 void build_tables_fp64(int d, int N, const double* h, Tables<double>* t);
 }  // namespace dg
@@ -114,7 +116,7 @@ extern "C" int dg_rhs_noalloc(int d, int N, const int* elements_per_dim, const d
   dg::Tables<double> tb;
   dg::build_tables_fp64(d, N, h, &tb);
   cudaError_t e = (d == 2 ? dg::rhs_launch_double_2 : dg::rhs_launch_double_3)(
-      N, u, du, scratch, g, tb, o.volume_flux, o.surface_flux, err, st, 3);
+      N, u, du, scratch, g, tb, o.volume_flux, o.surface_flux, err, st, 3, dg::StageFuse());
   if (e != cudaSuccess) return fail(DG_ERR_CUDA, "dg_rhs_noalloc: launch failed");
   return DG_OK;
 }

@@ -18,7 +18,7 @@ cudaError_t DG_CAT(rhs_launch, DG_INST_REAL, DG_INST_DIM)(int N, const double* u
                                                           DG_INST_REAL* fs, const Geom& g,
                                                           const Tables<DG_INST_REAL>& tb, int vf,
                                                           int sf, unsigned* err, cudaStream_t st,
-                                                          int parts) {
-  return launch_rhs_d<DG_INST_DIM, DG_INST_REAL>(N, u, du, fs, g, tb, vf, sf, err, st, parts);
+                                                          int parts, const StageFuse& fz) {
+  return launch_rhs_d<DG_INST_DIM, DG_INST_REAL>(N, u, du, fs, g, tb, vf, sf, err, st, parts, fz);
 }
 }  // namespace dg

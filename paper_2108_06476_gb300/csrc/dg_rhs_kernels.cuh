@@ -193,8 +193,8 @@ __device__ __forceinline__ void volume_direction(int dir, R (*sp)[4 + 2 * D][Sha
 
 template <int D, int N, typename R, int VF, int EPB>
 __global__ void __launch_bounds__(EPB* Shape<D, N>::LINES)
-    volume_kernel(const double* __restrict__ u, R* __restrict__ du, const R* __restrict__ fs,
-                  Geom g, Tables<R> tb, unsigned* __restrict__ err) {
+    volume_kernel(double* u, R* __restrict__ du, const R* __restrict__ fs, Geom g, Tables<R> tb,
+                  unsigned* __restrict__ err, StageFuse fz) {
   using S = Shape<D, N>;
   constexpr int NP = S::NP, P = S::P, NV = S::NV, LINES = S::LINES;
   constexpr bool F32 = sizeof(R) == 4;
@@ -224,10 +224,14 @@ __global__ void __launch_bounds__(EPB* Shape<D, N>::LINES)
       s_eref[el] = Er;
 #pragma unroll
       for (int k = 0; k < D; ++k) {
-        float Pl, cl;
-        double El;
-        pressure_ref(u, s_left[el][k], NV, P, g.gm1, Pl, cl, El);
-        s_pref[el][1 + k] = Pl;
+        if (fz.pref) {
+          s_pref[el][1 + k] = fz.pref[s_left[el][k]];
+        } else {
+          float Pl, cl;
+          double El;
+          pressure_ref(u, s_left[el][k], NV, P, g.gm1, Pl, cl, El);
+          s_pref[el][1 + k] = Pl;
+        }
       }
     }
   }
@@ -283,7 +287,9 @@ __global__ void __launch_bounds__(EPB* Shape<D, N>::LINES)
     if (active) volume_direction<D, N, R, VF, EPB>(dir, sp, sa, el, l, tb, gm1inv, Pe);
     __syncthreads();
   }
-  // epilogue: lifting of the surface fluxes, then the store
+  // epilogue: lifting of the surface fluxes, then the store (or the fused
+  // stage update)
+  const double dtv = fz.k ? *fz.dt : 0.0;
   for (int t = threadIdx.x; t < EPB * P; t += blockDim.x) {
     const int ell = t / P, node = t % P;
     const int e = e0 + ell;
@@ -308,7 +314,14 @@ __global__ void __launch_bounds__(EPB* Shape<D, N>::LINES)
           val = fma(tb.liftL[dir], F, val);
         }
       }
-      du[((long long)e * NV + v) * P + node] = val;
+      const long long i = ((long long)e * NV + v) * P + node;
+      if (fz.k) {
+        const double kk = fz.a * fz.k[i] + dtv * (double)val;
+        fz.k[i] = kk;
+        u[i] = u[i] + fz.b * kk;
+      } else {
+        du[i] = val;
+      }
     }
   }
 }
@@ -394,7 +407,7 @@ __device__ __forceinline__ void surface_nf(int sf, const Trace<R, D>& L, const T
 
 template <int D, int N, typename R, int dir>
 __device__ __forceinline__ void surface_body(const double* __restrict__ u, R* __restrict__ fs,
-                                             const Geom& g, int sf) {
+                                             const Geom& g, int sf, float* __restrict__ pref) {
   using S = Shape<D, N>;
   constexpr int NV = S::NV, P = S::P, NF = S::LINES;
   constexpr bool F32 = sizeof(R) == 4;
@@ -421,6 +434,7 @@ __device__ __forceinline__ void surface_body(const double* __restrict__ u, R* __
       double ErL, ErR;
       pressure_ref(u, e, NV, P, g.gm1, PeL, ceL, ErL);
       pressure_ref(u, er, NV, P, g.gm1, PeR, ceR, ErR);
+      if (dir == 0 && l == 0 && pref) pref[e] = PeL;
       prim_f32<D>(cl, (float)g.gm1, PeL, ceL, ErL, rL, vL, ppL, pL);
       prim_f32<D>(cr, (float)g.gm1, PeR, ceR, ErR, rR, vR, ppR, pR);
       L.rho = R(rL);
@@ -480,10 +494,11 @@ __device__ __forceinline__ void surface_body(const double* __restrict__ u, R* __
 }
 
 template <int D, int N, typename R>
-__global__ void surface_kernel(const double* __restrict__ u, R* __restrict__ fs, Geom g, int sf) {
-  if (blockIdx.y == 0) surface_body<D, N, R, 0>(u, fs, g, sf);
-  else if (blockIdx.y == 1) surface_body<D, N, R, 1>(u, fs, g, sf);
-  else surface_body<D, N, R, (D == 3 ? 2 : 1)>(u, fs, g, sf);
+__global__ void surface_kernel(const double* __restrict__ u, R* __restrict__ fs, Geom g, int sf,
+                               float* __restrict__ pref) {
+  if (blockIdx.y == 0) surface_body<D, N, R, 0>(u, fs, g, sf, pref);
+  else if (blockIdx.y == 1) surface_body<D, N, R, 1>(u, fs, g, sf, pref);
+  else surface_body<D, N, R, (D == 3 ? 2 : 1)>(u, fs, g, sf, pref);
 }
 
 // elements per CTA: about 128 threads, dynamic shared memory <= 96 KB
@@ -506,7 +521,8 @@ cudaError_t allow_smem(K kernel, int bytes) {
 // parts: bit 0 = surface kernel, bit 1 = volume kernel (both for an rhs)
 template <int D, int N, typename R>
 cudaError_t launch_rhs_dn(const double* u, R* du, R* fs, const Geom& g, const Tables<R>& tb,
-                          int vf, int sf, unsigned* err, cudaStream_t st, int parts) {
+                          int vf, int sf, unsigned* err, cudaStream_t st, int parts,
+                          const StageFuse& fz) {
   using L = Launch<D, N, R>;
   constexpr int EPB = L::EPB;
   if (parts & 1) {
@@ -514,7 +530,7 @@ cudaError_t launch_rhs_dn(const double* u, R* du, R* fs, const Geom& g, const Ta
     long long blocks = (total + 255) / 256;
     if (blocks > 152 * 16) blocks = 152 * 16;
     if (blocks < 1) blocks = 1;
-    surface_kernel<D, N, R><<<dim3((unsigned)blocks, D), 256, 0, st>>>(u, fs, g, sf);
+    surface_kernel<D, N, R><<<dim3((unsigned)blocks, D), 256, 0, st>>>(u, fs, g, sf, fz.pref);
   }
   if (!(parts & 2)) return cudaGetLastError();
   const long long grid = (g.nelem + EPB - 1) / EPB;
@@ -523,28 +539,32 @@ cudaError_t launch_rhs_dn(const double* u, R* du, R* fs, const Geom& g, const Ta
   cudaError_t e;
   if (vf == kVRanocha) {
     if ((e = allow_smem(volume_kernel<D, N, R, kVRanocha, EPB>, SM)) != cudaSuccess) return e;
-    volume_kernel<D, N, R, kVRanocha, EPB><<<(unsigned)grid, threads, SM, st>>>(u, du, fs, g, tb, err);
+    volume_kernel<D, N, R, kVRanocha, EPB><<<(unsigned)grid, threads, SM, st>>>(
+        const_cast<double*>(u), du, fs, g, tb, err, fz);
   } else if (vf == kVChandrashekar) {
     if ((e = allow_smem(volume_kernel<D, N, R, kVChandrashekar, EPB>, SM)) != cudaSuccess) return e;
-    volume_kernel<D, N, R, kVChandrashekar, EPB><<<(unsigned)grid, threads, SM, st>>>(u, du, fs, g, tb, err);
+    volume_kernel<D, N, R, kVChandrashekar, EPB><<<(unsigned)grid, threads, SM, st>>>(
+        const_cast<double*>(u), du, fs, g, tb, err, fz);
   } else {
     if ((e = allow_smem(volume_kernel<D, N, R, kVCentral, EPB>, SM)) != cudaSuccess) return e;
-    volume_kernel<D, N, R, kVCentral, EPB><<<(unsigned)grid, threads, SM, st>>>(u, du, fs, g, tb, err);
+    volume_kernel<D, N, R, kVCentral, EPB><<<(unsigned)grid, threads, SM, st>>>(
+        const_cast<double*>(u), du, fs, g, tb, err, fz);
   }
   return cudaGetLastError();
 }
 
 template <int D, typename R>
 cudaError_t launch_rhs_d(int N, const double* u, R* du, R* fs, const Geom& g, const Tables<R>& tb,
-                         int vf, int sf, unsigned* err, cudaStream_t st, int parts) {
+                         int vf, int sf, unsigned* err, cudaStream_t st, int parts,
+                         const StageFuse& fz) {
   switch (N) {
-    case 1: return launch_rhs_dn<D, 1, R>(u, du, fs, g, tb, vf, sf, err, st, parts);
-    case 2: return launch_rhs_dn<D, 2, R>(u, du, fs, g, tb, vf, sf, err, st, parts);
-    case 3: return launch_rhs_dn<D, 3, R>(u, du, fs, g, tb, vf, sf, err, st, parts);
-    case 4: return launch_rhs_dn<D, 4, R>(u, du, fs, g, tb, vf, sf, err, st, parts);
-    case 5: return launch_rhs_dn<D, 5, R>(u, du, fs, g, tb, vf, sf, err, st, parts);
-    case 6: return launch_rhs_dn<D, 6, R>(u, du, fs, g, tb, vf, sf, err, st, parts);
-    case 7: return launch_rhs_dn<D, 7, R>(u, du, fs, g, tb, vf, sf, err, st, parts);
+    case 1: return launch_rhs_dn<D, 1, R>(u, du, fs, g, tb, vf, sf, err, st, parts, fz);
+    case 2: return launch_rhs_dn<D, 2, R>(u, du, fs, g, tb, vf, sf, err, st, parts, fz);
+    case 3: return launch_rhs_dn<D, 3, R>(u, du, fs, g, tb, vf, sf, err, st, parts, fz);
+    case 4: return launch_rhs_dn<D, 4, R>(u, du, fs, g, tb, vf, sf, err, st, parts, fz);
+    case 5: return launch_rhs_dn<D, 5, R>(u, du, fs, g, tb, vf, sf, err, st, parts, fz);
+    case 6: return launch_rhs_dn<D, 6, R>(u, du, fs, g, tb, vf, sf, err, st, parts, fz);
+    case 7: return launch_rhs_dn<D, 7, R>(u, du, fs, g, tb, vf, sf, err, st, parts, fz);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -28,7 +28,8 @@ RK_B = (1432997174477.0 / 9575080441755.0, 5161836677717.0 / 13612068292357.0,
         2277821191437.0 / 14882151754819.0)
 
 EXPORTS = ("dg_mesh_create", "dg_mesh_destroy", "dg_mesh_info", "dg_mesh_set_stream",
-           "dg_lgl_nodes", "dg_rhs", "dg_rhs_part", "dg_rhs_vjp", "dg_rk_stage", "dg_rk_reset", "dg_step", "dg_max_dt",
+           "dg_lgl_nodes", "dg_rhs", "dg_rhs_part", "dg_rhs_vjp", "dg_rk_stage", "dg_rk_reset", "dg_step", "dg_step_cfl", "dg_step_graph",
+           "dg_last_dt", "dg_max_dt",
            "dg_integrals", "dg_mesh_check", "dg_last_error", "dg_rhs_noalloc",
            "dg_ensemble_create", "dg_ensemble_destroy", "dg_ensemble_info",
            "dg_ensemble_set_dt", "dg_ensemble_get_dt", "dg_ensemble_compute_dt",
@@ -71,6 +72,9 @@ def load(path: str = SO_PATH):
     L.dg_rk_stage.argtypes = [vp, vp, vp, ctypes.c_double, ctypes.c_double, ctypes.c_double]
     L.dg_rk_reset.argtypes = [vp]
     L.dg_step.argtypes = [vp, vp, vp, ctypes.c_double]
+    L.dg_step_cfl.argtypes = [vp, vp, ctypes.c_double]
+    L.dg_step_graph.argtypes = [vp, vp, ctypes.c_double]
+    L.dg_last_dt.argtypes = [vp, dp]
     L.dg_max_dt.argtypes = [vp, vp, ctypes.c_double, dp]
     L.dg_integrals.argtypes = [vp, vp, dp]
     L.dg_mesh_check.argtypes = [vp, ip]
@@ -238,6 +242,20 @@ class Mesh:
         self._sync_stream()
         _check(load().dg_step(self._h, _ptr(u), _ptr(du), float(dt)), "dg_step")
         return du
+
+    def step_cfl(self, u, cfl=0.5, graph=False):
+        """One LSRK step with the CFL time step computed on the device and the
+        stage updates fused into the volume kernel (optionally as a replayed
+        CUDA graph)."""
+        self._check_state(u)
+        self._sync_stream()
+        fn = load().dg_step_graph if graph else load().dg_step_cfl
+        _check(fn(self._h, _ptr(u), float(cfl)), "dg_step_cfl")
+
+    def last_dt(self):
+        out = ctypes.c_double()
+        _check(load().dg_last_dt(self._h, ctypes.byref(out)), "dg_last_dt")
+        return out.value
 
     def max_dt(self, u, cfl=0.5):
         self._check_state(u)

@@ -250,3 +250,57 @@ def test_rhs_fp32_small(orc, d, N, n, vf, sf):
     ref = oracle_rhs(orc, d, N, n, dom, u, vf, sf)
     got = gpu_rhs(d, N, n, dom, u, vf, sf, precision="fp32")
     assert rel_l2(got, ref) <= TOL32, rel_l2(got, ref)
+
+
+# ---- fused step: device CFL time step, stage update inside the volume kernel ----
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_fused_step_matches_unfused(orc, precision):
+    d, N, n = 3, 3, (6, 5, 4)
+    dom = W.box(d)
+    xi, _ = orc.lgl(N)
+    u0 = W.noisy_density_wave(d, N, n, dom, xi, seed=8)
+    m1 = Mesh(d, N, n, precision=precision)
+    m2 = Mesh(d, N, n, precision=precision)
+    a = torch.from_numpy(u0.copy()).cuda()
+    b = torch.from_numpy(u0.copy()).cuda()
+    du = m1.empty_rhs()
+    for _ in range(3):
+        dt = m1.max_dt(a, cfl=0.5)
+        m1.step(a, dt, du)
+        m2.step_cfl(b, cfl=0.5)
+        assert m2.last_dt() == dt
+    inc_a = (a.cpu().numpy() - u0)
+    inc_b = (b.cpu().numpy() - u0)
+    bound = 1e-13 + 1e-15 * np.linalg.norm(u0) / np.linalg.norm(inc_a)
+    assert rel_l2(inc_b, inc_a) <= bound
+
+
+def test_graph_step_equals_fused_step(orc):
+    d, N, n = 3, 3, (4, 4, 4)
+    xi, _ = orc.lgl(N)
+    u0 = W.noisy_density_wave(d, N, n, W.box(d), xi, seed=9)
+    m1, m2 = Mesh(d, N, n), Mesh(d, N, n)
+    a = torch.from_numpy(u0.copy()).cuda()
+    b = torch.from_numpy(u0.copy()).cuda()
+    for _ in range(3):
+        m1.step_cfl(a, cfl=0.5)
+        m2.step_cfl(b, cfl=0.5, graph=True)
+    torch.cuda.synchronize()
+    assert torch.equal(a, b)
+
+
+def test_fused_20_steps_2d_against_oracle(orc):
+    # 2D 16^2 N=3 density wave, 20 steps at CFL 0.5 with the time step taken
+    # from each side's own state every step
+    d, N, n = 2, 3, (16, 16)
+    dom = W.box(d)
+    xi, _ = orc.lgl(N)
+    u0 = W.density_wave(d, N, n, dom, xi, velocity=(0.1, 0.2))
+    m = Mesh(d, N, n, tuple(dom))
+    ut = torch.from_numpy(u0.copy()).cuda()
+    uo = u0.copy()
+    for _ in range(20):
+        m.step_cfl(ut, cfl=0.5)
+        uo = orc.lsrk_step(d, N, n, dom, uo, orc.max_dt(d, N, n, dom, uo, cfl=0.5))
+    assert m.check() == 0
+    assert rel_l2(ut.cpu().numpy() - u0, uo - u0) <= 1e-11
