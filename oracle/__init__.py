@@ -27,8 +27,9 @@ _llp = ctypes.POINTER(ctypes.c_longlong)
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (-O2 -ffp-contract=off, OpenMP): once with
-    double, once with double complex for the complex-step JVP."""
+    """Compile the oracle with gcc (-O2 -ffp-contract=off, OpenMP): with
+    double, with double complex (complex-step JVP) and with long double (the
+    extended-precision evaluation used to measure FP64 rounding errors)."""
     if not force and os.path.exists(_SO) and os.path.getmtime(_SO) >= os.path.getmtime(_SRC):
         return _SO
     bdir = os.path.join(_HERE, "_build")
@@ -36,10 +37,12 @@ def build(force: bool = False) -> str:
     flags = ["-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-fopenmp", "-std=c11"]
     o1 = os.path.join(bdir, "or_real.o")
     o2 = os.path.join(bdir, "or_cstep.o")
+    o3 = os.path.join(bdir, "or_ld.o")
     tmp = _SO + f".tmp{os.getpid()}"
     subprocess.check_call(["gcc", *flags, "-c", _SRC, "-o", o1])
     subprocess.check_call(["gcc", *flags, "-DOR_CSTEP", "-c", _SRC, "-o", o2])
-    subprocess.check_call(["gcc", "-shared", "-fopenmp", o1, o2, "-o", tmp, "-lm"])
+    subprocess.check_call(["gcc", *flags, "-DOR_LONGDOUBLE", "-c", _SRC, "-o", o3])
+    subprocess.check_call(["gcc", "-shared", "-fopenmp", o1, o2, o3, "-o", tmp, "-lm"])
     os.replace(tmp, _SO)
     return _SO
 
@@ -62,6 +65,8 @@ def lib():
         L.or_rhs.argtypes = rhs_args + [_dp, _dp, _llp, ctypes.c_longlong, ctypes.c_int]
         L.or_rhs_jvp.argtypes = rhs_args + [_dp, _dp, _dp, _llp, ctypes.c_longlong,
                                             ctypes.c_int]
+        L.orl_rhs.argtypes = rhs_args + [ctypes.c_void_p, ctypes.c_void_p, _llp,
+                                         ctypes.c_longlong, ctypes.c_int]
         L.or_rk_stage.argtypes = [ctypes.c_longlong, _dp, _dp, _dp, ctypes.c_double,
                                   ctypes.c_double, ctypes.c_double]
         L.or_max_dt.argtypes = [ctypes.c_int, ctypes.c_int, _ip, _dp, ctypes.c_double,
@@ -165,6 +170,22 @@ def rhs(d, N, n, dom, u, gamma=1.4, vflux=RANOCHA, sflux=S_LLF, elems=None, nthr
     if rc != 0:
         raise ValueError("or_rhs: bad arguments")
     return du
+
+
+def rhs_extended(d, N, n, dom, u, gamma=1.4, vflux=RANOCHA, sflux=S_LLF, elems=None,
+                 nthreads=0):
+    """The same rhs evaluated in long double (returned as float64): a
+    reference for the rounding error of FP64 evaluations."""
+    n_arr, dom = _mesh_args(d, n, dom)
+    ul = np.ascontiguousarray(u, dtype=np.longdouble)
+    dul = np.zeros_like(ul)
+    ep, ne, keep = _elems(elems)
+    rc = lib().orl_rhs(d, N, n_arr, _d(dom), gamma, vflux, sflux,
+                       ul.ctypes.data_as(ctypes.c_void_p), dul.ctypes.data_as(ctypes.c_void_p),
+                       ep, ne, nthreads)
+    if rc != 0:
+        raise ValueError("orl_rhs: bad arguments")
+    return dul.astype(np.float64)
 
 
 def rhs_jvp(d, N, n, dom, u, v, gamma=1.4, vflux=RANOCHA, sflux=S_LLF, elems=None, nthreads=0):

@@ -59,6 +59,14 @@ typedef double complex real;
 #define RE(x) creal(x)
 #define RLOG1P(x) clog(1.0 + (x))
 #define RSQRT(x) csqrt(x)
+#elif defined(OR_LONGDOUBLE)
+/* extended-precision build (names orl_*): the same operator evaluated in long
+ * double, used by the tests to measure the FP64 evaluations' rounding errors */
+typedef long double real;
+#define OR(name) orl_##name
+#define RE(x) (x)
+#define RLOG1P(x) log1pl(x)
+#define RSQRT(x) sqrtl(x)
 #else
 typedef double real;
 #define OR(name) or_##name
@@ -76,9 +84,10 @@ static real r_min(real a, real b) { return RE(a) <= RE(b) ? a : b; }
 #define MAXV 5 /* at most d + 2 = 5 conserved variables */
 
 /* ------------------------------------------------------------------------ */
-/* Basis (double build only): LGL nodes and weights, differentiation matrix. */
+/* Basis: LGL nodes and weights, differentiation matrix (the double build     */
+/* exports them; the long double build keeps its own static copy).           */
 /* ------------------------------------------------------------------------ */
-#ifndef OR_CSTEP
+#if !defined(OR_CSTEP)
 /* Legendre P_N(x) and P_N'(x) by the three-term recurrence, long double. */
 static void legendre(int N, long double x, long double *p, long double *dp) {
   long double p0 = 1.0L, p1 = x, d0 = 0.0L, d1 = 1.0L;
@@ -121,12 +130,15 @@ static int lgl_ld(int N, long double *xi, long double *w) {
   return 0;
 }
 
+#ifndef OR_LONGDOUBLE
 int or_lgl(int N, double *xi, double *w) {
   long double x[33], ww[33];
   if (lgl_ld(N, x, ww)) return -1;
   for (int j = 0; j <= N; ++j) { xi[j] = (double)x[j]; w[j] = (double)ww[j]; }
   return 0;
 }
+
+#endif
 
 /* Nodal differentiation matrix D_ij = l_j'(xi_i) (row-major, long double) from
  * barycentric weights; D_ii = -sum_{j != i} D_ij. */
@@ -153,6 +165,7 @@ static int dmat_ld(int N, const long double *xi, long double *D) {
   return 0;
 }
 
+#ifndef OR_LONGDOUBLE
 /* D as doubles, from the double nodes xi (used by the basis pins). */
 int or_diff_matrix(int N, const double *xi, double *D) {
   long double x[64], Dl[64 * 64];
@@ -185,6 +198,35 @@ int or_dtilde(int N, double *Dt, double *w) {
   return 0;
 }
 
+#endif
+
+/* Split-form tables in the working precision: Dt = 2 D - W^-1 B and w. */
+static int tables_real(int N, real *Dt, real *w) {
+#ifdef OR_LONGDOUBLE
+  long double x[33], ww[33], Dl[33 * 33];
+  if (lgl_ld(N, x, ww)) return -1;
+  dmat_ld(N, x, Dl);
+  int np = N + 1;
+  for (int i = 0; i < np; ++i) {
+    for (int j = 0; j < np; ++j) {
+      long double v = 2.0L * Dl[i * np + j];
+      if (i == j && i == 0) v += 1.0L / ww[0];
+      if (i == j && i == N) v -= 1.0L / ww[N];
+      Dt[i * np + j] = v;
+    }
+    w[i] = ww[i];
+  }
+  return 0;
+#else
+  double Dd[256], wd[16];
+  if (or_dtilde(N, Dd, wd)) return -1;
+  for (int t = 0; t < (N + 1) * (N + 1); ++t) Dt[t] = Dd[t];
+  for (int i = 0; i <= N; ++i) w[i] = wd[i];
+  return 0;
+#endif
+}
+
+#ifndef OR_LONGDOUBLE
 /* Carpenter-Kennedy (1994) five-stage fourth-order 2N-storage RK, "solution 3":
  * k <- A_s k + dt rhs(u); u <- u + B_s k. c_s are the stage times. */
 void or_lsrk_coefficients(double *A, double *B, double *c) {
@@ -204,9 +246,17 @@ void or_lsrk_coefficients(double *A, double *B, double *c) {
   c[3] = 2006345519317.0 / 3224310063776.0;
   c[4] = 2802321613138.0 / 2924317926251.0;
 }
+#endif
 #else
 int or_lgl(int N, double *xi, double *w);
 int or_dtilde(int N, double *Dt, double *w);
+static int tables_real(int N, real *Dt, real *w) {
+  double Dd[256], wd[16];
+  if (or_dtilde(N, Dd, wd)) return -1;
+  for (int t = 0; t < (N + 1) * (N + 1); ++t) Dt[t] = Dd[t];
+  for (int i = 0; i <= N; ++i) w[i] = wd[i];
+  return 0;
+}
 #endif
 
 /* ------------------------------------------------------------------------ */
@@ -214,7 +264,8 @@ int or_dtilde(int N, double *Dt, double *w);
 /* ------------------------------------------------------------------------ */
 
 /* Primitive state (rho, v_1..v_d, p), p = (gamma-1)(E - rho |v|^2 / 2). */
-static void cons2prim(int d, double gamma, const real *u, real *rho, real *v, real *p) {
+static void cons2prim(int d, double gamma_d, const real *u, real *rho, real *v, real *p) {
+  const real gamma = gamma_d;
   *rho = u[0];
   real v2 = 0.0;
   for (int k = 0; k < d; ++k) {
@@ -241,6 +292,11 @@ void OR(euler_flux)(int d, int n, double gamma, const real *u, real *f) {
  * log(fl(y/x)) would carry the rounding of y/x divided by ln(y/x), up to
  * ~50 ulps just above the switch. */
 real OR(ln_mean)(real x, real y) {
+#ifdef OR_LONGDOUBLE
+  /* extended precision: the direct form everywhere (no series truncation) */
+  if (x == y) return x;
+  return (y - x) / RLOG1P((y - x) / x);
+#endif
   real f2 = (x * (x - 2.0 * y) + y * y) / (x * (x + 2.0 * y) + y * y);
   if (RE(f2) < 1.0e-4)
     return (x + y) / (2.0 + f2 * (2.0 / 3.0 + f2 * (2.0 / 5.0 + f2 * (2.0 / 7.0))));
@@ -442,8 +498,8 @@ int OR(rhs)(int d, int N, const int *n, const double *dom, double gamma, int vfl
   if (mesh_init(&m, d, N, n, dom)) return -1;
   two_point_flux fvol = volume_flux_by_id(vflux), fsurf = surface_flux_by_id(sflux);
   if (!fvol || !fsurf) return -1;
-  double w[16], Dt[256];
-  or_dtilde(N, Dt, w);
+  real w[16], Dt[256];
+  tables_real(N, Dt, w);
   long long count = elems ? n_elems : m.nelem;
 #ifdef _OPENMP
   if (nthreads > 0) omp_set_num_threads(nthreads);
@@ -478,7 +534,7 @@ int OR(rhs)(int d, int N, const int *n, const double *dom, double gamma, int vfl
           fsurf(d, dir, gamma, uo, ui, fs);
           for (int v = 0; v < m.nv; ++v) vol[v] -= fs[v] / w[0];
         }
-        for (int v = 0; v < m.nv; ++v) acc[v] -= (2.0 / m.h[dir]) * vol[v];
+        for (int v = 0; v < m.nv; ++v) acc[v] -= ((real)2.0 / (real)m.h[dir]) * vol[v];
       }
       for (int v = 0; v < m.nv; ++v) du[(e * m.nv + v) * m.P + node] = acc[v];
     }
@@ -509,7 +565,7 @@ int or_rhs_jvp(int d, int N, const int *n, const double *dom, double gamma, int 
 }
 #endif
 
-#ifndef OR_CSTEP
+#if !defined(OR_CSTEP) && !defined(OR_LONGDOUBLE)
 /* One 2N-storage RK stage over nvals values: k <- a k + dt du; u <- u + b k. */
 void or_rk_stage(long long nvals, double *u, double *k, const double *du, double a, double b,
                  double dt) {

@@ -103,13 +103,14 @@ def test_graph_step_and_tuner_are_bitwise_consistent(orc):
 
 
 # Bars. Noisy states (the workloads the FP64 1e-12 and FP32 1e-5 targets are
-# stated on) carry both targets. On the noise-free waves of the ensemble
-# configuration the energy equation is ~10^4-conditioned ((2/h)|Dt||f_E|
-# against |du_E|): the FP64 oracle itself is 7.6e-13 away from an 80-bit
-# evaluation of the same operator on the 32^3 wave, so FP64 agreement is
-# bounded by twice that; FP32 rounding (6e-8) lands between 4e-4 and 5e-3
-# (N=5, 24^3), bounded by 1e-2.
-@pytest.mark.parametrize("precision,noisy,tol", [("fp64", False, 2e-12), ("fp32", False, 1e-2),
+# stated on) carry both targets against the FP64 oracle. On the noise-free
+# waves of the ensemble configuration the energy equation is badly
+# conditioned ((2/h)|Dt||f_E| against |du_E| up to ~10^5 at N=5, 24^3): there
+# both the GPU and the FP64 oracle are measured against the oracle evaluated
+# in long double, and the GPU must be as accurate as the FP64 oracle (within
+# 2x) in FP64, and within 2 x 2^29 of the FP64 oracle's error (the ratio of
+# the unit roundoffs) in FP32.
+@pytest.mark.parametrize("precision,noisy,tol", [("fp64", False, 1e-12), ("fp32", False, 1e-5),
                                                  ("fp64", True, 1e-12), ("fp32", True, 1e-5)])
 def test_48_member_configuration(orc, precision, noisy, tol):
     mem = W.ensemble(n_sims=48, seed=0)
@@ -140,7 +141,13 @@ def test_48_member_configuration(orc, precision, noisy, tol):
         P = (m.N + 1) ** 3
         du = orc.rhs(3, m.N, m.n, W.box(3), parts0[s], elems=elems).reshape(ne, 5, P)[elems]
         gd = ((got[s] - parts0[s]) / (RK_B[0] * big)).reshape(ne, 5, P)[elems]
-        err = rel(gd, du)
+        if noisy:
+            err, bar = rel(gd, du), tol
+        else:
+            ext = orc.rhs_extended(3, m.N, m.n, W.box(3), parts0[s],
+                                   elems=elems).reshape(ne, 5, P)[elems]
+            err, err_or = rel(gd, ext), rel(du, ext)
+            bar = max(tol, 2.0 * err_or * (1.0 if precision == "fp64" else 2.0 ** 29))
         print(f"ensemble member {s} (N={m.N}, n={m.n[0]}) {precision} noisy={noisy} "
-              f"rel err {err:.3e}")
-        assert err <= tol
+              f"rel err {err:.3e} bar {bar:.3e}")
+        assert err <= bar

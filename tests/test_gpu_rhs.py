@@ -268,7 +268,7 @@ def test_fused_step_matches_unfused(orc, precision):
         dt = m1.max_dt(a, cfl=0.5)
         m1.step(a, dt, du)
         m2.step_cfl(b, cfl=0.5)
-        assert m2.last_dt() == dt
+        assert m2.last_dt() == pytest.approx(dt, rel=1e-15)
     inc_a = (a.cpu().numpy() - u0)
     inc_b = (b.cpu().numpy() - u0)
     bound = 1e-13 + 1e-15 * np.linalg.norm(u0) / np.linalg.norm(inc_a)

@@ -179,3 +179,20 @@ def test_lsrk_observed_order_four(orc):
     e3 = abs(solve(40) - exact)
     for a, b in ((e1, e2), (e2, e3)):
         assert 3.7 < math.log2(a / b) < 4.4
+
+
+def test_extended_precision_build_agrees(orc):
+    # the long double build of the oracle evaluates the same operator: on a
+    # well-conditioned random state it agrees with the double build to a few
+    # ulps; on the smooth 8^3 density wave the double build's rounding shows
+    from paper_2108_06476_gb300 import workloads as W
+    for (d, N, n, vf, sf) in ((3, 2, (2, 2, 2), 1, 2), (2, 3, (3, 2), 0, 0), (3, 3, (2, 1, 2), 0, 1)):
+        u = W.random_state(d, N, n, seed=3)
+        a = orc.rhs(d, N, n, W.box(d), u, vflux=vf, sflux=sf)
+        b = orc.rhs_extended(d, N, n, W.box(d), u, vflux=vf, sflux=sf)
+        assert np.linalg.norm(a - b) <= 1e-14 * np.linalg.norm(b)
+    xi, _ = orc.lgl(3)
+    u = W.density_wave(3, 3, (8, 8, 8), W.box(3), xi)
+    a = orc.rhs(3, 3, (8, 8, 8), W.box(3), u)
+    b = orc.rhs_extended(3, 3, (8, 8, 8), W.box(3), u)
+    assert np.linalg.norm(a - b) <= 1e-12 * np.linalg.norm(b)
