@@ -125,7 +125,9 @@ __device__ __forceinline__ void generic_nf(const LinePrim<R, D>& L, const LinePr
 template <int D, int N, typename R, int VF, int EPB>
 __device__ __forceinline__ void volume_direction(int dir, R (*sp)[4 + 2 * D][Shape<D, N>::P],
                                                  R (*sa)[D + 3][Shape<D, N>::P], int el, int l,
-                                                 const Tables<R>& tb, R gm1inv, R Pe) {
+                                                 const Tables<R>& tb, R gm1inv, R Pe,
+                                                 const R* __restrict__ fs, int nelem, int e,
+                                                 int eleft, R pcorr) {
   using S = Shape<D, N>;
   constexpr int NP = S::NP, NV = S::NV;
   constexpr bool F32 = sizeof(R) == 4;
@@ -179,6 +181,30 @@ __device__ __forceinline__ void volume_direction(int dir, R (*sp)[4 + 2 * D][Sha
       }
     }
   }
+  // lifting at the two ends of the line: + liftR F*_R at node N (this
+  // element's face), + liftL F*_L at node 0 (the left neighbour's face); the
+  // face-node index of this line is l. FP32: the left face's normal momentum
+  // is stored relative to the neighbour's pressure reference (pcorr).
+  {
+    const R lr = tb.liftR[dir], ll = tb.liftL[dir];
+    const long long base = (long long)nelem * Shape<D, N>::LINES;
+    const long long oR = (long long)e * Shape<D, N>::LINES + l;
+    const long long oL = (long long)eleft * Shape<D, N>::LINES + l;
+    int comp[NV];
+    comp[0] = 0;
+    comp[1] = 1 + dir;
+    comp[2] = 1 + t1;
+    if (D == 3) comp[D] = 1 + t2;
+    comp[D + 1] = D + 1;
+#pragma unroll
+    for (int c = 0; c < NV; ++c) {
+      const long long row = (long long)(dir * NV + comp[c]) * base;
+      acc[N][c] = fma(lr, fs[row + oR], acc[N][c]);
+      R fl = fs[row + oL];
+      if (F32 && c == 1) fl += pcorr;
+      acc[0][c] = fma(ll, fl, acc[0][c]);
+    }
+  }
 #pragma unroll
   for (int a = 0; a < NP; ++a) {
     const int nd = node[a];
@@ -196,7 +222,7 @@ __global__ void __launch_bounds__(EPB* Shape<D, N>::LINES)
     volume_kernel(double* u, R* __restrict__ du, const R* __restrict__ fs, Geom g, Tables<R> tb,
                   unsigned* __restrict__ err, StageFuse fz) {
   using S = Shape<D, N>;
-  constexpr int NP = S::NP, P = S::P, NV = S::NV, LINES = S::LINES;
+  constexpr int P = S::P, NV = S::NV, LINES = S::LINES;
   constexpr bool F32 = sizeof(R) == 4;
   constexpr int NC = 4 + 2 * D;  // rho, p, p/2 (or p'/2), p/(gamma-1), v[D], v[D]/2
   extern __shared__ __align__(16) unsigned char dg_smem[];
@@ -284,7 +310,11 @@ __global__ void __launch_bounds__(EPB* Shape<D, N>::LINES)
   const R Pe = F32 ? R(s_pref[active ? el : 0][0]) : R(0);
 #pragma unroll 1
   for (int dir = 0; dir < D; ++dir) {
-    if (active) volume_direction<D, N, R, VF, EPB>(dir, sp, sa, el, l, tb, gm1inv, Pe);
+    if (active) {
+      const R pcorr = F32 ? R(s_pref[el][1 + dir]) - Pe : R(0);
+      volume_direction<D, N, R, VF, EPB>(dir, sp, sa, el, l, tb, gm1inv, Pe, fs, nelem, e0 + el,
+                                         s_left[el][dir], pcorr);
+    }
     __syncthreads();
   }
   // epilogue: lifting of the surface fluxes, then the store (or the fused
@@ -294,26 +324,11 @@ __global__ void __launch_bounds__(EPB* Shape<D, N>::LINES)
     const int ell = t / P, node = t % P;
     const int e = e0 + ell;
     if (e >= nelem) continue;
-    const int c[3] = {node % NP, (node / NP) % NP, node / (NP * NP)};
     const R Pself = F32 ? R(s_pref[ell][0]) : R(0);
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
       R val = sa[ell][v][node];
       if (F32 && VF == kVRanocha && v == D + 1) val = fma(Pself, sa[ell][D + 2][node], val);
-#pragma unroll
-      for (int dir = 0; dir < D; ++dir) {
-        // face-node index: the node's other coordinates, first one fastest
-        const int lf = (D == 2) ? ((dir == 0) ? c[1] : c[0])
-                                : (dir == 0) ? (c[1] + NP * c[2])
-                                : (dir == 1) ? (c[0] + NP * c[2]) : (c[0] + NP * c[1]);
-        if (c[dir] == N)
-          val = fma(tb.liftR[dir], fs[((long long)(dir * NV + v) * nelem + e) * LINES + lf], val);
-        if (c[dir] == 0) {
-          R F = fs[((long long)(dir * NV + v) * nelem + s_left[ell][dir]) * LINES + lf];
-          if (F32 && v == 1 + dir) F += R(s_pref[ell][1 + dir]) - Pself;
-          val = fma(tb.liftL[dir], F, val);
-        }
-      }
       const long long i = ((long long)e * NV + v) * P + node;
       if (fz.k) {
         const double kk = fz.a * fz.k[i] + dtv * (double)val;
@@ -388,13 +403,16 @@ __device__ __forceinline__ void surface_nf(int sf, const Trace<R, D>& L, const T
   dq[0] = Rt.rho - L.rho;
   dq[1] = Rt.mn - L.mn;
   dq[D + 1] = dE;
-  const R cl = sqrt(gamma * L.p * rcp(L.rho)), cr = sqrt(gamma * Rt.p * rcp(Rt.rho));
+  const R c2l = gamma * L.p * rcp(L.rho), c2r = gamma * Rt.p * rcp(Rt.rho);
   if (sf == kSLLF) {
-    const R lam = fmax(fabs(L.vn), fabs(Rt.vn)) + fmax(cl, cr);
+    // max(c_L, c_R) = sqrt(max(c_L^2, c_R^2)) exactly (sqrt is monotone and
+    // correctly rounded)
+    const R lam = fmax(fabs(L.vn), fabs(Rt.vn)) + sqrt(fmax(c2l, c2r));
 #pragma unroll
     for (int v = 0; v < D + 2; ++v) f[v] = R(0.5) * (fl[v] + fr[v]) - R(0.5) * lam * dq[v];
     return;
   }
+  const R cl = sqrt(c2l), cr = sqrt(c2r);
   const R sL = fmin(L.vn - cl, Rt.vn - cr);
   const R sR = fmax(L.vn + cl, Rt.vn + cr);
 #pragma unroll
