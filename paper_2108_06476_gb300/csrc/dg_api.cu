@@ -190,14 +190,48 @@ __global__ void rk_stage_kernel(double* __restrict__ u, double* __restrict__ k,
 
 // Max over elements of sum_k (2/h_k) max_nodes(|v_k| + c); one warp per
 // element, one atomic per block on the ordered bit pattern of the result.
-template <int D>
+// R = float evaluates the wave speeds in FP32 (FP32 meshes: the time step
+// needs no more than a few digits), R = double as the FP64 path.
+__device__ __forceinline__ void speed_node(const double* c, int D, const Geom& g, double* lam,
+                                           unsigned& bad, double) {
+  double cc[5];
+  for (int v = 0; v < D + 2; ++v) cc[v] = c[v];
+  if (D == 2) {
+    const dg::Prim<double, 2> q = dg::cons2prim<double, 2>(cc, g.gm1);
+    bad |= dg::prim_check(q);
+    const double cs = sqrt(g.gamma * q.p * (1.0 / q.rho));
+    for (int k = 0; k < 2; ++k) lam[k] = fmax(lam[k], fabs(q.v[k]) + cs);
+  } else {
+    const dg::Prim<double, 3> q = dg::cons2prim<double, 3>(cc, g.gm1);
+    bad |= dg::prim_check(q);
+    const double cs = sqrt(g.gamma * q.p * (1.0 / q.rho));
+    for (int k = 0; k < 3; ++k) lam[k] = fmax(lam[k], fabs(q.v[k]) + cs);
+  }
+}
+__device__ __forceinline__ void speed_node(const double* c, int D, const Geom& g, double* lam,
+                                           unsigned& bad, float) {
+  const float rho = (float)c[0];
+  const float rr = 1.0f / rho;
+  float v[3], v2 = 0.0f;
+  for (int k = 0; k < D; ++k) {
+    v[k] = (float)c[1 + k] * rr;
+    v2 = fmaf(v[k], v[k], v2);
+  }
+  const float p = (float)g.gm1 * ((float)c[D + 1] - 0.5f * rho * v2);
+  if (!(rho > 0.0f)) bad |= dg::kErrRho;
+  if (!(p > 0.0f)) bad |= dg::kErrP;
+  if (!isfinite(rho) || !isfinite(p)) bad |= dg::kErrNaN;
+  const float cs = sqrtf((float)g.gamma * p * rr);
+  for (int k = 0; k < D; ++k) lam[k] = fmax(lam[k], (double)(fabsf(v[k]) + cs));
+}
+
+template <int D, typename R>
 __global__ void speed_kernel(const double* __restrict__ u, Geom g, int P, double s0, double s1,
                              double s2, unsigned long long* out, unsigned* err) {
   constexpr int NV = D + 2;
   const int lane = threadIdx.x & 31;
   const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
-  const double gm1 = g.gamma - 1.0;
   double best = 0.0;
   unsigned bad = 0;
   for (long long e = warp; e < g.nelem; e += nwarps) {
@@ -206,11 +240,7 @@ __global__ void speed_kernel(const double* __restrict__ u, Geom g, int P, double
       double c[NV];
 #pragma unroll
       for (int v = 0; v < NV; ++v) c[v] = u[(e * NV + v) * P + node];
-      const dg::Prim<double, D> q = dg::cons2prim<double, D>(c, gm1);
-      bad |= dg::prim_check(q);
-      const double cs = sqrt(g.gamma * q.p * (1.0 / q.rho));
-#pragma unroll
-      for (int k = 0; k < D; ++k) lam[k] = fmax(lam[k], fabs(q.v[k]) + cs);
+      speed_node(c, D, g, lam, bad, R(0));
     }
 #pragma unroll
     for (int k = 0; k < D; ++k)
@@ -340,6 +370,33 @@ __global__ void integrals_final_kernel(const double* __restrict__ partials, int 
 }
 
 bool valid_mesh(const dg_mesh* m) { return m != nullptr && m->k != nullptr; }
+
+int grid_for(long long work, int threads);
+
+// wave-speed reduction into m->speed (FP32 arithmetic on FP32 meshes)
+int launch_speed(dg_mesh* m, const double* u) {
+  const int threads = 256;
+  const int grid = grid_for(m->nelem * 32, threads);
+  const double s0 = 2.0 / m->h[0], s1 = 2.0 / m->h[1], s2 = 2.0 / m->h[2];
+  const bool f32 = m->opt.precision == DG_FP32;
+  if (m->d == 2) {
+    if (f32)
+      speed_kernel<2, float><<<grid, threads, 0, m->stream>>>(u, m->geom, (int)m->P, s0, s1, s2,
+                                                              m->speed, m->err);
+    else
+      speed_kernel<2, double><<<grid, threads, 0, m->stream>>>(u, m->geom, (int)m->P, s0, s1, s2,
+                                                               m->speed, m->err);
+  } else {
+    if (f32)
+      speed_kernel<3, float><<<grid, threads, 0, m->stream>>>(u, m->geom, (int)m->P, s0, s1, s2,
+                                                              m->speed, m->err);
+    else
+      speed_kernel<3, double><<<grid, threads, 0, m->stream>>>(u, m->geom, (int)m->P, s0, s1, s2,
+                                                               m->speed, m->err);
+  }
+  DG_CUDA(cudaGetLastError(), "speed kernel launch");
+  return DG_OK;
+}
 
 int grid_for(long long work, int threads) {
   long long b = (work + threads - 1) / threads;
@@ -612,19 +669,6 @@ int dg_step(dg_mesh* m, double* u, void* du, double dt) {
 }
 
 namespace {
-int launch_speed(dg_mesh* m, const double* u) {
-  const int threads = 256;
-  const int grid = grid_for(m->nelem * 32, threads);
-  const double s0 = 2.0 / m->h[0], s1 = 2.0 / m->h[1], s2 = 2.0 / m->h[2];
-  if (m->d == 2)
-    speed_kernel<2><<<grid, threads, 0, m->stream>>>(u, m->geom, (int)m->P, s0, s1, s2, m->speed,
-                                                     m->err);
-  else
-    speed_kernel<3><<<grid, threads, 0, m->stream>>>(u, m->geom, (int)m->P, s0, s1, s2, m->speed,
-                                                     m->err);
-  DG_CUDA(cudaGetLastError(), "speed kernel launch");
-  return DG_OK;
-}
 
 // dt on the device, then five stages with the update fused into the volume
 // kernel (no du buffer, no host synchronisation)
@@ -721,13 +765,8 @@ int dg_max_dt(dg_mesh* m, const double* u, double cfl, double* dt_out) {
   const int threads = 256;
   const int grid = grid_for(m->nelem * 32, threads);
   const double s0 = 2.0 / m->h[0], s1 = 2.0 / m->h[1], s2 = 2.0 / m->h[2];
-  if (m->d == 2)
-    speed_kernel<2><<<grid, threads, 0, m->stream>>>(u, m->geom, (int)m->P, s0, s1, s2, m->speed,
-                                                     m->err);
-  else
-    speed_kernel<3><<<grid, threads, 0, m->stream>>>(u, m->geom, (int)m->P, s0, s1, s2, m->speed,
-                                                     m->err);
-  DG_CUDA(cudaGetLastError(), "dg_max_dt: launch");
+  int rc0 = launch_speed(m, u);
+  if (rc0) return rc0;
   unsigned long long bits = 0;
   DG_CUDA(cudaMemcpyAsync(&bits, m->speed, sizeof(bits), cudaMemcpyDeviceToHost, m->stream),
           "dg_max_dt: copy");

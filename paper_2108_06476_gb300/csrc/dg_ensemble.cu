@@ -68,8 +68,7 @@ int fail(int code, const char* msg) { return dg::set_last_error(code, msg); }
 
 template <int N>
 struct EShape {
-  static constexpr int NP = N + 1, P = NP * NP * NP, LINES = NP * NP, NV = 5, NC = 10;
-  static constexpr int BYTES_PER_ELEM = (NC + 6) * P;  // times sizeof(R)
+  static constexpr int NP = N + 1, P = NP * NP * NP, LINES = NP * NP, NC = 10;
 };
 
 // conserved trace of node `node` of element e -> Trace (normal-first) with ps
@@ -113,7 +112,7 @@ template <typename R, int N>
 __device__ void ens_process(const EnsArgs& a, const SimDesc& sd, int sim, int e0, int count,
                             const EnsTables& et, unsigned char* smem) {
   using S = EShape<N>;
-  constexpr int NP = S::NP, P = S::P, LINES = S::LINES, NV = 5, NC = S::NC, D = 3;
+  constexpr int NP = S::NP, P = S::P, LINES = S::LINES, NV = 5, NC = S::NC;
   constexpr bool F32 = sizeof(R) == 4;
   R(*sp)[NC][P] = reinterpret_cast<R(*)[NC][P]>(smem);
   R(*sa)[6][P] = reinterpret_cast<R(*)[6][P]>(smem + sizeof(R) * count * NC * P);
