@@ -97,11 +97,13 @@ int dg_lgl_nodes(int N, double *xi, double *w);
  * Non-physical states set the device error word (see dg_mesh_check). */
 int dg_rhs(dg_mesh *mesh, const double *u, void *du);
 
-/* One kernel of dg_rhs, for timing the two kernels separately: parts = 1
+/* One kernel of dg_rhs, for timing the kernels separately: parts = 1
  * launches only the surface-flux kernel (fills the library's face buffer),
  * parts = 2 only the volume kernel with lifting (reads the face buffer of the
- * previous part-1 call on the same u), parts = 3 both (same as dg_rhs).
- * Asynchronous. */
+ * previous part-1 call on the same u), parts = 3 both (same as dg_rhs),
+ * parts = 6 the volume kernel of the fused step (stage update in its
+ * epilogue) with zero stage coefficients: k <- dt du with the last device
+ * time step, u unchanged, du not written. Asynchronous. */
 int dg_rhs_part(dg_mesh *mesh, const double *u, void *du, int parts);
 
 /* Vector-Jacobian product of the rhs: ubar = (d rhs/d u)(u)^T w, for

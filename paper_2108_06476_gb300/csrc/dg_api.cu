@@ -604,16 +604,28 @@ int dg_rhs(dg_mesh* m, const double* u, void* du) { return dg_rhs_part(m, u, du,
 
 int dg_rhs_part(dg_mesh* m, const double* u, void* du, int parts) {
   if (!valid_mesh(m) || !u || !du) return fail(DG_ERR_ARG, "dg_rhs: null argument");
-  if (parts < 1 || parts > 3) return fail(DG_ERR_ARG, "dg_rhs_part: parts must be 1, 2 or 3");
+  if (parts < 1 || (parts > 3 && parts != 6))
+    return fail(DG_ERR_ARG, "dg_rhs_part: parts must be 1, 2, 3 or 6");
+  dg::StageFuse fz;
+  if (parts == 6) {
+    // the volume kernel with the stage update fused in, zero coefficients:
+    // k <- dt du, u unchanged (times the kernel of the fused step)
+    fz.k = m->k;
+    fz.dt = m->dt_dev;
+    fz.a = 0.0;
+    fz.b = 0.0;
+    fz.pref = nullptr;
+    parts = 2;
+  }
   cudaError_t e;
   if (m->opt.precision == DG_FP64) {
     e = (m->d == 2 ? dg::rhs_launch_double_2 : dg::rhs_launch_double_3)(
         m->N, u, (double*)du, (double*)m->fs, m->geom, m->t64, m->opt.volume_flux,
-        m->opt.surface_flux, m->err, m->stream, parts, dg::StageFuse());
+        m->opt.surface_flux, m->err, m->stream, parts, fz);
   } else {
     e = (m->d == 2 ? dg::rhs_launch_float_2 : dg::rhs_launch_float_3)(
         m->N, u, (float*)du, (float*)m->fs, m->geom, m->t32, m->opt.volume_flux,
-        m->opt.surface_flux, m->err, m->stream, parts, dg::StageFuse());
+        m->opt.surface_flux, m->err, m->stream, parts, fz);
   }
   if (e != cudaSuccess) return cuda_fail(e, "dg_rhs: launch");
   return DG_OK;
