@@ -47,35 +47,73 @@ def build(force: bool = False) -> str:
     return _SO
 
 
+def _declare(L):
+    """Argument types of the oracle's C entry points on a loaded library."""
+    L.or_lgl.argtypes = [ctypes.c_int, _dp, _dp]
+    L.or_diff_matrix.argtypes = [ctypes.c_int, _dp, _dp]
+    L.or_dtilde.argtypes = [ctypes.c_int, _dp, _dp]
+    L.or_lsrk_coefficients.argtypes = [_dp, _dp, _dp]
+    L.or_ln_mean.argtypes = [ctypes.c_double, ctypes.c_double]
+    L.or_ln_mean.restype = ctypes.c_double
+    L.or_two_point.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                               _dp, _dp, _dp]
+    rhs_args = [ctypes.c_int, ctypes.c_int, _ip, _dp, ctypes.c_double, ctypes.c_int,
+                ctypes.c_int]
+    L.or_rhs.argtypes = rhs_args + [_dp, _dp, _llp, ctypes.c_longlong, ctypes.c_int]
+    L.or_rhs_jvp.argtypes = rhs_args + [_dp, _dp, _dp, _llp, ctypes.c_longlong,
+                                        ctypes.c_int]
+    L.orl_rhs.argtypes = rhs_args + [ctypes.c_void_p, ctypes.c_void_p, _llp,
+                                     ctypes.c_longlong, ctypes.c_int]
+    L.or_rk_stage.argtypes = [ctypes.c_longlong, _dp, _dp, _dp, ctypes.c_double,
+                              ctypes.c_double, ctypes.c_double]
+    L.or_max_dt.argtypes = [ctypes.c_int, ctypes.c_int, _ip, _dp, ctypes.c_double,
+                            ctypes.c_double, _dp]
+    L.or_max_dt.restype = ctypes.c_double
+    L.or_integrals.argtypes = [ctypes.c_int, ctypes.c_int, _ip, _dp, ctypes.c_double, _dp,
+                               _dp]
+    return L
+
+
 def lib():
     global _lib
     if _lib is None:
         build()
-        L = ctypes.CDLL(_SO)
-        L.or_lgl.argtypes = [ctypes.c_int, _dp, _dp]
-        L.or_diff_matrix.argtypes = [ctypes.c_int, _dp, _dp]
-        L.or_dtilde.argtypes = [ctypes.c_int, _dp, _dp]
-        L.or_lsrk_coefficients.argtypes = [_dp, _dp, _dp]
-        L.or_ln_mean.argtypes = [ctypes.c_double, ctypes.c_double]
-        L.or_ln_mean.restype = ctypes.c_double
-        L.or_two_point.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
-                                   _dp, _dp, _dp]
-        rhs_args = [ctypes.c_int, ctypes.c_int, _ip, _dp, ctypes.c_double, ctypes.c_int,
-                    ctypes.c_int]
-        L.or_rhs.argtypes = rhs_args + [_dp, _dp, _llp, ctypes.c_longlong, ctypes.c_int]
-        L.or_rhs_jvp.argtypes = rhs_args + [_dp, _dp, _dp, _llp, ctypes.c_longlong,
-                                            ctypes.c_int]
-        L.orl_rhs.argtypes = rhs_args + [ctypes.c_void_p, ctypes.c_void_p, _llp,
-                                         ctypes.c_longlong, ctypes.c_int]
-        L.or_rk_stage.argtypes = [ctypes.c_longlong, _dp, _dp, _dp, ctypes.c_double,
-                                  ctypes.c_double, ctypes.c_double]
-        L.or_max_dt.argtypes = [ctypes.c_int, ctypes.c_int, _ip, _dp, ctypes.c_double,
-                                ctypes.c_double, _dp]
-        L.or_max_dt.restype = ctypes.c_double
-        L.or_integrals.argtypes = [ctypes.c_int, ctypes.c_int, _ip, _dp, ctypes.c_double, _dp,
-                                   _dp]
-        _lib = L
+        _lib = _declare(ctypes.CDLL(_SO))
     return _lib
+
+
+def build_variant(src_text: str, out_dir: str) -> str:
+    """Compile a (modified) copy of the oracle source into out_dir, for tests
+    that plant mistakes and check that the pins catch them."""
+    src = os.path.join(out_dir, "variant.c")
+    with open(src, "w") as fh:
+        fh.write(src_text)
+    flags = ["-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-fopenmp", "-std=c11"]
+    objs = []
+    for tag, defs in (("r", []), ("c", ["-DOR_CSTEP"]), ("l", ["-DOR_LONGDOUBLE"])):
+        o = os.path.join(out_dir, f"v_{tag}.o")
+        subprocess.check_call(["gcc", *flags, *defs, "-c", src, "-o", o])
+        objs.append(o)
+    so = os.path.join(out_dir, "libvariant.so")
+    subprocess.check_call(["gcc", "-shared", "-fopenmp", *objs, "-o", so, "-lm"])
+    return so
+
+
+class use_library:
+    """Context manager: route this module's functions to another build."""
+
+    def __init__(self, so_path):
+        self.so_path = so_path
+
+    def __enter__(self):
+        global _lib
+        self.saved = lib()
+        _lib = _declare(ctypes.CDLL(self.so_path))
+        return self
+
+    def __exit__(self, *exc):
+        global _lib
+        _lib = self.saved
 
 
 def _d(a):
