@@ -165,9 +165,20 @@ __device__ __forceinline__ unsigned prim_check(const Prim<R, D>& q) {
 // relative to the result; outside it ln(y/x) = log1p((y - x)/x). Neither
 // branch divides a rounding error by ln(y/x), which the flux differencing
 // would amplify by (2/h)|Dt||f|/|du|, and the series branch divides nothing.
-// FP64: series for f2 < 1e-2, Q and S through f2^7 (truncation < 2e-18).
-__device__ __forceinline__ double series_q(double f2) {
-  double q = -25865068.0 / 1915538625.0;
+// Three ranges of f2, each lane choosing its own (so a result never depends
+// on which other lanes share its warp):
+//   short  the low-order terms only (FP64 f2 < 1e-2, FP32 f2 < 4e-2),
+//   long   the same terms plus a higher-order tail (FP64 f2 < 0.16,
+//          FP32 f2 < 0.25): the tail enters Horner's scheme as the value
+//          the low-order part starts from, so a short lane, whose tail is
+//          zero, gets bitwise the short result,
+//   far    log1p.
+// On rough data a warp with one lane past the short range pays the tail
+// (about a dozen FMAs) rather than a logarithm and a division.
+// FP64 short: Q and S through f2^7 (truncation < 6e-18); long: Q through
+// f2^19 and S through f2^20 (truncation < 6e-19).
+__device__ __forceinline__ double series_q(double f2, double tail) {
+  double q = fma(f2, tail, -25865068.0 / 1915538625.0);
   q = fma(f2, q, -10719068.0 / 638512875.0);
   q = fma(f2, q, -10196.0 / 467775.0);
   q = fma(f2, q, -428.0 / 14175.0);
@@ -176,8 +187,8 @@ __device__ __forceinline__ double series_q(double f2) {
   q = fma(f2, q, -1.0 / 3.0);
   return fma(f2, q, 1.0);
 }
-__device__ __forceinline__ double series_s(double f2) {
-  double S = 2.0 / 15.0;
+__device__ __forceinline__ double series_s(double f2, double tail) {
+  double S = fma(f2, tail, 2.0 / 15.0);
   S = fma(f2, S, 2.0 / 13.0);
   S = fma(f2, S, 2.0 / 11.0);
   S = fma(f2, S, 2.0 / 9.0);
@@ -186,46 +197,102 @@ __device__ __forceinline__ double series_s(double f2) {
   S = fma(f2, S, 2.0 / 3.0);
   return fma(f2, S, 2.0);
 }
-// FP32: series for f2 < 4e-2, Q and S through f2^5 (truncation < 1e-9).
-__device__ __forceinline__ float series_q(float f2) {
-  float q = -10196.0f / 467775.0f;
+// sum_{k=8..19} q_k f2^(k-8), q_k the coefficients of Q above
+__device__ __forceinline__ double series_q_tail(double f2) {
+  double r = -0.003460014667462103;
+  r = fma(f2, r, -0.0037184010824199377);
+  r = fma(f2, r, -0.004013287468010989);
+  r = fma(f2, r, -0.004352550122988381);
+  r = fma(f2, r, -0.004746430692874202);
+  r = fma(f2, r, -0.005208475658374312);
+  r = fma(f2, r, -0.005756954446288888);
+  r = fma(f2, r, -0.006417063031397296);
+  r = fma(f2, r, -0.007224464737393906);
+  r = fma(f2, r, -0.008231206567350501);
+  r = fma(f2, r, -0.009516073194527899);
+  return fma(f2, r, -0.011203745637718733);
+}
+// sum_{k=8..20} 2 f2^(k-8) / (2k + 1)
+__device__ __forceinline__ double series_s_tail(double f2) {
+  double r = 2.0 / 41.0;
+  r = fma(f2, r, 2.0 / 39.0);
+  r = fma(f2, r, 2.0 / 37.0);
+  r = fma(f2, r, 2.0 / 35.0);
+  r = fma(f2, r, 2.0 / 33.0);
+  r = fma(f2, r, 2.0 / 31.0);
+  r = fma(f2, r, 2.0 / 29.0);
+  r = fma(f2, r, 2.0 / 27.0);
+  r = fma(f2, r, 2.0 / 25.0);
+  r = fma(f2, r, 2.0 / 23.0);
+  r = fma(f2, r, 2.0 / 21.0);
+  r = fma(f2, r, 2.0 / 19.0);
+  return fma(f2, r, 2.0 / 17.0);
+}
+// FP32 short: Q and S through f2^5 (truncation < 1e-9); long: Q through
+// f2^10 and S through f2^11 (truncation < 4e-9).
+__device__ __forceinline__ float series_q(float f2, float tail) {
+  float q = fmaf(f2, tail, -10196.0f / 467775.0f);
   q = fmaf(f2, q, -428.0f / 14175.0f);
   q = fmaf(f2, q, -44.0f / 945.0f);
   q = fmaf(f2, q, -4.0f / 45.0f);
   q = fmaf(f2, q, -1.0f / 3.0f);
   return fmaf(f2, q, 1.0f);
 }
-__device__ __forceinline__ float series_s(float f2) {
-  float S = 2.0f / 11.0f;
+__device__ __forceinline__ float series_s(float f2, float tail) {
+  float S = fmaf(f2, tail, 2.0f / 11.0f);
   S = fmaf(f2, S, 2.0f / 9.0f);
   S = fmaf(f2, S, 2.0f / 7.0f);
   S = fmaf(f2, S, 2.0f / 5.0f);
   S = fmaf(f2, S, 2.0f / 3.0f);
   return fmaf(f2, S, 2.0f);
 }
+__device__ __forceinline__ float series_q_tail(float f2) {  // sum_{k=6..10} q_k f2^(k-6)
+  float r = -0.00823120679706335f;
+  r = fmaf(f2, r, -0.009516073390841484f);
+  r = fmaf(f2, r, -0.011203745380043983f);
+  r = fmaf(f2, r, -0.013502765446901321f);
+  return fmaf(f2, r, -0.01678755134344101f);
+}
+__device__ __forceinline__ float series_s_tail(float f2) {  // sum_{k=6..11} 2 f2^(k-6)/(2k+1)
+  float r = 2.0f / 23.0f;
+  r = fmaf(f2, r, 2.0f / 21.0f);
+  r = fmaf(f2, r, 2.0f / 19.0f);
+  r = fmaf(f2, r, 2.0f / 17.0f);
+  r = fmaf(f2, r, 2.0f / 15.0f);
+  return fmaf(f2, r, 2.0f / 13.0f);
+}
+__device__ __forceinline__ double series_q(double f2) { return series_q(f2, 0.0); }
+__device__ __forceinline__ double series_s(double f2) { return series_s(f2, 0.0); }
+__device__ __forceinline__ float series_q(float f2) { return series_q(f2, 0.0f); }
+__device__ __forceinline__ float series_s(float f2) { return series_s(f2, 0.0f); }
 __device__ __forceinline__ double series_limit(double) { return 1.0e-2; }
 __device__ __forceinline__ float series_limit(float) { return 4.0e-2f; }
 
-// far from x = y: the direct forms (rare on smooth data; kept out of line)
+// far from x = y: the direct forms (rare; kept out of line)
 static __device__ __noinline__ double ln_mean_far(double x, double y) { return (y - x) / log1p((y - x) / x); }
 static __device__ __noinline__ float ln_mean_far(float x, float y) { return (y - x) / log1pf((y - x) / x); }
 static __device__ __noinline__ double inv_ln_mean_far(double x, double y) { return log1p((y - x) / x) / (y - x); }
 static __device__ __noinline__ float inv_ln_mean_far(float x, float y) { return log1pf((y - x) / x) / (y - x); }
 
-// f2 >= 0, so the branch test compares IEEE bit patterns on the integer
+// f2 >= 0, so the FP64 range tests compare IEEE bit patterns on the integer
 // pipe (the FP64 pipe is the bottleneck of the FP64 kernels)
-__device__ __forceinline__ bool in_series(double f2) {
+__device__ __forceinline__ bool in_short(double f2) {
   return __double_as_longlong(f2) < 0x3F847AE147AE147BLL;  // bits of 1e-2
 }
-__device__ __forceinline__ bool in_series(float f2) { return f2 < 4.0e-2f; }
+__device__ __forceinline__ bool in_long(double f2) {
+  return __double_as_longlong(f2) < 0x3FC47AE147AE147BLL;  // bits of 0.16
+}
+__device__ __forceinline__ bool in_short(float f2) { return f2 < 4.0e-2f; }
+__device__ __forceinline__ bool in_long(float f2) { return f2 < 0.25f; }
 
 template <typename R>
 __device__ __forceinline__ R ln_mean(R x, R y) {
   const R s = x + y;
   const R t = (y - x) * rcp(s);
   const R f2 = t * t;
-  if (in_series(f2)) return R(0.5) * s * series_q(f2);
-  return ln_mean_far(x, y);
+  if (!in_long(f2)) return ln_mean_far(x, y);
+  const R tail = in_short(f2) ? R(0) : series_q_tail(f2);
+  return R(0.5) * s * series_q(f2, tail);
 }
 
 template <typename R>
@@ -233,8 +300,9 @@ __device__ __forceinline__ R inv_ln_mean(R x, R y) {
   const R rs = rcp(x + y);
   const R t = (y - x) * rs;
   const R f2 = t * t;
-  if (in_series(f2)) return series_s(f2) * rs;
-  return inv_ln_mean_far(x, y);
+  if (!in_long(f2)) return inv_ln_mean_far(x, y);
+  const R tail = in_short(f2) ? R(0) : series_s_tail(f2);
+  return series_s(f2, tail) * rs;
 }
 
 // ---- two-point volume fluxes f#(L, R) in direction DIR ----
