@@ -126,7 +126,8 @@ DG_DUAL Dual<R, K> fmin(const Dual<R, K>& a, const Dual<R, K>& b) { return a.v <
 DG_DUAL Dual<R, K> fabs(const Dual<R, K>& a) { return a.v < R(0) ? -a : a; }
 
 DG_DUAL Dual<R, K> series_q(const Dual<R, K>& f2) {
-  // same coefficients as the scalar series (t / atanh t in powers of f2)
+  // Taylor coefficients of t / atanh t in powers of f2 through f2^7
+  // (truncation below 2e-18 for f2 < 1e-2; log1p beyond)
   const R c[8] = {R(1.0), R(-1.0 / 3.0), R(-4.0 / 45.0), R(-44.0 / 945.0), R(-428.0 / 14175.0),
                   R(-10196.0 / 467775.0), R(-10719068.0 / 638512875.0),
                   R(-25865068.0 / 1915538625.0)};

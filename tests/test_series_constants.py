@@ -1,31 +1,24 @@
-"""The log-mean series constants of the CUDA kernels, read from the header
-and checked on the CPU against exact rational arithmetic.
+"""The log-mean polynomials of the CUDA kernels, read from the header and
+checked on the CPU against 40-digit values of the functions they replace.
 
 The device code evaluates ln_mean(x, y) = (s/2) Q(f2) and 1/ln_mean(x, y) =
-S(f2)/s, with s = x + y, f2 = ((y - x)/s)^2, S(f2) = 2 atanh(t)/t =
-2 sum_k f2^k/(2k+1) and Q = 1/(S/2) (the logarithmic mean of Ranocha's flux,
-Sec. 2 of the paper; the series follows from ln(y/x) = 2 atanh t). Q's
-coefficients are rebuilt here by inverting the power series of atanh(t)/t
-with fractions; the range limits are checked against their bit patterns and
-the truncation bounds the header states."""
-import math
+S(f2)/s with s = x + y, f2 = ((y - x)/s)^2, S(f2) = 2 atanh(t)/t =
+2 sum_k f2^k/(2k+1) and Q = 2/S (the logarithmic mean of Ranocha's flux,
+Sec. 3.2 of the paper; ln(y/x) = 2 atanh t). Here S is summed from its
+series in decimal arithmetic, the header's coefficients are taken exactly as
+the doubles (floats) they are, and the relative error over each polynomial's
+interval must stay within the bound its comment states."""
 import os
 import re
 import struct
-from fractions import Fraction
+from decimal import Decimal, getcontext
 
 import numpy as np
 import pytest
 
 HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
                       "paper_2108_06476_gb300", "csrc", "dg_device.cuh")
-
-K = 24
-A = [Fraction(1, 2 * k + 1) for k in range(K)]  # atanh(t)/t in powers of f2
-Q = [Fraction(1)] + [Fraction(0)] * (K - 1)
-for _n in range(1, K):
-    Q[_n] = -sum(A[j] * Q[_n - j] for j in range(1, _n + 1))
-S = [2 * a for a in A]
+getcontext().prec = 40
 
 
 @pytest.fixture(scope="module")
@@ -45,88 +38,75 @@ def _body(text, signature):
         k += 1
 
 
-def _value(expr):
-    expr = re.sub(r"(\d)f\b", r"\1", expr.strip())
-    assert re.fullmatch(r"[-+0-9.e/ ]+", expr), expr
-    return eval(expr)  # a literal or a quotient of two literals
+def polynomial(text, real, name):
+    """(coefficients lowest order first, interval end, stated error)."""
+    sig = f"{real} {name}({real} f2)"
+    body = _body(text, sig)
+    comment = text[:text.rfind("\n", 0, text.index(sig))].splitlines()[-1]
+    m = re.search(r"degree (\d+) on f2 in \[0, ([0-9.e-]+)\]; measured relative error ([0-9.e-]+)",
+                  comment)
+    assert m, comment
+    lits = re.findall(r"(-?\d+\.\d*(?:e-?\d+)?)f?[;)]", body)
+    coeffs = [float(x) for x in lits][::-1]
+    if real == "float":
+        assert all(float(np.float32(c)) == c for c in coeffs)
+    assert len(coeffs) == int(m.group(1)) + 1
+    return coeffs, Decimal(m.group(2)), float(m.group(3))
 
 
-def coefficients(text, signature):
-    """Horner constants of one device function, lowest order first."""
-    body = _body(text, signature)
-    consts = []
-    m = re.search(r"(?:double|float) \w+ = ([^;]+);", body)
-    if m and "fma" not in m.group(1):
-        consts.append(_value(m.group(1)))
-    for m in re.finditer(r"fmaf?\(f2, \w+, ([^;]+?)\)(?:;|$)", body, re.M):
-        consts.append(_value(m.group(1)))
-    return consts[::-1]
+def S_ref(f2):
+    total, term, k = Decimal(0), Decimal(1), 0
+    while term > Decimal("1e-45") or k < 2:
+        total += term / (2 * k + 1)
+        term *= f2
+        k += 1
+    return 2 * total
 
 
-CASES = [
-    # (real, series, tail, exact coefficients, short terms, long terms, limits, rtol)
-    ("double", "series_q", "series_q_tail", Q, 8, 20, (1e-2, 0.16), 2e-16),
-    ("double", "series_s", "series_s_tail", S, 8, 21, (1e-2, 0.16), 2e-16),
-    ("float", "series_q", "series_q_tail", Q, 6, 11, (4e-2, 0.25), 1e-7),
-    ("float", "series_s", "series_s_tail", S, 6, 12, (4e-2, 0.25), 1e-7),
-]
+def Q_ref(f2):
+    return 2 / S_ref(f2)
 
 
-@pytest.mark.parametrize("real,series,tail,exact,n_short,n_long,limits,rtol", CASES)
-def test_coefficients_are_the_series(header, real, series, tail, exact, n_short, n_long,
-                                     limits, rtol):
-    low = coefficients(header, f"{real} {series}({real} f2, {real} tail)")
-    high = coefficients(header, f"{real} {tail}({real} f2)")
-    assert len(low) == n_short and len(low) + len(high) == n_long
-    for k, c in enumerate(low + high):
-        assert abs(c - float(exact[k])) <= rtol * abs(float(exact[k])), (series, k)
+POLYS = [("double", "q_short", Q_ref, 2e-19), ("double", "s_short", S_ref, 5e-19),
+         ("double", "q_long", Q_ref, 2e-17), ("double", "s_long", S_ref, 1e-17),
+         ("float", "q_short", Q_ref, 3e-9), ("float", "s_short", S_ref, 1e-9),
+         ("float", "q_long", Q_ref, 5e-9), ("float", "s_long", S_ref, 6e-9)]
 
 
-@pytest.mark.parametrize("real,series,tail,exact,n_short,n_long,limits,rtol", CASES)
-def test_truncation_within_stated_bounds(real, series, tail, exact, n_short, n_long, limits,
-                                         rtol):
-    # the coefficients' magnitudes never grow and every omitted term has
-    # the sign of the first one, so the omitted sum is below
-    # |first term| / (1 - f2) relative to the value at f2 = 0
-    assert all(abs(exact[k + 1]) <= abs(exact[k]) for k in range(K - 1))
-    bound = {"double": (6e-18, 6e-19), "float": (1e-9, 4e-9)}[real]
-    for n, lim, b in ((n_short, limits[0], bound[0]), (n_long, limits[1], bound[1])):
-        first = abs(exact[n]) * Fraction(lim) ** n
-        assert float(first / (1 - Fraction(lim)) / abs(exact[0])) < b
+@pytest.mark.parametrize("real,name,ref,cap", POLYS, ids=[f"{p[0]}-{p[1]}" for p in POLYS])
+def test_polynomial_accuracy(header, real, name, ref, cap):
+    coeffs, a, stated = polynomial(header, real, name)
+    assert stated <= cap
+    assert coeffs[0] == (1.0 if name.startswith("q") else 2.0)  # ln_mean(x, x) = x exactly
+    exact = [Decimal(c) for c in coeffs]
+    worst = Decimal(0)
+    n = 600
+    for k in range(n + 1):
+        x = a * k / n
+        p = Decimal(0)
+        for c in reversed(exact):
+            p = p * x + c
+        worst = max(worst, abs(p / ref(x) - 1))
+    assert float(worst) <= 1.05 * stated, (name, float(worst))
 
 
-def test_range_limits_bit_patterns(header):
-    for value, name in ((1e-2, "in_short"), (0.16, "in_long")):
+def test_series_reference_is_the_logarithmic_mean():
+    # Q_ref(f2) with x = 1 - t, y = 1 + t (s/2 = 1) against (y - x)/ln(y/x)
+    for t in ("0.01", "0.1", "0.3", "0.49"):
+        t = Decimal(t)
+        lm = 2 * t / ((1 + t) / (1 - t)).ln()
+        assert abs(Q_ref(t * t) / lm - 1) < Decimal("1e-35")
+
+
+def test_range_limits(header):
+    for value, name in ((1e-2, "in_short"), (0.25, "in_long")):
         body = _body(header, f"bool {name}(double f2)")
         bits = int(re.search(r"0x([0-9A-F]+)LL", body).group(1), 16)
         assert struct.unpack("<q", struct.pack("<d", value))[0] == bits
     assert "f2 < 4.0e-2f" in _body(header, "bool in_short(float f2)")
     assert "f2 < 0.25f" in _body(header, "bool in_long(float f2)")
-
-
-def _horner(f2, coeffs):
-    r = 0.0
-    for c in reversed(coeffs):
-        r = r * f2 + c
-    return r
-
-
-def test_long_range_log_mean_accuracy(header):
-    """The long-range FP64 evaluation (tail, then the low-order part) matches
-    the logarithmic mean to a few ulp over f2 in [1e-2, 0.16], and the short
-    one over [0, 1e-2]; x = 1 - t and y = 1 + t make s = 2 and the reference
-    2t / (log1p(t) - log1p(-t)), correct to about one ulp."""
-    q_lo = coefficients(header, "double series_q(double f2, double tail)")
-    q_hi = coefficients(header, "double series_q_tail(double f2)")
-    s_lo = coefficients(header, "double series_s(double f2, double tail)")
-    s_hi = coefficients(header, "double series_s_tail(double f2)")
-    worst = 0.0
-    for t in np.concatenate([np.linspace(0.0, 0.0999, 40), np.linspace(0.1, 0.3999, 60)]):
-        f2 = t * t
-        longer = f2 >= 1e-2
-        qv = _horner(f2, q_lo + q_hi if longer else q_lo)
-        sv = _horner(f2, s_lo + s_hi if longer else s_lo)
-        # x = 1 - t, y = 1 + t: s = 2, ln_mean = 2 t / ln((1+t)/(1-t))
-        exact = 1.0 if t == 0 else 2 * t / (math.log1p(t) - math.log1p(-t))
-        worst = max(worst, abs(qv - exact) / exact, abs(sv / 2 - 1 / exact) * exact)
-    assert worst < 2e-15
+    # every polynomial covers the range that selects it
+    for real, short, long_ in (("double", 1e-2, 0.25), ("float", 4e-2, 0.25)):
+        for name, lim in (("q_short", short), ("s_short", short), ("q_long", long_),
+                          ("s_long", long_)):
+            assert float(polynomial(header, real, name)[1]) >= lim
