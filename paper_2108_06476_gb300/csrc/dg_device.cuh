@@ -315,6 +315,38 @@ __device__ __forceinline__ R inv_ln_mean(R x, R y) {
   return S * rs;
 }
 
+// ln_mean(2 hx, 2 hy) from the halves: every step is the one of
+// ln_mean(x, y) scaled by an exact factor 2, so the result is bitwise
+// ln_mean(x, y), without the product (x + y)/2.
+template <typename R>
+__device__ __forceinline__ R ln_mean_halves(R hx, R hy) {
+  const R hs = hx + hy;
+  const R t = (hy - hx) * rcp(hs);
+  const R f2 = t * t;
+  if (!in_long(f2)) return R(2) * ln_mean_far(hx, hy);
+  R q;
+  if (in_short(f2))
+    q = q_short(f2);
+  else
+    q = q_long(f2);
+  return hs * q;
+}
+
+// a + 1/ln_mean(x, y), the last product fused into the addition
+template <typename R>
+__device__ __forceinline__ R add_inv_ln_mean(R x, R y, R a) {
+  const R rs = rcp(x + y);
+  const R t = (y - x) * rs;
+  const R f2 = t * t;
+  if (!in_long(f2)) return a + inv_ln_mean_far(x, y);
+  R S;
+  if (in_short(f2))
+    S = s_short(f2);
+  else
+    S = s_long(f2);
+  return fma(S, rs, a);
+}
+
 // ---- two-point volume fluxes f#(L, R) in direction DIR ----
 enum { kVRanocha = 0, kVChandrashekar = 1, kVCentral = 2 };
 

@@ -68,7 +68,7 @@ int fail(int code, const char* msg) { return dg::set_last_error(code, msg); }
 
 template <int N>
 struct EShape {
-  static constexpr int NP = N + 1, P = NP * NP * NP, LINES = NP * NP, NC = 10;
+  static constexpr int NP = N + 1, P = NP * NP * NP, LINES = NP * NP, NC = 9;
 };
 
 // conserved trace of node `node` of element e -> Trace (normal-first) with ps
@@ -165,14 +165,12 @@ __device__ void ens_process(const EnsArgs& a, const SimDesc& sd, int sim, int e0
 #pragma unroll
       for (int k = 0; k < 3; ++k) vv[k] = R(q.v[k]);
     }
-    sp[el][0][node] = rho;
-    sp[el][1][node] = p;
+    node_slots<kVRanocha, R>(rho, p, R(a.gm1), sp[el][0][node], sp[el][1][node]);
     sp[el][2][node] = hp;
-    sp[el][3][node] = p * gm1inv;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-      sp[el][4 + k][node] = vv[k];
-      sp[el][7 + k][node] = R(0.5) * vv[k];
+      sp[el][3 + k][node] = vv[k];
+      sp[el][6 + k][node] = R(0.5) * vv[k];
     }
 #pragma unroll
     for (int k = 0; k < 6; ++k) sa[el][k][node] = R(0);
@@ -193,16 +191,15 @@ __device__ void ens_process(const EnsArgs& a, const SimDesc& sd, int sim, int e0
       for (int i = 0; i < NP; ++i) {
         node[i] = line_node_rt<3, N>(dir, l, i);
         const int nd = node[i];
-        q[i].rho = sp[el][0][nd];
-        q[i].p = sp[el][1][nd];
+        q[i].s0 = sp[el][0][nd];
+        q[i].s1 = sp[el][1][nd];
         q[i].hp = sp[el][2][nd];
-        q[i].pg = sp[el][3][nd];
-        q[i].vn = sp[el][4 + dir][nd];
-        q[i].hvn = sp[el][7 + dir][nd];
-        q[i].vt[0] = sp[el][4 + t1][nd];
-        q[i].hvt[0] = sp[el][7 + t1][nd];
-        q[i].vt[1] = sp[el][4 + t2][nd];
-        q[i].hvt[1] = sp[el][7 + t2][nd];
+        q[i].vn = sp[el][3 + dir][nd];
+        q[i].hvn = sp[el][6 + dir][nd];
+        q[i].vt[0] = sp[el][3 + t1][nd];
+        q[i].hvt[0] = sp[el][6 + t1][nd];
+        q[i].vt[1] = sp[el][3 + t2][nd];
+        q[i].hvt[1] = sp[el][6 + t2][nd];
       }
       constexpr int NA = F32 ? 6 : 5;
       R acc[NP][NA];
@@ -434,7 +431,7 @@ int smem_for(int precision, int block) {
   int m = 0;
   for (int N = kEnsMinN; N <= kEnsMaxN; ++N) {
     const int P = (N + 1) * (N + 1) * (N + 1);
-    const int b = items_epb(N, block) * 16 * P * rs;
+    const int b = items_epb(N, block) * (9 + 6) * P * rs;  // node slots + accumulators
     if (b > m) m = b;
   }
   return m;

@@ -76,30 +76,46 @@ __device__ __forceinline__ void prim_f32(const double* c, float gm1, float Pe, f
   p = Pe + pp;
 }
 
-// node primitives as seen by one direction: normal component first
+// node primitives as seen by one direction, normal component first. The two
+// leading slots depend on the volume flux: Ranocha's flux takes s0 = rho/2
+// and s1 = sig = (gamma-1) rho / p, since the log mean is homogeneous,
+//   p_L p_R / ((gamma-1) ln_mean(rho_L p_R, rho_R p_L)) = 1 / ln_mean(sig_L, sig_R),
+// which leaves no product of left and right values inside either log mean;
+// the other fluxes take s0 = rho, s1 = p.
 template <typename R, int D>
 struct LinePrim {
-  R rho, p, hp, pg, vn, hvn;
+  R s0, s1, hp, vn, hvn;
   R vt[D - 1], hvt[D - 1];
 };
+
+template <int VF, typename R>
+__device__ __forceinline__ void node_slots(R rho, R p, R gm1, R& s0, R& s1) {
+  if (VF == kVRanocha) {
+    s0 = R(0.5) * rho;
+    s1 = gm1 * rho * rcp(p);
+  } else {
+    s0 = rho;
+    s1 = p;
+  }
+}
 
 // Ranocha's EC/KEP flux in normal-first order. hp is p/2 (FP64) or p'/2
 // (FP32, then the P_e parts are handled by the caller); an = avg(v_n).
 template <typename R, int D>
 __device__ __forceinline__ void ranocha_nf(const LinePrim<R, D>& L, const LinePrim<R, D>& Rt,
                                            R f[D + 2], R& an) {
-  const R rho_ln = ln_mean(L.rho, Rt.rho);
-  const R inv = inv_ln_mean(L.rho * Rt.p, Rt.rho * L.p);
+  const R rho_ln = ln_mean_halves(L.s0, Rt.s0);
+  R vd = L.hvn * Rt.vn;
+#pragma unroll
+  for (int j = 0; j < D - 1; ++j) vd = fma(L.hvt[j], Rt.vt[j], vd);
+  // v_L.v_R / 2 + 1 / ((gamma-1) ln_mean(rho/p))
+  const R ee = add_inv_ln_mean(L.s1, Rt.s1, vd);
   an = L.hvn + Rt.hvn;
   const R f0 = rho_ln * an;
   f[0] = f0;
   f[1] = fma(f0, an, L.hp + Rt.hp);
 #pragma unroll
   for (int j = 0; j < D - 1; ++j) f[2 + j] = f0 * (L.hvt[j] + Rt.hvt[j]);
-  R vd = L.hvn * Rt.vn;
-#pragma unroll
-  for (int j = 0; j < D - 1; ++j) vd = fma(L.hvt[j], Rt.vt[j], vd);
-  const R ee = fma(L.p * Rt.pg, inv, vd);  // v_L.v_R / 2 + p_L p_R / ((gamma-1) ln_mean(rho p))
   f[D + 1] = fma(f0, ee, fma(L.hp, Rt.vn, Rt.hp * L.vn));
 }
 
@@ -108,11 +124,11 @@ template <int VF, typename R, int D>
 __device__ __forceinline__ void generic_nf(const LinePrim<R, D>& L, const LinePrim<R, D>& Rt,
                                            R gm1inv, R f[D + 2]) {
   Prim<R, D> a, b;
-  a.rho = L.rho;
-  a.p = L.p;
+  a.rho = L.s0;
+  a.p = L.s1;
   a.v[0] = L.vn;
-  b.rho = Rt.rho;
-  b.p = Rt.p;
+  b.rho = Rt.s0;
+  b.p = Rt.s1;
   b.v[0] = Rt.vn;
 #pragma unroll
   for (int j = 0; j < D - 1; ++j) {
@@ -123,7 +139,7 @@ __device__ __forceinline__ void generic_nf(const LinePrim<R, D>& L, const LinePr
 }
 
 template <int D, int N, typename R, int VF, int EPB>
-__device__ __forceinline__ void volume_direction(int dir, R (*sp)[4 + 2 * D][Shape<D, N>::P],
+__device__ __forceinline__ void volume_direction(int dir, R (*sp)[3 + 2 * D][Shape<D, N>::P],
                                                  R (*sa)[D + 3][Shape<D, N>::P], int el, int l,
                                                  const Tables<R>& tb, R gm1inv, R Pe,
                                                  const R* __restrict__ fs, int nelem, int e,
@@ -140,17 +156,16 @@ __device__ __forceinline__ void volume_direction(int dir, R (*sp)[4 + 2 * D][Sha
   for (int a = 0; a < NP; ++a) {
     node[a] = line_node_rt<D, N>(dir, l, a);
     const int nd = node[a];
-    q[a].rho = sp[el][0][nd];
-    q[a].p = sp[el][1][nd];
+    q[a].s0 = sp[el][0][nd];
+    q[a].s1 = sp[el][1][nd];
     q[a].hp = sp[el][2][nd];
-    q[a].pg = sp[el][3][nd];
-    q[a].vn = sp[el][4 + dir][nd];
-    q[a].hvn = sp[el][4 + D + dir][nd];
-    q[a].vt[0] = sp[el][4 + t1][nd];
-    q[a].hvt[0] = sp[el][4 + D + t1][nd];
+    q[a].vn = sp[el][3 + dir][nd];
+    q[a].hvn = sp[el][3 + D + dir][nd];
+    q[a].vt[0] = sp[el][3 + t1][nd];
+    q[a].hvt[0] = sp[el][3 + D + t1][nd];
     if (D == 3) {
-      q[a].vt[D - 2] = sp[el][4 + t2][nd];
-      q[a].hvt[D - 2] = sp[el][4 + D + t2][nd];
+      q[a].vt[D - 2] = sp[el][3 + t2][nd];
+      q[a].hvt[D - 2] = sp[el][3 + D + t2][nd];
     }
   }
   R acc[NP][NA];
@@ -224,7 +239,7 @@ __global__ void __launch_bounds__(EPB* Shape<D, N>::LINES)
   using S = Shape<D, N>;
   constexpr int P = S::P, NV = S::NV, LINES = S::LINES;
   constexpr bool F32 = sizeof(R) == 4;
-  constexpr int NC = 4 + 2 * D;  // rho, p, p/2 (or p'/2), p/(gamma-1), v[D], v[D]/2
+  constexpr int NC = 3 + 2 * D;  // s0, s1 (see LinePrim), p/2 (or p'/2), v[D], v[D]/2
   extern __shared__ __align__(16) unsigned char dg_smem[];
   R(*sp)[NC][P] = reinterpret_cast<R(*)[NC][P]>(dg_smem);
   R(*sa)[D + 3][P] = reinterpret_cast<R(*)[D + 3][P]>(dg_smem + sizeof(R) * EPB * NC * P);
@@ -291,14 +306,12 @@ __global__ void __launch_bounds__(EPB* Shape<D, N>::LINES)
 #pragma unroll
       for (int k = 0; k < D; ++k) v[k] = R(q.v[k]);
     }
-    sp[el][0][node] = rho;
-    sp[el][1][node] = p;
+    node_slots<VF, R>(rho, p, R(g.gm1), sp[el][0][node], sp[el][1][node]);
     sp[el][2][node] = hp;
-    sp[el][3][node] = p * gm1inv;
 #pragma unroll
     for (int k = 0; k < D; ++k) {
-      sp[el][4 + k][node] = v[k];
-      sp[el][4 + D + k][node] = R(0.5) * v[k];
+      sp[el][3 + k][node] = v[k];
+      sp[el][3 + D + k][node] = R(0.5) * v[k];
     }
 #pragma unroll
     for (int k = 0; k < D + 3; ++k) sa[el][k][node] = R(0);
@@ -524,7 +537,7 @@ template <int D, int N, typename R>
 struct Launch {
   static constexpr int LINES = Shape<D, N>::LINES;
   static constexpr int BY_THREADS = (128 / LINES) > 0 ? (128 / LINES) : 1;
-  static constexpr int PER_ELEM = (4 + 2 * D + D + 3) * Shape<D, N>::P * (int)sizeof(R);
+  static constexpr int PER_ELEM = (3 + 2 * D + D + 3) * Shape<D, N>::P * (int)sizeof(R);
   static constexpr int BY_SMEM = (98304 / PER_ELEM) > 0 ? (98304 / PER_ELEM) : 1;
   static constexpr int EPB = BY_THREADS < BY_SMEM ? BY_THREADS : BY_SMEM;
   static constexpr int SMEM = EPB * PER_ELEM;
@@ -532,7 +545,11 @@ struct Launch {
 
 template <typename K>
 cudaError_t allow_smem(K kernel, int bytes) {
-  if (bytes <= 48 * 1024) return cudaSuccess;
+  // the 48 KB default covers static and dynamic shared memory together
+  cudaFuncAttributes fa;
+  const cudaError_t e = cudaFuncGetAttributes(&fa, kernel);
+  if (e != cudaSuccess) return e;
+  if (bytes + (int)fa.sharedSizeBytes <= 48 * 1024) return cudaSuccess;
   return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
