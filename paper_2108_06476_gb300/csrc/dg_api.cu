@@ -196,15 +196,16 @@ __device__ __forceinline__ void speed_node(const double* c, int D, const Geom& g
                                            unsigned& bad, double) {
   double cc[5];
   for (int v = 0; v < D + 2; ++v) cc[v] = c[v];
+  double rr;
   if (D == 2) {
-    const dg::Prim<double, 2> q = dg::cons2prim<double, 2>(cc, g.gm1);
+    const dg::Prim<double, 2> q = dg::prim_rcp<2>(cc, g.gm1, rr);
     bad |= dg::prim_check(q);
-    const double cs = sqrt(g.gamma * q.p * (1.0 / q.rho));
+    const double cs = sqrt(g.gamma * q.p * rr);
     for (int k = 0; k < 2; ++k) lam[k] = fmax(lam[k], fabs(q.v[k]) + cs);
   } else {
-    const dg::Prim<double, 3> q = dg::cons2prim<double, 3>(cc, g.gm1);
+    const dg::Prim<double, 3> q = dg::prim_rcp<3>(cc, g.gm1, rr);
     bad |= dg::prim_check(q);
-    const double cs = sqrt(g.gamma * q.p * (1.0 / q.rho));
+    const double cs = sqrt(g.gamma * q.p * rr);
     for (int k = 0; k < 3; ++k) lam[k] = fmax(lam[k], fabs(q.v[k]) + cs);
   }
 }

@@ -144,6 +144,26 @@ __device__ __forceinline__ Prim<R, D> cons2prim(const R* c, R gm1) {
   return q;
 }
 
+// Primitive variables for the flux and time-step kernels: one reciprocal
+// rr = 1/rho (kept for the sound speed), v_k = m_k rr and
+// p = (gamma-1) (E - m.v/2) with fused products. The fluxes' rounding is
+// dominated by the pressure terms and the time step needs a few ulp, so the
+// quotients need no correction there.
+template <int D>
+__device__ __forceinline__ Prim<double, D> prim_rcp(const double* c, double gm1, double& rr) {
+  Prim<double, D> q;
+  q.rho = c[0];
+  rr = rcp(c[0]);
+  double mv = 0.0;
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    q.v[k] = c[1 + k] * rr;
+    mv = fma(c[1 + k], q.v[k], mv);
+  }
+  q.p = gm1 * fma(-0.5, mv, c[D + 1]);
+  return q;
+}
+
 template <typename R, int D>
 __device__ __forceinline__ unsigned prim_check(const Prim<R, D>& q) {
   unsigned bad = 0;
@@ -167,9 +187,14 @@ __device__ __forceinline__ unsigned prim_check(const Prim<R, D>& q) {
 //
 // Three ranges of f2, each lane choosing its own (no result depends on the
 // other lanes of its warp):
-//   short  a low-degree polynomial (FP64 f2 < 1e-2, FP32 f2 < 4e-2),
-//   long   a higher-degree one on [0, 0.25] (both precisions),
+//   short  a low-degree polynomial (FP64 kernels f2 < 1e-2, FP32 kernels
+//          f2 < 4e-2),
+//   long   a higher-degree one on [0, 0.25],
 //   far    log1p.
+// The FP32 kernels take t from their FP32 inputs but evaluate the
+// small-difference branch itself, f2 = t^2 and its polynomial, in FP64 (with
+// polynomials accurate to about a tenth of an FP32 ulp), rounding the
+// result once to FP32; their far branch is FP32.
 // Each polynomial is c_0 + f2 r(f2) with c_0 = Q(0) = 1 or S(0) = 2 exactly
 // and r interpolating (F - c_0)/f2 at the Chebyshev points of its interval
 // (gen_log_mean_poly.py writes them): degree 6 where the Taylor series
@@ -231,40 +256,40 @@ __device__ __forceinline__ double s_long(double f2) {
   r = fma(f2, r, 0.6666666666666666);
   return fma(f2, r, 2.0);
 }
-// degree 3 on f2 in [0, 4e-2]; measured relative error 2.4e-09
-__device__ __forceinline__ float q_short(float f2) {
-  float r = -0.04843324422836304f;
-  r = fmaf(f2, r, -0.08886054158210754f);
-  r = fmaf(f2, r, -0.33333340287208557f);
-  return fmaf(f2, r, 1.0f);
+// degree 3 on f2 in [0, 4e-2]; measured relative error 2.6e-09
+__device__ __forceinline__ double q_short32(double f2) {
+  double r = -0.048433244596931685;
+  r = fma(f2, r, -0.08886054076664304);
+  r = fma(f2, r, -0.3333333964306796);
+  return fma(f2, r, 1.0);
 }
-// degree 4 on f2 in [0, 4e-2]; measured relative error 4.8e-10
-__device__ __forceinline__ float s_short(float f2) {
-  float r = 0.23747344315052032f;
-  r = fmaf(f2, r, 0.2853274345397949f);
-  r = fmaf(f2, r, 0.4000031054019928f);
-  r = fmaf(f2, r, 0.6666666865348816f);
-  return fmaf(f2, r, 2.0f);
+// degree 4 on f2 in [0, 4e-2]; measured relative error 8.0e-11
+__device__ __forceinline__ double s_short32(double f2) {
+  double r = 0.23747344538291254;
+  r = fma(f2, r, 0.28532744768803825);
+  r = fma(f2, r, 0.4000031125070458);
+  r = fma(f2, r, 0.6666666627719066);
+  return fma(f2, r, 2.0);
 }
-// degree 6 on f2 in [0, 0.25]; measured relative error 4.5e-09
-__device__ __forceinline__ float q_long(float f2) {
-  float r = -0.03261576220393181f;
-  r = fmaf(f2, r, -0.0167341660708189f);
-  r = fmaf(f2, r, -0.030890846624970436f);
-  r = fmaf(f2, r, -0.046518709510564804f);
-  r = fmaf(f2, r, -0.08888980746269226f);
-  r = fmaf(f2, r, -0.3333333432674408f);
-  return fmaf(f2, r, 1.0f);
+// degree 6 on f2 in [0, 0.25]; measured relative error 1.1e-09
+__device__ __forceinline__ double q_long32(double f2) {
+  double r = -0.032615763305775085;
+  r = fma(f2, r, -0.016734165299453707);
+  r = fma(f2, r, -0.030890845926155427);
+  r = fma(f2, r, -0.04651870774759431);
+  r = fma(f2, r, -0.08888980573746398);
+  r = fma(f2, r, -0.33333333014048266);
+  return fma(f2, r, 1.0);
 }
-// degree 6 on f2 in [0, 0.25]; measured relative error 5.9e-09
-__device__ __forceinline__ float s_long(float f2) {
-  float r = 0.3150356113910675f;
-  r = fmaf(f2, r, 0.12986978888511658f);
-  r = fmaf(f2, r, 0.2293975055217743f);
-  r = fmaf(f2, r, 0.28527960181236267f);
-  r = fmaf(f2, r, 0.4000094532966614f);
-  r = fmaf(f2, r, 0.6666666269302368f);
-  return fmaf(f2, r, 2.0f);
+// degree 6 on f2 in [0, 0.25]; measured relative error 4.8e-09
+__device__ __forceinline__ double s_long32(double f2) {
+  double r = 0.31503560518305207;
+  r = fma(f2, r, 0.12986979135338692);
+  r = fma(f2, r, 0.22939750323237523);
+  r = fma(f2, r, 0.2852795970529254);
+  r = fma(f2, r, 0.400009466190787);
+  r = fma(f2, r, 0.6666666336958909);
+  return fma(f2, r, 2.0);
 }
 
 __device__ __forceinline__ double series_limit(double) { return 1.0e-2; }
@@ -276,43 +301,75 @@ static __device__ __noinline__ float ln_mean_far(float x, float y) { return (y -
 static __device__ __noinline__ double inv_ln_mean_far(double x, double y) { return log1p((y - x) / x) / (y - x); }
 static __device__ __noinline__ float inv_ln_mean_far(float x, float y) { return log1pf((y - x) / x) / (y - x); }
 
-// f2 >= 0, so the FP64 range tests compare IEEE bit patterns on the integer
-// pipe (the FP64 pipe is the bottleneck of the FP64 kernels)
+// f2 >= 0 (an FP64 value in both kernel precisions), so the range tests
+// compare IEEE bit patterns on the integer pipe (the FP64 pipe is the
+// bottleneck of the FP64 kernels)
 __device__ __forceinline__ bool in_short(double f2) {
   return __double_as_longlong(f2) < 0x3F847AE147AE147BLL;  // bits of 1e-2
+}
+__device__ __forceinline__ bool in_short32(double f2) {
+  return __double_as_longlong(f2) < 0x3FA47AE147AE147BLL;  // bits of 4e-2
 }
 __device__ __forceinline__ bool in_long(double f2) {
   return __double_as_longlong(f2) < 0x3FD0000000000000LL;  // bits of 0.25
 }
-__device__ __forceinline__ bool in_short(float f2) { return f2 < 4.0e-2f; }
-__device__ __forceinline__ bool in_long(float f2) { return f2 < 0.25f; }
+
+// f2 = t^2 in FP64 for a t of either precision, and the Q and S of its range
+// (second argument: the kernel precision)
+__device__ __forceinline__ double f2_of(double t) { return t * t; }
+__device__ __forceinline__ double f2_of(float t) {
+  const double td = t;
+  return td * td;
+}
+__device__ __forceinline__ double q_of(double f2, double) {
+  double q;
+  if (in_short(f2))
+    q = q_short(f2);
+  else
+    q = q_long(f2);
+  return q;
+}
+__device__ __forceinline__ double s_of(double f2, double) {
+  double S;
+  if (in_short(f2))
+    S = s_short(f2);
+  else
+    S = s_long(f2);
+  return S;
+}
+__device__ __forceinline__ float q_of(double f2, float) {
+  double q;
+  if (in_short32(f2))
+    q = q_short32(f2);
+  else
+    q = q_long32(f2);
+  return (float)q;
+}
+__device__ __forceinline__ float s_of(double f2, float) {
+  double S;
+  if (in_short32(f2))
+    S = s_short32(f2);
+  else
+    S = s_long32(f2);
+  return (float)S;
+}
 
 template <typename R>
 __device__ __forceinline__ R ln_mean(R x, R y) {
   const R s = x + y;
   const R t = (y - x) * rcp(s);
-  const R f2 = t * t;
+  const double f2 = f2_of(t);
   if (!in_long(f2)) return ln_mean_far(x, y);
-  R q;
-  if (in_short(f2))
-    q = q_short(f2);
-  else
-    q = q_long(f2);
-  return R(0.5) * s * q;
+  return R(0.5) * s * q_of(f2, R(0));
 }
 
 template <typename R>
 __device__ __forceinline__ R inv_ln_mean(R x, R y) {
   const R rs = rcp(x + y);
   const R t = (y - x) * rs;
-  const R f2 = t * t;
+  const double f2 = f2_of(t);
   if (!in_long(f2)) return inv_ln_mean_far(x, y);
-  R S;
-  if (in_short(f2))
-    S = s_short(f2);
-  else
-    S = s_long(f2);
-  return S * rs;
+  return s_of(f2, R(0)) * rs;
 }
 
 // ln_mean(2 hx, 2 hy) from the halves: every step is the one of
@@ -322,14 +379,9 @@ template <typename R>
 __device__ __forceinline__ R ln_mean_halves(R hx, R hy) {
   const R hs = hx + hy;
   const R t = (hy - hx) * rcp(hs);
-  const R f2 = t * t;
+  const double f2 = f2_of(t);
   if (!in_long(f2)) return R(2) * ln_mean_far(hx, hy);
-  R q;
-  if (in_short(f2))
-    q = q_short(f2);
-  else
-    q = q_long(f2);
-  return hs * q;
+  return hs * q_of(f2, R(0));
 }
 
 // a + 1/ln_mean(x, y), the last product fused into the addition
@@ -337,14 +389,9 @@ template <typename R>
 __device__ __forceinline__ R add_inv_ln_mean(R x, R y, R a) {
   const R rs = rcp(x + y);
   const R t = (y - x) * rs;
-  const R f2 = t * t;
+  const double f2 = f2_of(t);
   if (!in_long(f2)) return a + inv_ln_mean_far(x, y);
-  R S;
-  if (in_short(f2))
-    S = s_short(f2);
-  else
-    S = s_long(f2);
-  return fma(S, rs, a);
+  return fma(s_of(f2, R(0)), rs, a);
 }
 
 // ---- two-point volume fluxes f#(L, R) in direction DIR ----

@@ -88,14 +88,17 @@ __device__ __forceinline__ void load_trace(const double* __restrict__ u, long lo
     float rho, v[3], pp, p;
     prim_f32<3>(c, (float)gm1, Pe, ce, Er, rho, v, pp, p);
     T.rho = R(rho);
+    T.rr = R(rcp(rho));
     T.p = R(p);
     T.ps = R(pp + (Pe - Pown));
     T.vn = R(v[dir]);
     T.vt[0] = R(v[t1]);
     T.vt[1] = R(v[t2]);
   } else {
-    const Prim<double, 3> q = cons2prim<double, 3>(c, gm1);
+    double rr;
+    const Prim<double, 3> q = prim_rcp<3>(c, gm1, rr);
     T.rho = R(q.rho);
+    T.rr = R(rr);
     T.p = R(q.p);
     T.ps = T.p;
     T.vn = R(q.v[dir]);
@@ -157,7 +160,8 @@ __device__ void ens_process(const EnsArgs& a, const SimDesc& sd, int sim, int e0
       if (!(pf > 0.0f)) bad |= kErrP;
       if (!isfinite(rf) || !isfinite(pf)) bad |= kErrNaN;
     } else {
-      const Prim<double, 3> q = cons2prim<double, 3>(c, a.gm1);
+      double rr;
+      const Prim<double, 3> q = prim_rcp<3>(c, a.gm1, rr);
       bad |= prim_check(q);
       rho = R(q.rho);
       p = R(q.p);
@@ -311,9 +315,10 @@ __global__ void ensemble_speed_kernel(const SimDesc* __restrict__ sims,
         double c[5];
 #pragma unroll
         for (int v = 0; v < 5; ++v) c[v] = u[base + (long long)v * P + node];
-        const Prim<double, 3> q = cons2prim<double, 3>(c, gm1);
+        double rr;
+        const Prim<double, 3> q = prim_rcp<3>(c, gm1, rr);
         bad |= prim_check(q);
-        const double cs = sqrt(gamma * q.p * (1.0 / q.rho));
+        const double cs = sqrt(gamma * q.p * rr);
 #pragma unroll
         for (int k = 0; k < 3; ++k) lam[k] = fmax(lam[k], fabs(q.v[k]) + cs);
       }

@@ -298,7 +298,8 @@ __global__ void __launch_bounds__(EPB* Shape<D, N>::LINES)
       if (!(pf > 0.0f)) bad |= kErrP;
       if (!isfinite(rf) || !isfinite(pf)) bad |= kErrNaN;
     } else {
-      const Prim<double, D> q = cons2prim<double, D>(c, g.gm1);
+      double rr;
+      const Prim<double, D> q = prim_rcp<D>(c, g.gm1, rr);
       bad |= prim_check(q);
       rho = R(q.rho);
       p = R(q.p);
@@ -357,10 +358,10 @@ __global__ void __launch_bounds__(EPB* Shape<D, N>::LINES)
 // ---- surface ----
 // trace state for the surface flux, normal component first; ps is the
 // pressure in the additive normal-momentum term (p itself in FP64, p minus the
-// left element's P_e in FP32)
+// left element's P_e in FP32); rr = 1/rho
 template <typename R, int D>
 struct Trace {
-  R rho, p, ps, vn, vt[D - 1], mn, mt[D - 1], E;
+  R rho, rr, p, ps, vn, vt[D - 1], mn, mt[D - 1], E;
 };
 
 template <typename R, int D>
@@ -416,7 +417,7 @@ __device__ __forceinline__ void surface_nf(int sf, const Trace<R, D>& L, const T
   dq[0] = Rt.rho - L.rho;
   dq[1] = Rt.mn - L.mn;
   dq[D + 1] = dE;
-  const R c2l = gamma * L.p * rcp(L.rho), c2r = gamma * Rt.p * rcp(Rt.rho);
+  const R c2l = gamma * L.p * L.rr, c2r = gamma * Rt.p * Rt.rr;
   if (sf == kSLLF) {
     // max(c_L, c_R) = sqrt(max(c_L^2, c_R^2)) exactly (sqrt is monotone and
     // correctly rounded)
@@ -469,9 +470,11 @@ __device__ __forceinline__ void surface_body(const double* __restrict__ u, R* __
       prim_f32<D>(cl, (float)g.gm1, PeL, ceL, ErL, rL, vL, ppL, pL);
       prim_f32<D>(cr, (float)g.gm1, PeR, ceR, ErR, rR, vR, ppR, pR);
       L.rho = R(rL);
+      L.rr = R(rcp(rL));
       L.p = R(pL);
       L.ps = R(ppL);
       Rt.rho = R(rR);
+      Rt.rr = R(rcp(rR));
       Rt.p = R(pR);
       Rt.ps = R(ppR + (PeR - PeL));
       L.vn = R(vL[dir]);
@@ -484,8 +487,11 @@ __device__ __forceinline__ void surface_body(const double* __restrict__ u, R* __
       }
       dE = R((float)(cr[NV - 1] - cl[NV - 1]));
     } else {
-      const Prim<double, D> ql = cons2prim<double, D>(cl, g.gm1);
-      const Prim<double, D> qr = cons2prim<double, D>(cr, g.gm1);
+      double rrl, rrr;
+      const Prim<double, D> ql = prim_rcp<D>(cl, g.gm1, rrl);
+      const Prim<double, D> qr = prim_rcp<D>(cr, g.gm1, rrr);
+      L.rr = R(rrl);
+      Rt.rr = R(rrr);
       L.rho = R(ql.rho);
       L.p = R(ql.p);
       L.ps = L.p;

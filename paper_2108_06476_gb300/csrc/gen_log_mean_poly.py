@@ -28,10 +28,12 @@ POLYS = [
     ("s_short", "S", "double", "1e-2", 6),
     ("q_long", "Q", "double", "0.25", 13),
     ("s_long", "S", "double", "0.25", 14),
-    ("q_short", "Q", "float", "4e-2", 3),
-    ("s_short", "S", "float", "4e-2", 4),
-    ("q_long", "Q", "float", "0.25", 6),
-    ("s_long", "S", "float", "0.25", 6),
+    # the FP32 kernels' ranges, evaluated in FP64 (f2 = t^2 of an FP32 t),
+    # within about a tenth of the FP32 rounding of the result
+    ("q_short32", "Q", "double", "4e-2", 3),
+    ("s_short32", "S", "double", "4e-2", 4),
+    ("q_long32", "Q", "double", "0.25", 6),
+    ("s_long32", "S", "double", "0.25", 6),
 ]
 
 

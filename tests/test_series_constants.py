@@ -6,8 +6,8 @@ S(f2)/s with s = x + y, f2 = ((y - x)/s)^2, S(f2) = 2 atanh(t)/t =
 2 sum_k f2^k/(2k+1) and Q = 2/S (the logarithmic mean of Ranocha's flux,
 Sec. 3.2 of the paper; ln(y/x) = 2 atanh t). Here S is summed from its
 series in decimal arithmetic, the header's coefficients are taken exactly as
-the doubles (floats) they are, and the relative error over each polynomial's
-interval must stay within the bound its comment states."""
+the doubles they are, and the relative error over each polynomial's interval
+must stay within the bound its comment states."""
 import os
 import re
 import struct
@@ -69,8 +69,9 @@ def Q_ref(f2):
 
 POLYS = [("double", "q_short", Q_ref, 2e-19), ("double", "s_short", S_ref, 5e-19),
          ("double", "q_long", Q_ref, 2e-17), ("double", "s_long", S_ref, 1e-17),
-         ("float", "q_short", Q_ref, 3e-9), ("float", "s_short", S_ref, 1e-9),
-         ("float", "q_long", Q_ref, 5e-9), ("float", "s_long", S_ref, 6e-9)]
+         # the FP32 kernels' small-difference branch, evaluated in FP64
+         ("double", "q_short32", Q_ref, 3e-9), ("double", "s_short32", S_ref, 1e-10),
+         ("double", "q_long32", Q_ref, 2e-9), ("double", "s_long32", S_ref, 6e-9)]
 
 
 @pytest.mark.parametrize("real,name,ref,cap", POLYS, ids=[f"{p[0]}-{p[1]}" for p in POLYS])
@@ -99,14 +100,12 @@ def test_series_reference_is_the_logarithmic_mean():
 
 
 def test_range_limits(header):
-    for value, name in ((1e-2, "in_short"), (0.25, "in_long")):
+    for value, name in ((1e-2, "in_short"), (4e-2, "in_short32"), (0.25, "in_long")):
         body = _body(header, f"bool {name}(double f2)")
         bits = int(re.search(r"0x([0-9A-F]+)LL", body).group(1), 16)
         assert struct.unpack("<q", struct.pack("<d", value))[0] == bits
-    assert "f2 < 4.0e-2f" in _body(header, "bool in_short(float f2)")
-    assert "f2 < 0.25f" in _body(header, "bool in_long(float f2)")
     # every polynomial covers the range that selects it
-    for real, short, long_ in (("double", 1e-2, 0.25), ("float", 4e-2, 0.25)):
-        for name, lim in (("q_short", short), ("s_short", short), ("q_long", long_),
-                          ("s_long", long_)):
-            assert float(polynomial(header, real, name)[1]) >= lim
+    for suffix, short in (("", 1e-2), ("32", 4e-2)):
+        for name, lim in ((f"q_short{suffix}", short), (f"s_short{suffix}", short),
+                          (f"q_long{suffix}", 0.25), (f"s_long{suffix}", 0.25)):
+            assert float(polynomial(header, "double", name)[1]) >= lim
