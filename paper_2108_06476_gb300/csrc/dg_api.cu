@@ -161,8 +161,9 @@ __global__ void rk_stage_kernel(double* __restrict__ u, double* __restrict__ k,
   const long long n2 = n / 2;
   double2* u2 = reinterpret_cast<double2*>(u);
   double2* k2 = reinterpret_cast<double2*>(k);
+  // k <- a k + dt du as fma(a, k, dt du); a = 0 (the first stage) reads no k
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += stride) {
-    double2 kk = k2[i], uu = u2[i];
+    double2 kk, uu = u2[i];
     double d0, d1;
     if (sizeof(RD) == 8) {
       const double2 dd = reinterpret_cast<const double2*>(du)[i];
@@ -173,8 +174,13 @@ __global__ void rk_stage_kernel(double* __restrict__ u, double* __restrict__ k,
       d0 = dd.x;
       d1 = dd.y;
     }
-    kk.x = a * kk.x + dt * d0;
-    kk.y = a * kk.y + dt * d1;
+    kk.x = dt * d0;
+    kk.y = dt * d1;
+    if (a != 0.0) {
+      const double2 k0 = k2[i];
+      kk.x = fma(a, k0.x, kk.x);
+      kk.y = fma(a, k0.y, kk.y);
+    }
     uu.x = uu.x + b * kk.x;
     uu.y = uu.y + b * kk.y;
     k2[i] = kk;
@@ -182,7 +188,8 @@ __global__ void rk_stage_kernel(double* __restrict__ u, double* __restrict__ k,
   }
   if (blockIdx.x == 0 && threadIdx.x == 0 && (n & 1)) {
     const long long i = n - 1;
-    const double kk = a * k[i] + dt * (double)du[i];
+    double kk = dt * (double)du[i];
+    if (a != 0.0) kk = fma(a, k[i], kk);
     k[i] = kk;
     u[i] = u[i] + b * kk;
   }

@@ -273,7 +273,8 @@ __device__ void ens_process(const EnsArgs& a, const SimDesc& sd, int sim, int e0
       if (F32 && v == 4) val = fma(R(s_pe[ell]), sa[ell][5][node], val);
       const double du = sd.s * (double)val;
       const long long i = sd.off + ((long long)e * NV + v) * P + node;
-      const double kk = a.A * a.k[i] + dt * du;
+      double kk = dt * du;
+      if (a.A != 0.0) kk = fma(a.A, a.k[i], kk);  // the first stage reads no k
       a.k[i] = kk;
       a.uout[i] = a.uin[i] + a.B * kk;
     }

@@ -345,7 +345,9 @@ __global__ void __launch_bounds__(EPB* Shape<D, N>::LINES)
       if (F32 && VF == kVRanocha && v == D + 1) val = fma(Pself, sa[ell][D + 2][node], val);
       const long long i = ((long long)e * NV + v) * P + node;
       if (fz.k) {
-        const double kk = fz.a * fz.k[i] + dtv * (double)val;
+        // the first stage (A = 0) neither reads k nor lets stale k values in
+        double kk = dtv * (double)val;
+        if (fz.a != 0.0) kk = fma(fz.a, fz.k[i], kk);
         fz.k[i] = kk;
         u[i] = u[i] + fz.b * kk;
       } else {
