@@ -363,7 +363,7 @@ def run_ours(args, spec, world, rank, local):
     u.copy_(u0)
     # the dominant kernel of the timed region is the fused volume kernel
     # (flux differencing, lifting and the stage update); parts=6 launches it
-    # with zero stage coefficients (u unchanged)
+    # as in stages 2-5 (k read and written) with B = 0 (u unchanged)
     vol_ms = kernel_ms(mesh, u, du, 6)
     rhs_vol_ms = kernel_ms(mesh, u, du, 2)
     surf_ms = kernel_ms(mesh, u, du, 1)

@@ -102,8 +102,9 @@ int dg_rhs(dg_mesh *mesh, const double *u, void *du);
  * parts = 2 only the volume kernel with lifting (reads the face buffer of the
  * previous part-1 call on the same u), parts = 3 both (same as dg_rhs),
  * parts = 6 the volume kernel of the fused step (stage update in its
- * epilogue) with zero stage coefficients: k <- dt du with the last device
- * time step, u unchanged, du not written. Asynchronous. */
+ * epilogue) as in stages 2-5, with coefficients A = 1, B = 0:
+ * k <- k + dt du with the last device time step, u unchanged (read and
+ * written back), du not written. Asynchronous. */
 int dg_rhs_part(dg_mesh *mesh, const double *u, void *du, int parts);
 
 /* Vector-Jacobian product of the rhs: ubar = (d rhs/d u)(u)^T w, for

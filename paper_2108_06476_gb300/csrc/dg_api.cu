@@ -616,11 +616,12 @@ int dg_rhs_part(dg_mesh* m, const double* u, void* du, int parts) {
     return fail(DG_ERR_ARG, "dg_rhs_part: parts must be 1, 2, 3 or 6");
   dg::StageFuse fz;
   if (parts == 6) {
-    // the volume kernel with the stage update fused in, zero coefficients:
-    // k <- dt du, u unchanged (times the kernel of the fused step)
+    // the volume kernel with the stage update fused in, as in stages 2-5
+    // (A != 0 reads k): k <- k + dt du, u unchanged (times the kernel of the
+    // fused step)
     fz.k = m->k;
     fz.dt = m->dt_dev;
-    fz.a = 0.0;
+    fz.a = 1.0;
     fz.b = 0.0;
     fz.pref = nullptr;
     parts = 2;

@@ -221,7 +221,9 @@ class Mesh:
 
     def rhs_part(self, u, du, parts):
         """Launch only the surface kernel (parts=1), only the volume kernel
-        (parts=2) or both (3); used to time the kernels separately."""
+        (parts=2), both (3), or the volume kernel of the fused step with stage
+        coefficients A = 1, B = 0 (6: k <- k + dt du, u unchanged); used to
+        time the kernels separately."""
         self._sync_stream()
         _check(load().dg_rhs_part(self._h, _ptr(u), _ptr(du), int(parts)), "dg_rhs_part")
 

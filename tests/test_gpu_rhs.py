@@ -289,6 +289,27 @@ def test_graph_step_equals_fused_step(orc):
     assert torch.equal(a, b)
 
 
+def test_rhs_part_fused_volume_leaves_state_unchanged(orc):
+    # parts=6 (the fused step's volume kernel with B = 0) must not move u and
+    # must leave the face-buffer/volume pair consistent with a plain rhs
+    d, N, n = 3, 3, (4, 3, 2)
+    xi, _ = orc.lgl(N)
+    u0 = W.noisy_density_wave(d, N, n, W.box(d), xi, seed=4)
+    m = Mesh(d, N, n)
+    u = torch.from_numpy(u0.copy()).cuda()
+    m.step_cfl(u, cfl=0.5)  # sets the device time step
+    before = u.clone()
+    du = m.empty_rhs()
+    m.rhs_part(u, du, 1)
+    for _ in range(3):
+        m.rhs_part(u, du, 6)
+    torch.cuda.synchronize()
+    assert torch.equal(u, before)
+    assert m.check() == 0
+    ref = oracle_rhs(orc, d, N, n, W.box(d), before.cpu().numpy())
+    assert rel_l2(m.rhs(u).cpu().numpy(), ref) <= TOL64
+
+
 def test_fused_20_steps_2d_against_oracle(orc):
     # 2D 16^2 N=3 density wave, 20 steps at CFL 0.5 with the time step taken
     # from each side's own state every step
