@@ -74,9 +74,9 @@ def source_sha():
     return h.hexdigest()[:12]
 
 
-def ncu_traffic(key):
-    """DRAM bytes per node of a kernel from a committed ncu summary, or None
-    when the kernels changed since that capture."""
+def ncu_record(key, field):
+    """A per-node figure of a kernel from a committed ncu summary (DRAM bytes,
+    counted flops), or None when the kernels changed since that capture."""
     path = os.path.join(ROOT, "profiles", "dram_traffic.json")
     try:
         with open(path) as fh:
@@ -85,7 +85,11 @@ def ncu_traffic(key):
         return None
     if not rec or rec.get("src_sha") != source_sha():
         return None
-    return rec.get("bytes_per_node")
+    return rec.get(field)
+
+
+def ncu_traffic(key):
+    return ncu_record(key, "bytes_per_node")
 
 
 class ClockSampler:
@@ -370,6 +374,14 @@ def run_ours(args, spec, world, rank, local):
     flops_node = volume_flops_per_node(d, N)
     achieved = flops_node * M / (vol_ms / 1e3) / 1e12
     traffic = ncu_traffic(f"fp64_volume_{d}d_n{N}")
+    # the hardware's view: FP64 flops the kernel executes per node (ncu
+    # DADD + DMUL + 2 DFMA thread instructions), at the live kernel time
+    counted_node = ncu_record(f"fp64_volume_{d}d_n{N}", "fp64_flops_executed_per_node")
+    counted = None
+    if counted_node is not None:
+        c_ach = counted_node * M / (vol_ms / 1e3) / 1e12
+        counted = {"flops_per_node": counted_node, "achieved": c_ach,
+                   "frac": c_ach / FP64_PEAK_TFLOPS}
 
     # ---- FP32 kernels with FP64 state and RK accumulation ----
     fp32 = None
@@ -438,7 +450,8 @@ def run_ours(args, spec, world, rank, local):
                      "kernel": "volume_kernel (FP64, stage update fused)",
                      "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz "
                                     "(nominal 1.25 TFLOP/s FP64)",
-                     "flops_per_node": flops_node, "kernel_ms": vol_ms},
+                     "flops_per_node": flops_node, "kernel_ms": vol_ms,
+                     "counted": counted},
         "kernels_ms": {"volume_fused_stage": vol_ms, "volume_rhs_only": rhs_vol_ms,
                        "surface": surf_ms},
         "fp32": fp32,
