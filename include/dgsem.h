@@ -141,6 +141,20 @@ int dg_step_cfl(dg_mesh *mesh, double *u, double cfl);
  * later calls with the same arguments. Asynchronous. */
 int dg_step_graph(dg_mesh *mesh, double *u, double cfl);
 
+/* n_steps >= 1 steps of dg_step_cfl on a state held in HOST memory: u_host
+ * (n_values doubles, layout as dg_rhs) holds the state on entry and the
+ * state after the steps on return. The library keeps a device copy
+ * (n_values doubles, allocated on first use). When u_host is pinned and
+ * mapped (cudaHostAlloc, or host memory registered with cudaHostRegister)
+ * the first step's wave-speed pass reads it directly and fills the device
+ * copy, and the last step's final stage stores the new state straight into
+ * it, so the host-device traffic overlaps the kernels; other host memory is
+ * copied in and out with cudaMemcpyAsync. Synchronous (returns once u_host
+ * is written). A nonphysical state is reported by dg_mesh_check, as for
+ * dg_step_cfl. Errors: DG_ERR_ARG (null pointer, cfl <= 0, n_steps < 1,
+ * device memory), DG_ERR_OOM, DG_ERR_CUDA. */
+int dg_step_cfl_host(dg_mesh *mesh, double *u_host, double cfl, int n_steps);
+
 /* The time step used by the last dg_step_cfl / dg_step_graph (synchronises). */
 int dg_last_dt(dg_mesh *mesh, double *dt_out);
 

@@ -61,6 +61,7 @@ struct dg_mesh {
   cudaGraphExec_t graph;
   const double* graph_u;
   double graph_cfl;
+  double* u_dev;       // device copy of a host state (dg_step_cfl_host), first use
 };
 
 namespace {
@@ -233,9 +234,12 @@ __device__ __forceinline__ void speed_node(const double* c, int D, const Geom& g
   for (int k = 0; k < D; ++k) lam[k] = fmax(lam[k], (double)(fabsf(v[k]) + cs));
 }
 
+// copy_to (optional) receives a copy of u: the host-state step reads a
+// mapped host buffer here once and continues on the device copy.
 template <int D, typename R>
 __global__ void speed_kernel(const double* __restrict__ u, Geom g, int P, double s0, double s1,
-                             double s2, unsigned long long* out, unsigned* err) {
+                             double s2, unsigned long long* out, unsigned* err,
+                             double* __restrict__ copy_to) {
   constexpr int NV = D + 2;
   const int lane = threadIdx.x & 31;
   const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -248,6 +252,10 @@ __global__ void speed_kernel(const double* __restrict__ u, Geom g, int P, double
       double c[NV];
 #pragma unroll
       for (int v = 0; v < NV; ++v) c[v] = u[(e * NV + v) * P + node];
+      if (copy_to) {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) copy_to[(e * NV + v) * P + node] = c[v];
+      }
       speed_node(c, D, g, lam, bad, R(0));
     }
 #pragma unroll
@@ -381,8 +389,9 @@ bool valid_mesh(const dg_mesh* m) { return m != nullptr && m->k != nullptr; }
 
 int grid_for(long long work, int threads);
 
-// wave-speed reduction into m->speed (FP32 arithmetic on FP32 meshes)
-int launch_speed(dg_mesh* m, const double* u) {
+// wave-speed reduction into m->speed (FP32 arithmetic on FP32 meshes);
+// copy_to (optional): device buffer that receives a copy of u
+int launch_speed(dg_mesh* m, const double* u, double* copy_to = nullptr) {
   const int threads = 256;
   const int grid = grid_for(m->nelem * 32, threads);
   const double s0 = 2.0 / m->h[0], s1 = 2.0 / m->h[1], s2 = 2.0 / m->h[2];
@@ -390,17 +399,17 @@ int launch_speed(dg_mesh* m, const double* u) {
   if (m->d == 2) {
     if (f32)
       speed_kernel<2, float><<<grid, threads, 0, m->stream>>>(u, m->geom, (int)m->P, s0, s1, s2,
-                                                              m->speed, m->err);
+                                                              m->speed, m->err, copy_to);
     else
       speed_kernel<2, double><<<grid, threads, 0, m->stream>>>(u, m->geom, (int)m->P, s0, s1, s2,
-                                                               m->speed, m->err);
+                                                               m->speed, m->err, copy_to);
   } else {
     if (f32)
       speed_kernel<3, float><<<grid, threads, 0, m->stream>>>(u, m->geom, (int)m->P, s0, s1, s2,
-                                                              m->speed, m->err);
+                                                              m->speed, m->err, copy_to);
     else
       speed_kernel<3, double><<<grid, threads, 0, m->stream>>>(u, m->geom, (int)m->P, s0, s1, s2,
-                                                               m->speed, m->err);
+                                                               m->speed, m->err, copy_to);
   }
   DG_CUDA(cudaGetLastError(), "speed kernel launch");
   return DG_OK;
@@ -589,6 +598,7 @@ int dg_mesh_destroy(dg_mesh* m) {
   cudaFree(m->fbar);
   cudaFree(m->pref);
   cudaFree(m->dt_dev);
+  cudaFree(m->u_dev);
   if (m->graph) cudaGraphExecDestroy(m->graph);
   delete m;
   return DG_OK;
@@ -693,8 +703,12 @@ namespace {
 
 // dt on the device, then five stages with the update fused into the volume
 // kernel (no du buffer, no host synchronisation)
-int enqueue_fused_step(dg_mesh* m, double* u, double cfl) {
-  int rc = launch_speed(m, u);
+// One CFL step on the device state u. src (optional): where the step's
+// input state is read by the wave-speed pass, which then copies it into u;
+// out (optional): where the last stage stores the new state instead of u.
+int enqueue_fused_step(dg_mesh* m, double* u, double cfl, const double* src = nullptr,
+                       double* out = nullptr) {
+  int rc = src ? launch_speed(m, src, u) : launch_speed(m, u);
   if (rc) return rc;
   dt_kernel<<<1, 1, 0, m->stream>>>(m->speed, m->N, cfl, m->dt_dev, m->err);
   DG_CUDA(cudaGetLastError(), "dt kernel launch");
@@ -704,6 +718,7 @@ int enqueue_fused_step(dg_mesh* m, double* u, double cfl) {
     fz.dt = m->dt_dev;
     fz.a = kRkA[s];
     fz.b = kRkB[s];
+    if (s == 4) fz.u_out = out;
     cudaError_t e;
     if (m->opt.precision == DG_FP64) {
       e = (m->d == 2 ? dg::rhs_launch_double_2 : dg::rhs_launch_double_3)(
@@ -754,6 +769,36 @@ int dg_step_graph(dg_mesh* m, double* u, double cfl) {
     m->graph_cfl = cfl;
   }
   DG_CUDA(cudaGraphLaunch(m->graph, m->stream), "dg_step_graph: launch");
+  return DG_OK;
+}
+
+int dg_step_cfl_host(dg_mesh* m, double* u_host, double cfl, int n_steps) {
+  if (!valid_mesh(m) || !u_host || !(cfl > 0.0) || n_steps < 1)
+    return fail(DG_ERR_ARG, "dg_step_cfl_host: bad argument");
+  cudaPointerAttributes pa;
+  DG_CUDA(cudaPointerGetAttributes(&pa, u_host), "dg_step_cfl_host: pointer attributes");
+  if (pa.type == cudaMemoryTypeDevice)
+    return fail(DG_ERR_ARG, "dg_step_cfl_host: u_host is device memory (use dg_step_cfl)");
+  if (!m->u_dev)
+    DG_CUDA(cudaMalloc(&m->u_dev, sizeof(double) * m->nvalues), "dg_step_cfl_host: alloc");
+  const size_t bytes = sizeof(double) * m->nvalues;
+  // pinned and mapped: the first wave-speed pass reads the host buffer and
+  // fills the device copy, the last stage stores the new state into it
+  const bool mapped = pa.type == cudaMemoryTypeHost && pa.devicePointer != nullptr;
+  double* hdev = mapped ? static_cast<double*>(pa.devicePointer) : nullptr;
+  if (!mapped)
+    DG_CUDA(cudaMemcpyAsync(m->u_dev, u_host, bytes, cudaMemcpyHostToDevice, m->stream),
+            "dg_step_cfl_host: copy in");
+  for (int i = 0; i < n_steps; ++i) {
+    const double* src = (mapped && i == 0) ? hdev : nullptr;
+    double* out = (mapped && i == n_steps - 1) ? hdev : nullptr;
+    const int rc = enqueue_fused_step(m, m->u_dev, cfl, src, out);
+    if (rc) return rc;
+  }
+  if (!mapped)
+    DG_CUDA(cudaMemcpyAsync(u_host, m->u_dev, bytes, cudaMemcpyDeviceToHost, m->stream),
+            "dg_step_cfl_host: copy out");
+  DG_CUDA(cudaStreamSynchronize(m->stream), "dg_step_cfl_host: sync");
   return DG_OK;
 }
 

@@ -51,6 +51,7 @@ struct StageFuse {
   const double* dt = nullptr;
   double a = 0.0, b = 0.0;
   float* pref = nullptr;
+  double* u_out = nullptr;  // where u + b k goes (nullptr: u, in place)
 };
 
 template <int D, int N>

@@ -334,6 +334,7 @@ __global__ void __launch_bounds__(EPB* Shape<D, N>::LINES)
   // epilogue: lifting of the surface fluxes, then the store (or the fused
   // stage update)
   const double dtv = fz.k ? *fz.dt : 0.0;
+  double* const uo = fz.u_out ? fz.u_out : u;
   for (int t = threadIdx.x; t < EPB * P; t += blockDim.x) {
     const int ell = t / P, node = t % P;
     const int e = e0 + ell;
@@ -349,7 +350,7 @@ __global__ void __launch_bounds__(EPB* Shape<D, N>::LINES)
         double kk = dtv * (double)val;
         if (fz.a != 0.0) kk = fma(fz.a, fz.k[i], kk);
         fz.k[i] = kk;
-        u[i] = u[i] + fz.b * kk;
+        uo[i] = u[i] + fz.b * kk;
       } else {
         du[i] = val;
       }

@@ -6,6 +6,7 @@ rounding order (pair halving with the symmetric flux, FMA contraction, scaled
 tables), so the error is a few ulps of the flux-sized terms, amplified by the
 cancellation in sum_m Dt_im f#(u_i,u_m) (terms ~ (2/h)|Dt||f|, result ~|du|).
 """
+import ctypes
 import numpy as np
 import pytest
 
@@ -308,6 +309,41 @@ def test_rhs_part_fused_volume_leaves_state_unchanged(orc):
     assert m.check() == 0
     ref = oracle_rhs(orc, d, N, n, W.box(d), before.cpu().numpy())
     assert rel_l2(m.rhs(u).cpu().numpy(), ref) <= TOL64
+
+
+@pytest.mark.parametrize("memory", ["pinned", "pageable"])
+@pytest.mark.parametrize("n_steps", [1, 3])
+def test_host_state_step_equals_device_step(orc, memory, n_steps):
+    # dg_step_cfl_host: pinned buffers are read by the wave-speed pass and
+    # written by the last stage, pageable ones copied; both must give the
+    # device step's state bitwise
+    d, N, n = 3, 3, (4, 3, 5)
+    xi, _ = orc.lgl(N)
+    u0 = W.noisy_density_wave(d, N, n, W.box(d), xi, seed=13)
+    m1, m2 = Mesh(d, N, n), Mesh(d, N, n)
+    ud = torch.from_numpy(u0.copy()).cuda()
+    for _ in range(n_steps):
+        m1.step_cfl(ud, cfl=0.5)
+    if memory == "pinned":
+        uh = torch.from_numpy(u0.copy()).pin_memory()
+        m2.step_cfl_host(uh, cfl=0.5, n_steps=n_steps)
+        got = uh.numpy()
+    else:
+        got = u0.copy()
+        m2.step_cfl_host(got, cfl=0.5, n_steps=n_steps)
+    assert np.array_equal(got, ud.cpu().numpy())
+    assert m2.last_dt() == m1.last_dt()
+    assert m2.check() == 0
+
+
+def test_host_state_step_rejects_device_memory():
+    from paper_2108_06476_gb300 import load
+    m = Mesh(2, 2, (2, 2))
+    u = torch.zeros(m.n_values, dtype=torch.float64, device="cuda")
+    rc = load().dg_step_cfl_host(m._h, ctypes.c_void_p(u.data_ptr()), 0.5, 1)
+    assert rc == -1
+    rc = load().dg_step_cfl_host(m._h, ctypes.c_void_p(u.data_ptr()), 0.5, 0)
+    assert rc == -1
 
 
 def test_fused_20_steps_2d_against_oracle(orc):
