@@ -364,6 +364,15 @@ def run_ours(args, spec, world, rank, local):
         torch.cuda.synchronize()
         return a.elapsed_time(b) / reps
 
+    # rhs-only rate: 50 back-to-back dg_rhs calls (surface + volume kernels,
+    # du written), the paper's PID without the stage updates
+    u.copy_(u0)
+    rhs_reps = 50
+    mesh.rhs(u, du)
+    ms_rhs = timed(lambda: [mesh.rhs(u, du) for _ in range(rhs_reps)])
+    rhs_only = {"value": M * rhs_reps * world / (ms_rhs / 1e3), "unit": UNIT,
+                "ms_per_rhs": ms_rhs / rhs_reps, "calls": rhs_reps}
+
     u.copy_(u0)
     # the dominant kernel of the timed region is the fused volume kernel
     # (flux differencing, lifting and the stage update); parts=6 launches it
@@ -454,6 +463,7 @@ def run_ours(args, spec, world, rank, local):
                      "counted": counted},
         "kernels_ms": {"volume_fused_stage": vol_ms, "volume_rhs_only": rhs_vol_ms,
                        "surface": surf_ms},
+        "rhs_only": rhs_only,
         "fp32": fp32,
         "ensemble": ensemble,
         "e2e": e2e,

@@ -137,6 +137,12 @@ int dg_step(dg_mesh *mesh, double *u, void *du, double dt);
  * the volume kernel (no du buffer, no host synchronisation). Asynchronous. */
 int dg_step_cfl(dg_mesh *mesh, double *u, double cfl);
 
+/* One full LSRK step with a given time step dt > 0 (Sec. 3.1 Carpenter-
+ * Kennedy stages): the five stages of dg_step_cfl, the update fused into the
+ * volume kernel, without the CFL reduction; dg_last_dt then returns dt.
+ * Asynchronous. Errors: DG_ERR_ARG (null u, dt <= 0), DG_ERR_CUDA. */
+int dg_step_dt(dg_mesh *mesh, double *u, double dt);
+
 /* dg_step_cfl recorded once as a CUDA graph for (u, cfl) and replayed on
  * later calls with the same arguments. Asynchronous. */
 int dg_step_graph(dg_mesh *mesh, double *u, double cfl);

@@ -18,6 +18,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "dgsem_oracle.c")
+_SRC_CURVED = os.path.join(_HERE, "dgsem_curved.c")
 _SO = os.path.join(_HERE, "liboracle.so")
 _lib = None
 
@@ -29,8 +30,10 @@ _llp = ctypes.POINTER(ctypes.c_longlong)
 def build(force: bool = False) -> str:
     """Compile the oracle with gcc (-O2 -ffp-contract=off, OpenMP): with
     double, with double complex (complex-step JVP) and with long double (the
-    extended-precision evaluation used to measure FP64 rounding errors)."""
-    if not force and os.path.exists(_SO) and os.path.getmtime(_SO) >= os.path.getmtime(_SRC):
+    extended-precision evaluation used to measure FP64 rounding errors), plus
+    the curvilinear-mesh operator (double)."""
+    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_SRC_CURVED))
+    if not force and os.path.exists(_SO) and os.path.getmtime(_SO) >= newest:
         return _SO
     bdir = os.path.join(_HERE, "_build")
     os.makedirs(bdir, exist_ok=True)
@@ -38,11 +41,13 @@ def build(force: bool = False) -> str:
     o1 = os.path.join(bdir, "or_real.o")
     o2 = os.path.join(bdir, "or_cstep.o")
     o3 = os.path.join(bdir, "or_ld.o")
+    o4 = os.path.join(bdir, "or_curved.o")
     tmp = _SO + f".tmp{os.getpid()}"
     subprocess.check_call(["gcc", *flags, "-c", _SRC, "-o", o1])
     subprocess.check_call(["gcc", *flags, "-DOR_CSTEP", "-c", _SRC, "-o", o2])
     subprocess.check_call(["gcc", *flags, "-DOR_LONGDOUBLE", "-c", _SRC, "-o", o3])
-    subprocess.check_call(["gcc", "-shared", "-fopenmp", o1, o2, o3, "-o", tmp, "-lm"])
+    subprocess.check_call(["gcc", *flags, "-c", _SRC_CURVED, "-o", o4])
+    subprocess.check_call(["gcc", "-shared", "-fopenmp", o1, o2, o3, o4, "-o", tmp, "-lm"])
     os.replace(tmp, _SO)
     return _SO
 
@@ -71,6 +76,16 @@ def _declare(L):
     L.or_max_dt.restype = ctypes.c_double
     L.or_integrals.argtypes = [ctypes.c_int, ctypes.c_int, _ip, _dp, ctypes.c_double, _dp,
                                _dp]
+    if hasattr(L, "or_curved_rhs"):  # variant builds of dgsem_oracle.c alone lack these
+        L.or_curved_geometry.argtypes = [ctypes.c_int, _ip, ctypes.c_double, _dp, _dp, _dp]
+        L.or_curved_rhs.argtypes = [ctypes.c_int, _ip, ctypes.c_double, ctypes.c_int,
+                                    ctypes.c_int, ctypes.c_int, ctypes.c_double, _dp, _dp, _dp,
+                                    _dp, _dp, _llp, ctypes.c_longlong, ctypes.c_int]
+        L.or_curved_max_dt.argtypes = [ctypes.c_int, _ip, ctypes.c_double, ctypes.c_double,
+                                       _dp, _dp, _dp]
+        L.or_curved_max_dt.restype = ctypes.c_double
+        L.or_manufactured_state.argtypes = [ctypes.c_double, _dp, _dp]
+        L.or_manufactured_source.argtypes = [ctypes.c_double, ctypes.c_double, _dp, _dp]
     return L
 
 
@@ -271,3 +286,77 @@ def lsrk_step(d, N, n, dom, u, dt, gamma=1.4, vflux=RANOCHA, sflux=S_LLF, nthrea
         du = rhs(d, N, n, dom, u, gamma, vflux, sflux, nthreads=nthreads)
         rk_stage(u, k, du, A[s], B[s], dt)
     return u
+
+
+# ---- curvilinear (warped) periodic box, 3D Euler (dgsem_curved.c) ----
+
+class CurvedGeometry:
+    """Node coordinates X[e][3][P], metric terms Ja[e][r][n][P] = (J a^r)_n
+    and Jacobians J[e][P] of the warped periodic box [-1,1]^3."""
+
+    def __init__(self, N, n, warp=0.15):
+        self.N, self.n, self.warp = N, tuple(int(x) for x in n), float(warp)
+        ne = int(np.prod(self.n))
+        P = (N + 1) ** 3
+        self.X = np.zeros((ne, 3, P))
+        self.Ja = np.zeros((ne, 3, 3, P))
+        self.J = np.zeros((ne, P))
+        rc = lib().or_curved_geometry(N, _n3(self.n), self.warp, _d(self.X), _d(self.Ja),
+                                      _d(self.J))
+        if rc != 0:
+            raise ValueError(f"or_curved_geometry failed ({rc})")
+
+
+def _n3(n):
+    return (ctypes.c_int * 3)(*[int(x) for x in n])
+
+
+def curved_rhs(geom, u, vflux=RANOCHA, sflux=S_LLF, source=False, t=0.0, gamma=1.4,
+               elems=None, out=None, nthreads=0):
+    """du on the curved mesh (plus the manufactured source at time t)."""
+    u = _f64(u)
+    du = np.zeros_like(u) if out is None else out
+    if elems is None:
+        ep, ne = None, 0
+    else:
+        elems = np.ascontiguousarray(elems, dtype=np.int64)
+        ep, ne = elems.ctypes.data_as(_llp), len(elems)
+    rc = lib().or_curved_rhs(geom.N, _n3(geom.n), gamma, vflux, sflux, int(bool(source)),
+                             float(t), _d(geom.Ja), _d(geom.J), _d(geom.X), _d(u), _d(du), ep,
+                             ne, nthreads)
+    if rc != 0:
+        raise ValueError("bad curved rhs arguments")
+    return du
+
+
+def curved_max_dt(geom, u, cfl=0.5, gamma=1.4):
+    return lib().or_curved_max_dt(geom.N, _n3(geom.n), gamma, cfl, _d(geom.Ja), _d(geom.J),
+                                  _d(_f64(u)))
+
+
+def curved_lsrk_step(geom, u, dt, t=0.0, vflux=RANOCHA, sflux=S_LLF, source=False, gamma=1.4,
+                     nthreads=0):
+    """One Carpenter-Kennedy step on a copy of u; stage s evaluates the source
+    at t + c_s dt."""
+    A, B, C = lsrk_coefficients()
+    u = _f64(u).copy()
+    k = np.zeros_like(u)
+    for s in range(5):
+        du = curved_rhs(geom, u, vflux, sflux, source, t + C[s] * dt, gamma, nthreads=nthreads)
+        rk_stage(u, k, du, A[s], B[s], dt)
+    return u
+
+
+def manufactured_state_at(t, X):
+    """The manufactured state at one point X (3,)."""
+    x = np.ascontiguousarray(X, dtype=np.float64)
+    u = np.zeros(5)
+    lib().or_manufactured_state(float(t), _d(x), _d(u))
+    return u
+
+
+def manufactured_source_at(t, X, gamma=1.4):
+    x = np.ascontiguousarray(X, dtype=np.float64)
+    S = np.zeros(5)
+    lib().or_manufactured_source(float(gamma), float(t), _d(x), _d(S))
+    return S

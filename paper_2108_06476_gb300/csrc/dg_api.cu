@@ -703,15 +703,11 @@ namespace {
 
 // dt on the device, then five stages with the update fused into the volume
 // kernel (no du buffer, no host synchronisation)
-// One CFL step on the device state u. src (optional): where the step's
-// input state is read by the wave-speed pass, which then copies it into u;
-// out (optional): where the last stage stores the new state instead of u.
-int enqueue_fused_step(dg_mesh* m, double* u, double cfl, const double* src = nullptr,
-                       double* out = nullptr) {
-  int rc = src ? launch_speed(m, src, u) : launch_speed(m, u);
-  if (rc) return rc;
-  dt_kernel<<<1, 1, 0, m->stream>>>(m->speed, m->N, cfl, m->dt_dev, m->err);
-  DG_CUDA(cudaGetLastError(), "dt kernel launch");
+__global__ void set_dt_kernel(double* dt_dev, double dt) { *dt_dev = dt; }
+
+// The five fused stages on the device state u with the time step in
+// m->dt_dev; out (optional): where the last stage stores the new state.
+int enqueue_fused_stages(dg_mesh* m, double* u, double* out) {
   for (int s = 0; s < 5; ++s) {
     dg::StageFuse fz;
     fz.k = m->k;
@@ -734,7 +730,26 @@ int enqueue_fused_step(dg_mesh* m, double* u, double cfl, const double* src = nu
   }
   return DG_OK;
 }
+
+// One CFL step on the device state u. src (optional): where the step's
+// input state is read by the wave-speed pass, which then copies it into u;
+// out (optional): where the last stage stores the new state instead of u.
+int enqueue_fused_step(dg_mesh* m, double* u, double cfl, const double* src = nullptr,
+                       double* out = nullptr) {
+  int rc = src ? launch_speed(m, src, u) : launch_speed(m, u);
+  if (rc) return rc;
+  dt_kernel<<<1, 1, 0, m->stream>>>(m->speed, m->N, cfl, m->dt_dev, m->err);
+  DG_CUDA(cudaGetLastError(), "dt kernel launch");
+  return enqueue_fused_stages(m, u, out);
+}
 }  // namespace
+
+int dg_step_dt(dg_mesh* m, double* u, double dt) {
+  if (!valid_mesh(m) || !u || !(dt > 0.0)) return fail(DG_ERR_ARG, "dg_step_dt: bad argument");
+  set_dt_kernel<<<1, 1, 0, m->stream>>>(m->dt_dev, dt);
+  DG_CUDA(cudaGetLastError(), "dg_step_dt: launch");
+  return enqueue_fused_stages(m, u, nullptr);
+}
 
 int dg_step_cfl(dg_mesh* m, double* u, double cfl) {
   if (!valid_mesh(m) || !u || !(cfl > 0.0)) return fail(DG_ERR_ARG, "dg_step_cfl: bad argument");

@@ -29,7 +29,7 @@ RK_B = (1432997174477.0 / 9575080441755.0, 5161836677717.0 / 13612068292357.0,
 
 EXPORTS = ("dg_mesh_create", "dg_mesh_destroy", "dg_mesh_info", "dg_mesh_set_stream",
            "dg_lgl_nodes", "dg_rhs", "dg_rhs_part", "dg_rhs_vjp", "dg_rk_stage", "dg_rk_reset", "dg_step", "dg_step_cfl", "dg_step_graph",
-           "dg_step_cfl_host", "dg_last_dt", "dg_max_dt",
+           "dg_step_dt", "dg_step_cfl_host", "dg_last_dt", "dg_max_dt",
            "dg_integrals", "dg_mesh_check", "dg_last_error", "dg_rhs_noalloc",
            "dg_ensemble_create", "dg_ensemble_destroy", "dg_ensemble_info",
            "dg_ensemble_set_dt", "dg_ensemble_get_dt", "dg_ensemble_compute_dt",
@@ -75,6 +75,7 @@ def load(path: str = SO_PATH):
     L.dg_step_cfl.argtypes = [vp, vp, ctypes.c_double]
     L.dg_step_graph.argtypes = [vp, vp, ctypes.c_double]
     L.dg_step_cfl_host.argtypes = [vp, vp, ctypes.c_double, ctypes.c_int]
+    L.dg_step_dt.argtypes = [vp, vp, ctypes.c_double]
     L.dg_last_dt.argtypes = [vp, dp]
     L.dg_max_dt.argtypes = [vp, vp, ctypes.c_double, dp]
     L.dg_integrals.argtypes = [vp, vp, dp]
@@ -254,6 +255,13 @@ class Mesh:
         self._sync_stream()
         fn = load().dg_step_graph if graph else load().dg_step_cfl
         _check(fn(self._h, _ptr(u), float(cfl)), "dg_step_cfl")
+
+    def step_dt(self, u, dt):
+        """One LSRK step with the given time step, the stage updates fused
+        into the volume kernel."""
+        self._check_state(u)
+        self._sync_stream()
+        _check(load().dg_step_dt(self._h, _ptr(u), float(dt)), "dg_step_dt")
 
     def step_cfl_host(self, u, cfl=0.5, n_steps=1):
         """n_steps CFL steps on a state in host memory: a contiguous float64

@@ -139,6 +139,30 @@ def ensemble_state(members, nodes_of_degree):
     return np.ascontiguousarray(np.concatenate(parts))
 
 
+def warped_node_coordinates(N, n, xi, warp=0.15):
+    """Physical node coordinates, shape (3, n_elem, (N+1)^3), of the periodic
+    box [-1,1]^3 of n[0] x n[1] x n[2] elements warped by the mapping of the
+    paper's curvilinear benchmark: Cartesian reference coordinates c of the
+    box go to y = c1 + a cos(1.5 pi c0) cos(0.5 pi c1) cos(0.5 pi c2), then
+    x = c0 + a cos(0.5 pi c0) cos(2 pi y) cos(0.5 pi c2), then
+    z = c2 + a cos(0.5 pi x) cos(pi y) cos(0.5 pi c2), with a = warp."""
+    c0, c1, c2 = node_coordinates(3, N, n, box(3), xi)
+    pi = np.pi
+    y = c1 + warp * np.cos(1.5 * pi * c0) * np.cos(0.5 * pi * c1) * np.cos(0.5 * pi * c2)
+    x = c0 + warp * np.cos(0.5 * pi * c0) * np.cos(2.0 * pi * y) * np.cos(0.5 * pi * c2)
+    z = c2 + warp * np.cos(0.5 * pi * x) * np.cos(pi * y) * np.cos(0.5 * pi * c2)
+    return np.stack([x, y, z])
+
+
+def manufactured_state(X, t=0.0, amplitude=0.1):
+    """The manufactured solution used with source terms: rho = 2 +
+    A sin(pi (x + y + z - t)), v = (1, 1, 1), E = rho^2, at the node
+    coordinates X (3, n_elem, P); flat state in the usual layout."""
+    rho = 2.0 + amplitude * np.sin(np.pi * (X[0] + X[1] + X[2] - t))
+    u = np.stack([rho, rho, rho, rho, rho * rho], axis=1)
+    return np.ascontiguousarray(u.reshape(-1))
+
+
 def box(d, lo=-1.0, hi=1.0):
     """Domain [lo, hi]^d as [lo0, hi0, lo1, hi1, ...]."""
     return np.array([lo, hi] * d, dtype=np.float64)

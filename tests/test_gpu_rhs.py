@@ -336,6 +336,21 @@ def test_host_state_step_equals_device_step(orc, memory, n_steps):
     assert m2.check() == 0
 
 
+def test_step_with_given_dt_equals_cfl_step(orc):
+    d, N, n = 2, 4, (5, 3)
+    xi, _ = orc.lgl(N)
+    u0 = W.noisy_density_wave(d, N, n, W.box(d), xi, seed=6)
+    m1, m2 = Mesh(d, N, n), Mesh(d, N, n)
+    a = torch.from_numpy(u0.copy()).cuda()
+    b = torch.from_numpy(u0.copy()).cuda()
+    for _ in range(3):
+        m1.step_cfl(a, cfl=0.5)
+        m2.step_dt(b, m1.last_dt())
+        assert m2.last_dt() == m1.last_dt()
+    torch.cuda.synchronize()
+    assert torch.equal(a, b)
+
+
 def test_host_state_step_rejects_device_memory():
     from paper_2108_06476_gb300 import load
     m = Mesh(2, 2, (2, 2))
