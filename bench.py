@@ -255,6 +255,53 @@ def run_ensemble(args, timed, rank):
     return out
 
 
+def run_curved(args, timed):
+    """The paper's PID setup (Sec. 3.1) on the GPU: the warped periodic box
+    [-1,1]^3 of 4^3 elements, the manufactured solution with its source
+    terms, CFL 0.5 steps (device time step, CUDA graph), degrees 3..7, for the
+    flux-differencing solver (Ranocha volume and surface flux) and the
+    weak-form solver (central volume flux, HLL surface flux); PID =
+    time / (steps * 5 * nodes). Plus the same operator on 64^3 warped
+    elements (N = 3, flux differencing) for throughput."""
+    import torch
+    from paper_2108_06476_gb300 import Mesh, lgl_nodes, workloads as W
+    out = {"workload": "warped periodic box [-1,1]^3 (warp 0.15), manufactured solution "
+                       "with source terms, CFL 0.5, CUDA-graph steps", "pid_4cubed": {}}
+    k = max(1, min(args.steps, 5)) * 20
+    for solver, vf, sf in (("flux_differencing", "ranocha", "ranocha"),
+                           ("weak_form", "central", "hll")):
+        rows = {}
+        for N in range(3, 8):
+            n = (4, 4, 4)
+            m = Mesh(3, N, n, warp=0.15, volume_flux=vf, surface_flux=sf)
+            m.set_source("manufactured")
+            xi, _ = lgl_nodes(N)
+            u = torch.from_numpy(W.manufactured_state(
+                W.warped_node_coordinates(N, n, xi, 0.15), 0.0)).cuda()
+            for _ in range(max(3, args.warmup)):
+                m.step_cfl(u, cfl=0.5, graph=True)
+            ms = timed(lambda: [m.step_cfl(u, cfl=0.5, graph=True) for _ in range(k)])
+            m.check()
+            rows[str(N)] = {"pid_s": ms / 1e3 / (k * 5 * m.n_nodes), "ms_per_step": ms / k,
+                            "nodes": m.n_nodes}
+            del m, u
+        out["pid_4cubed"][solver] = rows
+    n = (64, 64, 64)
+    m = Mesh(3, 3, n, warp=0.15)
+    m.set_source("manufactured")
+    xi, _ = lgl_nodes(3)
+    u = torch.from_numpy(W.manufactured_state(
+        W.warped_node_coordinates(3, n, xi, 0.15), 0.0)).cuda()
+    for _ in range(max(3, args.warmup)):
+        m.step_cfl(u, cfl=0.5, graph=True)
+    kk = max(1, min(args.steps, 5))
+    ms = timed(lambda: [m.step_cfl(u, cfl=0.5, graph=True) for _ in range(kk)])
+    m.check()
+    out["warped_64cubed_n3"] = {"value": m.n_nodes * 5 * kk / (ms / 1e3), "unit": UNIT,
+                                "ms_per_step": ms / kk, "nodes": m.n_nodes}
+    return out
+
+
 def max_over_ranks(ms, dist, device="cuda"):
     """The slowest rank's time (the job's time); identity without a process
     group."""
@@ -439,6 +486,11 @@ def run_ours(args, spec, world, rank, local):
     if not args.no_ensemble:
         ensemble = run_ensemble(args, timed, rank)
 
+    # ---- the paper's curvilinear benchmark setup ----
+    curved = None
+    if not args.no_curved:
+        curved = run_curved(args, timed)
+
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
@@ -466,6 +518,7 @@ def run_ours(args, spec, world, rank, local):
         "rhs_only": rhs_only,
         "fp32": fp32,
         "ensemble": ensemble,
+        "curved": curved,
         "e2e": e2e,
         "clocks": clk.summary(),
     }
@@ -487,6 +540,7 @@ def main():
                     help="override elements per dimension (small cases for profiling)")
     ap.add_argument("--no-fp32", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-curved", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-ensemble", action="store_true")
     args = ap.parse_args()

@@ -76,6 +76,42 @@ typedef struct {
 int dg_mesh_create(int d, int N, const int *elements_per_dim, const double *domain,
                    const dg_options *opt, void *cuda_stream, dg_mesh **out);
 
+/* Create the curvilinear mesh of the paper's performance benchmark
+ * (Sec. 3.1): the periodic box [-1,1]^3 of elements_per_dim[0] x [1] x [2]
+ * elements of degree N (1..7) whose interior is warped by
+ *   y = eta  + warp cos(1.5 pi xi) cos(0.5 pi eta) cos(0.5 pi zeta),
+ *   x = xi   + warp cos(0.5 pi xi) cos(2 pi y)    cos(0.5 pi zeta),
+ *   z = zeta + warp cos(0.5 pi x)  cos(pi y)      cos(0.5 pi zeta)
+ * ((xi, eta, zeta) the Cartesian coordinates of the box; warp = 0.15 in the
+ * paper, 0 gives the Cartesian mesh). Each element is the image of the
+ * reference cube under the degree-N interpolant of the mapping at the LGL
+ * nodes; the library computes the metric terms in the conservative curl form
+ * (free-stream preserving) and the Jacobians on the device. dg_rhs,
+ * dg_rhs_part, dg_step, dg_step_cfl, dg_step_dt, dg_step_graph,
+ * dg_step_cfl_host, dg_max_dt and dg_integrals accept such meshes (the
+ * split-form operator with contravariant two-point fluxes, surface fluxes
+ * along the left element's metric vector, du scaled by 1/J; the CFL rule with
+ * contravariant wave speeds); dg_rhs_vjp does not. FP64 only
+ * (opt->precision must be DG_FP64); 2D is not offered. Errors: DG_ERR_ARG
+ * (also for |warp| > 0.5), DG_ERR_OOM, DG_ERR_CUDA. */
+int dg_mesh_create_curved(int N, const int *elements_per_dim, double warp, const dg_options *opt,
+                          void *cuda_stream, dg_mesh **out);
+
+/* Source terms (curved meshes only): DG_SOURCE_MANUFACTURED adds
+ * S = d_t u + div F(u) of the manufactured solution rho = 2 + 0.1 sin(pi (x +
+ * y + z - t)), v = (1, 1, 1), E = rho^2 (the smooth Euler problem of the
+ * benchmark; the paper names it without a formula), evaluated at the node
+ * coordinates and the mesh time: dg_rhs at the mesh time, the steps at the
+ * stage times t + c_s dt. Errors: DG_ERR_ARG. */
+enum { DG_SOURCE_NONE = 0, DG_SOURCE_MANUFACTURED = 1 };
+int dg_set_source(dg_mesh *mesh, int kind);
+
+/* Simulation time of the mesh (0 at creation; the steps of a curved mesh
+ * advance it by their dt). dg_set_time is asynchronous, dg_get_time waits for
+ * the mesh's stream. Errors: DG_ERR_ARG, DG_ERR_CUDA. */
+int dg_set_time(dg_mesh *mesh, double t);
+int dg_get_time(dg_mesh *mesh, double *t);
+
 /* Free the mesh and its device buffers (after synchronising its stream).
  * NULL is accepted. */
 int dg_mesh_destroy(dg_mesh *mesh);

@@ -8,6 +8,7 @@
 #include <string.h>
 
 #include "dgsem.h"
+#include "dg_curved_decl.cuh"
 #include "dg_device.cuh"
 
 namespace dg {
@@ -62,6 +63,16 @@ struct dg_mesh {
   const double* graph_u;
   double graph_cfl;
   double* u_dev;       // device copy of a host state (dg_step_cfl_host), first use
+  double* t_dev;       // simulation time (source terms), advanced by the fused steps
+  // curvilinear meshes (dg_mesh_create_curved)
+  int curved;
+  double warp;
+  int source;          // DG_SOURCE_*
+  double* Ja;          // metric terms (J a^r)_n, [e][r][n][P]
+  double* invJ;        // 1 / J per node
+  double* Jdet;        // J per node
+  double* X;           // node coordinates [e][3][P]
+  dg::CTables ctab;
 };
 
 namespace {
@@ -144,7 +155,19 @@ void split_matrix(int N, const long double* x, const long double* w, long double
   }
 }
 
-// Carpenter & Kennedy (1994) five-stage fourth-order 2N-storage scheme.
+// the LGL differentiation matrix itself (same closed form)
+void diff_matrix(int N, const long double* x, long double D[8][8]) {
+  for (int i = 0; i <= N; ++i)
+    for (int j = 0; j <= N; ++j) {
+      if (i != j) D[i][j] = legendre_p(N, x[i]) / (legendre_p(N, x[j]) * (x[i] - x[j]));
+      else if (i == 0) D[i][j] = -(long double)N * (N + 1) / 4.0L;
+      else if (i == N) D[i][j] = (long double)N * (N + 1) / 4.0L;
+      else D[i][j] = 0.0L;
+    }
+}
+
+// Carpenter & Kennedy (1994) five-stage fourth-order 2N-storage scheme
+// (A, B; the stage times c_s, used by time-dependent source terms, follow).
 const double kRkA[5] = {0.0, -567301805773.0 / 1357537059087.0,
                         -2404267990393.0 / 2016746695238.0,
                         -3550918686646.0 / 2091501179385.0,
@@ -152,6 +175,10 @@ const double kRkA[5] = {0.0, -567301805773.0 / 1357537059087.0,
 const double kRkB[5] = {1432997174477.0 / 9575080441755.0, 5161836677717.0 / 13612068292357.0,
                         1720146321549.0 / 2090206949498.0, 3134564353537.0 / 4481467310338.0,
                         2277821191437.0 / 14882151754819.0};
+const double kRkC[5] = {0.0, 1432997174477.0 / 9575080441755.0,
+                        2526269341429.0 / 6820363962896.0,
+                        2006345519317.0 / 3224310063776.0,
+                        2802321613138.0 / 2924317926251.0};
 
 // ---- kernels ----
 template <typename RD>
@@ -292,6 +319,10 @@ __global__ void dt_kernel(unsigned long long* speed, int N, double cfl, double* 
   *dt = cfl * 2.0 / ((N + 1) * worst);
 }
 
+// a given time step; the simulation time advanced by the step's dt
+__global__ void set_dt_kernel(double* dt_dev, double dt) { *dt_dev = dt; }
+__global__ void advance_time_kernel(double* t, const double* dt) { *t += *dt; }
+
 // double-double accumulation (Knuth two-sum)
 struct dd {
   double hi, lo;
@@ -308,8 +339,8 @@ __device__ __forceinline__ dd dd_add1(dd a, double x) { return dd_add(a, dd{x, 0
 
 template <int D>
 __global__ void integrals_kernel(const double* __restrict__ u, Geom g, int P,
-                                 const double* __restrict__ wq, double* __restrict__ partials,
-                                 unsigned* err) {
+                                 const double* __restrict__ wq, const double* __restrict__ Jn,
+                                 double* __restrict__ partials, unsigned* err) {
   constexpr int NV = D + 2, NQ = D + 4;
   dd acc[NQ];
 #pragma unroll
@@ -326,7 +357,7 @@ __global__ void integrals_kernel(const double* __restrict__ u, Geom g, int P,
     for (int v = 0; v < NV; ++v) c[v] = u[(e * NV + v) * P + node];
     const dg::Prim<double, D> q = dg::cons2prim<double, D>(c, gm1);
     bad |= dg::prim_check(q);
-    const double w = wq[node];
+    const double w = Jn ? wq[node] * Jn[t] : wq[node];  // curved meshes: w J
     double v2 = 0.0;
 #pragma unroll
     for (int k = 0; k < D; ++k) v2 += q.v[k] * q.v[k];
@@ -394,6 +425,12 @@ int grid_for(long long work, int threads);
 int launch_speed(dg_mesh* m, const double* u, double* copy_to = nullptr) {
   const int threads = 256;
   const int grid = grid_for(m->nelem * 32, threads);
+  if (m->curved) {
+    DG_CUDA(dg::curved_speed_launch(m->N, u, m->Ja, m->invJ, m->geom, m->speed, m->err, copy_to,
+                                    grid, m->stream),
+            "curved speed kernel launch");
+    return DG_OK;
+  }
   const double s0 = 2.0 / m->h[0], s1 = 2.0 / m->h[1], s2 = 2.0 / m->h[2];
   const bool f32 = m->opt.precision == DG_FP32;
   if (m->d == 2) {
@@ -556,7 +593,8 @@ int dg_mesh_create(int d, int N, const int* epd, const double* domain, const dg_
       (e = cudaMalloc(&m->speed, sizeof(unsigned long long))) != cudaSuccess ||
       (e = cudaMalloc(&m->err, sizeof(unsigned))) != cudaSuccess ||
       (e = cudaMalloc(&m->pref, m->nelem * sizeof(float))) != cudaSuccess ||
-      (e = cudaMalloc(&m->dt_dev, sizeof(double))) != cudaSuccess) {
+      (e = cudaMalloc(&m->dt_dev, sizeof(double))) != cudaSuccess ||
+      (e = cudaMalloc(&m->t_dev, sizeof(double))) != cudaSuccess) {
     int rc = cuda_fail(e, "dg_mesh_create: cudaMalloc");
     cudaFree(m->k);
     cudaFree(m->fs);
@@ -567,6 +605,7 @@ int dg_mesh_create(int d, int N, const int* epd, const double* domain, const dg_
     cudaFree(m->err);
     cudaFree(m->pref);
     cudaFree(m->dt_dev);
+    cudaFree(m->t_dev);
     delete m;
     return rc;
   }
@@ -576,12 +615,102 @@ int dg_mesh_create(int d, int N, const int* epd, const double* domain, const dg_
       (e = cudaMemsetAsync(m->err, 0, sizeof(unsigned), m->stream)) != cudaSuccess ||
       (e = cudaMemsetAsync(m->speed, 0, sizeof(unsigned long long), m->stream)) != cudaSuccess ||
       (e = cudaMemsetAsync(m->dt_dev, 0, sizeof(double), m->stream)) != cudaSuccess ||
+      (e = cudaMemsetAsync(m->t_dev, 0, sizeof(double), m->stream)) != cudaSuccess ||
       (e = cudaStreamSynchronize(m->stream)) != cudaSuccess) {
     int rc = cuda_fail(e, "dg_mesh_create: initialisation");
     dg_mesh_destroy(m);
     return rc;
   }
   *out = m;
+  return DG_OK;
+}
+
+int dg_mesh_create_curved(int N, const int* epd, double warp, const dg_options* opt,
+                          void* cuda_stream, dg_mesh** out) {
+  if (out) *out = nullptr;
+  if (!out || !epd) return fail(DG_ERR_ARG, "dg_mesh_create_curved: null argument");
+  if (!isfinite(warp) || fabs(warp) > 0.5)
+    return fail(DG_ERR_ARG, "dg_mesh_create_curved: warp must be finite and |warp| <= 0.5");
+  if (opt && opt->precision != DG_FP64)
+    return fail(DG_ERR_ARG, "dg_mesh_create_curved: curved meshes are FP64");
+  const double box[6] = {-1.0, 1.0, -1.0, 1.0, -1.0, 1.0};
+  dg_mesh* m = nullptr;
+  int rc = dg_mesh_create(3, N, epd, box, opt, cuda_stream, &m);
+  if (rc != DG_OK) return rc;
+  m->curved = 1;
+  m->warp = warp;
+  const long long nn = m->nnodes;
+  cudaError_t e;
+  if ((e = cudaMalloc(&m->Ja, 9 * nn * sizeof(double))) != cudaSuccess ||
+      (e = cudaMalloc(&m->invJ, nn * sizeof(double))) != cudaSuccess ||
+      (e = cudaMalloc(&m->Jdet, nn * sizeof(double))) != cudaSuccess ||
+      (e = cudaMalloc(&m->X, 3 * nn * sizeof(double))) != cudaSuccess) {
+    rc = cuda_fail(e, "dg_mesh_create_curved: cudaMalloc");
+    dg_mesh_destroy(m);
+    return rc;
+  }
+  // basis: nodes, derivative matrix, unscaled split form with the sign of du
+  long double x[8], w[8], D[8][8], Dt[8][8];
+  lgl_basis(N, x, w);
+  diff_matrix(N, x, D);
+  split_matrix(N, x, w, Dt);
+  dg::CGeom cg;
+  memset(&cg, 0, sizeof(cg));
+  cg.g = m->geom;
+  cg.warp = warp;
+  memset(&m->ctab, 0, sizeof(m->ctab));
+  for (int a = 0; a <= N; ++a) {
+    cg.xi[a] = (double)x[a];
+    for (int b = 0; b <= N; ++b) {
+      cg.D[a][b] = (double)D[a][b];
+      m->ctab.Ds[a][b] = (double)(-Dt[a][b]);
+    }
+  }
+  m->ctab.liftR = (double)(-1.0L / w[N]);
+  m->ctab.liftL = (double)(1.0L / w[0]);
+  // reference quadrature weights (the integrals multiply by J per node)
+  double wq_host[512];
+  for (long long node = 0; node < m->P; ++node)
+    wq_host[node] = m->w[node % m->np] * m->w[(node / m->np) % m->np] * m->w[node / (m->np * m->np)];
+  if ((e = dg::curved_geometry_launch(N, cg, m->Ja, m->invJ, m->Jdet, m->X, m->stream)) !=
+          cudaSuccess ||
+      (e = cudaMemcpyAsync(m->wq, wq_host, m->P * sizeof(double), cudaMemcpyHostToDevice,
+                           m->stream)) != cudaSuccess ||
+      (e = cudaStreamSynchronize(m->stream)) != cudaSuccess) {
+    rc = cuda_fail(e, "dg_mesh_create_curved: geometry");
+    dg_mesh_destroy(m);
+    return rc;
+  }
+  *out = m;
+  return DG_OK;
+}
+
+int dg_set_source(dg_mesh* m, int kind) {
+  if (!valid_mesh(m)) return fail(DG_ERR_ARG, "dg_set_source: invalid mesh");
+  if (kind != DG_SOURCE_NONE && kind != DG_SOURCE_MANUFACTURED)
+    return fail(DG_ERR_ARG, "dg_set_source: unknown source %d", kind);
+  if (kind != DG_SOURCE_NONE && !m->curved)
+    return fail(DG_ERR_ARG, "dg_set_source: source terms need a mesh from dg_mesh_create_curved");
+  m->source = kind;
+  if (m->graph) {  // a recorded step holds the old source choice
+    cudaGraphExecDestroy(m->graph);
+    m->graph = nullptr;
+  }
+  return DG_OK;
+}
+
+int dg_set_time(dg_mesh* m, double t) {
+  if (!valid_mesh(m) || !isfinite(t)) return fail(DG_ERR_ARG, "dg_set_time: bad argument");
+  set_dt_kernel<<<1, 1, 0, m->stream>>>(m->t_dev, t);
+  DG_CUDA(cudaGetLastError(), "dg_set_time: launch");
+  return DG_OK;
+}
+
+int dg_get_time(dg_mesh* m, double* t) {
+  if (!valid_mesh(m) || !t) return fail(DG_ERR_ARG, "dg_get_time: bad argument");
+  DG_CUDA(cudaMemcpyAsync(t, m->t_dev, sizeof(double), cudaMemcpyDeviceToHost, m->stream),
+          "dg_get_time: copy");
+  DG_CUDA(cudaStreamSynchronize(m->stream), "dg_get_time: sync");
   return DG_OK;
 }
 
@@ -599,6 +728,11 @@ int dg_mesh_destroy(dg_mesh* m) {
   cudaFree(m->pref);
   cudaFree(m->dt_dev);
   cudaFree(m->u_dev);
+  cudaFree(m->t_dev);
+  cudaFree(m->Ja);
+  cudaFree(m->invJ);
+  cudaFree(m->Jdet);
+  cudaFree(m->X);
   if (m->graph) cudaGraphExecDestroy(m->graph);
   delete m;
   return DG_OK;
@@ -637,7 +771,14 @@ int dg_rhs_part(dg_mesh* m, const double* u, void* du, int parts) {
     parts = 2;
   }
   cudaError_t e;
-  if (m->opt.precision == DG_FP64) {
+  if (m->curved) {
+    dg::SourceArgs src;  // the source at the mesh time
+    src.kind = m->source;
+    src.t0 = m->t_dev;
+    e = dg::curved_rhs_launch(m->N, const_cast<double*>(u), (double*)du, (double*)m->fs, m->Ja,
+                              m->invJ, m->X, m->geom, m->ctab, m->opt.volume_flux,
+                              m->opt.surface_flux, m->err, m->stream, parts, fz, src);
+  } else if (m->opt.precision == DG_FP64) {
     e = (m->d == 2 ? dg::rhs_launch_double_2 : dg::rhs_launch_double_3)(
         m->N, u, (double*)du, (double*)m->fs, m->geom, m->t64, m->opt.volume_flux,
         m->opt.surface_flux, m->err, m->stream, parts, fz);
@@ -652,6 +793,7 @@ int dg_rhs_part(dg_mesh* m, const double* u, void* du, int parts) {
 
 int dg_rhs_vjp(dg_mesh* m, const double* u, const double* w, double* ubar) {
   if (!valid_mesh(m) || !u || !w || !ubar) return fail(DG_ERR_ARG, "dg_rhs_vjp: null argument");
+  if (m->curved) return fail(DG_ERR_ARG, "dg_rhs_vjp: not available on curved meshes");
   if (!m->fbar) {
     const long long n = 2LL * m->d * m->nv * m->nelem * (m->P / m->np);
     DG_CUDA(cudaMalloc(&m->fbar, n * sizeof(double)), "dg_rhs_vjp: cudaMalloc");
@@ -690,6 +832,27 @@ int dg_rk_reset(dg_mesh* m) {
 
 int dg_step(dg_mesh* m, double* u, void* du, double dt) {
   if (!valid_mesh(m) || !u || !du) return fail(DG_ERR_ARG, "dg_step: null argument");
+  if (m->curved) {
+    // source terms at the stage times t + c_s dt; the mesh time advances by dt
+    set_dt_kernel<<<1, 1, 0, m->stream>>>(m->dt_dev, dt);
+    DG_CUDA(cudaGetLastError(), "dg_step: launch");
+    for (int s = 0; s < 5; ++s) {
+      dg::SourceArgs src;
+      src.kind = m->source;
+      src.t0 = m->t_dev;
+      src.dt = m->dt_dev;
+      src.c = kRkC[s];
+      DG_CUDA(dg::curved_rhs_launch(m->N, u, (double*)du, (double*)m->fs, m->Ja, m->invJ, m->X,
+                                    m->geom, m->ctab, m->opt.volume_flux, m->opt.surface_flux,
+                                    m->err, m->stream, 3, dg::StageFuse(), src),
+              "dg_step: rhs launch");
+      const int rc = dg_rk_stage(m, u, du, kRkA[s], kRkB[s], dt);
+      if (rc != DG_OK) return rc;
+    }
+    advance_time_kernel<<<1, 1, 0, m->stream>>>(m->t_dev, m->dt_dev);
+    DG_CUDA(cudaGetLastError(), "dg_step: launch");
+    return DG_OK;
+  }
   for (int s = 0; s < 5; ++s) {
     int rc = dg_rhs(m, u, du);
     if (rc != DG_OK) return rc;
@@ -703,7 +866,6 @@ namespace {
 
 // dt on the device, then five stages with the update fused into the volume
 // kernel (no du buffer, no host synchronisation)
-__global__ void set_dt_kernel(double* dt_dev, double dt) { *dt_dev = dt; }
 
 // The five fused stages on the device state u with the time step in
 // m->dt_dev; out (optional): where the last stage stores the new state.
@@ -716,7 +878,16 @@ int enqueue_fused_stages(dg_mesh* m, double* u, double* out) {
     fz.b = kRkB[s];
     if (s == 4) fz.u_out = out;
     cudaError_t e;
-    if (m->opt.precision == DG_FP64) {
+    if (m->curved) {
+      dg::SourceArgs src;  // stage time t + c_s dt
+      src.kind = m->source;
+      src.t0 = m->t_dev;
+      src.dt = m->dt_dev;
+      src.c = kRkC[s];
+      e = dg::curved_rhs_launch(m->N, u, nullptr, (double*)m->fs, m->Ja, m->invJ, m->X, m->geom,
+                                m->ctab, m->opt.volume_flux, m->opt.surface_flux, m->err,
+                                m->stream, 3, fz, src);
+    } else if (m->opt.precision == DG_FP64) {
       e = (m->d == 2 ? dg::rhs_launch_double_2 : dg::rhs_launch_double_3)(
           m->N, u, nullptr, (double*)m->fs, m->geom, m->t64, m->opt.volume_flux,
           m->opt.surface_flux, m->err, m->stream, 3, fz);
@@ -727,6 +898,10 @@ int enqueue_fused_stages(dg_mesh* m, double* u, double* out) {
           m->opt.surface_flux, m->err, m->stream, 3, fz);
     }
     if (e != cudaSuccess) return cuda_fail(e, "fused stage launch");
+  }
+  if (m->curved) {
+    advance_time_kernel<<<1, 1, 0, m->stream>>>(m->t_dev, m->dt_dev);
+    DG_CUDA(cudaGetLastError(), "time advance launch");
   }
   return DG_OK;
 }
@@ -865,10 +1040,10 @@ int dg_integrals(dg_mesh* m, const double* u, double* out) {
   const int nq = m->d + 4;
   if (m->d == 2)
     integrals_kernel<2><<<kRedBlocks, kRedThreads, 0, m->stream>>>(u, m->geom, (int)m->P, m->wq,
-                                                                   m->partials, m->err);
+                                                                   m->Jdet, m->partials, m->err);
   else
     integrals_kernel<3><<<kRedBlocks, kRedThreads, 0, m->stream>>>(u, m->geom, (int)m->P, m->wq,
-                                                                   m->partials, m->err);
+                                                                   m->Jdet, m->partials, m->err);
   DG_CUDA(cudaGetLastError(), "dg_integrals: launch");
   integrals_final_kernel<<<1, kRedThreads, 0, m->stream>>>(m->partials, kRedBlocks, nq,
                                                            m->red_out);

@@ -1,0 +1,97 @@
+// Launchers of the curvilinear-mesh kernels (dg_curved.cuh), degrees 1..7.
+#include "dg_curved.cuh"
+
+namespace dg {
+
+namespace {
+
+template <int N>
+cudaError_t geometry_n(const CGeom& cg, double* Ja, double* invJ, double* Jdet, double* X,
+                       cudaStream_t st) {
+  constexpr int P = (N + 1) * (N + 1) * (N + 1);
+  curved_geometry_kernel<N><<<(unsigned)cg.g.nelem, P, 0, st>>>(cg, Ja, invJ, Jdet, X);
+  return cudaGetLastError();
+}
+
+template <int N, int VF>
+cudaError_t volume_n(double* u, double* du, const double* fs, const double* Ja,
+                     const double* invJ, const double* X, const Geom& g, const CTables& tb,
+                     unsigned* err, cudaStream_t st, const StageFuse& fz, const SourceArgs& src) {
+  using L = CLaunch<N>;
+  constexpr int EPB = L::EPB;
+  cudaError_t e = allow_smem(curved_volume_kernel<N, VF, EPB>, L::SMEM);
+  if (e != cudaSuccess) return e;
+  const long long grid = (g.nelem + EPB - 1) / EPB;
+  curved_volume_kernel<N, VF, EPB><<<(unsigned)grid, EPB * L::LINES, L::SMEM, st>>>(
+      u, du, fs, Ja, invJ, X, g, tb, err, fz, src);
+  return cudaGetLastError();
+}
+
+template <int N>
+cudaError_t rhs_n(double* u, double* du, double* fs, const double* Ja, const double* invJ,
+                  const double* X, const Geom& g, const CTables& tb, int vf, int sf,
+                  unsigned* err, cudaStream_t st, int parts, const StageFuse& fz,
+                  const SourceArgs& src) {
+  if (parts & 1) {
+    constexpr int NF = (N + 1) * (N + 1);
+    long long blocks = (g.nelem * NF + 255) / 256;
+    if (blocks > 152 * 32) blocks = 152 * 32;
+    if (blocks < 1) blocks = 1;
+    curved_surface_kernel<N><<<dim3((unsigned)blocks, 3), 256, 0, st>>>(u, fs, Ja, g, sf);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  if (!(parts & 2)) return cudaSuccess;
+  if (vf == kVRanocha) return volume_n<N, kVRanocha>(u, du, fs, Ja, invJ, X, g, tb, err, st, fz, src);
+  if (vf == kVChandrashekar)
+    return volume_n<N, kVChandrashekar>(u, du, fs, Ja, invJ, X, g, tb, err, st, fz, src);
+  return volume_n<N, kVCentral>(u, du, fs, Ja, invJ, X, g, tb, err, st, fz, src);
+}
+
+template <int N>
+cudaError_t speed_n(const double* u, const double* Ja, const double* invJ, const Geom& g,
+                    unsigned long long* out, unsigned* err, double* copy_to, int grid,
+                    cudaStream_t st) {
+  curved_speed_kernel<N><<<grid, 256, 0, st>>>(u, Ja, invJ, g, out, err, copy_to);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+#define DG_CURVED_SWITCH(CALL)        \
+  switch (N) {                        \
+    case 1: return CALL(1);           \
+    case 2: return CALL(2);           \
+    case 3: return CALL(3);           \
+    case 4: return CALL(4);           \
+    case 5: return CALL(5);           \
+    case 6: return CALL(6);           \
+    case 7: return CALL(7);           \
+    default: return cudaErrorInvalidValue; \
+  }
+
+cudaError_t curved_geometry_launch(int N, const CGeom& cg, double* Ja, double* invJ, double* Jdet,
+                                   double* X, cudaStream_t st) {
+#define G(n) geometry_n<n>(cg, Ja, invJ, Jdet, X, st)
+  DG_CURVED_SWITCH(G)
+#undef G
+}
+
+cudaError_t curved_rhs_launch(int N, double* u, double* du, double* fs, const double* Ja,
+                              const double* invJ, const double* X, const Geom& g,
+                              const CTables& tb, int vf, int sf, unsigned* err, cudaStream_t st,
+                              int parts, const StageFuse& fz, const SourceArgs& src) {
+#define R(n) rhs_n<n>(u, du, fs, Ja, invJ, X, g, tb, vf, sf, err, st, parts, fz, src)
+  DG_CURVED_SWITCH(R)
+#undef R
+}
+
+cudaError_t curved_speed_launch(int N, const double* u, const double* Ja, const double* invJ,
+                                const Geom& g, unsigned long long* out, unsigned* err,
+                                double* copy_to, int grid, cudaStream_t st) {
+#define S(n) speed_n<n>(u, Ja, invJ, g, out, err, copy_to, grid, st)
+  DG_CURVED_SWITCH(S)
+#undef S
+}
+
+}  // namespace dg

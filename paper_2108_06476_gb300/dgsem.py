@@ -27,7 +27,8 @@ RK_B = (1432997174477.0 / 9575080441755.0, 5161836677717.0 / 13612068292357.0,
         1720146321549.0 / 2090206949498.0, 3134564353537.0 / 4481467310338.0,
         2277821191437.0 / 14882151754819.0)
 
-EXPORTS = ("dg_mesh_create", "dg_mesh_destroy", "dg_mesh_info", "dg_mesh_set_stream",
+EXPORTS = ("dg_mesh_create", "dg_mesh_create_curved", "dg_set_source", "dg_set_time",
+           "dg_get_time", "dg_mesh_destroy", "dg_mesh_info", "dg_mesh_set_stream",
            "dg_lgl_nodes", "dg_rhs", "dg_rhs_part", "dg_rhs_vjp", "dg_rk_stage", "dg_rk_reset", "dg_step", "dg_step_cfl", "dg_step_graph",
            "dg_step_dt", "dg_step_cfl_host", "dg_last_dt", "dg_max_dt",
            "dg_integrals", "dg_mesh_check", "dg_last_error", "dg_rhs_noalloc",
@@ -76,6 +77,11 @@ def load(path: str = SO_PATH):
     L.dg_step_graph.argtypes = [vp, vp, ctypes.c_double]
     L.dg_step_cfl_host.argtypes = [vp, vp, ctypes.c_double, ctypes.c_int]
     L.dg_step_dt.argtypes = [vp, vp, ctypes.c_double]
+    L.dg_mesh_create_curved.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                        ctypes.c_double, vp, vp, vp]
+    L.dg_set_source.argtypes = [vp, ctypes.c_int]
+    L.dg_set_time.argtypes = [vp, ctypes.c_double]
+    L.dg_get_time.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
     L.dg_last_dt.argtypes = [vp, dp]
     L.dg_max_dt.argtypes = [vp, vp, ctypes.c_double, dp]
     L.dg_integrals.argtypes = [vp, vp, dp]
@@ -134,14 +140,19 @@ class MeshSpec:
     precision: str = "fp64"
 
 
+SOURCE = {"none": 0, "manufactured": 1}
+
+
 class Mesh:
-    """A uniform periodic Cartesian DGSEM mesh on the current CUDA device.
+    """A periodic DGSEM mesh on the current CUDA device: uniform Cartesian, or
+    with warp given, the warped box [-1,1]^3 of the paper's curvilinear
+    benchmark (3D, FP64; warp = 0.15 is the paper's amplitude).
 
     State tensors are float64 CUDA tensors of n_values entries in the layout
     u[e][v][k][j][i]; rhs outputs are float64 (fp64) or float32 (fp32)."""
 
     def __init__(self, d, N, n, domain=None, gamma=1.4, volume_flux="ranocha",
-                 surface_flux="llf", precision="fp64", stream=None):
+                 surface_flux="llf", precision="fp64", stream=None, warp=None):
         import torch
         self._torch = torch
         L = load()
@@ -157,9 +168,17 @@ class Mesh:
         h = ctypes.c_void_p()
         st = stream if stream is not None else torch.cuda.current_stream()
         self._stream = st
-        _check(L.dg_mesh_create(self.d, self.N, n_arr, dom, ctypes.byref(opt),
-                                ctypes.c_void_p(st.cuda_stream), ctypes.byref(h)),
-               "dg_mesh_create")
+        self.warp = warp
+        if warp is None:
+            _check(L.dg_mesh_create(self.d, self.N, n_arr, dom, ctypes.byref(opt),
+                                    ctypes.c_void_p(st.cuda_stream), ctypes.byref(h)),
+                   "dg_mesh_create")
+        else:
+            if self.d != 3 or tuple(self.domain) != (-1.0, 1.0) * 3:
+                raise DGError("curved meshes are the 3D box [-1,1]^3")
+            _check(L.dg_mesh_create_curved(self.N, n_arr, float(warp), ctypes.byref(opt),
+                                           ctypes.c_void_p(st.cuda_stream), ctypes.byref(h)),
+                   "dg_mesh_create_curved")
         self._h = h
         nn, nv, nvals = ctypes.c_longlong(), ctypes.c_int(), ctypes.c_longlong()
         _check(L.dg_mesh_info(h, ctypes.byref(nn), ctypes.byref(nv), ctypes.byref(nvals)),
@@ -255,6 +274,20 @@ class Mesh:
         self._sync_stream()
         fn = load().dg_step_graph if graph else load().dg_step_cfl
         _check(fn(self._h, _ptr(u), float(cfl)), "dg_step_cfl")
+
+    def set_source(self, kind):
+        """Source terms on a curved mesh: "none" or "manufactured"."""
+        _check(load().dg_set_source(self._h, SOURCE[kind]), "dg_set_source")
+
+    def set_time(self, t):
+        self._sync_stream()
+        _check(load().dg_set_time(self._h, float(t)), "dg_set_time")
+
+    @property
+    def time(self):
+        out = ctypes.c_double()
+        _check(load().dg_get_time(self._h, ctypes.byref(out)), "dg_get_time")
+        return out.value
 
     def step_dt(self, u, dt):
         """One LSRK step with the given time step, the stage updates fused

@@ -1,0 +1,157 @@
+"""GPU parity of the curvilinear-mesh path (the warped periodic box of the
+paper's performance benchmark) against the curvilinear oracle, through the
+C ABI: rhs for every degree and flux pair, the manufactured-solution source,
+fused and unfused steps with stage times, the CFL time step, the integrals
+and the Cartesian limit. FP64 bar 1e-12 relative L2, as on Cartesian meshes.
+"""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle as orc  # noqa: E402
+from paper_2108_06476_gb300 import DGError, Mesh, workloads as W  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-12
+VF = {0: "ranocha", 1: "chandrashekar", 2: "central"}
+SF = {0: "llf", 1: "ranocha", 2: "hll", 3: "chandrashekar"}
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def noisy_warped_state(N, n, seed, warp=0.15):
+    """manufactured state plus 1e-2 uniform noise in every variable"""
+    xi, _ = orc.lgl(N)
+    u = W.manufactured_state(W.warped_node_coordinates(N, n, xi, warp), 0.0)
+    return u + 1e-2 * np.random.default_rng(seed).uniform(-1, 1, u.size)
+
+
+def gpu_rhs(N, n, u, vf=0, sf=0, warp=0.15, source=False, t=0.0):
+    m = Mesh(3, N, n, warp=warp, volume_flux=VF[vf], surface_flux=SF[sf])
+    if source:
+        m.set_source("manufactured")
+        m.set_time(t)
+    out = m.rhs(torch.from_numpy(u).cuda())
+    assert m.check() == 0
+    return out.cpu().numpy()
+
+
+@pytest.mark.parametrize("N", range(1, 8))
+def test_curved_rhs_every_degree(N):
+    n = (3, 2, 2) if N < 6 else (2, 2, 1)
+    g = orc.CurvedGeometry(N, n, 0.15)
+    u = noisy_warped_state(N, n, seed=N)
+    ref = orc.curved_rhs(g, u)
+    assert rel(gpu_rhs(N, n, u), ref) <= TOL
+
+
+@pytest.mark.parametrize("vf", [0, 1, 2])
+@pytest.mark.parametrize("sf", [0, 1, 2, 3])
+def test_curved_rhs_every_flux(vf, sf):
+    N, n = 3, (2, 3, 2)
+    g = orc.CurvedGeometry(N, n, 0.15)
+    u = noisy_warped_state(N, n, seed=10 * vf + sf)
+    ref = orc.curved_rhs(g, u, vflux=vf, sflux=sf)
+    assert rel(gpu_rhs(N, n, u, vf, sf), ref) <= TOL
+
+
+@pytest.mark.parametrize("N", [3, 5])
+def test_curved_rhs_paper_mesh_with_source(N):
+    # the benchmark mesh: 4^3 warped elements, manufactured solution + source
+    n = (4, 4, 4)
+    g = orc.CurvedGeometry(N, n, 0.15)
+    u = noisy_warped_state(N, n, seed=3)
+    t = 0.37
+    ref = orc.curved_rhs(g, u, source=True, t=t)
+    assert rel(gpu_rhs(N, n, u, source=True, t=t), ref) <= TOL
+
+
+def test_curved_path_without_warping_equals_cartesian_path():
+    N, n = 3, (3, 2, 4)
+    u = W.random_state(3, N, n, seed=8)
+    a = gpu_rhs(N, n, u, warp=0.0)
+    m = Mesh(3, N, n)
+    b = m.rhs(torch.from_numpy(u).cuda()).cpu().numpy()
+    assert rel(a, b) <= 1e-13
+
+
+def test_curved_free_stream():
+    N, n = 4, (3, 3, 2)
+    du = gpu_rhs(N, n, W.uniform_state(3, N, n))
+    assert np.abs(du).max() < 1e-10
+
+
+def test_curved_steps_with_source_against_oracle():
+    N, n = 3, (3, 3, 3)
+    g = orc.CurvedGeometry(N, n, 0.15)
+    xi, _ = orc.lgl(N)
+    u0 = W.manufactured_state(W.warped_node_coordinates(N, n, xi, 0.15), 0.0)
+    dt = 0.5 * orc.curved_max_dt(g, u0, 0.5)
+    uo, t = u0.copy(), 0.0
+    for _ in range(4):
+        uo = orc.curved_lsrk_step(g, uo, dt, t, source=True)
+        t += dt
+    for fused in (True, False):
+        m = Mesh(3, N, n, warp=0.15)
+        m.set_source("manufactured")
+        u = torch.from_numpy(u0.copy()).cuda()
+        du = m.empty_rhs()
+        for _ in range(4):
+            if fused:
+                m.step_dt(u, dt)
+            else:
+                m.step(u, dt, du)
+        assert m.check() == 0
+        assert m.time == pytest.approx(4 * dt, rel=1e-15)
+        got = u.cpu().numpy()
+        assert rel(got - u0, uo - u0) <= 1e-11
+
+
+def test_curved_cfl_step_graph_and_time_step():
+    N, n = 3, (3, 2, 3)
+    g = orc.CurvedGeometry(N, n, 0.15)
+    u0 = noisy_warped_state(N, n, seed=21)
+    m1, m2 = Mesh(3, N, n, warp=0.15), Mesh(3, N, n, warp=0.15)
+    assert m1.max_dt(torch.from_numpy(u0).cuda(), 0.5) == pytest.approx(
+        orc.curved_max_dt(g, u0, 0.5), rel=1e-13)
+    for m in (m1, m2):
+        m.set_source("manufactured")
+    a = torch.from_numpy(u0.copy()).cuda()
+    b = torch.from_numpy(u0.copy()).cuda()
+    for _ in range(3):
+        m1.step_cfl(a, cfl=0.5)
+        m2.step_cfl(b, cfl=0.5, graph=True)
+    torch.cuda.synchronize()
+    assert torch.equal(a, b)
+    assert m1.time == m2.time
+
+
+def test_curved_integrals():
+    N, n = 3, (2, 3, 2)
+    g = orc.CurvedGeometry(N, n, 0.15)
+    u = noisy_warped_state(N, n, seed=2)
+    m = Mesh(3, N, n, warp=0.15)
+    got = m.integrals(torch.from_numpy(u).cuda())
+    _, w = orc.lgl(N)
+    w3 = np.einsum("i,j,k->kji", w, w, w).reshape(-1)
+    wJ = g.J * w3
+    uu = u.reshape(-1, 5, (N + 1) ** 3)
+    for v in range(5):
+        assert got[v] == pytest.approx((wJ * uu[:, v]).sum(), rel=1e-13)
+
+
+def test_curved_mesh_rejects_what_it_does_not_offer():
+    with pytest.raises(DGError):
+        Mesh(3, 3, (2, 2, 2), warp=0.15, precision="fp32")
+    m = Mesh(3, 2, (2, 2, 2), warp=0.15)
+    u = torch.from_numpy(W.uniform_state(3, 2, (2, 2, 2))).cuda()
+    with pytest.raises(DGError):
+        m.rhs_vjp(u, u)
+    c = Mesh(3, 2, (2, 2, 2))
+    with pytest.raises(DGError):
+        c.set_source("manufactured")
