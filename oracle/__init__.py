@@ -97,9 +97,10 @@ def lib():
     return _lib
 
 
-def build_variant(src_text: str, out_dir: str) -> str:
+def build_variant(src_text: str, out_dir: str, curved_text: str | None = None) -> str:
     """Compile a (modified) copy of the oracle source into out_dir, for tests
-    that plant mistakes and check that the pins catch them."""
+    that plant mistakes and check that the pins catch them; curved_text, when
+    given, replaces the curvilinear source as well."""
     src = os.path.join(out_dir, "variant.c")
     with open(src, "w") as fh:
         fh.write(src_text)
@@ -108,6 +109,13 @@ def build_variant(src_text: str, out_dir: str) -> str:
     for tag, defs in (("r", []), ("c", ["-DOR_CSTEP"]), ("l", ["-DOR_LONGDOUBLE"])):
         o = os.path.join(out_dir, f"v_{tag}.o")
         subprocess.check_call(["gcc", *flags, *defs, "-c", src, "-o", o])
+        objs.append(o)
+    if curved_text is not None:
+        csrc = os.path.join(out_dir, "variant_curved.c")
+        with open(csrc, "w") as fh:
+            fh.write(curved_text)
+        o = os.path.join(out_dir, "v_curved.o")
+        subprocess.check_call(["gcc", *flags, "-c", csrc, "-o", o])
         objs.append(o)
     so = os.path.join(out_dir, "libvariant.so")
     subprocess.check_call(["gcc", "-shared", "-fopenmp", *objs, "-o", so, "-lm"])

@@ -75,6 +75,25 @@ def test_metric_identities_and_volume(N):
     assert np.abs(np.moveaxis(X, 0, 1) - g.X).max() < 1e-15
 
 
+def jacobian_det(N, g):
+    """det(dX/dxi) at every node from the nodal derivatives of X (numpy)."""
+    D = orc.diff_matrix(N)
+    np1 = N + 1
+    X = g.X.reshape(-1, 3, np1, np1, np1)  # [e][k][zeta][eta][xi]
+    d_xi = np.einsum("ia,ekcba->ekcbi", D, X)
+    d_eta = np.einsum("jb,ekcba->ekcja", D, X)
+    d_zeta = np.einsum("zc,ekcba->ekzba", D, X)
+    A = np.stack([d_xi, d_eta, d_zeta], axis=-1)  # [e][k][zeta][eta][xi][r]
+    return np.linalg.det(np.moveaxis(A, 1, -2)).reshape(g.J.shape)
+
+
+@pytest.mark.parametrize("N", [2, 3, 5])
+def test_jacobian_is_the_determinant_of_the_mapping_derivative(N):
+    g = orc.CurvedGeometry(N, (4, 3, 2), warp=0.15)
+    ref = jacobian_det(N, g)
+    assert np.abs(g.J - ref).max() < 1e-13 * np.abs(ref).max()
+
+
 def test_face_metric_terms_agree_across_interior_faces():
     # the curl form builds (J a^r) at a face from the face's own nodes, so the
     # two elements sharing an interior face compute the same normal vector
