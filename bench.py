@@ -268,8 +268,9 @@ def run_curved(args, timed):
     out = {"workload": "warped periodic box [-1,1]^3 (warp 0.15), manufactured solution "
                        "with source terms, CFL 0.5, CUDA-graph steps", "pid_4cubed": {}}
     k = max(1, min(args.steps, 5)) * 20
-    for solver, vf, sf in (("flux_differencing", "ranocha", "ranocha"),
-                           ("weak_form", "central", "hll")):
+    for solver, vf, sf in (() if args.no_pid else
+                           (("flux_differencing", "ranocha", "ranocha"),
+                            ("weak_form", "central", "hll"))):
         rows = {}
         for N in range(3, 8):
             n = (4, 4, 4)
@@ -286,7 +287,8 @@ def run_curved(args, timed):
                             "nodes": m.n_nodes}
             del m, u
         out["pid_4cubed"][solver] = rows
-    n = (64, 64, 64)
+    ne = args.curved_elements
+    n = (ne, ne, ne)
     m = Mesh(3, 3, n, warp=0.15)
     m.set_source("manufactured")
     xi, _ = lgl_nodes(3)
@@ -297,8 +299,8 @@ def run_curved(args, timed):
     kk = max(1, min(args.steps, 5))
     ms = timed(lambda: [m.step_cfl(u, cfl=0.5, graph=True) for _ in range(kk)])
     m.check()
-    out["warped_64cubed_n3"] = {"value": m.n_nodes * 5 * kk / (ms / 1e3), "unit": UNIT,
-                                "ms_per_step": ms / kk, "nodes": m.n_nodes}
+    out[f"warped_{ne}cubed_n3"] = {"value": m.n_nodes * 5 * kk / (ms / 1e3), "unit": UNIT,
+                                   "ms_per_step": ms / kk, "nodes": m.n_nodes}
     return out
 
 
@@ -541,6 +543,10 @@ def main():
     ap.add_argument("--no-fp32", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-curved", action="store_true")
+    ap.add_argument("--no-pid", action="store_true",
+                    help="curved section: skip the 4^3 PID sweep")
+    ap.add_argument("--curved-elements", type=int, default=64,
+                    help="elements per direction of the curved throughput case")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-ensemble", action="store_true")
     args = ap.parse_args()
