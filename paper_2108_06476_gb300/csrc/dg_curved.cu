@@ -13,18 +13,33 @@ cudaError_t geometry_n(const CGeom& cg, double* Ja, double* invJ, double* Jdet, 
   return cudaGetLastError();
 }
 
+template <int N, int VF, int EPB>
+cudaError_t volume_epb(double* u, double* du, const double* fs, const double* Ja,
+                       const double* invJ, const double* X, const Geom& g, const CTables& tb,
+                       unsigned* err, cudaStream_t st, const StageFuse& fz,
+                       const SourceArgs& src) {
+  using L = CLaunch<N>;
+  constexpr int SMEM = EPB * L::PER_ELEM;
+  cudaError_t e = allow_smem(curved_volume_kernel<N, VF, EPB>, SMEM);
+  if (e != cudaSuccess) return e;
+  const long long grid = (g.nelem + EPB - 1) / EPB;
+  curved_volume_kernel<N, VF, EPB><<<(unsigned)grid, EPB * L::LINES, SMEM, st>>>(
+      u, du, fs, Ja, invJ, X, g, tb, err, fz, src);
+  return cudaGetLastError();
+}
+
+// A CTA's FP64 work runs on one SM, whose FP64 pipe retires 2 lanes per
+// clock: meshes with fewer elements than about two CTAs per SM get one
+// element per CTA, spreading the work over more SMs (same arithmetic per
+// node, same results).
 template <int N, int VF>
 cudaError_t volume_n(double* u, double* du, const double* fs, const double* Ja,
                      const double* invJ, const double* X, const Geom& g, const CTables& tb,
                      unsigned* err, cudaStream_t st, const StageFuse& fz, const SourceArgs& src) {
   using L = CLaunch<N>;
-  constexpr int EPB = L::EPB;
-  cudaError_t e = allow_smem(curved_volume_kernel<N, VF, EPB>, L::SMEM);
-  if (e != cudaSuccess) return e;
-  const long long grid = (g.nelem + EPB - 1) / EPB;
-  curved_volume_kernel<N, VF, EPB><<<(unsigned)grid, EPB * L::LINES, L::SMEM, st>>>(
-      u, du, fs, Ja, invJ, X, g, tb, err, fz, src);
-  return cudaGetLastError();
+  if (L::EPB > 1 && g.nelem < 2LL * 152 * L::EPB)
+    return volume_epb<N, VF, 1>(u, du, fs, Ja, invJ, X, g, tb, err, st, fz, src);
+  return volume_epb<N, VF, L::EPB>(u, du, fs, Ja, invJ, X, g, tb, err, st, fz, src);
 }
 
 template <int N>
@@ -34,10 +49,12 @@ cudaError_t rhs_n(double* u, double* du, double* fs, const double* Ja, const dou
                   const SourceArgs& src) {
   if (parts & 1) {
     constexpr int NF = (N + 1) * (N + 1);
-    long long blocks = (g.nelem * NF + 255) / 256;
+    // small meshes: 64-thread blocks, so that the face nodes reach more SMs
+    const int threads = (g.nelem * NF < 152LL * 4 * 256) ? 64 : 256;
+    long long blocks = (g.nelem * NF + threads - 1) / threads;
     if (blocks > 152 * 32) blocks = 152 * 32;
     if (blocks < 1) blocks = 1;
-    curved_surface_kernel<N><<<dim3((unsigned)blocks, 3), 256, 0, st>>>(u, fs, Ja, g, sf);
+    curved_surface_kernel<N><<<dim3((unsigned)blocks, 3), threads, 0, st>>>(u, fs, Ja, g, sf);
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }

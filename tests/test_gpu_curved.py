@@ -87,6 +87,24 @@ def test_curved_rhs_paper_mesh_with_source(N):
     assert rel(gpu_rhs(N, n, u, source=True, t=t), ref) <= geometry_tol(g, u, source=True, t=t)
 
 
+def test_curved_rhs_large_mesh_sampled():
+    # 2,548 elements: the launch with 8 elements per CTA (smaller meshes run
+    # one element per CTA); compared on sampled elements incl. the corners
+    N, n = 3, (14, 14, 13)
+    g = orc.CurvedGeometry(N, n, 0.15)
+    u = noisy_warped_state(N, n, seed=30)
+    ne = int(np.prod(n))
+    rng = np.random.default_rng(31)
+    elems = np.unique(np.concatenate([[0, n[0] - 1, ne - n[0], ne - 1],
+                                      rng.choice(ne, 300, replace=False)]))
+    P = (N + 1) ** 3
+    ref = orc.curved_rhs(g, u, elems=elems).reshape(ne, 5 * P)[elems]
+    got = gpu_rhs(N, n, u).reshape(ne, 5 * P)[elems]
+    g1 = orc.CurvedGeometry(N, n, np.nextafter(0.15, 1.0))
+    r1 = orc.curved_rhs(g1, u, elems=elems).reshape(ne, 5 * P)[elems]
+    assert rel(got, ref) <= max(TOL, 30.0 * rel(r1, ref))
+
+
 def test_curved_path_without_warping_equals_cartesian_path():
     N, n = 3, (3, 2, 4)
     u = W.random_state(3, N, n, seed=8)
