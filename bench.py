@@ -255,6 +255,41 @@ def run_ensemble(args, timed, rank):
     return out
 
 
+def run_configs(args, timed):
+    """rhs-only rates (50 back-to-back dg_rhs calls, FP64 and FP32 kernels)
+    and the fused-step rate (FP64, CUDA-graph CFL steps) of the other
+    configured cases: 2D 16^2 N=3 and 3D 32^3 N=3 density waves, 3D 24^3 N=7
+    noisy density wave."""
+    import torch
+    from paper_2108_06476_gb300 import Mesh, lgl_nodes, workloads as W
+    out = {}
+    for name, d, N, ne, noisy in (("euler2d_n3_16sq_density_wave", 2, 3, 16, False),
+                                  ("euler3d_n3_32cubed_density_wave", 3, 3, 32, False),
+                                  ("euler3d_n7_24cubed_noisy_wave", 3, 7, 24, True)):
+        n = (ne,) * d
+        xi, _ = lgl_nodes(N)
+        gen = W.noisy_density_wave if noisy else W.density_wave
+        u0 = torch.from_numpy(gen(d, N, n, W.box(d), xi)).cuda()
+        row = {"nodes": ne ** d * (N + 1) ** d}
+        for prec in ("fp64", "fp32"):
+            m = Mesh(d, N, n, precision=prec)
+            du = m.empty_rhs()
+            m.rhs(u0, du)
+            ms = timed(lambda: [m.rhs(u0, du) for _ in range(50)])
+            row[f"rhs_{prec}"] = row["nodes"] * 50 / (ms / 1e3)
+            if prec == "fp64":
+                u = u0.clone()
+                for _ in range(3):
+                    m.step_cfl(u, cfl=0.5, graph=True)
+                ms = timed(lambda: [m.step_cfl(u, cfl=0.5, graph=True) for _ in range(10)])
+                row["step_fp64"] = row["nodes"] * 5 * 10 / (ms / 1e3)
+            m.check()
+            del m, du
+        out[name] = row
+    out["unit"] = UNIT
+    return out
+
+
 def run_curved(args, timed):
     """The paper's PID setup (Sec. 3.1) on the GPU: the warped periodic box
     [-1,1]^3 of 4^3 elements, the manufactured solution with its source
@@ -488,6 +523,11 @@ def run_ours(args, spec, world, rank, local):
     if not args.no_ensemble:
         ensemble = run_ensemble(args, timed, rank)
 
+    # ---- the other configured cases (rates only) ----
+    configs = None
+    if not args.no_configs:
+        configs = run_configs(args, timed)
+
     # ---- the paper's curvilinear benchmark setup ----
     curved = None
     if not args.no_curved:
@@ -521,6 +561,7 @@ def run_ours(args, spec, world, rank, local):
         "fp32": fp32,
         "ensemble": ensemble,
         "curved": curved,
+        "configs": configs,
         "e2e": e2e,
         "clocks": clk.summary(),
     }
@@ -543,6 +584,7 @@ def main():
     ap.add_argument("--no-fp32", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-curved", action="store_true")
+    ap.add_argument("--no-configs", action="store_true")
     ap.add_argument("--no-pid", action="store_true",
                     help="curved section: skip the 4^3 PID sweep")
     ap.add_argument("--curved-elements", type=int, default=64,

@@ -79,6 +79,23 @@ def test_smooth_wave_fp32_keeps_the_discretisation_error(orc):
     assert abs(e32 - e64) <= 1e-3 * e64
 
 
+def test_100_steps_32cubed_against_oracle(orc):
+    # the 3D 32^3 N = 3 density-wave configuration: 100 steps at the CFL
+    # time step of the initial state, GPU (fused steps) against the oracle;
+    # the state increments agree to the trajectory bar 1e-11
+    d, N, n = 3, 3, (32, 32, 32)
+    xi, _ = orc.lgl(N)
+    u0 = W.density_wave(d, N, n, W.box(d), xi)
+    dt = orc.max_dt(d, N, n, W.box(d), u0, 0.5)
+    uo = u0.copy()
+    for _ in range(100):
+        uo = orc.lsrk_step(d, N, n, W.box(d), uo, dt)
+    ug = run_gpu(d, N, n, u0, 100, dt, "fp64")
+    e = rel(ug - u0, uo - u0)
+    print(f"\n32^3 N=3, 100 steps of dt {dt:.4e}: increments rel L2 {e:.3e}")
+    assert e <= 1e-11
+
+
 @pytest.mark.skipif(os.environ.get("DG_LONG_TRAJECTORIES") != "1",
                     reason="full-size trajectories take about half an hour")
 @pytest.mark.parametrize("N,ne", [(3, 64), (7, 24)])
