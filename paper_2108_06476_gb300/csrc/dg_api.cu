@@ -423,11 +423,13 @@ int grid_for(long long work, int threads);
 // wave-speed reduction into m->speed (FP32 arithmetic on FP32 meshes);
 // copy_to (optional): device buffer that receives a copy of u
 int launch_speed(dg_mesh* m, const double* u, double* copy_to = nullptr) {
-  const int threads = 256;
+  // one warp per element; small meshes get one-warp blocks so that the FP64
+  // work (2 lanes per clock per SM) spreads over more SMs
+  const int threads = (m->nelem * 32 < 152LL * 4 * 256) ? 32 : 256;
   const int grid = grid_for(m->nelem * 32, threads);
   if (m->curved) {
     DG_CUDA(dg::curved_speed_launch(m->N, u, m->Ja, m->invJ, m->geom, m->speed, m->err, copy_to,
-                                    grid, m->stream),
+                                    grid, threads, m->stream),
             "curved speed kernel launch");
     return DG_OK;
   }

@@ -68,8 +68,8 @@ cudaError_t rhs_n(double* u, double* du, double* fs, const double* Ja, const dou
 template <int N>
 cudaError_t speed_n(const double* u, const double* Ja, const double* invJ, const Geom& g,
                     unsigned long long* out, unsigned* err, double* copy_to, int grid,
-                    cudaStream_t st) {
-  curved_speed_kernel<N><<<grid, 256, 0, st>>>(u, Ja, invJ, g, out, err, copy_to);
+                    int threads, cudaStream_t st) {
+  curved_speed_kernel<N><<<grid, threads, 0, st>>>(u, Ja, invJ, g, out, err, copy_to);
   return cudaGetLastError();
 }
 
@@ -105,8 +105,8 @@ cudaError_t curved_rhs_launch(int N, double* u, double* du, double* fs, const do
 
 cudaError_t curved_speed_launch(int N, const double* u, const double* Ja, const double* invJ,
                                 const Geom& g, unsigned long long* out, unsigned* err,
-                                double* copy_to, int grid, cudaStream_t st) {
-#define S(n) speed_n<n>(u, Ja, invJ, g, out, err, copy_to, grid, st)
+                                double* copy_to, int grid, int threads, cudaStream_t st) {
+#define S(n) speed_n<n>(u, Ja, invJ, g, out, err, copy_to, grid, threads, st)
   DG_CURVED_SWITCH(S)
 #undef S
 }

@@ -40,6 +40,6 @@ cudaError_t curved_rhs_launch(int N, double* u, double* du, double* fs, const do
                               int parts, const StageFuse& fz, const SourceArgs& src);
 cudaError_t curved_speed_launch(int N, const double* u, const double* Ja, const double* invJ,
                                 const Geom& g, unsigned long long* out, unsigned* err,
-                                double* copy_to, int grid, cudaStream_t st);
+                                double* copy_to, int grid, int threads, cudaStream_t st);
 
 }  // namespace dg

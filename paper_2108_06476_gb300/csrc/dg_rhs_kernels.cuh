@@ -563,23 +563,13 @@ cudaError_t allow_smem(K kernel, int bytes) {
 }
 
 // parts: bit 0 = surface kernel, bit 1 = volume kernel (both for an rhs)
-template <int D, int N, typename R>
-cudaError_t launch_rhs_dn(const double* u, R* du, R* fs, const Geom& g, const Tables<R>& tb,
-                          int vf, int sf, unsigned* err, cudaStream_t st, int parts,
-                          const StageFuse& fz) {
+template <int D, int N, typename R, int EPB>
+cudaError_t launch_volume_epb(const double* u, R* du, R* fs, const Geom& g, const Tables<R>& tb,
+                              int vf, unsigned* err, cudaStream_t st, const StageFuse& fz) {
   using L = Launch<D, N, R>;
-  constexpr int EPB = L::EPB;
-  if (parts & 1) {
-    const long long total = g.nelem * Shape<D, N>::LINES;
-    long long blocks = (total + 255) / 256;
-    if (blocks > 152 * 16) blocks = 152 * 16;
-    if (blocks < 1) blocks = 1;
-    surface_kernel<D, N, R><<<dim3((unsigned)blocks, D), 256, 0, st>>>(u, fs, g, sf, fz.pref);
-  }
-  if (!(parts & 2)) return cudaGetLastError();
   const long long grid = (g.nelem + EPB - 1) / EPB;
   const int threads = EPB * L::LINES;
-  constexpr int SM = L::SMEM;
+  constexpr int SM = EPB * L::PER_ELEM;
   cudaError_t e;
   if (vf == kVRanocha) {
     if ((e = allow_smem(volume_kernel<D, N, R, kVRanocha, EPB>, SM)) != cudaSuccess) return e;
@@ -595,6 +585,30 @@ cudaError_t launch_rhs_dn(const double* u, R* du, R* fs, const Geom& g, const Ta
         const_cast<double*>(u), du, fs, g, tb, err, fz);
   }
   return cudaGetLastError();
+}
+
+// Meshes with fewer elements than about two CTAs per SM run one element per
+// CTA (and the face kernel in 64-thread blocks), spreading the FP64 work (2
+// lanes per clock per SM) over more SMs; the arithmetic per node, and so the
+// result, is the same.
+template <int D, int N, typename R>
+cudaError_t launch_rhs_dn(const double* u, R* du, R* fs, const Geom& g, const Tables<R>& tb,
+                          int vf, int sf, unsigned* err, cudaStream_t st, int parts,
+                          const StageFuse& fz) {
+  using L = Launch<D, N, R>;
+  constexpr int EPB = L::EPB;
+  if (parts & 1) {
+    const long long total = g.nelem * Shape<D, N>::LINES;
+    const int threads = (total < 152LL * 4 * 256) ? 64 : 256;
+    long long blocks = (total + threads - 1) / threads;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    if (blocks < 1) blocks = 1;
+    surface_kernel<D, N, R><<<dim3((unsigned)blocks, D), threads, 0, st>>>(u, fs, g, sf, fz.pref);
+  }
+  if (!(parts & 2)) return cudaGetLastError();
+  if (EPB > 1 && g.nelem < 2LL * 152 * EPB)
+    return launch_volume_epb<D, N, R, 1>(u, du, fs, g, tb, vf, err, st, fz);
+  return launch_volume_epb<D, N, R, EPB>(u, du, fs, g, tb, vf, err, st, fz);
 }
 
 template <int D, typename R>

@@ -100,14 +100,26 @@ def test_100_steps_32cubed_against_oracle(orc):
                     reason="full-size trajectories take about half an hour")
 @pytest.mark.parametrize("N,ne", [(3, 64), (7, 24)])
 def test_full_size_noisy_wave_fp32_against_fp64(orc, N, ne):
+    # the FP64 mesh takes the CFL step of its own state each step (the
+    # paper's adaptive rule; a step held at its initial value is not stable
+    # for this input once the troughs thin out), the FP32 mesh takes the same
+    # step, and the last step ends exactly at t = 0.5
     d, n = 3, (ne,) * 3
     xi, _ = orc.lgl(N)
     u0 = W.noisy_density_wave(d, N, n, W.box(d), xi, seed=0)
-    m = Mesh(d, N, n)
-    steps, dt = fixed_step(m.max_dt(torch.from_numpy(u0).cuda(), 0.5))
-    u64 = run_gpu(d, N, n, u0, steps, dt, "fp64")
-    u32 = run_gpu(d, N, n, u0, steps, dt, "fp32")
-    e = rel(rho(u32, d, N), rho(u64, d, N))
-    print(f"\n{ne}^3 N={N} noisy, {steps} steps of dt {dt:.4e}: "
+    m64, m32 = Mesh(d, N, n), Mesh(d, N, n, precision="fp32")
+    a = torch.from_numpy(u0.copy()).cuda()
+    b = torch.from_numpy(u0.copy()).cuda()
+    t, steps = 0.0, 0
+    while t < T:
+        dt = m64.max_dt(a, 0.5)
+        dt = min(dt, T - t)
+        m64.step_dt(a, dt)
+        m32.step_dt(b, dt)
+        t += dt
+        steps += 1
+    assert m64.check() == 0 and m32.check() == 0
+    e = rel(rho(b.cpu().numpy(), d, N), rho(a.cpu().numpy(), d, N))
+    print(f"\n{ne}^3 N={N} noisy, {steps} adaptive steps to t = {T}: "
           f"rho rel L2 FP32 vs FP64 {e:.3e}")
     assert e <= 1e-4
