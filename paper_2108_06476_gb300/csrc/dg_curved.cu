@@ -29,16 +29,22 @@ cudaError_t volume_epb(double* u, double* du, const double* fs, const double* Ja
 }
 
 // A CTA's FP64 work runs on one SM, whose FP64 pipe retires 2 lanes per
-// clock: meshes with fewer elements than about two CTAs per SM get one
-// element per CTA, spreading the work over more SMs (same arithmetic per
-// node, same results).
+// clock: meshes with fewer elements than about two CTAs per SM run the
+// pair-parallel kernel (one element per CTA, one thread per line pair),
+// which shortens each thread's chain of FP64 work.
 template <int N, int VF>
 cudaError_t volume_n(double* u, double* du, const double* fs, const double* Ja,
                      const double* invJ, const double* X, const Geom& g, const CTables& tb,
                      unsigned* err, cudaStream_t st, const StageFuse& fz, const SourceArgs& src) {
   using L = CLaunch<N>;
-  if (L::EPB > 1 && g.nelem < 2LL * 152 * L::EPB)
-    return volume_epb<N, VF, 1>(u, du, fs, Ja, invJ, X, g, tb, err, st, fz, src);
+  if (g.nelem < 2LL * 152 * L::EPB) {
+    using C = CPairs<N>;
+    cudaError_t e = allow_smem(curved_volume_pp_kernel<N, VF>, C::SMEM);
+    if (e != cudaSuccess) return e;
+    curved_volume_pp_kernel<N, VF><<<(unsigned)g.nelem, C::THREADS, C::SMEM, st>>>(
+        u, du, fs, Ja, invJ, X, g, tb, err, fz, src);
+    return cudaGetLastError();
+  }
   return volume_epb<N, VF, L::EPB>(u, du, fs, Ja, invJ, X, g, tb, err, st, fz, src);
 }
 

@@ -418,6 +418,177 @@ __global__ void __launch_bounds__(EPB*(N + 1) * (N + 1))
   }
 }
 
+// ---- volume, pair-parallel variant for small meshes ----
+// One element per CTA; per direction, one thread per (line, node pair)
+// evaluates the contravariant flux into shared memory, then one thread per
+// node sums its line's pairs in ascending partner order and adds the
+// lifting: the order of the line-owning kernel above, with the pair work
+// spread over LINES * N (N+1) / 2 threads instead of LINES (a tiny mesh does
+// not fill the GPU, and each thread's FP64 chain is its latency).
+template <int N>
+struct CPairs {
+  static constexpr int NP = N + 1, P = NP * NP * NP, LINES = NP * NP;
+  static constexpr int NPAIRS = N * (N + 1) / 2;
+  static constexpr int WORK = LINES * NPAIRS;
+  static constexpr int THREADS = WORK < 512 ? ((WORK + 31) / 32) * 32 : 512;
+  static constexpr int SMEM = (9 + 3 + 5) * P * (int)sizeof(double) + WORK * 5 * (int)sizeof(double);
+};
+
+// pair (a, b), a < b, of index p in the order (0,1), (0,2), ..., (0,N), (1,2), ...
+template <int N>
+__device__ __forceinline__ void pair_of(int p, int& a, int& b) {
+  a = 0;
+  while (p >= N - a) {
+    p -= N - a;
+    ++a;
+  }
+  b = a + 1 + p;
+}
+template <int N>
+__device__ __forceinline__ int pair_index(int a, int b) {  // a < b
+  return a * N - a * (a - 1) / 2 + (b - a - 1);
+}
+
+// line l and position i along direction r of a node (inverse of line_node)
+template <int N>
+__device__ __forceinline__ void line_of(int r, int node, int& l, int& i) {
+  constexpr int NP = N + 1;
+  if (r == 0) {
+    l = node / NP;
+    i = node % NP;
+  } else if (r == 1) {
+    i = (node / NP) % NP;
+    l = node % NP + NP * (node / (NP * NP));
+  } else {
+    i = node / (NP * NP);
+    l = node % (NP * NP);
+  }
+}
+
+template <int N, int VF>
+__global__ void __launch_bounds__(CPairs<N>::THREADS)
+    curved_volume_pp_kernel(double* u, double* __restrict__ du, const double* __restrict__ fs,
+                            const double* __restrict__ Ja, const double* __restrict__ invJ,
+                            const double* __restrict__ X, Geom g, CTables tb,
+                            unsigned* __restrict__ err, StageFuse fz, SourceArgs src) {
+  using C = CPairs<N>;
+  constexpr int NP = C::NP, P = C::P, NV = 5, LINES = C::LINES, NPAIRS = C::NPAIRS;
+  extern __shared__ __align__(16) unsigned char dg_smem[];
+  double(*sp)[P] = reinterpret_cast<double(*)[P]>(dg_smem);                         // [9][P]
+  double(*sg)[P] = reinterpret_cast<double(*)[P]>(dg_smem + sizeof(double) * 9 * P);  // [3][P]
+  double(*sa)[P] = reinterpret_cast<double(*)[P]>(dg_smem + sizeof(double) * 12 * P); // [5][P]
+  double* sf = reinterpret_cast<double*>(dg_smem + sizeof(double) * 17 * P);          // [WORK][5]
+  const int e = blockIdx.x;
+  __shared__ int s_left[3];
+  if (threadIdx.x < 3) s_left[threadIdx.x] = neighbour32(g, e, threadIdx.x, -1);
+  unsigned bad = 0;
+  for (int node = threadIdx.x; node < P; node += blockDim.x) {
+    double c[NV], rr;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) c[v] = u[((long long)e * NV + v) * P + node];
+    const Prim<double, 3> q = prim_rcp<3>(c, g.gm1, rr);
+    bad |= prim_check(q);
+    node_slots<VF, double>(q.rho, q.p, g.gm1, sp[0][node], sp[1][node]);
+    sp[2][node] = 0.5 * q.p;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      sp[3 + k][node] = q.v[k];
+      sp[6 + k][node] = 0.5 * q.v[k];
+    }
+#pragma unroll
+    for (int v = 0; v < NV; ++v) sa[v][node] = 0.0;
+  }
+  if (bad) atomicOr(err, bad);
+  const long long base = (long long)g.nelem * LINES;
+#pragma unroll 1
+  for (int r = 0; r < 3; ++r) {
+    for (int node = threadIdx.x; node < P; node += blockDim.x) {
+#pragma unroll
+      for (int k = 0; k < 3; ++k)
+        sg[k][node] = 0.5 * Ja[(((long long)e * 3 + r) * 3 + k) * P + node];
+    }
+    __syncthreads();
+    for (int w = threadIdx.x; w < C::WORK; w += blockDim.x) {
+      const int l = w / NPAIRS;
+      int a, b;
+      pair_of<N>(w % NPAIRS, a, b);
+      const int na = line_node_rt<3, N>(r, l, a), nb = line_node_rt<3, N>(r, l, b);
+      CPrim qa, qb;
+      double gv[3], f[NV];
+      qa.s0 = sp[0][na];
+      qa.s1 = sp[1][na];
+      qa.hp = sp[2][na];
+      qb.s0 = sp[0][nb];
+      qb.s1 = sp[1][nb];
+      qb.hp = sp[2][nb];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        qa.v[k] = sp[3 + k][na];
+        qa.hv[k] = sp[6 + k][na];
+        qb.v[k] = sp[3 + k][nb];
+        qb.hv[k] = sp[6 + k][nb];
+        gv[k] = sg[k][na] + sg[k][nb];
+      }
+      if (VF == kVRanocha) ranocha_contra(qa, qb, gv, f);
+      else generic_contra<VF>(qa, qb, gv, g.gm1inv, f);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) sf[w * NV + v] = f[v];
+    }
+    __syncthreads();
+    for (int node = threadIdx.x; node < P; node += blockDim.x) {
+      int l, i;
+      line_of<N>(r, node, l, i);
+      double acc[NV];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) acc[v] = 0.0;
+      for (int j = 0; j < NP; ++j) {
+        if (j == i) continue;
+        const int p = j < i ? pair_index<N>(j, i) : pair_index<N>(i, j);
+        const double dij = tb.Ds[i][j];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) acc[v] = fma(dij, sf[(l * NPAIRS + p) * NV + v], acc[v]);
+      }
+      if (i == N) {
+#pragma unroll
+        for (int v = 0; v < NV; ++v)
+          acc[v] = fma(tb.liftR, fs[(long long)(r * NV + v) * base + (long long)e * LINES + l], acc[v]);
+      }
+      if (i == 0) {
+#pragma unroll
+        for (int v = 0; v < NV; ++v)
+          acc[v] = fma(tb.liftL, fs[(long long)(r * NV + v) * base + (long long)s_left[r] * LINES + l],
+                       acc[v]);
+      }
+#pragma unroll
+      for (int v = 0; v < NV; ++v) sa[v][node] += acc[v];
+    }
+    __syncthreads();
+  }
+  const double dtv = fz.k ? *fz.dt : 0.0;
+  double* const uo = fz.u_out ? fz.u_out : u;
+  const double ts = src.kind ? source_time(src) : 0.0;
+  for (int node = threadIdx.x; node < P; node += blockDim.x) {
+    const double ij = invJ[(long long)e * P + node];
+    double S[NV] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    if (src.kind == kSourceManufactured)
+      manufactured_source(X[((long long)e * 3 + 0) * P + node], X[((long long)e * 3 + 1) * P + node],
+                          X[((long long)e * 3 + 2) * P + node], ts, g.gm1, S);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      const double val = fma(ij, sa[v][node], S[v]);
+      const long long idx = ((long long)e * NV + v) * P + node;
+      if (fz.k) {
+        double kk = dtv * val;
+        if (fz.a != 0.0) kk = fma(fz.a, fz.k[idx], kk);
+        fz.k[idx] = kk;
+        uo[idx] = u[idx] + fz.b * kk;
+      } else {
+        du[idx] = val;
+      }
+    }
+  }
+}
+
 // ---- wave speeds for the CFL step: per element sum_r max_nodes
 // (|v . J a^r| + c |J a^r|) / J, max over elements (ordered bits) ----
 template <int N>
