@@ -1020,9 +1020,6 @@ int dg_max_dt(dg_mesh* m, const double* u, double cfl, double* dt_out) {
   if (!valid_mesh(m) || !u || !dt_out || !(cfl > 0.0))
     return fail(DG_ERR_ARG, "dg_max_dt: bad argument");
   DG_CUDA(cudaMemsetAsync(m->speed, 0, sizeof(unsigned long long), m->stream), "dg_max_dt: clear");
-  const int threads = 256;
-  const int grid = grid_for(m->nelem * 32, threads);
-  const double s0 = 2.0 / m->h[0], s1 = 2.0 / m->h[1], s2 = 2.0 / m->h[2];
   int rc0 = launch_speed(m, u);
   if (rc0) return rc0;
   unsigned long long bits = 0;
