@@ -24,6 +24,7 @@ import argparse
 import hashlib
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -63,14 +64,23 @@ def volume_flops_per_node(d, N):
 KERNEL_SOURCES = ("dg_device.cuh", "dg_rhs_kernels.cuh", "dg_rhs_inst.cu")
 
 
+def _code_only(text):
+    """Source text without comments and whitespace (a comment edit does not
+    change a kernel)."""
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    return re.sub(r"\s+", "", text)
+
+
 def source_sha():
-    """Hash of the sources that define the rhs kernels (a committed ncu
-    figure is only used while they are unchanged)."""
+    """Hash of the code (comments and whitespace removed) of the sources that
+    define the rhs kernels: a committed ncu figure is only used while it is
+    unchanged."""
     h = hashlib.sha1()
     csrc = os.path.join(ROOT, "paper_2108_06476_gb300", "csrc")
     for fn in KERNEL_SOURCES:
-        with open(os.path.join(csrc, fn), "rb") as fh:
-            h.update(fn.encode() + fh.read())
+        with open(os.path.join(csrc, fn)) as fh:
+            h.update(fn.encode() + _code_only(fh.read()).encode())
     return h.hexdigest()[:12]
 
 

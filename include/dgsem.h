@@ -2,7 +2,8 @@
  * dgsem.h - C ABI of the GB300 (sm_103a) DGSEM library: the right-hand side
  * du/dt = rhs(u) of the discontinuous Galerkin spectral element method for the
  * 2D/3D compressible Euler equations (ideal gas) on a uniform periodic
- * Cartesian mesh, and the low-storage Runge-Kutta stage that consumes it.
+ * Cartesian mesh or on the warped periodic box of the paper's benchmark (3D),
+ * and the low-storage Runge-Kutta stage that consumes it.
  *
  * Paper: H. Ranocha et al., "Adaptive numerical simulations with Trixi.jl: A
  * case study of Julia for scientific computing" (2021).
@@ -12,6 +13,8 @@
  *   - surface fluxes (local Lax-Friedrichs, EC, HLL): Sec. 2.2, Sec. 3.1;
  *   - Carpenter-Kennedy 5-stage 4th-order low-storage RK and the CFL time
  *     step: Sec. 3.1; performance index PID: Sec. 3.1, Eq. (3);
+ *   - the curvilinear benchmark mesh (warped periodic box) and its
+ *     manufactured-solution problem: Sec. 3.1;
  *   - analysis integrals: Sec. 2.2.
  *
  * Conventions shared by every entry point:
@@ -21,7 +24,8 @@
  *     lexicographically with x fastest: e = ex + n0 (ey + n1 ez). Element
  *     (ex, ey, ez) covers [lo + ex h, lo + (ex+1) h] in each direction.
  *   - Buffers passed to compute calls are DEVICE pointers owned by the caller
- *     (the library never frees them), at least 16-byte aligned. The state u
+ *     (the library never frees them), at least 16-byte aligned; the one
+ *     exception, dg_step_cfl_host, takes a host buffer. The state u
  *     is always float64. The rhs output du is float64 in DG_FP64 precision and
  *     float32 in DG_FP32 precision.
  *   - The library owns the mesh object and its device scratch: the RK

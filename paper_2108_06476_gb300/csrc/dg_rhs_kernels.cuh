@@ -13,9 +13,10 @@
 //    a single time for both nodes, since f# is symmetric and the split-form
 //    matrix has a zero diagonal:
 //      du_a += Ds[a][b] f#(u_a, u_b),  du_b += Ds[b][a] f#(u_a, u_b).
-//    Epilogue: lifting of the face fluxes at the element's boundary nodes,
-//    du += liftR F*_R (node N) + liftL F*_L (node 0) per direction, and one
-//    coalesced store of du.
+//    Lifting of the face fluxes at the line ends, du += liftR F*_R (node N)
+//    + liftL F*_L (node 0), inside each direction phase. Epilogue: one
+//    coalesced store of du, or the fused stage update k <- A k + dt du,
+//    u <- u + B k.
 //
 // FP32 kernels keep the pressure relative to a per-element reference P_e
 // (P_e = fl32((gamma-1) E at the element's first node); p' = p - P_e is formed
