@@ -1,0 +1,33 @@
+"""Host-side logic of bench.py (CPU only): the kernel-source hash that decides
+whether a committed ncu figure still describes the kernels, and the lookup of
+that figure."""
+import json
+
+import bench
+
+
+def test_code_only_drops_comments_and_whitespace():
+    a = "int f(int x) {  // the identity\n  return x; /* plain */ }\n"
+    b = "int f(int x){return x;}"
+    assert bench._code_only(a) == bench._code_only(b)
+    assert bench._code_only(a) != bench._code_only("int f(int x){return x+1;}")
+
+
+def test_committed_traffic_is_used_only_for_the_hashed_sources(tmp_path, monkeypatch):
+    rec = {"fp64_volume_3d_n3": {"bytes_per_node": 182.4, "fp64_flops_executed_per_node": 497.2,
+                                 "src_sha": bench.source_sha()}}
+    (tmp_path / "profiles").mkdir()
+    (tmp_path / "profiles" / "dram_traffic.json").write_text(json.dumps(rec))
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    monkeypatch.setattr(bench, "source_sha", lambda: rec["fp64_volume_3d_n3"]["src_sha"])
+    assert bench.ncu_traffic("fp64_volume_3d_n3") == 182.4
+    assert bench.ncu_record("fp64_volume_3d_n3", "fp64_flops_executed_per_node") == 497.2
+    assert bench.ncu_traffic("fp64_volume_2d_n3") is None
+    monkeypatch.setattr(bench, "source_sha", lambda: "000000000000")
+    assert bench.ncu_traffic("fp64_volume_3d_n3") is None
+
+
+def test_volume_flops_per_node_formula():
+    # 3D N = 3: 4.5 pairs per node of 81 flop, a 12-flop prologue and the
+    # lifting at the line ends
+    assert abs(bench.volume_flops_per_node(3, 3) - 391.5) < 1e-9
