@@ -96,14 +96,19 @@ def test_100_steps_32cubed_against_oracle(orc):
     assert e <= 1e-11
 
 
+T_FULL = 0.02
+
+
 @pytest.mark.skipif(os.environ.get("DG_LONG_TRAJECTORIES") != "1",
-                    reason="full-size trajectories take about half an hour")
+                    reason="full-size trajectories take a few minutes")
 @pytest.mark.parametrize("N,ne", [(3, 64), (7, 24)])
 def test_full_size_noisy_wave_fp32_against_fp64(orc, N, ne):
-    # the FP64 mesh takes the CFL step of its own state each step (the
-    # paper's adaptive rule; a step held at its initial value is not stable
-    # for this input once the troughs thin out), the FP32 mesh takes the same
-    # step, and the last step ends exactly at t = 0.5
+    # The full-size noisy wave does not reach t = 0.5: with the 1e-2
+    # perturbation on troughs where rho = 0.02 the unlimited scheme drives
+    # the density below zero near t = 0.05 at 64^3 (FP64, fixed or adaptive
+    # CFL steps alike). The comparison runs to t = 0.02: the FP64 mesh takes
+    # the CFL step of its own state each step, the FP32 mesh the same step,
+    # and the last step ends exactly at T_FULL.
     d, n = 3, (ne,) * 3
     xi, _ = orc.lgl(N)
     u0 = W.noisy_density_wave(d, N, n, W.box(d), xi, seed=0)
@@ -111,9 +116,8 @@ def test_full_size_noisy_wave_fp32_against_fp64(orc, N, ne):
     a = torch.from_numpy(u0.copy()).cuda()
     b = torch.from_numpy(u0.copy()).cuda()
     t, steps = 0.0, 0
-    while t < T:
-        dt = m64.max_dt(a, 0.5)
-        dt = min(dt, T - t)
+    while t < T_FULL:
+        dt = min(m64.max_dt(a, 0.5), T_FULL - t)
         m64.step_dt(a, dt)
         m32.step_dt(b, dt)
         t += dt
@@ -122,6 +126,6 @@ def test_full_size_noisy_wave_fp32_against_fp64(orc, N, ne):
             assert m64.check() == 0 and m32.check() == 0, (steps, t)
     assert m64.check() == 0 and m32.check() == 0
     e = rel(rho(b.cpu().numpy(), d, N), rho(a.cpu().numpy(), d, N))
-    print(f"\n{ne}^3 N={N} noisy, {steps} adaptive steps to t = {T}: "
+    print(f"\n{ne}^3 N={N} noisy, {steps} adaptive steps to t = {T_FULL}: "
           f"rho rel L2 FP32 vs FP64 {e:.3e}")
-    assert e <= 1e-4
+    assert e <= 1e-5
