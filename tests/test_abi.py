@@ -71,6 +71,30 @@ def test_mesh_create_rejects_bad_arguments(lib):
     assert lib.dg_mesh_destroy(None) == 0
 
 
+def test_curved_and_step_entry_points_reject_bad_arguments(lib):
+    # checked before any CUDA call, so this runs without a GPU
+    from paper_2108_06476_gb300 import dgsem
+    h = ctypes.c_void_p()
+    n = (ctypes.c_int * 3)(4, 4, 4)
+    for N, warp in ((0, 0.15), (8, 0.15), (3, 0.6), (3, float("nan"))):
+        rc = lib.dg_mesh_create_curved(N, n, warp, None, None, ctypes.byref(h))
+        assert rc == -1 and not h.value, (N, warp)
+        assert lib.dg_last_error()
+    assert lib.dg_mesh_create_curved(3, None, 0.15, None, None, ctypes.byref(h)) == -1
+    bad_n = (ctypes.c_int * 3)(4, 4, 0)
+    assert lib.dg_mesh_create_curved(3, bad_n, 0.15, None, None, ctypes.byref(h)) == -1
+    fp32 = dgsem._Options(1.4, 0, 0, 1)
+    assert lib.dg_mesh_create_curved(3, n, 0.15, ctypes.byref(fp32), None, ctypes.byref(h)) == -1
+    assert b"FP64" in lib.dg_last_error()
+    # a null mesh is rejected by every mesh call
+    t = ctypes.c_double()
+    assert lib.dg_set_source(None, 1) == -1
+    assert lib.dg_set_time(None, 0.0) == -1
+    assert lib.dg_get_time(None, ctypes.byref(t)) == -1
+    assert lib.dg_step_dt(None, None, 1e-3) == -1
+    assert lib.dg_step_cfl_host(None, None, 0.5, 1) == -1
+
+
 def test_built_for_sm_103a():
     from paper_2108_06476_gb300 import build
     assert "arch=compute_103a,code=sm_103a" in " ".join(build.ARCH)
