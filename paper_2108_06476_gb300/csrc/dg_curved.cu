@@ -22,6 +22,12 @@ cudaError_t volume_epb(double* u, double* du, const double* fs, const double* Ja
   constexpr int SMEM = EPB * L::PER_ELEM;
   cudaError_t e = allow_smem(curved_volume_kernel<N, VF, EPB>, SMEM);
   if (e != cudaSuccess) return e;
+  // the largest shared-memory carveout, so that the shared memory of the
+  // CTAs that the registers allow fits on one SM
+  e = cudaFuncSetAttribute(curved_volume_kernel<N, VF, EPB>,
+                           cudaFuncAttributePreferredSharedMemoryCarveout,
+                           cudaSharedmemCarveoutMaxShared);
+  if (e != cudaSuccess) return e;
   const long long grid = (g.nelem + EPB - 1) / EPB;
   curved_volume_kernel<N, VF, EPB><<<(unsigned)grid, EPB * L::LINES, SMEM, st>>>(
       u, du, fs, Ja, invJ, X, g, tb, err, fz, src);

@@ -333,8 +333,10 @@ __device__ __forceinline__ void curved_direction(int r, double (*sp)[9][(N + 1) 
     for (int v = 0; v < NV; ++v) sa[el][v][node[a]] += acc[a][v];
 }
 
+// N = 3: three CTAs per SM (168 registers, the shared memory of three
+// 8-element CTAs fits the maximum carveout)
 template <int N, int VF, int EPB>
-__global__ void __launch_bounds__(EPB*(N + 1) * (N + 1))
+__global__ void __launch_bounds__(EPB*(N + 1) * (N + 1), (N == 3 && EPB == 8) ? 3 : 1)
     curved_volume_kernel(double* u, double* __restrict__ du, const double* __restrict__ fs,
                          const double* __restrict__ Ja, const double* __restrict__ invJ,
                          const double* __restrict__ X, Geom g, CTables tb,
