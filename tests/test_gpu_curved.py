@@ -165,6 +165,25 @@ def test_curved_cfl_step_graph_and_time_step():
     assert m1.time == m2.time
 
 
+@pytest.mark.parametrize("n", [(4, 4, 4), (14, 14, 13)])
+def test_curved_host_state_step_equals_device_step(n):
+    # pinned host state: read by the wave-speed pass, written by the last
+    # stage (pair-parallel kernel on 4^3, the 8-element kernel on 2,548
+    # elements); the source follows the stage times of both
+    N = 3
+    u0 = noisy_warped_state(N, n, seed=40)
+    m1, m2 = Mesh(3, N, n, warp=0.15), Mesh(3, N, n, warp=0.15)
+    for m in (m1, m2):
+        m.set_source("manufactured")
+    ud = torch.from_numpy(u0.copy()).cuda()
+    for _ in range(2):
+        m1.step_cfl(ud, cfl=0.5)
+    uh = torch.from_numpy(u0.copy()).pin_memory()
+    m2.step_cfl_host(uh, cfl=0.5, n_steps=2)
+    assert np.array_equal(uh.numpy(), ud.cpu().numpy())
+    assert m1.time == m2.time
+
+
 def test_curved_integrals():
     N, n = 3, (2, 3, 2)
     g = orc.CurvedGeometry(N, n, 0.15)
