@@ -19,6 +19,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "dgsem_oracle.c")
 _SRC_CURVED = os.path.join(_HERE, "dgsem_curved.c")
+_SRC_MHD = os.path.join(_HERE, "dgsem_mhd.c")
 _SO = os.path.join(_HERE, "liboracle.so")
 _lib = None
 
@@ -31,8 +32,9 @@ def build(force: bool = False) -> str:
     """Compile the oracle with gcc (-O2 -ffp-contract=off, OpenMP): with
     double, with double complex (complex-step JVP) and with long double (the
     extended-precision evaluation used to measure FP64 rounding errors), plus
-    the curvilinear-mesh operator (double)."""
-    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_SRC_CURVED))
+    the curvilinear-mesh operator and the MHD operator (double)."""
+    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_SRC_CURVED),
+                 os.path.getmtime(_SRC_MHD))
     if not force and os.path.exists(_SO) and os.path.getmtime(_SO) >= newest:
         return _SO
     bdir = os.path.join(_HERE, "_build")
@@ -42,12 +44,14 @@ def build(force: bool = False) -> str:
     o2 = os.path.join(bdir, "or_cstep.o")
     o3 = os.path.join(bdir, "or_ld.o")
     o4 = os.path.join(bdir, "or_curved.o")
+    o5 = os.path.join(bdir, "or_mhd.o")
     tmp = _SO + f".tmp{os.getpid()}"
     subprocess.check_call(["gcc", *flags, "-c", _SRC, "-o", o1])
     subprocess.check_call(["gcc", *flags, "-DOR_CSTEP", "-c", _SRC, "-o", o2])
     subprocess.check_call(["gcc", *flags, "-DOR_LONGDOUBLE", "-c", _SRC, "-o", o3])
     subprocess.check_call(["gcc", *flags, "-c", _SRC_CURVED, "-o", o4])
-    subprocess.check_call(["gcc", "-shared", "-fopenmp", o1, o2, o3, o4, "-o", tmp, "-lm"])
+    subprocess.check_call(["gcc", *flags, "-c", _SRC_MHD, "-o", o5])
+    subprocess.check_call(["gcc", "-shared", "-fopenmp", o1, o2, o3, o4, o5, "-o", tmp, "-lm"])
     os.replace(tmp, _SO)
     return _SO
 
@@ -86,6 +90,15 @@ def _declare(L):
         L.or_curved_max_dt.restype = ctypes.c_double
         L.or_manufactured_state.argtypes = [ctypes.c_double, _dp, _dp]
         L.or_manufactured_source.argtypes = [ctypes.c_double, ctypes.c_double, _dp, _dp]
+    if hasattr(L, "or_mhd_rhs"):
+        L.or_mhd_flux.argtypes = [ctypes.c_int, ctypes.c_double, _dp, _dp]
+        L.or_mhd_fast_speed.argtypes = [ctypes.c_int, ctypes.c_double, _dp]
+        L.or_mhd_fast_speed.restype = ctypes.c_double
+        L.or_mhd_llf.argtypes = [ctypes.c_int, ctypes.c_double, _dp, _dp, _dp]
+        L.or_mhd_rhs.argtypes = [ctypes.c_int, _ip, _dp, ctypes.c_double, ctypes.c_int, _dp, _dp,
+                                 _llp, ctypes.c_longlong, ctypes.c_int]
+        L.or_mhd_max_dt.argtypes = [ctypes.c_int, _ip, _dp, ctypes.c_double, ctypes.c_double, _dp]
+        L.or_mhd_max_dt.restype = ctypes.c_double
     return L
 
 
@@ -97,10 +110,11 @@ def lib():
     return _lib
 
 
-def build_variant(src_text: str, out_dir: str, curved_text: str | None = None) -> str:
+def build_variant(src_text: str, out_dir: str, curved_text: str | None = None,
+                  mhd_text: str | None = None) -> str:
     """Compile a (modified) copy of the oracle source into out_dir, for tests
-    that plant mistakes and check that the pins catch them; curved_text, when
-    given, replaces the curvilinear source as well."""
+    that plant mistakes and check that the pins catch them; curved_text and
+    mhd_text, when given, replace the curvilinear and the MHD sources too."""
     src = os.path.join(out_dir, "variant.c")
     with open(src, "w") as fh:
         fh.write(src_text)
@@ -116,6 +130,13 @@ def build_variant(src_text: str, out_dir: str, curved_text: str | None = None) -
             fh.write(curved_text)
         o = os.path.join(out_dir, "v_curved.o")
         subprocess.check_call(["gcc", *flags, "-c", csrc, "-o", o])
+        objs.append(o)
+    if mhd_text is not None:
+        msrc = os.path.join(out_dir, "variant_mhd.c")
+        with open(msrc, "w") as fh:
+            fh.write(mhd_text)
+        o = os.path.join(out_dir, "v_mhd.o")
+        subprocess.check_call(["gcc", *flags, "-c", msrc, "-o", o])
         objs.append(o)
     so = os.path.join(out_dir, "libvariant.so")
     subprocess.check_call(["gcc", "-shared", "-fopenmp", *objs, "-o", so, "-lm"])
@@ -368,3 +389,51 @@ def manufactured_source_at(t, X, gamma=1.4):
     S = np.zeros(5)
     lib().or_manufactured_source(float(gamma), float(t), _d(x), _d(S))
     return S
+
+
+# ---- 3D ideal MHD on the Cartesian periodic mesh (dgsem_mhd.c) ----
+
+def mhd_flux(n, u, gamma=5.0 / 3.0):
+    f = np.zeros(8)
+    lib().or_mhd_flux(n, gamma, _d(_f64(u)), _d(f))
+    return f
+
+
+def mhd_fast_speed(n, u, gamma=5.0 / 3.0):
+    return lib().or_mhd_fast_speed(n, gamma, _d(_f64(u)))
+
+
+def mhd_llf(n, uL, uR, gamma=5.0 / 3.0):
+    f = np.zeros(8)
+    lib().or_mhd_llf(n, gamma, _d(_f64(uL)), _d(_f64(uR)), _d(f))
+    return f
+
+
+def mhd_rhs(N, n, dom, u, gamma=5.0 / 3.0, powell=True, elems=None, out=None, nthreads=0):
+    """du of the weak-form MHD operator (+ the Powell term)."""
+    u = _f64(u)
+    du = np.zeros_like(u) if out is None else out
+    if elems is None:
+        ep, ne = None, 0
+    else:
+        elems = np.ascontiguousarray(elems, dtype=np.int64)
+        ep, ne = elems.ctypes.data_as(_llp), len(elems)
+    rc = lib().or_mhd_rhs(N, _n3(n), _d(_f64(dom)), gamma, int(bool(powell)), _d(u), _d(du), ep,
+                          ne, nthreads)
+    if rc != 0:
+        raise ValueError("bad MHD rhs arguments")
+    return du
+
+
+def mhd_max_dt(N, n, dom, u, cfl=0.5, gamma=5.0 / 3.0):
+    return lib().or_mhd_max_dt(N, _n3(n), _d(_f64(dom)), gamma, cfl, _d(_f64(u)))
+
+
+def mhd_lsrk_step(N, n, dom, u, dt, gamma=5.0 / 3.0, powell=True, nthreads=0):
+    A, B, _ = lsrk_coefficients()
+    u = _f64(u).copy()
+    k = np.zeros_like(u)
+    for s in range(5):
+        du = mhd_rhs(N, n, dom, u, gamma, powell, nthreads=nthreads)
+        rk_stage(u, k, du, A[s], B[s], dt)
+    return u

@@ -1,0 +1,226 @@
+/*
+ * Plain FP64 CPU oracle of the DGSEM right-hand side for the 3D ideal
+ * magnetohydrodynamics (MHD) equations on a uniform periodic Cartesian mesh.
+ *
+ * TEST INFRASTRUCTURE ONLY, like dgsem_oracle.c (whose basis routines it
+ * calls): only tests/, __graft_entry__.smoke() and the cpu_baseline /
+ * reference legs of bench.py use it; it shares nothing with the CUDA library.
+ *
+ * What it follows (paper: "Adaptive numerical simulations with Trixi.jl"):
+ *   - Sec. 3.1 runs the 3D ideal MHD equations (Alfven wave propagation)
+ *     with a weak-form solver and notes that the MHD discretisations need
+ *     non-conservative terms; the weak form is the split form with the
+ *     central volume flux (Sec. 3.1, gassner2016split);
+ *   - ideal MHD, u = (rho, rho v, E, B), E = p/(gamma-1) + rho|v|^2/2 +
+ *     |B|^2/2, flux in direction n:
+ *       (rho v_n, rho v_n v + (p + |B|^2/2) e_n - B_n B,
+ *        v_n (E + p + |B|^2/2) - B_n (v.B), v_n B - B_n v);
+ *   - the non-conservative (Powell) term -(div B) Phi(u),
+ *     Phi = (0, B, v.B, v), with div B discretised like the flux divergence:
+ *     the split form with the central two-point value (B_i + B_m)/2 and the
+ *     interface average of the two traces (this equals the nodal derivative
+ *     of the interpolant plus the SBP correction toward the interface
+ *     average);
+ *   - local Lax-Friedrichs at the faces with lambda = max(|v_n,L|, |v_n,R|) +
+ *     max(c_f,L, c_f,R), c_f the fast magnetosonic speed in direction n:
+ *       c_f^2 = (a^2 + b^2 + sqrt((a^2 + b^2)^2 - 4 a^2 b_n^2)) / 2,
+ *       a^2 = gamma p / rho, b^2 = |B|^2 / rho, b_n^2 = B_n^2 / rho.
+ * Readings (the paper gives no formulas): the weak form with the Powell
+ * term in this form, the LLF wave speed, the Alfven wave of the tests.
+ *
+ * du_i = -(2/h) sum_dir [ sum_m Dt_im f#(u_i, u_m) + delta_iN F*_R/w_N
+ *                          - delta_i0 F*_L/w_0 ]
+ *        - Phi(u_i) (2/h) sum_dir [ sum_m Dt_im (B_i + B_m)/2 + delta_iN {B}_R/w_N
+ *                                   - delta_i0 {B}_L/w_0 ]
+ * (B = B_dir, {B} the average of the two traces), f# the central flux, each
+ * pair evaluated for the node it updates, every face value once per
+ * adjacent element.
+ */
+#include <math.h>
+#include <stdlib.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+int or_dtilde(int N, double *Dt, double *w);
+
+#define MV 8
+#define NPMAX 16
+
+/* primitive (rho, v, p) of an MHD state */
+static void mhd_prim(double gamma, const double *u, double *rho, double *v, double *p) {
+  *rho = u[0];
+  for (int k = 0; k < 3; ++k) v[k] = u[1 + k] / u[0];
+  const double v2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+  const double b2 = u[5] * u[5] + u[6] * u[6] + u[7] * u[7];
+  *p = (gamma - 1.0) * (u[4] - 0.5 * u[0] * v2 - 0.5 * b2);
+}
+
+/* physical flux in direction n */
+void or_mhd_flux(int n, double gamma, const double *u, double *f) {
+  double rho, v[3], p;
+  mhd_prim(gamma, u, &rho, v, &p);
+  const double *B = u + 5;
+  const double b2 = B[0] * B[0] + B[1] * B[1] + B[2] * B[2];
+  const double vb = v[0] * B[0] + v[1] * B[1] + v[2] * B[2];
+  const double pt = p + 0.5 * b2;
+  f[0] = rho * v[n];
+  for (int k = 0; k < 3; ++k) f[1 + k] = rho * v[n] * v[k] - B[n] * B[k];
+  f[1 + n] += pt;
+  f[4] = v[n] * (u[4] + pt) - B[n] * vb;
+  for (int k = 0; k < 3; ++k) f[5 + k] = v[n] * B[k] - B[n] * v[k];
+}
+
+/* fast magnetosonic speed in direction n */
+double or_mhd_fast_speed(int n, double gamma, const double *u) {
+  double rho, v[3], p;
+  mhd_prim(gamma, u, &rho, v, &p);
+  const double *B = u + 5;
+  const double a2 = gamma * p / rho;
+  const double b2 = (B[0] * B[0] + B[1] * B[1] + B[2] * B[2]) / rho;
+  const double bn2 = B[n] * B[n] / rho;
+  const double s = a2 + b2;
+  return sqrt(0.5 * (s + sqrt(s * s - 4.0 * a2 * bn2)));
+}
+
+/* local Lax-Friedrichs flux in direction n */
+void or_mhd_llf(int n, double gamma, const double *uL, const double *uR, double *f) {
+  double fL[MV], fR[MV];
+  or_mhd_flux(n, gamma, uL, fL);
+  or_mhd_flux(n, gamma, uR, fR);
+  const double vL = uL[1 + n] / uL[0], vR = uR[1 + n] / uR[0];
+  const double lam = fmax(fabs(vL), fabs(vR)) +
+                     fmax(or_mhd_fast_speed(n, gamma, uL), or_mhd_fast_speed(n, gamma, uR));
+  for (int v = 0; v < MV; ++v) f[v] = 0.5 * (fL[v] + fR[v]) - 0.5 * lam * (uR[v] - uL[v]);
+}
+
+typedef struct {
+  int N, np;
+  int n[3];
+  double h[3];
+  long long nelem, P;
+} mmesh_t;
+
+static int mmesh_init(mmesh_t *m, int N, const int *n, const double *dom) {
+  if (N < 1 || N > 15) return -1;
+  m->N = N;
+  m->np = N + 1;
+  m->nelem = 1;
+  for (int k = 0; k < 3; ++k) {
+    if (n[k] < 1 || !(dom[2 * k + 1] > dom[2 * k])) return -1;
+    m->n[k] = n[k];
+    m->h[k] = (dom[2 * k + 1] - dom[2 * k]) / n[k];
+    m->nelem *= n[k];
+  }
+  m->P = (long long)m->np * m->np * m->np;
+  return 0;
+}
+
+static long long m_with(const mmesh_t *m, long long node, int r, int a) {
+  int c[3] = {(int)(node % m->np), (int)((node / m->np) % m->np),
+              (int)(node / ((long long)m->np * m->np))};
+  c[r] = a;
+  return c[0] + (long long)m->np * (c[1] + (long long)m->np * c[2]);
+}
+
+static int m_coord(const mmesh_t *m, long long node, int r) {
+  long long q = node;
+  for (int k = 0; k < r; ++k) q /= m->np;
+  return (int)(q % m->np);
+}
+
+static long long m_neighbour(const mmesh_t *m, long long e, int r, int s) {
+  int c[3] = {(int)(e % m->n[0]), (int)((e / m->n[0]) % m->n[1]),
+              (int)(e / ((long long)m->n[0] * m->n[1]))};
+  c[r] = (c[r] + s + m->n[r]) % m->n[r];
+  return c[0] + (long long)m->n[0] * (c[1] + (long long)m->n[1] * c[2]);
+}
+
+static void m_load(const mmesh_t *m, const double *u, long long e, long long node, double *out) {
+  for (int v = 0; v < MV; ++v) out[v] = u[(e * MV + v) * m->P + node];
+}
+
+/* du = rhs(u) for the listed elements (all when elems is NULL); powell = 0
+ * drops the non-conservative term. Returns 0 or -1 on bad arguments. */
+int or_mhd_rhs(int N, const int *n, const double *dom, double gamma, int powell, const double *u,
+               double *du, const long long *elems, long long n_elems, int nthreads) {
+  mmesh_t m;
+  if (mmesh_init(&m, N, n, dom)) return -1;
+  double Dt[NPMAX * NPMAX], w[NPMAX];
+  or_dtilde(N, Dt, w);
+  const long long count = elems ? n_elems : m.nelem;
+#ifdef _OPENMP
+  if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 4)
+#endif
+  for (long long s = 0; s < count; ++s) {
+    const long long e = elems ? elems[s] : s;
+    for (long long node = 0; node < m.P; ++node) {
+      double ui[MV], acc[MV], divb = 0.0;
+      m_load(&m, u, e, node, ui);
+      for (int v = 0; v < MV; ++v) acc[v] = 0.0;
+      for (int r = 0; r < 3; ++r) {
+        const int i = m_coord(&m, node, r);
+        double vol[MV], db = 0.0, fi[MV];
+        or_mhd_flux(r, gamma, ui, fi);
+        for (int v = 0; v < MV; ++v) vol[v] = 0.0;
+        for (int a = 0; a <= N; ++a) {
+          double um[MV], fm[MV];
+          m_load(&m, u, e, m_with(&m, node, r, a), um);
+          or_mhd_flux(r, gamma, um, fm);
+          for (int v = 0; v < MV; ++v) vol[v] += Dt[i * m.np + a] * (0.5 * (fi[v] + fm[v]));
+          db += Dt[i * m.np + a] * (0.5 * (ui[5 + r] + um[5 + r]));
+        }
+        if (i == N) {
+          double uo[MV], fs[MV];
+          m_load(&m, u, m_neighbour(&m, e, r, +1), m_with(&m, node, r, 0), uo);
+          or_mhd_llf(r, gamma, ui, uo, fs);
+          for (int v = 0; v < MV; ++v) vol[v] += fs[v] / w[N];
+          db += 0.5 * (ui[5 + r] + uo[5 + r]) / w[N];
+        }
+        if (i == 0) {
+          double uo[MV], fs[MV];
+          m_load(&m, u, m_neighbour(&m, e, r, -1), m_with(&m, node, r, N), uo);
+          or_mhd_llf(r, gamma, uo, ui, fs);
+          for (int v = 0; v < MV; ++v) vol[v] -= fs[v] / w[0];
+          db -= 0.5 * (uo[5 + r] + ui[5 + r]) / w[0];
+        }
+        for (int v = 0; v < MV; ++v) acc[v] -= (2.0 / m.h[r]) * vol[v];
+        divb += (2.0 / m.h[r]) * db;
+      }
+      if (powell) {
+        double rho, v[3], p;
+        mhd_prim(gamma, ui, &rho, v, &p);
+        const double *B = ui + 5;
+        const double phi[MV] = {0.0, B[0], B[1], B[2], v[0] * B[0] + v[1] * B[1] + v[2] * B[2],
+                                v[0], v[1], v[2]};
+        for (int q = 0; q < MV; ++q) acc[q] -= phi[q] * divb;
+      }
+      for (int v = 0; v < MV; ++v) du[(e * MV + v) * m.P + node] = acc[v];
+    }
+  }
+  return 0;
+}
+
+/* CFL time step: dt = cfl 2 / ((N+1) max_e sum_dir (2/h_dir) max_nodes(|v_dir| + c_f,dir)). */
+double or_mhd_max_dt(int N, const int *n, const double *dom, double gamma, double cfl,
+                     const double *u) {
+  mmesh_t m;
+  if (mmesh_init(&m, N, n, dom)) return -1.0;
+  double worst = 0.0;
+  for (long long e = 0; e < m.nelem; ++e) {
+    double lam[3] = {0.0, 0.0, 0.0};
+    for (long long node = 0; node < m.P; ++node) {
+      double un[MV];
+      m_load(&m, u, e, node, un);
+      for (int r = 0; r < 3; ++r) {
+        const double s = fabs(un[1 + r] / un[0]) + or_mhd_fast_speed(r, gamma, un);
+        if (s > lam[r]) lam[r] = s;
+      }
+    }
+    double sum = 0.0;
+    for (int r = 0; r < 3; ++r) sum += (2.0 / m.h[r]) * lam[r];
+    if (sum > worst) worst = sum;
+  }
+  return cfl * 2.0 / ((N + 1) * worst);
+}

@@ -163,6 +163,46 @@ def manufactured_state(X, t=0.0, amplitude=0.1):
     return np.ascontiguousarray(u.reshape(-1))
 
 
+def alfven_wave(N, n, xi, t=0.0, amplitude=0.1, gamma=5.0 / 3.0, pressure=0.1):
+    """Circularly polarised Alfven wave on the periodic box [-1,1]^3 (3D ideal
+    MHD state (rho, rho v, E, B), E = p/(gamma-1) + rho|v|^2/2 + |B|^2/2):
+    rho = 1, p = pressure, B = n + A (sin phi e1 + cos phi e2),
+    v = -A (sin phi e1 + cos phi e2), phi = pi (x + y + z) - pi sqrt(3) t,
+    n = (1,1,1)/sqrt(3), e1 = (1,-1,0)/sqrt(2), e2 = n x e1: a wave moving
+    along n at the Alfven speed |B.n|/sqrt(rho) = 1, an exact solution."""
+    X = node_coordinates(3, N, n, box(3), xi)
+    phi = np.pi * (X[0] + X[1] + X[2]) - np.pi * np.sqrt(3.0) * t
+    nv = np.ones(3) / np.sqrt(3.0)
+    e1 = np.array([1.0, -1.0, 0.0]) / np.sqrt(2.0)
+    e2 = np.cross(nv, e1)
+    s, c = np.sin(phi), np.cos(phi)
+    B = [nv[k] + amplitude * (s * e1[k] + c * e2[k]) for k in range(3)]
+    v = [-amplitude * (s * e1[k] + c * e2[k]) for k in range(3)]
+    rho = np.ones_like(phi)
+    v2 = sum(vk * vk for vk in v)
+    b2 = sum(bk * bk for bk in B)
+    E = pressure / (gamma - 1.0) + 0.5 * rho * v2 + 0.5 * b2
+    u = np.stack([rho, *(rho * vk for vk in v), E, *B], axis=1)
+    return np.ascontiguousarray(u.reshape(-1))
+
+
+def mhd_random_state(N, n, seed=0, gamma=5.0 / 3.0):
+    """Seeded random physical MHD state: rho U[0.5, 2], v U[-0.5, 0.5]^3,
+    p U[0.5, 3], B U[-1, 1]^3 per node."""
+    rng = np.random.default_rng(seed)
+    ne = int(np.prod(n))
+    P = (N + 1) ** 3
+    rho = rng.uniform(0.5, 2.0, size=(ne, P))
+    v = [rng.uniform(-0.5, 0.5, size=(ne, P)) for _ in range(3)]
+    p = rng.uniform(0.5, 3.0, size=(ne, P))
+    B = [rng.uniform(-1.0, 1.0, size=(ne, P)) for _ in range(3)]
+    v2 = sum(vk * vk for vk in v)
+    b2 = sum(bk * bk for bk in B)
+    E = p / (gamma - 1.0) + 0.5 * rho * v2 + 0.5 * b2
+    u = np.stack([rho, *(rho * vk for vk in v), E, *B], axis=1)
+    return np.ascontiguousarray(u.reshape(-1))
+
+
 def box(d, lo=-1.0, hi=1.0):
     """Domain [lo, hi]^d as [lo0, hi0, lo1, hi1, ...]."""
     return np.array([lo, hi] * d, dtype=np.float64)
