@@ -349,6 +349,50 @@ def run_curved(args, timed):
     return out
 
 
+def mhd_volume_flops_per_node(N):
+    """Algorithmic FP64 flops per node of the MHD volume kernel (rhs only, a
+    fused multiply-add counted as two): 41 for the node's primitives and the
+    Powell term, and per direction 29 for the flux and the accumulation,
+    18 (N+1) for the nine D-row products, and the lifting (27 flops) at the 2
+    of N+1 line nodes that lie on a face."""
+    return 41 + 3 * (29 + 18 * (N + 1) + 54 / (N + 1))
+
+
+def run_mhd(args, timed, kernel_ms):
+    """3D ideal MHD (weak form, Powell term, LLF faces; the Alfven-wave
+    setting of Sec. 3.1) on the GPU: the circularly polarised Alfven wave on
+    ne^3 elements of degree 3, CFL 0.5 steps (device time step, CUDA graph),
+    and the kernel times of one rhs."""
+    import torch
+    from paper_2108_06476_gb300 import Mesh, lgl_nodes, workloads as W
+    ne, N = args.mhd_elements, 3
+    n = (ne, ne, ne)
+    m = Mesh(3, N, n, equations="mhd")
+    xi, _ = lgl_nodes(N)
+    u = torch.from_numpy(W.alfven_wave(N, n, xi, 0.0)).cuda()
+    du = m.empty_rhs()
+    for _ in range(max(3, args.warmup)):
+        m.step_cfl(u, cfl=0.5, graph=True)
+    kk = max(1, min(args.steps, 10))
+    ms = timed(lambda: [m.step_cfl(u, cfl=0.5, graph=True) for _ in range(kk)])
+    m.check()
+    vol_fused = kernel_ms(m, u, du, 6)
+    vol = kernel_ms(m, u, du, 2)
+    surf = kernel_ms(m, u, du, 1)
+    M = m.n_nodes
+    fl = mhd_volume_flops_per_node(N)
+    ach = fl * M / (vol / 1e3) / 1e12
+    return {"workload": f"3D ideal MHD, circularly polarised Alfven wave, {ne}^3 elements, "
+                        "N = 3, weak form + Powell term + LLF, CFL 0.5, CUDA-graph steps",
+            "value": M * 5 * kk / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / kk,
+            "nodes": M, "state_mb": M * 8 * 8 / 1e6,
+            "kernels_ms": {"volume_fused_stage": vol_fused, "volume_rhs_only": vol,
+                           "surface": surf},
+            "roofline": {"bound": "alu", "kernel": "mhd_volume_kernel (rhs only)",
+                         "flops_per_node": fl, "achieved": ach, "peak": FP64_PEAK_TFLOPS,
+                         "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS}}
+
+
 def max_over_ranks(ms, dist, device="cuda"):
     """The slowest rank's time (the job's time); identity without a process
     group."""
@@ -543,6 +587,11 @@ def run_ours(args, spec, world, rank, local):
     if not args.no_curved:
         curved = run_curved(args, timed)
 
+    # ---- 3D ideal MHD (Alfven wave) ----
+    mhd = None
+    if not args.no_mhd:
+        mhd = run_mhd(args, timed, kernel_ms)
+
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
@@ -571,6 +620,7 @@ def run_ours(args, spec, world, rank, local):
         "fp32": fp32,
         "ensemble": ensemble,
         "curved": curved,
+        "mhd": mhd,
         "configs": configs,
         "e2e": e2e,
         "clocks": clk.summary(),
@@ -600,6 +650,9 @@ def main():
     ap.add_argument("--curved-elements", type=int, default=64,
                     help="elements per direction of the curved throughput case")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-mhd", action="store_true")
+    ap.add_argument("--mhd-elements", type=int, default=64,
+                    help="MHD section: elements per dimension of the Alfven-wave mesh")
     ap.add_argument("--no-ensemble", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:

@@ -15,11 +15,14 @@
  *     step: Sec. 3.1; performance index PID: Sec. 3.1, Eq. (3);
  *   - the curvilinear benchmark mesh (warped periodic box) and its
  *     manufactured-solution problem: Sec. 3.1;
- *   - analysis integrals: Sec. 2.2.
+ *   - analysis integrals: Sec. 2.2;
+ *   - 3D ideal MHD (weak form, Powell term, LLF) for the Alfven-wave runs:
+ *     Sec. 3.1.
  *
  * Conventions shared by every entry point:
  *   - State layout u[e][v][k][j][i]: element-major; inside an element the
- *     d+2 conserved variables (rho, rho v_1..rho v_d, E) one after another,
+ *     d+2 conserved variables (rho, rho v_1..rho v_d, E) one after another
+ *     (eight, (rho, rho v, E, B), on an MHD mesh),
  *     each as (N+1)^d nodal values with i (x) fastest. Elements are ordered
  *     lexicographically with x fastest: e = ex + n0 (ey + n1 ez). Element
  *     (ex, ey, ez) covers [lo + ex h, lo + (ex+1) h] in each direction.
@@ -101,6 +104,25 @@ int dg_mesh_create(int d, int N, const int *elements_per_dim, const double *doma
 int dg_mesh_create_curved(int N, const int *elements_per_dim, double warp, const dg_options *opt,
                           void *cuda_stream, dg_mesh **out);
 
+/* Create a uniform periodic Cartesian mesh (as dg_mesh_create with d = 3) for
+ * the 3D ideal MHD equations, u = (rho, rho v_1..3, E, B_1..3), E = p/(gamma-1)
+ * + rho |v|^2/2 + |B|^2/2 (the magnetic Alfven-wave setting of Sec. 3.1; the
+ * paper gives no formulas, the discretisation below is this library's reading):
+ *   - weak-form DGSEM: the split form with the central two-point flux
+ *     (f(u_i) + f(u_m))/2, which is the strong-form derivative of the nodal
+ *     flux; local Lax-Friedrichs faces with lambda = max(|v_n,L|, |v_n,R|) +
+ *     max(c_f,L, c_f,R), c_f the fast magnetosonic speed;
+ *   - powell = 1 adds the non-conservative term -(div B) (0, B, v.B, v), div B
+ *     the same strong-form derivative of B_n with the interface average
+ *     {B_n} at the faces; powell = 0 leaves the conservative system.
+ * 1 <= N <= 7, gamma > 1, FP64. dg_rhs, dg_rhs_part, dg_rk_stage, dg_rk_reset,
+ * dg_step, dg_step_dt, dg_step_cfl (CFL rule with |v_dir| + c_f,dir),
+ * dg_step_graph, dg_step_cfl_host, dg_max_dt, dg_last_dt and dg_mesh_check
+ * accept such meshes; dg_rhs_vjp, dg_integrals and dg_set_source do not
+ * (DG_ERR_ARG). Errors: DG_ERR_ARG, DG_ERR_OOM, DG_ERR_CUDA. */
+int dg_mesh_create_mhd(int N, const int *elements_per_dim, const double *domain, double gamma,
+                       int powell, void *cuda_stream, dg_mesh **out);
+
 /* Source terms (curved meshes only): DG_SOURCE_MANUFACTURED adds
  * S = d_t u + div F(u) of the manufactured solution rho = 2 + 0.1 sin(pi (x +
  * y + z - t)), v = (1, 1, 1), E = rho^2 (the smooth Euler problem of the
@@ -120,7 +142,8 @@ int dg_get_time(dg_mesh *mesh, double *t);
  * NULL is accepted. */
 int dg_mesh_destroy(dg_mesh *mesh);
 
-/* Sizes: nodes M = n_elem (N+1)^d, variables d+2, values (d+2) M. */
+/* Sizes: nodes M = n_elem (N+1)^d, variables V = d+2 (8 on an MHD mesh),
+ * values V M. */
 int dg_mesh_info(const dg_mesh *mesh, long long *n_nodes, int *n_vars, long long *n_values);
 
 /* Change the CUDA stream used by subsequent calls on this mesh. */

@@ -23,6 +23,7 @@ FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE,
 
 UNITS = [("dg_api.cu", [], "dg_api.o"), ("dg_noalloc.cu", [], "dg_noalloc.o"),
          ("dg_curved.cu", [], "dg_curved.o"),
+         ("dg_mhd.cu", [], "dg_mhd.o"),
          ("dg_ensemble.cu", [], "dg_ensemble.o")] + [
     ("dg_rhs_inst.cu", [f"-DDG_INST_REAL={r}", f"-DDG_INST_DIM={d}"], f"dg_rhs_{r}_{d}.o")
     for r in ("double", "float") for d in (3, 2)

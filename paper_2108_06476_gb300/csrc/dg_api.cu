@@ -11,6 +11,7 @@
 
 #include "dgsem.h"
 #include "dg_curved_decl.cuh"
+#include "dg_mhd_decl.cuh"
 #include "dg_device.cuh"
 
 namespace dg {
@@ -75,6 +76,10 @@ struct dg_mesh {
   double* Jdet;        // J per node
   double* X;           // node coordinates [e][3][P]
   dg::CTables ctab;
+  // 3D ideal MHD meshes (dg_mesh_create_mhd)
+  int mhd;
+  int powell;
+  Tables<double> tmhd;  // Ds = -(2/h) D per direction, lifting factors
 };
 
 namespace {
@@ -429,6 +434,13 @@ int launch_speed(dg_mesh* m, const double* u, double* copy_to = nullptr) {
   // work (2 lanes per clock per SM) spreads over more SMs
   const int threads = (m->nelem * 32 < 152LL * 4 * 256) ? 32 : 256;
   const int grid = grid_for(m->nelem * 32, threads);
+  if (m->mhd) {
+    const double s[3] = {2.0 / m->h[0], 2.0 / m->h[1], 2.0 / m->h[2]};
+    DG_CUDA(dg::mhd_speed_launch(u, m->geom, (int)m->P, s, m->speed, m->err, copy_to, grid,
+                                 threads, m->stream),
+            "MHD speed kernel launch");
+    return DG_OK;
+  }
   if (m->curved) {
     DG_CUDA(dg::curved_speed_launch(m->N, u, m->Ja, m->invJ, m->geom, m->speed, m->err, copy_to,
                                     grid, threads, m->stream),
@@ -689,6 +701,51 @@ int dg_mesh_create_curved(int N, const int* epd, double warp, const dg_options* 
   return DG_OK;
 }
 
+int dg_mesh_create_mhd(int N, const int* epd, const double* domain, double gamma, int powell,
+                       void* cuda_stream, dg_mesh** out) {
+  if (out) *out = nullptr;
+  if (!out || !epd || !domain) return fail(DG_ERR_ARG, "dg_mesh_create_mhd: null argument");
+  if (!(gamma > 1.0) || (powell != 0 && powell != 1))
+    return fail(DG_ERR_ARG, "dg_mesh_create_mhd: gamma must be > 1 and powell 0 or 1");
+  const dg_options o = {gamma, DG_VFLUX_CENTRAL, DG_SFLUX_LLF, DG_FP64};
+  dg_mesh* m = nullptr;
+  int rc = dg_mesh_create(3, N, epd, domain, &o, cuda_stream, &m);
+  if (rc != DG_OK) return rc;
+  m->mhd = 1;
+  m->powell = powell;
+  // eight variables: the RK register and the face buffer (nine values per
+  // face node) are sized anew
+  cudaFree(m->k);
+  cudaFree(m->fs);
+  m->k = nullptr;
+  m->fs = nullptr;
+  m->nv = 8;
+  m->nvalues = m->nnodes * 8;
+  const long long nface = 3LL * 9 * m->nelem * (m->P / m->np);
+  cudaError_t e;
+  if ((e = cudaMalloc(&m->k, m->nvalues * sizeof(double))) != cudaSuccess ||
+      (e = cudaMalloc(&m->fs, nface * sizeof(double))) != cudaSuccess ||
+      (e = cudaMemsetAsync(m->k, 0, m->nvalues * sizeof(double), m->stream)) != cudaSuccess ||
+      (e = cudaStreamSynchronize(m->stream)) != cudaSuccess) {
+    rc = cuda_fail(e, "dg_mesh_create_mhd: cudaMalloc");
+    dg_mesh_destroy(m);
+    return rc;
+  }
+  long double x[8], w[8], D[8][8];
+  lgl_basis(N, x, w);
+  diff_matrix(N, x, D);
+  memset(&m->tmhd, 0, sizeof(m->tmhd));
+  for (int k = 0; k < 3; ++k) {
+    const long double sc = -2.0L / (long double)m->h[k];
+    for (int a = 0; a <= N; ++a)
+      for (int b = 0; b <= N; ++b) m->tmhd.Ds[k][a][b] = (double)(sc * D[a][b]);
+    m->tmhd.liftR[k] = (double)(sc / w[N]);
+    m->tmhd.liftL[k] = (double)(-sc / w[0]);
+  }
+  *out = m;
+  return DG_OK;
+}
+
 int dg_set_source(dg_mesh* m, int kind) {
   if (!valid_mesh(m)) return fail(DG_ERR_ARG, "dg_set_source: invalid mesh");
   if (kind != DG_SOURCE_NONE && kind != DG_SOURCE_MANUFACTURED)
@@ -775,7 +832,10 @@ int dg_rhs_part(dg_mesh* m, const double* u, void* du, int parts) {
     parts = 2;
   }
   cudaError_t e;
-  if (m->curved) {
+  if (m->mhd) {
+    e = dg::mhd_rhs_launch(m->N, u, (double*)du, (double*)m->fs, m->geom, m->tmhd, m->powell,
+                           m->err, m->stream, parts, fz);
+  } else if (m->curved) {
     dg::SourceArgs src;  // the source at the mesh time
     src.kind = m->source;
     src.t0 = m->t_dev;
@@ -797,7 +857,8 @@ int dg_rhs_part(dg_mesh* m, const double* u, void* du, int parts) {
 
 int dg_rhs_vjp(dg_mesh* m, const double* u, const double* w, double* ubar) {
   if (!valid_mesh(m) || !u || !w || !ubar) return fail(DG_ERR_ARG, "dg_rhs_vjp: null argument");
-  if (m->curved) return fail(DG_ERR_ARG, "dg_rhs_vjp: not available on curved meshes");
+  if (m->curved || m->mhd)
+    return fail(DG_ERR_ARG, "dg_rhs_vjp: not available on curved or MHD meshes");
   if (!m->fbar) {
     const long long n = 2LL * m->d * m->nv * m->nelem * (m->P / m->np);
     DG_CUDA(cudaMalloc(&m->fbar, n * sizeof(double)), "dg_rhs_vjp: cudaMalloc");
@@ -882,7 +943,10 @@ int enqueue_fused_stages(dg_mesh* m, double* u, double* out) {
     fz.b = kRkB[s];
     if (s == 4) fz.u_out = out;
     cudaError_t e;
-    if (m->curved) {
+    if (m->mhd) {
+      e = dg::mhd_rhs_launch(m->N, u, nullptr, (double*)m->fs, m->geom, m->tmhd, m->powell,
+                             m->err, m->stream, 3, fz);
+    } else if (m->curved) {
       dg::SourceArgs src;  // stage time t + c_s dt
       src.kind = m->source;
       src.t0 = m->t_dev;
@@ -1038,6 +1102,7 @@ int dg_max_dt(dg_mesh* m, const double* u, double cfl, double* dt_out) {
 
 int dg_integrals(dg_mesh* m, const double* u, double* out) {
   if (!valid_mesh(m) || !u || !out) return fail(DG_ERR_ARG, "dg_integrals: null argument");
+  if (m->mhd) return fail(DG_ERR_ARG, "dg_integrals: not available on MHD meshes");
   const int nq = m->d + 4;
   if (m->d == 2)
     integrals_kernel<2><<<kRedBlocks, kRedThreads, 0, m->stream>>>(u, m->geom, (int)m->P, m->wq,

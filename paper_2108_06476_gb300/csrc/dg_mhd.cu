@@ -1,0 +1,347 @@
+// 3D ideal magnetohydrodynamics (MHD) on the uniform periodic Cartesian mesh:
+// the weak-form DGSEM (the split form with the central volume flux, written
+// in its strong form) with the Powell non-conservative term and local
+// Lax-Friedrichs surface fluxes, as used for the Alfven-wave runs of
+// Sec. 3.1.
+//
+// Variables u = (rho, rho v, E, B), E = p/(gamma-1) + rho|v|^2/2 + |B|^2/2.
+// With D the LGL derivative matrix, Dn = -(2/h) D, liftR = -(2/h)/w_N and
+// liftL = +(2/h)/w_0 per direction, node i of a line gets
+//   du_i += sum_b Dn_ib f(u_b) + [i = N] liftR (F*_R - f(u_i))
+//                              + [i = 0] liftL (F*_L - f(u_i)),
+// which equals -(2/h) (sum_m Dt_im (f_i + f_m)/2 + [i = N] F*_R/w_N -
+// [i = 0] F*_L/w_0), Dt = 2D - W^-1 B, since the rows of Dt sum to -B_ii/w_i.
+// The Powell term is -Phi(u_i) div B_i with Phi = (0, B, v.B, v) and div B
+// the same strong-form derivative of B_n with the interface average {B_n} in
+// place of F*: the kernel accumulates -div B with the tables above and adds
+// Phi times it.
+//
+// Kernels of one rhs evaluation:
+//   mhd_surface_kernel: one thread per face node; F* = LLF(u_L, u_R) with
+//     lambda = max(|v_n,L|, |v_n,R|) + max(c_f,L, c_f,R), and {B_n}, stored as
+//     nine values per face node in fs[dir][q][e_left][l].
+//   mhd_volume_kernel: one CTA per EPB elements, one thread per node; per
+//     direction each thread writes f(u_i) (and B_n) to shared memory, then
+//     applies its line's row of Dn and the lifting; epilogue: the Powell
+//     term, then the store of du or the fused stage update.
+//   mhd_speed_kernel: one warp per element; sum_dir (2/h) max(|v_dir| + c_f)
+//     into the mesh's wave-speed word (CFL step).
+#include <cuda_runtime.h>
+
+#include "dg_device.cuh"
+#include "dg_mhd_decl.cuh"
+
+namespace dg {
+
+namespace {
+
+constexpr int kMV = 8;  // conserved MHD variables
+constexpr int kMQ = 9;  // face values: F* (8) and {B_n}
+
+struct MState {
+  double rho, v[3], p, B[3], vb, pt, E;
+};
+
+__device__ __forceinline__ MState mhd_state(const double* c, double gm1, unsigned& bad) {
+  MState s;
+  s.rho = c[0];
+  const double rr = 1.0 / c[0];
+  double mv = 0.0, b2 = 0.0;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    s.v[k] = c[1 + k] * rr;
+    s.B[k] = c[5 + k];
+    mv = fma(c[1 + k], s.v[k], mv);
+    b2 = fma(s.B[k], s.B[k], b2);
+  }
+  s.E = c[4];
+  s.p = gm1 * (c[4] - 0.5 * mv - 0.5 * b2);
+  s.pt = s.p + 0.5 * b2;
+  s.vb = s.v[0] * s.B[0] + s.v[1] * s.B[1] + s.v[2] * s.B[2];
+  if (!(s.rho > 0.0)) bad |= kErrRho;
+  if (!(s.p > 0.0)) bad |= kErrP;
+  if (!isfinite(s.rho) || !isfinite(s.p)) bad |= kErrNaN;
+  return s;
+}
+
+// physical flux in direction DIR (the B_DIR entry is zero)
+template <int DIR>
+__device__ __forceinline__ void mhd_flux(const MState& s, const double* c, double* f) {
+  const double vn = s.v[DIR], bn = s.B[DIR];
+  f[0] = c[1 + DIR];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) f[1 + k] = c[1 + DIR] * s.v[k] - bn * s.B[k];
+  f[1 + DIR] += s.pt;
+  f[4] = vn * (s.E + s.pt) - bn * s.vb;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) f[5 + k] = (k == DIR) ? 0.0 : vn * s.B[k] - bn * s.v[k];
+}
+
+// fast magnetosonic speed in direction DIR; the discriminant is >= (a^2 -
+// b^2)^2 >= 0 in exact arithmetic and is clamped at zero against rounding
+template <int DIR>
+__device__ __forceinline__ double fast_speed(const MState& s, double gamma) {
+  const double rr = 1.0 / s.rho;
+  const double a2 = gamma * s.p * rr;
+  const double b2 = (s.B[0] * s.B[0] + s.B[1] * s.B[1] + s.B[2] * s.B[2]) * rr;
+  const double bn2 = s.B[DIR] * s.B[DIR] * rr;
+  const double q = a2 + b2;
+  return sqrt(0.5 * (q + sqrt(fmax(q * q - 4.0 * a2 * bn2, 0.0))));
+}
+
+template <int N, int DIR>
+__device__ __forceinline__ void mhd_surface_body(const double* __restrict__ u,
+                                                 double* __restrict__ fs, const Geom& g,
+                                                 unsigned& bad) {
+  constexpr int NP = N + 1, P = NP * NP * NP, NF = NP * NP;
+  const long long total = g.nelem * NF;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const long long e = t / NF;
+    const int l = (int)(t % NF);
+    const long long er = neighbour(g, e, DIR, +1);
+    const int nl = line_node<3, N, DIR>(l, N), nr = line_node<3, N, DIR>(l, 0);
+    double cl[kMV], cr[kMV];
+#pragma unroll
+    for (int v = 0; v < kMV; ++v) {
+      cl[v] = u[(e * kMV + v) * P + nl];
+      cr[v] = u[(er * kMV + v) * P + nr];
+    }
+    const MState sl = mhd_state(cl, g.gm1, bad), sr = mhd_state(cr, g.gm1, bad);
+    double fl[kMV], fr[kMV];
+    mhd_flux<DIR>(sl, cl, fl);
+    mhd_flux<DIR>(sr, cr, fr);
+    const double lam = fmax(fabs(sl.v[DIR]), fabs(sr.v[DIR])) +
+                       fmax(fast_speed<DIR>(sl, g.gamma), fast_speed<DIR>(sr, g.gamma));
+    const long long base = g.nelem * NF;
+    const long long off = e * NF + l;
+#pragma unroll
+    for (int v = 0; v < kMV; ++v)
+      fs[(long long)(DIR * kMQ + v) * base + off] = 0.5 * (fl[v] + fr[v]) - 0.5 * lam * (cr[v] - cl[v]);
+    fs[(long long)(DIR * kMQ + 8) * base + off] = 0.5 * (cl[5 + DIR] + cr[5 + DIR]);
+  }
+}
+
+template <int N>
+__global__ void mhd_surface_kernel(const double* __restrict__ u, double* __restrict__ fs, Geom g,
+                                   unsigned* __restrict__ err) {
+  unsigned bad = 0;
+  if (blockIdx.y == 0) mhd_surface_body<N, 0>(u, fs, g, bad);
+  else if (blockIdx.y == 1) mhd_surface_body<N, 1>(u, fs, g, bad);
+  else mhd_surface_body<N, 2>(u, fs, g, bad);
+  if (bad) atomicOr(err, bad);
+}
+
+// one direction of the volume pass for the thread's node (index ia along DIR)
+template <int N, int DIR, int EPB>
+__device__ __forceinline__ void mhd_direction(const MState& s, const double* c,
+                                              double (*sf)[kMQ][(N + 1) * (N + 1) * (N + 1)],
+                                              int el, int node, bool active, long long e,
+                                              const Geom& g, const Tables<double>& tb,
+                                              const double* __restrict__ fs, double* acc,
+                                              double& divneg) {
+  constexpr int NP = N + 1, NF = NP * NP;
+  constexpr int STRIDE = DIR == 0 ? 1 : (DIR == 1 ? NP : NF);
+  double f[kMQ];
+  mhd_flux<DIR>(s, c, f);
+  f[8] = s.B[DIR];
+  if (active) {
+#pragma unroll
+    for (int q = 0; q < kMQ; ++q) sf[el][q][node] = f[q];
+  }
+  __syncthreads();
+  if (active) {
+    const int ia = (node / STRIDE) % NP;
+    const int first = node - ia * STRIDE;
+    double a[kMQ];
+#pragma unroll
+    for (int q = 0; q < kMQ; ++q) a[q] = 0.0;
+#pragma unroll
+    for (int b = 0; b < NP; ++b) {
+      const double w = tb.Ds[DIR][ia][b];
+#pragma unroll
+      for (int q = 0; q < kMQ; ++q) a[q] = fma(w, sf[el][q][first + b * STRIDE], a[q]);
+    }
+    if (ia == N || ia == 0) {
+      // face-node index of this line (see line_node)
+      const int l = DIR == 0 ? node / NP : (DIR == 1 ? node % NP + NP * (node / NF) : node % NF);
+      const long long ef = ia == N ? e : neighbour(g, e, DIR, -1);
+      const double lift = ia == N ? tb.liftR[DIR] : tb.liftL[DIR];
+      const long long base = g.nelem * NF;
+      const double* src = fs + (long long)DIR * kMQ * base + ef * NF + l;
+#pragma unroll
+      for (int q = 0; q < kMQ; ++q) a[q] = fma(lift, src[q * base] - f[q], a[q]);
+    }
+#pragma unroll
+    for (int q = 0; q < kMV; ++q) acc[q] += a[q];
+    divneg += a[8];
+  }
+  __syncthreads();
+}
+
+template <int N, int EPB>
+__global__ void __launch_bounds__(EPB*(N + 1) * (N + 1) * (N + 1))
+    mhd_volume_kernel(double* u, double* __restrict__ du, const double* __restrict__ fs, Geom g,
+                      Tables<double> tb, int powell, unsigned* __restrict__ err, StageFuse fz) {
+  constexpr int NP = N + 1, P = NP * NP * NP;
+  extern __shared__ __align__(16) unsigned char dg_smem[];
+  double(*sf)[kMQ][P] = reinterpret_cast<double(*)[kMQ][P]>(dg_smem);
+  const int el = threadIdx.x / P, node = threadIdx.x % P;
+  const long long e = (long long)blockIdx.x * EPB + el;
+  const bool active = e < g.nelem;
+  double c[kMV];
+  if (active) {
+#pragma unroll
+    for (int v = 0; v < kMV; ++v) c[v] = u[(e * kMV + v) * P + node];
+  } else {
+#pragma unroll
+    for (int v = 0; v < kMV; ++v) c[v] = (v == 0 || v == 4) ? 1.0 : 0.0;
+  }
+  unsigned bad = 0;
+  const MState s = mhd_state(c, g.gm1, bad);
+  if (bad && active) atomicOr(err, bad);
+  double acc[kMV], divneg = 0.0;
+#pragma unroll
+  for (int v = 0; v < kMV; ++v) acc[v] = 0.0;
+  mhd_direction<N, 0, EPB>(s, c, sf, el, node, active, e, g, tb, fs, acc, divneg);
+  mhd_direction<N, 1, EPB>(s, c, sf, el, node, active, e, g, tb, fs, acc, divneg);
+  mhd_direction<N, 2, EPB>(s, c, sf, el, node, active, e, g, tb, fs, acc, divneg);
+  if (!active) return;
+  if (powell) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      acc[1 + k] = fma(s.B[k], divneg, acc[1 + k]);
+      acc[5 + k] = fma(s.v[k], divneg, acc[5 + k]);
+    }
+    acc[4] = fma(s.vb, divneg, acc[4]);
+  }
+  const double dtv = fz.k ? *fz.dt : 0.0;
+  double* const uo = fz.u_out ? fz.u_out : u;
+#pragma unroll
+  for (int v = 0; v < kMV; ++v) {
+    const long long i = (e * kMV + v) * P + node;
+    if (fz.k) {
+      // the first stage (A = 0) neither reads k nor lets stale k values in
+      double kk = dtv * acc[v];
+      if (fz.a != 0.0) kk = fma(fz.a, fz.k[i], kk);
+      fz.k[i] = kk;
+      uo[i] = c[v] + fz.b * kk;
+    } else {
+      du[i] = acc[v];
+    }
+  }
+}
+
+__global__ void mhd_speed_kernel(const double* __restrict__ u, Geom g, int P, double s0, double s1,
+                                 double s2, unsigned long long* out, unsigned* err,
+                                 double* __restrict__ copy_to) {
+  const int lane = threadIdx.x & 31;
+  const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  double best = 0.0;
+  unsigned bad = 0;
+  for (long long e = warp; e < g.nelem; e += nwarps) {
+    double lam[3] = {0.0, 0.0, 0.0};
+    for (int node = lane; node < P; node += 32) {
+      double c[kMV];
+#pragma unroll
+      for (int v = 0; v < kMV; ++v) c[v] = u[(e * kMV + v) * P + node];
+      if (copy_to) {
+#pragma unroll
+        for (int v = 0; v < kMV; ++v) copy_to[(e * kMV + v) * P + node] = c[v];
+      }
+      const MState s = mhd_state(c, g.gm1, bad);
+      lam[0] = fmax(lam[0], fabs(s.v[0]) + fast_speed<0>(s, g.gamma));
+      lam[1] = fmax(lam[1], fabs(s.v[1]) + fast_speed<1>(s, g.gamma));
+      lam[2] = fmax(lam[2], fabs(s.v[2]) + fast_speed<2>(s, g.gamma));
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+      for (int off = 16; off > 0; off >>= 1)
+        lam[k] = fmax(lam[k], __shfl_xor_sync(0xffffffffu, lam[k], off));
+    double sum = s0 * lam[0];
+    sum = sum + s1 * lam[1];
+    sum = sum + s2 * lam[2];
+    best = fmax(best, sum);
+  }
+  __shared__ double sb[32];
+  if (lane == 0) sb[threadIdx.x >> 5] = best;
+  if (bad) atomicOr(err, bad);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double m = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmax(m, sb[w]);
+    atomicMax(out, (unsigned long long)__double_as_longlong(m));
+  }
+}
+
+// elements per CTA: about 256 threads
+template <int N>
+struct MLaunch {
+  static constexpr int P = (N + 1) * (N + 1) * (N + 1);
+  static constexpr int EPB = (256 / P) > 0 ? (256 / P) : 1;
+};
+
+template <int N, int EPB>
+cudaError_t mhd_volume_epb(const double* u, double* du, const double* fs, const Geom& g,
+                           const Tables<double>& tb, int powell, unsigned* err, cudaStream_t st,
+                           const StageFuse& fz) {
+  constexpr int P = MLaunch<N>::P;
+  constexpr int SMEM = EPB * kMQ * P * (int)sizeof(double);
+  auto kern = mhd_volume_kernel<N, EPB>;
+  if (SMEM > 48 * 1024) {
+    const cudaError_t e =
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
+    if (e != cudaSuccess) return e;
+  }
+  const long long grid = (g.nelem + EPB - 1) / EPB;
+  kern<<<(unsigned)grid, EPB * P, SMEM, st>>>(const_cast<double*>(u), du, fs, g, tb, powell, err,
+                                               fz);
+  return cudaGetLastError();
+}
+
+template <int N>
+cudaError_t mhd_rhs_n(const double* u, double* du, double* fs, const Geom& g,
+                      const Tables<double>& tb, int powell, unsigned* err, cudaStream_t st,
+                      int parts, const StageFuse& fz) {
+  constexpr int NF = (N + 1) * (N + 1);
+  if (parts & 1) {
+    const long long total = g.nelem * NF;
+    const int threads = (total < 152LL * 4 * 256) ? 64 : 256;
+    long long blocks = (total + threads - 1) / threads;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    if (blocks < 1) blocks = 1;
+    mhd_surface_kernel<N><<<dim3((unsigned)blocks, 3), threads, 0, st>>>(u, fs, g, err);
+  }
+  if (!(parts & 2)) return cudaGetLastError();
+  constexpr int EPB = MLaunch<N>::EPB;
+  if (EPB > 1 && g.nelem < 2LL * 152 * EPB)
+    return mhd_volume_epb<N, 1>(u, du, fs, g, tb, powell, err, st, fz);
+  return mhd_volume_epb<N, EPB>(u, du, fs, g, tb, powell, err, st, fz);
+}
+
+}  // namespace
+
+cudaError_t mhd_rhs_launch(int N, const double* u, double* du, double* fs, const Geom& g,
+                           const Tables<double>& tb, int powell, unsigned* err, cudaStream_t st,
+                           int parts, const StageFuse& fz) {
+  switch (N) {
+    case 1: return mhd_rhs_n<1>(u, du, fs, g, tb, powell, err, st, parts, fz);
+    case 2: return mhd_rhs_n<2>(u, du, fs, g, tb, powell, err, st, parts, fz);
+    case 3: return mhd_rhs_n<3>(u, du, fs, g, tb, powell, err, st, parts, fz);
+    case 4: return mhd_rhs_n<4>(u, du, fs, g, tb, powell, err, st, parts, fz);
+    case 5: return mhd_rhs_n<5>(u, du, fs, g, tb, powell, err, st, parts, fz);
+    case 6: return mhd_rhs_n<6>(u, du, fs, g, tb, powell, err, st, parts, fz);
+    case 7: return mhd_rhs_n<7>(u, du, fs, g, tb, powell, err, st, parts, fz);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t mhd_speed_launch(const double* u, const Geom& g, int P, const double* s,
+                             unsigned long long* out, unsigned* err, double* copy_to, int grid,
+                             int threads, cudaStream_t st) {
+  mhd_speed_kernel<<<grid, threads, 0, st>>>(u, g, P, s[0], s[1], s[2], out, err, copy_to);
+  return cudaGetLastError();
+}
+
+}  // namespace dg

@@ -1,0 +1,22 @@
+// Launchers of the 3D ideal MHD kernels (dg_mhd.cu), for the C ABI.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "dg_device.cuh"
+
+namespace dg {
+
+// One rhs evaluation (parts: bit 0 face kernel, bit 1 volume kernel); tb
+// holds Ds = -(2/h) D per direction and the lifting factors; fs holds
+// 3 * 9 * nelem * (N+1)^2 doubles; fz (optional) fuses the stage update.
+cudaError_t mhd_rhs_launch(int N, const double* u, double* du, double* fs, const Geom& g,
+                           const Tables<double>& tb, int powell, unsigned* err, cudaStream_t st,
+                           int parts, const StageFuse& fz);
+
+// Wave-speed reduction sum_dir s[dir] max(|v_dir| + c_f,dir) into out (as
+// ordered bits); copy_to (optional) receives a copy of u.
+cudaError_t mhd_speed_launch(const double* u, const Geom& g, int P, const double* s,
+                             unsigned long long* out, unsigned* err, double* copy_to, int grid,
+                             int threads, cudaStream_t st);
+
+}  // namespace dg

@@ -27,7 +27,7 @@ RK_B = (1432997174477.0 / 9575080441755.0, 5161836677717.0 / 13612068292357.0,
         1720146321549.0 / 2090206949498.0, 3134564353537.0 / 4481467310338.0,
         2277821191437.0 / 14882151754819.0)
 
-EXPORTS = ("dg_mesh_create", "dg_mesh_create_curved", "dg_set_source", "dg_set_time",
+EXPORTS = ("dg_mesh_create", "dg_mesh_create_curved", "dg_mesh_create_mhd", "dg_set_source", "dg_set_time",
            "dg_get_time", "dg_mesh_destroy", "dg_mesh_info", "dg_mesh_set_stream",
            "dg_lgl_nodes", "dg_rhs", "dg_rhs_part", "dg_rhs_vjp", "dg_rk_stage", "dg_rk_reset", "dg_step", "dg_step_cfl", "dg_step_graph",
            "dg_step_dt", "dg_step_cfl_host", "dg_last_dt", "dg_max_dt",
@@ -79,6 +79,8 @@ def load(path: str = SO_PATH):
     L.dg_step_dt.argtypes = [vp, vp, ctypes.c_double]
     L.dg_mesh_create_curved.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                         ctypes.c_double, vp, vp, vp]
+    L.dg_mesh_create_mhd.argtypes = [ctypes.c_int, ip, dp, ctypes.c_double, ctypes.c_int, vp,
+                                     ctypes.POINTER(vp)]
     L.dg_set_source.argtypes = [vp, ctypes.c_int]
     L.dg_set_time.argtypes = [vp, ctypes.c_double]
     L.dg_get_time.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
@@ -146,13 +148,17 @@ SOURCE = {"none": 0, "manufactured": 1}
 class Mesh:
     """A periodic DGSEM mesh on the current CUDA device: uniform Cartesian, or
     with warp given, the warped box [-1,1]^3 of the paper's curvilinear
-    benchmark (3D, FP64; warp = 0.15 is the paper's amplitude).
+    benchmark (3D, FP64; warp = 0.15 is the paper's amplitude). With
+    equations="mhd": the 3D ideal MHD equations (eight variables; weak form,
+    LLF faces, the Powell term unless powell=False; FP64; gamma defaults
+    to 5/3).
 
     State tensors are float64 CUDA tensors of n_values entries in the layout
     u[e][v][k][j][i]; rhs outputs are float64 (fp64) or float32 (fp32)."""
 
-    def __init__(self, d, N, n, domain=None, gamma=1.4, volume_flux="ranocha",
-                 surface_flux="llf", precision="fp64", stream=None, warp=None):
+    def __init__(self, d, N, n, domain=None, gamma=None, volume_flux="ranocha",
+                 surface_flux="llf", precision="fp64", stream=None, warp=None,
+                 equations="euler", powell=True):
         import torch
         self._torch = torch
         L = load()
@@ -161,6 +167,11 @@ class Mesh:
         self.d, self.N, self.n = int(d), int(N), tuple(int(x) for x in n)
         self.domain = tuple(float(x) for x in domain)
         self.precision = precision
+        self.equations = equations
+        if equations not in ("euler", "mhd"):
+            raise DGError(f"unknown equations {equations!r}")
+        if gamma is None:
+            gamma = 5.0 / 3.0 if equations == "mhd" else 1.4
         self.rhs_dtype = torch.float64 if precision == "fp64" else torch.float32
         opt = _Options(gamma, VFLUX[volume_flux], SFLUX[surface_flux], PRECISION[precision])
         n_arr = (ctypes.c_int * 3)(*(list(self.n) + [1] * (3 - len(self.n))))
@@ -169,7 +180,13 @@ class Mesh:
         st = stream if stream is not None else torch.cuda.current_stream()
         self._stream = st
         self.warp = warp
-        if warp is None:
+        if equations == "mhd":
+            if self.d != 3 or warp is not None or precision != "fp64":
+                raise DGError("MHD meshes are 3D, Cartesian and FP64")
+            _check(L.dg_mesh_create_mhd(self.N, n_arr, dom, float(gamma), int(bool(powell)),
+                                        ctypes.c_void_p(st.cuda_stream), ctypes.byref(h)),
+                   "dg_mesh_create_mhd")
+        elif warp is None:
             _check(L.dg_mesh_create(self.d, self.N, n_arr, dom, ctypes.byref(opt),
                                     ctypes.c_void_p(st.cuda_stream), ctypes.byref(h)),
                    "dg_mesh_create")

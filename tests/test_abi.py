@@ -95,6 +95,23 @@ def test_curved_and_step_entry_points_reject_bad_arguments(lib):
     assert lib.dg_step_cfl_host(None, None, 0.5, 1) == -1
 
 
+def test_mhd_mesh_create_rejects_bad_arguments(lib):
+    # checked before any CUDA call, so this runs without a GPU
+    h = ctypes.c_void_p()
+    n = (ctypes.c_int * 3)(4, 4, 4)
+    dom = (ctypes.c_double * 6)(-1, 1, -1, 1, -1, 1)
+    for N, gamma, powell in ((0, 5 / 3, 1), (8, 5 / 3, 1), (3, 1.0, 1), (3, 5 / 3, 2),
+                             (3, float("nan"), 0)):
+        rc = lib.dg_mesh_create_mhd(N, n, dom, gamma, powell, None, ctypes.byref(h))
+        assert rc == -1 and not h.value, (N, gamma, powell)
+        assert lib.dg_last_error()
+    assert lib.dg_mesh_create_mhd(3, None, dom, 5 / 3, 1, None, ctypes.byref(h)) == -1
+    bad_n = (ctypes.c_int * 3)(4, 0, 4)
+    assert lib.dg_mesh_create_mhd(3, bad_n, dom, 5 / 3, 1, None, ctypes.byref(h)) == -1
+    bad_dom = (ctypes.c_double * 6)(-1, 1, -1, 1, 2, 1)
+    assert lib.dg_mesh_create_mhd(3, n, bad_dom, 5 / 3, 1, None, ctypes.byref(h)) == -1
+
+
 def test_built_for_sm_103a():
     from paper_2108_06476_gb300 import build
     assert "arch=compute_103a,code=sm_103a" in " ".join(build.ARCH)

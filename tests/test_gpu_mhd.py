@@ -1,0 +1,198 @@
+"""GPU parity of the 3D ideal MHD path (weak form, Powell term, LLF faces;
+through the C ABI) against the FP64 CPU oracle.
+
+Bar: relative L2 error <= 1e-12, as for the Euler path. The GPU applies the
+strong-form derivative sum_b Dn_ib f_b plus the lifting of F* - f_i, the
+oracle the split form sum_m Dt_im (f_i + f_m)/2 plus F*/w: the same operator
+in another rounding order (the rows of Dt sum to -B_ii/w_i)."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from paper_2108_06476_gb300 import DGError, Mesh, workloads as W  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-12
+G = 5.0 / 3.0
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2108_06476_gb300 import build
+    build.build()
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def mesh(N, n, dom=None, powell=True):
+    return Mesh(3, N, n, tuple(W.box(3) if dom is None else dom), equations="mhd",
+                powell=powell)
+
+
+def gpu_rhs(N, n, u, dom=None, powell=True):
+    m = mesh(N, n, dom, powell)
+    du = m.rhs(torch.from_numpy(np.ascontiguousarray(u)).cuda())
+    assert m.check() == 0
+    return du.cpu().numpy()
+
+
+@pytest.mark.parametrize("powell", [True, False])
+@pytest.mark.parametrize("N", range(1, 8))
+def test_mhd_rhs_every_degree(orc, N, powell):
+    n = (3, 2, 2) if N < 6 else (2, 2, 1)
+    u = W.mhd_random_state(N, n, seed=40 + N, gamma=G)
+    ref = orc.mhd_rhs(N, n, W.box(3), u, G, powell)
+    got = gpu_rhs(N, n, u, powell=powell)
+    assert rel_l2(got, ref) <= TOL64, rel_l2(got, ref)
+
+
+@pytest.mark.parametrize("N,n", [(3, (5, 4, 3)), (4, (1, 1, 1)), (2, (1, 3, 2))])
+def test_mhd_rhs_ragged_and_single_element_meshes(orc, N, n):
+    dom = np.array([-1.0, 1.0, -0.5, 1.5, 0.0, 3.0])
+    u = W.mhd_random_state(N, n, seed=7, gamma=G)
+    ref = orc.mhd_rhs(N, n, dom, u, G, True)
+    got = gpu_rhs(N, n, u, dom=dom)
+    assert rel_l2(got, ref) <= TOL64, rel_l2(got, ref)
+
+
+@pytest.mark.parametrize("N,n", [(3, (4, 4, 4)), (5, (3, 3, 2))])
+def test_mhd_rhs_alfven_wave(orc, N, n):
+    xi, _ = orc.lgl(N)
+    u = W.alfven_wave(N, n, xi, 0.2, gamma=G)
+    ref = orc.mhd_rhs(N, n, W.box(3), u, G, True)
+    got = gpu_rhs(N, n, u)
+    assert rel_l2(got, ref) <= TOL64, rel_l2(got, ref)
+
+
+def _sample_elements(n, count, seed):
+    rng = np.random.default_rng(seed)
+    ne = int(np.prod(n))
+    corners = [0, ne - 1, n[0] - 1, ne - n[0]]
+    return np.unique(np.concatenate([corners, rng.choice(ne, size=count, replace=False)]))
+
+
+@pytest.mark.parametrize("N,ne,count", [(3, 64, 300), (7, 24, 40)])
+def test_mhd_rhs_full_size_sampled(orc, N, ne, count):
+    """The Alfven wave on the full-size meshes of the benchmark, the oracle on
+    a sample of elements including the domain's corners."""
+    n = (ne, ne, ne)
+    xi, _ = orc.lgl(N)
+    u = W.alfven_wave(N, n, xi, 0.0, gamma=G)
+    elems = _sample_elements(n, count, seed=N)
+    P = (N + 1) ** 3
+    ref = orc.mhd_rhs(N, n, W.box(3), u, G, True, elems=elems).reshape(-1, 8, P)[elems]
+    got = gpu_rhs(N, n, u).reshape(-1, 8, P)[elems]
+    err = rel_l2(got, ref)
+    print(f"MHD {ne}^3 N={N} sampled rel L2 = {err:.3e}")
+    assert err <= TOL64
+
+
+def test_mhd_max_dt(orc):
+    N, n = 4, (3, 4, 2)
+    dom = np.array([-1.0, 1.0, -0.5, 1.5, 0.0, 3.0])
+    u = W.mhd_random_state(N, n, seed=3, gamma=G)
+    got = mesh(N, n, dom).max_dt(torch.from_numpy(u).cuda(), cfl=0.7)
+    assert got == pytest.approx(orc.mhd_max_dt(N, n, dom, u, 0.7, G), rel=1e-14)
+
+
+def test_mhd_steps_match_oracle(orc):
+    """Five CFL steps on the device (stage updates fused into the volume
+    kernel) against the oracle's LSRK steps with the device's dt."""
+    N, n = 3, (4, 3, 2)
+    xi, _ = orc.lgl(N)
+    u0 = W.alfven_wave(N, n, xi, 0.0, gamma=G)
+    m = mesh(N, n)
+    ut = torch.from_numpy(u0.copy()).cuda()
+    ref = u0.copy()
+    for _ in range(5):
+        m.step_cfl(ut, cfl=0.5)
+        ref = orc.mhd_lsrk_step(N, n, W.box(3), ref, m.last_dt(), G, True)
+    assert m.check() == 0
+    got = ut.cpu().numpy()
+    assert rel_l2(got - u0, ref - u0) <= 1e-11
+
+
+def test_mhd_fused_graph_and_unfused_steps_agree(orc):
+    N, n = 3, (4, 4, 3)
+    u0 = W.mhd_random_state(N, n, seed=12, gamma=G)
+    m1, m2, m3 = mesh(N, n), mesh(N, n), mesh(N, n)
+    a = torch.from_numpy(u0.copy()).cuda()
+    b = torch.from_numpy(u0.copy()).cuda()
+    c = torch.from_numpy(u0.copy()).cuda()
+    du = m1.empty_rhs()
+    for _ in range(3):
+        dt = m1.max_dt(a, cfl=0.3)
+        m1.step(a, dt, du)
+        m2.step_cfl(b, cfl=0.3)
+        m3.step_cfl(c, cfl=0.3, graph=True)
+        assert m2.last_dt() == pytest.approx(dt, rel=1e-15)
+    torch.cuda.synchronize()
+    assert torch.equal(b, c)
+    inc_a, inc_b = a.cpu().numpy() - u0, b.cpu().numpy() - u0
+    assert rel_l2(inc_b, inc_a) <= 1e-13
+
+
+def test_mhd_host_state_step_equals_device_step(orc):
+    N, n = 2, (3, 3, 3)
+    u0 = W.mhd_random_state(N, n, seed=13, gamma=G)
+    m1, m2 = mesh(N, n), mesh(N, n)
+    a = torch.from_numpy(u0.copy()).cuda()
+    for _ in range(2):
+        m1.step_cfl(a, cfl=0.4)
+    h = torch.from_numpy(u0.copy()).pin_memory()
+    m2.step_cfl_host(h, cfl=0.4, n_steps=2)
+    assert torch.equal(a.cpu(), h)
+
+
+def test_mhd_nonphysical_state_is_reported():
+    N, n = 2, (2, 2, 2)
+    u = W.mhd_random_state(N, n, seed=1, gamma=G).reshape(-1, 8, 27)
+    u[5, 4, 3] = -1.0  # negative energy: negative pressure at one node
+    m = mesh(N, n)
+    ut = torch.from_numpy(u.reshape(-1).copy()).cuda()
+    m.rhs(ut)
+    with pytest.raises(DGError):
+        m.check()
+    assert m.check() == 0
+    with pytest.raises(DGError):
+        m.max_dt(ut)
+
+
+def test_mhd_mesh_refuses_euler_only_calls():
+    N, n = 2, (2, 2, 2)
+    m = mesh(N, n)
+    u = torch.from_numpy(W.mhd_random_state(N, n, seed=2, gamma=G)).cuda()
+    assert m.n_vars == 8 and m.n_values == 8 * 8 * 27
+    with pytest.raises(DGError):
+        m.rhs_vjp(u, u)
+    with pytest.raises(DGError):
+        m.integrals(u)
+    with pytest.raises(DGError):
+        m.set_source("manufactured")
+
+
+def test_mhd_alfven_wave_trajectory(orc):
+    """Twenty device steps of the Alfven wave against the oracle's steps, and
+    both against the exact wave."""
+    N, n = 4, (3, 3, 3)
+    xi, _ = orc.lgl(N)
+    u0 = W.alfven_wave(N, n, xi, 0.0, gamma=G)
+    m = mesh(N, n)
+    ut = torch.from_numpy(u0.copy()).cuda()
+    ref = u0.copy()
+    t = 0.0
+    for _ in range(20):
+        m.step_cfl(ut, cfl=0.5)
+        dt = m.last_dt()
+        ref = orc.mhd_lsrk_step(N, n, W.box(3), ref, dt, G, True)
+        t += dt
+    got = ut.cpu().numpy()
+    assert rel_l2(got - u0, ref - u0) <= 1e-11
+    exact = W.alfven_wave(N, n, xi, t, gamma=G)
+    assert np.max(np.abs(got - exact)) < 2e-3
