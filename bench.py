@@ -351,11 +351,11 @@ def run_curved(args, timed):
 
 def mhd_volume_flops_per_node(N):
     """Algorithmic FP64 flops per node of the MHD volume kernel (rhs only, a
-    fused multiply-add counted as two): 41 for the node's primitives and the
-    Powell term, and per direction 29 for the flux and the accumulation,
-    18 (N+1) for the nine D-row products, and the lifting (27 flops) at the 2
-    of N+1 line nodes that lie on a face."""
-    return 41 + 3 * (29 + 18 * (N + 1) + 54 / (N + 1))
+    fused multiply-add counted as two, a reciprocal as one): 28 for the
+    node's primitives, 14 for the Powell term, and per direction 20 for the
+    flux, 16 (N+1) for the eight D-row products (seven flux components and
+    B_n), and the lifting (26 flops) at the 2 of N+1 line nodes on a face."""
+    return 42 + 3 * (20 + 16 * (N + 1) + 52 / (N + 1))
 
 
 def run_mhd(args, timed, kernel_ms):

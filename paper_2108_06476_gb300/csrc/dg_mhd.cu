@@ -21,9 +21,10 @@
 //     lambda = max(|v_n,L|, |v_n,R|) + max(c_f,L, c_f,R), and {B_n}, stored as
 //     nine values per face node in fs[dir][q][e_left][l].
 //   mhd_volume_kernel: one CTA per EPB elements, one thread per node; per
-//     direction each thread writes f(u_i) (and B_n) to shared memory, then
-//     applies its line's row of Dn and the lifting; epilogue: the Powell
-//     term, then the store of du or the fused stage update.
+//     direction each thread writes f(u_i) (B_n in the slot of the zero
+//     normal induction flux) to shared memory, then applies its line's row
+//     of Dn and the lifting; epilogue: the Powell term, then the store of du
+//     or the fused stage update.
 //   mhd_speed_kernel: one warp per element; sum_dir (2/h) max(|v_dir| + c_f)
 //     into the mesh's wave-speed word (CFL step).
 #include <cuda_runtime.h>
@@ -37,15 +38,20 @@ namespace {
 
 constexpr int kMV = 8;  // conserved MHD variables
 constexpr int kMQ = 9;  // face values: F* (8) and {B_n}
+// volume CTAs of about kMhdThreads threads; those up to that size ask for
+// kMhdMinBlocks resident CTAs per SM (80 registers a thread at 256 threads)
+constexpr int kMhdThreads = 256;
+constexpr int kMhdMinBlocks = 3;
 
 struct MState {
-  double rho, v[3], p, B[3], vb, pt, E;
+  double rho, rr, v[3], p, B[3], b2, vb, pt, E;
 };
 
 __device__ __forceinline__ MState mhd_state(const double* c, double gm1, unsigned& bad) {
   MState s;
   s.rho = c[0];
   const double rr = 1.0 / c[0];
+  s.rr = rr;
   double mv = 0.0, b2 = 0.0;
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
@@ -55,6 +61,7 @@ __device__ __forceinline__ MState mhd_state(const double* c, double gm1, unsigne
     b2 = fma(s.B[k], s.B[k], b2);
   }
   s.E = c[4];
+  s.b2 = b2;
   s.p = gm1 * (c[4] - 0.5 * mv - 0.5 * b2);
   s.pt = s.p + 0.5 * b2;
   s.vb = s.v[0] * s.B[0] + s.v[1] * s.B[1] + s.v[2] * s.B[2];
@@ -77,16 +84,16 @@ __device__ __forceinline__ void mhd_flux(const MState& s, const double* c, doubl
   for (int k = 0; k < 3; ++k) f[5 + k] = (k == DIR) ? 0.0 : vn * s.B[k] - bn * s.v[k];
 }
 
-// fast magnetosonic speed in direction DIR; the discriminant is >= (a^2 -
-// b^2)^2 >= 0 in exact arithmetic and is clamped at zero against rounding
+// square of the fast magnetosonic speed in direction DIR; the discriminant
+// is >= (a^2 - b^2)^2 >= 0 in exact arithmetic and is clamped at zero
+// against rounding
 template <int DIR>
-__device__ __forceinline__ double fast_speed(const MState& s, double gamma) {
-  const double rr = 1.0 / s.rho;
-  const double a2 = gamma * s.p * rr;
-  const double b2 = (s.B[0] * s.B[0] + s.B[1] * s.B[1] + s.B[2] * s.B[2]) * rr;
-  const double bn2 = s.B[DIR] * s.B[DIR] * rr;
+__device__ __forceinline__ double fast_speed2(const MState& s, double gamma) {
+  const double a2 = gamma * s.p * s.rr;
+  const double b2 = s.b2 * s.rr;
+  const double bn2 = s.B[DIR] * s.B[DIR] * s.rr;
   const double q = a2 + b2;
-  return sqrt(0.5 * (q + sqrt(fmax(q * q - 4.0 * a2 * bn2, 0.0))));
+  return 0.5 * (q + sqrt(fmax(q * q - 4.0 * a2 * bn2, 0.0)));
 }
 
 template <int N, int DIR>
@@ -111,8 +118,10 @@ __device__ __forceinline__ void mhd_surface_body(const double* __restrict__ u,
     double fl[kMV], fr[kMV];
     mhd_flux<DIR>(sl, cl, fl);
     mhd_flux<DIR>(sr, cr, fr);
+    // max(c_L, c_R) = sqrt(max(c_L^2, c_R^2)) exactly (sqrt is monotone and
+    // correctly rounded)
     const double lam = fmax(fabs(sl.v[DIR]), fabs(sr.v[DIR])) +
-                       fmax(fast_speed<DIR>(sl, g.gamma), fast_speed<DIR>(sr, g.gamma));
+                       sqrt(fmax(fast_speed2<DIR>(sl, g.gamma), fast_speed2<DIR>(sr, g.gamma)));
     const long long base = g.nelem * NF;
     const long long off = e * NF + l;
 #pragma unroll
@@ -132,35 +141,41 @@ __global__ void mhd_surface_kernel(const double* __restrict__ u, double* __restr
   if (bad) atomicOr(err, bad);
 }
 
-// one direction of the volume pass for the thread's node (index ia along DIR)
+// one direction of the volume pass for the thread's node (index ia along
+// DIR). The normal induction flux v_n B_n - B_n v_n is zero, so its shared-
+// memory slot 5 + DIR carries B_n instead, whose derivative goes to -div B;
+// du of B_n gets only the lifting of F*_{5+DIR} (the LLF dissipation).
+// Contributions accumulate straight into acc and divneg.
 template <int N, int DIR, int EPB>
 __device__ __forceinline__ void mhd_direction(const MState& s, const double* c,
-                                              double (*sf)[kMQ][(N + 1) * (N + 1) * (N + 1)],
-                                              int el, int node, bool active, long long e,
-                                              const Geom& g, const Tables<double>& tb,
+                                              double (*sf)[kMV][(N + 1) * (N + 1) * (N + 1)],
+                                              const double (*sD)[N + 1][N + 1], int el, int node,
+                                              bool active, long long e, const Geom& g,
+                                              const Tables<double>& tb,
                                               const double* __restrict__ fs, double* acc,
                                               double& divneg) {
   constexpr int NP = N + 1, NF = NP * NP;
   constexpr int STRIDE = DIR == 0 ? 1 : (DIR == 1 ? NP : NF);
-  double f[kMQ];
-  mhd_flux<DIR>(s, c, f);
-  f[8] = s.B[DIR];
+  constexpr int QB = 5 + DIR;  // the slot of B_n
   if (active) {
+    double f[kMV];
+    mhd_flux<DIR>(s, c, f);
+    f[QB] = s.B[DIR];
 #pragma unroll
-    for (int q = 0; q < kMQ; ++q) sf[el][q][node] = f[q];
+    for (int q = 0; q < kMV; ++q) sf[el][q][node] = f[q];
   }
   __syncthreads();
   if (active) {
     const int ia = (node / STRIDE) % NP;
     const int first = node - ia * STRIDE;
-    double a[kMQ];
-#pragma unroll
-    for (int q = 0; q < kMQ; ++q) a[q] = 0.0;
 #pragma unroll
     for (int b = 0; b < NP; ++b) {
-      const double w = tb.Ds[DIR][ia][b];
+      const double w = sD[DIR][ia][b];
 #pragma unroll
-      for (int q = 0; q < kMQ; ++q) a[q] = fma(w, sf[el][q][first + b * STRIDE], a[q]);
+      for (int q = 0; q < kMV; ++q) {
+        if (q == QB) divneg = fma(w, sf[el][q][first + b * STRIDE], divneg);
+        else acc[q] = fma(w, sf[el][q][first + b * STRIDE], acc[q]);
+      }
     }
     if (ia == N || ia == 0) {
       // face-node index of this line (see line_node)
@@ -170,22 +185,30 @@ __device__ __forceinline__ void mhd_direction(const MState& s, const double* c,
       const long long base = g.nelem * NF;
       const double* src = fs + (long long)DIR * kMQ * base + ef * NF + l;
 #pragma unroll
-      for (int q = 0; q < kMQ; ++q) a[q] = fma(lift, src[q * base] - f[q], a[q]);
+      for (int q = 0; q < kMV; ++q) {
+        if (q == QB) acc[q] = fma(lift, src[q * base], acc[q]);
+        else acc[q] = fma(lift, src[q * base] - sf[el][q][node], acc[q]);
+      }
+      divneg = fma(lift, src[8 * base] - sf[el][QB][node], divneg);
     }
-#pragma unroll
-    for (int q = 0; q < kMV; ++q) acc[q] += a[q];
-    divneg += a[8];
   }
   __syncthreads();
 }
 
 template <int N, int EPB>
-__global__ void __launch_bounds__(EPB*(N + 1) * (N + 1) * (N + 1))
+__global__ void __launch_bounds__(EPB*(N + 1) * (N + 1) * (N + 1),
+                                  (EPB * (N + 1) * (N + 1) * (N + 1) <= kMhdThreads) ? kMhdMinBlocks
+                                                                                   : 1)
     mhd_volume_kernel(double* u, double* __restrict__ du, const double* __restrict__ fs, Geom g,
                       Tables<double> tb, int powell, unsigned* __restrict__ err, StageFuse fz) {
   constexpr int NP = N + 1, P = NP * NP * NP;
   extern __shared__ __align__(16) unsigned char dg_smem[];
-  double(*sf)[kMQ][P] = reinterpret_cast<double(*)[kMQ][P]>(dg_smem);
+  double(*sf)[kMV][P] = reinterpret_cast<double(*)[kMV][P]>(dg_smem);
+  // the derivative rows, indexed per thread: from shared memory rather than
+  // the parameter bank, whose divergent reads serialise
+  __shared__ double sD[3][NP][NP];
+  for (int t = threadIdx.x; t < 3 * NP * NP; t += blockDim.x)
+    sD[t / (NP * NP)][(t / NP) % NP][t % NP] = tb.Ds[t / (NP * NP)][(t / NP) % NP][t % NP];
   const int el = threadIdx.x / P, node = threadIdx.x % P;
   const long long e = (long long)blockIdx.x * EPB + el;
   const bool active = e < g.nelem;
@@ -203,9 +226,9 @@ __global__ void __launch_bounds__(EPB*(N + 1) * (N + 1) * (N + 1))
   double acc[kMV], divneg = 0.0;
 #pragma unroll
   for (int v = 0; v < kMV; ++v) acc[v] = 0.0;
-  mhd_direction<N, 0, EPB>(s, c, sf, el, node, active, e, g, tb, fs, acc, divneg);
-  mhd_direction<N, 1, EPB>(s, c, sf, el, node, active, e, g, tb, fs, acc, divneg);
-  mhd_direction<N, 2, EPB>(s, c, sf, el, node, active, e, g, tb, fs, acc, divneg);
+  mhd_direction<N, 0, EPB>(s, c, sf, sD, el, node, active, e, g, tb, fs, acc, divneg);
+  mhd_direction<N, 1, EPB>(s, c, sf, sD, el, node, active, e, g, tb, fs, acc, divneg);
+  mhd_direction<N, 2, EPB>(s, c, sf, sD, el, node, active, e, g, tb, fs, acc, divneg);
   if (!active) return;
   if (powell) {
 #pragma unroll
@@ -225,7 +248,7 @@ __global__ void __launch_bounds__(EPB*(N + 1) * (N + 1) * (N + 1))
       double kk = dtv * acc[v];
       if (fz.a != 0.0) kk = fma(fz.a, fz.k[i], kk);
       fz.k[i] = kk;
-      uo[i] = c[v] + fz.b * kk;
+      uo[i] = u[i] + fz.b * kk;
     } else {
       du[i] = acc[v];
     }
@@ -251,9 +274,9 @@ __global__ void mhd_speed_kernel(const double* __restrict__ u, Geom g, int P, do
         for (int v = 0; v < kMV; ++v) copy_to[(e * kMV + v) * P + node] = c[v];
       }
       const MState s = mhd_state(c, g.gm1, bad);
-      lam[0] = fmax(lam[0], fabs(s.v[0]) + fast_speed<0>(s, g.gamma));
-      lam[1] = fmax(lam[1], fabs(s.v[1]) + fast_speed<1>(s, g.gamma));
-      lam[2] = fmax(lam[2], fabs(s.v[2]) + fast_speed<2>(s, g.gamma));
+      lam[0] = fmax(lam[0], fabs(s.v[0]) + sqrt(fast_speed2<0>(s, g.gamma)));
+      lam[1] = fmax(lam[1], fabs(s.v[1]) + sqrt(fast_speed2<1>(s, g.gamma)));
+      lam[2] = fmax(lam[2], fabs(s.v[2]) + sqrt(fast_speed2<2>(s, g.gamma)));
     }
 #pragma unroll
     for (int k = 0; k < 3; ++k)
@@ -275,11 +298,11 @@ __global__ void mhd_speed_kernel(const double* __restrict__ u, Geom g, int P, do
   }
 }
 
-// elements per CTA: about 256 threads
+// elements per CTA: about kMhdThreads threads
 template <int N>
 struct MLaunch {
   static constexpr int P = (N + 1) * (N + 1) * (N + 1);
-  static constexpr int EPB = (256 / P) > 0 ? (256 / P) : 1;
+  static constexpr int EPB = (kMhdThreads / P) > 0 ? (kMhdThreads / P) : 1;
 };
 
 template <int N, int EPB>
@@ -287,7 +310,7 @@ cudaError_t mhd_volume_epb(const double* u, double* du, const double* fs, const 
                            const Tables<double>& tb, int powell, unsigned* err, cudaStream_t st,
                            const StageFuse& fz) {
   constexpr int P = MLaunch<N>::P;
-  constexpr int SMEM = EPB * kMQ * P * (int)sizeof(double);
+  constexpr int SMEM = EPB * kMV * P * (int)sizeof(double);
   auto kern = mhd_volume_kernel<N, EPB>;
   if (SMEM > 48 * 1024) {
     const cudaError_t e =
