@@ -196,3 +196,31 @@ def test_mhd_alfven_wave_trajectory(orc):
     assert rel_l2(got - u0, ref - u0) <= 1e-11
     exact = W.alfven_wave(N, n, xi, t, gamma=G)
     assert np.max(np.abs(got - exact)) < 2e-3
+
+
+def test_mhd_alfven_wave_converges_at_full_size():
+    """Device steps of the Alfven wave to t = 0.1 on 16^3, 32^3 and 64^3
+    elements (N = 3, CFL 0.5): the error against the exact wave falls at
+    about the order N + 1 of the scheme (no oracle: the meshes are too big
+    for it; the exact solution is the reference)."""
+    from paper_2108_06476_gb300 import lgl_nodes
+    N, T = 3, 0.1
+    xi, _ = lgl_nodes(N)
+    errs = []
+    for ne in (16, 32, 64):
+        n = (ne, ne, ne)
+        m = mesh(N, n)
+        u = torch.from_numpy(W.alfven_wave(N, n, xi, 0.0, gamma=G)).cuda()
+        dt0 = m.max_dt(u, cfl=0.5)
+        steps = int(np.ceil(T / dt0))
+        for _ in range(steps):
+            m.step_dt(u, T / steps)
+        assert m.check() == 0
+        exact = torch.from_numpy(W.alfven_wave(N, n, xi, T, gamma=G)).cuda()
+        errs.append(float((u - exact).abs().max()))
+        del u, exact, m
+        torch.cuda.empty_cache()
+    eoc = [np.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    print(f"Alfven wave N=3 max errors {errs}, EOC {eoc}")
+    assert errs[2] < 1e-6
+    assert min(eoc) > 3.0
