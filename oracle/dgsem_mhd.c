@@ -24,7 +24,10 @@
  *   - local Lax-Friedrichs at the faces with lambda = max(|v_n,L|, |v_n,R|) +
  *     max(c_f,L, c_f,R), c_f the fast magnetosonic speed in direction n:
  *       c_f^2 = (a^2 + b^2 + sqrt((a^2 + b^2)^2 - 4 a^2 b_n^2)) / 2,
- *       a^2 = gamma p / rho, b^2 = |B|^2 / rho, b_n^2 = B_n^2 / rho.
+ *       a^2 = gamma p / rho, b^2 = |B|^2 / rho, b_n^2 = B_n^2 / rho;
+ *     or HLL (the weak-form runs of Sec. 3.1 couple elements with HLL) with
+ *     the signal speeds S_L = min(v_n,L - c_f,L, v_n,R - c_f,R), S_R =
+ *     max(v_n,L + c_f,L, v_n,R + c_f,R).
  * Readings (the paper gives no formulas): the weak form with the Powell
  * term in this form, the LLF wave speed, the Alfven wave of the tests.
  *
@@ -94,6 +97,29 @@ void or_mhd_llf(int n, double gamma, const double *uL, const double *uR, double 
   for (int v = 0; v < MV; ++v) f[v] = 0.5 * (fL[v] + fR[v]) - 0.5 * lam * (uR[v] - uL[v]);
 }
 
+/* HLL flux in direction n: f(u_L) if S_L >= 0, f(u_R) if S_R <= 0, else
+ * (S_R f_L - S_L f_R + S_L S_R (u_R - u_L)) / (S_R - S_L). */
+void or_mhd_hll(int n, double gamma, const double *uL, const double *uR, double *f) {
+  double fL[MV], fR[MV];
+  or_mhd_flux(n, gamma, uL, fL);
+  or_mhd_flux(n, gamma, uR, fR);
+  const double vL = uL[1 + n] / uL[0], vR = uR[1 + n] / uR[0];
+  const double cL = or_mhd_fast_speed(n, gamma, uL), cR = or_mhd_fast_speed(n, gamma, uR);
+  const double sL = fmin(vL - cL, vR - cR), sR = fmax(vL + cL, vR + cR);
+  for (int v = 0; v < MV; ++v) {
+    if (sL >= 0.0) f[v] = fL[v];
+    else if (sR <= 0.0) f[v] = fR[v];
+    else f[v] = (sR * fL[v] - sL * fR[v] + sL * sR * (uR[v] - uL[v])) / (sR - sL);
+  }
+}
+
+/* surface flux ids of or_mhd_rhs */
+static void mhd_surface(int sflux, int n, double gamma, const double *uL, const double *uR,
+                        double *f) {
+  if (sflux == 1) or_mhd_hll(n, gamma, uL, uR, f);
+  else or_mhd_llf(n, gamma, uL, uR, f);
+}
+
 typedef struct {
   int N, np;
   int n[3];
@@ -141,11 +167,13 @@ static void m_load(const mmesh_t *m, const double *u, long long e, long long nod
 }
 
 /* du = rhs(u) for the listed elements (all when elems is NULL); powell = 0
- * drops the non-conservative term. Returns 0 or -1 on bad arguments. */
-int or_mhd_rhs(int N, const int *n, const double *dom, double gamma, int powell, const double *u,
-               double *du, const long long *elems, long long n_elems, int nthreads) {
+ * drops the non-conservative term; sflux 0 LLF, 1 HLL. Returns 0 or -1 on
+ * bad arguments. */
+int or_mhd_rhs(int N, const int *n, const double *dom, double gamma, int powell, int sflux,
+               const double *u, double *du, const long long *elems, long long n_elems,
+               int nthreads) {
   mmesh_t m;
-  if (mmesh_init(&m, N, n, dom)) return -1;
+  if (mmesh_init(&m, N, n, dom) || sflux < 0 || sflux > 1) return -1;
   double Dt[NPMAX * NPMAX], w[NPMAX];
   or_dtilde(N, Dt, w);
   const long long count = elems ? n_elems : m.nelem;
@@ -174,14 +202,14 @@ int or_mhd_rhs(int N, const int *n, const double *dom, double gamma, int powell,
         if (i == N) {
           double uo[MV], fs[MV];
           m_load(&m, u, m_neighbour(&m, e, r, +1), m_with(&m, node, r, 0), uo);
-          or_mhd_llf(r, gamma, ui, uo, fs);
+          mhd_surface(sflux, r, gamma, ui, uo, fs);
           for (int v = 0; v < MV; ++v) vol[v] += fs[v] / w[N];
           db += 0.5 * (ui[5 + r] + uo[5 + r]) / w[N];
         }
         if (i == 0) {
           double uo[MV], fs[MV];
           m_load(&m, u, m_neighbour(&m, e, r, -1), m_with(&m, node, r, N), uo);
-          or_mhd_llf(r, gamma, uo, ui, fs);
+          mhd_surface(sflux, r, gamma, uo, ui, fs);
           for (int v = 0; v < MV; ++v) vol[v] -= fs[v] / w[0];
           db -= 0.5 * (uo[5 + r] + ui[5 + r]) / w[0];
         }

@@ -123,18 +123,68 @@ def test_llf_is_consistent_and_dissipates_at_the_largest_speed():
             assert np.allclose(diss, 0.5 * rad * (uR - uL), rtol=1e-5, atol=1e-6)
 
 
+def test_hll_consistency_upwinding_and_llf_limit():
+    """HLL: consistent; the upwind flux when every signal moves one way; and
+    equal to LLF when both normal velocities vanish (then S_R = -S_L =
+    max(c_f,L, c_f,R) = the LLF speed)."""
+    rng = np.random.default_rng(11)
+    us = rand_state(rng, 16)
+    for uL, uR in zip(us[:8], us[8:]):
+        for d in range(3):
+            assert np.allclose(orc.mhd_hll(d, uL, uL, G), orc.mhd_flux(d, uL, G), rtol=1e-14,
+                               atol=1e-14)
+            for sgn, side in ((1.0, uL), (-1.0, uR)):
+                a, b = uL.copy(), uR.copy()
+                for x in (a, b):  # normal velocity 6, beyond every fast speed
+                    e_kin = 0.5 * (x[1:4] ** 2).sum() / x[0]
+                    x[1 + d] = sgn * 6.0 * x[0]
+                    x[4] += 0.5 * (x[1:4] ** 2).sum() / x[0] - e_kin
+                want = orc.mhd_flux(d, a if sgn > 0 else b, G)
+                assert np.array_equal(orc.mhd_hll(d, a, b, G), want)
+            a, b = uL.copy(), uR.copy()
+            for x in (a, b):
+                x[4] -= 0.5 * x[1 + d] ** 2 / x[0]
+                x[1 + d] = 0.0
+            assert np.allclose(orc.mhd_hll(d, a, b, G), orc.mhd_llf(d, a, b, G),
+                               rtol=1e-13, atol=1e-13)
+
+
+def test_surface_flux_enters_through_the_lifting():
+    """Between the LLF and the HLL operator only the lifting of the face flux
+    changes: at an x-face node off the y and z faces the rhs differs by
+    -(2/h) (F_LLF - F_HLL)/w_N at i = N and +(2/h) (F_LLF - F_HLL)/w_0 at
+    i = 0, F evaluated on the two traces."""
+    N, n = 2, (3, 2, 2)
+    u = W.mhd_random_state(N, n, seed=12, gamma=G)
+    d = (orc.mhd_rhs(N, n, BOX, u, G, True, sflux="llf")
+         - orc.mhd_rhs(N, n, BOX, u, G, True, sflux="hll"))
+    g = as_grid(u, N, n)
+    dg = as_grid(d, N, n)
+    _, w = orc.lgl(N)
+    h = 2.0 / n[0]
+    for ex in range(n[0]):
+        er = (ex + 1) % n[0]
+        uL, uR = g[0, 0, ex, :, 1, 1, N], g[0, 0, er, :, 1, 1, 0]
+        dF = orc.mhd_llf(0, uL, uR, G) - orc.mhd_hll(0, uL, uR, G)
+        assert np.allclose(dg[0, 0, ex, :, 1, 1, N], -(2 / h) * dF / w[N], rtol=1e-10, atol=1e-11)
+        assert np.allclose(dg[0, 0, er, :, 1, 1, 0], (2 / h) * dF / w[0], rtol=1e-10, atol=1e-11)
+        assert np.max(np.abs(dF)) > 1e-3
+
+
+@pytest.mark.parametrize("sflux", ["llf", "hll"])
 @pytest.mark.parametrize("powell", [False, True])
-def test_free_stream(powell):
+def test_free_stream(powell, sflux):
     N, n = 3, (2, 3, 2)
     rng = np.random.default_rng(5)
     u0 = rand_state(rng, 1)[0]
     P = (N + 1) ** 3
     u = np.tile(np.repeat(u0, P), int(np.prod(n)))
-    du = orc.mhd_rhs(N, n, BOX, u, G, powell)
+    du = orc.mhd_rhs(N, n, BOX, u, G, powell, sflux=sflux)
     assert np.max(np.abs(du)) < 1e-12 * np.max(np.abs(u))
 
 
-def test_conservation_without_powell_term():
+@pytest.mark.parametrize("sflux", ["llf", "hll"])
+def test_conservation_without_powell_term(sflux):
     """The conservative part conserves all eight integrals; the Powell term
     leaves mass conserved and moves momentum when div B != 0."""
     N, n = 3, (2, 3, 2)
@@ -142,9 +192,9 @@ def test_conservation_without_powell_term():
     w = weights3(N)
     P = (N + 1) ** 3
     tot = lambda du: np.einsum("evp,p->v", du.reshape(-1, 8, P), w)
-    c = tot(orc.mhd_rhs(N, n, BOX, u, G, powell=False))
+    c = tot(orc.mhd_rhs(N, n, BOX, u, G, powell=False, sflux=sflux))
     assert np.max(np.abs(c)) < 1e-11
-    c = tot(orc.mhd_rhs(N, n, BOX, u, G, powell=True))
+    c = tot(orc.mhd_rhs(N, n, BOX, u, G, powell=True, sflux=sflux))
     assert abs(c[0]) < 1e-11
     assert np.max(np.abs(c[1:4])) > 1e-3
 
@@ -241,15 +291,15 @@ def exact_time_derivative(N, n, t, delta=1e-5):
     return (a - b) / (2 * delta)
 
 
-@pytest.mark.parametrize("powell", [False, True])
-def test_alfven_wave_rhs_converges(powell):
+@pytest.mark.parametrize("powell,sflux", [(False, "llf"), (True, "llf"), (True, "hll")])
+def test_alfven_wave_rhs_converges(powell, sflux):
     """rhs(u) of the exact wave approaches du/dt, spectrally in N."""
     n = (2, 2, 2)
     errs = []
     for N in (3, 5, 7):
         xi, _ = orc.lgl(N)
         u = W.alfven_wave(N, n, xi, 0.3, gamma=G)
-        du = orc.mhd_rhs(N, n, BOX, u, G, powell)
+        du = orc.mhd_rhs(N, n, BOX, u, G, powell, sflux=sflux)
         errs.append(np.max(np.abs(du - exact_time_derivative(N, n, 0.3))))
     assert errs[0] < 0.2 and errs[1] < 1e-2 and errs[2] < 2e-4
     assert errs[1] < errs[0] / 5 and errs[2] < errs[1] / 5
