@@ -110,18 +110,22 @@ int dg_mesh_create_curved(int N, const int *elements_per_dim, double warp, const
  * paper gives no formulas, the discretisation below is this library's reading):
  *   - weak-form DGSEM: the split form with the central two-point flux
  *     (f(u_i) + f(u_m))/2, which is the strong-form derivative of the nodal
- *     flux; local Lax-Friedrichs faces with lambda = max(|v_n,L|, |v_n,R|) +
- *     max(c_f,L, c_f,R), c_f the fast magnetosonic speed;
+ *     flux; faces by local Lax-Friedrichs, lambda = max(|v_n,L|, |v_n,R|) +
+ *     max(c_f,L, c_f,R), c_f the fast magnetosonic speed, or by HLL (the
+ *     paper's weak-form coupling) with S_L = min(v_n,L - c_f,L, v_n,R -
+ *     c_f,R), S_R = max(v_n,L + c_f,L, v_n,R + c_f,R);
  *   - powell = 1 adds the non-conservative term -(div B) (0, B, v.B, v), div B
  *     the same strong-form derivative of B_n with the interface average
  *     {B_n} at the faces; powell = 0 leaves the conservative system.
- * 1 <= N <= 7, gamma > 1, FP64. dg_rhs, dg_rhs_part, dg_rk_stage, dg_rk_reset,
+ * opt NULL selects gamma = 5/3 and LLF; otherwise opt->volume_flux must be
+ * DG_VFLUX_CENTRAL, opt->surface_flux DG_SFLUX_LLF or DG_SFLUX_HLL and
+ * opt->precision DG_FP64. 1 <= N <= 7. dg_rhs, dg_rhs_part, dg_rk_stage, dg_rk_reset,
  * dg_step, dg_step_dt, dg_step_cfl (CFL rule with |v_dir| + c_f,dir),
  * dg_step_graph, dg_step_cfl_host, dg_max_dt, dg_last_dt and dg_mesh_check
  * accept such meshes; dg_rhs_vjp, dg_integrals and dg_set_source do not
  * (DG_ERR_ARG). Errors: DG_ERR_ARG, DG_ERR_OOM, DG_ERR_CUDA. */
-int dg_mesh_create_mhd(int N, const int *elements_per_dim, const double *domain, double gamma,
-                       int powell, void *cuda_stream, dg_mesh **out);
+int dg_mesh_create_mhd(int N, const int *elements_per_dim, const double *domain,
+                       const dg_options *opt, int powell, void *cuda_stream, dg_mesh **out);
 
 /* Source terms (curved meshes only): DG_SOURCE_MANUFACTURED adds
  * S = d_t u + div F(u) of the manufactured solution rho = 2 + 0.1 sin(pi (x +

@@ -79,6 +79,7 @@ struct dg_mesh {
   // 3D ideal MHD meshes (dg_mesh_create_mhd)
   int mhd;
   int powell;
+  int mhd_sf;           // 0 LLF, 1 HLL
   Tables<double> tmhd;  // Ds = -(2/h) D per direction, lifting factors
 };
 
@@ -701,17 +702,23 @@ int dg_mesh_create_curved(int N, const int* epd, double warp, const dg_options* 
   return DG_OK;
 }
 
-int dg_mesh_create_mhd(int N, const int* epd, const double* domain, double gamma, int powell,
-                       void* cuda_stream, dg_mesh** out) {
+int dg_mesh_create_mhd(int N, const int* epd, const double* domain, const dg_options* opt,
+                       int powell, void* cuda_stream, dg_mesh** out) {
   if (out) *out = nullptr;
   if (!out || !epd || !domain) return fail(DG_ERR_ARG, "dg_mesh_create_mhd: null argument");
-  if (!(gamma > 1.0) || (powell != 0 && powell != 1))
-    return fail(DG_ERR_ARG, "dg_mesh_create_mhd: gamma must be > 1 and powell 0 or 1");
-  const dg_options o = {gamma, DG_VFLUX_CENTRAL, DG_SFLUX_LLF, DG_FP64};
+  dg_options o = {5.0 / 3.0, DG_VFLUX_CENTRAL, DG_SFLUX_LLF, DG_FP64};
+  if (opt) o = *opt;
+  if (!(o.gamma > 1.0) || (powell != 0 && powell != 1) || o.volume_flux != DG_VFLUX_CENTRAL ||
+      (o.surface_flux != DG_SFLUX_LLF && o.surface_flux != DG_SFLUX_HLL) ||
+      o.precision != DG_FP64)
+    return fail(DG_ERR_ARG,
+                "dg_mesh_create_mhd: needs gamma > 1, powell 0 or 1, the central volume flux, "
+                "an LLF or HLL surface flux and FP64");
   dg_mesh* m = nullptr;
   int rc = dg_mesh_create(3, N, epd, domain, &o, cuda_stream, &m);
   if (rc != DG_OK) return rc;
   m->mhd = 1;
+  m->mhd_sf = o.surface_flux == DG_SFLUX_HLL ? 1 : 0;
   m->powell = powell;
   // eight variables: the RK register and the face buffer (nine values per
   // face node) are sized anew
@@ -833,7 +840,7 @@ int dg_rhs_part(dg_mesh* m, const double* u, void* du, int parts) {
   }
   cudaError_t e;
   if (m->mhd) {
-    e = dg::mhd_rhs_launch(m->N, u, (double*)du, (double*)m->fs, m->geom, m->tmhd, m->powell,
+    e = dg::mhd_rhs_launch(m->N, u, (double*)du, (double*)m->fs, m->geom, m->tmhd, m->powell, m->mhd_sf,
                            m->err, m->stream, parts, fz);
   } else if (m->curved) {
     dg::SourceArgs src;  // the source at the mesh time
@@ -944,7 +951,7 @@ int enqueue_fused_stages(dg_mesh* m, double* u, double* out) {
     if (s == 4) fz.u_out = out;
     cudaError_t e;
     if (m->mhd) {
-      e = dg::mhd_rhs_launch(m->N, u, nullptr, (double*)m->fs, m->geom, m->tmhd, m->powell,
+      e = dg::mhd_rhs_launch(m->N, u, nullptr, (double*)m->fs, m->geom, m->tmhd, m->powell, m->mhd_sf,
                              m->err, m->stream, 3, fz);
     } else if (m->curved) {
       dg::SourceArgs src;  // stage time t + c_s dt

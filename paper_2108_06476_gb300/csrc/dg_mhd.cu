@@ -18,8 +18,10 @@
 //
 // Kernels of one rhs evaluation:
 //   mhd_surface_kernel: one thread per face node; F* = LLF(u_L, u_R) with
-//     lambda = max(|v_n,L|, |v_n,R|) + max(c_f,L, c_f,R), and {B_n}, stored as
-//     nine values per face node in fs[dir][q][e_left][l].
+//     lambda = max(|v_n,L|, |v_n,R|) + max(c_f,L, c_f,R), or HLL with S_L =
+//     min(v_n,L - c_f,L, v_n,R - c_f,R), S_R = max(v_n,L + c_f,L, v_n,R +
+//     c_f,R), and {B_n}, stored as nine values per face node in
+//     fs[dir][q][e_left][l].
 //   mhd_volume_kernel: one CTA per EPB elements, one thread per node; per
 //     direction each thread writes f(u_i) (B_n in the slot of the zero
 //     normal induction flux) to shared memory, then applies its line's row
@@ -38,6 +40,7 @@ namespace {
 
 constexpr int kMV = 8;  // conserved MHD variables
 constexpr int kMQ = 9;  // face values: F* (8) and {B_n}
+constexpr int kMhdLlf = 0, kMhdHll = 1;  // surface fluxes
 // volume CTAs of about kMhdThreads threads; those up to that size ask for
 // kMhdMinBlocks resident CTAs per SM (80 registers a thread at 256 threads)
 constexpr int kMhdThreads = 256;
@@ -96,7 +99,7 @@ __device__ __forceinline__ double fast_speed2(const MState& s, double gamma) {
   return 0.5 * (q + sqrt(fmax(q * q - 4.0 * a2 * bn2, 0.0)));
 }
 
-template <int N, int DIR>
+template <int N, int DIR, int SF>
 __device__ __forceinline__ void mhd_surface_body(const double* __restrict__ u,
                                                  double* __restrict__ fs, const Geom& g,
                                                  unsigned& bad) {
@@ -118,26 +121,43 @@ __device__ __forceinline__ void mhd_surface_body(const double* __restrict__ u,
     double fl[kMV], fr[kMV];
     mhd_flux<DIR>(sl, cl, fl);
     mhd_flux<DIR>(sr, cr, fr);
-    // max(c_L, c_R) = sqrt(max(c_L^2, c_R^2)) exactly (sqrt is monotone and
-    // correctly rounded)
-    const double lam = fmax(fabs(sl.v[DIR]), fabs(sr.v[DIR])) +
-                       sqrt(fmax(fast_speed2<DIR>(sl, g.gamma), fast_speed2<DIR>(sr, g.gamma)));
     const long long base = g.nelem * NF;
     const long long off = e * NF + l;
+    if (SF == kMhdHll) {
+      const double cfl = sqrt(fast_speed2<DIR>(sl, g.gamma));
+      const double cfr = sqrt(fast_speed2<DIR>(sr, g.gamma));
+      const double sL = fmin(sl.v[DIR] - cfl, sr.v[DIR] - cfr);
+      const double sR = fmax(sl.v[DIR] + cfl, sr.v[DIR] + cfr);
+      const double inv = 1.0 / (sR - sL);
 #pragma unroll
-    for (int v = 0; v < kMV; ++v)
-      fs[(long long)(DIR * kMQ + v) * base + off] = 0.5 * (fl[v] + fr[v]) - 0.5 * lam * (cr[v] - cl[v]);
+      for (int v = 0; v < kMV; ++v) {
+        double F;
+        if (sL >= 0.0) F = fl[v];
+        else if (sR <= 0.0) F = fr[v];
+        else F = (sR * fl[v] - sL * fr[v] + sL * sR * (cr[v] - cl[v])) * inv;
+        fs[(long long)(DIR * kMQ + v) * base + off] = F;
+      }
+    } else {
+      // max(c_L, c_R) = sqrt(max(c_L^2, c_R^2)) exactly (sqrt is monotone
+      // and correctly rounded)
+      const double lam = fmax(fabs(sl.v[DIR]), fabs(sr.v[DIR])) +
+                         sqrt(fmax(fast_speed2<DIR>(sl, g.gamma), fast_speed2<DIR>(sr, g.gamma)));
+#pragma unroll
+      for (int v = 0; v < kMV; ++v)
+        fs[(long long)(DIR * kMQ + v) * base + off] =
+            0.5 * (fl[v] + fr[v]) - 0.5 * lam * (cr[v] - cl[v]);
+    }
     fs[(long long)(DIR * kMQ + 8) * base + off] = 0.5 * (cl[5 + DIR] + cr[5 + DIR]);
   }
 }
 
-template <int N>
+template <int N, int SF>
 __global__ void mhd_surface_kernel(const double* __restrict__ u, double* __restrict__ fs, Geom g,
                                    unsigned* __restrict__ err) {
   unsigned bad = 0;
-  if (blockIdx.y == 0) mhd_surface_body<N, 0>(u, fs, g, bad);
-  else if (blockIdx.y == 1) mhd_surface_body<N, 1>(u, fs, g, bad);
-  else mhd_surface_body<N, 2>(u, fs, g, bad);
+  if (blockIdx.y == 0) mhd_surface_body<N, 0, SF>(u, fs, g, bad);
+  else if (blockIdx.y == 1) mhd_surface_body<N, 1, SF>(u, fs, g, bad);
+  else mhd_surface_body<N, 2, SF>(u, fs, g, bad);
   if (bad) atomicOr(err, bad);
 }
 
@@ -325,8 +345,8 @@ cudaError_t mhd_volume_epb(const double* u, double* du, const double* fs, const 
 
 template <int N>
 cudaError_t mhd_rhs_n(const double* u, double* du, double* fs, const Geom& g,
-                      const Tables<double>& tb, int powell, unsigned* err, cudaStream_t st,
-                      int parts, const StageFuse& fz) {
+                      const Tables<double>& tb, int powell, int sf, unsigned* err,
+                      cudaStream_t st, int parts, const StageFuse& fz) {
   constexpr int NF = (N + 1) * (N + 1);
   if (parts & 1) {
     const long long total = g.nelem * NF;
@@ -334,7 +354,10 @@ cudaError_t mhd_rhs_n(const double* u, double* du, double* fs, const Geom& g,
     long long blocks = (total + threads - 1) / threads;
     if (blocks > 152 * 16) blocks = 152 * 16;
     if (blocks < 1) blocks = 1;
-    mhd_surface_kernel<N><<<dim3((unsigned)blocks, 3), threads, 0, st>>>(u, fs, g, err);
+    if (sf == kMhdHll)
+      mhd_surface_kernel<N, kMhdHll><<<dim3((unsigned)blocks, 3), threads, 0, st>>>(u, fs, g, err);
+    else
+      mhd_surface_kernel<N, kMhdLlf><<<dim3((unsigned)blocks, 3), threads, 0, st>>>(u, fs, g, err);
   }
   if (!(parts & 2)) return cudaGetLastError();
   constexpr int EPB = MLaunch<N>::EPB;
@@ -346,16 +369,16 @@ cudaError_t mhd_rhs_n(const double* u, double* du, double* fs, const Geom& g,
 }  // namespace
 
 cudaError_t mhd_rhs_launch(int N, const double* u, double* du, double* fs, const Geom& g,
-                           const Tables<double>& tb, int powell, unsigned* err, cudaStream_t st,
-                           int parts, const StageFuse& fz) {
+                           const Tables<double>& tb, int powell, int sf, unsigned* err,
+                           cudaStream_t st, int parts, const StageFuse& fz) {
   switch (N) {
-    case 1: return mhd_rhs_n<1>(u, du, fs, g, tb, powell, err, st, parts, fz);
-    case 2: return mhd_rhs_n<2>(u, du, fs, g, tb, powell, err, st, parts, fz);
-    case 3: return mhd_rhs_n<3>(u, du, fs, g, tb, powell, err, st, parts, fz);
-    case 4: return mhd_rhs_n<4>(u, du, fs, g, tb, powell, err, st, parts, fz);
-    case 5: return mhd_rhs_n<5>(u, du, fs, g, tb, powell, err, st, parts, fz);
-    case 6: return mhd_rhs_n<6>(u, du, fs, g, tb, powell, err, st, parts, fz);
-    case 7: return mhd_rhs_n<7>(u, du, fs, g, tb, powell, err, st, parts, fz);
+    case 1: return mhd_rhs_n<1>(u, du, fs, g, tb, powell, sf, err, st, parts, fz);
+    case 2: return mhd_rhs_n<2>(u, du, fs, g, tb, powell, sf, err, st, parts, fz);
+    case 3: return mhd_rhs_n<3>(u, du, fs, g, tb, powell, sf, err, st, parts, fz);
+    case 4: return mhd_rhs_n<4>(u, du, fs, g, tb, powell, sf, err, st, parts, fz);
+    case 5: return mhd_rhs_n<5>(u, du, fs, g, tb, powell, sf, err, st, parts, fz);
+    case 6: return mhd_rhs_n<6>(u, du, fs, g, tb, powell, sf, err, st, parts, fz);
+    case 7: return mhd_rhs_n<7>(u, du, fs, g, tb, powell, sf, err, st, parts, fz);
     default: return cudaErrorInvalidValue;
   }
 }

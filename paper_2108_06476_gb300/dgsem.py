@@ -79,8 +79,8 @@ def load(path: str = SO_PATH):
     L.dg_step_dt.argtypes = [vp, vp, ctypes.c_double]
     L.dg_mesh_create_curved.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                         ctypes.c_double, vp, vp, vp]
-    L.dg_mesh_create_mhd.argtypes = [ctypes.c_int, ip, dp, ctypes.c_double, ctypes.c_int, vp,
-                                     ctypes.POINTER(vp)]
+    L.dg_mesh_create_mhd.argtypes = [ctypes.c_int, ip, dp, ctypes.POINTER(_Options), ctypes.c_int,
+                                     vp, ctypes.POINTER(vp)]
     L.dg_set_source.argtypes = [vp, ctypes.c_int]
     L.dg_set_time.argtypes = [vp, ctypes.c_double]
     L.dg_get_time.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
@@ -150,8 +150,8 @@ class Mesh:
     with warp given, the warped box [-1,1]^3 of the paper's curvilinear
     benchmark (3D, FP64; warp = 0.15 is the paper's amplitude). With
     equations="mhd": the 3D ideal MHD equations (eight variables; weak form,
-    LLF faces, the Powell term unless powell=False; FP64; gamma defaults
-    to 5/3).
+    LLF or HLL faces (surface_flux), the Powell term unless powell=False;
+    FP64; gamma defaults to 5/3).
 
     State tensors are float64 CUDA tensors of n_values entries in the layout
     u[e][v][k][j][i]; rhs outputs are float64 (fp64) or float32 (fp32)."""
@@ -183,7 +183,8 @@ class Mesh:
         if equations == "mhd":
             if self.d != 3 or warp is not None or precision != "fp64":
                 raise DGError("MHD meshes are 3D, Cartesian and FP64")
-            _check(L.dg_mesh_create_mhd(self.N, n_arr, dom, float(gamma), int(bool(powell)),
+            mopt = _Options(gamma, VFLUX["central"], SFLUX[surface_flux], PRECISION["fp64"])
+            _check(L.dg_mesh_create_mhd(self.N, n_arr, dom, ctypes.byref(mopt), int(bool(powell)),
                                         ctypes.c_void_p(st.cuda_stream), ctypes.byref(h)),
                    "dg_mesh_create_mhd")
         elif warp is None:

@@ -97,19 +97,25 @@ def test_curved_and_step_entry_points_reject_bad_arguments(lib):
 
 def test_mhd_mesh_create_rejects_bad_arguments(lib):
     # checked before any CUDA call, so this runs without a GPU
+    from paper_2108_06476_gb300 import dgsem
     h = ctypes.c_void_p()
     n = (ctypes.c_int * 3)(4, 4, 4)
     dom = (ctypes.c_double * 6)(-1, 1, -1, 1, -1, 1)
-    for N, gamma, powell in ((0, 5 / 3, 1), (8, 5 / 3, 1), (3, 1.0, 1), (3, 5 / 3, 2),
-                             (3, float("nan"), 0)):
-        rc = lib.dg_mesh_create_mhd(N, n, dom, gamma, powell, None, ctypes.byref(h))
-        assert rc == -1 and not h.value, (N, gamma, powell)
+    good = dgsem._Options(5 / 3, 2, 2, 0)  # central volume flux, HLL, FP64
+    for N, powell in ((0, 1), (8, 1), (3, 2), (3, -1)):
+        rc = lib.dg_mesh_create_mhd(N, n, dom, ctypes.byref(good), powell, None, ctypes.byref(h))
+        assert rc == -1 and not h.value, (N, powell)
         assert lib.dg_last_error()
-    assert lib.dg_mesh_create_mhd(3, None, dom, 5 / 3, 1, None, ctypes.byref(h)) == -1
+    for opt in (dgsem._Options(1.0, 2, 0, 0), dgsem._Options(float("nan"), 2, 0, 0),
+                dgsem._Options(5 / 3, 0, 0, 0), dgsem._Options(5 / 3, 2, 1, 0),
+                dgsem._Options(5 / 3, 2, 3, 0), dgsem._Options(5 / 3, 2, 0, 1)):
+        rc = lib.dg_mesh_create_mhd(3, n, dom, ctypes.byref(opt), 1, None, ctypes.byref(h))
+        assert rc == -1 and not h.value
+    assert lib.dg_mesh_create_mhd(3, None, dom, None, 1, None, ctypes.byref(h)) == -1
     bad_n = (ctypes.c_int * 3)(4, 0, 4)
-    assert lib.dg_mesh_create_mhd(3, bad_n, dom, 5 / 3, 1, None, ctypes.byref(h)) == -1
+    assert lib.dg_mesh_create_mhd(3, bad_n, dom, None, 1, None, ctypes.byref(h)) == -1
     bad_dom = (ctypes.c_double * 6)(-1, 1, -1, 1, 2, 1)
-    assert lib.dg_mesh_create_mhd(3, n, bad_dom, 5 / 3, 1, None, ctypes.byref(h)) == -1
+    assert lib.dg_mesh_create_mhd(3, n, bad_dom, None, 1, None, ctypes.byref(h)) == -1
 
 
 def test_built_for_sm_103a():

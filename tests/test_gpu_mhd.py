@@ -30,13 +30,13 @@ def rel_l2(a, b):
     return float(np.linalg.norm(a - b) / np.linalg.norm(b))
 
 
-def mesh(N, n, dom=None, powell=True):
+def mesh(N, n, dom=None, powell=True, sflux="llf"):
     return Mesh(3, N, n, tuple(W.box(3) if dom is None else dom), equations="mhd",
-                powell=powell)
+                powell=powell, surface_flux=sflux)
 
 
-def gpu_rhs(N, n, u, dom=None, powell=True):
-    m = mesh(N, n, dom, powell)
+def gpu_rhs(N, n, u, dom=None, powell=True, sflux="llf"):
+    m = mesh(N, n, dom, powell, sflux)
     du = m.rhs(torch.from_numpy(np.ascontiguousarray(u)).cuda())
     assert m.check() == 0
     return du.cpu().numpy()
@@ -49,6 +49,29 @@ def test_mhd_rhs_every_degree(orc, N, powell):
     u = W.mhd_random_state(N, n, seed=40 + N, gamma=G)
     ref = orc.mhd_rhs(N, n, W.box(3), u, G, powell)
     got = gpu_rhs(N, n, u, powell=powell)
+    assert rel_l2(got, ref) <= TOL64, rel_l2(got, ref)
+
+
+@pytest.mark.parametrize("N", range(1, 8))
+def test_mhd_rhs_hll_every_degree(orc, N):
+    n = (3, 2, 2) if N < 6 else (2, 2, 1)
+    u = W.mhd_random_state(N, n, seed=60 + N, gamma=G)
+    ref = orc.mhd_rhs(N, n, W.box(3), u, G, True, sflux="hll")
+    got = gpu_rhs(N, n, u, sflux="hll")
+    assert rel_l2(got, ref) <= TOL64, rel_l2(got, ref)
+
+
+def test_mhd_rhs_hll_supersonic_faces(orc):
+    """A uniform flow faster than every fast wave (v_x = 6): the HLL faces
+    upwind (S_L >= 0 on the x faces), both sides agree."""
+    N, n = 3, (3, 2, 2)
+    u = W.mhd_random_state(N, n, seed=5, gamma=G).reshape(-1, 8, 64)
+    ek = 0.5 * (u[:, 1:4] ** 2).sum(1) / u[:, 0]
+    u[:, 1] = 6.0 * u[:, 0]
+    u[:, 4] += 0.5 * (u[:, 1:4] ** 2).sum(1) / u[:, 0] - ek
+    u = u.reshape(-1)
+    ref = orc.mhd_rhs(N, n, W.box(3), u, G, True, sflux="hll")
+    got = gpu_rhs(N, n, u, sflux="hll")
     assert rel_l2(got, ref) <= TOL64, rel_l2(got, ref)
 
 
@@ -101,18 +124,19 @@ def test_mhd_max_dt(orc):
     assert got == pytest.approx(orc.mhd_max_dt(N, n, dom, u, 0.7, G), rel=1e-14)
 
 
-def test_mhd_steps_match_oracle(orc):
+@pytest.mark.parametrize("sflux", ["llf", "hll"])
+def test_mhd_steps_match_oracle(orc, sflux):
     """Five CFL steps on the device (stage updates fused into the volume
     kernel) against the oracle's LSRK steps with the device's dt."""
     N, n = 3, (4, 3, 2)
     xi, _ = orc.lgl(N)
     u0 = W.alfven_wave(N, n, xi, 0.0, gamma=G)
-    m = mesh(N, n)
+    m = mesh(N, n, sflux=sflux)
     ut = torch.from_numpy(u0.copy()).cuda()
     ref = u0.copy()
     for _ in range(5):
         m.step_cfl(ut, cfl=0.5)
-        ref = orc.mhd_lsrk_step(N, n, W.box(3), ref, m.last_dt(), G, True)
+        ref = orc.mhd_lsrk_step(N, n, W.box(3), ref, m.last_dt(), G, True, sflux=sflux)
     assert m.check() == 0
     got = ut.cpu().numpy()
     assert rel_l2(got - u0, ref - u0) <= 1e-11
