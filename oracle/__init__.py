@@ -96,8 +96,10 @@ def _declare(L):
         L.or_mhd_fast_speed.restype = ctypes.c_double
         L.or_mhd_llf.argtypes = [ctypes.c_int, ctypes.c_double, _dp, _dp, _dp]
         L.or_mhd_hll.argtypes = [ctypes.c_int, ctypes.c_double, _dp, _dp, _dp]
+        L.or_mhd_flux_ec.argtypes = [ctypes.c_int, ctypes.c_double, _dp, _dp, _dp]
         L.or_mhd_rhs.argtypes = [ctypes.c_int, _ip, _dp, ctypes.c_double, ctypes.c_int,
-                                 ctypes.c_int, _dp, _dp, _llp, ctypes.c_longlong, ctypes.c_int]
+                                 ctypes.c_int, ctypes.c_int, _dp, _dp, _llp, ctypes.c_longlong,
+                                 ctypes.c_int]
         L.or_mhd_max_dt.argtypes = [ctypes.c_int, _ip, _dp, ctypes.c_double, ctypes.c_double, _dp]
         L.or_mhd_max_dt.restype = ctypes.c_double
     return L
@@ -410,7 +412,14 @@ def mhd_llf(n, uL, uR, gamma=5.0 / 3.0):
     return f
 
 
-MHD_SFLUX = {"llf": 0, "hll": 1}
+MHD_SFLUX = {"llf": 0, "hll": 1, "ec": 2}
+MHD_VFLUX = {"central": 0, "ec": 1}
+
+
+def mhd_flux_ec(n, uL, uR, gamma=5.0 / 3.0):
+    f = np.zeros(8)
+    lib().or_mhd_flux_ec(n, gamma, _d(_f64(uL)), _d(_f64(uR)), _d(f))
+    return f
 
 
 def mhd_hll(n, uL, uR, gamma=5.0 / 3.0):
@@ -420,9 +429,9 @@ def mhd_hll(n, uL, uR, gamma=5.0 / 3.0):
 
 
 def mhd_rhs(N, n, dom, u, gamma=5.0 / 3.0, powell=True, elems=None, out=None, nthreads=0,
-            sflux="llf"):
-    """du of the weak-form MHD operator (+ the Powell term); sflux "llf" or
-    "hll"."""
+            sflux="llf", vflux="central"):
+    """du of the MHD operator (+ the Powell term): volume flux "central" (the
+    weak form) or "ec"; surface flux "llf", "hll" or "ec"."""
     u = _f64(u)
     du = np.zeros_like(u) if out is None else out
     if elems is None:
@@ -431,7 +440,7 @@ def mhd_rhs(N, n, dom, u, gamma=5.0 / 3.0, powell=True, elems=None, out=None, nt
         elems = np.ascontiguousarray(elems, dtype=np.int64)
         ep, ne = elems.ctypes.data_as(_llp), len(elems)
     rc = lib().or_mhd_rhs(N, _n3(n), _d(_f64(dom)), gamma, int(bool(powell)),
-                          MHD_SFLUX[sflux], _d(u), _d(du), ep, ne, nthreads)
+                          MHD_VFLUX[vflux], MHD_SFLUX[sflux], _d(u), _d(du), ep, ne, nthreads)
     if rc != 0:
         raise ValueError("bad MHD rhs arguments")
     return du
@@ -441,11 +450,12 @@ def mhd_max_dt(N, n, dom, u, cfl=0.5, gamma=5.0 / 3.0):
     return lib().or_mhd_max_dt(N, _n3(n), _d(_f64(dom)), gamma, cfl, _d(_f64(u)))
 
 
-def mhd_lsrk_step(N, n, dom, u, dt, gamma=5.0 / 3.0, powell=True, nthreads=0, sflux="llf"):
+def mhd_lsrk_step(N, n, dom, u, dt, gamma=5.0 / 3.0, powell=True, nthreads=0, sflux="llf",
+                  vflux="central"):
     A, B, _ = lsrk_coefficients()
     u = _f64(u).copy()
     k = np.zeros_like(u)
     for s in range(5):
-        du = mhd_rhs(N, n, dom, u, gamma, powell, nthreads=nthreads, sflux=sflux)
+        du = mhd_rhs(N, n, dom, u, gamma, powell, nthreads=nthreads, sflux=sflux, vflux=vflux)
         rk_stage(u, k, du, A[s], B[s], dt)
     return u

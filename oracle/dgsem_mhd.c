@@ -28,8 +28,21 @@
  *     or HLL (the weak-form runs of Sec. 3.1 couple elements with HLL) with
  *     the signal speeds S_L = min(v_n,L - c_f,L, v_n,R - c_f,R), S_R =
  *     max(v_n,L + c_f,L, v_n,R + c_f,R).
+ *   - flux differencing with an entropy-conservative (EC) two-point flux in
+ *     the volume and at the faces (the paper's second MHD solver, Sec. 3.1,
+ *     whose EC flux it cites without formulas; the non-conservative term
+ *     keeps the split form above). With beta = rho/(2p), entropy variables
+ *     w = ((gamma - s)/(gamma-1) - beta|v|^2, 2 beta v, -2 beta, 2 beta B),
+ *     theta = w . Phi = 2 beta v.B and psi_n = rho v_n + beta v_n |B|^2, a
+ *     two-point flux f# makes the scheme entropy conservative when
+ *       [[w]] . f# + {B_n} [[theta]] = [[psi_n]]
+ *     ({a} the mean, [[a]] the jump). Splitting every jump of a product
+ *     into means times jumps ([[psi_n]] grouped as {beta |B|^2} [[v_n]] +
+ *     {v_n} [[beta |B|^2]]) and matching the jumps of rho, beta, v and B
+ *     gives the flux of or_mhd_flux_ec below.
  * Readings (the paper gives no formulas): the weak form with the Powell
- * term in this form, the LLF wave speed, the Alfven wave of the tests.
+ * term in this form, the LLF wave speed, this EC flux, the Alfven wave of
+ * the tests.
  *
  * du_i = -(2/h) sum_dir [ sum_m Dt_im f#(u_i, u_m) + delta_iN F*_R/w_N
  *                          - delta_i0 F*_L/w_0 ]
@@ -46,6 +59,7 @@
 #endif
 
 int or_dtilde(int N, double *Dt, double *w);
+double or_ln_mean(double x, double y);
 
 #define MV 8
 #define NPMAX 16
@@ -97,6 +111,44 @@ void or_mhd_llf(int n, double gamma, const double *uL, const double *uR, double 
   for (int v = 0; v < MV; ++v) f[v] = 0.5 * (fL[v] + fR[v]) - 0.5 * lam * (uR[v] - uL[v]);
 }
 
+/* Entropy-conservative two-point flux in direction n (derivation in the
+ * header): with rho_ln, beta_ln the logarithmic means and {.} arithmetic
+ * means,
+ *   f_rho = rho_ln {v_n}
+ *   f_m   = f_rho {v} - {B_n} {B} + ({rho} + {beta |B|^2}) / (2 {beta}) e_n
+ *   f_B   = {v_n} {B} - {B_n} {v}            (zero in component n)
+ *   f_E   = f_rho (1/(2 (gamma-1) beta_ln) - {|v|^2}/2) + f_m . {v}
+ *           + f_B . {B} - {v_n} {|B|^2}/2 + {B_n} {v.B} */
+void or_mhd_flux_ec(int n, double gamma, const double *uL, const double *uR, double *f) {
+  double rL, vL[3], pL, rR, vR[3], pR;
+  mhd_prim(gamma, uL, &rL, vL, &pL);
+  mhd_prim(gamma, uR, &rR, vR, &pR);
+  const double *BL = uL + 5, *BR = uR + 5;
+  const double bL = rL / (2.0 * pL), bR = rR / (2.0 * pR);
+  double va[3], Ba[3], v2 = 0.0, B2 = 0.0, vB = 0.0, bB2 = 0.0;
+  for (int k = 0; k < 3; ++k) {
+    va[k] = 0.5 * (vL[k] + vR[k]);
+    Ba[k] = 0.5 * (BL[k] + BR[k]);
+    v2 += 0.5 * (vL[k] * vL[k] + vR[k] * vR[k]);
+    B2 += 0.5 * (BL[k] * BL[k] + BR[k] * BR[k]);
+    vB += 0.5 * (vL[k] * BL[k] + vR[k] * BR[k]);
+    bB2 += 0.5 * (bL * BL[k] * BL[k] + bR * BR[k] * BR[k]);
+  }
+  const double rho_ln = or_ln_mean(rL, rR), beta_ln = or_ln_mean(bL, bR);
+  const double ra = 0.5 * (rL + rR), ba = 0.5 * (bL + bR);
+  f[0] = rho_ln * va[n];
+  for (int k = 0; k < 3; ++k) f[1 + k] = f[0] * va[k] - Ba[n] * Ba[k];
+  f[1 + n] += (ra + bB2) / (2.0 * ba);
+  for (int k = 0; k < 3; ++k) f[5 + k] = va[n] * Ba[k] - Ba[n] * va[k];
+  double fmv = 0.0, fBB = 0.0;
+  for (int k = 0; k < 3; ++k) {
+    fmv += f[1 + k] * va[k];
+    fBB += f[5 + k] * Ba[k];
+  }
+  f[4] = f[0] * (1.0 / (2.0 * (gamma - 1.0) * beta_ln) - 0.5 * v2) + fmv + fBB - 0.5 * va[n] * B2 +
+         Ba[n] * vB;
+}
+
 /* HLL flux in direction n: f(u_L) if S_L >= 0, f(u_R) if S_R <= 0, else
  * (S_R f_L - S_L f_R + S_L S_R (u_R - u_L)) / (S_R - S_L). */
 void or_mhd_hll(int n, double gamma, const double *uL, const double *uR, double *f) {
@@ -113,11 +165,25 @@ void or_mhd_hll(int n, double gamma, const double *uL, const double *uR, double 
   }
 }
 
-/* surface flux ids of or_mhd_rhs */
+/* surface flux ids of or_mhd_rhs: 0 LLF, 1 HLL, 2 EC */
 static void mhd_surface(int sflux, int n, double gamma, const double *uL, const double *uR,
                         double *f) {
   if (sflux == 1) or_mhd_hll(n, gamma, uL, uR, f);
+  else if (sflux == 2) or_mhd_flux_ec(n, gamma, uL, uR, f);
   else or_mhd_llf(n, gamma, uL, uR, f);
+}
+
+/* volume two-point flux ids of or_mhd_rhs: 0 central (the weak form), 1 EC */
+static void mhd_volume(int vflux, int n, double gamma, const double *ui, const double *um,
+                       double *f) {
+  if (vflux == 1) {
+    or_mhd_flux_ec(n, gamma, ui, um, f);
+  } else {
+    double fi[MV], fm[MV];
+    or_mhd_flux(n, gamma, ui, fi);
+    or_mhd_flux(n, gamma, um, fm);
+    for (int v = 0; v < MV; ++v) f[v] = 0.5 * (fi[v] + fm[v]);
+  }
 }
 
 typedef struct {
@@ -167,13 +233,13 @@ static void m_load(const mmesh_t *m, const double *u, long long e, long long nod
 }
 
 /* du = rhs(u) for the listed elements (all when elems is NULL); powell = 0
- * drops the non-conservative term; sflux 0 LLF, 1 HLL. Returns 0 or -1 on
- * bad arguments. */
-int or_mhd_rhs(int N, const int *n, const double *dom, double gamma, int powell, int sflux,
-               const double *u, double *du, const long long *elems, long long n_elems,
+ * drops the non-conservative term; vflux 0 central (weak form), 1 EC;
+ * sflux 0 LLF, 1 HLL, 2 EC. Returns 0 or -1 on bad arguments. */
+int or_mhd_rhs(int N, const int *n, const double *dom, double gamma, int powell, int vflux,
+               int sflux, const double *u, double *du, const long long *elems, long long n_elems,
                int nthreads) {
   mmesh_t m;
-  if (mmesh_init(&m, N, n, dom) || sflux < 0 || sflux > 1) return -1;
+  if (mmesh_init(&m, N, n, dom) || vflux < 0 || vflux > 1 || sflux < 0 || sflux > 2) return -1;
   double Dt[NPMAX * NPMAX], w[NPMAX];
   or_dtilde(N, Dt, w);
   const long long count = elems ? n_elems : m.nelem;
@@ -189,14 +255,13 @@ int or_mhd_rhs(int N, const int *n, const double *dom, double gamma, int powell,
       for (int v = 0; v < MV; ++v) acc[v] = 0.0;
       for (int r = 0; r < 3; ++r) {
         const int i = m_coord(&m, node, r);
-        double vol[MV], db = 0.0, fi[MV];
-        or_mhd_flux(r, gamma, ui, fi);
+        double vol[MV], db = 0.0;
         for (int v = 0; v < MV; ++v) vol[v] = 0.0;
         for (int a = 0; a <= N; ++a) {
-          double um[MV], fm[MV];
+          double um[MV], fp[MV];
           m_load(&m, u, e, m_with(&m, node, r, a), um);
-          or_mhd_flux(r, gamma, um, fm);
-          for (int v = 0; v < MV; ++v) vol[v] += Dt[i * m.np + a] * (0.5 * (fi[v] + fm[v]));
+          mhd_volume(vflux, r, gamma, ui, um, fp);
+          for (int v = 0; v < MV; ++v) vol[v] += Dt[i * m.np + a] * fp[v];
           db += Dt[i * m.np + a] * (0.5 * (ui[5 + r] + um[5 + r]));
         }
         if (i == N) {

@@ -397,3 +397,108 @@ def test_alfven_wave_is_an_exact_solution():
         for node in (0, 7, 26):
             want = f(Xn[0, e, node], Xn[1, e, node], Xn[2, e, node], 0.25)
             assert np.allclose(u[e, :, node], want, rtol=1e-13, atol=1e-13)
+
+
+# ---- entropy-conservative flux differencing (the paper's second MHD solver) ----
+
+def entropy_parts(u, n):
+    """Entropy variables w, theta = w . Phi and the potential psi_n =
+    rho v_n + beta v_n |B|^2 of a state (beta = rho / (2p), s = ln p - gamma
+    ln rho), from the entropy -rho s / (gamma - 1)."""
+    rho, v, B = u[0], u[1:4] / u[0], u[5:8]
+    p = (G - 1) * (u[4] - 0.5 * rho * v @ v - 0.5 * B @ B)
+    beta = rho / (2 * p)
+    s = np.log(p) - G * np.log(rho)
+    w = np.array([(G - s) / (G - 1) - beta * v @ v, *(2 * beta * v), -2 * beta, *(2 * beta * B)])
+    return w, 2 * beta * (v @ B), rho * v[n] + beta * v[n] * (B @ B)
+
+
+def test_ec_flux_consistency_and_symmetry():
+    rng = np.random.default_rng(21)
+    us = rand_state(rng, 16)
+    for uL, uR in zip(us[:8], us[8:]):
+        for d in range(3):
+            assert np.allclose(orc.mhd_flux_ec(d, uL, uL, G), orc.mhd_flux(d, uL, G), rtol=1e-14,
+                               atol=1e-14)
+            assert np.allclose(orc.mhd_flux_ec(d, uL, uR, G), orc.mhd_flux_ec(d, uR, uL, G),
+                               rtol=1e-14, atol=1e-14)
+            assert orc.mhd_flux_ec(d, uL, uR, G)[5 + d] == 0.0
+
+
+def test_ec_flux_satisfies_the_discrete_entropy_condition():
+    """[[w]] . f# + {B_n} [[theta]] = [[psi_n]] for random pairs (the
+    condition under which flux differencing with the Powell term in split
+    form conserves entropy); the central flux does not satisfy it."""
+    rng = np.random.default_rng(22)
+    us = rand_state(rng, 80)
+    worst, central = 0.0, 0.0
+    for uL, uR in zip(us[:40], us[40:]):
+        for d in range(3):
+            wL, tL, pL = entropy_parts(uL, d)
+            wR, tR, pR = entropy_parts(uR, d)
+            bn = 0.5 * (uL[5 + d] + uR[5 + d])
+            scale = np.abs(wR - wL) @ np.abs(orc.mhd_flux_ec(d, uL, uR, G)) + abs(pR) + abs(pL)
+            r = (wR - wL) @ orc.mhd_flux_ec(d, uL, uR, G) + bn * (tR - tL) - (pR - pL)
+            worst = max(worst, abs(r) / scale)
+            fc = 0.5 * (orc.mhd_flux(d, uL, G) + orc.mhd_flux(d, uR, G))
+            central = max(central, abs((wR - wL) @ fc + bn * (tR - tL) - (pR - pL)) / scale)
+    assert worst < 1e-14
+    assert central > 1e-3
+
+
+def entropy_rate(N, n, u, du):
+    P = (N + 1) ** 3
+    wq = weights3(N) * np.prod([(BOX[2 * k + 1] - BOX[2 * k]) / n[k] / 2 for k in range(3)])
+    U, D = u.reshape(-1, 8, P), du.reshape(-1, 8, P)
+    tot, mag = 0.0, 0.0
+    for e in range(U.shape[0]):
+        for i in range(P):
+            w, _, _ = entropy_parts(U[e, :, i], 0)
+            tot += wq[i] * (w @ D[e, :, i])
+            mag += wq[i] * np.abs(w) @ np.abs(D[e, :, i])
+    return tot, mag
+
+
+def test_ec_rhs_conserves_entropy():
+    """EC volume and surface fluxes with the Powell term: sum_nodes W w . du
+    = 0; without the Powell term, or with the central volume flux, it is
+    not; with LLF faces it decreases."""
+    N, n = 3, (2, 2, 2)
+    u = W.mhd_random_state(N, n, seed=23, gamma=G)
+    tot, mag = entropy_rate(N, n, u, orc.mhd_rhs(N, n, BOX, u, G, True, vflux="ec", sflux="ec"))
+    assert abs(tot) < 1e-13 * mag
+    tot, mag = entropy_rate(N, n, u, orc.mhd_rhs(N, n, BOX, u, G, False, vflux="ec", sflux="ec"))
+    assert abs(tot) > 1e-6 * mag
+    tot, mag = entropy_rate(N, n, u, orc.mhd_rhs(N, n, BOX, u, G, True, vflux="central",
+                                                 sflux="ec"))
+    assert abs(tot) > 1e-6 * mag
+    tot, mag = entropy_rate(N, n, u, orc.mhd_rhs(N, n, BOX, u, G, True, vflux="ec", sflux="llf"))
+    assert tot < -1e-6 * mag
+
+
+@pytest.mark.parametrize("sflux", ["ec", "llf"])
+def test_ec_free_stream_and_conservation(sflux):
+    N, n = 3, (2, 3, 2)
+    rng = np.random.default_rng(24)
+    u0 = rand_state(rng, 1)[0]
+    P = (N + 1) ** 3
+    uc = np.tile(np.repeat(u0, P), int(np.prod(n)))
+    du = orc.mhd_rhs(N, n, BOX, uc, G, True, vflux="ec", sflux=sflux)
+    assert np.max(np.abs(du)) < 1e-12 * np.max(np.abs(uc))
+    u = W.mhd_random_state(N, n, seed=25, gamma=G)
+    w = weights3(N)
+    c = np.einsum("evp,p->v", orc.mhd_rhs(N, n, BOX, u, G, False, vflux="ec",
+                                          sflux=sflux).reshape(-1, 8, P), w)
+    assert np.max(np.abs(c)) < 1e-11
+
+
+def test_ec_alfven_wave_rhs_converges():
+    n = (2, 2, 2)
+    errs = []
+    for N in (3, 5, 7):
+        xi, _ = orc.lgl(N)
+        u = W.alfven_wave(N, n, xi, 0.3, gamma=G)
+        du = orc.mhd_rhs(N, n, BOX, u, G, True, vflux="ec", sflux="ec")
+        errs.append(np.max(np.abs(du - exact_time_derivative(N, n, 0.3))))
+    assert errs[0] < 0.2 and errs[1] < 1e-2 and errs[2] < 2e-4
+    assert errs[1] < errs[0] / 5 and errs[2] < errs[1] / 5

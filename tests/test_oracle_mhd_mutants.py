@@ -27,8 +27,7 @@ MUTANTS = [
     ("LLF speed from the mean velocity", "fmax(fabs(vL), fabs(vR)) +",
      "0.5 * (fabs(vL) + fabs(vR)) +"),
     ("transposed volume derivative",
-     "vol[v] += Dt[i * m.np + a] * (0.5 * (fi[v] + fm[v]));",
-     "vol[v] += Dt[a * m.np + i] * (0.5 * (fi[v] + fm[v]));"),
+     "vol[v] += Dt[i * m.np + a] * fp[v];", "vol[v] += Dt[a * m.np + i] * fp[v];"),
     ("sign of the left surface term", "for (int v = 0; v < MV; ++v) vol[v] -= fs[v] / w[0];",
      "for (int v = 0; v < MV; ++v) vol[v] += fs[v] / w[0];"),
     ("left neighbour taken on the right",
@@ -49,6 +48,15 @@ MUTANTS = [
      "if (sL >= 0.0) f[v] = fR[v];"),
     ("surface flux ids swapped", "if (sflux == 1) or_mhd_hll(n, gamma, uL, uR, f);",
      "if (sflux == 0) or_mhd_hll(n, gamma, uL, uR, f);"),
+    ("EC magnetic pressure without the beta weighting", "f[1 + n] += (ra + bB2) / (2.0 * ba);",
+     "f[1 + n] += ra / (2.0 * ba) + 0.5 * B2;"),
+    ("EC energy flux drops the {B_n} {v.B} term", "- 0.5 * va[n] * B2 +\n         Ba[n] * vB;",
+     "- 0.5 * va[n] * B2;"),
+    ("EC flux with the arithmetic mean of beta", "beta_ln = or_ln_mean(bL, bR);",
+     "beta_ln = 0.5 * (bL + bR);"),
+    ("EC induction flux with the sign of {B_n} {v} flipped",
+     "f[5 + k] = va[n] * Ba[k] - Ba[n] * va[k];", "f[5 + k] = va[n] * Ba[k] + Ba[n] * va[k];"),
+    ("EC volume flux id ignored", "if (vflux == 1) {", "if (vflux == 7) {"),
 ]
 
 PINS = [
@@ -67,6 +75,9 @@ PINS = [
     lambda: TM.test_alfven_wave_rhs_converges(True, "llf"),
     TM.test_powell_system_advects_a_divergence_error,
     TM.test_max_dt_uses_the_fast_speed,
+    TM.test_ec_flux_consistency_and_symmetry,
+    TM.test_ec_flux_satisfies_the_discrete_entropy_condition,
+    TM.test_ec_rhs_conserves_entropy,
 ]
 
 
@@ -96,6 +107,7 @@ def test_battery_accepts_the_mhd_oracle():
 @pytest.mark.parametrize("name,old,new", MUTANTS, ids=[m[0] for m in MUTANTS])
 def test_battery_rejects_planted_mistake(sources, tmp_path, name, old, new):
     main, curved, mhd = sources
+    old, new = old.replace("\\n", "\n"), new.replace("\\n", "\n")
     assert mhd.count(old) == 1, f"mutation site not found: {name}"
     so = orc.build_variant(main, str(tmp_path), curved, mhd.replace(old, new))
     with orc.use_library(so):
