@@ -58,10 +58,18 @@ typedef enum {
   DG_ERR_TIMEOUT = -5      /* a bounded device wait gave up */
 } dg_status;
 
-/* Two-point volume fluxes (flux differencing, Sec. 2.1/3.1). */
-enum { DG_VFLUX_RANOCHA = 0, DG_VFLUX_CHANDRASHEKAR = 1, DG_VFLUX_CENTRAL = 2 };
-/* Surface fluxes. LLF wave speed: max(|v_n,L|, |v_n,R|) + max(c_L, c_R). */
-enum { DG_SFLUX_LLF = 0, DG_SFLUX_RANOCHA = 1, DG_SFLUX_HLL = 2, DG_SFLUX_CHANDRASHEKAR = 3 };
+/* Two-point volume fluxes (flux differencing, Sec. 2.1/3.1). DG_VFLUX_EC is
+ * the entropy-conservative MHD flux (MHD meshes only). */
+enum { DG_VFLUX_RANOCHA = 0, DG_VFLUX_CHANDRASHEKAR = 1, DG_VFLUX_CENTRAL = 2, DG_VFLUX_EC = 3 };
+/* Surface fluxes. LLF wave speed: max(|v_n,L|, |v_n,R|) + max(c_L, c_R).
+ * DG_SFLUX_EC is the entropy-conservative MHD flux (MHD meshes only). */
+enum {
+  DG_SFLUX_LLF = 0,
+  DG_SFLUX_RANOCHA = 1,
+  DG_SFLUX_HLL = 2,
+  DG_SFLUX_CHANDRASHEKAR = 3,
+  DG_SFLUX_EC = 4
+};
 /* Arithmetic of the rhs kernels. RK accumulation and reductions are FP64. */
 enum { DG_FP64 = 0, DG_FP32 = 1 };
 
@@ -116,10 +124,16 @@ int dg_mesh_create_curved(int N, const int *elements_per_dim, double warp, const
  *     c_f,R), S_R = max(v_n,L + c_f,L, v_n,R + c_f,R);
  *   - powell = 1 adds the non-conservative term -(div B) (0, B, v.B, v), div B
  *     the same strong-form derivative of B_n with the interface average
- *     {B_n} at the faces; powell = 0 leaves the conservative system.
- * opt NULL selects gamma = 5/3 and LLF; otherwise opt->volume_flux must be
- * DG_VFLUX_CENTRAL, opt->surface_flux DG_SFLUX_LLF or DG_SFLUX_HLL and
- * opt->precision DG_FP64. 1 <= N <= 7. dg_rhs, dg_rhs_part, dg_rk_stage, dg_rk_reset,
+ *     {B_n} at the faces; powell = 0 leaves the conservative system;
+ *   - or flux differencing with the entropy-conservative two-point flux
+ *     (opt->volume_flux = DG_VFLUX_EC; the paper's second MHD solver) that
+ *     satisfies [[w]] . f + {B_n} [[theta]] = [[rho v_n + beta v_n |B|^2]]
+ *     (w the entropy variables, theta = 2 beta v.B, beta = rho/(2p)), with
+ *     the Powell term in the same split form; with DG_SFLUX_EC at the faces
+ *     the semi-discrete entropy is conserved.
+ * opt NULL selects gamma = 5/3, the weak form and LLF; otherwise
+ * opt->volume_flux must be DG_VFLUX_CENTRAL or DG_VFLUX_EC, opt->surface_flux
+ * DG_SFLUX_LLF, DG_SFLUX_HLL or DG_SFLUX_EC and opt->precision DG_FP64. 1 <= N <= 7. dg_rhs, dg_rhs_part, dg_rk_stage, dg_rk_reset,
  * dg_step, dg_step_dt, dg_step_cfl (CFL rule with |v_dir| + c_f,dir),
  * dg_step_graph, dg_step_cfl_host, dg_max_dt, dg_last_dt and dg_mesh_check
  * accept such meshes; dg_rhs_vjp, dg_integrals and dg_set_source do not

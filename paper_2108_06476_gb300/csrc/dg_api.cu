@@ -79,7 +79,8 @@ struct dg_mesh {
   // 3D ideal MHD meshes (dg_mesh_create_mhd)
   int mhd;
   int powell;
-  int mhd_sf;           // 0 LLF, 1 HLL
+  int mhd_sf;           // 0 LLF, 1 HLL, 2 EC
+  int mhd_vf;           // 0 weak form, 1 EC flux differencing
   Tables<double> tmhd;  // Ds = -(2/h) D per direction, lifting factors
 };
 
@@ -708,17 +709,26 @@ int dg_mesh_create_mhd(int N, const int* epd, const double* domain, const dg_opt
   if (!out || !epd || !domain) return fail(DG_ERR_ARG, "dg_mesh_create_mhd: null argument");
   dg_options o = {5.0 / 3.0, DG_VFLUX_CENTRAL, DG_SFLUX_LLF, DG_FP64};
   if (opt) o = *opt;
-  if (!(o.gamma > 1.0) || (powell != 0 && powell != 1) || o.volume_flux != DG_VFLUX_CENTRAL ||
-      (o.surface_flux != DG_SFLUX_LLF && o.surface_flux != DG_SFLUX_HLL) ||
+  if (!(o.gamma > 1.0) || (powell != 0 && powell != 1) ||
+      (o.volume_flux != DG_VFLUX_CENTRAL && o.volume_flux != DG_VFLUX_EC) ||
+      (o.surface_flux != DG_SFLUX_LLF && o.surface_flux != DG_SFLUX_HLL &&
+       o.surface_flux != DG_SFLUX_EC) ||
       o.precision != DG_FP64)
     return fail(DG_ERR_ARG,
-                "dg_mesh_create_mhd: needs gamma > 1, powell 0 or 1, the central volume flux, "
-                "an LLF or HLL surface flux and FP64");
+                "dg_mesh_create_mhd: needs gamma > 1, powell 0 or 1, the central or EC volume "
+                "flux, an LLF, HLL or EC surface flux and FP64");
+  const int vf_mhd = o.volume_flux == DG_VFLUX_EC ? 1 : 0;
+  const int sf_mhd =
+      o.surface_flux == DG_SFLUX_HLL ? 1 : (o.surface_flux == DG_SFLUX_EC ? 2 : 0);
+  // the Euler options' checks of dg_mesh_create; the MHD path reads its own
+  o.volume_flux = DG_VFLUX_CENTRAL;
+  o.surface_flux = DG_SFLUX_LLF;
   dg_mesh* m = nullptr;
   int rc = dg_mesh_create(3, N, epd, domain, &o, cuda_stream, &m);
   if (rc != DG_OK) return rc;
   m->mhd = 1;
-  m->mhd_sf = o.surface_flux == DG_SFLUX_HLL ? 1 : 0;
+  m->mhd_sf = sf_mhd;
+  m->mhd_vf = vf_mhd;
   m->powell = powell;
   // eight variables: the RK register and the face buffer (nine values per
   // face node) are sized anew
@@ -840,7 +850,7 @@ int dg_rhs_part(dg_mesh* m, const double* u, void* du, int parts) {
   }
   cudaError_t e;
   if (m->mhd) {
-    e = dg::mhd_rhs_launch(m->N, u, (double*)du, (double*)m->fs, m->geom, m->tmhd, m->powell, m->mhd_sf,
+    e = dg::mhd_rhs_launch(m->N, u, (double*)du, (double*)m->fs, m->geom, m->tmhd, m->t64, m->mhd_vf, m->powell, m->mhd_sf,
                            m->err, m->stream, parts, fz);
   } else if (m->curved) {
     dg::SourceArgs src;  // the source at the mesh time
@@ -951,7 +961,7 @@ int enqueue_fused_stages(dg_mesh* m, double* u, double* out) {
     if (s == 4) fz.u_out = out;
     cudaError_t e;
     if (m->mhd) {
-      e = dg::mhd_rhs_launch(m->N, u, nullptr, (double*)m->fs, m->geom, m->tmhd, m->powell, m->mhd_sf,
+      e = dg::mhd_rhs_launch(m->N, u, nullptr, (double*)m->fs, m->geom, m->tmhd, m->t64, m->mhd_vf, m->powell, m->mhd_sf,
                              m->err, m->stream, 3, fz);
     } else if (m->curved) {
       dg::SourceArgs src;  // stage time t + c_s dt

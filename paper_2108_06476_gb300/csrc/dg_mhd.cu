@@ -31,6 +31,7 @@
 //     into the mesh's wave-speed word (CFL step).
 #include <cuda_runtime.h>
 
+#include "dg_curved.cuh"  // pair_of, pair_index, line_of
 #include "dg_device.cuh"
 #include "dg_mhd_decl.cuh"
 
@@ -40,7 +41,7 @@ namespace {
 
 constexpr int kMV = 8;  // conserved MHD variables
 constexpr int kMQ = 9;  // face values: F* (8) and {B_n}
-constexpr int kMhdLlf = 0, kMhdHll = 1;  // surface fluxes
+constexpr int kMhdLlf = 0, kMhdHll = 1, kMhdEc = 2;  // surface fluxes
 // volume CTAs of about kMhdThreads threads; those up to that size ask for
 // kMhdMinBlocks resident CTAs per SM (80 registers a thread at 256 threads)
 constexpr int kMhdThreads = 256;
@@ -99,6 +100,60 @@ __device__ __forceinline__ double fast_speed2(const MState& s, double gamma) {
   return 0.5 * (q + sqrt(fmax(q * q - 4.0 * a2 * bn2, 0.0)));
 }
 
+// node quantities of the entropy-conservative two-point flux: beta =
+// rho/(2p) and the products whose means it takes
+struct ECq {
+  double rho, beta, v[3], B[3], v2, B2, vB, bB2;
+};
+
+__device__ __forceinline__ ECq ec_of(const MState& s) {
+  ECq q;
+  q.rho = s.rho;
+  q.beta = 0.5 * s.rho / s.p;
+  q.v2 = 0.0;
+  q.vB = s.vb;
+  q.B2 = s.b2;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    q.v[k] = s.v[k];
+    q.B[k] = s.B[k];
+    q.v2 = fma(s.v[k], s.v[k], q.v2);
+  }
+  q.bB2 = q.beta * s.b2;
+  return q;
+}
+
+// Entropy-conservative two-point flux in direction DIR, the flux that
+// satisfies [[w]] . f + {B_n} [[theta]] = [[psi_n]] with the Powell term in
+// split form (theta = 2 beta v.B, psi_n = rho v_n + beta v_n |B|^2):
+//   f_rho = rho_ln {v_n},  f_m = f_rho {v} - {B_n}{B} + ({rho} + {beta|B|^2})/(2{beta}) e_n,
+//   f_B = {v_n}{B} - {B_n}{v} (zero in component DIR),
+//   f_E = f_rho (1/(2(gamma-1) beta_ln) - {|v|^2}/2) + f_m.{v} + f_B.{B}
+//         - {v_n}{|B|^2}/2 + {B_n}{v.B}.
+template <int DIR>
+__device__ __forceinline__ void mhd_ec_flux(const ECq& a, const ECq& b, double gm1inv, double* f) {
+  double va[3], Ba[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    va[k] = 0.5 * (a.v[k] + b.v[k]);
+    Ba[k] = 0.5 * (a.B[k] + b.B[k]);
+  }
+  const double rho_ln = ln_mean(a.rho, b.rho);
+  const double inv_beta_ln = inv_ln_mean(a.beta, b.beta);
+  const double f0 = rho_ln * va[DIR];
+  f[0] = f0;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) f[1 + k] = fma(f0, va[k], -Ba[DIR] * Ba[k]);
+  f[1 + DIR] += (0.5 * (a.rho + b.rho) + 0.5 * (a.bB2 + b.bB2)) / (a.beta + b.beta);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) f[5 + k] = (k == DIR) ? 0.0 : fma(va[DIR], Ba[k], -Ba[DIR] * va[k]);
+  double e = f0 * (0.5 * gm1inv * inv_beta_ln - 0.25 * (a.v2 + b.v2));
+#pragma unroll
+  for (int k = 0; k < 3; ++k) e = fma(f[1 + k], va[k], fma(f[5 + k], Ba[k], e));
+  e = fma(-0.25 * va[DIR], a.B2 + b.B2, e);
+  f[4] = fma(0.5 * Ba[DIR], a.vB + b.vB, e);
+}
+
 template <int N, int DIR, int SF>
 __device__ __forceinline__ void mhd_surface_body(const double* __restrict__ u,
                                                  double* __restrict__ fs, const Geom& g,
@@ -123,7 +178,12 @@ __device__ __forceinline__ void mhd_surface_body(const double* __restrict__ u,
     mhd_flux<DIR>(sr, cr, fr);
     const long long base = g.nelem * NF;
     const long long off = e * NF + l;
-    if (SF == kMhdHll) {
+    if (SF == kMhdEc) {
+      double f[kMV];
+      mhd_ec_flux<DIR>(ec_of(sl), ec_of(sr), g.gm1inv, f);
+#pragma unroll
+      for (int v = 0; v < kMV; ++v) fs[(long long)(DIR * kMQ + v) * base + off] = f[v];
+    } else if (SF == kMhdHll) {
       const double cfl = sqrt(fast_speed2<DIR>(sl, g.gamma));
       const double cfr = sqrt(fast_speed2<DIR>(sr, g.gamma));
       const double sL = fmin(sl.v[DIR] - cfl, sr.v[DIR] - cfr);
@@ -275,6 +335,163 @@ __global__ void __launch_bounds__(EPB*(N + 1) * (N + 1) * (N + 1),
   }
 }
 
+// ---- entropy-conservative flux differencing: one element per CTA ----
+// Per direction, one thread per (line, node pair) evaluates the EC flux once
+// for both nodes into shared memory (the flux is symmetric and the split-
+// form matrix has a zero diagonal); then one thread per node sums
+// Ds_ij f#(u_i, u_j) over its line, the Powell part Ds_ij (B_i + B_j)/2 of
+// -div B, and the lifting of F* and {B_n} at the line ends (Ds = -(2/h) Dt,
+// the split form of the oracle). Epilogue: the Powell term, the store or the
+// fused stage update.
+template <int N>
+struct MPairs {
+  static constexpr int NP = N + 1, P = NP * NP * NP, LINES = NP * NP;
+  static constexpr int NPAIRS = N * (N + 1) / 2;
+  static constexpr int WORK = LINES * NPAIRS;
+  static constexpr int MAXW = WORK > P ? WORK : P;
+  static constexpr int THREADS = MAXW < 512 ? ((MAXW + 31) / 32) * 32 : 512;
+  static constexpr int NQ = 12;  // rho, beta, v, B, |v|^2, |B|^2, v.B, beta |B|^2
+  static constexpr int SMEM = (NQ + kMV + 1) * P * (int)sizeof(double) +
+                              WORK * kMV * (int)sizeof(double);
+};
+
+template <int N>
+__device__ __forceinline__ ECq ec_load(const double (*sq)[(N + 1) * (N + 1) * (N + 1)], int n) {
+  ECq q;
+  q.rho = sq[0][n];
+  q.beta = sq[1][n];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    q.v[k] = sq[2 + k][n];
+    q.B[k] = sq[5 + k][n];
+  }
+  q.v2 = sq[8][n];
+  q.B2 = sq[9][n];
+  q.vB = sq[10][n];
+  q.bB2 = sq[11][n];
+  return q;
+}
+
+template <int N, int DIR>
+__device__ __forceinline__ void mhd_ec_direction(const double (*sq)[(N + 1) * (N + 1) * (N + 1)],
+                                                 double (*sa)[(N + 1) * (N + 1) * (N + 1)],
+                                                 double* pf, const double (*sD)[N + 1][N + 1],
+                                                 long long e, const Geom& g,
+                                                 const Tables<double>& tb,
+                                                 const double* __restrict__ fs) {
+  using C = MPairs<N>;
+  constexpr int NP = C::NP, P = C::P, LINES = C::LINES, NPAIRS = C::NPAIRS;
+  for (int w = threadIdx.x; w < C::WORK; w += blockDim.x) {
+    const int l = w / NPAIRS;
+    int a, b;
+    pair_of<N>(w % NPAIRS, a, b);
+    double f[kMV];
+    mhd_ec_flux<DIR>(ec_load<N>(sq, line_node<3, N, DIR>(l, a)),
+                     ec_load<N>(sq, line_node<3, N, DIR>(l, b)), g.gm1inv, f);
+#pragma unroll
+    for (int v = 0; v < kMV; ++v) pf[w * kMV + v] = f[v];
+  }
+  __syncthreads();
+  for (int node = threadIdx.x; node < P; node += blockDim.x) {
+    int l, i;
+    line_of<N>(DIR, node, l, i);
+    double acc[kMV], dn = 0.0;
+#pragma unroll
+    for (int v = 0; v < kMV; ++v) acc[v] = 0.0;
+    const double bi = sq[5 + DIR][node];
+    for (int j = 0; j < NP; ++j) {
+      if (j == i) continue;
+      const int p = j < i ? pair_index<N>(j, i) : pair_index<N>(i, j);
+      const double dij = sD[DIR][i][j];
+#pragma unroll
+      for (int v = 0; v < kMV; ++v) acc[v] = fma(dij, pf[(l * NPAIRS + p) * kMV + v], acc[v]);
+      dn = fma(dij, 0.5 * (bi + sq[5 + DIR][line_node<3, N, DIR>(l, j)]), dn);
+    }
+    if (i == N || i == 0) {
+      const long long ef = i == N ? e : neighbour(g, e, DIR, -1);
+      const double lift = i == N ? tb.liftR[DIR] : tb.liftL[DIR];
+      const long long base = g.nelem * LINES;
+      const double* src = fs + (long long)DIR * kMQ * base + ef * LINES + l;
+#pragma unroll
+      for (int v = 0; v < kMV; ++v) acc[v] = fma(lift, src[v * base], acc[v]);
+      dn = fma(lift, src[8 * base], dn);
+    }
+#pragma unroll
+    for (int v = 0; v < kMV; ++v) sa[v][node] += acc[v];
+    sa[kMV][node] += dn;
+  }
+  __syncthreads();
+}
+
+template <int N>
+__global__ void __launch_bounds__(MPairs<N>::THREADS)
+    mhd_volume_ec_kernel(double* u, double* __restrict__ du, const double* __restrict__ fs, Geom g,
+                         Tables<double> tb, int powell, unsigned* __restrict__ err, StageFuse fz) {
+  using C = MPairs<N>;
+  constexpr int NP = C::NP, P = C::P;
+  extern __shared__ __align__(16) unsigned char dg_smem[];
+  double(*sq)[P] = reinterpret_cast<double(*)[P]>(dg_smem);                              // [NQ][P]
+  double(*sa)[P] = reinterpret_cast<double(*)[P]>(dg_smem + sizeof(double) * C::NQ * P);  // [9][P]
+  double* pf = reinterpret_cast<double*>(dg_smem + sizeof(double) * (C::NQ + kMV + 1) * P);
+  __shared__ double sD[3][NP][NP];
+  for (int t = threadIdx.x; t < 3 * NP * NP; t += blockDim.x)
+    sD[t / (NP * NP)][(t / NP) % NP][t % NP] = tb.Ds[t / (NP * NP)][(t / NP) % NP][t % NP];
+  const long long e = blockIdx.x;
+  unsigned bad = 0;
+  for (int node = threadIdx.x; node < P; node += blockDim.x) {
+    double c[kMV];
+#pragma unroll
+    for (int v = 0; v < kMV; ++v) c[v] = u[(e * kMV + v) * P + node];
+    const ECq q = ec_of(mhd_state(c, g.gm1, bad));
+    sq[0][node] = q.rho;
+    sq[1][node] = q.beta;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      sq[2 + k][node] = q.v[k];
+      sq[5 + k][node] = q.B[k];
+    }
+    sq[8][node] = q.v2;
+    sq[9][node] = q.B2;
+    sq[10][node] = q.vB;
+    sq[11][node] = q.bB2;
+#pragma unroll
+    for (int v = 0; v <= kMV; ++v) sa[v][node] = 0.0;
+  }
+  if (bad) atomicOr(err, bad);
+  __syncthreads();
+  mhd_ec_direction<N, 0>(sq, sa, pf, sD, e, g, tb, fs);
+  mhd_ec_direction<N, 1>(sq, sa, pf, sD, e, g, tb, fs);
+  mhd_ec_direction<N, 2>(sq, sa, pf, sD, e, g, tb, fs);
+  const double dtv = fz.k ? *fz.dt : 0.0;
+  double* const uo = fz.u_out ? fz.u_out : u;
+  for (int node = threadIdx.x; node < P; node += blockDim.x) {
+    double acc[kMV];
+#pragma unroll
+    for (int v = 0; v < kMV; ++v) acc[v] = sa[v][node];
+    if (powell) {
+      const double dn = sa[kMV][node];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        acc[1 + k] = fma(sq[5 + k][node], dn, acc[1 + k]);
+        acc[5 + k] = fma(sq[2 + k][node], dn, acc[5 + k]);
+      }
+      acc[4] = fma(sq[10][node], dn, acc[4]);
+    }
+#pragma unroll
+    for (int v = 0; v < kMV; ++v) {
+      const long long i = (e * kMV + v) * P + node;
+      if (fz.k) {
+        double kk = dtv * acc[v];
+        if (fz.a != 0.0) kk = fma(fz.a, fz.k[i], kk);
+        fz.k[i] = kk;
+        uo[i] = u[i] + fz.b * kk;
+      } else {
+        du[i] = acc[v];
+      }
+    }
+  }
+}
+
 __global__ void mhd_speed_kernel(const double* __restrict__ u, Geom g, int P, double s0, double s1,
                                  double s2, unsigned long long* out, unsigned* err,
                                  double* __restrict__ copy_to) {
@@ -344,9 +561,25 @@ cudaError_t mhd_volume_epb(const double* u, double* du, const double* fs, const 
 }
 
 template <int N>
+cudaError_t mhd_volume_ec(const double* u, double* du, const double* fs, const Geom& g,
+                          const Tables<double>& tdt, int powell, unsigned* err, cudaStream_t st,
+                          const StageFuse& fz) {
+  using C = MPairs<N>;
+  auto kern = mhd_volume_ec_kernel<N>;
+  if (C::SMEM > 48 * 1024) {
+    const cudaError_t e =
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+    if (e != cudaSuccess) return e;
+  }
+  kern<<<(unsigned)g.nelem, C::THREADS, C::SMEM, st>>>(const_cast<double*>(u), du, fs, g, tdt,
+                                                        powell, err, fz);
+  return cudaGetLastError();
+}
+
+template <int N>
 cudaError_t mhd_rhs_n(const double* u, double* du, double* fs, const Geom& g,
-                      const Tables<double>& tb, int powell, int sf, unsigned* err,
-                      cudaStream_t st, int parts, const StageFuse& fz) {
+                      const Tables<double>& tb, const Tables<double>& tdt, int vf, int powell,
+                      int sf, unsigned* err, cudaStream_t st, int parts, const StageFuse& fz) {
   constexpr int NF = (N + 1) * (N + 1);
   if (parts & 1) {
     const long long total = g.nelem * NF;
@@ -356,10 +589,13 @@ cudaError_t mhd_rhs_n(const double* u, double* du, double* fs, const Geom& g,
     if (blocks < 1) blocks = 1;
     if (sf == kMhdHll)
       mhd_surface_kernel<N, kMhdHll><<<dim3((unsigned)blocks, 3), threads, 0, st>>>(u, fs, g, err);
+    else if (sf == kMhdEc)
+      mhd_surface_kernel<N, kMhdEc><<<dim3((unsigned)blocks, 3), threads, 0, st>>>(u, fs, g, err);
     else
       mhd_surface_kernel<N, kMhdLlf><<<dim3((unsigned)blocks, 3), threads, 0, st>>>(u, fs, g, err);
   }
   if (!(parts & 2)) return cudaGetLastError();
+  if (vf == 1) return mhd_volume_ec<N>(u, du, fs, g, tdt, powell, err, st, fz);
   constexpr int EPB = MLaunch<N>::EPB;
   if (EPB > 1 && g.nelem < 2LL * 152 * EPB)
     return mhd_volume_epb<N, 1>(u, du, fs, g, tb, powell, err, st, fz);
@@ -369,16 +605,17 @@ cudaError_t mhd_rhs_n(const double* u, double* du, double* fs, const Geom& g,
 }  // namespace
 
 cudaError_t mhd_rhs_launch(int N, const double* u, double* du, double* fs, const Geom& g,
-                           const Tables<double>& tb, int powell, int sf, unsigned* err,
-                           cudaStream_t st, int parts, const StageFuse& fz) {
+                           const Tables<double>& tb, const Tables<double>& tdt, int vf,
+                           int powell, int sf, unsigned* err, cudaStream_t st, int parts,
+                           const StageFuse& fz) {
   switch (N) {
-    case 1: return mhd_rhs_n<1>(u, du, fs, g, tb, powell, sf, err, st, parts, fz);
-    case 2: return mhd_rhs_n<2>(u, du, fs, g, tb, powell, sf, err, st, parts, fz);
-    case 3: return mhd_rhs_n<3>(u, du, fs, g, tb, powell, sf, err, st, parts, fz);
-    case 4: return mhd_rhs_n<4>(u, du, fs, g, tb, powell, sf, err, st, parts, fz);
-    case 5: return mhd_rhs_n<5>(u, du, fs, g, tb, powell, sf, err, st, parts, fz);
-    case 6: return mhd_rhs_n<6>(u, du, fs, g, tb, powell, sf, err, st, parts, fz);
-    case 7: return mhd_rhs_n<7>(u, du, fs, g, tb, powell, sf, err, st, parts, fz);
+    case 1: return mhd_rhs_n<1>(u, du, fs, g, tb, tdt, vf, powell, sf, err, st, parts, fz);
+    case 2: return mhd_rhs_n<2>(u, du, fs, g, tb, tdt, vf, powell, sf, err, st, parts, fz);
+    case 3: return mhd_rhs_n<3>(u, du, fs, g, tb, tdt, vf, powell, sf, err, st, parts, fz);
+    case 4: return mhd_rhs_n<4>(u, du, fs, g, tb, tdt, vf, powell, sf, err, st, parts, fz);
+    case 5: return mhd_rhs_n<5>(u, du, fs, g, tb, tdt, vf, powell, sf, err, st, parts, fz);
+    case 6: return mhd_rhs_n<6>(u, du, fs, g, tb, tdt, vf, powell, sf, err, st, parts, fz);
+    case 7: return mhd_rhs_n<7>(u, du, fs, g, tb, tdt, vf, powell, sf, err, st, parts, fz);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -7,12 +7,14 @@
 namespace dg {
 
 // One rhs evaluation (parts: bit 0 face kernel, bit 1 volume kernel); tb
-// holds Ds = -(2/h) D per direction and the lifting factors; fs holds
-// 3 * 9 * nelem * (N+1)^2 doubles; sf 0 LLF, 1 HLL; fz (optional) fuses the
-// stage update.
+// holds Ds = -(2/h) D per direction and the lifting factors (weak form),
+// tdt Ds = -(2/h) Dt (split form); vf 0 weak form, 1 entropy-conservative
+// flux differencing; fs holds 3 * 9 * nelem * (N+1)^2 doubles; sf 0 LLF,
+// 1 HLL, 2 EC; fz (optional) fuses the stage update.
 cudaError_t mhd_rhs_launch(int N, const double* u, double* du, double* fs, const Geom& g,
-                           const Tables<double>& tb, int powell, int sf, unsigned* err,
-                           cudaStream_t st, int parts, const StageFuse& fz);
+                           const Tables<double>& tb, const Tables<double>& tdt, int vf,
+                           int powell, int sf, unsigned* err, cudaStream_t st, int parts,
+                           const StageFuse& fz);
 
 // Wave-speed reduction sum_dir s[dir] max(|v_dir| + c_f,dir) into out (as
 // ordered bits); copy_to (optional) receives a copy of u.

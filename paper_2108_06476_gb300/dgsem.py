@@ -16,8 +16,8 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 SO_PATH = os.path.join(_HERE, "libdgsem.so")
 
-VFLUX = {"ranocha": 0, "chandrashekar": 1, "central": 2}
-SFLUX = {"llf": 0, "ranocha": 1, "hll": 2, "chandrashekar": 3}
+VFLUX = {"ranocha": 0, "chandrashekar": 1, "central": 2, "ec": 3}
+SFLUX = {"llf": 0, "ranocha": 1, "hll": 2, "chandrashekar": 3, "ec": 4}
 PRECISION = {"fp64": 0, "fp32": 1}
 
 # Carpenter-Kennedy (1994) five-stage fourth-order 2N-storage coefficients
@@ -149,9 +149,10 @@ class Mesh:
     """A periodic DGSEM mesh on the current CUDA device: uniform Cartesian, or
     with warp given, the warped box [-1,1]^3 of the paper's curvilinear
     benchmark (3D, FP64; warp = 0.15 is the paper's amplitude). With
-    equations="mhd": the 3D ideal MHD equations (eight variables; weak form,
-    LLF or HLL faces (surface_flux), the Powell term unless powell=False;
-    FP64; gamma defaults to 5/3).
+    equations="mhd": the 3D ideal MHD equations (eight variables; the weak
+    form, or EC flux differencing with volume_flux="ec"; LLF, HLL or EC
+    faces (surface_flux); the Powell term unless powell=False; FP64; gamma
+    defaults to 5/3).
 
     State tensors are float64 CUDA tensors of n_values entries in the layout
     u[e][v][k][j][i]; rhs outputs are float64 (fp64) or float32 (fp32)."""
@@ -183,7 +184,8 @@ class Mesh:
         if equations == "mhd":
             if self.d != 3 or warp is not None or precision != "fp64":
                 raise DGError("MHD meshes are 3D, Cartesian and FP64")
-            mopt = _Options(gamma, VFLUX["central"], SFLUX[surface_flux], PRECISION["fp64"])
+            vf = volume_flux if volume_flux in ("central", "ec") else "central"
+            mopt = _Options(gamma, VFLUX[vf], SFLUX[surface_flux], PRECISION["fp64"])
             _check(L.dg_mesh_create_mhd(self.N, n_arr, dom, ctypes.byref(mopt), int(bool(powell)),
                                         ctypes.c_void_p(st.cuda_stream), ctypes.byref(h)),
                    "dg_mesh_create_mhd")

@@ -67,6 +67,9 @@ def test_mesh_create_rejects_bad_arguments(lib):
     assert lib.dg_mesh_create(3, 3, n, dom, ctypes.byref(opt), None, ctypes.byref(h)) == -1
     opt = dgsem._Options(1.4, 7, 0, 0)
     assert lib.dg_mesh_create(3, 3, n, dom, ctypes.byref(opt), None, ctypes.byref(h)) == -1
+    for vf, sf in ((3, 0), (0, 4)):  # the MHD-only EC fluxes
+        opt = dgsem._Options(1.4, vf, sf, 0)
+        assert lib.dg_mesh_create(3, 3, n, dom, ctypes.byref(opt), None, ctypes.byref(h)) == -1
     assert lib.dg_rhs(None, None, None) == -1
     assert lib.dg_mesh_destroy(None) == 0
 

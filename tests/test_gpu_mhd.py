@@ -30,13 +30,13 @@ def rel_l2(a, b):
     return float(np.linalg.norm(a - b) / np.linalg.norm(b))
 
 
-def mesh(N, n, dom=None, powell=True, sflux="llf"):
+def mesh(N, n, dom=None, powell=True, sflux="llf", vflux="central"):
     return Mesh(3, N, n, tuple(W.box(3) if dom is None else dom), equations="mhd",
-                powell=powell, surface_flux=sflux)
+                powell=powell, surface_flux=sflux, volume_flux=vflux)
 
 
-def gpu_rhs(N, n, u, dom=None, powell=True, sflux="llf"):
-    m = mesh(N, n, dom, powell, sflux)
+def gpu_rhs(N, n, u, dom=None, powell=True, sflux="llf", vflux="central"):
+    m = mesh(N, n, dom, powell, sflux, vflux)
     du = m.rhs(torch.from_numpy(np.ascontiguousarray(u)).cuda())
     assert m.check() == 0
     return du.cpu().numpy()
@@ -257,3 +257,79 @@ def test_mhd_alfven_wave_trajectories_at_full_size():
         assert abs(got[ne][1] - g["max_err"]) <= 1e-12
         assert abs(got[ne][2] - g["rms_err"]) <= 1e-12
     assert got[64][1] < got[32][1] / 4 and got[64][2] < got[32][2] / 3
+
+
+
+# ---- entropy-conservative flux differencing ----
+
+@pytest.mark.parametrize("sflux", ["ec", "llf"])
+@pytest.mark.parametrize("N", range(1, 8))
+def test_mhd_ec_rhs_every_degree(orc, N, sflux):
+    n = (3, 2, 2) if N < 6 else (2, 2, 1)
+    u = W.mhd_random_state(N, n, seed=80 + N, gamma=G)
+    ref = orc.mhd_rhs(N, n, W.box(3), u, G, True, sflux=sflux, vflux="ec")
+    got = gpu_rhs(N, n, u, sflux=sflux, vflux="ec")
+    assert rel_l2(got, ref) <= TOL64, rel_l2(got, ref)
+
+
+def test_mhd_ec_rhs_without_powell_and_on_a_ragged_box(orc):
+    N, n = 3, (5, 4, 3)
+    dom = np.array([-1.0, 1.0, -0.5, 1.5, 0.0, 3.0])
+    u = W.mhd_random_state(N, n, seed=9, gamma=G)
+    for powell in (False, True):
+        ref = orc.mhd_rhs(N, n, dom, u, G, powell, sflux="ec", vflux="ec")
+        got = gpu_rhs(N, n, u, dom=dom, powell=powell, sflux="ec", vflux="ec")
+        assert rel_l2(got, ref) <= TOL64, rel_l2(got, ref)
+
+
+@pytest.mark.parametrize("N,ne,count", [(3, 64, 200), (7, 24, 30)])
+def test_mhd_ec_rhs_full_size_sampled(orc, N, ne, count):
+    n = (ne, ne, ne)
+    xi, _ = orc.lgl(N)
+    u = W.alfven_wave(N, n, xi, 0.0, gamma=G)
+    elems = _sample_elements(n, count, seed=N + 1)
+    P = (N + 1) ** 3
+    ref = orc.mhd_rhs(N, n, W.box(3), u, G, True, elems=elems, sflux="ec",
+                      vflux="ec").reshape(-1, 8, P)[elems]
+    got = gpu_rhs(N, n, u, sflux="ec", vflux="ec").reshape(-1, 8, P)[elems]
+    err = rel_l2(got, ref)
+    print(f"MHD EC {ne}^3 N={N} sampled rel L2 = {err:.3e}")
+    assert err <= TOL64
+
+
+def test_mhd_ec_entropy_conservation_on_the_device():
+    """The device's EC/EC rhs with the Powell term conserves the discrete
+    entropy: sum over nodes of W w(u) . du vanishes relative to the sum of
+    its magnitudes (a property at any size; 12^3 elements, N = 3)."""
+    N, n = 3, (12, 12, 12)
+    u = W.mhd_random_state(N, n, seed=31, gamma=G)
+    du = gpu_rhs(N, n, u, sflux="ec", vflux="ec")
+    P = (N + 1) ** 3
+    xi, w1 = (np.asarray(a) for a in __import__("oracle").lgl(N))
+    wq = np.einsum("i,j,k->kji", w1, w1, w1).reshape(-1)
+    U, D = u.reshape(-1, 8, P), du.reshape(-1, 8, P)
+    rho, v, B = U[:, 0], U[:, 1:4] / U[:, :1], U[:, 5:8]
+    p = (G - 1) * (U[:, 4] - 0.5 * rho * (v * v).sum(1) - 0.5 * (B * B).sum(1))
+    beta = rho / (2 * p)
+    s = np.log(p) - G * np.log(rho)
+    w = np.concatenate([((G - s) / (G - 1) - beta * (v * v).sum(1))[:, None], 2 * beta[:, None] * v,
+                        -2 * beta[:, None], 2 * beta[:, None] * B], axis=1)
+    rate = np.einsum("evp,evp,p->", w, D, wq)
+    mag = np.einsum("evp,evp,p->", np.abs(w), np.abs(D), wq)
+    assert abs(rate) < 1e-12 * mag, (rate, mag)
+
+
+def test_mhd_ec_steps_match_oracle(orc):
+    N, n = 3, (4, 3, 2)
+    xi, _ = orc.lgl(N)
+    u0 = W.alfven_wave(N, n, xi, 0.0, gamma=G)
+    m = mesh(N, n, sflux="ec", vflux="ec")
+    ut = torch.from_numpy(u0.copy()).cuda()
+    ref = u0.copy()
+    for _ in range(5):
+        m.step_cfl(ut, cfl=0.5)
+        ref = orc.mhd_lsrk_step(N, n, W.box(3), ref, m.last_dt(), G, True, sflux="ec",
+                                vflux="ec")
+    assert m.check() == 0
+    got = ut.cpu().numpy()
+    assert rel_l2(got - u0, ref - u0) <= 1e-11
