@@ -100,26 +100,28 @@ __device__ __forceinline__ double fast_speed2(const MState& s, double gamma) {
   return 0.5 * (q + sqrt(fmax(q * q - 4.0 * a2 * bn2, 0.0)));
 }
 
-// node quantities of the entropy-conservative two-point flux: beta =
-// rho/(2p) and the products whose means it takes
+// node quantities of the entropy-conservative two-point flux, pre-scaled so
+// that each mean is one addition: beta = rho/(2p), hv = v/2, hB = B/2,
+// pm = (rho + beta |B|^2)/2, qv2 = |v|^2/4, qB2 = |B|^2/4, hvB = v.B/2
 struct ECq {
-  double rho, beta, v[3], B[3], v2, B2, vB, bB2;
+  double rho, beta, hv[3], hB[3], pm, qv2, qB2, hvB;
 };
 
 __device__ __forceinline__ ECq ec_of(const MState& s) {
   ECq q;
   q.rho = s.rho;
   q.beta = 0.5 * s.rho / s.p;
-  q.v2 = 0.0;
-  q.vB = s.vb;
-  q.B2 = s.b2;
+  double v2 = 0.0;
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
-    q.v[k] = s.v[k];
-    q.B[k] = s.B[k];
-    q.v2 = fma(s.v[k], s.v[k], q.v2);
+    q.hv[k] = 0.5 * s.v[k];
+    q.hB[k] = 0.5 * s.B[k];
+    v2 = fma(s.v[k], s.v[k], v2);
   }
-  q.bB2 = q.beta * s.b2;
+  q.pm = 0.5 * fma(q.beta, s.b2, s.rho);
+  q.qv2 = 0.25 * v2;
+  q.qB2 = 0.25 * s.b2;
+  q.hvB = 0.5 * s.vb;
   return q;
 }
 
@@ -131,12 +133,13 @@ __device__ __forceinline__ ECq ec_of(const MState& s) {
 //   f_E = f_rho (1/(2(gamma-1) beta_ln) - {|v|^2}/2) + f_m.{v} + f_B.{B}
 //         - {v_n}{|B|^2}/2 + {B_n}{v.B}.
 template <int DIR>
-__device__ __forceinline__ void mhd_ec_flux(const ECq& a, const ECq& b, double gm1inv, double* f) {
+__device__ __forceinline__ void mhd_ec_flux(const ECq& a, const ECq& b, double hgm1inv,
+                                            double* f) {
   double va[3], Ba[3];
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
-    va[k] = 0.5 * (a.v[k] + b.v[k]);
-    Ba[k] = 0.5 * (a.B[k] + b.B[k]);
+    va[k] = a.hv[k] + b.hv[k];
+    Ba[k] = a.hB[k] + b.hB[k];
   }
   const double rho_ln = ln_mean(a.rho, b.rho);
   const double inv_beta_ln = inv_ln_mean(a.beta, b.beta);
@@ -144,14 +147,17 @@ __device__ __forceinline__ void mhd_ec_flux(const ECq& a, const ECq& b, double g
   f[0] = f0;
 #pragma unroll
   for (int k = 0; k < 3; ++k) f[1 + k] = fma(f0, va[k], -Ba[DIR] * Ba[k]);
-  f[1 + DIR] += (0.5 * (a.rho + b.rho) + 0.5 * (a.bB2 + b.bB2)) / (a.beta + b.beta);
+  f[1 + DIR] += (a.pm + b.pm) / (a.beta + b.beta);
 #pragma unroll
   for (int k = 0; k < 3; ++k) f[5 + k] = (k == DIR) ? 0.0 : fma(va[DIR], Ba[k], -Ba[DIR] * va[k]);
-  double e = f0 * (0.5 * gm1inv * inv_beta_ln - 0.25 * (a.v2 + b.v2));
+  double e = f0 * fma(hgm1inv, inv_beta_ln, -(a.qv2 + b.qv2));
 #pragma unroll
-  for (int k = 0; k < 3; ++k) e = fma(f[1 + k], va[k], fma(f[5 + k], Ba[k], e));
-  e = fma(-0.25 * va[DIR], a.B2 + b.B2, e);
-  f[4] = fma(0.5 * Ba[DIR], a.vB + b.vB, e);
+  for (int k = 0; k < 3; ++k) {
+    e = fma(f[1 + k], va[k], e);
+    if (k != DIR) e = fma(f[5 + k], Ba[k], e);
+  }
+  e = fma(-va[DIR], a.qB2 + b.qB2, e);
+  f[4] = fma(Ba[DIR], a.hvB + b.hvB, e);
 }
 
 template <int N, int DIR, int SF>
@@ -180,7 +186,7 @@ __device__ __forceinline__ void mhd_surface_body(const double* __restrict__ u,
     const long long off = e * NF + l;
     if (SF == kMhdEc) {
       double f[kMV];
-      mhd_ec_flux<DIR>(ec_of(sl), ec_of(sr), g.gm1inv, f);
+      mhd_ec_flux<DIR>(ec_of(sl), ec_of(sr), 0.5 * g.gm1inv, f);
 #pragma unroll
       for (int v = 0; v < kMV; ++v) fs[(long long)(DIR * kMQ + v) * base + off] = f[v];
     } else if (SF == kMhdHll) {
@@ -350,7 +356,7 @@ struct MPairs {
   static constexpr int WORK = LINES * NPAIRS;
   static constexpr int MAXW = WORK > P ? WORK : P;
   static constexpr int THREADS = MAXW < 512 ? ((MAXW + 31) / 32) * 32 : 512;
-  static constexpr int NQ = 12;  // rho, beta, v, B, |v|^2, |B|^2, v.B, beta |B|^2
+  static constexpr int NQ = 12;  // the ECq slots: rho, beta, hv, hB, pm, qv2, qB2, hvB
   static constexpr int SMEM = (NQ + kMV + 1) * P * (int)sizeof(double) +
                               WORK * kMV * (int)sizeof(double);
 };
@@ -362,13 +368,13 @@ __device__ __forceinline__ ECq ec_load(const double (*sq)[(N + 1) * (N + 1) * (N
   q.beta = sq[1][n];
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
-    q.v[k] = sq[2 + k][n];
-    q.B[k] = sq[5 + k][n];
+    q.hv[k] = sq[2 + k][n];
+    q.hB[k] = sq[5 + k][n];
   }
-  q.v2 = sq[8][n];
-  q.B2 = sq[9][n];
-  q.vB = sq[10][n];
-  q.bB2 = sq[11][n];
+  q.pm = sq[8][n];
+  q.qv2 = sq[9][n];
+  q.qB2 = sq[10][n];
+  q.hvB = sq[11][n];
   return q;
 }
 
@@ -387,9 +393,9 @@ __device__ __forceinline__ void mhd_ec_direction(const double (*sq)[(N + 1) * (N
     pair_of<N>(w % NPAIRS, a, b);
     double f[kMV];
     mhd_ec_flux<DIR>(ec_load<N>(sq, line_node<3, N, DIR>(l, a)),
-                     ec_load<N>(sq, line_node<3, N, DIR>(l, b)), g.gm1inv, f);
+                     ec_load<N>(sq, line_node<3, N, DIR>(l, b)), 0.5 * g.gm1inv, f);
 #pragma unroll
-    for (int v = 0; v < kMV; ++v) pf[w * kMV + v] = f[v];
+    for (int v = 0; v < kMV; ++v) pf[v * C::WORK + w] = f[v];
   }
   __syncthreads();
   for (int node = threadIdx.x; node < P; node += blockDim.x) {
@@ -398,14 +404,14 @@ __device__ __forceinline__ void mhd_ec_direction(const double (*sq)[(N + 1) * (N
     double acc[kMV], dn = 0.0;
 #pragma unroll
     for (int v = 0; v < kMV; ++v) acc[v] = 0.0;
-    const double bi = sq[5 + DIR][node];
+    const double bi = sq[5 + DIR][node];  // B_n / 2
     for (int j = 0; j < NP; ++j) {
       if (j == i) continue;
       const int p = j < i ? pair_index<N>(j, i) : pair_index<N>(i, j);
       const double dij = sD[DIR][i][j];
 #pragma unroll
-      for (int v = 0; v < kMV; ++v) acc[v] = fma(dij, pf[(l * NPAIRS + p) * kMV + v], acc[v]);
-      dn = fma(dij, 0.5 * (bi + sq[5 + DIR][line_node<3, N, DIR>(l, j)]), dn);
+      for (int v = 0; v < kMV; ++v) acc[v] = fma(dij, pf[v * C::WORK + l * NPAIRS + p], acc[v]);
+      dn = fma(dij, bi + sq[5 + DIR][line_node<3, N, DIR>(l, j)], dn);
     }
     if (i == N || i == 0) {
       const long long ef = i == N ? e : neighbour(g, e, DIR, -1);
@@ -447,13 +453,13 @@ __global__ void __launch_bounds__(MPairs<N>::THREADS)
     sq[1][node] = q.beta;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-      sq[2 + k][node] = q.v[k];
-      sq[5 + k][node] = q.B[k];
+      sq[2 + k][node] = q.hv[k];
+      sq[5 + k][node] = q.hB[k];
     }
-    sq[8][node] = q.v2;
-    sq[9][node] = q.B2;
-    sq[10][node] = q.vB;
-    sq[11][node] = q.bB2;
+    sq[8][node] = q.pm;
+    sq[9][node] = q.qv2;
+    sq[10][node] = q.qB2;
+    sq[11][node] = q.hvB;
 #pragma unroll
     for (int v = 0; v <= kMV; ++v) sa[v][node] = 0.0;
   }
@@ -469,13 +475,14 @@ __global__ void __launch_bounds__(MPairs<N>::THREADS)
 #pragma unroll
     for (int v = 0; v < kMV; ++v) acc[v] = sa[v][node];
     if (powell) {
-      const double dn = sa[kMV][node];
+      // Phi = (0, B, v.B, v) from the halved slots: 2 x (hB, hvB, hv)
+      const double dn2 = 2.0 * sa[kMV][node];
 #pragma unroll
       for (int k = 0; k < 3; ++k) {
-        acc[1 + k] = fma(sq[5 + k][node], dn, acc[1 + k]);
-        acc[5 + k] = fma(sq[2 + k][node], dn, acc[5 + k]);
+        acc[1 + k] = fma(sq[5 + k][node], dn2, acc[1 + k]);
+        acc[5 + k] = fma(sq[2 + k][node], dn2, acc[5 + k]);
       }
-      acc[4] = fma(sq[10][node], dn, acc[4]);
+      acc[4] = fma(sq[11][node], dn2, acc[4]);
     }
 #pragma unroll
     for (int v = 0; v < kMV; ++v) {
