@@ -72,13 +72,16 @@ def _code_only(text):
     return re.sub(r"\s+", "", text)
 
 
-def source_sha():
+MHD_KERNEL_SOURCES = ("dg_device.cuh", "dg_mhd.cu")
+
+
+def source_sha(files=KERNEL_SOURCES):
     """Hash of the code (comments and whitespace removed) of the sources that
-    define the rhs kernels: a committed ncu figure is only used while it is
-    unchanged."""
+    define a family of kernels (the Euler rhs kernels by default): a
+    committed ncu figure is only used while it is unchanged."""
     h = hashlib.sha1()
     csrc = os.path.join(ROOT, "paper_2108_06476_gb300", "csrc")
-    for fn in KERNEL_SOURCES:
+    for fn in files:
         with open(os.path.join(csrc, fn)) as fh:
             h.update(fn.encode() + _code_only(fh.read()).encode())
     return h.hexdigest()[:12]
@@ -93,7 +96,10 @@ def ncu_record(key, field):
             rec = json.load(fh).get(key)
     except (OSError, ValueError):
         return None
-    if not rec or rec.get("src_sha") != source_sha():
+    if not rec:
+        return None
+    files = tuple(rec.get("sources", KERNEL_SOURCES))
+    if rec.get("src_sha") != (source_sha() if files == KERNEL_SOURCES else source_sha(files)):
         return None
     return rec.get(field)
 
@@ -391,6 +397,7 @@ def run_mhd(args, timed, kernel_ms):
     fl = mhd_volume_flops_per_node(N)
     vol = out["hll"]["kernels_ms"]["volume_rhs_only"]
     ach = fl * M / (vol / 1e3) / 1e12
+    traffic = ncu_traffic("fp64_mhd_volume_n3")
     return {"workload": f"3D ideal MHD, circularly polarised Alfven wave, {ne}^3 elements, "
                         "N = 3, weak form + Powell term, HLL faces, CFL 0.5, CUDA-graph steps",
             "value": out["hll"]["value"], "unit": UNIT, "ms_per_step": out["hll"]["ms_per_step"],
@@ -399,7 +406,8 @@ def run_mhd(args, timed, kernel_ms):
             "ec_flux_differencing": out["ec"],
             "roofline": {"bound": "alu", "kernel": "mhd_volume_kernel (rhs only)",
                          "flops_per_node": fl, "achieved": ach, "peak": FP64_PEAK_TFLOPS,
-                         "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS}}
+                         "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS,
+                         "traffic": None if traffic is None else traffic * M}}
 
 
 def max_over_ranks(ms, dist, device="cuda"):

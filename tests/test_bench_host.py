@@ -31,3 +31,20 @@ def test_volume_flops_per_node_formula():
     # 3D N = 3: 4.5 pairs per node of 81 flop, a 12-flop prologue and the
     # lifting at the line ends
     assert abs(bench.volume_flops_per_node(3, 3) - 391.5) < 1e-9
+
+
+def test_traffic_records_of_other_kernel_families_use_their_own_sources(tmp_path, monkeypatch):
+    files = bench.MHD_KERNEL_SOURCES
+    rec = {"fp64_mhd_volume_n3": {"bytes_per_node": 130.0, "sources": list(files),
+                                  "src_sha": bench.source_sha(files)}}
+    (tmp_path / "profiles").mkdir()
+    (tmp_path / "profiles" / "dram_traffic.json").write_text(json.dumps(rec))
+    real_root = bench.ROOT
+    sha = bench.source_sha(files)
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    monkeypatch.setattr(bench, "source_sha",
+                        lambda f=bench.KERNEL_SOURCES: sha if f == files else "000000000000")
+    assert bench.ncu_traffic("fp64_mhd_volume_n3") == 130.0
+    monkeypatch.setattr(bench, "source_sha", lambda f=bench.KERNEL_SOURCES: "111111111111")
+    assert bench.ncu_traffic("fp64_mhd_volume_n3") is None
+    assert real_root

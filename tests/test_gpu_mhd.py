@@ -142,10 +142,11 @@ def test_mhd_steps_match_oracle(orc, sflux):
     assert rel_l2(got - u0, ref - u0) <= 1e-11
 
 
-def test_mhd_fused_graph_and_unfused_steps_agree(orc):
+@pytest.mark.parametrize("vflux,sflux", [("central", "llf"), ("ec", "ec")])
+def test_mhd_fused_graph_and_unfused_steps_agree(orc, vflux, sflux):
     N, n = 3, (4, 4, 3)
     u0 = W.mhd_random_state(N, n, seed=12, gamma=G)
-    m1, m2, m3 = mesh(N, n), mesh(N, n), mesh(N, n)
+    m1, m2, m3 = (mesh(N, n, sflux=sflux, vflux=vflux) for _ in range(3))
     a = torch.from_numpy(u0.copy()).cuda()
     b = torch.from_numpy(u0.copy()).cuda()
     c = torch.from_numpy(u0.copy()).cuda()
@@ -162,10 +163,11 @@ def test_mhd_fused_graph_and_unfused_steps_agree(orc):
     assert rel_l2(inc_b, inc_a) <= 1e-13
 
 
-def test_mhd_host_state_step_equals_device_step(orc):
+@pytest.mark.parametrize("vflux,sflux", [("central", "hll"), ("ec", "ec")])
+def test_mhd_host_state_step_equals_device_step(orc, vflux, sflux):
     N, n = 2, (3, 3, 3)
     u0 = W.mhd_random_state(N, n, seed=13, gamma=G)
-    m1, m2 = mesh(N, n), mesh(N, n)
+    m1, m2 = mesh(N, n, sflux=sflux, vflux=vflux), mesh(N, n, sflux=sflux, vflux=vflux)
     a = torch.from_numpy(u0.copy()).cuda()
     for _ in range(2):
         m1.step_cfl(a, cfl=0.4)
@@ -333,3 +335,25 @@ def test_mhd_ec_steps_match_oracle(orc):
     assert m.check() == 0
     got = ut.cpu().numpy()
     assert rel_l2(got - u0, ref - u0) <= 1e-11
+
+
+
+@pytest.mark.parametrize("vflux,sflux", [("central", "hll"), ("ec", "ec")])
+def test_mhd_rhs_part_fused_volume_leaves_state_unchanged(orc, vflux, sflux):
+    """parts = 6 (the fused step's volume kernel with B = 0, used to time it)
+    leaves u unchanged and the face buffer consistent with a plain rhs."""
+    N, n = 3, (4, 3, 2)
+    u0 = W.mhd_random_state(N, n, seed=14, gamma=G)
+    m = mesh(N, n, sflux=sflux, vflux=vflux)
+    u = torch.from_numpy(u0.copy()).cuda()
+    m.step_cfl(u, cfl=0.3)  # sets the device time step
+    before = u.clone()
+    du = m.empty_rhs()
+    m.rhs_part(u, du, 1)
+    for _ in range(3):
+        m.rhs_part(u, du, 6)
+    torch.cuda.synchronize()
+    assert torch.equal(u, before)
+    assert m.check() == 0
+    ref = orc.mhd_rhs(N, n, W.box(3), before.cpu().numpy(), G, True, sflux=sflux, vflux=vflux)
+    assert rel_l2(m.rhs(u).cpu().numpy(), ref) <= TOL64
