@@ -1,32 +1,38 @@
-// 3D ideal magnetohydrodynamics (MHD) on the uniform periodic Cartesian mesh:
-// the weak-form DGSEM (the split form with the central volume flux, written
-// in its strong form) with the Powell non-conservative term and local
-// Lax-Friedrichs surface fluxes, as used for the Alfven-wave runs of
-// Sec. 3.1.
+// 3D ideal magnetohydrodynamics (MHD) on the uniform periodic Cartesian mesh
+// with the Powell non-conservative term: the paper's two MHD solvers for the
+// Alfven-wave runs of Sec. 3.1, the weak-form DGSEM (the split form with the
+// central volume flux, written in its strong form) with HLL or local
+// Lax-Friedrichs faces, and flux differencing with an entropy-conservative
+// (EC) two-point flux in the volume and at the faces.
 //
 // Variables u = (rho, rho v, E, B), E = p/(gamma-1) + rho|v|^2/2 + |B|^2/2.
-// With D the LGL derivative matrix, Dn = -(2/h) D, liftR = -(2/h)/w_N and
-// liftL = +(2/h)/w_0 per direction, node i of a line gets
+// Weak form: with D the LGL derivative matrix, Dn = -(2/h) D, liftR =
+// -(2/h)/w_N and liftL = +(2/h)/w_0 per direction, node i of a line gets
 //   du_i += sum_b Dn_ib f(u_b) + [i = N] liftR (F*_R - f(u_i))
 //                              + [i = 0] liftL (F*_L - f(u_i)),
 // which equals -(2/h) (sum_m Dt_im (f_i + f_m)/2 + [i = N] F*_R/w_N -
 // [i = 0] F*_L/w_0), Dt = 2D - W^-1 B, since the rows of Dt sum to -B_ii/w_i.
+// EC flux differencing: the split form itself, -(2/h) (sum_m Dt_im
+// f#(u_i, u_m) + the same lifting of F*), f# the EC flux.
 // The Powell term is -Phi(u_i) div B_i with Phi = (0, B, v.B, v) and div B
-// the same strong-form derivative of B_n with the interface average {B_n} in
-// place of F*: the kernel accumulates -div B with the tables above and adds
-// Phi times it.
+// the split-form derivative of B_n (central two-point value (B_i + B_m)/2,
+// the interface average {B_n} at faces): the kernels accumulate -div B and
+// add Phi times it.
 //
 // Kernels of one rhs evaluation:
 //   mhd_surface_kernel: one thread per face node; F* = LLF(u_L, u_R) with
-//     lambda = max(|v_n,L|, |v_n,R|) + max(c_f,L, c_f,R), or HLL with S_L =
+//     lambda = max(|v_n,L|, |v_n,R|) + max(c_f,L, c_f,R), HLL with S_L =
 //     min(v_n,L - c_f,L, v_n,R - c_f,R), S_R = max(v_n,L + c_f,L, v_n,R +
-//     c_f,R), and {B_n}, stored as nine values per face node in
+//     c_f,R), or the EC flux; and {B_n}; nine values per face node in
 //     fs[dir][q][e_left][l].
-//   mhd_volume_kernel: one CTA per EPB elements, one thread per node; per
-//     direction each thread writes f(u_i) (B_n in the slot of the zero
-//     normal induction flux) to shared memory, then applies its line's row
-//     of Dn and the lifting; epilogue: the Powell term, then the store of du
-//     or the fused stage update.
+//   mhd_volume_kernel (weak form): one CTA per EPB elements, one thread per
+//     node; per direction each thread writes f(u_i) (B_n in the slot of the
+//     zero normal induction flux) to shared memory, then applies its line's
+//     row of Dn and the lifting; epilogue: the Powell term, then the store
+//     of du or the fused stage update.
+//   mhd_volume_ec_kernel (EC flux differencing): one element per CTA; per
+//     direction one thread per (line, node pair) evaluates f# once for both
+//     nodes, then one thread per node sums its line (below).
 //   mhd_speed_kernel: one warp per element; sum_dir (2/h) max(|v_dir| + c_f)
 //     into the mesh's wave-speed word (CFL step).
 #include <cuda_runtime.h>
