@@ -102,6 +102,12 @@ def _declare(L):
                                  ctypes.c_int]
         L.or_mhd_max_dt.argtypes = [ctypes.c_int, _ip, _dp, ctypes.c_double, ctypes.c_double, _dp]
         L.or_mhd_max_dt.restype = ctypes.c_double
+        L.or_mhd_curved_rhs.argtypes = [ctypes.c_int, _ip, ctypes.c_double, ctypes.c_int,
+                                        ctypes.c_int, ctypes.c_int, _dp, _dp, _dp, _dp, _llp,
+                                        ctypes.c_longlong, ctypes.c_int]
+        L.or_mhd_curved_max_dt.argtypes = [ctypes.c_int, _ip, ctypes.c_double, ctypes.c_double,
+                                           _dp, _dp, _dp]
+        L.or_mhd_curved_max_dt.restype = ctypes.c_double
     return L
 
 
@@ -459,3 +465,26 @@ def mhd_lsrk_step(N, n, dom, u, dt, gamma=5.0 / 3.0, powell=True, nthreads=0, sf
         du = mhd_rhs(N, n, dom, u, gamma, powell, nthreads=nthreads, sflux=sflux, vflux=vflux)
         rk_stage(u, k, du, A[s], B[s], dt)
     return u
+
+
+def mhd_curved_rhs(geom, u, gamma=5.0 / 3.0, powell=True, vflux="central", sflux="llf",
+                   elems=None, nthreads=0):
+    """du of the MHD operator on the warped box (geometry from CurvedGeometry)."""
+    u = _f64(u)
+    du = np.zeros_like(u)
+    if elems is None:
+        ep, ne = None, 0
+    else:
+        elems = np.ascontiguousarray(elems, dtype=np.int64)
+        ep, ne = elems.ctypes.data_as(_llp), len(elems)
+    rc = lib().or_mhd_curved_rhs(geom.N, _n3(geom.n), gamma, int(bool(powell)), MHD_VFLUX[vflux],
+                                 MHD_SFLUX[sflux], _d(geom.Ja), _d(geom.J), _d(u), _d(du), ep,
+                                 ne, nthreads)
+    if rc != 0:
+        raise ValueError("bad curved MHD rhs arguments")
+    return du
+
+
+def mhd_curved_max_dt(geom, u, cfl=0.5, gamma=5.0 / 3.0):
+    return lib().or_mhd_curved_max_dt(geom.N, _n3(geom.n), gamma, cfl, _d(geom.Ja), _d(geom.J),
+                                      _d(_f64(u)))

@@ -317,3 +317,194 @@ double or_mhd_max_dt(int N, const int *n, const double *dom, double gamma, doubl
   }
   return cfl * 2.0 / ((N + 1) * worst);
 }
+
+/* ---- the warped periodic box of the paper's performance runs (Sec. 3.1) ----
+ * The same operators on the curvilinear mesh of dgsem_curved.c (geometry:
+ * metric terms Ja[e][r][d][P] = (J a^r)_d and Jacobians J[e][P] from
+ * or_curved_geometry): in direction r the two-point flux is taken along the
+ * mean of the two nodes' metric vectors, sum_d g_d f#_d, the face flux along
+ * the metric vector of the left element's face node (LLF and HLL in the unit
+ * direction, scaled by its length), the Powell divergence as
+ * (1/J) sum_r [sum_m Dt_im g_im . (B_i + B_m)/2 + face terms with
+ * {B} . g], and du = -(1/J) (...) - Phi (div B). */
+
+/* fast magnetosonic speed in the unit direction nh */
+static double mhd_fast_speed_dir(double gamma, const double *nh, const double *u) {
+  double rho, v[3], p;
+  mhd_prim(gamma, u, &rho, v, &p);
+  const double *B = u + 5;
+  const double a2 = gamma * p / rho;
+  const double b2 = (B[0] * B[0] + B[1] * B[1] + B[2] * B[2]) / rho;
+  const double bn = B[0] * nh[0] + B[1] * nh[1] + B[2] * nh[2];
+  const double bn2 = bn * bn / rho;
+  const double s = a2 + b2;
+  return sqrt(0.5 * (s + sqrt(s * s - 4.0 * a2 * bn2)));
+}
+
+/* sum_d g_d f_d(u) */
+static void mhd_flux_dir(double gamma, const double *g, const double *u, double *f) {
+  double fd[MV];
+  for (int v = 0; v < MV; ++v) f[v] = 0.0;
+  for (int d = 0; d < 3; ++d) {
+    or_mhd_flux(d, gamma, u, fd);
+    for (int v = 0; v < MV; ++v) f[v] += g[d] * fd[v];
+  }
+}
+
+/* two-point volume flux along g: central or EC (sum_d g_d f#_d) */
+static void mhd_volume_dir(int vflux, double gamma, const double *g, const double *ui,
+                           const double *um, double *f) {
+  if (vflux == 1) {
+    double fd[MV];
+    for (int v = 0; v < MV; ++v) f[v] = 0.0;
+    for (int d = 0; d < 3; ++d) {
+      or_mhd_flux_ec(d, gamma, ui, um, fd);
+      for (int v = 0; v < MV; ++v) f[v] += g[d] * fd[v];
+    }
+    return;
+  }
+  double fi[MV], fm[MV];
+  mhd_flux_dir(gamma, g, ui, fi);
+  mhd_flux_dir(gamma, g, um, fm);
+  for (int v = 0; v < MV; ++v) f[v] = 0.5 * (fi[v] + fm[v]);
+}
+
+/* face flux along the (non-normalised) metric vector g: 0 LLF, 1 HLL (in the
+ * unit direction, scaled by |g|), 2 EC */
+static void mhd_surface_dir(int sflux, double gamma, const double *g, const double *uL,
+                            const double *uR, double *f) {
+  if (sflux == 2) {
+    mhd_volume_dir(1, gamma, g, uL, uR, f);
+    return;
+  }
+  const double gn = sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
+  const double nh[3] = {g[0] / gn, g[1] / gn, g[2] / gn};
+  double fl[MV], fr[MV];
+  mhd_flux_dir(gamma, g, uL, fl);
+  mhd_flux_dir(gamma, g, uR, fr);
+  const double vl = (uL[1] * nh[0] + uL[2] * nh[1] + uL[3] * nh[2]) / uL[0];
+  const double vr = (uR[1] * nh[0] + uR[2] * nh[1] + uR[3] * nh[2]) / uR[0];
+  const double cl = mhd_fast_speed_dir(gamma, nh, uL), cr = mhd_fast_speed_dir(gamma, nh, uR);
+  if (sflux == 0) {
+    const double lam = fmax(fabs(vl), fabs(vr)) + fmax(cl, cr);
+    for (int v = 0; v < MV; ++v) f[v] = 0.5 * (fl[v] + fr[v]) - 0.5 * lam * gn * (uR[v] - uL[v]);
+    return;
+  }
+  const double sL = fmin(vl - cl, vr - cr), sR = fmax(vl + cl, vr + cr);
+  for (int v = 0; v < MV; ++v) {
+    if (sL >= 0.0) f[v] = fl[v];
+    else if (sR <= 0.0) f[v] = fr[v];
+    else f[v] = (sR * fl[v] - sL * fr[v] + sL * sR * gn * (uR[v] - uL[v])) / (sR - sL);
+  }
+}
+
+static void mhd_metric(const mmesh_t *m, const double *Ja, long long e, int r, long long node,
+                       double *g) {
+  for (int d = 0; d < 3; ++d) g[d] = Ja[((e * 3 + r) * 3 + d) * m->P + node];
+}
+
+/* du = rhs(u) on the warped box with geometry (Ja, J) of or_curved_geometry
+ * (elements_per_dim n, degree N), for the listed elements (all when elems is
+ * NULL). Flux ids as in or_mhd_rhs. Returns 0 or -1 on bad arguments. */
+int or_mhd_curved_rhs(int N, const int *n, double gamma, int powell, int vflux, int sflux,
+                      const double *Ja, const double *J, const double *u, double *du,
+                      const long long *elems, long long n_elems, int nthreads) {
+  mmesh_t m;
+  const double box[6] = {-1.0, 1.0, -1.0, 1.0, -1.0, 1.0};
+  if (mmesh_init(&m, N, n, box) || vflux < 0 || vflux > 1 || sflux < 0 || sflux > 2) return -1;
+  double Dt[NPMAX * NPMAX], w[NPMAX];
+  or_dtilde(N, Dt, w);
+  const long long count = elems ? n_elems : m.nelem;
+#ifdef _OPENMP
+  if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 4)
+#endif
+  for (long long s = 0; s < count; ++s) {
+    const long long e = elems ? elems[s] : s;
+    for (long long node = 0; node < m.P; ++node) {
+      double ui[MV], acc[MV], db = 0.0;
+      m_load(&m, u, e, node, ui);
+      for (int v = 0; v < MV; ++v) acc[v] = 0.0;
+      for (int r = 0; r < 3; ++r) {
+        const int i = m_coord(&m, node, r);
+        double gi[3];
+        mhd_metric(&m, Ja, e, r, node, gi);
+        for (int a = 0; a <= N; ++a) {
+          const long long nm = m_with(&m, node, r, a);
+          double um[MV], gm[3], g[3], f[MV];
+          m_load(&m, u, e, nm, um);
+          mhd_metric(&m, Ja, e, r, nm, gm);
+          for (int k = 0; k < 3; ++k) g[k] = 0.5 * (gi[k] + gm[k]);
+          mhd_volume_dir(vflux, gamma, g, ui, um, f);
+          for (int v = 0; v < MV; ++v) acc[v] += Dt[i * m.np + a] * f[v];
+          double bg = 0.0;
+          for (int k = 0; k < 3; ++k) bg += g[k] * 0.5 * (ui[5 + k] + um[5 + k]);
+          db += Dt[i * m.np + a] * bg;
+        }
+        if (i == N) {
+          double uo[MV], f[MV], bg = 0.0;
+          m_load(&m, u, m_neighbour(&m, e, r, +1), m_with(&m, node, r, 0), uo);
+          mhd_surface_dir(sflux, gamma, gi, ui, uo, f);
+          for (int v = 0; v < MV; ++v) acc[v] += f[v] / w[N];
+          for (int k = 0; k < 3; ++k) bg += gi[k] * 0.5 * (ui[5 + k] + uo[5 + k]);
+          db += bg / w[N];
+        }
+        if (i == 0) {
+          const long long el = m_neighbour(&m, e, r, -1), nl = m_with(&m, node, r, N);
+          double uo[MV], gl[3], f[MV], bg = 0.0;
+          m_load(&m, u, el, nl, uo);
+          mhd_metric(&m, Ja, el, r, nl, gl);
+          mhd_surface_dir(sflux, gamma, gl, uo, ui, f);
+          for (int v = 0; v < MV; ++v) acc[v] -= f[v] / w[0];
+          for (int k = 0; k < 3; ++k) bg += gl[k] * 0.5 * (uo[5 + k] + ui[5 + k]);
+          db -= bg / w[0];
+        }
+      }
+      const double Jn = J[e * m.P + node];
+      double phi[MV] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+      if (powell) {
+        double rho, v[3], p;
+        mhd_prim(gamma, ui, &rho, v, &p);
+        const double *B = ui + 5;
+        phi[1] = B[0];
+        phi[2] = B[1];
+        phi[3] = B[2];
+        phi[4] = v[0] * B[0] + v[1] * B[1] + v[2] * B[2];
+        phi[5] = v[0];
+        phi[6] = v[1];
+        phi[7] = v[2];
+      }
+      for (int v = 0; v < MV; ++v) du[(e * MV + v) * m.P + node] = -(acc[v] + phi[v] * db) / Jn;
+    }
+  }
+  return 0;
+}
+
+/* CFL time step on the warped box: dt = cfl 2 / ((N+1) max_e sum_r lam_r),
+ * lam_r = max over the element's nodes of (|v . J a^r| + c_f(a^r) |J a^r|) / J. */
+double or_mhd_curved_max_dt(int N, const int *n, double gamma, double cfl, const double *Ja,
+                            const double *J, const double *u) {
+  mmesh_t m;
+  const double box[6] = {-1.0, 1.0, -1.0, 1.0, -1.0, 1.0};
+  if (mmesh_init(&m, N, n, box)) return -1.0;
+  double worst = 0.0;
+  for (long long e = 0; e < m.nelem; ++e) {
+    double lam[3] = {0.0, 0.0, 0.0};
+    for (long long node = 0; node < m.P; ++node) {
+      double un[MV];
+      m_load(&m, u, e, node, un);
+      for (int r = 0; r < 3; ++r) {
+        double g[3];
+        mhd_metric(&m, Ja, e, r, node, g);
+        const double gn = sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
+        const double nh[3] = {g[0] / gn, g[1] / gn, g[2] / gn};
+        const double vg = (un[1] * g[0] + un[2] * g[1] + un[3] * g[2]) / un[0];
+        const double s = (fabs(vg) + mhd_fast_speed_dir(gamma, nh, un) * gn) / J[e * m.P + node];
+        if (s > lam[r]) lam[r] = s;
+      }
+    }
+    const double sum = lam[0] + lam[1] + lam[2];
+    if (sum > worst) worst = sum;
+  }
+  return cfl * 2.0 / ((N + 1) * worst);
+}

@@ -170,7 +170,12 @@ def alfven_wave(N, n, xi, t=0.0, amplitude=0.1, gamma=5.0 / 3.0, pressure=0.1):
     v = -A (sin phi e1 + cos phi e2), phi = pi (x + y + z) - pi sqrt(3) t,
     n = (1,1,1)/sqrt(3), e1 = (1,-1,0)/sqrt(2), e2 = n x e1: a wave moving
     along n at the Alfven speed |B.n|/sqrt(rho) = 1, an exact solution."""
-    X = node_coordinates(3, N, n, box(3), xi)
+    return alfven_wave_at(node_coordinates(3, N, n, box(3), xi), t, amplitude, gamma, pressure)
+
+
+def alfven_wave_at(X, t=0.0, amplitude=0.1, gamma=5.0 / 3.0, pressure=0.1):
+    """The Alfven wave of alfven_wave at given node coordinates X (3, n_elem,
+    nodes per element), e.g. those of the warped box."""
     phi = np.pi * (X[0] + X[1] + X[2]) - np.pi * np.sqrt(3.0) * t
     nv = np.ones(3) / np.sqrt(3.0)
     e1 = np.array([1.0, -1.0, 0.0]) / np.sqrt(2.0)
