@@ -141,6 +141,21 @@ int dg_mesh_create_curved(int N, const int *elements_per_dim, double warp, const
 int dg_mesh_create_mhd(int N, const int *elements_per_dim, const double *domain,
                        const dg_options *opt, int powell, void *cuda_stream, dg_mesh **out);
 
+/* The MHD operators of dg_mesh_create_mhd on the warped periodic box of
+ * dg_mesh_create_curved (the mesh of the paper's MHD performance runs,
+ * Sec. 3.1; same warp rule, geometry computed on the device): two-point
+ * fluxes along the mean metric vector of each node pair, sum_d g_d f#_d;
+ * face fluxes along the metric vector of the left element's face node (LLF
+ * and HLL in the unit direction scaled by its length, or EC); the Powell
+ * divergence (1/J) times the split-form sums of g . (B_i + B_m)/2 and the
+ * face terms {B} . g; du scaled by 1/J; the CFL rule with the contravariant
+ * speeds |v . J a^r| + c_f |J a^r|. The same calls as on dg_mesh_create_mhd
+ * meshes are accepted. Errors: DG_ERR_ARG (also for |warp| > 0.5),
+ * DG_ERR_OOM, DG_ERR_CUDA. */
+int dg_mesh_create_mhd_curved(int N, const int *elements_per_dim, double warp,
+                              const dg_options *opt, int powell, void *cuda_stream,
+                              dg_mesh **out);
+
 /* Source terms (curved meshes only): DG_SOURCE_MANUFACTURED adds
  * S = d_t u + div F(u) of the manufactured solution rho = 2 + 0.1 sin(pi (x +
  * y + z - t)), v = (1, 1, 1), E = rho^2 (the smooth Euler problem of the

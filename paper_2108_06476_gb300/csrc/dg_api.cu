@@ -436,6 +436,12 @@ int launch_speed(dg_mesh* m, const double* u, double* copy_to = nullptr) {
   // work (2 lanes per clock per SM) spreads over more SMs
   const int threads = (m->nelem * 32 < 152LL * 4 * 256) ? 32 : 256;
   const int grid = grid_for(m->nelem * 32, threads);
+  if (m->mhd && m->curved) {
+    DG_CUDA(dg::mhd_curved_speed_launch(u, m->Ja, m->invJ, m->geom, (int)m->P, m->speed, m->err,
+                                        copy_to, grid, threads, m->stream),
+            "MHD curved speed kernel launch");
+    return DG_OK;
+  }
   if (m->mhd) {
     const double s[3] = {2.0 / m->h[0], 2.0 / m->h[1], 2.0 / m->h[2]};
     DG_CUDA(dg::mhd_speed_launch(u, m->geom, (int)m->P, s, m->speed, m->err, copy_to, grid,
@@ -703,10 +709,11 @@ int dg_mesh_create_curved(int N, const int* epd, double warp, const dg_options* 
   return DG_OK;
 }
 
-int dg_mesh_create_mhd(int N, const int* epd, const double* domain, const dg_options* opt,
-                       int powell, void* cuda_stream, dg_mesh** out) {
-  if (out) *out = nullptr;
-  if (!out || !epd || !domain) return fail(DG_ERR_ARG, "dg_mesh_create_mhd: null argument");
+namespace {
+// Check and translate the MHD options; *euler receives options that the Euler
+// creators accept (the MHD path reads its own flux ids).
+int mhd_options(const char* who, const dg_options* opt, int powell, dg_options* euler, int* vf,
+                int* sf) {
   dg_options o = {5.0 / 3.0, DG_VFLUX_CENTRAL, DG_SFLUX_LLF, DG_FP64};
   if (opt) o = *opt;
   if (!(o.gamma > 1.0) || (powell != 0 && powell != 1) ||
@@ -715,23 +722,25 @@ int dg_mesh_create_mhd(int N, const int* epd, const double* domain, const dg_opt
        o.surface_flux != DG_SFLUX_EC) ||
       o.precision != DG_FP64)
     return fail(DG_ERR_ARG,
-                "dg_mesh_create_mhd: needs gamma > 1, powell 0 or 1, the central or EC volume "
-                "flux, an LLF, HLL or EC surface flux and FP64");
-  const int vf_mhd = o.volume_flux == DG_VFLUX_EC ? 1 : 0;
-  const int sf_mhd =
-      o.surface_flux == DG_SFLUX_HLL ? 1 : (o.surface_flux == DG_SFLUX_EC ? 2 : 0);
-  // the Euler options' checks of dg_mesh_create; the MHD path reads its own
+                "%s: needs gamma > 1, powell 0 or 1, the central or EC volume flux, an LLF, HLL "
+                "or EC surface flux and FP64",
+                who);
+  *vf = o.volume_flux == DG_VFLUX_EC ? 1 : 0;
+  *sf = o.surface_flux == DG_SFLUX_HLL ? 1 : (o.surface_flux == DG_SFLUX_EC ? 2 : 0);
   o.volume_flux = DG_VFLUX_CENTRAL;
   o.surface_flux = DG_SFLUX_LLF;
-  dg_mesh* m = nullptr;
-  int rc = dg_mesh_create(3, N, epd, domain, &o, cuda_stream, &m);
-  if (rc != DG_OK) return rc;
+  *euler = o;
+  return DG_OK;
+}
+
+// Turn a freshly created 3D mesh into an MHD mesh: eight variables (the RK
+// register and the face buffer, nine values per face node, sized anew) and
+// the weak-form tables Ds = -(2/h) D. Destroys the mesh on failure.
+int make_mhd(dg_mesh* m, int vf, int sf, int powell, const char* who) {
   m->mhd = 1;
-  m->mhd_sf = sf_mhd;
-  m->mhd_vf = vf_mhd;
+  m->mhd_sf = sf;
+  m->mhd_vf = vf;
   m->powell = powell;
-  // eight variables: the RK register and the face buffer (nine values per
-  // face node) are sized anew
   cudaFree(m->k);
   cudaFree(m->fs);
   m->k = nullptr;
@@ -744,21 +753,52 @@ int dg_mesh_create_mhd(int N, const int* epd, const double* domain, const dg_opt
       (e = cudaMalloc(&m->fs, nface * sizeof(double))) != cudaSuccess ||
       (e = cudaMemsetAsync(m->k, 0, m->nvalues * sizeof(double), m->stream)) != cudaSuccess ||
       (e = cudaStreamSynchronize(m->stream)) != cudaSuccess) {
-    rc = cuda_fail(e, "dg_mesh_create_mhd: cudaMalloc");
+    const int rc = cuda_fail(e, who);
     dg_mesh_destroy(m);
     return rc;
   }
   long double x[8], w[8], D[8][8];
-  lgl_basis(N, x, w);
-  diff_matrix(N, x, D);
+  lgl_basis(m->N, x, w);
+  diff_matrix(m->N, x, D);
   memset(&m->tmhd, 0, sizeof(m->tmhd));
   for (int k = 0; k < 3; ++k) {
     const long double sc = -2.0L / (long double)m->h[k];
-    for (int a = 0; a <= N; ++a)
-      for (int b = 0; b <= N; ++b) m->tmhd.Ds[k][a][b] = (double)(sc * D[a][b]);
-    m->tmhd.liftR[k] = (double)(sc / w[N]);
+    for (int a = 0; a <= m->N; ++a)
+      for (int b = 0; b <= m->N; ++b) m->tmhd.Ds[k][a][b] = (double)(sc * D[a][b]);
+    m->tmhd.liftR[k] = (double)(sc / w[m->N]);
     m->tmhd.liftL[k] = (double)(-sc / w[0]);
   }
+  return DG_OK;
+}
+}  // namespace
+
+int dg_mesh_create_mhd(int N, const int* epd, const double* domain, const dg_options* opt,
+                       int powell, void* cuda_stream, dg_mesh** out) {
+  if (out) *out = nullptr;
+  if (!out || !epd || !domain) return fail(DG_ERR_ARG, "dg_mesh_create_mhd: null argument");
+  dg_options o;
+  int vf, sf;
+  int rc = mhd_options("dg_mesh_create_mhd", opt, powell, &o, &vf, &sf);
+  if (rc != DG_OK) return rc;
+  dg_mesh* m = nullptr;
+  if ((rc = dg_mesh_create(3, N, epd, domain, &o, cuda_stream, &m)) != DG_OK) return rc;
+  if ((rc = make_mhd(m, vf, sf, powell, "dg_mesh_create_mhd: cudaMalloc")) != DG_OK) return rc;
+  *out = m;
+  return DG_OK;
+}
+
+int dg_mesh_create_mhd_curved(int N, const int* epd, double warp, const dg_options* opt,
+                              int powell, void* cuda_stream, dg_mesh** out) {
+  if (out) *out = nullptr;
+  if (!out || !epd) return fail(DG_ERR_ARG, "dg_mesh_create_mhd_curved: null argument");
+  dg_options o;
+  int vf, sf;
+  int rc = mhd_options("dg_mesh_create_mhd_curved", opt, powell, &o, &vf, &sf);
+  if (rc != DG_OK) return rc;
+  dg_mesh* m = nullptr;
+  if ((rc = dg_mesh_create_curved(N, epd, warp, &o, cuda_stream, &m)) != DG_OK) return rc;
+  if ((rc = make_mhd(m, vf, sf, powell, "dg_mesh_create_mhd_curved: cudaMalloc")) != DG_OK)
+    return rc;
   *out = m;
   return DG_OK;
 }
@@ -767,7 +807,7 @@ int dg_set_source(dg_mesh* m, int kind) {
   if (!valid_mesh(m)) return fail(DG_ERR_ARG, "dg_set_source: invalid mesh");
   if (kind != DG_SOURCE_NONE && kind != DG_SOURCE_MANUFACTURED)
     return fail(DG_ERR_ARG, "dg_set_source: unknown source %d", kind);
-  if (kind != DG_SOURCE_NONE && !m->curved)
+  if (kind != DG_SOURCE_NONE && (!m->curved || m->mhd))
     return fail(DG_ERR_ARG, "dg_set_source: source terms need a mesh from dg_mesh_create_curved");
   m->source = kind;
   if (m->graph) {  // a recorded step holds the old source choice
@@ -849,7 +889,11 @@ int dg_rhs_part(dg_mesh* m, const double* u, void* du, int parts) {
     parts = 2;
   }
   cudaError_t e;
-  if (m->mhd) {
+  if (m->mhd && m->curved) {
+    e = dg::mhd_curved_rhs_launch(m->N, u, (double*)du, (double*)m->fs, m->Ja, m->invJ, m->geom,
+                                  m->ctab, m->mhd_vf, m->powell, m->mhd_sf, m->err, m->stream,
+                                  parts, fz);
+  } else if (m->mhd) {
     e = dg::mhd_rhs_launch(m->N, u, (double*)du, (double*)m->fs, m->geom, m->tmhd, m->t64, m->mhd_vf, m->powell, m->mhd_sf,
                            m->err, m->stream, parts, fz);
   } else if (m->curved) {
@@ -914,7 +958,7 @@ int dg_rk_reset(dg_mesh* m) {
 
 int dg_step(dg_mesh* m, double* u, void* du, double dt) {
   if (!valid_mesh(m) || !u || !du) return fail(DG_ERR_ARG, "dg_step: null argument");
-  if (m->curved) {
+  if (m->curved && !m->mhd) {
     // source terms at the stage times t + c_s dt; the mesh time advances by dt
     set_dt_kernel<<<1, 1, 0, m->stream>>>(m->dt_dev, dt);
     DG_CUDA(cudaGetLastError(), "dg_step: launch");
@@ -960,7 +1004,11 @@ int enqueue_fused_stages(dg_mesh* m, double* u, double* out) {
     fz.b = kRkB[s];
     if (s == 4) fz.u_out = out;
     cudaError_t e;
-    if (m->mhd) {
+    if (m->mhd && m->curved) {
+      e = dg::mhd_curved_rhs_launch(m->N, u, nullptr, (double*)m->fs, m->Ja, m->invJ, m->geom,
+                                    m->ctab, m->mhd_vf, m->powell, m->mhd_sf, m->err, m->stream,
+                                    3, fz);
+    } else if (m->mhd) {
       e = dg::mhd_rhs_launch(m->N, u, nullptr, (double*)m->fs, m->geom, m->tmhd, m->t64, m->mhd_vf, m->powell, m->mhd_sf,
                              m->err, m->stream, 3, fz);
     } else if (m->curved) {

@@ -548,6 +548,429 @@ __global__ void mhd_speed_kernel(const double* __restrict__ u, Geom g, int P, do
   }
 }
 
+// ---- the warped periodic box (the paper's benchmark mesh) ----
+// Metric terms Ja[e][r][d][P] = (J a^r)_d and 1/J per node from the curved
+// geometry kernel. In direction r a two-point flux is taken along the mean
+// of the pair's metric vectors g, f(u; g) = sum_d g_d f_d(u) (every flux
+// component is linear in the direction), face fluxes along the metric vector
+// of the left element's face node (LLF, HLL in the unit direction scaled by
+// |g|, or EC), the Powell divergence as (1/J) times the split-form sums of
+// g . (B_i + B_m)/2 and {B} . g, du = (1/J) (...) with the unscaled
+// split-form table Ds = -Dt and liftR = -1/w_N, liftL = 1/w_0.
+
+// node quantities of the directional physical flux
+struct CMq {
+  double m[3], v[3], B[3], Ept, pt, vB;
+};
+
+__device__ __forceinline__ CMq cmq_of(const MState& s, const double* c) {
+  CMq q;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    q.m[k] = c[1 + k];
+    q.v[k] = s.v[k];
+    q.B[k] = s.B[k];
+  }
+  q.Ept = s.E + s.pt;
+  q.pt = s.pt;
+  q.vB = s.vb;
+  return q;
+}
+
+// f(u; g) = sum_d g_d f_d(u)
+__device__ __forceinline__ void mhd_flux_dir(const CMq& q, const double* g, double* f) {
+  const double vn = q.v[0] * g[0] + q.v[1] * g[1] + q.v[2] * g[2];
+  const double bn = q.B[0] * g[0] + q.B[1] * g[1] + q.B[2] * g[2];
+  f[0] = q.m[0] * g[0] + q.m[1] * g[1] + q.m[2] * g[2];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    f[1 + k] = fma(q.m[k], vn, fma(-q.B[k], bn, q.pt * g[k]));
+    f[5 + k] = fma(vn, q.B[k], -bn * q.v[k]);
+  }
+  f[4] = fma(vn, q.Ept, -bn * q.vB);
+}
+
+// EC flux along g (the Cartesian EC flux with its direction replaced by g)
+__device__ __forceinline__ void mhd_ec_flux_dir(const ECq& a, const ECq& b, const double* g,
+                                                double hgm1inv, double* f) {
+  double va[3], Ba[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    va[k] = a.hv[k] + b.hv[k];
+    Ba[k] = a.hB[k] + b.hB[k];
+  }
+  const double vg = va[0] * g[0] + va[1] * g[1] + va[2] * g[2];
+  const double bg = Ba[0] * g[0] + Ba[1] * g[1] + Ba[2] * g[2];
+  const double rho_ln = ln_mean(a.rho, b.rho);
+  const double inv_beta_ln = inv_ln_mean(a.beta, b.beta);
+  const double ph = (a.pm + b.pm) / (a.beta + b.beta);
+  const double f0 = rho_ln * vg;
+  f[0] = f0;
+  double e = f0 * fma(hgm1inv, inv_beta_ln, -(a.qv2 + b.qv2));
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    f[1 + k] = fma(f0, va[k], fma(-bg, Ba[k], ph * g[k]));
+    f[5 + k] = fma(vg, Ba[k], -bg * va[k]);
+    e = fma(f[1 + k], va[k], fma(f[5 + k], Ba[k], e));
+  }
+  e = fma(-vg, a.qB2 + b.qB2, e);
+  f[4] = fma(bg, a.hvB + b.hvB, e);
+}
+
+// fast magnetosonic speed squared in the unit direction nh
+__device__ __forceinline__ double fast_speed2_dir(const MState& s, const double* nh,
+                                                  double gamma) {
+  const double a2 = gamma * s.p * s.rr;
+  const double b2 = s.b2 * s.rr;
+  const double bn = s.B[0] * nh[0] + s.B[1] * nh[1] + s.B[2] * nh[2];
+  const double bn2 = bn * bn * s.rr;
+  const double q = a2 + b2;
+  return 0.5 * (q + sqrt(fmax(q * q - 4.0 * a2 * bn2, 0.0)));
+}
+
+template <int N, int DIR, int SF>
+__device__ __forceinline__ void mhd_curved_surface_body(const double* __restrict__ u,
+                                                        const double* __restrict__ Ja,
+                                                        double* __restrict__ fs, const Geom& g,
+                                                        unsigned& bad) {
+  constexpr int NP = N + 1, P = NP * NP * NP, NF = NP * NP;
+  const long long total = g.nelem * NF;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const long long e = t / NF;
+    const int l = (int)(t % NF);
+    const long long er = neighbour(g, e, DIR, +1);
+    const int nl = line_node<3, N, DIR>(l, N), nr = line_node<3, N, DIR>(l, 0);
+    double cl[kMV], cr[kMV], gv[3];
+#pragma unroll
+    for (int v = 0; v < kMV; ++v) {
+      cl[v] = u[(e * kMV + v) * P + nl];
+      cr[v] = u[(er * kMV + v) * P + nr];
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) gv[k] = Ja[((e * 3 + DIR) * 3 + k) * P + nl];
+    const MState sl = mhd_state(cl, g.gm1, bad), sr = mhd_state(cr, g.gm1, bad);
+    const long long base = g.nelem * NF;
+    const long long off = e * NF + l;
+    double F[kMV];
+    if (SF == kMhdEc) {
+      mhd_ec_flux_dir(ec_of(sl), ec_of(sr), gv, 0.5 * g.gm1inv, F);
+    } else {
+      double fl[kMV], fr[kMV];
+      mhd_flux_dir(cmq_of(sl, cl), gv, fl);
+      mhd_flux_dir(cmq_of(sr, cr), gv, fr);
+      const double gn = sqrt(gv[0] * gv[0] + gv[1] * gv[1] + gv[2] * gv[2]);
+      const double ign = 1.0 / gn;
+      const double nh[3] = {gv[0] * ign, gv[1] * ign, gv[2] * ign};
+      const double vl = sl.v[0] * nh[0] + sl.v[1] * nh[1] + sl.v[2] * nh[2];
+      const double vr = sr.v[0] * nh[0] + sr.v[1] * nh[1] + sr.v[2] * nh[2];
+      if (SF == kMhdHll) {
+        const double csl = sqrt(fast_speed2_dir(sl, nh, g.gamma));
+        const double csr = sqrt(fast_speed2_dir(sr, nh, g.gamma));
+        const double sL = fmin(vl - csl, vr - csr), sR = fmax(vl + csl, vr + csr);
+        const double inv = 1.0 / (sR - sL);
+#pragma unroll
+        for (int v = 0; v < kMV; ++v) {
+          if (sL >= 0.0) F[v] = fl[v];
+          else if (sR <= 0.0) F[v] = fr[v];
+          else F[v] = (sR * fl[v] - sL * fr[v] + sL * sR * gn * (cr[v] - cl[v])) * inv;
+        }
+      } else {
+        const double lam = fmax(fabs(vl), fabs(vr)) +
+                           sqrt(fmax(fast_speed2_dir(sl, nh, g.gamma),
+                                     fast_speed2_dir(sr, nh, g.gamma)));
+#pragma unroll
+        for (int v = 0; v < kMV; ++v) F[v] = 0.5 * (fl[v] + fr[v]) - 0.5 * lam * gn * (cr[v] - cl[v]);
+      }
+    }
+#pragma unroll
+    for (int v = 0; v < kMV; ++v) fs[(long long)(DIR * kMQ + v) * base + off] = F[v];
+    fs[(long long)(DIR * kMQ + 8) * base + off] =
+        0.5 * ((cl[5] + cr[5]) * gv[0] + (cl[6] + cr[6]) * gv[1] + (cl[7] + cr[7]) * gv[2]);
+  }
+}
+
+template <int N, int SF>
+__global__ void mhd_curved_surface_kernel(const double* __restrict__ u,
+                                          const double* __restrict__ Ja, double* __restrict__ fs,
+                                          Geom g, unsigned* __restrict__ err) {
+  unsigned bad = 0;
+  if (blockIdx.y == 0) mhd_curved_surface_body<N, 0, SF>(u, Ja, fs, g, bad);
+  else if (blockIdx.y == 1) mhd_curved_surface_body<N, 1, SF>(u, Ja, fs, g, bad);
+  else mhd_curved_surface_body<N, 2, SF>(u, Ja, fs, g, bad);
+  if (bad) atomicOr(err, bad);
+}
+
+// Volume: one element per CTA, the pair-parallel scheme of the EC kernel;
+// each thread owns at most one node (THREADS >= P for N <= 7), so the node
+// sums stay in registers across the three directions.
+template <int N>
+struct MCPairs {
+  static constexpr int NP = N + 1, P = NP * NP * NP, LINES = NP * NP;
+  static constexpr int NPAIRS = N * (N + 1) / 2;
+  static constexpr int WORK = LINES * NPAIRS;
+  static constexpr int MAXW = WORK > P ? WORK : P;
+  static constexpr int THREADS = MAXW < 512 ? ((MAXW + 31) / 32) * 32 : 512;
+  static constexpr int NQ = 12;  // ECq slots (EC) or CMq slots (central)
+  static constexpr int SMEM = (NQ + 3) * P * (int)sizeof(double) + WORK * kMQ * (int)sizeof(double);
+  static_assert(THREADS >= P, "one node per thread");
+};
+
+template <int N, int VF>
+__device__ __forceinline__ void cq_store(double (*sq)[(N + 1) * (N + 1) * (N + 1)], int n,
+                                         const MState& s, const double* c) {
+  if (VF == 1) {
+    const ECq q = ec_of(s);
+    sq[0][n] = q.rho;
+    sq[1][n] = q.beta;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      sq[2 + k][n] = q.hv[k];
+      sq[5 + k][n] = q.hB[k];
+    }
+    sq[8][n] = q.pm;
+    sq[9][n] = q.qv2;
+    sq[10][n] = q.qB2;
+    sq[11][n] = q.hvB;
+  } else {
+    const CMq q = cmq_of(s, c);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      sq[k][n] = q.m[k];
+      sq[3 + k][n] = q.v[k];
+      sq[6 + k][n] = q.B[k];
+    }
+    sq[9][n] = q.Ept;
+    sq[10][n] = q.pt;
+    sq[11][n] = q.vB;
+  }
+}
+
+template <int N>
+__device__ __forceinline__ CMq cmq_load(const double (*sq)[(N + 1) * (N + 1) * (N + 1)], int n) {
+  CMq q;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    q.m[k] = sq[k][n];
+    q.v[k] = sq[3 + k][n];
+    q.B[k] = sq[6 + k][n];
+  }
+  q.Ept = sq[9][n];
+  q.pt = sq[10][n];
+  q.vB = sq[11][n];
+  return q;
+}
+
+template <int N, int VF>
+__global__ void __launch_bounds__(MCPairs<N>::THREADS)
+    mhd_curved_volume_kernel(double* u, double* __restrict__ du, const double* __restrict__ fs,
+                             const double* __restrict__ Ja, const double* __restrict__ invJ,
+                             Geom g, CTables tb, int powell, unsigned* __restrict__ err,
+                             StageFuse fz) {
+  using C = MCPairs<N>;
+  constexpr int NP = C::NP, P = C::P, LINES = C::LINES, NPAIRS = C::NPAIRS;
+  extern __shared__ __align__(16) unsigned char dg_smem[];
+  double(*sq)[P] = reinterpret_cast<double(*)[P]>(dg_smem);                              // [NQ][P]
+  double(*sg)[P] = reinterpret_cast<double(*)[P]>(dg_smem + sizeof(double) * C::NQ * P);  // [3][P]
+  double* pf = reinterpret_cast<double*>(dg_smem + sizeof(double) * (C::NQ + 3) * P);  // [9][WORK]
+  __shared__ double sD[NP][NP];
+  for (int t = threadIdx.x; t < NP * NP; t += blockDim.x) sD[t / NP][t % NP] = tb.Ds[t / NP][t % NP];
+  const long long e = blockIdx.x;
+  const int node = threadIdx.x;
+  const bool owner = node < P;
+  unsigned bad = 0;
+  double c[kMV];
+  MState s;
+  if (owner) {
+#pragma unroll
+    for (int v = 0; v < kMV; ++v) c[v] = u[(e * kMV + v) * P + node];
+    s = mhd_state(c, g.gm1, bad);
+    cq_store<N, VF>(sq, node, s, c);
+  }
+  if (bad) atomicOr(err, bad);
+  double acc[kMV], dn = 0.0;
+#pragma unroll
+  for (int v = 0; v < kMV; ++v) acc[v] = 0.0;
+  const long long base = g.nelem * LINES;
+  const double hgm1inv = 0.5 * g.gm1inv;
+#pragma unroll 1
+  for (int r = 0; r < 3; ++r) {
+    if (owner) {
+#pragma unroll
+      for (int k = 0; k < 3; ++k) sg[k][node] = 0.5 * Ja[((e * 3 + r) * 3 + k) * P + node];
+    }
+    __syncthreads();
+    for (int w = threadIdx.x; w < C::WORK; w += blockDim.x) {
+      const int l = w / NPAIRS;
+      int a, b;
+      pair_of<N>(w % NPAIRS, a, b);
+      const int na = line_node_rt<3, N>(r, l, a), nb = line_node_rt<3, N>(r, l, b);
+      const double gv[3] = {sg[0][na] + sg[0][nb], sg[1][na] + sg[1][nb], sg[2][na] + sg[2][nb]};
+      double f[kMV], bb;
+      if (VF == 1) {
+        const ECq qa = ec_load<N>(sq, na), qb = ec_load<N>(sq, nb);
+        mhd_ec_flux_dir(qa, qb, gv, hgm1inv, f);
+        bb = (qa.hB[0] + qb.hB[0]) * gv[0] + (qa.hB[1] + qb.hB[1]) * gv[1] +
+             (qa.hB[2] + qb.hB[2]) * gv[2];
+      } else {
+        const CMq qa = cmq_load<N>(sq, na), qb = cmq_load<N>(sq, nb);
+        double fa[kMV], fb[kMV];
+        mhd_flux_dir(qa, gv, fa);
+        mhd_flux_dir(qb, gv, fb);
+#pragma unroll
+        for (int v = 0; v < kMV; ++v) f[v] = 0.5 * (fa[v] + fb[v]);
+        bb = 0.5 * ((qa.B[0] + qb.B[0]) * gv[0] + (qa.B[1] + qb.B[1]) * gv[1] +
+                    (qa.B[2] + qb.B[2]) * gv[2]);
+      }
+#pragma unroll
+      for (int v = 0; v < kMV; ++v) pf[v * C::WORK + w] = f[v];
+      pf[kMV * C::WORK + w] = bb;
+    }
+    __syncthreads();
+    if (owner) {
+      int l, i;
+      line_of<N>(r, node, l, i);
+      for (int j = 0; j < NP; ++j) {
+        if (j == i) continue;
+        const int p = j < i ? pair_index<N>(j, i) : pair_index<N>(i, j);
+        const double dij = sD[i][j];
+#pragma unroll
+        for (int v = 0; v < kMV; ++v) acc[v] = fma(dij, pf[v * C::WORK + l * NPAIRS + p], acc[v]);
+        dn = fma(dij, pf[kMV * C::WORK + l * NPAIRS + p], dn);
+      }
+      if (i == N || i == 0) {
+        const long long ef = i == N ? e : neighbour(g, e, r, -1);
+        const double lift = i == N ? tb.liftR : tb.liftL;
+        const double* src = fs + (long long)r * kMQ * base + ef * LINES + l;
+#pragma unroll
+        for (int v = 0; v < kMV; ++v) acc[v] = fma(lift, src[v * base], acc[v]);
+        dn = fma(lift, src[8 * base], dn);
+      }
+    }
+    __syncthreads();
+  }
+  if (!owner) return;
+  if (powell) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      acc[1 + k] = fma(s.B[k], dn, acc[1 + k]);
+      acc[5 + k] = fma(s.v[k], dn, acc[5 + k]);
+    }
+    acc[4] = fma(s.vb, dn, acc[4]);
+  }
+  const double ij = invJ[e * P + node];
+  const double dtv = fz.k ? *fz.dt : 0.0;
+  double* const uo = fz.u_out ? fz.u_out : u;
+#pragma unroll
+  for (int v = 0; v < kMV; ++v) {
+    const long long i = (e * kMV + v) * P + node;
+    const double val = ij * acc[v];
+    if (fz.k) {
+      double kk = dtv * val;
+      if (fz.a != 0.0) kk = fma(fz.a, fz.k[i], kk);
+      fz.k[i] = kk;
+      uo[i] = c[v] + fz.b * kk;
+    } else {
+      du[i] = val;
+    }
+  }
+}
+
+// per element sum_r max_nodes (|v . J a^r| + c_f(a^r) |J a^r|) / J, max over
+// elements (ordered bits)
+__global__ void mhd_curved_speed_kernel(const double* __restrict__ u,
+                                        const double* __restrict__ Ja,
+                                        const double* __restrict__ invJ, Geom g, int P,
+                                        unsigned long long* out, unsigned* err,
+                                        double* __restrict__ copy_to) {
+  const int lane = threadIdx.x & 31;
+  const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  double best = 0.0;
+  unsigned bad = 0;
+  for (long long e = warp; e < g.nelem; e += nwarps) {
+    double lam[3] = {0.0, 0.0, 0.0};
+    for (int node = lane; node < P; node += 32) {
+      double c[kMV];
+#pragma unroll
+      for (int v = 0; v < kMV; ++v) c[v] = u[(e * kMV + v) * P + node];
+      if (copy_to) {
+#pragma unroll
+        for (int v = 0; v < kMV; ++v) copy_to[(e * kMV + v) * P + node] = c[v];
+      }
+      const MState s = mhd_state(c, g.gm1, bad);
+      const double ij = invJ[e * P + node];
+#pragma unroll
+      for (int r = 0; r < 3; ++r) {
+        double gv[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) gv[k] = Ja[((e * 3 + r) * 3 + k) * P + node];
+        const double gn = sqrt(gv[0] * gv[0] + gv[1] * gv[1] + gv[2] * gv[2]);
+        const double nh[3] = {gv[0] / gn, gv[1] / gn, gv[2] / gn};
+        const double vg = s.v[0] * gv[0] + s.v[1] * gv[1] + s.v[2] * gv[2];
+        lam[r] = fmax(lam[r], (fabs(vg) + sqrt(fast_speed2_dir(s, nh, g.gamma)) * gn) * ij);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+      for (int off = 16; off > 0; off >>= 1)
+        lam[k] = fmax(lam[k], __shfl_xor_sync(0xffffffffu, lam[k], off));
+    best = fmax(best, lam[0] + lam[1] + lam[2]);
+  }
+  __shared__ double sb[32];
+  if (lane == 0) sb[threadIdx.x >> 5] = best;
+  if (bad) atomicOr(err, bad);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double m = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmax(m, sb[w]);
+    atomicMax(out, (unsigned long long)__double_as_longlong(m));
+  }
+}
+
+template <int N>
+cudaError_t mhd_curved_rhs_n(const double* u, double* du, double* fs, const double* Ja,
+                             const double* invJ, const Geom& g, const CTables& tb, int vf,
+                             int powell, int sf, unsigned* err, cudaStream_t st, int parts,
+                             const StageFuse& fz) {
+  constexpr int NF = (N + 1) * (N + 1);
+  if (parts & 1) {
+    const long long total = g.nelem * NF;
+    const int threads = (total < 152LL * 4 * 256) ? 64 : 256;
+    long long blocks = (total + threads - 1) / threads;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    if (blocks < 1) blocks = 1;
+    const dim3 grid((unsigned)blocks, 3);
+    if (sf == kMhdHll)
+      mhd_curved_surface_kernel<N, kMhdHll><<<grid, threads, 0, st>>>(u, Ja, fs, g, err);
+    else if (sf == kMhdEc)
+      mhd_curved_surface_kernel<N, kMhdEc><<<grid, threads, 0, st>>>(u, Ja, fs, g, err);
+    else
+      mhd_curved_surface_kernel<N, kMhdLlf><<<grid, threads, 0, st>>>(u, Ja, fs, g, err);
+  }
+  if (!(parts & 2)) return cudaGetLastError();
+  using C = MCPairs<N>;
+  cudaError_t e;
+  if (vf == 1) {
+    auto kern = mhd_curved_volume_kernel<N, 1>;
+    if (C::SMEM > 48 * 1024 &&
+        (e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM)) !=
+            cudaSuccess)
+      return e;
+    kern<<<(unsigned)g.nelem, C::THREADS, C::SMEM, st>>>(const_cast<double*>(u), du, fs, Ja,
+                                                          invJ, g, tb, powell, err, fz);
+  } else {
+    auto kern = mhd_curved_volume_kernel<N, 0>;
+    if (C::SMEM > 48 * 1024 &&
+        (e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM)) !=
+            cudaSuccess)
+      return e;
+    kern<<<(unsigned)g.nelem, C::THREADS, C::SMEM, st>>>(const_cast<double*>(u), du, fs, Ja,
+                                                          invJ, g, tb, powell, err, fz);
+  }
+  return cudaGetLastError();
+}
+
 // elements per CTA: about kMhdThreads threads
 template <int N>
 struct MLaunch {
@@ -631,6 +1054,33 @@ cudaError_t mhd_rhs_launch(int N, const double* u, double* du, double* fs, const
     case 7: return mhd_rhs_n<7>(u, du, fs, g, tb, tdt, vf, powell, sf, err, st, parts, fz);
     default: return cudaErrorInvalidValue;
   }
+}
+
+cudaError_t mhd_curved_rhs_launch(int N, const double* u, double* du, double* fs, const double* Ja,
+                                  const double* invJ, const Geom& g, const CTables& tb, int vf,
+                                  int powell, int sf, unsigned* err, cudaStream_t st, int parts,
+                                  const StageFuse& fz) {
+  switch (N) {
+#define DG_MC(n) \
+  case n:        \
+    return mhd_curved_rhs_n<n>(u, du, fs, Ja, invJ, g, tb, vf, powell, sf, err, st, parts, fz);
+    DG_MC(1)
+    DG_MC(2)
+    DG_MC(3)
+    DG_MC(4)
+    DG_MC(5)
+    DG_MC(6)
+    DG_MC(7)
+#undef DG_MC
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t mhd_curved_speed_launch(const double* u, const double* Ja, const double* invJ,
+                                    const Geom& g, int P, unsigned long long* out, unsigned* err,
+                                    double* copy_to, int grid, int threads, cudaStream_t st) {
+  mhd_curved_speed_kernel<<<grid, threads, 0, st>>>(u, Ja, invJ, g, P, out, err, copy_to);
+  return cudaGetLastError();
 }
 
 cudaError_t mhd_speed_launch(const double* u, const Geom& g, int P, const double* s,

@@ -2,6 +2,7 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include "dg_curved_decl.cuh"
 #include "dg_device.cuh"
 
 namespace dg {
@@ -21,5 +22,18 @@ cudaError_t mhd_rhs_launch(int N, const double* u, double* du, double* fs, const
 cudaError_t mhd_speed_launch(const double* u, const Geom& g, int P, const double* s,
                              unsigned long long* out, unsigned* err, double* copy_to, int grid,
                              int threads, cudaStream_t st);
+
+// The same on the warped box: Ja, invJ from the curved geometry, tb the
+// unscaled split-form table (Ds = -Dt, liftR = -1/w_N, liftL = 1/w_0).
+cudaError_t mhd_curved_rhs_launch(int N, const double* u, double* du, double* fs, const double* Ja,
+                                  const double* invJ, const Geom& g, const CTables& tb, int vf,
+                                  int powell, int sf, unsigned* err, cudaStream_t st, int parts,
+                                  const StageFuse& fz);
+
+// Wave-speed reduction on the warped box: sum_r max_nodes (|v . J a^r| +
+// c_f |J a^r|) / J per element, max over elements.
+cudaError_t mhd_curved_speed_launch(const double* u, const double* Ja, const double* invJ,
+                                    const Geom& g, int P, unsigned long long* out, unsigned* err,
+                                    double* copy_to, int grid, int threads, cudaStream_t st);
 
 }  // namespace dg

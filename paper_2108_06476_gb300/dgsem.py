@@ -27,7 +27,8 @@ RK_B = (1432997174477.0 / 9575080441755.0, 5161836677717.0 / 13612068292357.0,
         1720146321549.0 / 2090206949498.0, 3134564353537.0 / 4481467310338.0,
         2277821191437.0 / 14882151754819.0)
 
-EXPORTS = ("dg_mesh_create", "dg_mesh_create_curved", "dg_mesh_create_mhd", "dg_set_source", "dg_set_time",
+EXPORTS = ("dg_mesh_create", "dg_mesh_create_curved", "dg_mesh_create_mhd",
+           "dg_mesh_create_mhd_curved", "dg_set_source", "dg_set_time",
            "dg_get_time", "dg_mesh_destroy", "dg_mesh_info", "dg_mesh_set_stream",
            "dg_lgl_nodes", "dg_rhs", "dg_rhs_part", "dg_rhs_vjp", "dg_rk_stage", "dg_rk_reset", "dg_step", "dg_step_cfl", "dg_step_graph",
            "dg_step_dt", "dg_step_cfl_host", "dg_last_dt", "dg_max_dt",
@@ -81,6 +82,9 @@ def load(path: str = SO_PATH):
                                         ctypes.c_double, vp, vp, vp]
     L.dg_mesh_create_mhd.argtypes = [ctypes.c_int, ip, dp, ctypes.POINTER(_Options), ctypes.c_int,
                                      vp, ctypes.POINTER(vp)]
+    L.dg_mesh_create_mhd_curved.argtypes = [ctypes.c_int, ip, ctypes.c_double,
+                                            ctypes.POINTER(_Options), ctypes.c_int, vp,
+                                            ctypes.POINTER(vp)]
     L.dg_set_source.argtypes = [vp, ctypes.c_int]
     L.dg_set_time.argtypes = [vp, ctypes.c_double]
     L.dg_get_time.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
@@ -152,7 +156,7 @@ class Mesh:
     equations="mhd": the 3D ideal MHD equations (eight variables; the weak
     form, or EC flux differencing with volume_flux="ec"; LLF, HLL or EC
     faces (surface_flux); the Powell term unless powell=False; FP64; gamma
-    defaults to 5/3).
+    defaults to 5/3), on the Cartesian mesh or, with warp, the warped box.
 
     State tensors are float64 CUDA tensors of n_values entries in the layout
     u[e][v][k][j][i]; rhs outputs are float64 (fp64) or float32 (fp32)."""
@@ -182,13 +186,21 @@ class Mesh:
         self._stream = st
         self.warp = warp
         if equations == "mhd":
-            if self.d != 3 or warp is not None or precision != "fp64":
-                raise DGError("MHD meshes are 3D, Cartesian and FP64")
+            if self.d != 3 or precision != "fp64":
+                raise DGError("MHD meshes are 3D and FP64")
             vf = volume_flux if volume_flux in ("central", "ec") else "central"
             mopt = _Options(gamma, VFLUX[vf], SFLUX[surface_flux], PRECISION["fp64"])
-            _check(L.dg_mesh_create_mhd(self.N, n_arr, dom, ctypes.byref(mopt), int(bool(powell)),
-                                        ctypes.c_void_p(st.cuda_stream), ctypes.byref(h)),
-                   "dg_mesh_create_mhd")
+            if warp is None:
+                _check(L.dg_mesh_create_mhd(self.N, n_arr, dom, ctypes.byref(mopt),
+                                            int(bool(powell)), ctypes.c_void_p(st.cuda_stream),
+                                            ctypes.byref(h)), "dg_mesh_create_mhd")
+            else:
+                if tuple(self.domain) != (-1.0, 1.0) * 3:
+                    raise DGError("curved meshes are the 3D box [-1,1]^3")
+                _check(L.dg_mesh_create_mhd_curved(self.N, n_arr, float(warp), ctypes.byref(mopt),
+                                                   int(bool(powell)),
+                                                   ctypes.c_void_p(st.cuda_stream),
+                                                   ctypes.byref(h)), "dg_mesh_create_mhd_curved")
         elif warp is None:
             _check(L.dg_mesh_create(self.d, self.N, n_arr, dom, ctypes.byref(opt),
                                     ctypes.c_void_p(st.cuda_stream), ctypes.byref(h)),

@@ -119,6 +119,15 @@ def test_mhd_mesh_create_rejects_bad_arguments(lib):
     assert lib.dg_mesh_create_mhd(3, bad_n, dom, None, 1, None, ctypes.byref(h)) == -1
     bad_dom = (ctypes.c_double * 6)(-1, 1, -1, 1, 2, 1)
     assert lib.dg_mesh_create_mhd(3, n, bad_dom, None, 1, None, ctypes.byref(h)) == -1
+    # the warped-box MHD creator: the same option checks, the curved mesh's own
+    for N, warp, powell in ((0, 0.15, 1), (8, 0.15, 1), (3, 0.6, 1), (3, float("nan"), 1),
+                            (3, 0.15, 2)):
+        rc = lib.dg_mesh_create_mhd_curved(N, n, warp, None, powell, None, ctypes.byref(h))
+        assert rc == -1 and not h.value, (N, warp, powell)
+    bad = dgsem._Options(5 / 3, 0, 0, 0)
+    assert lib.dg_mesh_create_mhd_curved(3, n, 0.15, ctypes.byref(bad), 1, None,
+                                         ctypes.byref(h)) == -1
+    assert lib.dg_mesh_create_mhd_curved(3, None, 0.15, None, 1, None, ctypes.byref(h)) == -1
 
 
 def test_built_for_sm_103a():

@@ -1,0 +1,184 @@
+"""GPU parity of the 3D ideal MHD path on the warped periodic box (the mesh
+of the paper's MHD performance runs) against the warped-box MHD oracle,
+through the C ABI. Bar: 1e-12 relative L2, raised per case to 30x the
+oracle's own rhs change under a one-ulp change of the warp amplitude (the
+two sides build the geometry independently, a few ulp apart at every node,
+as for the curvilinear Euler path)."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle as orc  # noqa: E402
+from paper_2108_06476_gb300 import DGError, Mesh, workloads as W  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-12
+G = 5.0 / 3.0
+WARP = 0.15
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2108_06476_gb300 import build
+    build.build()
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def mesh(N, n, vflux="central", sflux="hll", powell=True, warp=WARP):
+    return Mesh(3, N, n, equations="mhd", warp=warp, volume_flux=vflux, surface_flux=sflux,
+                powell=powell)
+
+
+def state(N, n, seed, warp=WARP):
+    """the Alfven wave at the warped nodes plus 1e-2 uniform noise"""
+    xi, _ = orc.lgl(N)
+    u = W.alfven_wave_at(W.warped_node_coordinates(N, n, xi, warp), 0.0, gamma=G)
+    return u + 1e-2 * np.random.default_rng(seed).uniform(-1, 1, u.size)
+
+
+def bar(g, u, vflux, sflux, powell=True, elems=None):
+    g1 = orc.CurvedGeometry(g.N, g.n, np.nextafter(g.warp, 1.0))
+    r0 = orc.mhd_curved_rhs(g, u, G, powell, vflux=vflux, sflux=sflux, elems=elems)
+    r1 = orc.mhd_curved_rhs(g1, u, G, powell, vflux=vflux, sflux=sflux, elems=elems)
+    return r0, max(TOL, 30.0 * rel(r1, r0))
+
+
+@pytest.mark.parametrize("vflux,sflux", [("central", "hll"), ("ec", "ec")])
+@pytest.mark.parametrize("N", range(1, 8))
+def test_mhd_curved_rhs_every_degree(N, vflux, sflux):
+    n = (3, 2, 2) if N < 6 else (2, 2, 1)
+    g = orc.CurvedGeometry(N, n, WARP)
+    u = state(N, n, seed=70 + N)
+    ref, tol = bar(g, u, vflux, sflux)
+    m = mesh(N, n, vflux, sflux)
+    got = m.rhs(torch.from_numpy(u).cuda()).cpu().numpy()
+    assert m.check() == 0
+    assert rel(got, ref) <= tol, (rel(got, ref), tol)
+
+
+@pytest.mark.parametrize("vflux,sflux,powell", [("central", "llf", True), ("ec", "llf", True),
+                                                ("central", "hll", False)])
+def test_mhd_curved_rhs_other_flux_pairs(vflux, sflux, powell):
+    N, n = 3, (3, 3, 2)
+    g = orc.CurvedGeometry(N, n, WARP)
+    u = state(N, n, seed=9)
+    ref, tol = bar(g, u, vflux, sflux, powell)
+    got = mesh(N, n, vflux, sflux, powell).rhs(torch.from_numpy(u).cuda()).cpu().numpy()
+    assert rel(got, ref) <= tol, (rel(got, ref), tol)
+
+
+def test_mhd_curved_rhs_large_mesh_sampled():
+    """2,548 warped elements, sampled elements incl. the corners."""
+    N, n = 3, (14, 14, 13)
+    g = orc.CurvedGeometry(N, n, WARP)
+    u = state(N, n, seed=30)
+    ne = int(np.prod(n))
+    rng = np.random.default_rng(31)
+    elems = np.unique(np.concatenate([[0, n[0] - 1, ne - n[0], ne - 1],
+                                      rng.choice(ne, 200, replace=False)]))
+    P = (N + 1) ** 3
+    for vflux, sflux in (("central", "hll"), ("ec", "ec")):
+        ref, tol = bar(g, u, vflux, sflux, elems=elems)
+        ref = ref.reshape(ne, 8 * P)[elems]
+        got = mesh(N, n, vflux, sflux).rhs(torch.from_numpy(u).cuda()).cpu().numpy()
+        got = got.reshape(ne, 8 * P)[elems]
+        assert rel(got, ref) <= tol, (rel(got, ref), tol)
+
+
+def test_mhd_curved_without_warping_equals_cartesian_path():
+    N, n = 3, (3, 2, 4)
+    u = W.mhd_random_state(N, n, seed=8, gamma=G)
+    for vflux, sflux in (("central", "hll"), ("ec", "ec"), ("central", "llf")):
+        a = mesh(N, n, vflux, sflux, warp=0.0).rhs(torch.from_numpy(u).cuda()).cpu().numpy()
+        b = Mesh(3, N, n, equations="mhd", volume_flux=vflux, surface_flux=sflux).rhs(
+            torch.from_numpy(u).cuda()).cpu().numpy()
+        assert rel(a, b) <= 1e-13
+
+
+def test_mhd_curved_max_dt():
+    N, n = 4, (3, 3, 2)
+    g = orc.CurvedGeometry(N, n, WARP)
+    u = state(N, n, seed=3)
+    got = mesh(N, n).max_dt(torch.from_numpy(u).cuda(), cfl=0.5)
+    assert got == pytest.approx(orc.mhd_curved_max_dt(g, u, 0.5, G), rel=1e-12)
+
+
+def oracle_step(g, u, dt, vflux, sflux):
+    A, B, _ = orc.lsrk_coefficients()
+    u = u.copy()
+    k = np.zeros_like(u)
+    for s in range(5):
+        du = orc.mhd_curved_rhs(g, u, G, True, vflux=vflux, sflux=sflux)
+        orc.rk_stage(u, k, du, A[s], B[s], dt)
+    return u
+
+
+@pytest.mark.parametrize("vflux,sflux", [("central", "hll"), ("ec", "ec")])
+def test_mhd_curved_steps_match_oracle(vflux, sflux):
+    N, n = 3, (3, 3, 2)
+    g = orc.CurvedGeometry(N, n, WARP)
+    u0 = state(N, n, seed=4)
+    m = mesh(N, n, vflux, sflux)
+    ut = torch.from_numpy(u0.copy()).cuda()
+    ref = u0.copy()
+    for _ in range(3):
+        m.step_cfl(ut, cfl=0.5)
+        ref = oracle_step(g, ref, m.last_dt(), vflux, sflux)
+    assert m.check() == 0
+    got = ut.cpu().numpy()
+    _, tol = bar(g, u0, vflux, sflux)
+    assert rel(got - u0, ref - u0) <= max(1e-11, 10 * tol)
+
+
+def test_mhd_curved_graph_fused_unfused_and_host_steps_agree():
+    N, n = 3, (3, 2, 2)
+    u0 = state(N, n, seed=5)
+    m1, m2, m3, m4 = (mesh(N, n) for _ in range(4))
+    a, b, c = (torch.from_numpy(u0.copy()).cuda() for _ in range(3))
+    du = m1.empty_rhs()
+    for _ in range(2):
+        dt = m1.max_dt(a, cfl=0.4)
+        m1.step(a, dt, du)
+        m2.step_cfl(b, cfl=0.4)
+        m3.step_cfl(c, cfl=0.4, graph=True)
+    torch.cuda.synchronize()
+    assert torch.equal(b, c)
+    assert rel(b.cpu().numpy() - u0, a.cpu().numpy() - u0) <= 1e-13
+    h = torch.from_numpy(u0.copy()).pin_memory()
+    m4.step_cfl_host(h, cfl=0.4, n_steps=2)
+    assert torch.equal(b.cpu(), h)
+
+
+def test_mhd_curved_ec_entropy_conservation_on_the_device():
+    N, n = 3, (4, 4, 4)
+    g = orc.CurvedGeometry(N, n, WARP)
+    u = state(N, n, seed=6)
+    du = mesh(N, n, "ec", "ec").rhs(torch.from_numpy(u).cuda()).cpu().numpy()
+    P = (N + 1) ** 3
+    U, D = u.reshape(-1, 8, P), du.reshape(-1, 8, P)
+    rho, v, B = U[:, 0], U[:, 1:4] / U[:, :1], U[:, 5:8]
+    p = (G - 1) * (U[:, 4] - 0.5 * rho * (v * v).sum(1) - 0.5 * (B * B).sum(1))
+    beta = rho / (2 * p)
+    s = np.log(p) - G * np.log(rho)
+    w = np.concatenate([((G - s) / (G - 1) - beta * (v * v).sum(1))[:, None], 2 * beta[:, None] * v,
+                        -2 * beta[:, None], 2 * beta[:, None] * B], axis=1)
+    _, w1 = orc.lgl(N)
+    wq = np.einsum("i,j,k->kji", w1, w1, w1).reshape(-1)
+    rate = np.einsum("evp,evp,ep,p->", w, D, g.J, wq)
+    mag = np.einsum("evp,evp,ep,p->", np.abs(w), np.abs(D), g.J, wq)
+    assert abs(rate) < 1e-11 * mag, (rate, mag)
+
+
+def test_mhd_curved_mesh_refuses_sources_and_integrals():
+    m = mesh(2, (2, 2, 2))
+    u = torch.from_numpy(state(2, (2, 2, 2), seed=1)).cuda()
+    with pytest.raises(DGError):
+        m.set_source("manufactured")
+    with pytest.raises(DGError):
+        m.integrals(u)
