@@ -137,7 +137,11 @@ def test_mhd_curved_steps_match_oracle(vflux, sflux):
 
 
 def test_mhd_curved_graph_fused_unfused_and_host_steps_agree():
-    N, n = 3, (3, 2, 2)
+    # the paper's 4^3 warped mesh: on coarser, more distorted meshes such as
+    # 3 x 2 x 2 elements the weak form (central volume flux) is unstable at
+    # CFL 0.4 within two steps, in the oracle and on the GPU alike (EC flux
+    # differencing stays stable there)
+    N, n = 3, (4, 4, 4)
     u0 = state(N, n, seed=5)
     m1, m2, m3, m4 = (mesh(N, n) for _ in range(4))
     a, b, c = (torch.from_numpy(u0.copy()).cuda() for _ in range(3))
