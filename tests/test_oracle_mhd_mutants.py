@@ -23,7 +23,11 @@ MUTANTS = [
      "f[5 + k] = v[n] * B[k] + B[n] * v[k];"),
     ("energy flux without magnetic pressure", "f[4] = v[n] * (u[4] + pt) - B[n] * vb;",
      "f[4] = v[n] * (u[4] + p) - B[n] * vb;"),
-    ("fast speed discriminant", "sqrt(s * s - 4.0 * a2 * bn2)", "sqrt(s * s - 2.0 * a2 * bn2)"),
+    ("fast speed discriminant",
+     "const double bn2 = B[n] * B[n] / rho;\n  const double s = a2 + b2;\n"
+     "  return sqrt(0.5 * (s + sqrt(s * s - 4.0 * a2 * bn2)));",
+     "const double bn2 = B[n] * B[n] / rho;\n  const double s = a2 + b2;\n"
+     "  return sqrt(0.5 * (s + sqrt(s * s - 2.0 * a2 * bn2)));"),
     ("LLF speed from the mean velocity", "fmax(fabs(vL), fabs(vR)) +",
      "0.5 * (fabs(vL) + fabs(vR)) +"),
     ("transposed volume derivative",
@@ -39,8 +43,11 @@ MUTANTS = [
     ("Powell energy term drops a product", "v[0] * B[0] + v[1] * B[1] + v[2] * B[2],",
      "v[0] * B[0] + v[1] * B[1],"),
     ("Powell induction term permuted", "v[0], v[1], v[2]};", "v[1], v[0], v[2]};"),
-    ("CFL step without the N+1 factor", "return cfl * 2.0 / ((N + 1) * worst);",
-     "return cfl * 2.0 / (N * worst);"),
+    ("CFL step without the N+1 factor",
+     "sum += (2.0 / m.h[r]) * lam[r];\n    if (sum > worst) worst = sum;\n  }\n"
+     "  return cfl * 2.0 / ((N + 1) * worst);",
+     "sum += (2.0 / m.h[r]) * lam[r];\n    if (sum > worst) worst = sum;\n  }\n"
+     "  return cfl * 2.0 / (N * worst);"),
     ("HLL left speed takes the right state's fast wave the wrong way",
      "const double sL = fmin(vL - cL, vR - cR)", "const double sL = fmin(vL - cL, vR + cR)"),
     ("HLL jump term with the wrong sign", "sL * sR * (uR[v] - uL[v])", "sL * sR * (uL[v] - uR[v])"),
@@ -56,7 +63,8 @@ MUTANTS = [
      "beta_ln = 0.5 * (bL + bR);"),
     ("EC induction flux with the sign of {B_n} {v} flipped",
      "f[5 + k] = va[n] * Ba[k] - Ba[n] * va[k];", "f[5 + k] = va[n] * Ba[k] + Ba[n] * va[k];"),
-    ("EC volume flux id ignored", "if (vflux == 1) {", "if (vflux == 7) {"),
+    ("EC volume flux id ignored", "if (vflux == 1) {\n    or_mhd_flux_ec(n, gamma, ui, um, f);",
+     "if (vflux == 7) {\n    or_mhd_flux_ec(n, gamma, ui, um, f);"),
 ]
 
 PINS = [
