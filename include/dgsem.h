@@ -3,7 +3,8 @@
  * du/dt = rhs(u) of the discontinuous Galerkin spectral element method for the
  * 2D/3D compressible Euler equations (ideal gas) on a uniform periodic
  * Cartesian mesh or on the warped periodic box of the paper's benchmark (3D),
- * and the low-storage Runge-Kutta stage that consumes it.
+ * the same for the 3D ideal MHD equations, and the low-storage Runge-Kutta
+ * stage that consumes it.
  *
  * Paper: H. Ranocha et al., "Adaptive numerical simulations with Trixi.jl: A
  * case study of Julia for scientific computing" (2021).
@@ -16,8 +17,9 @@
  *   - the curvilinear benchmark mesh (warped periodic box) and its
  *     manufactured-solution problem: Sec. 3.1;
  *   - analysis integrals: Sec. 2.2;
- *   - 3D ideal MHD (weak form, Powell term, LLF) for the Alfven-wave runs:
- *     Sec. 3.1.
+ *   - 3D ideal MHD for the Alfven-wave runs, the weak form and EC flux
+ *     differencing with the Powell non-conservative term, HLL/LLF/EC faces,
+ *     on the Cartesian mesh and the warped box: Sec. 3.1.
  *
  * Conventions shared by every entry point:
  *   - State layout u[e][v][k][j][i]: element-major; inside an element the
