@@ -440,6 +440,41 @@ def run_mhd(args, timed, kernel_ms):
                              "frac": counted_node * M / (vol / 1e3) / 1e12 / FP64_PEAK_TFLOPS}}}
 
 
+def mhd_cpu_baseline(ne, seconds=3.0):
+    """The MHD oracle as it stands (OpenMP on all host cores) on a bounded
+    sample of the MHD leg's workload (the Alfven wave on ne^3 elements of
+    degree 3), for both solvers: rhs evaluations over sampled elements for
+    about `seconds` each."""
+    import numpy as np
+    import oracle
+    from paper_2108_06476_gb300 import workloads as W
+    oracle.build()
+    N = 3
+    n = (ne, ne, ne)
+    nelem, P = ne ** 3, (N + 1) ** 3
+    xi, _ = oracle.lgl(N)
+    u = W.alfven_wave(N, n, xi, 0.0)
+    du = np.zeros_like(u)
+    out = {"cores": os.cpu_count() or 1, "kind": "oracle", "unit": UNIT}
+    for key, vf, sf in (("weak_form_hll", "central", "hll"), ("ec_flux_differencing", "ec", "ec")):
+        probe = np.arange(0, nelem, max(1, nelem // 64))[:64]
+        t = time.perf_counter()
+        oracle.mhd_rhs(N, n, W.box(3), u, elems=probe, out=du, vflux=vf, sflux=sf)
+        per_elem = (time.perf_counter() - t) / len(probe)
+        count = int(min(nelem, max(64, 0.3 * seconds / max(per_elem, 1e-9))))
+        elems = np.sort(np.random.default_rng(3).choice(nelem, size=count, replace=False))
+        reps, el = 0, 0.0
+        t = time.perf_counter()
+        while reps == 0 or (el < seconds and reps < 20):
+            oracle.mhd_rhs(N, n, W.box(3), u, elems=elems, out=du, vflux=vf, sflux=sf)
+            reps += 1
+            el = time.perf_counter() - t
+        out[key] = {"value": count * P * reps / el,
+                    "sample": f"{reps} oracle rhs evaluation(s) over {count} of {nelem} "
+                              f"elements, {el:.1f} s"}
+    return out
+
+
 def max_over_ranks(ms, dist, device="cuda"):
     """The slowest rank's time (the job's time); identity without a process
     group."""
@@ -691,6 +726,8 @@ def run_ours(args, spec, world, rank, local):
     }
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(spec, xi, u_host)
+        if mhd is not None:
+            mhd["cpu_baseline"] = mhd_cpu_baseline(args.mhd_elements)
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

@@ -74,3 +74,10 @@ def test_reference_arm_prints_the_contract_line():
     assert line["cpu_baseline"]["value"] == line["value"]
     assert line["e2e"] == {"value": line["value"], "unit": line["unit"],
                            "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+
+
+def test_mhd_cpu_baseline_times_both_solvers():
+    out = bench.mhd_cpu_baseline(6, seconds=0.3)
+    assert out["kind"] == "oracle" and out["cores"] >= 1
+    for key in ("weak_form_hll", "ec_flux_differencing"):
+        assert out[key]["value"] > 0 and "oracle rhs" in out[key]["sample"]
