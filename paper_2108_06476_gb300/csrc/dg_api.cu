@@ -1,8 +1,9 @@
 // C ABI of the DGSEM library (declared in include/dgsem.h): mesh set-up with
-// the LGL basis (Cartesian, or the warped box with its geometry kernel), rhs
-// dispatch, the Carpenter-Kennedy stage update and the fused steps (device
-// CFL step, given step, CUDA graph, host-resident state), the CFL time step,
-// the simulation time and source terms, and the compensated integrals.
+// the LGL basis (Cartesian, or the warped box with its geometry kernel; Euler
+// or 3D ideal MHD), rhs dispatch, the Carpenter-Kennedy stage update and the
+// fused steps (device CFL step, given step, CUDA graph, host-resident state),
+// the CFL time step, the simulation time and source terms, and the
+// compensated integrals.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdarg.h>
