@@ -288,13 +288,17 @@ int dg_mesh_check(dg_mesh *mesh, int *flags);
  * arguments (as for dg_mesh_create; opt NULL = defaults, precision must be
  * DG_FP64) and u, du are caller-owned device float64 arrays of
  * (d+2) n_elem (N+1)^d values. The surface-flux scratch and the device error
- * word live in one static device array of 2^21 doubles (16 MiB) that every
- * GPU which loads the library holds until the process exits; meshes needing
- * more than 2^21 - 32 face values, d (d+2) n_elem (N+1)^(d-1), are rejected
- * with DG_ERR_ARG. No cudaMalloc, cudaFree or other allocating call is made.
- * The first call on a device looks up the array's device address (with
- * that device current) and caches it; make that first call before any stream
- * capture. Every call shares the array and it keeps the last call's
+ * word live in one static device array of 2^21 doubles (16 MiB). A CUDA
+ * context claims it when the library's module for this entry point is loaded
+ * there, which under lazy module loading is the first call in that context:
+ * make that first call during setup (and before any stream capture). If the
+ * device has no room for it then, that call returns DG_ERR_CUDA. The array is
+ * held until the context ends (process exit or cudaDeviceReset). Meshes
+ * needing more than 2^21 - 32 face values, d (d+2) n_elem (N+1)^(d-1), are
+ * rejected with DG_ERR_ARG. No cudaMalloc, cudaFree or other allocating call
+ * is made. The array's device address is looked up in the current context on
+ * every call (no cached pointer, so a device reset or a caller-owned context
+ * is safe). Every call shares the array and it keeps the last call's
  * contents: the error word is cleared at each call and non-physical states
  * are not reported by this entry point. Calls that overlap on the GPU (on
  * different streams, or from different threads) race on the shared scratch.

@@ -6,11 +6,11 @@
 // not allocate once their setup phase is over. dg_mesh_create allocates the
 // face-flux scratch and other buffers, so this entry point takes the mesh as
 // plain arguments and keeps its scratch -- the surface-flux buffer and the
-// device error word -- in one file-scope static device array. Every GPU that
-// loads the library holds that array (kStaticValues doubles, 16 MiB) until
-// the process exits.
+// device error word -- in one file-scope static device array
+// (kStaticValues doubles, 16 MiB). The array is claimed in a CUDA context
+// when this file's module is loaded there (with lazy module loading, at the
+// first call in that context) and is held until the context ends.
 #include <cuda_runtime.h>
-#include <mutex>
 #include <stdio.h>
 #include <string.h>
 
@@ -37,33 +37,29 @@ constexpr long long kStaticValues = 1LL << 21;  // 16 MiB of doubles
 
 static __device__ __align__(256) double g_noalloc_scratch[kStaticValues];
 
-constexpr int kMaxDevices = 64;
-double* g_scratch_ptr[kMaxDevices] = {nullptr};
-std::mutex g_scratch_mutex;
-
 int fail(int code, const char* fmt, long long a = 0, long long b = 0) {
   char buf[256];
   snprintf(buf, sizeof(buf), fmt, a, b);
   return dg::set_last_error(code, buf);
 }
 
-// Device address of the static scratch on the current device. In host code
+// Device address of the static scratch in the current context. In host code
 // the array's name is only a host-side stand-in, so the address is looked up
-// once per device (with that device current) and cached.
-int scratch_on_current_device(double** out) {
-  int dev = -1;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return fail(DG_ERR_CUDA, "dg_rhs_noalloc: cudaGetDevice failed");
-  if (dev < 0 || dev >= kMaxDevices) return fail(DG_ERR_ARG, "dg_rhs_noalloc: device %lld unsupported", dev);
-  std::lock_guard<std::mutex> lock(g_scratch_mutex);
-  if (!g_scratch_ptr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess || !p)
-      return fail(DG_ERR_CUDA, "dg_rhs_noalloc: cudaGetSymbolAddress failed on device %lld", dev);
-    g_scratch_ptr[dev] = static_cast<double*>(p);
-  }
-  *out = g_scratch_ptr[dev];
+// on every call: nothing is cached that could outlive a context (after
+// cudaDeviceReset, or under a caller's own non-primary context). Once the
+// module is loaded in the context the lookup allocates nothing; the first
+// lookup loads it and claims the array, and fails if the device has no room.
+int scratch_in_current_context(double** out) {
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e == cudaErrorMemoryAllocation)
+    return fail(DG_ERR_CUDA,
+                "dg_rhs_noalloc: the device has no room for the 16 MiB static scratch "
+                "(claimed when the module loads, at the first call in a context)");
+  if (e != cudaSuccess || !p)
+    return fail(DG_ERR_CUDA, "dg_rhs_noalloc: cudaGetSymbolAddress failed (error %lld)",
+                (long long)e);
+  *out = static_cast<double*>(p);
   return DG_OK;
 }
 
@@ -105,7 +101,7 @@ extern "C" int dg_rhs_noalloc(int d, int N, const int* elements_per_dim, const d
                 "holds (%lld); use dg_mesh_create/dg_rhs for larger meshes",
                 face_values, kFaceValues);
   double* scratch = nullptr;
-  int rc = scratch_on_current_device(&scratch);
+  int rc = scratch_in_current_context(&scratch);
   if (rc != DG_OK) return rc;
   unsigned* err = reinterpret_cast<unsigned*>(scratch + kFaceValues);
   cudaStream_t st = (cudaStream_t)cuda_stream;
