@@ -45,11 +45,46 @@ WORKLOADS = {
 }
 DEFAULT_WORKLOAD = "euler3d_n3_64cubed_noisy_wave"
 
-# FP64 vector peak derived from the nominal 1.25 TFLOP/s of the part: 2 DFMA
-# per clock per SM x 152 SMs x 2 flops x 2070 MHz. FP32: 128 FMA lanes/SM.
-SMS, SM_MAX_MHZ = 152, 2070.0
-FP64_PEAK_TFLOPS = SMS * 2 * 2 * SM_MAX_MHZ * 1e6 / 1e12
-FP32_PEAK_TFLOPS = SMS * 128 * 2 * SM_MAX_MHZ * 1e6 / 1e12
+# Vector peaks: measured on the device at start-up by the library's FMA
+# throughput probe (dg_measure_peaks); the nominal figures (2 DFMA and 128
+# FFMA lanes per clock per SM at 2070 MHz) are reported beside them.
+NOMINAL_SM_MHZ = 2070.0
+
+
+def nominal_peaks(sms):
+    return {"fp64_tflops": sms * 2 * 2 * NOMINAL_SM_MHZ * 1e6 / 1e12,
+            "fp32_tflops": sms * 128 * 2 * NOMINAL_SM_MHZ * 1e6 / 1e12}
+
+
+PEAKS = {}
+
+
+def measured_peaks():
+    """FP64/FP32 FMA throughput and SM count, measured once per process."""
+    if not PEAKS:
+        from paper_2108_06476_gb300 import measure_peaks
+        PEAKS.update(measure_peaks())
+    return PEAKS
+
+
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo)."""
+    try:
+        r = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=30)
+        for ln in r.stdout.splitlines():
+            if ln.startswith("Model name:"):
+                return ln.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for ln in fh:
+                if ln.lower().startswith(("model name", "cpu model")):
+                    return ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
 
 
 def volume_flops_per_node(d, N):
@@ -244,13 +279,17 @@ def run_reference(args, spec, world, rank):
     print(json.dumps(line), flush=True)
 
 
-def run_ensemble(args, timed, rank):
+def run_ensemble(args, timed, rank, checks):
     """The seeded 48-member ensemble advanced with one launch per stage and a
-    CUDA-graph step, after the autotuner picked the CTA shape; FP64 and FP32."""
+    CUDA-graph step, after the autotuner picked the CTA shape; FP64 and FP32.
+    Records one stage's rhs of every member on a few sampled elements for the
+    oracle check of the baseline leg."""
+    import numpy as np
     import torch
-    from paper_2108_06476_gb300 import Ensemble, lgl_nodes, workloads as W
+    from paper_2108_06476_gb300 import Ensemble, lgl_nodes, RK_B, workloads as W
     mem = W.ensemble(n_sims=48, seed=rank)
-    u0 = torch.from_numpy(W.ensemble_state(mem, lambda N: lgl_nodes(N)[0])).cuda()
+    u0h = W.ensemble_state(mem, lambda N: lgl_nodes(N)[0])
+    u0 = torch.from_numpy(u0h).cuda()
     out = {"workload": f"48 periodic 3D density waves (seed {rank}), N in {{3,4,5}}, "
                        "n in [8,24]", "members": len(mem)}
     k = max(1, min(args.steps, 5))
@@ -259,23 +298,51 @@ def run_ensemble(args, timed, rank):
         u = u0.clone()
         tmp = torch.empty_like(u)
         threads, per_sm, stage_ms = E.tune(u, tmp)
+        grid = E.get_block()[2]
+        # one stage with a large dt recovers every member's rhs (checked
+        # against the oracle on sampled elements in the baseline leg)
+        big = 1.0e6
+        E.set_dt(np.full(E.n_sims, big))
+        E.stage(u, tmp, 0)
+        E.rk_reset()
+        got = (tmp.cpu().numpy() - u0h) / (RK_B[0] * big)
+        samples = []
+        for s_, m in enumerate(mem):
+            ne, P = m.n[0] ** 3, (m.N + 1) ** 3
+            el = np.unique(np.concatenate([[0, ne - 1], np.random.default_rng(s_).choice(
+                ne, size=min(ne, 12), replace=False)]))
+            part = got[E.offsets[s_]:E.offsets[s_ + 1]].reshape(ne, 5, P)[el]
+            samples.append((m, u0h[E.offsets[s_]:E.offsets[s_ + 1]], el, part))
+        checks.append(("ensemble", prec, samples))
         for _ in range(args.warmup):
-            E.step(u, tmp, cfl=0.5, graph=True)
-        ms = timed(lambda: [E.step(u, tmp, cfl=0.5, graph=True) for _ in range(k)])
+            E.step(u, cfl=0.5, graph=True)
+        ms = timed(lambda: [E.step(u, cfl=0.5, graph=True) for _ in range(k)])
         E.check()
         out[prec] = {"value": E.n_nodes * 5 * k / (ms / 1e3), "unit": UNIT,
                      "ms_per_step": ms / k, "tuned_threads": threads,
-                     "tuned_ctas_per_sm": per_sm, "tuned_stage_ms": stage_ms}
+                     "tuned_ctas_per_sm": per_sm, "ctas_launched": grid,
+                     "tuned_stage_ms": stage_ms,
+                     "stage_launches_per_step": 5}
         out["nodes"] = E.n_nodes
         del E, u, tmp
     return out
 
 
-def run_configs(args, timed):
+def _sample_elements(nelem, count, seed):
+    import numpy as np
+    if nelem <= count:
+        return np.arange(nelem)
+    rng = np.random.default_rng(seed)
+    return np.unique(np.concatenate([[0, nelem - 1], rng.choice(nelem, size=count,
+                                                                  replace=False)]))
+
+
+def run_configs(args, timed, checks):
     """rhs-only rates (50 back-to-back dg_rhs calls, FP64 and FP32 kernels)
     and the fused-step rate (FP64, CUDA-graph CFL steps) of the other
     configured cases: 2D 16^2 N=3 and 3D 32^3 N=3 density waves, 3D 24^3 N=7
-    noisy density wave."""
+    noisy density wave. Each rhs is recorded on sampled elements for the
+    oracle check of the baseline leg."""
     import torch
     from paper_2108_06476_gb300 import Mesh, lgl_nodes, workloads as W
     out = {}
@@ -285,12 +352,17 @@ def run_configs(args, timed):
         n = (ne,) * d
         xi, _ = lgl_nodes(N)
         gen = W.noisy_density_wave if noisy else W.density_wave
-        u0 = torch.from_numpy(gen(d, N, n, W.box(d), xi)).cuda()
+        uh = gen(d, N, n, W.box(d), xi)
+        u0 = torch.from_numpy(uh).cuda()
         row = {"nodes": ne ** d * (N + 1) ** d}
+        elems = _sample_elements(ne ** d, 200 if N < 7 else 40, seed=ne)
         for prec in ("fp64", "fp32"):
             m = Mesh(d, N, n, precision=prec)
             du = m.empty_rhs()
             m.rhs(u0, du)
+            nv, P = d + 2, (N + 1) ** d
+            checks.append(("configs", (name, f"rhs_{prec}"), (d, N, n, uh, elems, du.double()
+                          .cpu().numpy().reshape(-1, nv, P)[elems])))
             ms = timed(lambda: [m.rhs(u0, du) for _ in range(50)])
             row[f"rhs_{prec}"] = row["nodes"] * 50 / (ms / 1e3)
             if prec == "fp64":
@@ -304,6 +376,45 @@ def run_configs(args, timed):
         out[name] = row
     out["unit"] = UNIT
     return out
+
+
+def oracle_checks(line, checks, headline):
+    """The baseline leg's accuracy record: the oracle's rhs on the sampled
+    elements of every recorded GPU rhs (headline FP64/FP32, the configured
+    cases, the 48 ensemble members), as relative L2 errors beside the rates."""
+    import numpy as np
+    import oracle
+    from paper_2108_06476_gb300 import workloads as W
+    oracle.build()
+
+    def rel(a, b):
+        return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+    d, N, n, uh, elems, gpu = headline
+    nv, P = d + 2, (N + 1) ** d
+    ref = oracle.rhs(d, N, n, W.box(d), uh, elems=elems).reshape(-1, nv, P)[elems]
+    line["rhs_rel_l2_vs_oracle"] = {prec: rel(g, ref) for prec, g in gpu.items()}
+    line["rhs_rel_l2_vs_oracle"]["sample"] = f"{len(elems)} of {int(np.prod(n))} elements"
+    if line.get("fp32") is not None:
+        line["fp32"]["rel_l2_vs_oracle"] = line["rhs_rel_l2_vs_oracle"]["fp32"]
+    for kind, key, data in checks:
+        if kind == "configs":
+            name, field = key
+            dd, NN, nn, u, el, g = data
+            r = oracle.rhs(dd, NN, nn, W.box(dd), u, elems=el).reshape(-1, dd + 2,
+                                                                      (NN + 1) ** dd)[el]
+            if line.get("configs"):
+                line["configs"][name][f"{field}_rel_l2_vs_oracle"] = rel(g, r)
+                line["configs"][name]["oracle_sample"] = f"{len(el)} of {int(np.prod(nn))} elements"
+        elif kind == "ensemble" and line.get("ensemble"):
+            errs = []
+            for m, u, el, g in data:
+                ne, PP = m.n[0] ** 3, (m.N + 1) ** 3
+                r = oracle.rhs(3, m.N, m.n, W.box(3), u, elems=el).reshape(ne, 5, PP)[el]
+                errs.append(rel(g, r))
+            line["ensemble"][key]["rel_l2_vs_oracle"] = {
+                "max_over_members": max(errs), "median": float(np.median(errs)),
+                "sample": "2 corner + 12 random elements of each of the 48 members"}
 
 
 def run_curved(args, timed):
@@ -431,13 +542,16 @@ def run_mhd(args, timed, kernel_ms):
             "pid_4cubed_warped": pid_warped,
             "pid_4cubed_cartesian": pid,
             "roofline": {"bound": "alu", "kernel": "mhd_volume_kernel (rhs only)",
-                         "flops_per_node": fl, "achieved": ach, "peak": FP64_PEAK_TFLOPS,
-                         "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS,
+                         "flops_per_node": fl, "achieved": ach,
+                         "peak": measured_peaks()["fp64_tflops"],
+                         "peak_source": "measured (dg_measure_peaks, FP64 FMA probe)",
+                         "unit": "TFLOP/s", "frac": ach / measured_peaks()["fp64_tflops"],
                          "traffic": None if traffic is None else traffic * M,
                          "counted": None if counted_node is None else {
                              "flops_per_node": counted_node,
                              "achieved": counted_node * M / (vol / 1e3) / 1e12,
-                             "frac": counted_node * M / (vol / 1e3) / 1e12 / FP64_PEAK_TFLOPS}}}
+                             "frac": counted_node * M / (vol / 1e3) / 1e12
+                             / measured_peaks()["fp64_tflops"]}}}
 
 
 def mhd_cpu_baseline(ne, seconds=3.0):
@@ -535,6 +649,7 @@ def cpu_baseline(spec, xi, u):
               "sample": f"best of up to 5 single-thread oracle rhs evaluations over "
                         f"{len(one)} elements"}
     return {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "cpu_model": cpu_model(),
             "sample": f"{reps} oracle rhs evaluation(s) over {count} of {nelem} elements "
                       f"({count * P} nodes each), {el:.1f} s, OpenMP on all host cores",
             "single_core": single}
@@ -555,8 +670,14 @@ def run_ours(args, spec, world, rank, local):
     xi, _ = lgl_nodes(N)
     u_host = make_state(spec, xi, seed=rank)
     M = ne ** d * (N + 1) ** d
+    peaks = measured_peaks()
+    FP64_PEAK = peaks["fp64_tflops"]
+    FP32_PEAK = peaks["fp32_tflops"]
     mesh = Mesh(d, N, n, precision="fp64")
     u0 = torch.from_numpy(u_host).cuda()
+    checks = []
+    head_elems = _sample_elements(ne ** d, 400, seed=N)
+    head_gpu = {}
     u = u0.clone()
     du = mesh.empty_rhs()
     stream = torch.cuda.current_stream()
@@ -611,6 +732,7 @@ def run_ours(args, spec, world, rank, local):
                 "ms_per_rhs": ms_rhs / rhs_reps, "calls": rhs_reps}
 
     u.copy_(u0)
+    head_gpu["fp64"] = mesh.rhs(u0).cpu().numpy().reshape(-1, d + 2, (N + 1) ** d)[head_elems]
     # the dominant kernel of the timed region is the fused volume kernel
     # (flux differencing, lifting and the stage update); parts=6 launches it
     # as in stages 2-5 (k read and written) with B = 0 (u unchanged)
@@ -627,7 +749,7 @@ def run_ours(args, spec, world, rank, local):
     if counted_node is not None:
         c_ach = counted_node * M / (vol_ms / 1e3) / 1e12
         counted = {"flops_per_node": counted_node, "achieved": c_ach,
-                   "frac": c_ach / FP64_PEAK_TFLOPS}
+                   "frac": c_ach / FP64_PEAK}
 
     # ---- FP32 kernels with FP64 state and RK accumulation ----
     fp32 = None
@@ -638,6 +760,8 @@ def run_ours(args, spec, world, rank, local):
         ref64 = mesh.rhs(u0).double()
         r32 = mesh32.rhs(u0, du32).double()
         err32 = float(torch.linalg.norm(r32 - ref64) / torch.linalg.norm(ref64))
+        head_gpu["fp32"] = r32.cpu().numpy().reshape(-1, d + 2, (N + 1) ** d)[head_elems]
+        del ref64, r32
         run_steps(mesh32, u32, du32, args.warmup)
         ms32 = timed(lambda: run_steps(mesh32, u32, du32, args.steps))
         mesh32.check()
@@ -649,7 +773,7 @@ def run_ours(args, spec, world, rank, local):
                 "volume_kernel_ms": vol32,
                 "volume_tflops": flops_node * M / (vol32 / 1e3) / 1e12,
                 "volume_frac_of_fp32_peak": flops_node * M / (vol32 / 1e3) / 1e12
-                / FP32_PEAK_TFLOPS}
+                / FP32_PEAK}
         del mesh32, u32, du32
 
     # ---- end to end through the C ABI with a host buffer ----
@@ -674,12 +798,12 @@ def run_ours(args, spec, world, rank, local):
     # ---- batched ensemble: 48 members (seed 0), N in {3,4,5}, n in [8,24] ----
     ensemble = None
     if not args.no_ensemble:
-        ensemble = run_ensemble(args, timed, rank)
+        ensemble = run_ensemble(args, timed, rank, checks)
 
     # ---- the other configured cases (rates only) ----
     configs = None
     if not args.no_configs:
-        configs = run_configs(args, timed)
+        configs = run_configs(args, timed, checks)
 
     # ---- the paper's curvilinear benchmark setup ----
     curved = None
@@ -705,12 +829,15 @@ def run_ours(args, spec, world, rank, local):
                    "l2": "inputs larger than L2 (state alone is "
                          f"{M * (d + 2) * 8 / 1e6:.0f} MB per buffer)"},
         "gpu_launches": launches_per_step * args.steps,
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-                     "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK,
+                     "unit": "TFLOP/s", "frac": achieved / FP64_PEAK,
                      "traffic": None if traffic is None else traffic * M,
                      "kernel": "volume_kernel (FP64, stage update fused)",
-                     "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz "
-                                    "(nominal 1.25 TFLOP/s FP64)",
+                     "peak_source": f"measured: dg_measure_peaks FP64 FMA probe on "
+                                    f"{peaks['sm_count']} SMs (cudaDeviceProp); nominal "
+                                    f"{nominal_peaks(peaks['sm_count'])['fp64_tflops']:.3f} "
+                                    f"TFLOP/s at {NOMINAL_SM_MHZ:.0f} MHz",
+                     "fp32_peak_measured": FP32_PEAK,
                      "flops_per_node": flops_node, "kernel_ms": vol_ms,
                      "counted": counted},
         "kernels_ms": {"volume_fused_stage": vol_ms, "volume_rhs_only": rhs_vol_ms,
@@ -726,6 +853,7 @@ def run_ours(args, spec, world, rank, local):
     }
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(spec, xi, u_host)
+        oracle_checks(line, checks, (d, N, n, u_host, head_elems, head_gpu))
         if mhd is not None:
             mhd["cpu_baseline"] = mhd_cpu_baseline(args.mhd_elements)
     print(json.dumps(line), flush=True)

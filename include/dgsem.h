@@ -307,19 +307,28 @@ int dg_rhs_noalloc(int d, int N, const int *elements_per_dim, const double *doma
                    const dg_options *opt, const double *u, double *du, void *cuda_stream);
 
 /* ---- Batched ensemble of independent 3D periodic simulations ----
- * n_sims meshes of N[s] in {3,4,5} and elements_per_dim[s]^3 elements on
- * [-1,1]^3 (Sec. 3.1 setup: periodic box, Carpenter-Kennedy LSRK, CFL step),
- * advanced together. The state of all members is one float64 device array:
- * member s occupies values [offsets[s], offsets[s+1]) in the layout of u above.
- * Every Runge-Kutta stage is ONE kernel launch over a work list of
- * (member, element batch) items that evaluates surface fluxes, the flux-
- * differencing volume term, lifting and the stage update per element; a
- * stage reads one state buffer and writes the other. Options: Ranocha volume
- * flux only; any surface flux; DG_FP64 or DG_FP32 arithmetic (FP64 state). */
+ * n_sims meshes of N[s] in {3,4,5} and elements_per_dim[s]^3 elements on the
+ * boxes domains[6 s .. 6 s + 5] = {lo_0, hi_0, lo_1, hi_1, lo_2, hi_2}
+ * (domains NULL: [-1,1]^3 for every member), the Sec. 3.1 setup (periodic
+ * box, Carpenter-Kennedy LSRK, CFL step), advanced together. d[s] must be 3
+ * (DG_ERR_ARG otherwise; d NULL means 3 for every member). The state of all
+ * members is one float64 device array: member s occupies values
+ * [offsets[s], offsets[s+1]) in the layout of u above.
+ * Every Runge-Kutta stage is ONE cooperative kernel launch over a work list
+ * of (member, element batch) items, in two phases separated by a grid-wide
+ * barrier: the surface fluxes of all faces (each face once), then the
+ * flux-differencing volume term, lifting and the stage update per element.
+ * The barrier's wait is bounded (about one second): if it runs out the launch
+ * stops and dg_ensemble_check returns DG_ERR_TIMEOUT. The arithmetic per
+ * member is that of dg_rhs on the same mesh. Options: Ranocha volume flux
+ * only; any surface flux; DG_FP64 or DG_FP32 arithmetic (FP64 state, FP32
+ * in the perturbation form of dg_rhs). The library owns the RK register, the
+ * face buffer and (FP32) the per-element reference states. */
 typedef struct dg_ensemble dg_ensemble;
 
-int dg_ensemble_create(int n_sims, const int *N, const int *elements_per_dim,
-                       const dg_options *opt, void *cuda_stream, dg_ensemble **out);
+int dg_ensemble_create(int n_sims, const int *d, const int *N, const int *elements_per_dim,
+                       const double *domains, const dg_options *opt, void *cuda_stream,
+                       dg_ensemble **out);
 int dg_ensemble_destroy(dg_ensemble *ens);
 /* total values and nodes; offsets[n_sims+1] (may be NULL) */
 int dg_ensemble_info(const dg_ensemble *ens, long long *n_values, long long *n_nodes,
@@ -331,24 +340,52 @@ int dg_ensemble_get_dt(dg_ensemble *ens, double *dt_host);
  * the values stay on the device for the next stages) */
 int dg_ensemble_compute_dt(dg_ensemble *ens, const double *u, double cfl);
 /* one stage s in [0,5): u_out = u_in + B_s k, k = A_s k + dt du(u_in);
- * u_in != u_out. Asynchronous. */
+ * u_out may be u_in (in place). Asynchronous. */
 int dg_ensemble_stage(dg_ensemble *ens, const double *u_in, double *u_out, int stage);
-/* one full step in place on u using u_tmp as the second buffer; when
- * cfl > 0 the time steps are first recomputed from u on the device. */
-int dg_ensemble_step(dg_ensemble *ens, double *u, double *u_tmp, double cfl);
-/* the same step recorded once as a CUDA graph (for these buffers and cfl)
- * and replayed on every later call. */
-int dg_ensemble_step_graph(dg_ensemble *ens, double *u, double *u_tmp, double cfl);
+/* one full step in place on u (five in-place stages, no second buffer);
+ * when cfl > 0 the time steps are first recomputed from u on the device. */
+int dg_ensemble_step(dg_ensemble *ens, double *u, double cfl);
+/* the same step recorded once as a CUDA graph (for this u and cfl) and
+ * replayed on every later call. */
+int dg_ensemble_step_graph(dg_ensemble *ens, double *u, double cfl);
 int dg_ensemble_rk_reset(dg_ensemble *ens);
-/* synchronise; DG_ERR_NONPHYSICAL if a non-physical state was met */
+/* synchronise; DG_ERR_NONPHYSICAL if a non-physical state was met,
+ * DG_ERR_TIMEOUT if a stage's barrier gave up; *flags gets the bits */
 int dg_ensemble_check(dg_ensemble *ens, int *flags);
-/* CTA shape: threads per CTA (multiple of 32) and persistent CTAs per SM;
- * elements per work item follow as threads / (N+1)^2 for each degree. */
+/* CTA shape: threads per CTA (multiple of 32, at most 256) and requested
+ * resident CTAs per SM (the launch takes at most what fits); elements per
+ * work item follow as threads / (N+1)^2 for each degree. */
 int dg_ensemble_set_block(dg_ensemble *ens, int threads, int blocks_per_sm);
-/* autotuner: times one stage for each candidate shape on (u, u_tmp), keeps
- * the fastest and reports it (outputs may be NULL); k is preserved. */
+/* the current shape: threads per CTA, requested CTAs per SM, CTAs launched */
+int dg_ensemble_get_block(const dg_ensemble *ens, int *threads, int *ctas_per_sm, int *grid);
+/* autotuner: times one stage from u into u_tmp (u unchanged) for each
+ * candidate shape, keeps the fastest and reports it (outputs may be NULL); k
+ * is preserved. Allocates a copy of k for the trials. */
 int dg_ensemble_tune(dg_ensemble *ens, const double *u, double *u_tmp, int *best_threads,
                      int *best_blocks_per_sm, float *best_ms);
+
+/* Measurement helper for the roofline of the flux kernels (the paper has no
+ * counterpart; its Sec. 3.1 performance index is a time per DOF): the FP64
+ * and FP32 vector fused-multiply-add throughput of the current device in
+ * TFLOP/s (an FMA counted as two flops), from a kernel of eight independent
+ * FMA chains per thread, 8 CTAs of 256 threads per SM, timed with CUDA events
+ * (the mean of three launches of at least 20 ms each), and the device's SM
+ * count. Outputs may be NULL (that rate is then not measured). Synchronous
+ * on cuda_stream; allocates nothing (the kernel's store target, never written
+ * in practice, is a static device array of 4 MiB (FP64) and 2 MiB (FP32)).
+ * Errors: DG_ERR_CUDA, DG_ERR_ARG (a device of more than 256 SMs). */
+int dg_measure_peaks(double *fp64_tflops, double *fp32_tflops, int *sm_count, void *cuda_stream);
+
+/* Self-check of the library's device arithmetic helpers (no paper
+ * counterpart; for the test suite): y[i] = f(x[i]) for n device doubles,
+ * evaluated by the same device functions the kernels use:
+ *   op 0  the FP64 reciprocal (hardware approximation + cubic Newton step),
+ *   op 1  the FP32 reciprocal of (float)x[i], widened,
+ *   op 2  the double -> float conversion of the FP32 kernels (integer pipe,
+ *         round to nearest even), widened,
+ *   op 3  the float -> double conversion of (float)x[i].
+ * Asynchronous on cuda_stream. Errors: DG_ERR_ARG, DG_ERR_CUDA. */
+int dg_selftest_arith(int op, const double *x, double *y, long long n, void *cuda_stream);
 
 /* Thread-local description of the last failed call ("" if none). */
 const char *dg_last_error(void);

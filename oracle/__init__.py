@@ -69,6 +69,7 @@ def _declare(L):
     rhs_args = [ctypes.c_int, ctypes.c_int, _ip, _dp, ctypes.c_double, ctypes.c_int,
                 ctypes.c_int]
     L.or_rhs.argtypes = rhs_args + [_dp, _dp, _llp, ctypes.c_longlong, ctypes.c_int]
+    L.or_set_direction_mask.argtypes = [ctypes.c_int]
     L.or_rhs_jvp.argtypes = rhs_args + [_dp, _dp, _dp, _llp, ctypes.c_longlong,
                                         ctypes.c_int]
     L.orl_rhs.argtypes = rhs_args + [ctypes.c_void_p, ctypes.c_void_p, _llp,
@@ -245,9 +246,11 @@ def _elems(elems):
 
 
 def rhs(d, N, n, dom, u, gamma=1.4, vflux=RANOCHA, sflux=S_LLF, elems=None, nthreads=0,
-        out=None):
+        out=None, directions=None):
     """du = rhs(u) (all elements, or only `elems`; other entries of du are 0,
-    or left as they are in `out` when an output buffer is given)."""
+    or left as they are in `out` when an output buffer is given).
+    directions: evaluate only the volume and surface terms of these
+    coordinate directions (their parts sum to the full rhs)."""
     n_arr, dom = _mesh_args(d, n, dom)
     u = _f64(u)
     if out is not None:
@@ -256,8 +259,15 @@ def rhs(d, N, n, dom, u, gamma=1.4, vflux=RANOCHA, sflux=S_LLF, elems=None, nthr
     else:
         du = np.zeros_like(u)
     ep, ne, keep = _elems(elems)
-    rc = lib().or_rhs(d, N, n_arr, _d(dom), gamma, vflux, sflux, _d(u), _d(du), ep, ne,
+    L = lib()
+    if directions is not None:
+        L.or_set_direction_mask(sum(1 << int(k) for k in directions))
+    try:
+        rc = L.or_rhs(d, N, n_arr, _d(dom), gamma, vflux, sflux, _d(u), _d(du), ep, ne,
                       nthreads)
+    finally:
+        if directions is not None:
+            L.or_set_direction_mask(7)
     if rc != 0:
         raise ValueError("or_rhs: bad arguments")
     return du

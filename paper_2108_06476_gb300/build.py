@@ -22,6 +22,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
 
 UNITS = [("dg_api.cu", [], "dg_api.o"), ("dg_noalloc.cu", [], "dg_noalloc.o"),
+         ("dg_probe.cu", [], "dg_probe.o"),
          ("dg_curved.cu", [], "dg_curved.o"),
          ("dg_mhd.cu", [], "dg_mhd.o"),
          ("dg_ensemble.cu", [], "dg_ensemble.o")] + [

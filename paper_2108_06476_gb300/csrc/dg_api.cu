@@ -61,7 +61,8 @@ struct dg_mesh {
   unsigned long long* speed;  // max wave-speed sum (as ordered bits)
   unsigned* err;       // device error word
   double* fbar;        // face adjoint buffer of dg_rhs_vjp, allocated on first use
-  float* pref;         // FP32 meshes: per-element pressure references
+  float* ref;          // FP32 meshes: per-element reference states (d+2 floats)
+  double* refE;        // FP32 meshes: the references' energies
   double* dt_dev;      // time step computed on the device (dg_step_cfl)
   cudaGraphExec_t graph;
   const double* graph_u;
@@ -505,6 +506,21 @@ void build_tables_fp64(int d, int N, const double* h, Tables<double>* t) {
     t->liftL[k] = (double)(-s / w[0]);
   }
 }
+
+// the same tables rounded from long double to FP32
+void build_tables_fp32(int d, int N, const double* h, Tables<float>* t) {
+  long double x[8], w[8], Dt[8][8];
+  lgl_basis(N, x, w);
+  split_matrix(N, x, w, Dt);
+  memset(t, 0, sizeof(*t));
+  for (int k = 0; k < d; ++k) {
+    const long double s = -2.0L / (long double)h[k];
+    for (int a = 0; a <= N; ++a)
+      for (int b = 0; b <= N; ++b) t->Ds[k][a][b] = (float)(s * Dt[a][b]);
+    t->liftR[k] = (float)(s / w[N]);
+    t->liftL[k] = (float)(-s / w[0]);
+  }
+}
 }  // namespace dg
 
 extern "C" {
@@ -617,7 +633,8 @@ int dg_mesh_create(int d, int N, const int* epd, const double* domain, const dg_
       (e = cudaMalloc(&m->red_out, 7 * 2 * sizeof(double))) != cudaSuccess ||
       (e = cudaMalloc(&m->speed, sizeof(unsigned long long))) != cudaSuccess ||
       (e = cudaMalloc(&m->err, sizeof(unsigned))) != cudaSuccess ||
-      (e = cudaMalloc(&m->pref, m->nelem * sizeof(float))) != cudaSuccess ||
+      (e = cudaMalloc(&m->ref, m->nelem * m->nv * sizeof(float))) != cudaSuccess ||
+      (e = cudaMalloc(&m->refE, m->nelem * sizeof(double))) != cudaSuccess ||
       (e = cudaMalloc(&m->dt_dev, sizeof(double))) != cudaSuccess ||
       (e = cudaMalloc(&m->t_dev, sizeof(double))) != cudaSuccess) {
     int rc = cuda_fail(e, "dg_mesh_create: cudaMalloc");
@@ -628,7 +645,8 @@ int dg_mesh_create(int d, int N, const int* epd, const double* domain, const dg_
     cudaFree(m->red_out);
     cudaFree(m->speed);
     cudaFree(m->err);
-    cudaFree(m->pref);
+    cudaFree(m->ref);
+    cudaFree(m->refE);
     cudaFree(m->dt_dev);
     cudaFree(m->t_dev);
     delete m;
@@ -844,7 +862,8 @@ int dg_mesh_destroy(dg_mesh* m) {
   cudaFree(m->speed);
   cudaFree(m->err);
   cudaFree(m->fbar);
-  cudaFree(m->pref);
+  cudaFree(m->ref);
+  cudaFree(m->refE);
   cudaFree(m->dt_dev);
   cudaFree(m->u_dev);
   cudaFree(m->t_dev);
@@ -886,7 +905,6 @@ int dg_rhs_part(dg_mesh* m, const double* u, void* du, int parts) {
     fz.dt = m->dt_dev;
     fz.a = 1.0;
     fz.b = 0.0;
-    fz.pref = nullptr;
     parts = 2;
   }
   cudaError_t e;
@@ -909,6 +927,8 @@ int dg_rhs_part(dg_mesh* m, const double* u, void* du, int parts) {
         m->N, u, (double*)du, (double*)m->fs, m->geom, m->t64, m->opt.volume_flux,
         m->opt.surface_flux, m->err, m->stream, parts, fz);
   } else {
+    fz.ref = m->ref;
+    fz.refE = m->refE;
     e = (m->d == 2 ? dg::rhs_launch_float_2 : dg::rhs_launch_float_3)(
         m->N, u, (float*)du, (float*)m->fs, m->geom, m->t32, m->opt.volume_flux,
         m->opt.surface_flux, m->err, m->stream, parts, fz);
@@ -1026,7 +1046,8 @@ int enqueue_fused_stages(dg_mesh* m, double* u, double* out) {
           m->N, u, nullptr, (double*)m->fs, m->geom, m->t64, m->opt.volume_flux,
           m->opt.surface_flux, m->err, m->stream, 3, fz);
     } else {
-      fz.pref = m->pref;
+      fz.ref = m->ref;
+      fz.refE = m->refE;
       e = (m->d == 2 ? dg::rhs_launch_float_2 : dg::rhs_launch_float_3)(
           m->N, u, nullptr, (float*)m->fs, m->geom, m->t32, m->opt.volume_flux,
           m->opt.surface_flux, m->err, m->stream, 3, fz);

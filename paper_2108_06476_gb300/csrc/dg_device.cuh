@@ -44,13 +44,15 @@ struct Tables {
 // epilogue: with k set, du is not stored; instead k <- a k + dt du and
 // u <- u + b k for the element (the surface kernel of the same stage has
 // already read every trace, and no other CTA reads this element's u).
-// pref (FP32 only): per-element pressure references published by the
-// surface kernel, read by the volume kernel for the left neighbours.
+// ref (FP32 meshes only): the per-element FP32 reference states of the
+// perturbation form (dg_f32.cuh), (d+2) floats per element, written by the
+// reference kernel before the surface kernel and read by both flux kernels.
 struct StageFuse {
   double* k = nullptr;
   const double* dt = nullptr;
   double a = 0.0, b = 0.0;
-  float* pref = nullptr;
+  float* ref = nullptr;
+  double* refE = nullptr;   // FP32 meshes: the references' FP64 energies
   double* u_out = nullptr;  // where u + b k goes (nullptr: u, in place)
 };
 
@@ -188,14 +190,11 @@ __device__ __forceinline__ unsigned prim_check(const Prim<R, D>& q) {
 //
 // Three ranges of f2, each lane choosing its own (no result depends on the
 // other lanes of its warp):
-//   short  a low-degree polynomial (FP64 kernels f2 < 1e-2, FP32 kernels
-//          f2 < 4e-2),
+//   short  a low-degree polynomial (f2 < 1e-2),
 //   long   a higher-degree one on [0, 0.25],
 //   far    log1p.
-// The FP32 kernels take t from their FP32 inputs but evaluate the
-// small-difference branch itself, f2 = t^2 and its polynomial, in FP64 (with
-// polynomials accurate to about a tenth of an FP32 ulp), rounding the
-// result once to FP32; their far branch is FP32.
+// (These are the FP64 kernels' log means; the FP32 kernels use the
+// perturbation form of dg_f32.cuh.)
 // Each polynomial is c_0 + f2 r(f2) with c_0 = Q(0) = 1 or S(0) = 2 exactly
 // and r interpolating (F - c_0)/f2 at the Chebyshev points of its interval
 // (gen_log_mean_poly.py writes them): degree 6 where the Taylor series
@@ -257,41 +256,6 @@ __device__ __forceinline__ double s_long(double f2) {
   r = fma(f2, r, 0.6666666666666666);
   return fma(f2, r, 2.0);
 }
-// degree 3 on f2 in [0, 4e-2]; measured relative error 2.6e-09
-__device__ __forceinline__ double q_short32(double f2) {
-  double r = -0.048433244596931685;
-  r = fma(f2, r, -0.08886054076664304);
-  r = fma(f2, r, -0.3333333964306796);
-  return fma(f2, r, 1.0);
-}
-// degree 4 on f2 in [0, 4e-2]; measured relative error 8.0e-11
-__device__ __forceinline__ double s_short32(double f2) {
-  double r = 0.23747344538291254;
-  r = fma(f2, r, 0.28532744768803825);
-  r = fma(f2, r, 0.4000031125070458);
-  r = fma(f2, r, 0.6666666627719066);
-  return fma(f2, r, 2.0);
-}
-// degree 6 on f2 in [0, 0.25]; measured relative error 1.1e-09
-__device__ __forceinline__ double q_long32(double f2) {
-  double r = -0.032615763305775085;
-  r = fma(f2, r, -0.016734165299453707);
-  r = fma(f2, r, -0.030890845926155427);
-  r = fma(f2, r, -0.04651870774759431);
-  r = fma(f2, r, -0.08888980573746398);
-  r = fma(f2, r, -0.33333333014048266);
-  return fma(f2, r, 1.0);
-}
-// degree 6 on f2 in [0, 0.25]; measured relative error 4.8e-09
-__device__ __forceinline__ double s_long32(double f2) {
-  double r = 0.31503560518305207;
-  r = fma(f2, r, 0.12986979135338692);
-  r = fma(f2, r, 0.22939750323237523);
-  r = fma(f2, r, 0.2852795970529254);
-  r = fma(f2, r, 0.400009466190787);
-  r = fma(f2, r, 0.6666666336958909);
-  return fma(f2, r, 2.0);
-}
 
 __device__ __forceinline__ double series_limit(double) { return 1.0e-2; }
 __device__ __forceinline__ float series_limit(float) { return 4.0e-2f; }
@@ -307,9 +271,6 @@ static __device__ __noinline__ float inv_ln_mean_far(float x, float y) { return 
 // bottleneck of the FP64 kernels)
 __device__ __forceinline__ bool in_short(double f2) {
   return __double_as_longlong(f2) < 0x3F847AE147AE147BLL;  // bits of 1e-2
-}
-__device__ __forceinline__ bool in_short32(double f2) {
-  return __double_as_longlong(f2) < 0x3FA47AE147AE147BLL;  // bits of 4e-2
 }
 __device__ __forceinline__ bool in_long(double f2) {
   return __double_as_longlong(f2) < 0x3FD0000000000000LL;  // bits of 0.25
@@ -338,23 +299,6 @@ __device__ __forceinline__ double s_of(double f2, double) {
     S = s_long(f2);
   return S;
 }
-__device__ __forceinline__ float q_of(double f2, float) {
-  double q;
-  if (in_short32(f2))
-    q = q_short32(f2);
-  else
-    q = q_long32(f2);
-  return (float)q;
-}
-__device__ __forceinline__ float s_of(double f2, float) {
-  double S;
-  if (in_short32(f2))
-    S = s_short32(f2);
-  else
-    S = s_long32(f2);
-  return (float)S;
-}
-
 template <typename R>
 __device__ __forceinline__ R ln_mean(R x, R y) {
   const R s = x + y;

@@ -1,17 +1,26 @@
 // Batched ensemble of independent 3D periodic Euler simulations with uneven
-// mesh sizes and polynomial degrees (N in {3, 4, 5}), advanced together:
-// one persistent kernel launch per Runge-Kutta stage over a work list of
-// (simulation, element batch) items, a graph-capturable step (the per-
-// simulation time steps stay on the device) and an autotuner that picks the
-// CTA size (hence the elements per CTA for every degree).
+// mesh sizes, boxes and polynomial degrees (N in {3, 4, 5}), advanced
+// together: one persistent kernel launch per Runge-Kutta stage over a work
+// list of (simulation, element batch) items, a graph-capturable step (the
+// per-simulation time steps stay on the device) and an autotuner that picks
+// the CTA size (hence the elements per work item for every degree) and the
+// number of resident CTAs per SM.
 //
-// Each work item evaluates, for its elements, the surface fluxes on all
-// element faces (reading the neighbours' traces; the two elements of a face
-// evaluate the same F* from the same inputs), the flux-differencing volume
-// term, the lifting, and the stage update k <- A k + dt du, u_out <- u_in + B k.
-// The stage reads u_in and writes u_out (two buffers), so no element waits
-// for another inside a launch. Arithmetic as in dg_rhs (same formulas,
-// tables unscaled and multiplied by -2/h per node at the end).
+// A stage launch is cooperative (all its CTAs resident) and runs two phases
+// over the work list, separated by a grid-wide barrier:
+//   A. for each item: the FP32 references of its elements (FP32 ensembles),
+//      then the surface flux of every face node on the right faces of its
+//      elements (each face once, by its left element), into the face buffer;
+//   B. for each item: the flux-differencing volume term, the lifting of both
+//      faces of every line and the stage update k <- A k + dt du,
+//      u_out <- u_in + B k.
+// Phase B reads only its own elements' states (the faces were read in phase
+// A), so u_out may be u_in: a step updates the state in place. The arithmetic
+// is that of dg_rhs: the same device functions (face_flux, volume_batch,
+// and their FP32 perturbation forms), with each member's own split-form
+// tables. The barrier's wait is bounded (about one second); if it runs out,
+// the launch sets the timeout bit of the error word and skips phase B, and
+// dg_ensemble_check reports DG_ERR_TIMEOUT.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdio.h>
@@ -25,6 +34,8 @@
 
 namespace dg {
 int set_last_error(int code, const char* msg);
+void build_tables_fp64(int d, int N, const double* h, Tables<double>* t);
+void build_tables_fp32(int d, int N, const double* h, Tables<float>* t);
 }
 
 namespace {
@@ -32,22 +43,20 @@ namespace {
 using namespace dg;
 
 constexpr int kEnsMinN = 3, kEnsMaxN = 5;
+constexpr int kEnsMaxItem = 32;          // elements per work item
+constexpr unsigned kErrTimeout = 8u;     // error-word bit: a bounded wait gave up
 
 struct SimDesc {
   int N, n, nelem;
-  long long off;  // offset of the simulation's first value
-  double s;       // -2/h
-  double lam_scale;  // 2/h (for the wave-speed sum)
+  long long off;     // first value of the member in the state
+  long long fsoff;   // first value of the member in the face buffer
+  long long refoff;  // first float of the member in the reference buffer
+  long long eoff;    // first element of the member (reference energies)
+  double lam_scale[3];  // 2/h_k (for the wave-speed sum)
 };
 
 struct WorkItem {
   int sim, e0, count;
-};
-
-// unscaled split-form matrices and inverse boundary weights per degree
-struct EnsTables {
-  double Dt[kEnsMaxN - kEnsMinN + 1][8][8];
-  double iw0[kEnsMaxN - kEnsMinN + 1];  // 1 / w_0 (= 1 / w_N)
 };
 
 struct EnsArgs {
@@ -61,237 +70,143 @@ struct EnsArgs {
   double A, B;
   double gamma, gm1, gm1inv;
   int sf;
+  void* fs;            // face buffer (rhs precision)
+  float* ref;          // FP32 references
+  double* refE;        // their FP64 energies
+  const void* tables;  // per member Tables<R>
   unsigned* err;
+  unsigned* bar;       // barrier counter, zero at launch
 };
 
 int fail(int code, const char* msg) { return dg::set_last_error(code, msg); }
 
 template <int N>
 struct EShape {
-  static constexpr int NP = N + 1, P = NP * NP * NP, LINES = NP * NP, NC = 9;
+  static constexpr int NP = N + 1, P = NP * NP * NP, LINES = NP * NP;
 };
 
-// conserved trace of node `node` of element e -> Trace (normal-first) with ps
-// relative to the pressure reference Pown (FP32) or p itself (FP64)
-template <typename R>
-__device__ __forceinline__ void load_trace(const double* __restrict__ u, long long base, int P,
-                                           int node, int dir, double gm1, float Pown, double* c,
-                                           Trace<R, 3>& T) {
-#pragma unroll
-  for (int v = 0; v < 5; ++v) c[v] = u[base + (long long)v * P + node];
-  const int t1 = (dir + 1) % 3, t2 = (dir + 2) % 3;
-  if (sizeof(R) == 4) {
-    // the node's own element reference: E at its first node
-    const double Er = u[base + 4LL * P];
-    const double pe = gm1 * Er;
-    const float Pe = (float)pe, ce = (float)(pe - (double)Pe);
-    float rho, v[3], pp, p;
-    prim_f32<3>(c, (float)gm1, Pe, ce, Er, rho, v, pp, p);
-    T.rho = R(rho);
-    T.rr = R(rcp(rho));
-    T.p = R(p);
-    T.ps = R(pp + (Pe - Pown));
-    T.vn = R(v[dir]);
-    T.vt[0] = R(v[t1]);
-    T.vt[1] = R(v[t2]);
-  } else {
-    double rr;
-    const Prim<double, 3> q = prim_rcp<3>(c, gm1, rr);
-    T.rho = R(q.rho);
-    T.rr = R(rr);
-    T.p = R(q.p);
-    T.ps = T.p;
-    T.vn = R(q.v[dir]);
-    T.vt[0] = R(q.v[t1]);
-    T.vt[1] = R(q.v[t2]);
-  }
-  T.mn = R(c[1 + dir]);
-  T.mt[0] = R(c[1 + t1]);
-  T.mt[1] = R(c[1 + t2]);
-  T.E = R(c[4]);
+__device__ __forceinline__ Geom member_geom(const SimDesc& sd, const EnsArgs& a) {
+  Geom g;
+  g.n[0] = g.n[1] = g.n[2] = sd.n;
+  g.nelem = sd.nelem;
+  g.gamma = a.gamma;
+  g.gm1 = a.gm1;
+  g.gm1inv = a.gm1inv;
+  return g;
 }
 
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Every CTA of the (cooperative, hence co-resident) launch arrives once;
+// returns false for all threads of the CTA if the others did not all arrive
+// within about one second (the timeout bit is then set).
+__device__ bool grid_barrier(unsigned* bar, unsigned nblocks, unsigned* err) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicAdd(bar, 1u);
+    const unsigned long long t0 = global_ns();
+    int ok = 1;
+    while (*(volatile unsigned*)bar < nblocks) {
+      if (global_ns() - t0 > 1000000000ull) {
+        ok = 0;
+        atomicOr(err, kErrTimeout);
+        break;
+      }
+      __nanosleep(100);
+    }
+    __threadfence();
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// phase A of one item: face fluxes of the right faces of its elements
 template <typename R, int N>
-__device__ void ens_process(const EnsArgs& a, const SimDesc& sd, int sim, int e0, int count,
-                            const EnsTables& et, unsigned char* smem) {
-  using S = EShape<N>;
-  constexpr int NP = S::NP, P = S::P, LINES = S::LINES, NV = 5, NC = S::NC;
+__device__ void ens_faces(const EnsArgs& a, const SimDesc& sd, const WorkItem& w) {
+  constexpr int LINES = EShape<N>::LINES;
   constexpr bool F32 = sizeof(R) == 4;
-  R(*sp)[NC][P] = reinterpret_cast<R(*)[NC][P]>(smem);
-  R(*sa)[6][P] = reinterpret_cast<R(*)[6][P]>(smem + sizeof(R) * count * NC * P);
-  __shared__ int s_nb[32][3][2];
-  __shared__ float s_pe[32], s_ce[32];
-  __shared__ double s_er[32];
-  const int n = sd.n;
-  const R gm1inv = R(a.gm1inv);
+  const Geom g = member_geom(sd, a);
   const double* u = a.uin + sd.off;
-  if ((int)threadIdx.x < count) {
-    const int el = threadIdx.x, e = e0 + el;
-    const int x = e % n, r = e / n, y = r % n, z = r / n;
-    s_nb[el][0][0] = ((x + n - 1) % n) + n * (y + n * z);
-    s_nb[el][0][1] = ((x + 1) % n) + n * (y + n * z);
-    s_nb[el][1][0] = x + n * (((y + n - 1) % n) + n * z);
-    s_nb[el][1][1] = x + n * (((y + 1) % n) + n * z);
-    s_nb[el][2][0] = x + n * (y + n * ((z + n - 1) % n));
-    s_nb[el][2][1] = x + n * (y + n * ((z + 1) % n));
-    const double Er = u[((long long)e * NV + 4) * P];
-    const double pe = a.gm1 * Er;
-    s_pe[el] = (float)pe;
-    s_ce[el] = (float)(pe - (double)(float)pe);
-    s_er[el] = Er;
-  }
-  __syncthreads();
-  unsigned bad = 0;
-  for (int t = threadIdx.x; t < count * P; t += blockDim.x) {
-    const int el = t / P, node = t % P, e = e0 + el;
-    double c[NV];
-#pragma unroll
-    for (int v = 0; v < NV; ++v) c[v] = u[((long long)e * NV + v) * P + node];
-    R rho, p, hp, vv[3];
-    if (F32) {
-      float vf[3], pp, pf, rf;
-      prim_f32<3>(c, (float)a.gm1, s_pe[el], s_ce[el], s_er[el], rf, vf, pp, pf);
-      rho = R(rf);
-      p = R(pf);
-      hp = R(0.5f * pp);
-#pragma unroll
-      for (int k = 0; k < 3; ++k) vv[k] = R(vf[k]);
-      if (!(rf > 0.0f)) bad |= kErrRho;
-      if (!(pf > 0.0f)) bad |= kErrP;
-      if (!isfinite(rf) || !isfinite(pf)) bad |= kErrNaN;
-    } else {
-      double rr;
-      const Prim<double, 3> q = prim_rcp<3>(c, a.gm1, rr);
-      bad |= prim_check(q);
-      rho = R(q.rho);
-      p = R(q.p);
-      hp = R(0.5) * p;
-#pragma unroll
-      for (int k = 0; k < 3; ++k) vv[k] = R(q.v[k]);
-    }
-    node_slots<kVRanocha, R>(rho, p, R(a.gm1), sp[el][0][node], sp[el][1][node]);
-    sp[el][2][node] = hp;
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      sp[el][3 + k][node] = vv[k];
-      sp[el][6 + k][node] = R(0.5) * vv[k];
-    }
-#pragma unroll
-    for (int k = 0; k < 6; ++k) sa[el][k][node] = R(0);
-  }
-  if (bad) atomicOr(a.err, bad);
-  __syncthreads();
-  const int el = threadIdx.x / LINES, l = threadIdx.x % LINES;
-  const bool active = el < count;
-  const R iw = R(et.iw0[N - kEnsMinN]);
-#pragma unroll 1
-  for (int dir = 0; dir < 3; ++dir) {
-    if (active) {
-      const int e = e0 + el;
-      const int t1 = (dir + 1) % 3, t2 = (dir + 2) % 3;
-      int node[NP];
-      LinePrim<R, 3> q[NP];
-#pragma unroll
-      for (int i = 0; i < NP; ++i) {
-        node[i] = line_node_rt<3, N>(dir, l, i);
-        const int nd = node[i];
-        q[i].s0 = sp[el][0][nd];
-        q[i].s1 = sp[el][1][nd];
-        q[i].hp = sp[el][2][nd];
-        q[i].vn = sp[el][3 + dir][nd];
-        q[i].hvn = sp[el][6 + dir][nd];
-        q[i].vt[0] = sp[el][3 + t1][nd];
-        q[i].hvt[0] = sp[el][6 + t1][nd];
-        q[i].vt[1] = sp[el][3 + t2][nd];
-        q[i].hvt[1] = sp[el][6 + t2][nd];
-      }
-      constexpr int NA = F32 ? 6 : 5;
-      R acc[NP][NA];
-#pragma unroll
-      for (int i = 0; i < NP; ++i)
-#pragma unroll
-        for (int v = 0; v < NA; ++v) acc[i][v] = R(0);
-#pragma unroll
-      for (int i = 0; i < NP; ++i) {
-#pragma unroll
-        for (int j = i + 1; j < NP; ++j) {
-          R f[NV], an;
-          ranocha_nf<R, 3>(q[i], q[j], f, an);
-          const R dij = R(et.Dt[N - kEnsMinN][i][j]), dji = R(et.Dt[N - kEnsMinN][j][i]);
-#pragma unroll
-          for (int v = 0; v < NV; ++v) {
-            acc[i][v] = fma(dij, f[v], acc[i][v]);
-            acc[j][v] = fma(dji, f[v], acc[j][v]);
-          }
-          if (F32) {
-            acc[i][NA - 1] = fma(dij, an, acc[i][NA - 1]);
-            acc[j][NA - 1] = fma(dji, an, acc[j][NA - 1]);
-          }
-        }
-      }
-      // the two faces at the ends of this line: left (node 0) and right (node N)
-      {
-        const long long base_e = sd.off + (long long)e * NV * P;
-        const int eL = s_nb[el][dir][0], eR = s_nb[el][dir][1];
-        double cn[NV], co[NV];
-        Trace<R, 3> TL, TO, TR;
-        R f[NV];
-        const float Pown = F32 ? s_pe[el] : 0.0f;
-        load_trace<R>(a.uin, sd.off + (long long)eL * NV * P, P, line_node_rt<3, N>(dir, l, N), dir,
-                      a.gm1, Pown, cn, TL);
-        load_trace<R>(a.uin, base_e, P, node[0], dir, a.gm1, Pown, co, TO);
-        surface_nf<R, 3>(a.sf, TL, TO, R(co[4] - cn[4]), R(a.gamma), gm1inv, f);
-#pragma unroll
-        for (int v = 0; v < NV; ++v) acc[0][v] = fma(-iw, f[v], acc[0][v]);
-        load_trace<R>(a.uin, base_e, P, node[N], dir, a.gm1, Pown, co, TO);
-        load_trace<R>(a.uin, sd.off + (long long)eR * NV * P, P, line_node_rt<3, N>(dir, l, 0), dir,
-                      a.gm1, Pown, cn, TR);
-        surface_nf<R, 3>(a.sf, TO, TR, R(cn[4] - co[4]), R(a.gamma), gm1inv, f);
-#pragma unroll
-        for (int v = 0; v < NV; ++v) acc[N][v] = fma(iw, f[v], acc[N][v]);
-      }
-#pragma unroll
-      for (int i = 0; i < NP; ++i) {
-        const int nd = node[i];
-        sa[el][0][nd] += acc[i][0];
-        sa[el][1 + dir][nd] += acc[i][1];
-        sa[el][1 + t1][nd] += acc[i][2];
-        sa[el][1 + t2][nd] += acc[i][3];
-        sa[el][4][nd] += acc[i][4];
-        if (F32) sa[el][5][nd] += acc[i][NA - 1];
-      }
-    }
+  R* fs = static_cast<R*>(a.fs) + sd.fsoff;
+  float* ref = a.ref + sd.refoff;
+  double* refE = a.refE + sd.eoff;
+  if (F32) {
+    for (int el = threadIdx.x; el < w.count; el += blockDim.x)
+      element_ref<3>(u, ref, refE, w.e0 + el, N + 1, a.gm1, a.gm1inv);
     __syncthreads();
   }
-  // epilogue: du = -(2/h) (volume + surface); stage update
-  const double dt = a.dt[sim];
-  for (int t = threadIdx.x; t < count * P; t += blockDim.x) {
-    const int ell = t / P, node = t % P, e = e0 + ell;
-#pragma unroll
-    for (int v = 0; v < NV; ++v) {
-      R val = sa[ell][v][node];
-      if (F32 && v == 4) val = fma(R(s_pe[ell]), sa[ell][5][node], val);
-      const double du = sd.s * (double)val;
-      const long long i = sd.off + ((long long)e * NV + v) * P + node;
-      double kk = dt * du;
-      if (a.A != 0.0) kk = fma(a.A, a.k[i], kk);  // the first stage reads no k
-      a.k[i] = kk;
-      a.uout[i] = a.uin[i] + a.B * kk;
+  const int per_dir = w.count * LINES;
+  for (int t = threadIdx.x; t < 3 * per_dir; t += blockDim.x) {
+    const int dir = t / per_dir, r = t % per_dir;
+    const int e = w.e0 + r / LINES, l = r % LINES;
+    if constexpr (F32) {
+      if (dir == 0) face_flux32<3, N, 0>(u, (float*)fs, g, a.sf, ref, refE, e, l);
+      else if (dir == 1) face_flux32<3, N, 1>(u, (float*)fs, g, a.sf, ref, refE, e, l);
+      else face_flux32<3, N, 2>(u, (float*)fs, g, a.sf, ref, refE, e, l);
+    } else {
+      if (dir == 0) face_flux<3, N, R, 0>(u, fs, g, a.sf, e, l);
+      else if (dir == 1) face_flux<3, N, R, 1>(u, fs, g, a.sf, e, l);
+      else face_flux<3, N, R, 2>(u, fs, g, a.sf, e, l);
     }
   }
 }
 
+// phase B of one item: volume term, lifting and the stage update
+template <typename R, int N>
+__device__ void ens_volume(const EnsArgs& a, const SimDesc& sd, const WorkItem& w,
+                           const Tables<R>& tb, unsigned char* smem) {
+  const Geom g = member_geom(sd, a);
+  StageFuse fz;
+  fz.k = a.k + sd.off;
+  fz.dt = a.dt + w.sim;
+  fz.a = a.A;
+  fz.b = a.B;
+  fz.ref = a.ref + sd.refoff;
+  fz.refE = a.refE + sd.eoff;
+  fz.u_out = a.uout + sd.off;
+  double* u = const_cast<double*>(a.uin) + sd.off;
+  if constexpr (sizeof(R) == 4)
+    volume_batch32<3, N, kVRanocha, kEnsMaxItem>(u, nullptr, static_cast<const float*>(a.fs) + sd.fsoff,
+                                                 g, tb, a.err, fz, w.e0, w.count, smem);
+  else
+    volume_batch<3, N, R, kVRanocha, kEnsMaxItem>(u, nullptr, static_cast<const R*>(a.fs) + sd.fsoff,
+                                                  g, tb, a.err, fz, w.e0, w.count, smem);
+}
 
-// one launch per stage: blocks walk the work list (largest degrees first)
+// one cooperative launch per stage: blocks walk the work list (largest
+// degrees first) in each phase
 template <typename R>
-__global__ void __launch_bounds__(256) ensemble_stage_kernel(EnsArgs a, EnsTables et) {
+__global__ void __launch_bounds__(256) ensemble_stage_kernel(EnsArgs a) {
   extern __shared__ __align__(16) unsigned char dg_smem[];
+  __shared__ Tables<R> s_tb;
   for (int it = blockIdx.x; it < a.nitems; it += gridDim.x) {
     const WorkItem w = a.items[it];
     const SimDesc sd = a.sims[w.sim];
-    if (sd.N == 3) ens_process<R, 3>(a, sd, w.sim, w.e0, w.count, et, dg_smem);
-    else if (sd.N == 4) ens_process<R, 4>(a, sd, w.sim, w.e0, w.count, et, dg_smem);
-    else ens_process<R, 5>(a, sd, w.sim, w.e0, w.count, et, dg_smem);
+    if (sd.N == 3) ens_faces<R, 3>(a, sd, w);
+    else if (sd.N == 4) ens_faces<R, 4>(a, sd, w);
+    else ens_faces<R, 5>(a, sd, w);
+  }
+  if (!grid_barrier(a.bar, gridDim.x, a.err)) return;
+  for (int it = blockIdx.x; it < a.nitems; it += gridDim.x) {
+    const WorkItem w = a.items[it];
+    const SimDesc sd = a.sims[w.sim];
+    {
+      const R* src = reinterpret_cast<const R*>(static_cast<const Tables<R>*>(a.tables) + w.sim);
+      R* dst = reinterpret_cast<R*>(&s_tb);
+      for (int i = threadIdx.x; i < (int)(sizeof(Tables<R>) / sizeof(R)); i += blockDim.x)
+        dst[i] = src[i];
+    }
+    __syncthreads();
+    if (sd.N == 3) ens_volume<R, 3>(a, sd, w, s_tb, dg_smem);
+    else if (sd.N == 4) ens_volume<R, 4>(a, sd, w, s_tb, dg_smem);
+    else ens_volume<R, 5>(a, sd, w, s_tb, dg_smem);
     __syncthreads();
   }
 }
@@ -328,9 +243,9 @@ __global__ void ensemble_speed_kernel(const SimDesc* __restrict__ sims,
         for (int off = 16; off > 0; off >>= 1)
           lam[k] = fmax(lam[k], __shfl_xor_sync(0xffffffffu, lam[k], off));
       if (lane == 0) {
-        double s = sd.lam_scale * lam[0];
-        s = s + sd.lam_scale * lam[1];
-        s = s + sd.lam_scale * lam[2];
+        double s = sd.lam_scale[0] * lam[0];
+        s = s + sd.lam_scale[1] * lam[1];
+        s = s + sd.lam_scale[2] * lam[2];
         atomicMax(&smax[w.sim], (unsigned long long)__double_as_longlong(s));
       }
     }
@@ -355,49 +270,6 @@ const double kB[5] = {1432997174477.0 / 9575080441755.0, 5161836677717.0 / 13612
                       1720146321549.0 / 2090206949498.0, 3134564353537.0 / 4481467310338.0,
                       2277821191437.0 / 14882151754819.0};
 
-// long double LGL basis for the ensemble's tables (the same construction as
-// the single-mesh path: Newton on P_{N+1} - P_{N-1}, closed-form D)
-long double leg(int n, long double x) {
-  if (n == 0) return 1.0L;
-  long double a = 1.0L, b = x;
-  for (int k = 1; k < n; ++k) {
-    long double c = ((2.0L * k + 1.0L) * x * b - k * a) / (k + 1.0L);
-    a = b;
-    b = c;
-  }
-  return b;
-}
-
-void ens_basis(int N, double Dt[8][8], double* iw0) {
-  const long double pi = 3.14159265358979323846264338327950288L;
-  long double x[8], w[8];
-  for (int j = 0; j <= N; ++j) {
-    long double t = -cosl(pi * j / N);
-    if (j > 0 && j < N)
-      for (int it = 0; it < 200; ++it) {
-        long double step = (leg(N + 1, t) - leg(N - 1, t)) / ((2.0L * N + 1.0L) * leg(N, t));
-        t -= step;
-        if (fabsl(step) <= 1e-32L) break;
-      }
-    if (j == 0) t = -1.0L;
-    if (j == N) t = 1.0L;
-    x[j] = t;
-    const long double pn = leg(N, t);
-    w[j] = 2.0L / ((long double)N * (N + 1) * pn * pn);
-  }
-  for (int i = 0; i <= N; ++i)
-    for (int j = 0; j <= N; ++j) {
-      long double dij;
-      if (i != j) dij = leg(N, x[i]) / (leg(N, x[j]) * (x[i] - x[j]));
-      else if (i == 0) dij = -(long double)N * (N + 1) / 4.0L;
-      else if (i == N) dij = (long double)N * (N + 1) / 4.0L;
-      else dij = 0.0L;
-      const long double b = (i == j && i == 0) ? -1.0L : (i == j && i == N) ? 1.0L : 0.0L;
-      Dt[i][j] = (double)(2.0L * dij - b / w[i]);
-    }
-  *iw0 = (double)(1.0L / w[0]);
-}
-
 }  // namespace
 
 struct dg_ensemble {
@@ -405,20 +277,24 @@ struct dg_ensemble {
   dg_options opt;
   cudaStream_t stream;
   std::vector<SimDesc> sims;
-  long long nvalues, nnodes;
+  long long nvalues, nnodes, nfs, nref;
   int block;  // threads per CTA (tunable)
-  int grid;   // persistent blocks
+  int per_sm; // requested resident CTAs per SM (tunable)
+  int grid;   // persistent CTAs (cooperative launch)
   int nitems;
   SimDesc* d_sims;
   WorkItem* d_items;
+  void* d_tables;  // per member Tables<R>
   double* k;
   double* dt;
+  void* fs;
+  float* ref;
+  double* refE;
   unsigned long long* smax;
   unsigned* err;
-  EnsTables tables;
+  unsigned* bar;
   cudaGraphExec_t graph;
   const double* graph_u;
-  const double* graph_tmp;
   double graph_cfl;
 };
 
@@ -428,16 +304,18 @@ namespace {
 int items_epb(int N, int block) {
   const int lines = (N + 1) * (N + 1);
   int e = block / lines;
-  if (e > 32) e = 32;
+  if (e > kEnsMaxItem) e = kEnsMaxItem;
   return e < 1 ? 0 : e;
 }
 
+// dynamic shared memory of a work item: FP64, node slots + accumulators;
+// FP32, the same in FP32 plus the staged RK register (volume32_smem)
 int smem_for(int precision, int block) {
-  const int rs = precision == DG_FP64 ? 8 : 4;
   int m = 0;
   for (int N = kEnsMinN; N <= kEnsMaxN; ++N) {
-    const int P = (N + 1) * (N + 1) * (N + 1);
-    const int b = items_epb(N, block) * (9 + 6) * P * rs;  // node slots + accumulators
+    const int P = (N + 1) * (N + 1) * (N + 1), epb = items_epb(N, block);
+    const int b = precision == DG_FP64 ? epb * (9 + 5) * P * 8
+                                       : ((4 * epb * 14 * P + 15) & ~15) + 8 * epb * 5 * P;
     if (b > m) m = b;
   }
   return m;
@@ -465,6 +343,23 @@ int build_items(dg_ensemble* E) {
   return DG_OK;
 }
 
+template <typename R>
+int configure_grid(dg_ensemble* E) {
+  const int sm = smem_for(E->opt.precision, E->block);
+  cudaError_t e = allow_smem(ensemble_stage_kernel<R>, sm);
+  if (e != cudaSuccess) return fail(DG_ERR_CUDA, "dg_ensemble: shared-memory attribute");
+  int dev = 0, nsm = 0, coop = 0, per = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+  if (!coop) return fail(DG_ERR_CUDA, "dg_ensemble: the device has no cooperative launch");
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, ensemble_stage_kernel<R>, E->block, sm);
+  if (e != cudaSuccess || per < 1) return fail(DG_ERR_CUDA, "dg_ensemble: occupancy query failed");
+  // at most the resident CTAs (the barrier needs every CTA of the launch)
+  E->grid = nsm * std::min(E->per_sm, per);
+  return DG_OK;
+}
+
 int launch_stage(dg_ensemble* E, const double* uin, double* uout, int s) {
   EnsArgs a;
   a.sims = E->d_sims;
@@ -480,24 +375,38 @@ int launch_stage(dg_ensemble* E, const double* uin, double* uout, int s) {
   a.gm1 = E->opt.gamma - 1.0;
   a.gm1inv = 1.0 / (E->opt.gamma - 1.0);
   a.sf = E->opt.surface_flux;
+  a.fs = E->fs;
+  a.ref = E->ref;
+  a.refE = E->refE;
+  a.tables = E->d_tables;
   a.err = E->err;
+  a.bar = E->bar;
+  if (cudaMemsetAsync(E->bar, 0, sizeof(unsigned), E->stream) != cudaSuccess)
+    return fail(DG_ERR_CUDA, "dg_ensemble: clearing the barrier counter failed");
   const int sm = smem_for(E->opt.precision, E->block);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(E->grid);
+  cfg.blockDim = dim3(E->block);
+  cfg.dynamicSmemBytes = sm;
+  cfg.stream = E->stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
   cudaError_t e;
-  if (E->opt.precision == DG_FP64) {
-    if ((e = allow_smem(ensemble_stage_kernel<double>, sm)) != cudaSuccess)
-      return fail(DG_ERR_CUDA, "dg_ensemble: shared-memory attribute");
-    ensemble_stage_kernel<double><<<E->grid, E->block, sm, E->stream>>>(a, E->tables);
-  } else {
-    if ((e = allow_smem(ensemble_stage_kernel<float>, sm)) != cudaSuccess)
-      return fail(DG_ERR_CUDA, "dg_ensemble: shared-memory attribute");
-    ensemble_stage_kernel<float><<<E->grid, E->block, sm, E->stream>>>(a, E->tables);
-  }
-  if ((e = cudaGetLastError()) != cudaSuccess) return fail(DG_ERR_CUDA, cudaGetErrorString(e));
+  if (E->opt.precision == DG_FP64) e = cudaLaunchKernelEx(&cfg, ensemble_stage_kernel<double>, a);
+  else e = cudaLaunchKernelEx(&cfg, ensemble_stage_kernel<float>, a);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(DG_ERR_CUDA, cudaGetErrorString(e));
   return DG_OK;
 }
 
 int launch_dt(dg_ensemble* E, const double* u, double cfl) {
-  ensemble_speed_kernel<<<E->grid, 256, 0, E->stream>>>(E->d_sims, E->d_items, E->nitems, u,
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  ensemble_speed_kernel<<<nsm * 4, 256, 0, E->stream>>>(E->d_sims, E->d_items, E->nitems, u,
                                                          E->opt.gamma, E->opt.gamma - 1.0,
                                                          E->smax, E->err);
   ensemble_dt_kernel<<<(E->nsims + 127) / 128, 128, 0, E->stream>>>(E->d_sims, E->nsims, cfl,
@@ -507,23 +416,14 @@ int launch_dt(dg_ensemble* E, const double* u, double cfl) {
   return DG_OK;
 }
 
-// one step: (dt from u when cfl > 0), five stages alternating u -> tmp -> u
-// ..., ending in tmp, then tmp copied back to u
-int enqueue_step(dg_ensemble* E, double* u, double* tmp, double cfl) {
+// one step in place on u: (dt from u when cfl > 0), then the five stages
+int enqueue_step(dg_ensemble* E, double* u, double cfl) {
   int rc = (cfl > 0.0) ? launch_dt(E, u, cfl) : DG_OK;
   if (rc) return rc;
-  const double* in = u;
-  double* out = tmp;
   for (int s = 0; s < 5; ++s) {
-    rc = launch_stage(E, in, out, s);
+    rc = launch_stage(E, u, u, s);
     if (rc) return rc;
-    double* nxt = (out == tmp) ? u : tmp;
-    in = out;
-    out = nxt;
   }
-  if (cudaMemcpyAsync(u, tmp, E->nvalues * sizeof(double), cudaMemcpyDeviceToDevice,
-                      E->stream) != cudaSuccess)
-    return fail(DG_ERR_CUDA, "dg_ensemble: copy of the step result failed");
   return DG_OK;
 }
 
@@ -537,16 +437,22 @@ int dg_ensemble_destroy(dg_ensemble* E) {
   if (E->graph) cudaGraphExecDestroy(E->graph);
   cudaFree(E->d_sims);
   cudaFree(E->d_items);
+  cudaFree(E->d_tables);
   cudaFree(E->k);
   cudaFree(E->dt);
+  cudaFree(E->fs);
+  cudaFree(E->ref);
+  cudaFree(E->refE);
   cudaFree(E->smax);
   cudaFree(E->err);
+  cudaFree(E->bar);
   delete E;
   return DG_OK;
 }
 
-int dg_ensemble_create(int n_sims, const int* N, const int* elements_per_dim,
-                       const dg_options* opt, void* cuda_stream, dg_ensemble** out) {
+int dg_ensemble_create(int n_sims, const int* d, const int* N, const int* elements_per_dim,
+                       const double* domains, const dg_options* opt, void* cuda_stream,
+                       dg_ensemble** out) {
   if (out) *out = nullptr;
   if (!out || !N || !elements_per_dim || n_sims < 1)
     return fail(DG_ERR_ARG, "dg_ensemble_create: bad arguments");
@@ -555,66 +461,99 @@ int dg_ensemble_create(int n_sims, const int* N, const int* elements_per_dim,
   if (!(o.gamma > 1.0) || o.volume_flux != DG_VFLUX_RANOCHA || o.surface_flux < 0 ||
       o.surface_flux > 3 || (o.precision != DG_FP64 && o.precision != DG_FP32))
     return fail(DG_ERR_ARG, "dg_ensemble_create: invalid options (Ranocha volume flux only)");
-  for (int s = 0; s < n_sims; ++s)
+  for (int s = 0; s < n_sims; ++s) {
+    if (d && d[s] != 3) return fail(DG_ERR_ARG, "dg_ensemble_create: members must be 3D (d = 3)");
     if (N[s] < kEnsMinN || N[s] > kEnsMaxN || elements_per_dim[s] < 1 ||
         elements_per_dim[s] > 1024)
       return fail(DG_ERR_ARG, "dg_ensemble_create: N must be in {3,4,5} and 1 <= n <= 1024");
+    if (domains)
+      for (int k = 0; k < 3; ++k)
+        if (!(domains[6 * s + 2 * k + 1] > domains[6 * s + 2 * k]))
+          return fail(DG_ERR_ARG, "dg_ensemble_create: every domain needs lo < hi");
+  }
   dg_ensemble* E = new dg_ensemble();
   E->nsims = n_sims;
   E->opt = o;
   E->stream = (cudaStream_t)cuda_stream;
   E->block = 128;
+  E->per_sm = 4;
   E->d_sims = nullptr;
   E->d_items = nullptr;
+  E->d_tables = nullptr;
   E->k = nullptr;
   E->dt = nullptr;
+  E->fs = nullptr;
+  E->ref = nullptr;
+  E->refE = nullptr;
   E->smax = nullptr;
   E->err = nullptr;
+  E->bar = nullptr;
   E->graph = nullptr;
-  E->graph_u = E->graph_tmp = nullptr;
+  E->graph_u = nullptr;
   E->graph_cfl = 0.0;
-  long long off = 0, nodes = 0;
+  const size_t rs = o.precision == DG_FP64 ? sizeof(double) : sizeof(float);
+  const size_t tsize = o.precision == DG_FP64 ? sizeof(Tables<double>) : sizeof(Tables<float>);
+  std::vector<unsigned char> tables(tsize * n_sims);
+  long long off = 0, nodes = 0, fsoff = 0, refoff = 0;
   for (int s = 0; s < n_sims; ++s) {
     SimDesc sd;
     sd.N = N[s];
     sd.n = elements_per_dim[s];
     sd.nelem = sd.n * sd.n * sd.n;
     sd.off = off;
-    const double h = 2.0 / sd.n;  // every member lives on [-1, 1]^3
-    sd.s = -2.0 / h;
-    sd.lam_scale = 2.0 / h;
+    sd.fsoff = fsoff;
+    sd.refoff = refoff;
+    sd.eoff = refoff / 5;
+    double h[3];
+    for (int k = 0; k < 3; ++k) {
+      const double lo = domains ? domains[6 * s + 2 * k] : -1.0;
+      const double hi = domains ? domains[6 * s + 2 * k + 1] : 1.0;
+      h[k] = (hi - lo) / sd.n;
+      sd.lam_scale[k] = 2.0 / h[k];
+    }
+    if (o.precision == DG_FP64)
+      build_tables_fp64(3, sd.N, h, reinterpret_cast<Tables<double>*>(tables.data()) + s);
+    else
+      build_tables_fp32(3, sd.N, h, reinterpret_cast<Tables<float>*>(tables.data()) + s);
     const long long P = (long long)(sd.N + 1) * (sd.N + 1) * (sd.N + 1);
     off += 5LL * sd.nelem * P;
     nodes += sd.nelem * P;
+    fsoff += 3LL * 5 * sd.nelem * (sd.N + 1) * (sd.N + 1);
+    refoff += 5LL * sd.nelem;
     E->sims.push_back(sd);
   }
   E->nvalues = off;
   E->nnodes = nodes;
-  memset(&E->tables, 0, sizeof(E->tables));
-  for (int n = kEnsMinN; n <= kEnsMaxN; ++n)
-    ens_basis(n, E->tables.Dt[n - kEnsMinN], &E->tables.iw0[n - kEnsMinN]);
-  int dev = 0, nsm = 152;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  E->grid = nsm * 4;
+  E->nfs = fsoff;
+  E->nref = refoff;
   if (cudaMalloc(&E->d_sims, n_sims * sizeof(SimDesc)) != cudaSuccess ||
+      cudaMalloc(&E->d_tables, tables.size()) != cudaSuccess ||
       cudaMalloc(&E->k, E->nvalues * sizeof(double)) != cudaSuccess ||
       cudaMalloc(&E->dt, n_sims * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&E->fs, E->nfs * rs) != cudaSuccess ||
+      cudaMalloc(&E->ref, std::max(E->nref, 1LL) * sizeof(float)) != cudaSuccess ||
+      cudaMalloc(&E->refE, std::max(E->nref / 5, 1LL) * sizeof(double)) != cudaSuccess ||
       cudaMalloc(&E->smax, n_sims * sizeof(unsigned long long)) != cudaSuccess ||
-      cudaMalloc(&E->err, sizeof(unsigned)) != cudaSuccess) {
+      cudaMalloc(&E->err, sizeof(unsigned)) != cudaSuccess ||
+      cudaMalloc(&E->bar, sizeof(unsigned)) != cudaSuccess) {
     dg_ensemble_destroy(E);
     return fail(DG_ERR_OOM, "dg_ensemble_create: cudaMalloc failed");
   }
   if (cudaMemcpy(E->d_sims, E->sims.data(), n_sims * sizeof(SimDesc), cudaMemcpyHostToDevice) !=
           cudaSuccess ||
+      cudaMemcpy(E->d_tables, tables.data(), tables.size(), cudaMemcpyHostToDevice) !=
+          cudaSuccess ||
       cudaMemset(E->k, 0, E->nvalues * sizeof(double)) != cudaSuccess ||
       cudaMemset(E->dt, 0, n_sims * sizeof(double)) != cudaSuccess ||
       cudaMemset(E->smax, 0, n_sims * sizeof(unsigned long long)) != cudaSuccess ||
-      cudaMemset(E->err, 0, sizeof(unsigned)) != cudaSuccess) {
+      cudaMemset(E->err, 0, sizeof(unsigned)) != cudaSuccess ||
+      cudaMemset(E->bar, 0, sizeof(unsigned)) != cudaSuccess) {
     dg_ensemble_destroy(E);
     return fail(DG_ERR_CUDA, "dg_ensemble_create: initialisation failed");
   }
   int rc = build_items(E);
+  if (rc == DG_OK)
+    rc = (o.precision == DG_FP64) ? configure_grid<double>(E) : configure_grid<float>(E);
   if (rc) {
     dg_ensemble_destroy(E);
     return rc;
@@ -659,20 +598,19 @@ int dg_ensemble_compute_dt(dg_ensemble* E, const double* u, double cfl) {
 }
 
 int dg_ensemble_stage(dg_ensemble* E, const double* u_in, double* u_out, int stage) {
-  if (!E || !u_in || !u_out || u_in == u_out || stage < 0 || stage > 4)
-    return fail(DG_ERR_ARG, "dg_ensemble_stage: bad argument (u_in and u_out must differ)");
+  if (!E || !u_in || !u_out || stage < 0 || stage > 4)
+    return fail(DG_ERR_ARG, "dg_ensemble_stage: bad argument");
   return launch_stage(E, u_in, u_out, stage);
 }
 
-int dg_ensemble_step(dg_ensemble* E, double* u, double* u_tmp, double cfl) {
-  if (!E || !u || !u_tmp || u == u_tmp) return fail(DG_ERR_ARG, "dg_ensemble_step: bad argument");
-  return enqueue_step(E, u, u_tmp, cfl);
+int dg_ensemble_step(dg_ensemble* E, double* u, double cfl) {
+  if (!E || !u) return fail(DG_ERR_ARG, "dg_ensemble_step: bad argument");
+  return enqueue_step(E, u, cfl);
 }
 
-int dg_ensemble_step_graph(dg_ensemble* E, double* u, double* u_tmp, double cfl) {
-  if (!E || !u || !u_tmp || u == u_tmp)
-    return fail(DG_ERR_ARG, "dg_ensemble_step_graph: bad argument");
-  if (!E->graph || E->graph_u != u || E->graph_tmp != u_tmp || E->graph_cfl != cfl) {
+int dg_ensemble_step_graph(dg_ensemble* E, double* u, double cfl) {
+  if (!E || !u) return fail(DG_ERR_ARG, "dg_ensemble_step_graph: bad argument");
+  if (!E->graph || E->graph_u != u || E->graph_cfl != cfl) {
     if (E->graph) {
       cudaGraphExecDestroy(E->graph);
       E->graph = nullptr;
@@ -688,7 +626,7 @@ int dg_ensemble_step_graph(dg_ensemble* E, double* u, double* u_tmp, double cfl)
       cudaStreamDestroy(cap);
       return fail(DG_ERR_CUDA, "dg_ensemble_step_graph: begin capture");
     }
-    int rc = enqueue_step(E, u, u_tmp, cfl);
+    int rc = enqueue_step(E, u, cfl);
     cudaError_t ce = cudaStreamEndCapture(cap, &g);
     E->stream = saved;
     cudaStreamDestroy(cap);
@@ -700,7 +638,6 @@ int dg_ensemble_step_graph(dg_ensemble* E, double* u, double* u_tmp, double cfl)
     cudaGraphDestroy(g);
     if (ce != cudaSuccess) return fail(DG_ERR_CUDA, "dg_ensemble_step_graph: instantiate");
     E->graph_u = u;
-    E->graph_tmp = u_tmp;
     E->graph_cfl = cfl;
   }
   if (cudaGraphLaunch(E->graph, E->stream) != cudaSuccess)
@@ -725,6 +662,8 @@ int dg_ensemble_check(dg_ensemble* E, int* flags) {
   if (flags) *flags = (int)h;
   if (h) {
     cudaMemsetAsync(E->err, 0, sizeof(unsigned), E->stream);
+    if (h & kErrTimeout)
+      return fail(DG_ERR_TIMEOUT, "dg_ensemble: a stage's grid barrier timed out");
     return fail(DG_ERR_NONPHYSICAL, "dg_ensemble: non-physical state met");
   }
   return DG_OK;
@@ -736,32 +675,36 @@ int dg_ensemble_set_block(dg_ensemble* E, int threads, int blocks_per_sm) {
     return fail(DG_ERR_ARG, "dg_ensemble_set_block: bad configuration");
   for (int N = kEnsMinN; N <= kEnsMaxN; ++N)
     if (items_epb(N, threads) < 1) return fail(DG_ERR_ARG, "dg_ensemble_set_block: CTA too small");
-  int dev = 0, nsm = 152;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   cudaStreamSynchronize(E->stream);
   E->block = threads;
-  E->grid = nsm * blocks_per_sm;
+  E->per_sm = blocks_per_sm;
   if (E->graph) {
     cudaGraphExecDestroy(E->graph);
     E->graph = nullptr;
   }
-  return build_items(E);
+  int rc = build_items(E);
+  if (rc) return rc;
+  return (E->opt.precision == DG_FP64) ? configure_grid<double>(E) : configure_grid<float>(E);
+}
+
+int dg_ensemble_get_block(const dg_ensemble* E, int* threads, int* ctas_per_sm, int* grid) {
+  if (!E) return fail(DG_ERR_ARG, "dg_ensemble_get_block: null ensemble");
+  if (threads) *threads = E->block;
+  if (ctas_per_sm) *ctas_per_sm = E->per_sm;
+  if (grid) *grid = E->grid;
+  return DG_OK;
 }
 
 // Autotuner: times one stage for every candidate (threads per CTA, CTAs per
-// SM) on (u, u_tmp) and keeps the fastest; the RK register is saved and
-// restored around the trials.
+// SM) from u into u_tmp (u is not changed) and keeps the fastest; the RK
+// register is saved and restored around the trials.
 int dg_ensemble_tune(dg_ensemble* E, const double* u, double* u_tmp, int* best_threads,
                      int* best_blocks_per_sm, float* best_ms) {
   if (!E || !u || !u_tmp || u == u_tmp) return fail(DG_ERR_ARG, "dg_ensemble_tune: bad argument");
   const int cand_t[] = {64, 128, 192, 256};  // at most the kernel's launch bound
-  const int cand_b[] = {2, 4, 8};
-  int dev = 0, nsm = 152;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const int cand_b[] = {1, 2, 4, 8};
   float best = 1e30f;
-  int bt = E->block, bb = E->grid / nsm;
+  int bt = E->block, bb = E->per_sm;
   double* ksave = nullptr;
   if (cudaMalloc(&ksave, E->nvalues * sizeof(double)) != cudaSuccess)
     return fail(DG_ERR_OOM, "dg_ensemble_tune: cudaMalloc");

@@ -18,16 +18,11 @@
 //    coalesced store of du, or the fused stage update k <- A k + dt du,
 //    u <- u + B k.
 //
-// FP32 kernels keep the pressure relative to a per-element reference P_e
-// (P_e = fl32((gamma-1) E at the element's first node); p' = p - P_e is formed
-// from the FP64 energy difference E - E_ref). Because the rows of Ds sum to
-// -lift at the boundary nodes and to zero inside, the constant P_e in the
-// normal-momentum flux and the term P_e avg(v_n) in the energy flux cancel
-// analytically against the lifting: the kernels accumulate only p' parts,
-// add P_e sum_b Ds_ab avg(v_n) to the energy once per node, and store the
-// normal-momentum surface flux relative to the left element's P_e.
+// These templates are instantiated for FP64 meshes; FP32 meshes run the
+// perturbation-form kernels of dg_rhs32.cuh.
 #pragma once
 #include "dg_device.cuh"
+#include "dg_f32.cuh"
 
 namespace dg {
 
@@ -45,36 +40,6 @@ __device__ __forceinline__ int neighbour32(const Geom& g, int e, int dir, int s)
   else if (dir == 1) y = (y + s + g.n[1]) % g.n[1];
   else z = (z + s + g.n[2]) % g.n[2];
   return elem_index(g, x, y, z);
-}
-
-// FP32 pressure reference of element e: P_e = fl32((gamma-1) E_ref) and the
-// residual c_e = fl32((gamma-1) E_ref - P_e), E_ref = E at the first node.
-__device__ __forceinline__ void pressure_ref(const double* __restrict__ u, int e, int nv, int P,
-                                             double gm1, float& Pe, float& ce, double& Eref) {
-  Eref = u[((long long)e * nv + nv - 1) * P];
-  const double pe = gm1 * Eref;
-  Pe = (float)pe;
-  ce = (float)(pe - (double)Pe);
-}
-
-// FP32 primitives of one node: rho, v, the pressure offset p' = p - P_e
-// (from the FP64 energy difference), and the full pressure P_e + p'.
-template <int D>
-__device__ __forceinline__ void prim_f32(const double* c, float gm1, float Pe, float ce,
-                                         double Eref, float& rho, float* v, float& pp,
-                                         float& p) {
-  rho = (float)c[0];
-  const float rr = rcp(rho);
-  float ke = 0.0f;
-#pragma unroll
-  for (int k = 0; k < D; ++k) {
-    v[k] = (float)c[1 + k] * rr;
-    ke = fmaf(v[k], v[k], ke);
-  }
-  ke *= 0.5f * rho;
-  const float dE = (float)(c[D + 1] - Eref);
-  pp = fmaf(gm1, dE - ke, ce);
-  p = Pe + pp;
 }
 
 // node primitives as seen by one direction, normal component first. The two
@@ -141,15 +106,12 @@ __device__ __forceinline__ void generic_nf(const LinePrim<R, D>& L, const LinePr
 
 template <int D, int N, typename R, int VF, int EPB>
 __device__ __forceinline__ void volume_direction(int dir, R (*sp)[3 + 2 * D][Shape<D, N>::P],
-                                                 R (*sa)[D + 3][Shape<D, N>::P], int el, int l,
-                                                 const Tables<R>& tb, R gm1inv, R Pe,
+                                                 R (*sa)[D + 2][Shape<D, N>::P], int el, int l,
+                                                 const Tables<R>& tb, R gm1inv,
                                                  const R* __restrict__ fs, int nelem, int e,
-                                                 int eleft, R pcorr) {
+                                                 int eleft) {
   using S = Shape<D, N>;
   constexpr int NP = S::NP, NV = S::NV;
-  constexpr bool F32 = sizeof(R) == 4;
-  constexpr bool SHIFT_E = F32 && VF == kVRanocha;  // P_e avg(v_n) accumulated apart
-  constexpr int NA = NV + (SHIFT_E ? 1 : 0);
   const int t1 = (dir + 1) % D, t2 = (dir + 2) % D;
   int node[NP];
   LinePrim<R, D> q[NP];
@@ -169,38 +131,29 @@ __device__ __forceinline__ void volume_direction(int dir, R (*sp)[3 + 2 * D][Sha
       q[a].hvt[D - 2] = sp[el][3 + D + t2][nd];
     }
   }
-  R acc[NP][NA];
+  R acc[NP][NV];
 #pragma unroll
   for (int a = 0; a < NP; ++a)
 #pragma unroll
-    for (int v = 0; v < NA; ++v) acc[a][v] = R(0);
+    for (int v = 0; v < NV; ++v) acc[a][v] = R(0);
 #pragma unroll
   for (int a = 0; a < NP; ++a) {
 #pragma unroll
     for (int b = a + 1; b < NP; ++b) {
       R f[NV], an = R(0);
-      if (VF == kVRanocha) {
-        ranocha_nf<R, D>(q[a], q[b], f, an);
-      } else {
-        generic_nf<VF, R, D>(q[a], q[b], gm1inv, f);
-        if (F32) f[1] -= Pe;
-      }
+      if (VF == kVRanocha) ranocha_nf<R, D>(q[a], q[b], f, an);
+      else generic_nf<VF, R, D>(q[a], q[b], gm1inv, f);
       const R dab = tb.Ds[dir][a][b], dba = tb.Ds[dir][b][a];
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
         acc[a][v] = fma(dab, f[v], acc[a][v]);
         acc[b][v] = fma(dba, f[v], acc[b][v]);
       }
-      if (SHIFT_E) {
-        acc[a][NA - 1] = fma(dab, an, acc[a][NA - 1]);
-        acc[b][NA - 1] = fma(dba, an, acc[b][NA - 1]);
-      }
     }
   }
   // lifting at the two ends of the line: + liftR F*_R at node N (this
   // element's face), + liftL F*_L at node 0 (the left neighbour's face); the
-  // face-node index of this line is l. FP32: the left face's normal momentum
-  // is stored relative to the neighbour's pressure reference (pcorr).
+  // face-node index of this line is l.
   {
     const R lr = tb.liftR[dir], ll = tb.liftL[dir];
     const long long base = (long long)nelem * Shape<D, N>::LINES;
@@ -216,9 +169,7 @@ __device__ __forceinline__ void volume_direction(int dir, R (*sp)[3 + 2 * D][Sha
     for (int c = 0; c < NV; ++c) {
       const long long row = (long long)(dir * NV + comp[c]) * base;
       acc[N][c] = fma(lr, fs[row + oR], acc[N][c]);
-      R fl = fs[row + oL];
-      if (F32 && c == 1) fl += pcorr;
-      acc[0][c] = fma(ll, fl, acc[0][c]);
+      acc[0][c] = fma(ll, fs[row + oL], acc[0][c]);
     }
   }
 #pragma unroll
@@ -229,122 +180,78 @@ __device__ __forceinline__ void volume_direction(int dir, R (*sp)[3 + 2 * D][Sha
     sa[el][1 + t1][nd] += acc[a][2];
     if (D == 3) sa[el][1 + t2][nd] += acc[a][D];
     sa[el][D + 1][nd] += acc[a][D + 1];
-    if (SHIFT_E) sa[el][D + 2][nd] += acc[a][NA - 1];
   }
 }
 
-template <int D, int N, typename R, int VF, int EPB>
-__global__ void __launch_bounds__(EPB* Shape<D, N>::LINES)
-    volume_kernel(double* u, R* __restrict__ du, const R* __restrict__ fs, Geom g, Tables<R> tb,
-                  unsigned* __restrict__ err, StageFuse fz) {
+// One batch of `count` (<= MAXE) elements from e0: the prologue into shared
+// memory (smem: count x (3 + 2D) staged slots, then count x (D + 2)
+// accumulators), the D direction phases with one thread per element line,
+// and the epilogue. Every thread of the block calls it (it synchronises the
+// block); threads beyond count x LINES only help with the prologue and the
+// epilogue.
+template <int D, int N, typename R, int VF, int MAXE>
+__device__ __forceinline__ void volume_batch(double* u, R* __restrict__ du,
+                                             const R* __restrict__ fs, const Geom& g,
+                                             const Tables<R>& tb, unsigned* __restrict__ err,
+                                             const StageFuse& fz, int e0, int count,
+                                             unsigned char* smem) {
   using S = Shape<D, N>;
   constexpr int P = S::P, NV = S::NV, LINES = S::LINES;
-  constexpr bool F32 = sizeof(R) == 4;
-  constexpr int NC = 3 + 2 * D;  // s0, s1 (see LinePrim), p/2 (or p'/2), v[D], v[D]/2
-  extern __shared__ __align__(16) unsigned char dg_smem[];
-  R(*sp)[NC][P] = reinterpret_cast<R(*)[NC][P]>(dg_smem);
-  R(*sa)[D + 3][P] = reinterpret_cast<R(*)[D + 3][P]>(dg_smem + sizeof(R) * EPB * NC * P);
-  __shared__ int s_left[EPB][3];
-  __shared__ float s_pref[EPB][4];  // FP32: own P_e, then the left neighbours' P
-  __shared__ float s_cref[EPB];
-  __shared__ double s_eref[EPB];
-  const int e0 = blockIdx.x * EPB;
-  const int nelem = (int)g.nelem;
+  constexpr int NC = 3 + 2 * D;  // s0, s1 (see LinePrim), p/2, v[D], v[D]/2
+  R(*sp)[NC][P] = reinterpret_cast<R(*)[NC][P]>(smem);
+  R(*sa)[NV][P] = reinterpret_cast<R(*)[NV][P]>(smem + sizeof(R) * count * NC * P);
+  __shared__ int s_left[MAXE][3];
   const R gm1inv = R(g.gm1inv);
-  if (threadIdx.x < EPB && e0 + (int)threadIdx.x < nelem) {
+  if ((int)threadIdx.x < count) {
     const int el = threadIdx.x, e = e0 + el;
     const int x = e % g.n[0], r = e / g.n[0], y = r % g.n[1], z = r / g.n[1];
     s_left[el][0] = elem_index(g, x == 0 ? g.n[0] - 1 : x - 1, y, z);
     s_left[el][1] = elem_index(g, x, y == 0 ? g.n[1] - 1 : y - 1, z);
     s_left[el][2] = (D == 3) ? elem_index(g, x, y, z == 0 ? g.n[2] - 1 : z - 1) : 0;
-    if (F32) {
-      float Pe, ce;
-      double Er;
-      pressure_ref(u, e, NV, P, g.gm1, Pe, ce, Er);
-      s_pref[el][0] = Pe;
-      s_cref[el] = ce;
-      s_eref[el] = Er;
-#pragma unroll
-      for (int k = 0; k < D; ++k) {
-        if (fz.pref) {
-          s_pref[el][1 + k] = fz.pref[s_left[el][k]];
-        } else {
-          float Pl, cl;
-          double El;
-          pressure_ref(u, s_left[el][k], NV, P, g.gm1, Pl, cl, El);
-          s_pref[el][1 + k] = Pl;
-        }
-      }
-    }
   }
   __syncthreads();
   unsigned bad = 0;
-  for (int t = threadIdx.x; t < EPB * P; t += blockDim.x) {
+  for (int t = threadIdx.x; t < count * P; t += blockDim.x) {
     const int el = t / P, node = t % P;
     const int e = e0 + el;
-    if (e >= nelem) continue;
     double c[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) c[v] = u[((long long)e * NV + v) * P + node];
-    R rho, p, hp, v[D];
-    if (F32) {
-      float vf[D], pp, pf, rf;
-      prim_f32<D>(c, (float)g.gm1, s_pref[el][0], s_cref[el], s_eref[el], rf, vf, pp, pf);
-      rho = R(rf);
-      p = R(pf);
-      hp = R(0.5f * pp);
-#pragma unroll
-      for (int k = 0; k < D; ++k) v[k] = R(vf[k]);
-      if (!(rf > 0.0f)) bad |= kErrRho;
-      if (!(pf > 0.0f)) bad |= kErrP;
-      if (!isfinite(rf) || !isfinite(pf)) bad |= kErrNaN;
-    } else {
-      double rr;
-      const Prim<double, D> q = prim_rcp<D>(c, g.gm1, rr);
-      bad |= prim_check(q);
-      rho = R(q.rho);
-      p = R(q.p);
-      hp = R(0.5) * p;
-#pragma unroll
-      for (int k = 0; k < D; ++k) v[k] = R(q.v[k]);
-    }
-    node_slots<VF, R>(rho, p, R(g.gm1), sp[el][0][node], sp[el][1][node]);
-    sp[el][2][node] = hp;
+    double rr;
+    const Prim<double, D> q = prim_rcp<D>(c, g.gm1, rr);
+    bad |= prim_check(q);
+    const R p = R(q.p);
+    node_slots<VF, R>(R(q.rho), p, R(g.gm1), sp[el][0][node], sp[el][1][node]);
+    sp[el][2][node] = R(0.5) * p;
 #pragma unroll
     for (int k = 0; k < D; ++k) {
-      sp[el][3 + k][node] = v[k];
-      sp[el][3 + D + k][node] = R(0.5) * v[k];
+      sp[el][3 + k][node] = R(q.v[k]);
+      sp[el][3 + D + k][node] = R(0.5) * R(q.v[k]);
     }
 #pragma unroll
-    for (int k = 0; k < D + 3; ++k) sa[el][k][node] = R(0);
+    for (int k = 0; k < NV; ++k) sa[el][k][node] = R(0);
   }
   if (bad) atomicOr(err, bad);
   __syncthreads();
   const int el = threadIdx.x / LINES, l = threadIdx.x % LINES;
-  const bool active = (e0 + el) < nelem;
-  const R Pe = F32 ? R(s_pref[active ? el : 0][0]) : R(0);
+  const bool active = el < count;
+  const int nelem = (int)g.nelem;
 #pragma unroll 1
   for (int dir = 0; dir < D; ++dir) {
-    if (active) {
-      const R pcorr = F32 ? R(s_pref[el][1 + dir]) - Pe : R(0);
-      volume_direction<D, N, R, VF, EPB>(dir, sp, sa, el, l, tb, gm1inv, Pe, fs, nelem, e0 + el,
-                                         s_left[el][dir], pcorr);
-    }
+    if (active)
+      volume_direction<D, N, R, VF, MAXE>(dir, sp, sa, el, l, tb, gm1inv, fs, nelem, e0 + el,
+                                          s_left[el][dir]);
     __syncthreads();
   }
-  // epilogue: lifting of the surface fluxes, then the store (or the fused
-  // stage update)
+  // epilogue: the store (or the fused stage update)
   const double dtv = fz.k ? *fz.dt : 0.0;
   double* const uo = fz.u_out ? fz.u_out : u;
-  for (int t = threadIdx.x; t < EPB * P; t += blockDim.x) {
+  for (int t = threadIdx.x; t < count * P; t += blockDim.x) {
     const int ell = t / P, node = t % P;
     const int e = e0 + ell;
-    if (e >= nelem) continue;
-    const R Pself = F32 ? R(s_pref[ell][0]) : R(0);
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
-      R val = sa[ell][v][node];
-      if (F32 && VF == kVRanocha && v == D + 1) val = fma(Pself, sa[ell][D + 2][node], val);
+      const R val = sa[ell][v][node];
       const long long i = ((long long)e * NV + v) * P + node;
       if (fz.k) {
         // the first stage (A = 0) neither reads k nor lets stale k values in
@@ -359,10 +266,20 @@ __global__ void __launch_bounds__(EPB* Shape<D, N>::LINES)
   }
 }
 
+template <int D, int N, typename R, int VF, int EPB>
+__global__ void __launch_bounds__(EPB* Shape<D, N>::LINES)
+    volume_kernel(double* u, R* __restrict__ du, const R* __restrict__ fs, Geom g, Tables<R> tb,
+                  unsigned* __restrict__ err, StageFuse fz) {
+  extern __shared__ __align__(16) unsigned char dg_smem[];
+  const int e0 = blockIdx.x * EPB;
+  const int left = (int)g.nelem - e0;
+  volume_batch<D, N, R, VF, EPB>(u, du, fs, g, tb, err, fz, e0, left < EPB ? left : EPB, dg_smem);
+}
+
 // ---- surface ----
 // trace state for the surface flux, normal component first; ps is the
-// pressure in the additive normal-momentum term (p itself in FP64, p minus the
-// left element's P_e in FP32); rr = 1/rho
+// pressure in the additive normal-momentum term (p itself here; the MHD-free
+// ensemble kernels pass other offsets); rr = 1/rho
 template <typename R, int D>
 struct Trace {
   R rho, rr, p, ps, vn, vt[D - 1], mn, mt[D - 1], E;
@@ -441,113 +358,94 @@ __device__ __forceinline__ void surface_nf(int sf, const Trace<R, D>& L, const T
   }
 }
 
+// the surface flux of face node l of element e's right face in direction
+// dir (the left element e, the right one its +dir neighbour), stored in
+// fs[dir][v][e][l]
 template <int D, int N, typename R, int dir>
-__device__ __forceinline__ void surface_body(const double* __restrict__ u, R* __restrict__ fs,
-                                             const Geom& g, int sf, float* __restrict__ pref) {
+__device__ __forceinline__ void face_flux(const double* __restrict__ u, R* __restrict__ fs,
+                                          const Geom& g, int sf, int e, int l) {
   using S = Shape<D, N>;
   constexpr int NV = S::NV, P = S::P, NF = S::LINES;
-  constexpr bool F32 = sizeof(R) == 4;
   const int nelem = (int)g.nelem;
-  const long long total = (long long)nelem * NF;
   const R gamma = R(g.gamma), gm1inv = R(g.gm1inv);
   constexpr int t1 = (dir + 1) % D, t2 = (dir + 2) % D;
-  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
-       t += (long long)gridDim.x * blockDim.x) {
-    const int e = (int)(t / NF);
-    const int l = (int)(t % NF);
-    const int er = neighbour32(g, e, dir, +1);
-    const int nl = line_node<D, N, dir>(l, N), nr = line_node<D, N, dir>(l, 0);
-    double cl[NV], cr[NV];
+  const int er = neighbour32(g, e, dir, +1);
+  const int nl = line_node<D, N, dir>(l, N), nr = line_node<D, N, dir>(l, 0);
+  double cl[NV], cr[NV];
 #pragma unroll
-    for (int v = 0; v < NV; ++v) {
-      cl[v] = u[((long long)e * NV + v) * P + nl];
-      cr[v] = u[((long long)er * NV + v) * P + nr];
-    }
-    Trace<R, D> L, Rt;
-    R dE;
-    if (F32) {
-      float PeL, ceL, PeR, ceR, vL[D], vR[D], ppL, ppR, pL, pR, rL, rR;
-      double ErL, ErR;
-      pressure_ref(u, e, NV, P, g.gm1, PeL, ceL, ErL);
-      pressure_ref(u, er, NV, P, g.gm1, PeR, ceR, ErR);
-      if (dir == 0 && l == 0 && pref) pref[e] = PeL;
-      prim_f32<D>(cl, (float)g.gm1, PeL, ceL, ErL, rL, vL, ppL, pL);
-      prim_f32<D>(cr, (float)g.gm1, PeR, ceR, ErR, rR, vR, ppR, pR);
-      L.rho = R(rL);
-      L.rr = R(rcp(rL));
-      L.p = R(pL);
-      L.ps = R(ppL);
-      Rt.rho = R(rR);
-      Rt.rr = R(rcp(rR));
-      Rt.p = R(pR);
-      Rt.ps = R(ppR + (PeR - PeL));
-      L.vn = R(vL[dir]);
-      Rt.vn = R(vR[dir]);
-      L.vt[0] = R(vL[t1]);
-      Rt.vt[0] = R(vR[t1]);
-      if (D == 3) {
-        L.vt[D - 2] = R(vL[t2]);
-        Rt.vt[D - 2] = R(vR[t2]);
-      }
-      dE = R((float)(cr[NV - 1] - cl[NV - 1]));
-    } else {
-      double rrl, rrr;
-      const Prim<double, D> ql = prim_rcp<D>(cl, g.gm1, rrl);
-      const Prim<double, D> qr = prim_rcp<D>(cr, g.gm1, rrr);
-      L.rr = R(rrl);
-      Rt.rr = R(rrr);
-      L.rho = R(ql.rho);
-      L.p = R(ql.p);
-      L.ps = L.p;
-      Rt.rho = R(qr.rho);
-      Rt.p = R(qr.p);
-      Rt.ps = Rt.p;
-      L.vn = R(ql.v[dir]);
-      Rt.vn = R(qr.v[dir]);
-      L.vt[0] = R(ql.v[t1]);
-      Rt.vt[0] = R(qr.v[t1]);
-      if (D == 3) {
-        L.vt[D - 2] = R(ql.v[t2]);
-        Rt.vt[D - 2] = R(qr.v[t2]);
-      }
-      dE = R(cr[NV - 1] - cl[NV - 1]);
-    }
-    L.mn = R(cl[1 + dir]);
-    Rt.mn = R(cr[1 + dir]);
-    L.mt[0] = R(cl[1 + t1]);
-    Rt.mt[0] = R(cr[1 + t1]);
-    if (D == 3) {
-      L.mt[D - 2] = R(cl[1 + t2]);
-      Rt.mt[D - 2] = R(cr[1 + t2]);
-    }
-    L.E = R(cl[NV - 1]);
-    Rt.E = R(cr[NV - 1]);
-    R f[NV];
-    surface_nf<R, D>(sf, L, Rt, dE, gamma, gm1inv, f);
-    const long long base = (long long)nelem * NF;
-    const long long off = (long long)e * NF + l;
-    fs[(long long)(dir * NV + 0) * base + off] = f[0];
-    fs[(long long)(dir * NV + 1 + dir) * base + off] = f[1];
-    fs[(long long)(dir * NV + 1 + t1) * base + off] = f[2];
-    if (D == 3) fs[(long long)(dir * NV + 1 + t2) * base + off] = f[D];
-    fs[(long long)(dir * NV + NV - 1) * base + off] = f[NV - 1];
+  for (int v = 0; v < NV; ++v) {
+    cl[v] = u[((long long)e * NV + v) * P + nl];
+    cr[v] = u[((long long)er * NV + v) * P + nr];
   }
+  Trace<R, D> L, Rt;
+  double rrl, rrr;
+  const Prim<double, D> ql = prim_rcp<D>(cl, g.gm1, rrl);
+  const Prim<double, D> qr = prim_rcp<D>(cr, g.gm1, rrr);
+  L.rr = R(rrl);
+  Rt.rr = R(rrr);
+  L.rho = R(ql.rho);
+  L.p = R(ql.p);
+  L.ps = L.p;
+  Rt.rho = R(qr.rho);
+  Rt.p = R(qr.p);
+  Rt.ps = Rt.p;
+  L.vn = R(ql.v[dir]);
+  Rt.vn = R(qr.v[dir]);
+  L.vt[0] = R(ql.v[t1]);
+  Rt.vt[0] = R(qr.v[t1]);
+  if (D == 3) {
+    L.vt[D - 2] = R(ql.v[t2]);
+    Rt.vt[D - 2] = R(qr.v[t2]);
+  }
+  const R dE = R(cr[NV - 1] - cl[NV - 1]);
+  L.mn = R(cl[1 + dir]);
+  Rt.mn = R(cr[1 + dir]);
+  L.mt[0] = R(cl[1 + t1]);
+  Rt.mt[0] = R(cr[1 + t1]);
+  if (D == 3) {
+    L.mt[D - 2] = R(cl[1 + t2]);
+    Rt.mt[D - 2] = R(cr[1 + t2]);
+  }
+  L.E = R(cl[NV - 1]);
+  Rt.E = R(cr[NV - 1]);
+  R f[NV];
+  surface_nf<R, D>(sf, L, Rt, dE, gamma, gm1inv, f);
+  const long long base = (long long)nelem * NF;
+  const long long off = (long long)e * NF + l;
+  fs[(long long)(dir * NV + 0) * base + off] = f[0];
+  fs[(long long)(dir * NV + 1 + dir) * base + off] = f[1];
+  fs[(long long)(dir * NV + 1 + t1) * base + off] = f[2];
+  if (D == 3) fs[(long long)(dir * NV + 1 + t2) * base + off] = f[D];
+  fs[(long long)(dir * NV + NV - 1) * base + off] = f[NV - 1];
+}
+
+template <int D, int N, typename R, int dir>
+__device__ __forceinline__ void surface_body(const double* __restrict__ u, R* __restrict__ fs,
+                                             const Geom& g, int sf) {
+  constexpr int NF = Shape<D, N>::LINES;
+  const long long total = g.nelem * NF;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x)
+    face_flux<D, N, R, dir>(u, fs, g, sf, (int)(t / NF), (int)(t % NF));
 }
 
 template <int D, int N, typename R>
-__global__ void surface_kernel(const double* __restrict__ u, R* __restrict__ fs, Geom g, int sf,
-                               float* __restrict__ pref) {
-  if (blockIdx.y == 0) surface_body<D, N, R, 0>(u, fs, g, sf, pref);
-  else if (blockIdx.y == 1) surface_body<D, N, R, 1>(u, fs, g, sf, pref);
-  else surface_body<D, N, R, (D == 3 ? 2 : 1)>(u, fs, g, sf, pref);
+__global__ void surface_kernel(const double* __restrict__ u, R* __restrict__ fs, Geom g, int sf) {
+  if (blockIdx.y == 0) surface_body<D, N, R, 0>(u, fs, g, sf);
+  else if (blockIdx.y == 1) surface_body<D, N, R, 1>(u, fs, g, sf);
+  else surface_body<D, N, R, (D == 3 ? 2 : 1)>(u, fs, g, sf);
 }
+
+}  // namespace dg
+#include "dg_rhs32.cuh"
+namespace dg {
 
 // elements per CTA: about 128 threads, dynamic shared memory <= 96 KB
 template <int D, int N, typename R>
 struct Launch {
   static constexpr int LINES = Shape<D, N>::LINES;
   static constexpr int BY_THREADS = (128 / LINES) > 0 ? (128 / LINES) : 1;
-  static constexpr int PER_ELEM = (3 + 2 * D + D + 3) * Shape<D, N>::P * (int)sizeof(R);
+  static constexpr int PER_ELEM = (3 + 2 * D + D + 2) * Shape<D, N>::P * (int)sizeof(R);
   static constexpr int BY_SMEM = (98304 / PER_ELEM) > 0 ? (98304 / PER_ELEM) : 1;
   static constexpr int EPB = BY_THREADS < BY_SMEM ? BY_THREADS : BY_SMEM;
   static constexpr int SMEM = EPB * PER_ELEM;
@@ -561,6 +459,14 @@ cudaError_t allow_smem(K kernel, int bytes) {
   if (e != cudaSuccess) return e;
   if (bytes + (int)fa.sharedSizeBytes <= 48 * 1024) return cudaSuccess;
   return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
+
+// the largest shared-memory carveout (the kernel keeps its working set in
+// shared memory and streams the rest)
+template <typename K>
+cudaError_t prefer_shared(K kernel) {
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                              (int)cudaSharedmemCarveoutMaxShared);
 }
 
 // parts: bit 0 = surface kernel, bit 1 = volume kernel (both for an rhs)
@@ -588,28 +494,91 @@ cudaError_t launch_volume_epb(const double* u, R* du, R* fs, const Geom& g, cons
   return cudaGetLastError();
 }
 
+// FP32 kernels: elements per CTA as for FP64 (about 128 threads, dynamic
+// shared memory <= 96 KB)
+template <int D, int N>
+struct Launch32 {
+  static constexpr int LINES = Shape<D, N>::LINES;
+  static constexpr int BY_THREADS = (128 / LINES) > 0 ? (128 / LINES) : 1;
+  // staged slots and accumulators (FP32) and the staged RK register (FP64)
+  static constexpr int PER_ELEM = volume32_smem<D, N>(1);
+  static constexpr int BY_SMEM = (98304 / PER_ELEM) > 0 ? (98304 / PER_ELEM) : 1;
+  static constexpr int EPB = BY_THREADS < BY_SMEM ? BY_THREADS : BY_SMEM;
+};
+
+template <int D, int N, int EPB>
+cudaError_t launch_volume32_epb(const double* u, float* du, float* fs, const Geom& g,
+                                const Tables<float>& tb, int vf, unsigned* err, cudaStream_t st,
+                                const StageFuse& fz) {
+  using L = Launch32<D, N>;
+  const long long grid = (g.nelem + EPB - 1) / EPB;
+  const int threads = EPB * L::LINES;
+  constexpr int SM = volume32_smem<D, N>(EPB);
+  cudaError_t e;
+  if (vf == kVRanocha) {
+    if ((e = allow_smem(volume_kernel32<D, N, kVRanocha, EPB>, SM)) != cudaSuccess ||
+        (e = prefer_shared(volume_kernel32<D, N, kVRanocha, EPB>)) != cudaSuccess)
+      return e;
+    volume_kernel32<D, N, kVRanocha, EPB><<<(unsigned)grid, threads, SM, st>>>(
+        const_cast<double*>(u), du, fs, g, tb, err, fz);
+  } else if (vf == kVChandrashekar) {
+    if ((e = allow_smem(volume_kernel32<D, N, kVChandrashekar, EPB>, SM)) != cudaSuccess ||
+        (e = prefer_shared(volume_kernel32<D, N, kVChandrashekar, EPB>)) != cudaSuccess)
+      return e;
+    volume_kernel32<D, N, kVChandrashekar, EPB><<<(unsigned)grid, threads, SM, st>>>(
+        const_cast<double*>(u), du, fs, g, tb, err, fz);
+  } else {
+    if ((e = allow_smem(volume_kernel32<D, N, kVCentral, EPB>, SM)) != cudaSuccess ||
+        (e = prefer_shared(volume_kernel32<D, N, kVCentral, EPB>)) != cudaSuccess)
+      return e;
+    volume_kernel32<D, N, kVCentral, EPB><<<(unsigned)grid, threads, SM, st>>>(
+        const_cast<double*>(u), du, fs, g, tb, err, fz);
+  }
+  return cudaGetLastError();
+}
+
 // Meshes with fewer elements than about two CTAs per SM run one element per
 // CTA (and the face kernel in 64-thread blocks), spreading the FP64 work (2
 // lanes per clock per SM) over more SMs; the arithmetic per node, and so the
-// result, is the same.
+// result, is the same. FP32 meshes first write the per-element references
+// (part 1), which both flux kernels read.
 template <int D, int N, typename R>
 cudaError_t launch_rhs_dn(const double* u, R* du, R* fs, const Geom& g, const Tables<R>& tb,
                           int vf, int sf, unsigned* err, cudaStream_t st, int parts,
                           const StageFuse& fz) {
-  using L = Launch<D, N, R>;
-  constexpr int EPB = L::EPB;
+  constexpr bool F32 = sizeof(R) == 4;
   if (parts & 1) {
     const long long total = g.nelem * Shape<D, N>::LINES;
     const int threads = (total < 152LL * 4 * 256) ? 64 : 256;
     long long blocks = (total + threads - 1) / threads;
     if (blocks > 152 * 16) blocks = 152 * 16;
     if (blocks < 1) blocks = 1;
-    surface_kernel<D, N, R><<<dim3((unsigned)blocks, D), threads, 0, st>>>(u, fs, g, sf, fz.pref);
+    if constexpr (F32) {
+      if (!fz.ref || !fz.refE) return cudaErrorInvalidValue;
+      long long eb = (g.nelem + 127) / 128;
+      if (eb > 152 * 16) eb = 152 * 16;
+      ref_kernel<D><<<(unsigned)eb, 128, 0, st>>>(u, fz.ref, fz.refE, g.nelem, N + 1, g.gm1,
+                                                  g.gm1inv);
+      surface_kernel32<D, N><<<dim3((unsigned)blocks, D), threads, 0, st>>>(u, fs, g, sf, fz.ref,
+                                                                            fz.refE);
+    } else {
+      surface_kernel<D, N, R><<<dim3((unsigned)blocks, D), threads, 0, st>>>(u, fs, g, sf);
+    }
   }
   if (!(parts & 2)) return cudaGetLastError();
-  if (EPB > 1 && g.nelem < 2LL * 152 * EPB)
-    return launch_volume_epb<D, N, R, 1>(u, du, fs, g, tb, vf, err, st, fz);
-  return launch_volume_epb<D, N, R, EPB>(u, du, fs, g, tb, vf, err, st, fz);
+  if constexpr (F32) {
+    if (!fz.ref || !fz.refE) return cudaErrorInvalidValue;
+    constexpr int EPB = Launch32<D, N>::EPB;
+    if (EPB > 1 && g.nelem < 2LL * 152 * EPB)
+      return launch_volume32_epb<D, N, 1>(u, du, fs, g, tb, vf, err, st, fz);
+    return launch_volume32_epb<D, N, EPB>(u, du, fs, g, tb, vf, err, st, fz);
+  } else {
+    using L = Launch<D, N, R>;
+    constexpr int EPB = L::EPB;
+    if (EPB > 1 && g.nelem < 2LL * 152 * EPB)
+      return launch_volume_epb<D, N, R, 1>(u, du, fs, g, tb, vf, err, st, fz);
+    return launch_volume_epb<D, N, R, EPB>(u, du, fs, g, tb, vf, err, st, fz);
+  }
 }
 
 template <int D, typename R>

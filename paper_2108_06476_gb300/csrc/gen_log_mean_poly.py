@@ -28,13 +28,13 @@ POLYS = [
     ("s_short", "S", "double", "1e-2", 6),
     ("q_long", "Q", "double", "0.25", 13),
     ("s_long", "S", "double", "0.25", 14),
-    # the FP32 kernels' ranges, evaluated in FP64 (f2 = t^2 of an FP32 t),
-    # within about a tenth of the FP32 rounding of the result
-    ("q_short32", "Q", "double", "4e-2", 3),
-    ("s_short32", "S", "double", "4e-2", 4),
-    ("q_long32", "Q", "double", "0.25", 6),
-    ("s_long32", "S", "double", "0.25", 6),
 ]
+
+# the FP32 kernels' perturbation form (dg_f32.cuh) uses R(f2) = (1 - Q(f2))/f2
+# (phi = 1 - Q = f2 R): its FP32 range is a plain interpolant of R at the
+# Chebyshev points of [0, 0.25], rounded to FP32; its FP64 small-difference
+# branch (f2 < 1e-4) is the Taylor series of R, printed by series_r().
+R_POLYS = [("phi_r32", "float", "0.25", 5)]
 
 
 def Q(f2):
@@ -49,6 +49,30 @@ def S(f2):
         return mp.mpf(2)
     t = mp.sqrt(f2)
     return 2 * mp.atanh(t) / t
+
+
+def R(f2):
+    if f2 == 0:
+        return mp.mpf(1) / 3
+    return (1 - Q(f2)) / f2
+
+
+def fit_plain(fun, a, degree):
+    """Monomial coefficients interpolating fun at degree + 1 Chebyshev points."""
+    nodes = [a * (1 + mp.cos(mp.pi * (2 * k + 1) / (2 * (degree + 1)))) / 2
+             for k in range(degree + 1)]
+    V = mp.matrix([[x ** j for j in range(degree + 1)] for x in nodes])
+    c = mp.lu_solve(V, mp.matrix([fun(x) for x in nodes]))
+    return [c[j] for j in range(degree + 1)]
+
+
+def series_r(terms=4):
+    """Taylor coefficients of R(f2): 1/Q = sum_k f2^k/(2k+1) inverted."""
+    s = [mp.mpf(1) / (2 * k + 1) for k in range(terms + 2)]
+    inv = [mp.mpf(1)]  # coefficients of Q = 1/s
+    for n in range(1, terms + 2):
+        inv.append(-sum(s[k] * inv[n - k] for k in range(1, n + 1)))
+    return [-inv[k + 1] for k in range(terms)]  # R = (1 - Q)/f2
 
 
 def fit(fun, a, degree):
@@ -95,6 +119,12 @@ def main():
         fun = {"Q": Q, "S": S}[fname]
         coeffs = rounded(fit(fun, mp.mpf(a), degree), real)
         print(c_function(name, real, coeffs, a, max_rel_error(fun, coeffs, mp.mpf(a))))
+    for name, real, a, degree in R_POLYS:
+        coeffs = rounded(fit_plain(R, mp.mpf(a), degree), real)
+        print(c_function(name, real, coeffs, a, max_rel_error(R, coeffs, mp.mpf(a))))
+    coeffs = [float(c) for c in series_r(4)]
+    print(c_function("phi_r64", "double", coeffs, "1e-4",
+                     max_rel_error(R, coeffs, mp.mpf("1e-4"))))
 
 
 if __name__ == "__main__":

@@ -37,7 +37,8 @@ EXPORTS = ("dg_mesh_create", "dg_mesh_create_curved", "dg_mesh_create_mhd",
            "dg_ensemble_set_dt", "dg_ensemble_get_dt", "dg_ensemble_compute_dt",
            "dg_ensemble_stage", "dg_ensemble_step", "dg_ensemble_step_graph",
            "dg_ensemble_rk_reset", "dg_ensemble_check", "dg_ensemble_set_block",
-           "dg_ensemble_tune")
+           "dg_ensemble_get_block", "dg_ensemble_tune", "dg_measure_peaks",
+           "dg_selftest_arith")
 
 
 class DGError(RuntimeError):
@@ -93,7 +94,7 @@ def load(path: str = SO_PATH):
     L.dg_integrals.argtypes = [vp, vp, dp]
     L.dg_mesh_check.argtypes = [vp, ip]
     L.dg_rhs_noalloc.argtypes = [ctypes.c_int, ctypes.c_int, ip, dp, vp, vp, vp, vp]
-    L.dg_ensemble_create.argtypes = [ctypes.c_int, ip, ip, ctypes.POINTER(_Options), vp,
+    L.dg_ensemble_create.argtypes = [ctypes.c_int, ip, ip, ip, dp, ctypes.POINTER(_Options), vp,
                                      ctypes.POINTER(vp)]
     L.dg_ensemble_destroy.argtypes = [vp]
     L.dg_ensemble_info.argtypes = [vp, llp, llp, llp]
@@ -101,11 +102,14 @@ def load(path: str = SO_PATH):
     L.dg_ensemble_get_dt.argtypes = [vp, dp]
     L.dg_ensemble_compute_dt.argtypes = [vp, vp, ctypes.c_double]
     L.dg_ensemble_stage.argtypes = [vp, vp, vp, ctypes.c_int]
-    L.dg_ensemble_step.argtypes = [vp, vp, vp, ctypes.c_double]
-    L.dg_ensemble_step_graph.argtypes = [vp, vp, vp, ctypes.c_double]
+    L.dg_ensemble_step.argtypes = [vp, vp, ctypes.c_double]
+    L.dg_ensemble_step_graph.argtypes = [vp, vp, ctypes.c_double]
     L.dg_ensemble_rk_reset.argtypes = [vp]
     L.dg_ensemble_check.argtypes = [vp, ip]
     L.dg_ensemble_set_block.argtypes = [vp, ctypes.c_int, ctypes.c_int]
+    L.dg_ensemble_get_block.argtypes = [vp, ip, ip, ip]
+    L.dg_measure_peaks.argtypes = [dp, dp, ip, vp]
+    L.dg_selftest_arith.argtypes = [ctypes.c_int, vp, vp, ctypes.c_longlong, vp]
     L.dg_ensemble_tune.argtypes = [vp, vp, vp, ip, ip, ctypes.POINTER(ctypes.c_float)]
     L.dg_last_error.restype = ctypes.c_char_p
     L.dg_last_error.argtypes = []
@@ -119,6 +123,20 @@ def _check(rc: int, what: str):
     if rc != 0:
         msg = load().dg_last_error().decode(errors="replace")
         raise DGError(f"{what} failed ({rc}): {msg}")
+
+
+def measure_peaks(fp64=True, fp32=True, stream=None):
+    """Measured FP64/FP32 vector FMA throughput (TFLOP/s) and SM count of the
+    current device (dg_measure_peaks)."""
+    import torch
+    L = load()
+    a, b, n = ctypes.c_double(0.0), ctypes.c_double(0.0), ctypes.c_int(0)
+    st = stream if stream is not None else torch.cuda.current_stream()
+    _check(L.dg_measure_peaks(ctypes.byref(a) if fp64 else None, ctypes.byref(b) if fp32 else None,
+                              ctypes.byref(n), ctypes.c_void_p(st.cuda_stream)),
+           "dg_measure_peaks")
+    return {"fp64_tflops": a.value if fp64 else None, "fp32_tflops": b.value if fp32 else None,
+            "sm_count": n.value}
 
 
 def lgl_nodes(N: int):
@@ -381,12 +399,14 @@ class Mesh:
 
 
 class Ensemble:
-    """A batch of independent 3D periodic Euler meshes on [-1, 1]^3 with
-    degrees N[s] in {3, 4, 5} and n[s]^3 elements, advanced together (one
-    kernel launch per Runge-Kutta stage). The state of all members is one
-    float64 CUDA tensor; member s is the slice offsets[s]:offsets[s+1]."""
+    """A batch of independent 3D periodic Euler meshes with degrees N[s] in
+    {3, 4, 5} and n[s]^3 elements on the boxes domains[s] ((lo, hi) per
+    direction; default [-1, 1]^3), advanced together (one kernel launch per
+    Runge-Kutta stage). The state of all members is one float64 CUDA tensor;
+    member s is the slice offsets[s]:offsets[s+1]."""
 
-    def __init__(self, N, n, gamma=1.4, surface_flux="llf", precision="fp64", stream=None):
+    def __init__(self, N, n, gamma=1.4, surface_flux="llf", precision="fp64", stream=None,
+                 domains=None, d=None):
         import torch
         self._torch = torch
         L = load()
@@ -396,9 +416,14 @@ class Ensemble:
         opt = _Options(gamma, VFLUX["ranocha"], SFLUX[surface_flux], PRECISION[precision])
         Na = (ctypes.c_int * self.n_sims)(*self.N)
         na = (ctypes.c_int * self.n_sims)(*self.n)
+        da = (ctypes.c_int * self.n_sims)(*([3] * self.n_sims if d is None else d))
+        doms = None
+        if domains is not None:
+            flat = np.ascontiguousarray(domains, dtype=np.float64).reshape(-1)
+            doms = (ctypes.c_double * flat.size)(*flat)
         st = stream if stream is not None else torch.cuda.current_stream()
         h = ctypes.c_void_p()
-        _check(L.dg_ensemble_create(self.n_sims, Na, na, ctypes.byref(opt),
+        _check(L.dg_ensemble_create(self.n_sims, da, Na, na, doms, ctypes.byref(opt),
                                     ctypes.c_void_p(st.cuda_stream), ctypes.byref(h)),
                "dg_ensemble_create")
         self._h = h
@@ -442,15 +467,16 @@ class Ensemble:
         _check(load().dg_ensemble_compute_dt(self._h, _ptr(u), float(cfl)), "dg_ensemble_compute_dt")
 
     def stage(self, u_in, u_out, s):
+        """u_out = u_in + B_s k with k = A_s k + dt du(u_in); u_out may be u_in."""
         self._chk(u_in)
         self._chk(u_out)
         _check(load().dg_ensemble_stage(self._h, _ptr(u_in), _ptr(u_out), int(s)), "dg_ensemble_stage")
 
-    def step(self, u, u_tmp, cfl=0.0, graph=False):
+    def step(self, u, cfl=0.0, graph=False):
+        """One LSRK step in place on u (device CFL steps first when cfl > 0)."""
         self._chk(u)
-        self._chk(u_tmp)
         fn = load().dg_ensemble_step_graph if graph else load().dg_ensemble_step
-        _check(fn(self._h, _ptr(u), _ptr(u_tmp), float(cfl)), "dg_ensemble_step")
+        _check(fn(self._h, _ptr(u), float(cfl)), "dg_ensemble_step")
 
     def rk_reset(self):
         _check(load().dg_ensemble_rk_reset(self._h), "dg_ensemble_rk_reset")
@@ -463,6 +489,13 @@ class Ensemble:
     def set_block(self, threads, blocks_per_sm):
         _check(load().dg_ensemble_set_block(self._h, int(threads), int(blocks_per_sm)),
                "dg_ensemble_set_block")
+
+    def get_block(self):
+        """(threads per CTA, requested CTAs per SM, CTAs launched)."""
+        t, b, g = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(load().dg_ensemble_get_block(self._h, ctypes.byref(t), ctypes.byref(b),
+                                            ctypes.byref(g)), "dg_ensemble_get_block")
+        return t.value, b.value, g.value
 
     def tune(self, u, u_tmp):
         """Autotune the CTA shape; returns (threads, ctas_per_sm, ms_per_stage)."""

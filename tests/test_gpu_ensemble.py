@@ -1,14 +1,16 @@
-"""GPU batched ensemble (one kernel launch per RK stage over all members)
-against the FP64 oracle member by member: one stage, one full step with the
-device-computed CFL time steps, the CUDA-graph step, the autotuner, and the
-seeded 48-member configuration (FP64 sampled against the oracle, FP32 against
-FP64)."""
+"""GPU batched ensemble (one cooperative kernel launch per RK stage over all
+members: face phase, grid barrier, volume phase) against the FP64 oracle
+member by member: one stage, one full step with the device-computed CFL time
+steps, in-place and out-of-place stages, the CUDA-graph step, the autotuner,
+members on their own boxes, the single-mesh path on the same member, and the
+seeded 48-member configuration with every member compared with the oracle on
+a sample of its elements."""
 import numpy as np
 import pytest
 
 torch = pytest.importorskip("torch")
 
-from paper_2108_06476_gb300 import Ensemble, workloads as W  # noqa: E402
+from paper_2108_06476_gb300 import Ensemble, Mesh, DGError, RK_B, workloads as W  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 
@@ -37,13 +39,25 @@ def rel(a, b):
     return float(np.linalg.norm(a - b) / np.linalg.norm(b))
 
 
+def stage_rhs(E, u0, precision="fp64"):
+    """rhs of every member from one stage with a large dt, so that the
+    increment dominates u and (u1 - u0) / (B_0 dt) recovers the rhs without
+    the rounding of u0 + increment."""
+    ut = torch.from_numpy(u0.copy()).cuda()
+    tmp = torch.empty_like(ut)
+    big = 1.0e6
+    E.set_dt(np.full(E.n_sims, big))
+    E.stage(ut, tmp, 0)
+    assert E.check() == 0
+    return [(g - p) / (RK_B[0] * big) for g, p in zip(split(E, tmp.cpu().numpy()), split(E, u0))]
+
+
 def test_ensemble_step_matches_oracle(orc):
     mem = small_members()
     u0 = W.ensemble_state(mem, lambda N: orc.lgl(N)[0])
     E = Ensemble([m.N for m in mem], [m.n[0] for m in mem])
     assert E.n_values == u0.size
     ut = torch.from_numpy(u0.copy()).cuda()
-    tmp = torch.empty_like(ut)
     # device CFL steps equal the oracle's per member
     E.compute_dt(ut, cfl=0.5)
     dts = E.get_dt()
@@ -51,23 +65,15 @@ def test_ensemble_step_matches_oracle(orc):
     for s, m in enumerate(mem):
         assert dts[s] == pytest.approx(orc.max_dt(3, m.N, m.n, W.box(3), parts0[s], cfl=0.5),
                                        rel=1e-14)
-    # one stage u1 = u0 + B_0 dt rhs(u0) with a large dt, so that the increment
-    # dominates u and (u1 - u0) / (B_0 dt) recovers the rhs without the
-    # rounding of u0 + increment
-    from paper_2108_06476_gb300 import RK_B
-    big = 1.0e6
-    E.set_dt(np.full(len(mem), big))
-    E.stage(ut, tmp, 0)
-    got = split(E, tmp.cpu().numpy())
-    for s, m in enumerate(mem):
-        du = orc.rhs(3, m.N, m.n, W.box(3), parts0[s])
-        assert rel((got[s] - parts0[s]) / (RK_B[0] * big), du) <= 1e-12
-    # a full step from u0 (k reset, CFL time steps) against the oracle's five
-    # stages; the state is rounded to ulp(u) once per stage on both sides
+    for s, (m, du) in enumerate(zip(mem, stage_rhs(E, u0))):
+        assert rel(du, orc.rhs(3, m.N, m.n, W.box(3), parts0[s])) <= 1e-12
+    # a full step in place from u0 (k reset, CFL time steps) against the
+    # oracle's five stages; the state is rounded to ulp(u) once per stage on
+    # both sides
     E.set_dt(dts)
     E.rk_reset()
     ut.copy_(torch.from_numpy(u0))
-    E.step(ut, tmp, cfl=0.0)
+    E.step(ut, cfl=0.0)
     assert E.check() == 0
     got = split(E, ut.cpu().numpy())
     for s, m in enumerate(mem):
@@ -75,6 +81,41 @@ def test_ensemble_step_matches_oracle(orc):
         inc = np.linalg.norm(ref - parts0[s])
         bound = 1e-11 + 1e-15 * np.linalg.norm(ref) / inc
         assert rel(got[s] - parts0[s], ref - parts0[s]) <= bound
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_in_place_stage_equals_out_of_place(orc, precision):
+    mem = small_members()
+    u0 = W.ensemble_state(mem, lambda N: orc.lgl(N)[0])
+    E = Ensemble([m.N for m in mem], [m.n[0] for m in mem], precision=precision)
+    a = torch.from_numpy(u0.copy()).cuda()
+    b = torch.empty_like(a)
+    E.set_dt(np.full(E.n_sims, 1e-3))
+    E.stage(a, b, 0)
+    E.rk_reset()
+    E.stage(a, a, 0)
+    torch.cuda.synchronize()
+    assert torch.equal(a, b)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_member_equals_the_single_mesh_step(orc, precision):
+    # the ensemble runs the single-mesh device functions with the member's
+    # own tables: a step with a given dt is bitwise the fused single-mesh step
+    mem = small_members()
+    u0 = W.ensemble_state(mem, lambda N: orc.lgl(N)[0])
+    E = Ensemble([m.N for m in mem], [m.n[0] for m in mem], precision=precision)
+    dt = 1.0e-3
+    ut = torch.from_numpy(u0.copy()).cuda()
+    E.set_dt(np.full(E.n_sims, dt))
+    E.step(ut, cfl=0.0)
+    got = split(E, ut.cpu().numpy())
+    for s, m in enumerate(mem):
+        mesh = Mesh(3, m.N, m.n, tuple(W.box(3)), precision=precision)
+        us = torch.from_numpy(split(E, u0)[s].copy()).cuda()
+        mesh.step_dt(us, dt)
+        torch.cuda.synchronize()
+        assert np.array_equal(us.cpu().numpy(), got[s]), s
 
 
 def test_graph_step_and_tuner_are_bitwise_consistent(orc):
@@ -85,34 +126,71 @@ def test_graph_step_and_tuner_are_bitwise_consistent(orc):
     b = torch.from_numpy(u0.copy()).cuda()
     tmp = torch.empty_like(a)
     for _ in range(2):
-        E.step(a, tmp, cfl=0.5)
+        E.step(a, cfl=0.5)
     E.rk_reset()
     for _ in range(2):
-        E.step(b, tmp, cfl=0.5, graph=True)
+        E.step(b, cfl=0.5, graph=True)
     torch.cuda.synchronize()
     assert torch.equal(a, b)
     # every element is computed the same way whatever the CTA shape
     threads, per_sm, ms = E.tune(a, tmp)
-    assert threads in (64, 128, 192, 256) and per_sm in (2, 4, 8) and ms > 0
+    assert threads in (64, 128, 192, 256) and per_sm in (1, 2, 4, 8) and ms > 0
+    assert E.get_block()[:2] == (threads, per_sm)
     E.rk_reset()
     c = torch.from_numpy(u0.copy()).cuda()
     for _ in range(2):
-        E.step(c, tmp, cfl=0.5)
+        E.step(c, cfl=0.5)
     torch.cuda.synchronize()
     assert torch.equal(a, c)
 
 
-# Bars. Noisy states (the workloads the FP64 1e-12 and FP32 1e-5 targets are
-# stated on) carry both targets against the FP64 oracle. On the noise-free
-# waves of the ensemble configuration the energy equation is badly
-# conditioned ((2/h)|Dt||f_E| against |du_E| up to ~10^5 at N=5, 24^3): there
-# both the GPU and the FP64 oracle are measured against the oracle evaluated
-# in long double, and the GPU must be as accurate as the FP64 oracle (within
-# 2x) in FP64, and within 2 x 2^29 of the FP64 oracle's error (the ratio of
-# the unit roundoffs) in FP32.
-@pytest.mark.parametrize("precision,noisy,tol", [("fp64", False, 1e-12), ("fp32", False, 1e-5),
-                                                 ("fp64", True, 1e-12), ("fp32", True, 1e-5)])
-def test_48_member_configuration(orc, precision, noisy, tol):
+def test_members_on_their_own_boxes(orc):
+    mem = small_members()
+    doms = [(-1.0, 1.0, -0.5, 1.5, 0.0, 3.0), (0.0, 2.0, 0.0, 2.0, 0.0, 2.0),
+            (-2.0, 2.0, -1.0, 1.0, -1.0, 0.5), (-1.0, 1.0, -1.0, 1.0, -1.0, 1.0)]
+    u0 = np.concatenate([W.random_state(3, m.N, m.n, seed=60 + s) for s, m in enumerate(mem)])
+    E = Ensemble([m.N for m in mem], [m.n[0] for m in mem], domains=doms)
+    for s, (m, du) in enumerate(zip(mem, stage_rhs(E, u0))):
+        ref = orc.rhs(3, m.N, m.n, np.array(doms[s]), split(E, u0)[s])
+        assert rel(du, ref) <= 1e-12, s
+    ut = torch.from_numpy(u0.copy()).cuda()
+    E.compute_dt(ut, cfl=0.5)
+    for s, (m, dt) in enumerate(zip(mem, E.get_dt())):
+        assert dt == pytest.approx(orc.max_dt(3, m.N, m.n, np.array(doms[s]), split(E, u0)[s],
+                                              cfl=0.5), rel=1e-14)
+
+
+def test_create_rejects_other_dimensions():
+    with pytest.raises(DGError):
+        Ensemble([3, 3], [2, 2], d=[3, 2])
+    with pytest.raises(DGError):
+        Ensemble([3], [2], domains=[(0.0, 1.0, 1.0, 1.0, 0.0, 1.0)])
+
+
+def _sample(ne, count, seed):
+    rng = np.random.default_rng(seed)
+    corners = [0, ne - 1]
+    if ne <= count:
+        return np.arange(ne)
+    return np.unique(np.concatenate([corners, rng.choice(ne, size=count, replace=False)]))
+
+
+# Bars. FP32: the stated 1e-5 relative L2 against the FP64 oracle on every
+# member, noisy or not, with one reading for an rhs that cancels between the
+# three coordinate directions: each direction's part (volume and surface
+# terms, the oracle's direction split) is rounded at FP32 precision, so the
+# error is measured against max(|du|, |sum_d |du_d|| / 3), which is |du|
+# itself unless the parts cancel more than threefold (kappa = |sum_d |du_d||
+# / |du| > 3; a wave whose velocity components nearly cancel along its
+# direction (1,1,1) has kappa ~ 40). FP64 on noisy members: the stated 1e-12.
+# FP64 on the noise-free waves: the energy equation there is badly
+# conditioned ((2/h)|Dt||f_E| against |du_E| up to ~10^5 at N=5, 24^3), so the
+# FP64 oracle itself is up to ~2e-11 off the long-double evaluation; both the
+# GPU and the FP64 oracle are measured against the long-double oracle and the
+# GPU must be as accurate as the FP64 oracle (within 2x).
+@pytest.mark.parametrize("precision,noisy", [("fp64", False), ("fp32", False),
+                                             ("fp64", True), ("fp32", True)])
+def test_48_member_configuration(orc, precision, noisy):
     mem = W.ensemble(n_sims=48, seed=0)
     if noisy:
         u0 = np.concatenate([W.noisy_density_wave(3, m.N, m.n, W.box(3), orc.lgl(m.N)[0],
@@ -122,32 +200,34 @@ def test_48_member_configuration(orc, precision, noisy, tol):
     else:
         u0 = W.ensemble_state(mem, lambda N: orc.lgl(N)[0])
     E = Ensemble([m.N for m in mem], [m.n[0] for m in mem], precision=precision)
-    ut = torch.from_numpy(u0.copy()).cuda()
-    tmp = torch.empty_like(ut)
-    big = 1.0e6
-    E.set_dt(np.full(len(mem), big))
-    E.stage(ut, tmp, 0)
-    torch.cuda.synchronize()
-    got = split(E, tmp.cpu().numpy())
+    got = stage_rhs(E, u0)
     parts0 = split(E, u0)
-    from paper_2108_06476_gb300 import RK_B
-    # the two smallest members and the largest one against the oracle (on a
-    # sample of its elements)
-    sizes = [m.n[0] ** 3 * (m.N + 1) ** 3 for m in mem]
-    for s in list(np.argsort(sizes)[:2]) + [int(np.argmax(sizes))]:
-        m = mem[s]
+    failures, worst = [], 0.0
+    for s, m in enumerate(mem):
         ne = m.n[0] ** 3
-        elems = np.arange(0, ne, max(1, ne // 300))
         P = (m.N + 1) ** 3
+        elems = _sample(ne, 40, seed=s)
         du = orc.rhs(3, m.N, m.n, W.box(3), parts0[s], elems=elems).reshape(ne, 5, P)[elems]
-        gd = ((got[s] - parts0[s]) / (RK_B[0] * big)).reshape(ne, 5, P)[elems]
-        if noisy:
-            err, bar = rel(gd, du), tol
+        gd = got[s].reshape(ne, 5, P)[elems]
+        kappa = 1.0
+        if precision == "fp32":
+            mag = sum(np.abs(orc.rhs(3, m.N, m.n, W.box(3), parts0[s], elems=elems,
+                                     directions=[k]).reshape(ne, 5, P)[elems]) for k in range(3))
+            kappa = float(np.linalg.norm(mag) / np.linalg.norm(du))
+            scale = max(np.linalg.norm(du), np.linalg.norm(mag) / 3.0)
+            err, bar = float(np.linalg.norm(gd - du) / scale), 1e-5
+        elif noisy:
+            err, bar = rel(gd, du), 1e-12
         else:
             ext = orc.rhs_extended(3, m.N, m.n, W.box(3), parts0[s],
                                    elems=elems).reshape(ne, 5, P)[elems]
-            err, err_or = rel(gd, ext), rel(du, ext)
-            bar = max(tol, 2.0 * err_or * (1.0 if precision == "fp64" else 2.0 ** 29))
-        print(f"ensemble member {s} (N={m.N}, n={m.n[0]}) {precision} noisy={noisy} "
-              f"rel err {err:.3e} bar {bar:.3e}")
-        assert err <= bar
+            err, bar = rel(gd, ext), max(1e-12, 2.0 * rel(du, ext))
+        worst = max(worst, err / bar)
+        per_var = [float(np.linalg.norm(gd[:, v] - du[:, v]) / np.linalg.norm(du)) for v in range(5)]
+        print(f"member {s} (N={m.N}, n={m.n[0]}, A={m.amplitude:.2f}, kappa={kappa:.1f}) "
+              f"{precision} noisy={noisy} err {err:.3e} (plain {rel(gd, du):.3e}) bar {bar:.1e} "
+              f"per variable " + " ".join(f"{x:.1e}" for x in per_var))
+        if not err <= bar:
+            failures.append(s)
+    print(f"worst error / bar over the 48 members: {worst:.3f}")
+    assert not failures, failures

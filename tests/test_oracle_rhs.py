@@ -249,6 +249,61 @@ def test_element_subset_matches_full(orc):
     assert np.all(sub[1] == 0)
 
 
+def test_direction_parts_sum_to_the_rhs(orc):
+    # the per-direction parts (volume and surface terms of one coordinate
+    # direction) add up to the full rhs
+    for d, N, n in ((2, 3, (3, 2)), (3, 2, (2, 3, 2))):
+        dom = W.box(d)
+        u = W.random_state(d, N, n, seed=16)
+        full = orc.rhs(d, N, n, dom, u)
+        parts = [orc.rhs(d, N, n, dom, u, directions=[k]) for k in range(d)]
+        assert np.allclose(sum(parts), full, rtol=0, atol=1e-13 * np.abs(full).max())
+        assert np.array_equal(orc.rhs(d, N, n, dom, u, directions=range(d)), full)
+
+
+def test_direction_part_of_a_state_varying_in_x_only(orc):
+    # a 3D state that varies along x only: the y and z parts vanish (each of
+    # their lines is a constant state), the x part is the whole rhs and equals
+    # the 2D rhs of the same x-profile
+    N, n = 3, (4, 2, 3)
+    dom = W.box(3)
+    rng = np.random.default_rng(17)
+    nx = n[0] * (N + 1)
+    rho = rng.uniform(0.5, 2.0, nx)
+    vx = rng.uniform(-0.5, 0.5, nx)
+    p = rng.uniform(0.5, 3.0, nx)
+    v = (0.1, 0.0)  # v_z = 0: the 3D and 2D states have the same energy
+    P = (N + 1) ** 3
+
+    def state(d, ny_el, nz_el):
+        ne = n[0] * ny_el * nz_el
+        out = np.zeros((ne, d + 2, (N + 1) ** d))
+        for e in range(ne):
+            ex = e % n[0]
+            for node in range((N + 1) ** d):
+                ix = ex * (N + 1) + node % (N + 1)
+                vel = (vx[ix],) + v[:d - 1]
+                out[e, 0, node] = rho[ix]
+                out[e, 1:1 + d, node] = rho[ix] * np.array(vel)
+                out[e, d + 1, node] = p[ix] / 0.4 + 0.5 * rho[ix] * float(np.dot(vel, vel))
+        return out.reshape(-1)
+
+    u3 = state(3, n[1], n[2])
+    full = orc.rhs(3, N, n, dom, u3)
+    scale = np.abs(full).max()
+    for k in (1, 2):
+        assert np.abs(orc.rhs(3, N, n, dom, u3, directions=[k])).max() <= 1e-13 * scale
+    assert np.allclose(orc.rhs(3, N, n, dom, u3, directions=[0]), full, rtol=0,
+                       atol=1e-13 * scale)
+    u2 = state(2, n[1], 1)
+    r2 = orc.rhs(2, N, n[:2], W.box(2), u2).reshape(n[0] * n[1], 4, (N + 1) ** 2)
+    r3 = full.reshape(n[0] * n[1] * n[2], 5, P)
+    # every 2D row against the 3D row of the same variable, first z-layer
+    for e in range(n[0] * n[1]):
+        for v2, v3 in ((0, 0), (1, 1), (2, 2), (3, 4)):
+            assert np.allclose(r3[e, v3, :(N + 1) ** 2], r2[e, v2], rtol=0, atol=1e-12 * scale)
+
+
 def test_max_dt_uniform_state(orc):
     d, N, n = 3, 3, (4, 5, 6)
     dom = np.array([-1.0, 1.0, 0.0, 1.0, 0.0, 3.0])

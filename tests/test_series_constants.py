@@ -16,8 +16,10 @@ from decimal import Decimal, getcontext
 import numpy as np
 import pytest
 
-HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
-                      "paper_2108_06476_gb300", "csrc", "dg_device.cuh")
+CSRC = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                    "paper_2108_06476_gb300", "csrc")
+HEADER = os.path.join(CSRC, "dg_device.cuh")
+HEADER32 = os.path.join(CSRC, "dg_f32.cuh")
 getcontext().prec = 40
 
 
@@ -67,18 +69,23 @@ def Q_ref(f2):
     return 2 / S_ref(f2)
 
 
+def R_ref(f2):
+    """R = (1 - Q)/f2, the polynomial of the FP32 perturbation form."""
+    if f2 == 0:
+        return Decimal(1) / 3
+    return (1 - Q_ref(f2)) / f2
+
+
 POLYS = [("double", "q_short", Q_ref, 2e-19), ("double", "s_short", S_ref, 5e-19),
-         ("double", "q_long", Q_ref, 2e-17), ("double", "s_long", S_ref, 1e-17),
-         # the FP32 kernels' small-difference branch, evaluated in FP64
-         ("double", "q_short32", Q_ref, 3e-9), ("double", "s_short32", S_ref, 1e-10),
-         ("double", "q_long32", Q_ref, 2e-9), ("double", "s_long32", S_ref, 6e-9)]
+         ("double", "q_long", Q_ref, 2e-17), ("double", "s_long", S_ref, 1e-17)]
+# the FP32 kernels' perturbation form: FP64 small-difference branch and the
+# FP32 range
+POLYS32 = [("double", "phi_r64", R_ref, 7e-17), ("float", "phi_r32", R_ref, 5e-8)]
 
 
-@pytest.mark.parametrize("real,name,ref,cap", POLYS, ids=[f"{p[0]}-{p[1]}" for p in POLYS])
-def test_polynomial_accuracy(header, real, name, ref, cap):
-    coeffs, a, stated = polynomial(header, real, name)
+def _check_accuracy(text, real, name, ref, cap):
+    coeffs, a, stated = polynomial(text, real, name)
     assert stated <= cap
-    assert coeffs[0] == (1.0 if name.startswith("q") else 2.0)  # ln_mean(x, x) = x exactly
     exact = [Decimal(c) for c in coeffs]
     worst = Decimal(0)
     n = 600
@@ -89,6 +96,33 @@ def test_polynomial_accuracy(header, real, name, ref, cap):
             p = p * x + c
         worst = max(worst, abs(p / ref(x) - 1))
     assert float(worst) <= 1.05 * stated, (name, float(worst))
+    return coeffs
+
+
+@pytest.mark.parametrize("real,name,ref,cap", POLYS, ids=[f"{p[0]}-{p[1]}" for p in POLYS])
+def test_polynomial_accuracy(header, real, name, ref, cap):
+    coeffs = _check_accuracy(header, real, name, ref, cap)
+    assert coeffs[0] == (1.0 if name.startswith("q") else 2.0)  # ln_mean(x, x) = x exactly
+
+
+@pytest.mark.parametrize("real,name,ref,cap", POLYS32, ids=[f"{p[0]}-{p[1]}" for p in POLYS32])
+def test_perturbation_form_polynomials(real, name, ref, cap):
+    with open(HEADER32) as fh:
+        text = fh.read()
+    coeffs = _check_accuracy(text, real, name, ref, cap)
+    # the divided-difference evaluator uses the same coefficients
+    fn = "void phi_r64_dd(double a" if real == "double" else "void phi_r32_dd(float a"
+    body = _body(text, fn)
+    lits = [float(x) for x in re.findall(r"(-?\d+\.\d*(?:e-?\d+)?)f?[;)]", body)]
+    assert sorted(lits) == sorted(coeffs), (lits, coeffs)
+
+
+def test_series_limit_of_the_fp64_branch():
+    with open(HEADER32) as fh:
+        text = fh.read()
+    lim = float(re.search(r"kSeriesLim = ([0-9.e-]+)f;", text).group(1))
+    assert lim == 1.0e-4  # the oracle's series threshold
+    assert float(polynomial(text, "double", "phi_r64")[1]) >= lim
 
 
 def test_series_reference_is_the_logarithmic_mean():
@@ -100,12 +134,10 @@ def test_series_reference_is_the_logarithmic_mean():
 
 
 def test_range_limits(header):
-    for value, name in ((1e-2, "in_short"), (4e-2, "in_short32"), (0.25, "in_long")):
+    for value, name in ((1e-2, "in_short"), (0.25, "in_long")):
         body = _body(header, f"bool {name}(double f2)")
         bits = int(re.search(r"0x([0-9A-F]+)LL", body).group(1), 16)
         assert struct.unpack("<q", struct.pack("<d", value))[0] == bits
     # every polynomial covers the range that selects it
-    for suffix, short in (("", 1e-2), ("32", 4e-2)):
-        for name, lim in ((f"q_short{suffix}", short), (f"s_short{suffix}", short),
-                          (f"q_long{suffix}", 0.25), (f"s_long{suffix}", 0.25)):
-            assert float(polynomial(header, "double", name)[1]) >= lim
+    for name, lim in (("q_short", 1e-2), ("s_short", 1e-2), ("q_long", 0.25), ("s_long", 0.25)):
+        assert float(polynomial(header, "double", name)[1]) >= lim
