@@ -378,6 +378,35 @@ def run_configs(args, timed, checks):
     return out
 
 
+def run_vjp(args, timed):
+    """dg_rhs_vjp (the hand-written vector-Jacobian product) on the VJP
+    configuration: 3D N=4, 16^3 periodic elements, noisy density wave, N(0,1)
+    cotangent; FP64 and FP32 Jacobians, 20 back-to-back calls each."""
+    import torch
+    from paper_2108_06476_gb300 import Mesh, lgl_nodes, workloads as W
+    d, N, n = 3, 4, (16, 16, 16)
+    xi, _ = lgl_nodes(N)
+    u = torch.from_numpy(W.noisy_density_wave(d, N, n, W.box(d), xi, seed=0)).cuda()
+    w = torch.from_numpy(W.gaussian(u.numel(), seed=1)).cuda()
+    out = {"workload": "VJP of the 3D Euler rhs, N=4, 16^3 periodic elements, noisy density "
+                       "wave, N(0,1) cotangent", "unit": UNIT}
+    reps = 20
+    for prec in ("fp64", "fp32"):
+        m = Mesh(d, N, n, precision=prec)
+        ub = torch.empty_like(u)
+        m.rhs_vjp(u, w, ub)
+        ms = timed(lambda: [m.rhs_vjp(u, w, ub) for _ in range(reps)])
+        du = m.empty_rhs()
+        m.rhs(u, du)
+        ms_rhs = timed(lambda: [m.rhs(u, du) for _ in range(reps)])
+        out[prec] = {"value": m.n_nodes * reps / (ms / 1e3), "ms_per_vjp": ms / reps,
+                     "vjp_over_rhs_time": ms / ms_rhs}
+        m.check()
+        del m, ub, du
+    out["nodes"] = 16 ** 3 * (N + 1) ** 3
+    return out
+
+
 def oracle_checks(line, checks, headline):
     """The baseline leg's accuracy record: the oracle's rhs on the sampled
     elements of every recorded GPU rhs (headline FP64/FP32, the configured
@@ -800,6 +829,9 @@ def run_ours(args, spec, world, rank, local):
     if not args.no_ensemble:
         ensemble = run_ensemble(args, timed, rank, checks)
 
+    # ---- VJP configuration ----
+    vjp = None if args.no_vjp else run_vjp(args, timed)
+
     # ---- the other configured cases (rates only) ----
     configs = None
     if not args.no_configs:
@@ -845,6 +877,7 @@ def run_ours(args, spec, world, rank, local):
         "rhs_only": rhs_only,
         "fp32": fp32,
         "ensemble": ensemble,
+        "vjp": vjp,
         "curved": curved,
         "mhd": mhd,
         "configs": configs,
@@ -883,6 +916,7 @@ def main():
     ap.add_argument("--mhd-elements", type=int, default=64,
                     help="MHD section: elements per dimension of the Alfven-wave mesh")
     ap.add_argument("--no-ensemble", action="store_true")
+    ap.add_argument("--no-vjp", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

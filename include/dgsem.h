@@ -352,7 +352,7 @@ int dg_ensemble_rk_reset(dg_ensemble *ens);
 /* synchronise; DG_ERR_NONPHYSICAL if a non-physical state was met,
  * DG_ERR_TIMEOUT if a stage's barrier gave up; *flags gets the bits */
 int dg_ensemble_check(dg_ensemble *ens, int *flags);
-/* CTA shape: threads per CTA (multiple of 32, at most 256) and requested
+/* CTA shape: threads per CTA (multiple of 32, at most 128) and requested
  * resident CTAs per SM (the launch takes at most what fits); elements per
  * work item follow as threads / (N+1)^2 for each degree. */
 int dg_ensemble_set_block(dg_ensemble *ens, int threads, int blocks_per_sm);

@@ -181,9 +181,11 @@ __device__ void ens_volume(const EnsArgs& a, const SimDesc& sd, const WorkItem& 
 }
 
 // one cooperative launch per stage: blocks walk the work list (largest
-// degrees first) in each phase
+// degrees first) in each phase; CTAs of at most 128 threads, at least three
+// resident per SM (at most 168 registers a thread)
+constexpr int kEnsMaxThreads = 128;
 template <typename R>
-__global__ void __launch_bounds__(256) ensemble_stage_kernel(EnsArgs a) {
+__global__ void __launch_bounds__(kEnsMaxThreads, 3) ensemble_stage_kernel(EnsArgs a) {
   extern __shared__ __align__(16) unsigned char dg_smem[];
   __shared__ Tables<R> s_tb;
   for (int it = blockIdx.x; it < a.nitems; it += gridDim.x) {
@@ -670,7 +672,7 @@ int dg_ensemble_check(dg_ensemble* E, int* flags) {
 }
 
 int dg_ensemble_set_block(dg_ensemble* E, int threads, int blocks_per_sm) {
-  if (!E || threads < 32 || threads > 256 || (threads & 31) || blocks_per_sm < 1 ||
+  if (!E || threads < 32 || threads > kEnsMaxThreads || (threads & 31) || blocks_per_sm < 1 ||
       blocks_per_sm > 32)
     return fail(DG_ERR_ARG, "dg_ensemble_set_block: bad configuration");
   for (int N = kEnsMinN; N <= kEnsMaxN; ++N)
@@ -701,8 +703,8 @@ int dg_ensemble_get_block(const dg_ensemble* E, int* threads, int* ctas_per_sm, 
 int dg_ensemble_tune(dg_ensemble* E, const double* u, double* u_tmp, int* best_threads,
                      int* best_blocks_per_sm, float* best_ms) {
   if (!E || !u || !u_tmp || u == u_tmp) return fail(DG_ERR_ARG, "dg_ensemble_tune: bad argument");
-  const int cand_t[] = {64, 128, 192, 256};  // at most the kernel's launch bound
-  const int cand_b[] = {1, 2, 4, 8};
+  const int cand_t[] = {64, 96, 128};  // at most the kernel's launch bound
+  const int cand_b[] = {1, 2, 3, 4, 6};
   float best = 1e30f;
   int bt = E->block, bb = E->per_sm;
   double* ksave = nullptr;

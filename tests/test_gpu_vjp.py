@@ -49,21 +49,57 @@ def test_vjp_equals_transposed_oracle_jacobian(orc, d, N, n, vf, sf):
     assert err <= 1e-12, err
 
 
-def test_vjp_adjoint_dot_16cubed_n4(orc):
+DIRECTIONS = 32  # the VJP configuration's number of random directions
+
+
+def vjp_config_state(xi):
     # VJP configuration: 3D N=4, 16^3 periodic elements, density wave plus 1e-2
     # noise, cotangent with i.i.d. N(0,1) entries
     d, N, n = 3, 4, (16, 16, 16)
+    u = W.noisy_density_wave(d, N, n, W.box(d), xi, seed=0)
+    return d, N, n, u, W.gaussian(u.size, seed=1)
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 1e-5)])
+def test_vjp_adjoint_dot_16cubed_n4(orc, precision, tol):
+    # <w, J v> from the oracle's exact (complex-step) JVP against <J^T w, v>
+    # from the GPU VJP, for 32 seeded directions v
+    d, N, n, u, w = vjp_config_state(orc.lgl(4)[0])
     dom = W.box(d)
-    xi, _ = orc.lgl(N)
-    u = W.noisy_density_wave(d, N, n, dom, xi, seed=0)
-    w = W.gaussian(u.size, seed=1)
-    ub = gpu_vjp(d, N, n, dom, u, w)
-    for s in range(3):
+    ub = gpu_vjp(d, N, n, dom, u, w, precision=precision)
+    worst = 0.0
+    for s in range(DIRECTIONS):
         v = W.gaussian(u.size, seed=100 + s)
         jv = orc.rhs_jvp(d, N, n, dom, u, v)
         lhs, rhs = float(w @ jv), float(ub @ v)
         scale = float(np.abs(w * jv).sum())
-        assert abs(lhs - rhs) <= 1e-12 * scale, (lhs, rhs, scale)
+        worst = max(worst, abs(lhs - rhs) / scale)
+    print(f"VJP 16^3 N=4 {precision}: worst adjoint dot gap / scale over "
+          f"{DIRECTIONS} directions {worst:.2e}")
+    assert worst <= tol
+
+
+def test_vjp_central_differences_16cubed_n4(orc):
+    # central differences of the GPU rhs with step 1e-6 along 32 seeded
+    # directions against <J^T w, v>; their O(eps^2) truncation error bounds
+    # the gap. The surface flux is the EC one, differentiable everywhere: with
+    # LLF's max/|.| kinks some face of the 2.5 M values lies within eps of a
+    # kink, where a central difference averages two one-sided derivatives
+    # (measured: a 7e-4 gap); the LLF VJP is pinned by the exact adjoint dot
+    # test above instead.
+    d, N, n, u, w = vjp_config_state(orc.lgl(4)[0])
+    m = Mesh(d, N, n, surface_flux="ranocha")
+    ut, wt = torch.from_numpy(u).cuda(), torch.from_numpy(w).cuda()
+    ub = m.rhs_vjp(ut, wt).cpu().numpy()
+    eps, worst = 1e-6, 0.0
+    for s in range(DIRECTIONS):
+        v = W.gaussian(u.size, seed=200 + s)
+        vt = torch.from_numpy(v).cuda()
+        fd = float((wt * (m.rhs(ut + eps * vt) - m.rhs(ut - eps * vt))).sum()) / (2 * eps)
+        b = float(ub @ v)
+        worst = max(worst, abs(fd - b) / abs(b))
+    print(f"VJP 16^3 N=4: worst central-difference gap over {DIRECTIONS} directions {worst:.2e}")
+    assert worst <= 1e-5
 
 
 def test_vjp_central_differences():
