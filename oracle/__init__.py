@@ -30,11 +30,13 @@ _llp = ctypes.POINTER(ctypes.c_longlong)
 
 def build(force: bool = False) -> str:
     """Compile the oracle with gcc (-O2 -ffp-contract=off, OpenMP): with
-    double, with double complex (complex-step JVP) and with long double (the
-    extended-precision evaluation used to measure FP64 rounding errors), plus
-    the curvilinear-mesh operator and the MHD operator (double)."""
+    double, with double complex (complex-step JVP), with long double (the
+    extended-precision evaluation used to measure FP64 rounding errors) and,
+    as C++, with an operation-counting scalar (the algorithmic work of the
+    method's pieces), plus the curvilinear-mesh operator and the MHD operator
+    (double)."""
     newest = max(os.path.getmtime(_SRC), os.path.getmtime(_SRC_CURVED),
-                 os.path.getmtime(_SRC_MHD))
+                 os.path.getmtime(_SRC_MHD), os.path.getmtime(os.path.join(_HERE, "op_count.hpp")))
     if not force and os.path.exists(_SO) and os.path.getmtime(_SO) >= newest:
         return _SO
     bdir = os.path.join(_HERE, "_build")
@@ -45,13 +47,19 @@ def build(force: bool = False) -> str:
     o3 = os.path.join(bdir, "or_ld.o")
     o4 = os.path.join(bdir, "or_curved.o")
     o5 = os.path.join(bdir, "or_mhd.o")
+    o6 = os.path.join(bdir, "or_count.o")
     tmp = _SO + f".tmp{os.getpid()}"
     subprocess.check_call(["gcc", *flags, "-c", _SRC, "-o", o1])
+    # the operation-counting build: the same source as C++ with a counting
+    # scalar (op_count.hpp), single-threaded
+    subprocess.check_call(["g++", "-x", "c++", "-O2", "-ffp-contract=off", "-fno-fast-math",
+                           "-fPIC", "-DOR_COUNT", "-c", _SRC, "-o", o6])
     subprocess.check_call(["gcc", *flags, "-DOR_CSTEP", "-c", _SRC, "-o", o2])
     subprocess.check_call(["gcc", *flags, "-DOR_LONGDOUBLE", "-c", _SRC, "-o", o3])
     subprocess.check_call(["gcc", *flags, "-c", _SRC_CURVED, "-o", o4])
     subprocess.check_call(["gcc", *flags, "-c", _SRC_MHD, "-o", o5])
-    subprocess.check_call(["gcc", "-shared", "-fopenmp", o1, o2, o3, o4, o5, "-o", tmp, "-lm"])
+    subprocess.check_call(["g++", "-shared", "-fopenmp", o1, o2, o3, o4, o5, o6, "-o", tmp,
+                           "-lm"])
     os.replace(tmp, _SO)
     return _SO
 
@@ -70,6 +78,13 @@ def _declare(L):
                 ctypes.c_int]
     L.or_rhs.argtypes = rhs_args + [_dp, _dp, _llp, ctypes.c_longlong, ctypes.c_int]
     L.or_set_direction_mask.argtypes = [ctypes.c_int]
+    L.orn_ops_two_point.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                    _dp, _dp]
+    L.orn_ops_two_point.restype = ctypes.c_longlong
+    L.orn_ops_cons2prim.argtypes = [ctypes.c_int, ctypes.c_double, _dp]
+    L.orn_ops_cons2prim.restype = ctypes.c_longlong
+    L.orn_ops_rhs.argtypes = rhs_args + [_dp, _llp, ctypes.c_longlong]
+    L.orn_ops_rhs.restype = ctypes.c_longlong
     L.or_rhs_jvp.argtypes = rhs_args + [_dp, _dp, _dp, _llp, ctypes.c_longlong,
                                         ctypes.c_int]
     L.orl_rhs.argtypes = rhs_args + [ctypes.c_void_p, ctypes.c_void_p, _llp,
@@ -230,6 +245,32 @@ def two_point(kind: int, d: int, n: int, uL, uR, gamma: float = 1.4):
     if lib().or_two_point(kind, d, n, gamma, _d(uL), _d(uR), _d(f)) != 0:
         raise ValueError("bad flux kind")
     return f
+
+
+def ops_two_point(kind: int, d: int, n: int, uL, uR, gamma: float = 1.4) -> int:
+    """Operations (+, -, *, /, log1p, sqrt) of one two-point flux of the
+    oracle between conserved states, including its two primitive conversions
+    (kind as two_point)."""
+    r = lib().orn_ops_two_point(kind, d, n, gamma, _d(_f64(uL)), _d(_f64(uR)))
+    if r < 0:
+        raise ValueError("orn_ops_two_point: bad arguments")
+    return int(r)
+
+
+def ops_cons2prim(d: int, u, gamma: float = 1.4) -> int:
+    """Operations of one conserved -> primitive conversion of the oracle."""
+    return int(lib().orn_ops_cons2prim(d, gamma, _d(_f64(u))))
+
+
+def ops_rhs(d, N, n, dom, u, gamma=1.4, vflux=RANOCHA, sflux=S_LLF, elems=None) -> int:
+    """Operations of the oracle's whole rhs (both orders of every pair,
+    primitives inside every flux) on the listed elements."""
+    n_arr, dom = _mesh_args(d, n, dom)
+    ep, ne, keep = _elems(elems)
+    r = lib().orn_ops_rhs(d, N, n_arr, _d(dom), gamma, vflux, sflux, _d(_f64(u)), ep, ne)
+    if r < 0:
+        raise ValueError("orn_ops_rhs: bad arguments")
+    return int(r)
 
 
 def _mesh_args(d, n, dom):

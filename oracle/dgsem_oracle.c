@@ -67,6 +67,16 @@ typedef long double real;
 #define RE(x) (x)
 #define RLOG1P(x) log1pl(x)
 #define RSQRT(x) sqrtl(x)
+#elif defined(OR_COUNT)
+/* operation-counting build (names orn_*, compiled as C++): every +, -, *, /,
+ * log1p and sqrt of real values adds one to or_op_count (op_count.hpp); the
+ * orn_ops_* entry points below report the counts of the method's pieces */
+#include "op_count.hpp"
+typedef counted real;
+#define OR(name) orn_##name
+#define RE(x) ((x).v)
+#define RLOG1P(x) counted_log1p(x)
+#define RSQRT(x) counted_sqrt(x)
 #else
 typedef double real;
 #define OR(name) or_##name
@@ -573,7 +583,51 @@ int or_rhs_jvp(int d, int N, const int *n, const double *dom, double gamma, int 
 }
 #endif
 
-#if !defined(OR_CSTEP) && !defined(OR_LONGDOUBLE)
+#ifdef OR_COUNT
+/* Operation counts of the method's pieces, from the formulas above evaluated
+ * with the counting scalar (one per +, -, *, /, log1p, sqrt). */
+long long or_op_count = 0;
+
+/* one two-point flux (kind as in or_two_point) between conserved states;
+ * includes the two conserved -> primitive conversions the flux makes */
+extern "C" long long orn_ops_two_point(int kind, int d, int n, double gamma, const double *uL,
+                                       const double *uR) {
+  real a[MAXV], b[MAXV], f[MAXV];
+  for (int v = 0; v < d + 2; ++v) { a[v] = uL[v]; b[v] = uR[v]; }
+  or_op_count = 0;
+  if (OR(two_point)(kind, d, n, gamma, a, b, f)) return -1;
+  return or_op_count;
+}
+
+/* one conserved -> primitive conversion */
+extern "C" long long orn_ops_cons2prim(int d, double gamma, const double *u) {
+  real a[MAXV], rho, v[3], p;
+  for (int k = 0; k < d + 2; ++k) a[k] = u[k];
+  or_op_count = 0;
+  cons2prim(d, gamma, a, &rho, v, &p);
+  return or_op_count;
+}
+
+/* the whole rhs of the elements listed (all when elems is NULL), as the
+ * oracle evaluates it (both orders of every pair, primitives per flux) */
+extern "C" long long orn_ops_rhs(int d, int N, const int *n, const double *dom, double gamma,
+                                 int vflux, int sflux, const double *u, const long long *elems,
+                                 long long n_elems) {
+  mesh_t m;
+  if (mesh_init(&m, d, N, n, dom)) return -1;
+  long long nv = m.nelem * m.nv * m.P;
+  real *uc = new real[nv], *dc = new real[nv];
+  for (long long t = 0; t < nv; ++t) uc[t] = u[t];
+  or_op_count = 0;
+  int rc = OR(rhs)(d, N, n, dom, gamma, vflux, sflux, uc, dc, elems, n_elems, 1);
+  long long ops = or_op_count;
+  delete[] uc;
+  delete[] dc;
+  return rc ? -1 : ops;
+}
+#endif
+
+#if !defined(OR_CSTEP) && !defined(OR_LONGDOUBLE) && !defined(OR_COUNT)
 /* One 2N-storage RK stage over nvals values: k <- a k + dt du; u <- u + b k. */
 void or_rk_stage(long long nvals, double *u, double *k, const double *du, double a, double b,
                  double dt) {
