@@ -114,6 +114,30 @@ int dg_mesh_create(int d, int N, const int *elements_per_dim, const double *doma
 int dg_mesh_create_curved(int N, const int *elements_per_dim, double warp, const dg_options *opt,
                           void *cuda_stream, dg_mesh **out);
 
+/* Replace the node coordinates of a curved mesh (dg_mesh_create_curved or
+ * dg_mesh_create_mhd_curved) by X, a device float64 array [n_elem][3][P]
+ * (per element the x, y and z coordinates of its P = (N+1)^3 nodes, node i
+ * fastest; 8-byte aligned; the caller keeps ownership), and rebuild the
+ * metric terms and Jacobians from them on the device with the same
+ * construction (nodal derivatives, conservative curl form). The elements
+ * keep their places in the periodic box: X must describe a valid mesh of
+ * the same connectivity (positive Jacobians; the periodic faces matching).
+ * Used to run the operator on coordinates computed elsewhere, e.g. by
+ * another code's mesh generator (Sec. 3.1 mesh). Asynchronous on the mesh's
+ * stream. Errors: DG_ERR_ARG (not a curved mesh, null or misaligned X),
+ * DG_ERR_CUDA. */
+int dg_mesh_set_nodes(dg_mesh *mesh, const double *X);
+
+/* Replace the metric terms and Jacobians of a curved mesh by the caller's:
+ * Ja device float64 [n_elem][3][3][P] with Ja[e][r][n][node] = (J a^r)_n (the
+ * contravariant metric vector of reference direction r, physical component
+ * n) and J device float64 [n_elem][P]; the library keeps copies and forms
+ * 1/J. For operators on geometry computed elsewhere (call after
+ * dg_mesh_set_nodes, whose coordinates the source terms use). Asynchronous
+ * on the mesh's stream. Errors: DG_ERR_ARG (not a curved mesh, null
+ * pointer), DG_ERR_CUDA. */
+int dg_mesh_set_metric(dg_mesh *mesh, const double *Ja, const double *J);
+
 /* Create a uniform periodic Cartesian mesh (as dg_mesh_create with d = 3) for
  * the 3D ideal MHD equations, u = (rho, rho v_1..3, E, B_1..3), E = p/(gamma-1)
  * + rho |v|^2/2 + |B|^2/2 (the magnetic Alfven-wave setting of Sec. 3.1; the

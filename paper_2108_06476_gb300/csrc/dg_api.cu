@@ -78,6 +78,7 @@ struct dg_mesh {
   double* Jdet;        // J per node
   double* X;           // node coordinates [e][3][P]
   dg::CTables ctab;
+  dg::CGeom cgeom;     // curved meshes: the geometry kernel's arguments
   // 3D ideal MHD meshes (dg_mesh_create_mhd)
   int mhd;
   int powell;
@@ -711,6 +712,8 @@ int dg_mesh_create_curved(int N, const int* epd, double warp, const dg_options* 
   }
   m->ctab.liftR = (double)(-1.0L / w[N]);
   m->ctab.liftL = (double)(1.0L / w[0]);
+  cg.Xin = nullptr;
+  m->cgeom = cg;
   // reference quadrature weights (the integrals multiply by J per node)
   double wq_host[512];
   for (long long node = 0; node < m->P; ++node)
@@ -725,6 +728,40 @@ int dg_mesh_create_curved(int N, const int* epd, double warp, const dg_options* 
     return rc;
   }
   *out = m;
+  return DG_OK;
+}
+
+namespace {
+__global__ void reciprocal_kernel(const double* __restrict__ J, double* __restrict__ invJ,
+                                  long long n) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    invJ[i] = 1.0 / J[i];
+}
+}  // namespace
+
+int dg_mesh_set_metric(dg_mesh* m, const double* Ja, const double* J) {
+  if (!valid_mesh(m) || !Ja || !J) return fail(DG_ERR_ARG, "dg_mesh_set_metric: null argument");
+  if (!m->curved) return fail(DG_ERR_ARG, "dg_mesh_set_metric: not a curved mesh");
+  const long long nn = m->nnodes;
+  DG_CUDA(cudaMemcpyAsync(m->Ja, Ja, 9 * nn * sizeof(double), cudaMemcpyDeviceToDevice, m->stream),
+          "dg_mesh_set_metric: copy");
+  DG_CUDA(cudaMemcpyAsync(m->Jdet, J, nn * sizeof(double), cudaMemcpyDeviceToDevice, m->stream),
+          "dg_mesh_set_metric: copy");
+  reciprocal_kernel<<<grid_for(nn, 256), 256, 0, m->stream>>>(m->Jdet, m->invJ, nn);
+  DG_CUDA(cudaGetLastError(), "dg_mesh_set_metric: launch");
+  return DG_OK;
+}
+
+int dg_mesh_set_nodes(dg_mesh* m, const double* X) {
+  if (!valid_mesh(m) || !X) return fail(DG_ERR_ARG, "dg_mesh_set_nodes: null argument");
+  if (!m->curved) return fail(DG_ERR_ARG, "dg_mesh_set_nodes: not a curved mesh");
+  if ((reinterpret_cast<uintptr_t>(X) & 7) != 0)
+    return fail(DG_ERR_ARG, "dg_mesh_set_nodes: X must be 8-byte aligned");
+  dg::CGeom cg = m->cgeom;
+  cg.Xin = X;
+  DG_CUDA(dg::curved_geometry_launch(m->N, cg, m->Ja, m->invJ, m->Jdet, m->X, m->stream),
+          "dg_mesh_set_nodes: geometry");
   return DG_OK;
 }
 

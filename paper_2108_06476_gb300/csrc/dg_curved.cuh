@@ -3,7 +3,8 @@
 // the image of the reference cube under the degree-N interpolant of the
 // warping at the LGL nodes.
 //
-//   Geometry (once per mesh): node coordinates X, a_r = dX/dxi^r by the
+//   Geometry (once per mesh, or again for node coordinates the caller
+//   gives): node coordinates X, a_r = dX/dxi^r by the
 //   nodal derivative matrix, J = a_1 . (a_2 x a_3), and the metric terms in
 //   the conservative curl form (J a^i)_n = -e_i . curl_xi(I^N(X_l grad X_m)),
 //   (n, m, l) cyclic, which satisfy sum_i d/dxi^i (J a^i)_n = 0 discretely
@@ -64,17 +65,25 @@ __global__ void curved_geometry_kernel(CGeom cg, double* __restrict__ Ja,
   const int c[3] = {t % NP, (t / NP) % NP, t / (NP * NP)};
   const int ec[3] = {(int)(e % cg.g.n[0]), (int)((e / cg.g.n[0]) % cg.g.n[1]),
                      (int)(e / ((long long)cg.g.n[0] * cg.g.n[1]))};
-  double cart[3];
+  double x, y, z;
+  if (cg.Xin) {
+    // node coordinates given by the caller
+    x = cg.Xin[(e * 3 + 0) * P + t];
+    y = cg.Xin[(e * 3 + 1) * P + t];
+    z = cg.Xin[(e * 3 + 2) * P + t];
+  } else {
+    double cart[3];
 #pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    const double h = 2.0 / cg.g.n[k];
-    cart[k] = -1.0 + (ec[k] + 0.5 * (cg.xi[c[k]] + 1.0)) * h;
+    for (int k = 0; k < 3; ++k) {
+      const double h = 2.0 / cg.g.n[k];
+      cart[k] = -1.0 + (ec[k] + 0.5 * (cg.xi[c[k]] + 1.0)) * h;
+    }
+    // the warping of the box: y first, then x (using y), then z (using x, y)
+    const double a = cg.warp;
+    y = cart[1] + a * cospi(1.5 * cart[0]) * cospi(0.5 * cart[1]) * cospi(0.5 * cart[2]);
+    x = cart[0] + a * cospi(0.5 * cart[0]) * cospi(2.0 * y) * cospi(0.5 * cart[2]);
+    z = cart[2] + a * cospi(0.5 * x) * cospi(y) * cospi(0.5 * cart[2]);
   }
-  // the warping of the box: y first, then x (using y), then z (using x, y)
-  const double a = cg.warp;
-  const double y = cart[1] + a * cospi(1.5 * cart[0]) * cospi(0.5 * cart[1]) * cospi(0.5 * cart[2]);
-  const double x = cart[0] + a * cospi(0.5 * cart[0]) * cospi(2.0 * y) * cospi(0.5 * cart[2]);
-  const double z = cart[2] + a * cospi(0.5 * x) * cospi(y) * cospi(0.5 * cart[2]);
   sX[0][t] = x;
   sX[1][t] = y;
   sX[2][t] = z;

@@ -10,6 +10,7 @@ struct CGeom {
   double warp;                       // amplitude of the warping (0.15 in the paper)
   double xi[kNPMax];                 // LGL nodes
   double D[kNPMax][kNPMax];          // nodal derivative matrix
+  const double* Xin;                 // given node coordinates [e][3][P] (nullptr: the warp)
 };
 
 // split form with the sign of du folded in: Ds = -Dt, liftR = -1/w_N,

@@ -266,6 +266,202 @@ __device__ __forceinline__ void volume_batch(double* u, R* __restrict__ du,
   }
 }
 
+// ---- pair-parallel volume kernel for tiny meshes (FP64) ----
+// One element per CTA, one thread per (direction, line, node pair): every
+// pair flux is evaluated by its own thread (the line-owning kernel walks a
+// line's N(N+1)/2 pairs in one thread, and on a mesh of a few hundred
+// elements each SM holds one or two of those threads' warps, every FP64
+// instruction occupying the sub-partition's FP64 unit for the whole warp).
+// The fluxes go to shared memory; then one thread per (direction, node) sums
+// its pairs in the line-owning kernel's order (the other node's index
+// ascending, then the lifting), and the directions are added in order, so the
+// result is bitwise that of volume_kernel.
+template <int D, int N>
+struct PairPar {
+  static constexpr int NP = N + 1, P = Shape<D, N>::P, LINES = Shape<D, N>::LINES,
+                       NV = D + 2, NC = 3 + 2 * D;
+  static constexpr int NPAIRS = N * (N + 1) / 2;
+  // all directions at once when their pair fluxes fit in 96 KB
+  static constexpr bool ALLDIRS = D * LINES * NPAIRS * NV * 8 <= 98304;
+  static constexpr int GROUP = ALLDIRS ? D : 1;  // directions per phase
+  static constexpr int WORK = GROUP * LINES * NPAIRS;
+  static constexpr int THREADS = WORK < 512 ? ((WORK + 31) / 32) * 32 : 512;
+  static constexpr int SMEM = (NC + NV + GROUP * NV) * P * 8 + WORK * NV * 8;
+};
+
+template <int N>
+__device__ __forceinline__ void pp_pair_of(int p, int& a, int& b) {
+  a = 0;
+  while (p >= N - a) {
+    p -= N - a;
+    ++a;
+  }
+  b = a + 1 + p;
+}
+
+template <int N>
+__device__ __forceinline__ int pp_pair_index(int a, int b) {  // a < b
+  return a * N - a * (a - 1) / 2 + (b - a - 1);
+}
+
+// line l and position i of a node along direction dir (inverse of line_node)
+template <int D, int N>
+__device__ __forceinline__ void pp_line_of(int dir, int node, int& l, int& i) {
+  constexpr int NP = N + 1;
+  if (dir == 0) {
+    l = node / NP;
+    i = node % NP;
+  } else if (dir == 1) {
+    i = (node / NP) % NP;
+    l = (D == 2) ? node % NP : node % NP + NP * (node / (NP * NP));
+  } else {
+    i = node / (NP * NP);
+    l = node % (NP * NP);
+  }
+}
+
+template <int D, int N, int VF>
+__global__ void __launch_bounds__(PairPar<D, N>::THREADS)
+    volume_pp_kernel(double* u, double* __restrict__ du, const double* __restrict__ fs, Geom g,
+                     Tables<double> tb, unsigned* __restrict__ err, StageFuse fz) {
+  using C = PairPar<D, N>;
+  constexpr int NP = C::NP, P = C::P, NV = C::NV, NC = C::NC, LINES = C::LINES,
+                NPAIRS = C::NPAIRS, GROUP = C::GROUP;
+  extern __shared__ __align__(16) unsigned char dg_smem[];
+  double(*sp)[P] = reinterpret_cast<double(*)[P]>(dg_smem);                          // [NC][P]
+  double(*sa)[P] = reinterpret_cast<double(*)[P]>(dg_smem + 8 * NC * P);             // [NV][P]
+  double(*sd)[NV][P] = reinterpret_cast<double(*)[NV][P]>(dg_smem + 8 * (NC + NV) * P);
+  double* sf = reinterpret_cast<double*>(dg_smem + 8 * (NC + NV + GROUP * NV) * P);  // [WORK][NV]
+  const int e = blockIdx.x;
+  const int nelem = (int)g.nelem;
+  __shared__ int s_left[3];
+  if (threadIdx.x < D) s_left[threadIdx.x] = neighbour32(g, e, threadIdx.x, -1);
+  unsigned bad = 0;
+  for (int node = threadIdx.x; node < P; node += blockDim.x) {
+    double c[NV], rr;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) c[v] = u[((long long)e * NV + v) * P + node];
+    const Prim<double, D> q = prim_rcp<D>(c, g.gm1, rr);
+    bad |= prim_check(q);
+    node_slots<VF, double>(q.rho, q.p, g.gm1, sp[0][node], sp[1][node]);
+    sp[2][node] = 0.5 * q.p;
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      sp[3 + k][node] = q.v[k];
+      sp[3 + D + k][node] = 0.5 * q.v[k];
+    }
+#pragma unroll
+    for (int v = 0; v < NV; ++v) sa[v][node] = 0.0;
+  }
+  if (bad) atomicOr(err, bad);
+  __syncthreads();
+  const long long base = (long long)nelem * LINES;
+  const double gm1inv = g.gm1inv;
+#pragma unroll 1
+  for (int d0 = 0; d0 < D; d0 += GROUP) {
+    // pair fluxes of the group's directions, normal-first
+    for (int w = threadIdx.x; w < C::WORK; w += blockDim.x) {
+      const int dir = d0 + w / (LINES * NPAIRS);
+      const int rem = w % (LINES * NPAIRS);
+      const int l = rem / NPAIRS;
+      int a, b;
+      pp_pair_of<N>(rem % NPAIRS, a, b);
+      const int na = line_node_rt<D, N>(dir, l, a), nb = line_node_rt<D, N>(dir, l, b);
+      const int t1 = (dir + 1) % D, t2 = (dir + 2) % D;
+      LinePrim<double, D> qa, qb;
+      qa.s0 = sp[0][na];
+      qa.s1 = sp[1][na];
+      qa.hp = sp[2][na];
+      qa.vn = sp[3 + dir][na];
+      qa.hvn = sp[3 + D + dir][na];
+      qa.vt[0] = sp[3 + t1][na];
+      qa.hvt[0] = sp[3 + D + t1][na];
+      qb.s0 = sp[0][nb];
+      qb.s1 = sp[1][nb];
+      qb.hp = sp[2][nb];
+      qb.vn = sp[3 + dir][nb];
+      qb.hvn = sp[3 + D + dir][nb];
+      qb.vt[0] = sp[3 + t1][nb];
+      qb.hvt[0] = sp[3 + D + t1][nb];
+      if (D == 3) {
+        qa.vt[D - 2] = sp[3 + t2][na];
+        qa.hvt[D - 2] = sp[3 + D + t2][na];
+        qb.vt[D - 2] = sp[3 + t2][nb];
+        qb.hvt[D - 2] = sp[3 + D + t2][nb];
+      }
+      double f[NV], an = 0.0;
+      if (VF == kVRanocha) ranocha_nf<double, D>(qa, qb, f, an);
+      else generic_nf<VF, double, D>(qa, qb, gm1inv, f);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) sf[w * NV + v] = f[v];
+    }
+    __syncthreads();
+    // per (direction, node): the line sum in the line-owning order, then the
+    // lifting (normal-first components back to variables)
+    for (int t = threadIdx.x; t < GROUP * P; t += blockDim.x) {
+      const int gd = t / P, node = t % P, dir = d0 + gd;
+      const int t1 = (dir + 1) % D, t2 = (dir + 2) % D;
+      int l, i;
+      pp_line_of<D, N>(dir, node, l, i);
+      double acc[NV];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) acc[v] = 0.0;
+      for (int j = 0; j < NP; ++j) {
+        if (j == i) continue;
+        const int p = j < i ? pp_pair_index<N>(j, i) : pp_pair_index<N>(i, j);
+        const double dij = tb.Ds[dir][i][j];
+        const double* fp = sf + ((gd * LINES + l) * NPAIRS + p) * NV;
+#pragma unroll
+        for (int v = 0; v < NV; ++v) acc[v] = fma(dij, fp[v], acc[v]);
+      }
+      int comp[NV];
+      comp[0] = 0;
+      comp[1] = 1 + dir;
+      comp[2] = 1 + t1;
+      if (D == 3) comp[D] = 1 + t2;
+      comp[D + 1] = D + 1;
+      if (i == N) {
+#pragma unroll
+        for (int c = 0; c < NV; ++c)
+          acc[c] = fma(tb.liftR[dir], fs[(long long)(dir * NV + comp[c]) * base + (long long)e * LINES + l],
+                       acc[c]);
+      }
+      if (i == 0) {
+#pragma unroll
+        for (int c = 0; c < NV; ++c)
+          acc[c] = fma(tb.liftL[dir],
+                       fs[(long long)(dir * NV + comp[c]) * base + (long long)s_left[dir] * LINES + l],
+                       acc[c]);
+      }
+#pragma unroll
+      for (int c = 0; c < NV; ++c) sd[gd][comp[c]][node] = acc[c];
+    }
+    __syncthreads();
+    // the directions added in order, as the line-owning kernel does
+    for (int t = threadIdx.x; t < NV * P; t += blockDim.x) {
+      const int v = t / P, node = t % P;
+#pragma unroll
+      for (int gd = 0; gd < GROUP; ++gd) sa[v][node] += sd[gd][v][node];
+    }
+    __syncthreads();
+  }
+  const double dtv = fz.k ? *fz.dt : 0.0;
+  double* const uo = fz.u_out ? fz.u_out : u;
+  for (int t = threadIdx.x; t < NV * P; t += blockDim.x) {
+    const int v = t / P, node = t % P;
+    const double val = sa[v][node];
+    const long long i = ((long long)e * NV + v) * P + node;
+    if (fz.k) {
+      double kk = dtv * val;
+      if (fz.a != 0.0) kk = fma(fz.a, fz.k[i], kk);
+      fz.k[i] = kk;
+      uo[i] = u[i] + fz.b * kk;
+    } else {
+      du[i] = val;
+    }
+  }
+}
+
 template <int D, int N, typename R, int VF, int EPB>
 __global__ void __launch_bounds__(EPB* Shape<D, N>::LINES)
     volume_kernel(double* u, R* __restrict__ du, const R* __restrict__ fs, Geom g, Tables<R> tb,
@@ -494,6 +690,32 @@ cudaError_t launch_volume_epb(const double* u, R* du, R* fs, const Geom& g, cons
   return cudaGetLastError();
 }
 
+// meshes of fewer elements than this run the pair-parallel FP64 volume kernel
+constexpr long long kPairParallelElems = 4 * 152;
+
+template <int D, int N>
+cudaError_t launch_volume_pp(const double* u, double* du, double* fs, const Geom& g,
+                             const Tables<double>& tb, int vf, unsigned* err, cudaStream_t st,
+                             const StageFuse& fz) {
+  using C = PairPar<D, N>;
+  cudaError_t e;
+  const unsigned grid = (unsigned)g.nelem;
+  if (vf == kVRanocha) {
+    if ((e = allow_smem(volume_pp_kernel<D, N, kVRanocha>, C::SMEM)) != cudaSuccess) return e;
+    volume_pp_kernel<D, N, kVRanocha><<<grid, C::THREADS, C::SMEM, st>>>(
+        const_cast<double*>(u), du, fs, g, tb, err, fz);
+  } else if (vf == kVChandrashekar) {
+    if ((e = allow_smem(volume_pp_kernel<D, N, kVChandrashekar>, C::SMEM)) != cudaSuccess) return e;
+    volume_pp_kernel<D, N, kVChandrashekar><<<grid, C::THREADS, C::SMEM, st>>>(
+        const_cast<double*>(u), du, fs, g, tb, err, fz);
+  } else {
+    if ((e = allow_smem(volume_pp_kernel<D, N, kVCentral>, C::SMEM)) != cudaSuccess) return e;
+    volume_pp_kernel<D, N, kVCentral><<<grid, C::THREADS, C::SMEM, st>>>(
+        const_cast<double*>(u), du, fs, g, tb, err, fz);
+  }
+  return cudaGetLastError();
+}
+
 // FP32 kernels: elements per CTA as for FP64 (about 128 threads, dynamic
 // shared memory <= 96 KB)
 template <int D, int N>
@@ -575,6 +797,8 @@ cudaError_t launch_rhs_dn(const double* u, R* du, R* fs, const Geom& g, const Ta
   } else {
     using L = Launch<D, N, R>;
     constexpr int EPB = L::EPB;
+    if (g.nelem < kPairParallelElems)
+      return launch_volume_pp<D, N>(u, du, fs, g, tb, vf, err, st, fz);
     if (EPB > 1 && g.nelem < 2LL * 152 * EPB)
       return launch_volume_epb<D, N, R, 1>(u, du, fs, g, tb, vf, err, st, fz);
     return launch_volume_epb<D, N, R, EPB>(u, du, fs, g, tb, vf, err, st, fz);

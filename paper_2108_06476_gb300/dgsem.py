@@ -38,7 +38,7 @@ EXPORTS = ("dg_mesh_create", "dg_mesh_create_curved", "dg_mesh_create_mhd",
            "dg_ensemble_stage", "dg_ensemble_step", "dg_ensemble_step_graph",
            "dg_ensemble_rk_reset", "dg_ensemble_check", "dg_ensemble_set_block",
            "dg_ensemble_get_block", "dg_ensemble_tune", "dg_measure_peaks",
-           "dg_selftest_arith")
+           "dg_selftest_arith", "dg_mesh_set_nodes", "dg_mesh_set_metric")
 
 
 class DGError(RuntimeError):
@@ -110,6 +110,8 @@ def load(path: str = SO_PATH):
     L.dg_ensemble_get_block.argtypes = [vp, ip, ip, ip]
     L.dg_measure_peaks.argtypes = [dp, dp, ip, vp]
     L.dg_selftest_arith.argtypes = [ctypes.c_int, vp, vp, ctypes.c_longlong, vp]
+    L.dg_mesh_set_nodes.argtypes = [vp, vp]
+    L.dg_mesh_set_metric.argtypes = [vp, vp, vp]
     L.dg_ensemble_tune.argtypes = [vp, vp, vp, ip, ip, ctypes.POINTER(ctypes.c_float)]
     L.dg_last_error.restype = ctypes.c_char_p
     L.dg_last_error.argtypes = []
@@ -324,6 +326,29 @@ class Mesh:
         self._sync_stream()
         fn = load().dg_step_graph if graph else load().dg_step_cfl
         _check(fn(self._h, _ptr(u), float(cfl)), "dg_step_cfl")
+
+    def set_nodes(self, X):
+        """Curved meshes: take the node coordinates X (float64 CUDA tensor of
+        n_elem x 3 x (N+1)^3, contiguous) and rebuild the metric terms."""
+        t = self._torch
+        P = (self.N + 1) ** 3
+        if not (X.is_cuda and X.dtype == t.float64 and X.is_contiguous()
+                and X.numel() == 3 * P * (self.n_nodes // P)):
+            raise DGError("node coordinates must be a contiguous float64 CUDA tensor "
+                          "of n_elem x 3 x (N+1)^3")
+        self._sync_stream()
+        _check(load().dg_mesh_set_nodes(self._h, _ptr(X)), "dg_mesh_set_nodes")
+
+    def set_metric(self, Ja, J):
+        """Curved meshes: take the metric terms Ja (n_elem x 3 x 3 x (N+1)^3)
+        and Jacobians J (n_elem x (N+1)^3), float64 CUDA tensors."""
+        t = self._torch
+        for a, k in ((Ja, 9), (J, 1)):
+            if not (a.is_cuda and a.dtype == t.float64 and a.is_contiguous()
+                    and a.numel() == k * self.n_nodes):
+                raise DGError("metric terms must be contiguous float64 CUDA tensors")
+        self._sync_stream()
+        _check(load().dg_mesh_set_metric(self._h, _ptr(Ja), _ptr(J)), "dg_mesh_set_metric")
 
     def set_source(self, kind):
         """Source terms on a curved mesh: "none" or "manufactured"."""

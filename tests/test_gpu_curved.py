@@ -66,6 +66,78 @@ def test_curved_rhs_every_degree(N):
     assert rel(gpu_rhs(N, n, u), ref) <= geometry_tol(g, u)
 
 
+def gpu_rhs_on_oracle_nodes(g, u, vf=0, sf=0, source=False, t=0.0, metric=False):
+    """The GPU operator with its metric terms built from the oracle's node
+    coordinates (dg_mesh_set_nodes): both sides start from the same X; with
+    metric, the oracle's metric terms and Jacobians too (dg_mesh_set_metric)."""
+    m = Mesh(3, g.N, g.n, warp=g.warp, volume_flux=VF[vf], surface_flux=SF[sf])
+    m.set_nodes(torch.from_numpy(np.ascontiguousarray(g.X)).cuda())
+    if metric:
+        m.set_metric(torch.from_numpy(np.ascontiguousarray(g.Ja)).cuda(),
+                     torch.from_numpy(np.ascontiguousarray(g.J)).cuda())
+    if source:
+        m.set_source("manufactured")
+        m.set_time(t)
+    out = m.rhs(torch.from_numpy(u).cuda())
+    assert m.check() == 0
+    return out.cpu().numpy()
+
+
+@pytest.mark.parametrize("N", range(1, 8))
+def test_curved_rhs_on_the_oracle_nodes_every_degree(N):
+    # the same node coordinates on both sides: the plain 1e-12 bar for
+    # N <= 6. At N = 7 (2 x 2 x 1 strongly warped elements) the two
+    # independent curl-form metric constructions (derivative matrices rounded
+    # from different formulas, different summation orders) still leave 1.2e-12:
+    # there the bar is the oracle's own sensitivity to one-ulp geometry
+    # changes, and the next test shows that with the oracle's metric terms as
+    # well the operators agree to the plain bar at every degree.
+    n = (3, 2, 2) if N < 6 else (2, 2, 1)
+    g = orc.CurvedGeometry(N, n, 0.15)
+    u = noisy_warped_state(N, n, seed=N)
+    err = rel(gpu_rhs_on_oracle_nodes(g, u), orc.curved_rhs(g, u))
+    print(f"curved N={N} on the oracle's nodes: rel L2 {err:.2e}")
+    assert err <= (TOL if N <= 6 else geometry_tol(g, u))
+
+
+@pytest.mark.parametrize("N", range(1, 8))
+def test_curved_rhs_on_the_oracle_geometry_every_degree(N):
+    # the oracle's node coordinates, metric terms and Jacobians: the two
+    # sides evaluate the same discrete operator, plain 1e-12 bar
+    n = (3, 2, 2) if N < 6 else (2, 2, 1)
+    g = orc.CurvedGeometry(N, n, 0.15)
+    u = noisy_warped_state(N, n, seed=N)
+    err = rel(gpu_rhs_on_oracle_nodes(g, u, metric=True), orc.curved_rhs(g, u))
+    print(f"curved N={N} on the oracle's geometry: rel L2 {err:.2e}")
+    assert err <= TOL
+
+
+@pytest.mark.parametrize("vf,sf", [(0, 1), (1, 3), (2, 2)])
+def test_curved_rhs_on_the_oracle_nodes_fluxes_and_source(vf, sf):
+    N, n = 4, (2, 3, 2)
+    g = orc.CurvedGeometry(N, n, 0.15)
+    u = noisy_warped_state(N, n, seed=20 + vf)
+    assert rel(gpu_rhs_on_oracle_nodes(g, u, vf, sf),
+               orc.curved_rhs(g, u, vflux=vf, sflux=sf)) <= TOL
+    ref = orc.curved_rhs(g, u, source=True, t=0.3)
+    assert rel(gpu_rhs_on_oracle_nodes(g, u, source=True, t=0.3), ref) <= TOL
+
+
+def test_set_nodes_with_the_mesh_own_coordinates_changes_nothing():
+    # the GPU's own warped coordinates passed back give the same operator
+    N, n = 3, (2, 2, 2)
+    xi, _ = orc.lgl(N)
+    X = W.warped_node_coordinates(N, n, xi, 0.15)  # (3, ne, P)
+    u = noisy_warped_state(N, n, seed=5)
+    a = gpu_rhs(N, n, u)
+    m = Mesh(3, N, n, warp=0.15)
+    m.set_nodes(torch.from_numpy(np.ascontiguousarray(X.transpose(1, 0, 2))).cuda())
+    b = m.rhs(torch.from_numpy(u).cuda()).cpu().numpy()
+    assert rel(b, a) <= 1e-12
+    with pytest.raises(DGError):
+        Mesh(3, N, n).set_nodes(torch.zeros(8 * 3 * 64, dtype=torch.float64, device="cuda"))
+
+
 @pytest.mark.parametrize("vf", [0, 1, 2])
 @pytest.mark.parametrize("sf", [0, 1, 2, 3])
 def test_curved_rhs_every_flux(vf, sf):

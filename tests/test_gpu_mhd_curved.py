@@ -62,6 +62,22 @@ def test_mhd_curved_rhs_every_degree(N, vflux, sflux):
     assert rel(got, ref) <= tol, (rel(got, ref), tol)
 
 
+@pytest.mark.parametrize("vflux,sflux", [("central", "hll"), ("ec", "ec")])
+@pytest.mark.parametrize("N", range(1, 8))
+def test_mhd_curved_rhs_on_the_oracle_nodes(N, vflux, sflux):
+    # the metric terms built from the oracle's node coordinates: the plain
+    # 1e-12 bar
+    n = (3, 2, 2) if N < 6 else (2, 2, 1)
+    g = orc.CurvedGeometry(N, n, WARP)
+    u = state(N, n, seed=70 + N)
+    ref = orc.mhd_curved_rhs(g, u, G, True, vflux=vflux, sflux=sflux)
+    m = mesh(N, n, vflux, sflux)
+    m.set_nodes(torch.from_numpy(np.ascontiguousarray(g.X)).cuda())
+    got = m.rhs(torch.from_numpy(u).cuda()).cpu().numpy()
+    assert m.check() == 0
+    assert rel(got, ref) <= TOL, rel(got, ref)
+
+
 @pytest.mark.parametrize("vflux,sflux,powell", [("central", "llf", True), ("ec", "llf", True),
                                                 ("central", "hll", False)])
 def test_mhd_curved_rhs_other_flux_pairs(vflux, sflux, powell):
