@@ -78,13 +78,14 @@ def _declare(L):
                 ctypes.c_int]
     L.or_rhs.argtypes = rhs_args + [_dp, _dp, _llp, ctypes.c_longlong, ctypes.c_int]
     L.or_set_direction_mask.argtypes = [ctypes.c_int]
-    L.orn_ops_two_point.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
-                                    _dp, _dp]
-    L.orn_ops_two_point.restype = ctypes.c_longlong
-    L.orn_ops_cons2prim.argtypes = [ctypes.c_int, ctypes.c_double, _dp]
-    L.orn_ops_cons2prim.restype = ctypes.c_longlong
-    L.orn_ops_rhs.argtypes = rhs_args + [_dp, _llp, ctypes.c_longlong]
-    L.orn_ops_rhs.restype = ctypes.c_longlong
+    if hasattr(L, "orn_ops_two_point"):  # the counting build (not in planted-mistake variants)
+        L.orn_ops_two_point.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                        ctypes.c_double, _dp, _dp]
+        L.orn_ops_two_point.restype = ctypes.c_longlong
+        L.orn_ops_cons2prim.argtypes = [ctypes.c_int, ctypes.c_double, _dp]
+        L.orn_ops_cons2prim.restype = ctypes.c_longlong
+        L.orn_ops_rhs.argtypes = rhs_args + [_dp, _llp, ctypes.c_longlong]
+        L.orn_ops_rhs.restype = ctypes.c_longlong
     L.or_rhs_jvp.argtypes = rhs_args + [_dp, _dp, _dp, _llp, ctypes.c_longlong,
                                         ctypes.c_int]
     L.orl_rhs.argtypes = rhs_args + [ctypes.c_void_p, ctypes.c_void_p, _llp,
