@@ -14,6 +14,7 @@
 #include "dg_curved_decl.cuh"
 #include "dg_mhd_decl.cuh"
 #include "dg_device.cuh"
+#include "dg_f32.cuh"
 
 namespace dg {
 cudaError_t rhs_launch_double_2(int, const double*, double*, double*, const Geom&,
@@ -256,21 +257,23 @@ __device__ __forceinline__ void speed_node(const double* c, int D, const Geom& g
     for (int k = 0; k < 3; ++k) lam[k] = fmax(lam[k], fabs(q.v[k]) + cs);
   }
 }
-__device__ __forceinline__ void speed_node(const double* c, int D, const Geom& g, double* lam,
+// (FP32: the maxima stay in float and the state is converted on the integer
+// pipe, d2f, so that no FP64-pipe instruction runs per node)
+__device__ __forceinline__ void speed_node(const double* c, int D, const Geom& g, float* lam,
                                            unsigned& bad, float) {
-  const float rho = (float)c[0];
+  const float rho = dg::d2f(c[0]);
   const float rr = 1.0f / rho;
   float v[3], v2 = 0.0f;
   for (int k = 0; k < D; ++k) {
-    v[k] = (float)c[1 + k] * rr;
+    v[k] = dg::d2f(c[1 + k]) * rr;
     v2 = fmaf(v[k], v[k], v2);
   }
-  const float p = (float)g.gm1 * ((float)c[D + 1] - 0.5f * rho * v2);
+  const float p = (float)g.gm1 * (dg::d2f(c[D + 1]) - 0.5f * rho * v2);
   if (!(rho > 0.0f)) bad |= dg::kErrRho;
   if (!(p > 0.0f)) bad |= dg::kErrP;
   if (!isfinite(rho) || !isfinite(p)) bad |= dg::kErrNaN;
   const float cs = sqrtf((float)g.gamma * p * rr);
-  for (int k = 0; k < D; ++k) lam[k] = fmax(lam[k], (double)(fabsf(v[k]) + cs));
+  for (int k = 0; k < D; ++k) lam[k] = fmaxf(lam[k], fabsf(v[k]) + cs);
 }
 
 // copy_to (optional) receives a copy of u: the host-state step reads a
@@ -286,7 +289,7 @@ __global__ void speed_kernel(const double* __restrict__ u, Geom g, int P, double
   double best = 0.0;
   unsigned bad = 0;
   for (long long e = warp; e < g.nelem; e += nwarps) {
-    double lam[3] = {0.0, 0.0, 0.0};
+    R lamr[3] = {R(0), R(0), R(0)};
     for (int node = lane; node < P; node += 32) {
       double c[NV];
 #pragma unroll
@@ -295,12 +298,15 @@ __global__ void speed_kernel(const double* __restrict__ u, Geom g, int P, double
 #pragma unroll
         for (int v = 0; v < NV; ++v) copy_to[(e * NV + v) * P + node] = c[v];
       }
-      speed_node(c, D, g, lam, bad, R(0));
+      speed_node(c, D, g, lamr, bad, R(0));
     }
+    double lam[3];
 #pragma unroll
-    for (int k = 0; k < D; ++k)
+    for (int k = 0; k < D; ++k) {
+      lam[k] = (double)lamr[k];
       for (int off = 16; off > 0; off >>= 1)
         lam[k] = fmax(lam[k], __shfl_xor_sync(0xffffffffu, lam[k], off));
+    }
     double s = s0 * lam[0];
     s = s + s1 * lam[1];
     if (D == 3) s = s + s2 * lam[2];
