@@ -352,6 +352,27 @@ def _sample_elements(nelem, count, seed):
                                                                   replace=False)]))
 
 
+def graph_ms(fn, timed):
+    """Record fn (library calls on the current stream) as one CUDA graph and
+    time a replay; None if the capture is refused."""
+    import torch
+    stream = torch.cuda.Stream()
+    stream.wait_stream(torch.cuda.current_stream())
+    try:
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.stream(stream):
+            fn()  # warm-up on the capture stream
+            torch.cuda.synchronize()
+            with torch.cuda.graph(g, stream=stream, capture_error_mode="thread_local"):
+                fn()
+        torch.cuda.synchronize()
+        g.replay()
+        torch.cuda.synchronize()
+        return timed(lambda: g.replay())
+    except RuntimeError:
+        return None
+
+
 def run_configs(args, timed, checks):
     """rhs-only rates (50 back-to-back dg_rhs calls, FP64 and FP32 kernels)
     and the fused-step rate (FP64, CUDA-graph CFL steps) of the other
@@ -380,6 +401,11 @@ def run_configs(args, timed, checks):
                           .cpu().numpy().reshape(-1, nv, P)[elems])))
             ms = timed(lambda: [m.rhs(u0, du) for _ in range(50)])
             row[f"rhs_{prec}"] = row["nodes"] * 50 / (ms / 1e3)
+            # the same 50 calls recorded once as a CUDA graph and replayed:
+            # the kernels' rate without the host's per-call cost (small meshes)
+            ms_g = graph_ms(lambda: [m.rhs(u0, du) for _ in range(50)], timed)
+            if ms_g is not None:
+                row[f"rhs_{prec}_graph"] = row["nodes"] * 50 / (ms_g / 1e3)
             if prec == "fp64":
                 u = u0.clone()
                 for _ in range(3):

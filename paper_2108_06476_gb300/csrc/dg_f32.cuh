@@ -152,9 +152,12 @@ struct DNode {
 
 // FP64 state of one node -> FP32 deviations from the reference (rho0, v0,
 // p0; E0 = p0/(gamma-1) + rho0 |v0|^2/2 in FP64), natural variable order.
+// dm (optional) receives m - rho v0 and dEo E - E0 (the face kernels form
+// the jumps of the conserved variables from them).
 template <int D>
 __device__ __forceinline__ void delta_node(const double* c, float rho0, const float* v0, double E0,
-                                           float gm1f, DNode<D>& q) {
+                                           float gm1f, DNode<D>& q, float* dm = nullptr,
+                                           float* dEo = nullptr) {
   q.drho = d2f(c[0] - f2d(rho0));
   q.rho = rho0 + q.drho;
   const float rr = rcp(q.rho);
@@ -162,12 +165,14 @@ __device__ __forceinline__ void delta_node(const double* c, float rho0, const fl
 #pragma unroll
   for (int k = 0; k < D; ++k) {
     const float dmk = d2f(fma(-c[0], f2d(v0[k]), c[1 + k]));  // m - rho v0
+    if (dm) dm[k] = dmk;
     q.dv[k] = dmk * rr;
     q.v[k] = v0[k] + q.dv[k];
     v2 = fmaf(q.v[k], q.v[k], v2);
     dvv = fmaf(q.dv[k], q.v[k] + v0[k], dvv);
   }
   const float dE = d2f(c[D + 1] - E0);
+  if (dEo) *dEo = dE;
   q.dp = gm1f * fmaf(-0.5f, fmaf(q.drho, v2, rho0 * dvv), dE);
 }
 

@@ -288,20 +288,21 @@ __device__ __forceinline__ void face_flux32(const double* __restrict__ u, float*
   load_ref<D>(ref, e, rho0, v0, p0);
   const double E0 = refE[e];
   DNode<D> L, R;
-  delta_node<D>(cl, rho0, v0, E0, gm1f, L);
-  delta_node<D>(cr, rho0, v0, E0, gm1f, R);
-  // jumps u_R - u_L, normal-first, for the dissipative fluxes: FP64
-  // differences of the traces rounded once (a difference of the two rounded
-  // deviations would leave a spurious jump of one FP32 ulp of the deviation
-  // where the state is continuous, multiplied by the sound speed)
+  float dmL[D], dmR[D], dEL, dER;
+  delta_node<D>(cl, rho0, v0, E0, gm1f, L, dmL, &dEL);
+  delta_node<D>(cr, rho0, v0, E0, gm1f, R, dmR, &dER);
+  // jumps u_R - u_L, normal-first, for the dissipative fluxes, from the two
+  // traces' deviations from the same reference: [rho] = [drho], [m] = [dm] +
+  // v0 [drho], [E] = [dE]. Each deviation is one FP64 difference rounded once
+  // to FP32, so traces equal to ~1e-16 (a continuous state) round alike unless
+  // an FP32 rounding boundary falls between them, about once in 1e8 face
+  // nodes, and then by one FP32 ulp of the deviation.
   float dq[NV];
-  if (sf == kSLLF || sf == kSHLL) {
-    dq[0] = d2f(cr[0] - cl[0]);
-    dq[1] = d2f(cr[1 + dir] - cl[1 + dir]);
-    dq[2] = d2f(cr[1 + t1] - cl[1 + t1]);
-    if (D == 3) dq[D] = d2f(cr[1 + t2] - cl[1 + t2]);
-    dq[D + 1] = d2f(cr[D + 1] - cl[D + 1]);
-  }
+  dq[0] = R.drho - L.drho;
+  dq[1] = fmaf(v0[dir], dq[0], dmR[dir] - dmL[dir]);
+  dq[2] = fmaf(v0[t1], dq[0], dmR[t1] - dmL[t1]);
+  if (D == 3) dq[D] = fmaf(v0[t2], dq[0], dmR[t2] - dmL[t2]);
+  dq[D + 1] = dER - dEL;
   const DRef<D> rf = dir_ref<D>(rho0, v0, p0, dir);
   float f[NV];
   delta_surface_flux<D>(sf, to_normal_first<D>(L, dir), to_normal_first<D>(R, dir), rf, dq,
