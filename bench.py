@@ -338,6 +338,19 @@ def run_ensemble(args, timed, rank, checks):
                      "tuned_ctas_per_sm": per_sm, "ctas_launched": grid,
                      "tuned_stage_ms": stage_ms,
                      "stage_launches_per_step": 5}
+        # the step's algorithmic work: every member's nodes x the operations
+        # per node of its degree (oracle operation counts) x 5 stages
+        per_n = {N: counted_ops(f"ensemble_member_n{N}") for N in (3, 4, 5)}
+        if all(per_n.values()):
+            ops = 5 * sum(m.n[0] ** 3 * (m.N + 1) ** 3 * per_n[m.N]["volume_fused_per_node"]
+                          for m in mem)
+            tf = ops / (ms / k / 1e3) / 1e12
+            peak = measured_peaks()["fp64_tflops" if prec == "fp64" else "fp32_tflops"]
+            out[prec]["step_tflops"] = tf
+            out[prec]["step_frac_of_peak"] = tf / peak
+            out[prec]["ops_source"] = ("oracle operation counts per degree "
+                                       "(tests/golden/op_counts.json, ensemble_member_n*), "
+                                       "whole step time, measured peak of the precision")
         out["nodes"] = E.n_nodes
         del E, u, tmp
     return out

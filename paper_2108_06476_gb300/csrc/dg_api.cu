@@ -59,7 +59,8 @@ struct dg_mesh {
   double* wq;          // quadrature weight of each node of an element, P doubles
   double* partials;    // integral partials, kRedBlocks * 7 * 2 doubles
   double* red_out;     // 7 * 2 doubles
-  unsigned long long* speed;  // max wave-speed sum (as ordered bits)
+  unsigned long long* speed;  // max wave-speed sum (as ordered bits), then a
+                              // block ticket of the fused wave-speed + dt pass
   unsigned* err;       // device error word
   double* fbar;        // face adjoint buffer of dg_rhs_vjp, allocated on first use
   float* ref;          // FP32 meshes: per-element reference states (d+2 floats)
@@ -70,6 +71,7 @@ struct dg_mesh {
   double graph_cfl;
   double* u_dev;       // device copy of a host state (dg_step_cfl_host), first use
   double* t_dev;       // simulation time (source terms), advanced by the fused steps
+  double* pp_buf;      // small FP64 Cartesian meshes: two stage buffers (2 nvalues)
   // curvilinear meshes (dg_mesh_create_curved)
   int curved;
   double warp;
@@ -277,11 +279,13 @@ __device__ __forceinline__ void speed_node(const double* c, int D, const Geom& g
 }
 
 // copy_to (optional) receives a copy of u: the host-state step reads a
-// mapped host buffer here once and continues on the device copy.
+// mapped host buffer here once and continues on the device copy. dt
+// (optional): the last block to finish (a ticket in out[1]) also computes
+// dt = cfl 2 / ((N+1) worst) and clears out[0] and out[1], as dt_kernel does.
 template <int D, typename R>
 __global__ void speed_kernel(const double* __restrict__ u, Geom g, int P, double s0, double s1,
                              double s2, unsigned long long* out, unsigned* err,
-                             double* __restrict__ copy_to) {
+                             double* __restrict__ copy_to, int N, double cfl, double* dt) {
   constexpr int NV = D + 2;
   const int lane = threadIdx.x & 31;
   const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -320,6 +324,21 @@ __global__ void speed_kernel(const double* __restrict__ u, Geom g, int P, double
     double m = 0.0;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmax(m, sb[w]);
     atomicMax(out, (unsigned long long)__double_as_longlong(m));
+    if (dt) {
+      __threadfence();
+      if (atomicAdd(out + 1, 1ull) == (unsigned long long)gridDim.x - 1ull) {
+        // every block's maximum is in
+        const double worst = __longlong_as_double((long long)atomicAdd(out, 0ull));
+        out[0] = 0ull;
+        out[1] = 0ull;
+        if (!(worst > 0.0)) {
+          atomicOr(err, 4u);
+          *dt = 0.0;
+        } else {
+          *dt = cfl * 2.0 / ((N + 1) * worst);
+        }
+      }
+    }
   }
 }
 
@@ -439,8 +458,12 @@ bool valid_mesh(const dg_mesh* m) { return m != nullptr && m->k != nullptr; }
 int grid_for(long long work, int threads);
 
 // wave-speed reduction into m->speed (FP32 arithmetic on FP32 meshes);
-// copy_to (optional): device buffer that receives a copy of u
-int launch_speed(dg_mesh* m, const double* u, double* copy_to = nullptr) {
+// copy_to (optional): device buffer that receives a copy of u; cfl > 0 on
+// Cartesian Euler meshes: the same launch writes the time step to m->dt_dev
+// (*dt_done is then set)
+int launch_speed(dg_mesh* m, const double* u, double* copy_to = nullptr, double cfl = 0.0,
+                 bool* dt_done = nullptr) {
+  if (dt_done) *dt_done = false;
   // one warp per element; small meshes get one-warp blocks so that the FP64
   // work (2 lanes per clock per SM) spreads over more SMs
   const int threads = (m->nelem * 32 < 152LL * 4 * 256) ? 32 : 256;
@@ -466,22 +489,28 @@ int launch_speed(dg_mesh* m, const double* u, double* copy_to = nullptr) {
   }
   const double s0 = 2.0 / m->h[0], s1 = 2.0 / m->h[1], s2 = 2.0 / m->h[2];
   const bool f32 = m->opt.precision == DG_FP32;
+  double* dt = cfl > 0.0 ? m->dt_dev : nullptr;
   if (m->d == 2) {
     if (f32)
       speed_kernel<2, float><<<grid, threads, 0, m->stream>>>(u, m->geom, (int)m->P, s0, s1, s2,
-                                                              m->speed, m->err, copy_to);
+                                                              m->speed, m->err, copy_to, m->N,
+                                                              cfl, dt);
     else
       speed_kernel<2, double><<<grid, threads, 0, m->stream>>>(u, m->geom, (int)m->P, s0, s1, s2,
-                                                               m->speed, m->err, copy_to);
+                                                               m->speed, m->err, copy_to, m->N,
+                                                               cfl, dt);
   } else {
     if (f32)
       speed_kernel<3, float><<<grid, threads, 0, m->stream>>>(u, m->geom, (int)m->P, s0, s1, s2,
-                                                              m->speed, m->err, copy_to);
+                                                              m->speed, m->err, copy_to, m->N,
+                                                              cfl, dt);
     else
       speed_kernel<3, double><<<grid, threads, 0, m->stream>>>(u, m->geom, (int)m->P, s0, s1, s2,
-                                                               m->speed, m->err, copy_to);
+                                                               m->speed, m->err, copy_to, m->N,
+                                                               cfl, dt);
   }
   DG_CUDA(cudaGetLastError(), "speed kernel launch");
+  if (dt_done) *dt_done = dt != nullptr;
   return DG_OK;
 }
 
@@ -638,12 +667,14 @@ int dg_mesh_create(int d, int N, const int* epd, const double* domain, const dg_
       (e = cudaMalloc(&m->wq, m->P * sizeof(double))) != cudaSuccess ||
       (e = cudaMalloc(&m->partials, kRedBlocks * 7 * 2 * sizeof(double))) != cudaSuccess ||
       (e = cudaMalloc(&m->red_out, 7 * 2 * sizeof(double))) != cudaSuccess ||
-      (e = cudaMalloc(&m->speed, sizeof(unsigned long long))) != cudaSuccess ||
+      (e = cudaMalloc(&m->speed, 2 * sizeof(unsigned long long))) != cudaSuccess ||
       (e = cudaMalloc(&m->err, sizeof(unsigned))) != cudaSuccess ||
       (e = cudaMalloc(&m->ref, m->nelem * m->nv * sizeof(float))) != cudaSuccess ||
       (e = cudaMalloc(&m->refE, m->nelem * sizeof(double))) != cudaSuccess ||
       (e = cudaMalloc(&m->dt_dev, sizeof(double))) != cudaSuccess ||
-      (e = cudaMalloc(&m->t_dev, sizeof(double))) != cudaSuccess) {
+      (e = cudaMalloc(&m->t_dev, sizeof(double))) != cudaSuccess ||
+      (o.precision == DG_FP64 && m->nelem < dg::kPairParallelElems &&
+       (e = cudaMalloc(&m->pp_buf, 2 * m->nvalues * sizeof(double))) != cudaSuccess)) {
     int rc = cuda_fail(e, "dg_mesh_create: cudaMalloc");
     cudaFree(m->k);
     cudaFree(m->fs);
@@ -656,6 +687,7 @@ int dg_mesh_create(int d, int N, const int* epd, const double* domain, const dg_
     cudaFree(m->refE);
     cudaFree(m->dt_dev);
     cudaFree(m->t_dev);
+    cudaFree(m->pp_buf);
     delete m;
     return rc;
   }
@@ -663,7 +695,7 @@ int dg_mesh_create(int d, int N, const int* epd, const double* domain, const dg_
                            m->stream)) != cudaSuccess ||
       (e = cudaMemsetAsync(m->k, 0, m->nvalues * sizeof(double), m->stream)) != cudaSuccess ||
       (e = cudaMemsetAsync(m->err, 0, sizeof(unsigned), m->stream)) != cudaSuccess ||
-      (e = cudaMemsetAsync(m->speed, 0, sizeof(unsigned long long), m->stream)) != cudaSuccess ||
+      (e = cudaMemsetAsync(m->speed, 0, 2 * sizeof(unsigned long long), m->stream)) != cudaSuccess ||
       (e = cudaMemsetAsync(m->dt_dev, 0, sizeof(double), m->stream)) != cudaSuccess ||
       (e = cudaMemsetAsync(m->t_dev, 0, sizeof(double), m->stream)) != cudaSuccess ||
       (e = cudaStreamSynchronize(m->stream)) != cudaSuccess) {
@@ -910,6 +942,7 @@ int dg_mesh_destroy(dg_mesh* m) {
   cudaFree(m->dt_dev);
   cudaFree(m->u_dev);
   cudaFree(m->t_dev);
+  cudaFree(m->pp_buf);
   cudaFree(m->Ja);
   cudaFree(m->invJ);
   cudaFree(m->Jdet);
@@ -1060,6 +1093,11 @@ namespace {
 // The five fused stages on the device state u with the time step in
 // m->dt_dev; out (optional): where the last stage stores the new state.
 int enqueue_fused_stages(dg_mesh* m, double* u, double* out) {
+  // small FP64 Cartesian meshes run each stage as one launch (faces and
+  // volume) from one buffer into another: u -> A -> B -> A -> B -> u (or out)
+  const bool pp = m->pp_buf && !m->mhd && !m->curved && m->opt.precision == DG_FP64;
+  double* const A = pp ? m->pp_buf : nullptr;
+  double* const B = pp ? m->pp_buf + m->nvalues : nullptr;
   for (int s = 0; s < 5; ++s) {
     dg::StageFuse fz;
     fz.k = m->k;
@@ -1067,6 +1105,8 @@ int enqueue_fused_stages(dg_mesh* m, double* u, double* out) {
     fz.a = kRkA[s];
     fz.b = kRkB[s];
     if (s == 4) fz.u_out = out;
+    double* const u_in = !pp ? u : (s == 0 ? u : (s % 2 == 1 ? A : B));
+    if (pp) fz.u_out = s == 4 ? (out ? out : u) : (s % 2 == 0 ? A : B);
     cudaError_t e;
     if (m->mhd && m->curved) {
       e = dg::mhd_curved_rhs_launch(m->N, u, nullptr, (double*)m->fs, m->Ja, m->invJ, m->geom,
@@ -1086,7 +1126,7 @@ int enqueue_fused_stages(dg_mesh* m, double* u, double* out) {
                                 m->stream, 3, fz, src);
     } else if (m->opt.precision == DG_FP64) {
       e = (m->d == 2 ? dg::rhs_launch_double_2 : dg::rhs_launch_double_3)(
-          m->N, u, nullptr, (double*)m->fs, m->geom, m->t64, m->opt.volume_flux,
+          m->N, u_in, nullptr, (double*)m->fs, m->geom, m->t64, m->opt.volume_flux,
           m->opt.surface_flux, m->err, m->stream, 3, fz);
     } else {
       fz.ref = m->ref;
@@ -1109,10 +1149,13 @@ int enqueue_fused_stages(dg_mesh* m, double* u, double* out) {
 // out (optional): where the last stage stores the new state instead of u.
 int enqueue_fused_step(dg_mesh* m, double* u, double cfl, const double* src = nullptr,
                        double* out = nullptr) {
-  int rc = src ? launch_speed(m, src, u) : launch_speed(m, u);
+  bool dt_done = false;
+  int rc = src ? launch_speed(m, src, u, cfl, &dt_done) : launch_speed(m, u, nullptr, cfl, &dt_done);
   if (rc) return rc;
-  dt_kernel<<<1, 1, 0, m->stream>>>(m->speed, m->N, cfl, m->dt_dev, m->err);
-  DG_CUDA(cudaGetLastError(), "dt kernel launch");
+  if (!dt_done) {
+    dt_kernel<<<1, 1, 0, m->stream>>>(m->speed, m->N, cfl, m->dt_dev, m->err);
+    DG_CUDA(cudaGetLastError(), "dt kernel launch");
+  }
   return enqueue_fused_stages(m, u, out);
 }
 }  // namespace

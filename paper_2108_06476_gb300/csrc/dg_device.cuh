@@ -18,6 +18,9 @@
 namespace dg {
 
 constexpr int kNPMax = 8;  // N <= 7
+// Cartesian FP64 meshes with fewer elements than this (about four per SM)
+// run the pair-parallel volume kernel, and a whole rhs or stage as one launch
+constexpr long long kPairParallelElems = 4 * 152;
 
 // error-word bits
 constexpr unsigned kErrRho = 1u, kErrP = 2u, kErrNaN = 4u;

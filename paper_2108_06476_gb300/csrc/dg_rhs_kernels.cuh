@@ -266,202 +266,6 @@ __device__ __forceinline__ void volume_batch(double* u, R* __restrict__ du,
   }
 }
 
-// ---- pair-parallel volume kernel for tiny meshes (FP64) ----
-// One element per CTA, one thread per (direction, line, node pair): every
-// pair flux is evaluated by its own thread (the line-owning kernel walks a
-// line's N(N+1)/2 pairs in one thread, and on a mesh of a few hundred
-// elements each SM holds one or two of those threads' warps, every FP64
-// instruction occupying the sub-partition's FP64 unit for the whole warp).
-// The fluxes go to shared memory; then one thread per (direction, node) sums
-// its pairs in the line-owning kernel's order (the other node's index
-// ascending, then the lifting), and the directions are added in order, so the
-// result is bitwise that of volume_kernel.
-template <int D, int N>
-struct PairPar {
-  static constexpr int NP = N + 1, P = Shape<D, N>::P, LINES = Shape<D, N>::LINES,
-                       NV = D + 2, NC = 3 + 2 * D;
-  static constexpr int NPAIRS = N * (N + 1) / 2;
-  // all directions at once when their pair fluxes fit in 96 KB
-  static constexpr bool ALLDIRS = D * LINES * NPAIRS * NV * 8 <= 98304;
-  static constexpr int GROUP = ALLDIRS ? D : 1;  // directions per phase
-  static constexpr int WORK = GROUP * LINES * NPAIRS;
-  static constexpr int THREADS = WORK < 512 ? ((WORK + 31) / 32) * 32 : 512;
-  static constexpr int SMEM = (NC + NV + GROUP * NV) * P * 8 + WORK * NV * 8;
-};
-
-template <int N>
-__device__ __forceinline__ void pp_pair_of(int p, int& a, int& b) {
-  a = 0;
-  while (p >= N - a) {
-    p -= N - a;
-    ++a;
-  }
-  b = a + 1 + p;
-}
-
-template <int N>
-__device__ __forceinline__ int pp_pair_index(int a, int b) {  // a < b
-  return a * N - a * (a - 1) / 2 + (b - a - 1);
-}
-
-// line l and position i of a node along direction dir (inverse of line_node)
-template <int D, int N>
-__device__ __forceinline__ void pp_line_of(int dir, int node, int& l, int& i) {
-  constexpr int NP = N + 1;
-  if (dir == 0) {
-    l = node / NP;
-    i = node % NP;
-  } else if (dir == 1) {
-    i = (node / NP) % NP;
-    l = (D == 2) ? node % NP : node % NP + NP * (node / (NP * NP));
-  } else {
-    i = node / (NP * NP);
-    l = node % (NP * NP);
-  }
-}
-
-template <int D, int N, int VF>
-__global__ void __launch_bounds__(PairPar<D, N>::THREADS)
-    volume_pp_kernel(double* u, double* __restrict__ du, const double* __restrict__ fs, Geom g,
-                     Tables<double> tb, unsigned* __restrict__ err, StageFuse fz) {
-  using C = PairPar<D, N>;
-  constexpr int NP = C::NP, P = C::P, NV = C::NV, NC = C::NC, LINES = C::LINES,
-                NPAIRS = C::NPAIRS, GROUP = C::GROUP;
-  extern __shared__ __align__(16) unsigned char dg_smem[];
-  double(*sp)[P] = reinterpret_cast<double(*)[P]>(dg_smem);                          // [NC][P]
-  double(*sa)[P] = reinterpret_cast<double(*)[P]>(dg_smem + 8 * NC * P);             // [NV][P]
-  double(*sd)[NV][P] = reinterpret_cast<double(*)[NV][P]>(dg_smem + 8 * (NC + NV) * P);
-  double* sf = reinterpret_cast<double*>(dg_smem + 8 * (NC + NV + GROUP * NV) * P);  // [WORK][NV]
-  const int e = blockIdx.x;
-  const int nelem = (int)g.nelem;
-  __shared__ int s_left[3];
-  if (threadIdx.x < D) s_left[threadIdx.x] = neighbour32(g, e, threadIdx.x, -1);
-  unsigned bad = 0;
-  for (int node = threadIdx.x; node < P; node += blockDim.x) {
-    double c[NV], rr;
-#pragma unroll
-    for (int v = 0; v < NV; ++v) c[v] = u[((long long)e * NV + v) * P + node];
-    const Prim<double, D> q = prim_rcp<D>(c, g.gm1, rr);
-    bad |= prim_check(q);
-    node_slots<VF, double>(q.rho, q.p, g.gm1, sp[0][node], sp[1][node]);
-    sp[2][node] = 0.5 * q.p;
-#pragma unroll
-    for (int k = 0; k < D; ++k) {
-      sp[3 + k][node] = q.v[k];
-      sp[3 + D + k][node] = 0.5 * q.v[k];
-    }
-#pragma unroll
-    for (int v = 0; v < NV; ++v) sa[v][node] = 0.0;
-  }
-  if (bad) atomicOr(err, bad);
-  __syncthreads();
-  const long long base = (long long)nelem * LINES;
-  const double gm1inv = g.gm1inv;
-#pragma unroll 1
-  for (int d0 = 0; d0 < D; d0 += GROUP) {
-    // pair fluxes of the group's directions, normal-first
-    for (int w = threadIdx.x; w < C::WORK; w += blockDim.x) {
-      const int dir = d0 + w / (LINES * NPAIRS);
-      const int rem = w % (LINES * NPAIRS);
-      const int l = rem / NPAIRS;
-      int a, b;
-      pp_pair_of<N>(rem % NPAIRS, a, b);
-      const int na = line_node_rt<D, N>(dir, l, a), nb = line_node_rt<D, N>(dir, l, b);
-      const int t1 = (dir + 1) % D, t2 = (dir + 2) % D;
-      LinePrim<double, D> qa, qb;
-      qa.s0 = sp[0][na];
-      qa.s1 = sp[1][na];
-      qa.hp = sp[2][na];
-      qa.vn = sp[3 + dir][na];
-      qa.hvn = sp[3 + D + dir][na];
-      qa.vt[0] = sp[3 + t1][na];
-      qa.hvt[0] = sp[3 + D + t1][na];
-      qb.s0 = sp[0][nb];
-      qb.s1 = sp[1][nb];
-      qb.hp = sp[2][nb];
-      qb.vn = sp[3 + dir][nb];
-      qb.hvn = sp[3 + D + dir][nb];
-      qb.vt[0] = sp[3 + t1][nb];
-      qb.hvt[0] = sp[3 + D + t1][nb];
-      if (D == 3) {
-        qa.vt[D - 2] = sp[3 + t2][na];
-        qa.hvt[D - 2] = sp[3 + D + t2][na];
-        qb.vt[D - 2] = sp[3 + t2][nb];
-        qb.hvt[D - 2] = sp[3 + D + t2][nb];
-      }
-      double f[NV], an = 0.0;
-      if (VF == kVRanocha) ranocha_nf<double, D>(qa, qb, f, an);
-      else generic_nf<VF, double, D>(qa, qb, gm1inv, f);
-#pragma unroll
-      for (int v = 0; v < NV; ++v) sf[w * NV + v] = f[v];
-    }
-    __syncthreads();
-    // per (direction, node): the line sum in the line-owning order, then the
-    // lifting (normal-first components back to variables)
-    for (int t = threadIdx.x; t < GROUP * P; t += blockDim.x) {
-      const int gd = t / P, node = t % P, dir = d0 + gd;
-      const int t1 = (dir + 1) % D, t2 = (dir + 2) % D;
-      int l, i;
-      pp_line_of<D, N>(dir, node, l, i);
-      double acc[NV];
-#pragma unroll
-      for (int v = 0; v < NV; ++v) acc[v] = 0.0;
-      for (int j = 0; j < NP; ++j) {
-        if (j == i) continue;
-        const int p = j < i ? pp_pair_index<N>(j, i) : pp_pair_index<N>(i, j);
-        const double dij = tb.Ds[dir][i][j];
-        const double* fp = sf + ((gd * LINES + l) * NPAIRS + p) * NV;
-#pragma unroll
-        for (int v = 0; v < NV; ++v) acc[v] = fma(dij, fp[v], acc[v]);
-      }
-      int comp[NV];
-      comp[0] = 0;
-      comp[1] = 1 + dir;
-      comp[2] = 1 + t1;
-      if (D == 3) comp[D] = 1 + t2;
-      comp[D + 1] = D + 1;
-      if (i == N) {
-#pragma unroll
-        for (int c = 0; c < NV; ++c)
-          acc[c] = fma(tb.liftR[dir], fs[(long long)(dir * NV + comp[c]) * base + (long long)e * LINES + l],
-                       acc[c]);
-      }
-      if (i == 0) {
-#pragma unroll
-        for (int c = 0; c < NV; ++c)
-          acc[c] = fma(tb.liftL[dir],
-                       fs[(long long)(dir * NV + comp[c]) * base + (long long)s_left[dir] * LINES + l],
-                       acc[c]);
-      }
-#pragma unroll
-      for (int c = 0; c < NV; ++c) sd[gd][comp[c]][node] = acc[c];
-    }
-    __syncthreads();
-    // the directions added in order, as the line-owning kernel does
-    for (int t = threadIdx.x; t < NV * P; t += blockDim.x) {
-      const int v = t / P, node = t % P;
-#pragma unroll
-      for (int gd = 0; gd < GROUP; ++gd) sa[v][node] += sd[gd][v][node];
-    }
-    __syncthreads();
-  }
-  const double dtv = fz.k ? *fz.dt : 0.0;
-  double* const uo = fz.u_out ? fz.u_out : u;
-  for (int t = threadIdx.x; t < NV * P; t += blockDim.x) {
-    const int v = t / P, node = t % P;
-    const double val = sa[v][node];
-    const long long i = ((long long)e * NV + v) * P + node;
-    if (fz.k) {
-      double kk = dtv * val;
-      if (fz.a != 0.0) kk = fma(fz.a, fz.k[i], kk);
-      fz.k[i] = kk;
-      uo[i] = u[i] + fz.b * kk;
-    } else {
-      du[i] = val;
-    }
-  }
-}
-
 template <int D, int N, typename R, int VF, int EPB>
 __global__ void __launch_bounds__(EPB* Shape<D, N>::LINES)
     volume_kernel(double* u, R* __restrict__ du, const R* __restrict__ fs, Geom g, Tables<R> tb,
@@ -557,12 +361,14 @@ __device__ __forceinline__ void surface_nf(int sf, const Trace<R, D>& L, const T
 // the surface flux of face node l of element e's right face in direction
 // dir (the left element e, the right one its +dir neighbour), stored in
 // fs[dir][v][e][l]
+// the surface flux of face node l of the right face (direction dir) of
+// element e, normal-first: f[0] mass, f[1] normal momentum, f[2..D]
+// tangential momenta (directions dir+1, dir+2), f[D+1] energy
 template <int D, int N, typename R, int dir>
-__device__ __forceinline__ void face_flux(const double* __restrict__ u, R* __restrict__ fs,
-                                          const Geom& g, int sf, int e, int l) {
+__device__ __forceinline__ void face_flux_nf(const double* __restrict__ u, const Geom& g, int sf,
+                                             int e, int l, R f[D + 2]) {
   using S = Shape<D, N>;
-  constexpr int NV = S::NV, P = S::P, NF = S::LINES;
-  const int nelem = (int)g.nelem;
+  constexpr int NV = S::NV, P = S::P;
   const R gamma = R(g.gamma), gm1inv = R(g.gm1inv);
   constexpr int t1 = (dir + 1) % D, t2 = (dir + 2) % D;
   const int er = neighbour32(g, e, dir, +1);
@@ -604,8 +410,17 @@ __device__ __forceinline__ void face_flux(const double* __restrict__ u, R* __res
   }
   L.E = R(cl[NV - 1]);
   Rt.E = R(cr[NV - 1]);
-  R f[NV];
   surface_nf<R, D>(sf, L, Rt, dE, gamma, gm1inv, f);
+}
+
+template <int D, int N, typename R, int dir>
+__device__ __forceinline__ void face_flux(const double* __restrict__ u, R* __restrict__ fs,
+                                          const Geom& g, int sf, int e, int l) {
+  constexpr int NV = D + 2, NF = Shape<D, N>::LINES;
+  constexpr int t1 = (dir + 1) % D, t2 = (dir + 2) % D;
+  const int nelem = (int)g.nelem;
+  R f[NV];
+  face_flux_nf<D, N, R, dir>(u, g, sf, e, l, f);
   const long long base = (long long)nelem * NF;
   const long long off = (long long)e * NF + l;
   fs[(long long)(dir * NV + 0) * base + off] = f[0];
@@ -630,6 +445,246 @@ __global__ void surface_kernel(const double* __restrict__ u, R* __restrict__ fs,
   if (blockIdx.y == 0) surface_body<D, N, R, 0>(u, fs, g, sf);
   else if (blockIdx.y == 1) surface_body<D, N, R, 1>(u, fs, g, sf);
   else surface_body<D, N, R, (D == 3 ? 2 : 1)>(u, fs, g, sf);
+}
+
+// ---- pair-parallel volume kernel for tiny meshes (FP64) ----
+// One element per CTA, one thread per (direction, line, node pair): every
+// pair flux is evaluated by its own thread (the line-owning kernel walks a
+// line's N(N+1)/2 pairs in one thread, and on a mesh of a few hundred
+// elements each SM holds one or two of those threads' warps, every FP64
+// instruction occupying the sub-partition's FP64 unit for the whole warp).
+// The fluxes go to shared memory; then one thread per (direction, node) sums
+// its pairs in the line-owning kernel's order (the other node's index
+// ascending, then the lifting), and the directions are added in order, so the
+// result is bitwise that of volume_kernel.
+//
+// With FACES the same launch also evaluates the surface fluxes its element
+// needs (both faces in every direction, in shared memory) in warps of their
+// own that run beside the prologue: a whole rhs, or a whole Runge-Kutta stage
+// that writes its new state to another buffer (neighbours read the input
+// state), in one launch. Each face is then evaluated by both of its elements,
+// with the same function and inputs as the face kernel, so the result is the
+// same as with the face kernel.
+template <int D, int N>
+struct PairPar {
+  static constexpr int NP = N + 1, P = Shape<D, N>::P, LINES = Shape<D, N>::LINES,
+                       NV = D + 2, NC = 3 + 2 * D;
+  static constexpr int NPAIRS = N * (N + 1) / 2;
+  // all directions at once when their pair fluxes fit in 96 KB
+  static constexpr bool ALLDIRS = D * LINES * NPAIRS * NV * 8 <= 98304;
+  static constexpr int GROUP = ALLDIRS ? D : 1;  // directions per phase
+  static constexpr int WORK = GROUP * LINES * NPAIRS;
+  static constexpr int THREADS = WORK < 512 ? ((WORK + 31) / 32) * 32 : 512;
+  static constexpr int SMEM = (NC + NV + GROUP * NV) * P * 8 + WORK * NV * 8;
+  // FACES: face warps after the THREADS volume threads; each direction has
+  // FSTRIDE slots for its 2 LINES face nodes (both sides)
+  static constexpr int FSTRIDE = ((2 * LINES + 31) / 32) * 32;
+  static constexpr int THREADS_F = THREADS + D * FSTRIDE;
+  static_assert(THREADS_F <= 1024, "face warps do not fit the CTA");
+  static constexpr int SMEM_F = SMEM + 2 * D * NV * LINES * 8;
+};
+
+template <int N>
+__device__ __forceinline__ void pp_pair_of(int p, int& a, int& b) {
+  a = 0;
+  while (p >= N - a) {
+    p -= N - a;
+    ++a;
+  }
+  b = a + 1 + p;
+}
+
+template <int N>
+__device__ __forceinline__ int pp_pair_index(int a, int b) {  // a < b
+  return a * N - a * (a - 1) / 2 + (b - a - 1);
+}
+
+// line l and position i of a node along direction dir (inverse of line_node)
+template <int D, int N>
+__device__ __forceinline__ void pp_line_of(int dir, int node, int& l, int& i) {
+  constexpr int NP = N + 1;
+  if (dir == 0) {
+    l = node / NP;
+    i = node % NP;
+  } else if (dir == 1) {
+    i = (node / NP) % NP;
+    l = (D == 2) ? node % NP : node % NP + NP * (node / (NP * NP));
+  } else {
+    i = node / (NP * NP);
+    l = node % (NP * NP);
+  }
+}
+
+template <int D, int N, int VF, bool FACES>
+__global__ void __launch_bounds__(FACES ? PairPar<D, N>::THREADS_F : PairPar<D, N>::THREADS)
+    volume_pp_kernel(double* u, double* __restrict__ du, const double* __restrict__ fs, Geom g,
+                     Tables<double> tb, unsigned* __restrict__ err, StageFuse fz, int sfk) {
+  using C = PairPar<D, N>;
+  constexpr int NP = C::NP, P = C::P, NV = C::NV, NC = C::NC, LINES = C::LINES,
+                NPAIRS = C::NPAIRS, GROUP = C::GROUP;
+  extern __shared__ __align__(16) unsigned char dg_smem[];
+  double(*sp)[P] = reinterpret_cast<double(*)[P]>(dg_smem);                          // [NC][P]
+  double(*sa)[P] = reinterpret_cast<double(*)[P]>(dg_smem + 8 * NC * P);             // [NV][P]
+  double(*sd)[NV][P] = reinterpret_cast<double(*)[NV][P]>(dg_smem + 8 * (NC + NV) * P);
+  double* sf = reinterpret_cast<double*>(dg_smem + 8 * (NC + NV + GROUP * NV) * P);  // [WORK][NV]
+  // FACES: [side][dir][c][l], side 0 the element's right face, 1 its left
+  // face; c in normal-first order
+  double* sfc = reinterpret_cast<double*>(dg_smem + C::SMEM);
+  const int e = blockIdx.x;
+  const int nelem = (int)g.nelem;
+  __shared__ int s_left[3];
+  if (threadIdx.x < D) s_left[threadIdx.x] = neighbour32(g, e, threadIdx.x, -1);
+  // FACES: the first THREADS threads (the volume threads) do the prologue and
+  // the first pair phase, synchronised among themselves by barrier 1, while
+  // the face warps (one direction per warp) evaluate the surface fluxes; all
+  // meet at the barrier before the first line sums
+  const int wt = FACES ? C::THREADS : (int)blockDim.x;
+  if (FACES && (int)threadIdx.x >= C::THREADS) {
+    const int t = (int)threadIdx.x - C::THREADS;
+    const int dir = t / C::FSTRIDE, r = t % C::FSTRIDE;
+    if (r < 2 * LINES) {
+      const int side = r / LINES, l = r % LINES;
+      const int owner = side == 0 ? e : neighbour32(g, e, dir, -1);
+      double f[NV];
+      if (dir == 0) face_flux_nf<D, N, double, 0>(u, g, sfk, owner, l, f);
+      else if (dir == 1) face_flux_nf<D, N, double, 1>(u, g, sfk, owner, l, f);
+      else face_flux_nf<D, N, double, (D == 3 ? 2 : 1)>(u, g, sfk, owner, l, f);
+#pragma unroll
+      for (int c = 0; c < NV; ++c) sfc[((side * D + dir) * NV + c) * LINES + l] = f[c];
+    }
+  }
+  unsigned bad = 0;
+  for (int node = threadIdx.x; node < P && (int)threadIdx.x < wt; node += wt) {
+    double c[NV], rr;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) c[v] = u[((long long)e * NV + v) * P + node];
+    const Prim<double, D> q = prim_rcp<D>(c, g.gm1, rr);
+    bad |= prim_check(q);
+    node_slots<VF, double>(q.rho, q.p, g.gm1, sp[0][node], sp[1][node]);
+    sp[2][node] = 0.5 * q.p;
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      sp[3 + k][node] = q.v[k];
+      sp[3 + D + k][node] = 0.5 * q.v[k];
+    }
+#pragma unroll
+    for (int v = 0; v < NV; ++v) sa[v][node] = 0.0;
+  }
+  if (bad) atomicOr(err, bad);
+  if (FACES) {
+    if ((int)threadIdx.x < C::THREADS) asm volatile("bar.sync 1, %0;" ::"r"(C::THREADS) : "memory");
+  } else {
+    __syncthreads();
+  }
+  const long long base = (long long)nelem * LINES;
+  const double gm1inv = g.gm1inv;
+#pragma unroll 1
+  for (int d0 = 0; d0 < D; d0 += GROUP) {
+    // pair fluxes of the group's directions, normal-first (volume threads)
+    for (int w = threadIdx.x; w < C::WORK && (int)threadIdx.x < wt; w += wt) {
+      const int dir = d0 + w / (LINES * NPAIRS);
+      const int rem = w % (LINES * NPAIRS);
+      const int l = rem / NPAIRS;
+      int a, b;
+      pp_pair_of<N>(rem % NPAIRS, a, b);
+      const int na = line_node_rt<D, N>(dir, l, a), nb = line_node_rt<D, N>(dir, l, b);
+      const int t1 = (dir + 1) % D, t2 = (dir + 2) % D;
+      LinePrim<double, D> qa, qb;
+      qa.s0 = sp[0][na];
+      qa.s1 = sp[1][na];
+      qa.hp = sp[2][na];
+      qa.vn = sp[3 + dir][na];
+      qa.hvn = sp[3 + D + dir][na];
+      qa.vt[0] = sp[3 + t1][na];
+      qa.hvt[0] = sp[3 + D + t1][na];
+      qb.s0 = sp[0][nb];
+      qb.s1 = sp[1][nb];
+      qb.hp = sp[2][nb];
+      qb.vn = sp[3 + dir][nb];
+      qb.hvn = sp[3 + D + dir][nb];
+      qb.vt[0] = sp[3 + t1][nb];
+      qb.hvt[0] = sp[3 + D + t1][nb];
+      if (D == 3) {
+        qa.vt[D - 2] = sp[3 + t2][na];
+        qa.hvt[D - 2] = sp[3 + D + t2][na];
+        qb.vt[D - 2] = sp[3 + t2][nb];
+        qb.hvt[D - 2] = sp[3 + D + t2][nb];
+      }
+      double f[NV], an = 0.0;
+      if (VF == kVRanocha) ranocha_nf<double, D>(qa, qb, f, an);
+      else generic_nf<VF, double, D>(qa, qb, gm1inv, f);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) sf[w * NV + v] = f[v];
+    }
+    __syncthreads();
+    // per (direction, node): the line sum in the line-owning order, then the
+    // lifting (normal-first components back to variables)
+    for (int t = threadIdx.x; t < GROUP * P; t += blockDim.x) {
+      const int gd = t / P, node = t % P, dir = d0 + gd;
+      const int t1 = (dir + 1) % D, t2 = (dir + 2) % D;
+      int l, i;
+      pp_line_of<D, N>(dir, node, l, i);
+      double acc[NV];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) acc[v] = 0.0;
+      for (int j = 0; j < NP; ++j) {
+        if (j == i) continue;
+        const int p = j < i ? pp_pair_index<N>(j, i) : pp_pair_index<N>(i, j);
+        const double dij = tb.Ds[dir][i][j];
+        const double* fp = sf + ((gd * LINES + l) * NPAIRS + p) * NV;
+#pragma unroll
+        for (int v = 0; v < NV; ++v) acc[v] = fma(dij, fp[v], acc[v]);
+      }
+      int comp[NV];
+      comp[0] = 0;
+      comp[1] = 1 + dir;
+      comp[2] = 1 + t1;
+      if (D == 3) comp[D] = 1 + t2;
+      comp[D + 1] = D + 1;
+      if (i == N) {
+#pragma unroll
+        for (int c = 0; c < NV; ++c)
+          acc[c] = fma(tb.liftR[dir],
+                       FACES ? sfc[((0 * D + dir) * NV + c) * LINES + l]
+                             : fs[(long long)(dir * NV + comp[c]) * base + (long long)e * LINES + l],
+                       acc[c]);
+      }
+      if (i == 0) {
+#pragma unroll
+        for (int c = 0; c < NV; ++c)
+          acc[c] = fma(tb.liftL[dir],
+                       FACES ? sfc[((1 * D + dir) * NV + c) * LINES + l]
+                             : fs[(long long)(dir * NV + comp[c]) * base +
+                                  (long long)s_left[dir] * LINES + l],
+                       acc[c]);
+      }
+#pragma unroll
+      for (int c = 0; c < NV; ++c) sd[gd][comp[c]][node] = acc[c];
+    }
+    __syncthreads();
+    // the directions added in order, as the line-owning kernel does
+    for (int t = threadIdx.x; t < NV * P; t += blockDim.x) {
+      const int v = t / P, node = t % P;
+#pragma unroll
+      for (int gd = 0; gd < GROUP; ++gd) sa[v][node] += sd[gd][v][node];
+    }
+    __syncthreads();
+  }
+  const double dtv = fz.k ? *fz.dt : 0.0;
+  double* const uo = fz.u_out ? fz.u_out : u;
+  for (int t = threadIdx.x; t < NV * P; t += blockDim.x) {
+    const int v = t / P, node = t % P;
+    const double val = sa[v][node];
+    const long long i = ((long long)e * NV + v) * P + node;
+    if (fz.k) {
+      double kk = dtv * val;
+      if (fz.a != 0.0) kk = fma(fz.a, fz.k[i], kk);
+      fz.k[i] = kk;
+      uo[i] = u[i] + fz.b * kk;
+    } else {
+      du[i] = val;
+    }
+  }
 }
 
 }  // namespace dg
@@ -691,29 +746,38 @@ cudaError_t launch_volume_epb(const double* u, R* du, R* fs, const Geom& g, cons
 }
 
 // meshes of fewer elements than this run the pair-parallel FP64 volume kernel
-constexpr long long kPairParallelElems = 4 * 152;
+template <int D, int N, int VF, bool FACES>
+cudaError_t launch_volume_pp_vf(const double* u, double* du, double* fs, const Geom& g,
+                                const Tables<double>& tb, int sf, unsigned* err, cudaStream_t st,
+                                const StageFuse& fz) {
+  using C = PairPar<D, N>;
+  constexpr int threads = FACES ? C::THREADS_F : C::THREADS;
+  constexpr int smem = FACES ? C::SMEM_F : C::SMEM;
+  cudaError_t e;
+  if ((e = allow_smem(volume_pp_kernel<D, N, VF, FACES>, smem)) != cudaSuccess) return e;
+  volume_pp_kernel<D, N, VF, FACES><<<(unsigned)g.nelem, threads, smem, st>>>(
+      const_cast<double*>(u), du, fs, g, tb, err, fz, sf);
+  return cudaGetLastError();
+}
 
+// faces: the surface fluxes in the same launch (a whole rhs, or a stage whose
+// output buffer is not its input)
 template <int D, int N>
 cudaError_t launch_volume_pp(const double* u, double* du, double* fs, const Geom& g,
-                             const Tables<double>& tb, int vf, unsigned* err, cudaStream_t st,
-                             const StageFuse& fz) {
-  using C = PairPar<D, N>;
-  cudaError_t e;
-  const unsigned grid = (unsigned)g.nelem;
-  if (vf == kVRanocha) {
-    if ((e = allow_smem(volume_pp_kernel<D, N, kVRanocha>, C::SMEM)) != cudaSuccess) return e;
-    volume_pp_kernel<D, N, kVRanocha><<<grid, C::THREADS, C::SMEM, st>>>(
-        const_cast<double*>(u), du, fs, g, tb, err, fz);
-  } else if (vf == kVChandrashekar) {
-    if ((e = allow_smem(volume_pp_kernel<D, N, kVChandrashekar>, C::SMEM)) != cudaSuccess) return e;
-    volume_pp_kernel<D, N, kVChandrashekar><<<grid, C::THREADS, C::SMEM, st>>>(
-        const_cast<double*>(u), du, fs, g, tb, err, fz);
-  } else {
-    if ((e = allow_smem(volume_pp_kernel<D, N, kVCentral>, C::SMEM)) != cudaSuccess) return e;
-    volume_pp_kernel<D, N, kVCentral><<<grid, C::THREADS, C::SMEM, st>>>(
-        const_cast<double*>(u), du, fs, g, tb, err, fz);
+                             const Tables<double>& tb, int vf, int sf, unsigned* err,
+                             cudaStream_t st, const StageFuse& fz, bool faces) {
+  if (faces) {
+    if (vf == kVRanocha)
+      return launch_volume_pp_vf<D, N, kVRanocha, true>(u, du, fs, g, tb, sf, err, st, fz);
+    if (vf == kVChandrashekar)
+      return launch_volume_pp_vf<D, N, kVChandrashekar, true>(u, du, fs, g, tb, sf, err, st, fz);
+    return launch_volume_pp_vf<D, N, kVCentral, true>(u, du, fs, g, tb, sf, err, st, fz);
   }
-  return cudaGetLastError();
+  if (vf == kVRanocha)
+    return launch_volume_pp_vf<D, N, kVRanocha, false>(u, du, fs, g, tb, sf, err, st, fz);
+  if (vf == kVChandrashekar)
+    return launch_volume_pp_vf<D, N, kVChandrashekar, false>(u, du, fs, g, tb, sf, err, st, fz);
+  return launch_volume_pp_vf<D, N, kVCentral, false>(u, du, fs, g, tb, sf, err, st, fz);
 }
 
 // FP32 kernels: elements per CTA as for FP64 (about 128 threads, dynamic
@@ -769,6 +833,12 @@ cudaError_t launch_rhs_dn(const double* u, R* du, R* fs, const Geom& g, const Ta
                           int vf, int sf, unsigned* err, cudaStream_t st, int parts,
                           const StageFuse& fz) {
   constexpr bool F32 = sizeof(R) == 4;
+  if constexpr (!F32) {
+    // small FP64 meshes: the whole rhs (or a stage into another buffer) in
+    // one launch
+    if (parts == 3 && g.nelem < kPairParallelElems && (!fz.k || (fz.u_out && fz.u_out != u)))
+      return launch_volume_pp<D, N>(u, du, fs, g, tb, vf, sf, err, st, fz, true);
+  }
   if (parts & 1) {
     const long long total = g.nelem * Shape<D, N>::LINES;
     const int threads = (total < 152LL * 4 * 256) ? 64 : 256;
@@ -798,7 +868,7 @@ cudaError_t launch_rhs_dn(const double* u, R* du, R* fs, const Geom& g, const Ta
     using L = Launch<D, N, R>;
     constexpr int EPB = L::EPB;
     if (g.nelem < kPairParallelElems)
-      return launch_volume_pp<D, N>(u, du, fs, g, tb, vf, err, st, fz);
+      return launch_volume_pp<D, N>(u, du, fs, g, tb, vf, sf, err, st, fz, false);
     if (EPB > 1 && g.nelem < 2LL * 152 * EPB)
       return launch_volume_epb<D, N, R, 1>(u, du, fs, g, tb, vf, err, st, fz);
     return launch_volume_epb<D, N, R, EPB>(u, du, fs, g, tb, vf, err, st, fz);

@@ -42,6 +42,9 @@ WORKLOADS = {
     "euler3d_n7_24cubed_noisy_wave": dict(N=7, ne=24, noisy=True),
 }
 SAMPLE_ELEMENTS = 24
+# the ensemble's degrees, each on a member-like density wave (8^3 elements,
+# amplitude 0.5, velocity (0.1, 0.2, -0.1)): the work per node of a member
+ENSEMBLE_DEGREES = (3, 4, 5)
 
 
 def line_nodes(N, direction, line):
@@ -91,6 +94,11 @@ def counts():
         nelem = ne ** 3
         elems = np.random.default_rng(ne).choice(nelem, size=SAMPLE_ELEMENTS, replace=False)
         out[name] = volume_counts(N, u, nelem, sorted(int(e) for e in elems))
+    for N in ENSEMBLE_DEGREES:
+        n = (8, 8, 8)
+        xi, _ = oracle.lgl(N)
+        u = W.density_wave(3, N, n, W.box(3), xi, amplitude=0.5, velocity=(0.1, 0.2, -0.1))
+        out[f"ensemble_member_n{N}"] = volume_counts(N, u, 512, list(range(0, 512, 37)))
     return out
 
 

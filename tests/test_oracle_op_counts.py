@@ -86,3 +86,5 @@ def test_stored_op_counts_are_current(orc):
     # the pressure and energy terms), the prologue 14
     for rec in stored.values():
         assert 60 < rec["pair_flux"] < 75 and rec["prim"] == 14.0
+        N = round(2 * rec["pairs_per_node"] / 3)
+        assert rec["lifting"] == 4 * 3 * 5 / (N + 1)
