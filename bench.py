@@ -329,6 +329,17 @@ def run_ensemble(args, timed, rank, checks):
             part = got[E.offsets[s_]:E.offsets[s_ + 1]].reshape(ne, 5, P)[el]
             samples.append((m, u0h[E.offsets[s_]:E.offsets[s_ + 1]], el, part))
         checks.append(("ensemble", prec, samples))
+        by_tpl = None
+        if prec == "fp64":
+            # one stage in each threads-per-line mode at the tuned CTA shape
+            tuned_pair = E.pair_parallel
+            by_tpl = {}
+            for mode, name in ((False, "1"), (True, "one per node pair")):
+                E.pair_parallel = mode
+                E.stage(u, tmp, 1)
+                by_tpl[name] = timed(lambda: E.stage(u, tmp, 1))
+            E.pair_parallel = tuned_pair
+            E.rk_reset()
         for _ in range(args.warmup):
             E.step(u, cfl=0.5, graph=True)
         ms = timed(lambda: [E.step(u, cfl=0.5, graph=True) for _ in range(k)])
@@ -336,7 +347,14 @@ def run_ensemble(args, timed, rank, checks):
         out[prec] = {"value": E.n_nodes * 5 * k / (ms / 1e3), "unit": UNIT,
                      "ms_per_step": ms / k, "tuned_threads": threads,
                      "tuned_ctas_per_sm": per_sm, "ctas_launched": grid,
+                     "tuned_threads_per_line": ("one per node pair" if E.pair_parallel
+                                                else 1),
+                     "tuner_searched": {"threads_per_cta": [64, 96, 128],
+                                        "ctas_per_sm": [1, 2, 3, 4, 6],
+                                        "threads_per_line": ([1, "one per node pair"]
+                                                             if prec == "fp64" else [1])},
                      "tuned_stage_ms": stage_ms,
+                     "stage_ms_by_threads_per_line": by_tpl,
                      "stage_launches_per_step": 5}
         # the step's algorithmic work: every member's nodes x the operations
         # per node of its degree (oracle operation counts) x 5 stages

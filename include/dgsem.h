@@ -382,9 +382,19 @@ int dg_ensemble_check(dg_ensemble *ens, int *flags);
 int dg_ensemble_set_block(dg_ensemble *ens, int threads, int blocks_per_sm);
 /* the current shape: threads per CTA, requested CTAs per SM, CTAs launched */
 int dg_ensemble_get_block(const dg_ensemble *ens, int *threads, int *ctas_per_sm, int *grid);
+/* threads per line of the volume phase (FP64 ensembles): on = 0, one thread
+ * per element line walking its N(N+1)/2 node pairs (elements per work item
+ * as above); on = 1, pair-parallel: the CTA takes the item's elements one
+ * after another, one thread per (line, node pair) of a direction, then one
+ * thread per node for the line sum (the same result, bitwise). DG_ERR_ARG
+ * for on not in {0, 1} or on = 1 on an FP32 ensemble. */
+int dg_ensemble_set_pair_parallel(dg_ensemble *ens, int on);
+int dg_ensemble_get_pair_parallel(const dg_ensemble *ens, int *on);
 /* autotuner: times one stage from u into u_tmp (u unchanged) for each
- * candidate shape, keeps the fastest and reports it (outputs may be NULL); k
- * is preserved. Allocates a copy of k for the trials. */
+ * candidate (threads per CTA, CTAs per SM and, for FP64, the threads per
+ * line above), keeps the fastest and reports it (outputs may be NULL; the
+ * chosen threads per line: dg_ensemble_get_pair_parallel); k is preserved.
+ * Allocates a copy of k for the trials. */
 int dg_ensemble_tune(dg_ensemble *ens, const double *u, double *u_tmp, int *best_threads,
                      int *best_blocks_per_sm, float *best_ms);
 

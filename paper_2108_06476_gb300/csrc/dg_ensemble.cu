@@ -76,6 +76,7 @@ struct EnsArgs {
   const void* tables;  // per member Tables<R>
   unsigned* err;
   unsigned* bar;       // barrier counter, zero at launch
+  int pair;            // FP64: phase B pair-parallel (see ens_volume_pp)
 };
 
 int fail(int code, const char* msg) { return dg::set_last_error(code, msg); }
@@ -180,6 +181,26 @@ __device__ void ens_volume(const EnsArgs& a, const SimDesc& sd, const WorkItem& 
                                                   g, tb, a.err, fz, w.e0, w.count, smem);
 }
 
+// phase B of one item, pair-parallel (FP64): the item's elements one after
+// another, each with the whole CTA: one thread per (line, node pair) of a
+// direction evaluates the pair flux into shared memory, then one thread per
+// node sums its line in the line-owning order (bitwise the same result)
+template <int N>
+__device__ void ens_volume_pp(const EnsArgs& a, const SimDesc& sd, const WorkItem& w,
+                              const Tables<double>& tb, unsigned char* smem) {
+  const Geom g = member_geom(sd, a);
+  StageFuse fz;
+  fz.k = a.k + sd.off;
+  fz.dt = a.dt + w.sim;
+  fz.a = a.A;
+  fz.b = a.B;
+  fz.u_out = a.uout + sd.off;
+  double* u = const_cast<double*>(a.uin) + sd.off;
+  const double* fs = static_cast<const double*>(a.fs) + sd.fsoff;
+  for (int el = 0; el < w.count; ++el)
+    pp_element<3, N, kVRanocha, false, 1>(u, nullptr, fs, g, tb, a.err, fz, 0, w.e0 + el, smem);
+}
+
 // one cooperative launch per stage: blocks walk the work list (largest
 // degrees first) in each phase; CTAs of at most 128 threads, at least three
 // resident per SM (at most 168 registers a thread)
@@ -206,6 +227,14 @@ __global__ void __launch_bounds__(kEnsMaxThreads, 3) ensemble_stage_kernel(EnsAr
         dst[i] = src[i];
     }
     __syncthreads();
+    if constexpr (sizeof(R) == 8) {
+      if (a.pair) {
+        if (sd.N == 3) ens_volume_pp<3>(a, sd, w, s_tb, dg_smem);
+        else if (sd.N == 4) ens_volume_pp<4>(a, sd, w, s_tb, dg_smem);
+        else ens_volume_pp<5>(a, sd, w, s_tb, dg_smem);
+        continue;
+      }
+    }
     if (sd.N == 3) ens_volume<R, 3>(a, sd, w, s_tb, dg_smem);
     else if (sd.N == 4) ens_volume<R, 4>(a, sd, w, s_tb, dg_smem);
     else ens_volume<R, 5>(a, sd, w, s_tb, dg_smem);
@@ -282,6 +311,7 @@ struct dg_ensemble {
   long long nvalues, nnodes, nfs, nref;
   int block;  // threads per CTA (tunable)
   int per_sm; // requested resident CTAs per SM (tunable)
+  int pair;   // FP64: pair-parallel volume phase (tunable; 0: one thread per line)
   int grid;   // persistent CTAs (cooperative launch)
   int nitems;
   SimDesc* d_sims;
@@ -311,8 +341,13 @@ int items_epb(int N, int block) {
 }
 
 // dynamic shared memory of a work item: FP64, node slots + accumulators;
-// FP32, the same in FP32 plus the staged RK register (volume32_smem)
-int smem_for(int precision, int block) {
+// FP32, the same in FP32 plus the staged RK register (volume32_smem);
+// pair-parallel, one element's slots, accumulators and pair fluxes of one
+// direction
+int smem_for(int precision, int block, int pair) {
+  if (pair)
+    return std::max(PairPar<3, 3, 1>::SMEM,
+                    std::max(PairPar<3, 4, 1>::SMEM, PairPar<3, 5, 1>::SMEM));
   int m = 0;
   for (int N = kEnsMinN; N <= kEnsMaxN; ++N) {
     const int P = (N + 1) * (N + 1) * (N + 1), epb = items_epb(N, block);
@@ -347,7 +382,7 @@ int build_items(dg_ensemble* E) {
 
 template <typename R>
 int configure_grid(dg_ensemble* E) {
-  const int sm = smem_for(E->opt.precision, E->block);
+  const int sm = smem_for(E->opt.precision, E->block, E->pair);
   cudaError_t e = allow_smem(ensemble_stage_kernel<R>, sm);
   if (e != cudaSuccess) return fail(DG_ERR_CUDA, "dg_ensemble: shared-memory attribute");
   int dev = 0, nsm = 0, coop = 0, per = 0;
@@ -383,9 +418,10 @@ int launch_stage(dg_ensemble* E, const double* uin, double* uout, int s) {
   a.tables = E->d_tables;
   a.err = E->err;
   a.bar = E->bar;
+  a.pair = E->pair;
   if (cudaMemsetAsync(E->bar, 0, sizeof(unsigned), E->stream) != cudaSuccess)
     return fail(DG_ERR_CUDA, "dg_ensemble: clearing the barrier counter failed");
-  const int sm = smem_for(E->opt.precision, E->block);
+  const int sm = smem_for(E->opt.precision, E->block, E->pair);
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(E->grid);
   cfg.blockDim = dim3(E->block);
@@ -479,6 +515,7 @@ int dg_ensemble_create(int n_sims, const int* d, const int* N, const int* elemen
   E->stream = (cudaStream_t)cuda_stream;
   E->block = 128;
   E->per_sm = 4;
+  E->pair = 0;
   E->d_sims = nullptr;
   E->d_items = nullptr;
   E->d_tables = nullptr;
@@ -689,6 +726,26 @@ int dg_ensemble_set_block(dg_ensemble* E, int threads, int blocks_per_sm) {
   return (E->opt.precision == DG_FP64) ? configure_grid<double>(E) : configure_grid<float>(E);
 }
 
+int dg_ensemble_set_pair_parallel(dg_ensemble* E, int on) {
+  if (!E || (on != 0 && on != 1))
+    return fail(DG_ERR_ARG, "dg_ensemble_set_pair_parallel: on must be 0 or 1");
+  if (on && E->opt.precision != DG_FP64)
+    return fail(DG_ERR_ARG, "dg_ensemble_set_pair_parallel: FP64 ensembles only");
+  cudaStreamSynchronize(E->stream);
+  E->pair = on;
+  if (E->graph) {
+    cudaGraphExecDestroy(E->graph);
+    E->graph = nullptr;
+  }
+  return (E->opt.precision == DG_FP64) ? configure_grid<double>(E) : configure_grid<float>(E);
+}
+
+int dg_ensemble_get_pair_parallel(const dg_ensemble* E, int* on) {
+  if (!E || !on) return fail(DG_ERR_ARG, "dg_ensemble_get_pair_parallel: null argument");
+  *on = E->pair;
+  return DG_OK;
+}
+
 int dg_ensemble_get_block(const dg_ensemble* E, int* threads, int* ctas_per_sm, int* grid) {
   if (!E) return fail(DG_ERR_ARG, "dg_ensemble_get_block: null ensemble");
   if (threads) *threads = E->block;
@@ -698,15 +755,17 @@ int dg_ensemble_get_block(const dg_ensemble* E, int* threads, int* ctas_per_sm, 
 }
 
 // Autotuner: times one stage for every candidate (threads per CTA, CTAs per
-// SM) from u into u_tmp (u is not changed) and keeps the fastest; the RK
-// register is saved and restored around the trials.
+// SM and, for FP64, one thread per line or pair-parallel) from u into u_tmp
+// (u is not changed) and keeps the fastest; the RK register is saved and
+// restored around the trials.
 int dg_ensemble_tune(dg_ensemble* E, const double* u, double* u_tmp, int* best_threads,
                      int* best_blocks_per_sm, float* best_ms) {
   if (!E || !u || !u_tmp || u == u_tmp) return fail(DG_ERR_ARG, "dg_ensemble_tune: bad argument");
   const int cand_t[] = {64, 96, 128};  // at most the kernel's launch bound
   const int cand_b[] = {1, 2, 3, 4, 6};
   float best = 1e30f;
-  int bt = E->block, bb = E->per_sm;
+  int bt = E->block, bb = E->per_sm, bp_mode = E->pair;
+  const int n_modes = E->opt.precision == DG_FP64 ? 2 : 1;
   double* ksave = nullptr;
   if (cudaMalloc(&ksave, E->nvalues * sizeof(double)) != cudaSuccess)
     return fail(DG_ERR_OOM, "dg_ensemble_tune: cudaMalloc");
@@ -714,22 +773,26 @@ int dg_ensemble_tune(dg_ensemble* E, const double* u, double* u_tmp, int* best_t
   cudaEvent_t a, b;
   cudaEventCreate(&a);
   cudaEventCreate(&b);
-  for (int t : cand_t) {
-    for (int bp : cand_b) {
-      if (dg_ensemble_set_block(E, t, bp) != DG_OK) continue;
-      if (launch_stage(E, u, u_tmp, 1) != DG_OK) continue;  // warm-up
-      cudaEventRecord(a, E->stream);
-      bool ok = true;
-      for (int r = 0; r < 3 && ok; ++r) ok = launch_stage(E, u, u_tmp, 1) == DG_OK;
-      cudaEventRecord(b, E->stream);
-      cudaEventSynchronize(b);
-      float ms = 0.0f;
-      cudaEventElapsedTime(&ms, a, b);
-      ms /= 3.0f;
-      if (ok && ms < best) {
-        best = ms;
-        bt = t;
-        bb = bp;
+  for (int mode = 0; mode < n_modes; ++mode) {
+    if (dg_ensemble_set_pair_parallel(E, mode) != DG_OK) continue;
+    for (int t : cand_t) {
+      for (int bp : cand_b) {
+        if (dg_ensemble_set_block(E, t, bp) != DG_OK) continue;
+        if (launch_stage(E, u, u_tmp, 1) != DG_OK) continue;  // warm-up
+        cudaEventRecord(a, E->stream);
+        bool ok = true;
+        for (int r = 0; r < 3 && ok; ++r) ok = launch_stage(E, u, u_tmp, 1) == DG_OK;
+        cudaEventRecord(b, E->stream);
+        cudaEventSynchronize(b);
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, a, b);
+        ms /= 3.0f;
+        if (ok && ms < best) {
+          best = ms;
+          bt = t;
+          bb = bp;
+          bp_mode = mode;
+        }
       }
     }
   }
@@ -738,7 +801,8 @@ int dg_ensemble_tune(dg_ensemble* E, const double* u, double* u_tmp, int* best_t
   cudaFree(ksave);
   cudaEventDestroy(a);
   cudaEventDestroy(b);
-  int rc = dg_ensemble_set_block(E, bt, bb);
+  int rc = dg_ensemble_set_pair_parallel(E, bp_mode);
+  if (rc == DG_OK) rc = dg_ensemble_set_block(E, bt, bb);
   if (best_threads) *best_threads = bt;
   if (best_blocks_per_sm) *best_blocks_per_sm = bb;
   if (best_ms) *best_ms = best;

@@ -465,14 +465,15 @@ __global__ void surface_kernel(const double* __restrict__ u, R* __restrict__ fs,
 // state), in one launch. Each face is then evaluated by both of its elements,
 // with the same function and inputs as the face kernel, so the result is the
 // same as with the face kernel.
-template <int D, int N>
+// G: directions per phase (0: all of them when their pair fluxes fit in
+// 96 KB, else one)
+template <int D, int N, int G = 0>
 struct PairPar {
   static constexpr int NP = N + 1, P = Shape<D, N>::P, LINES = Shape<D, N>::LINES,
                        NV = D + 2, NC = 3 + 2 * D;
   static constexpr int NPAIRS = N * (N + 1) / 2;
-  // all directions at once when their pair fluxes fit in 96 KB
   static constexpr bool ALLDIRS = D * LINES * NPAIRS * NV * 8 <= 98304;
-  static constexpr int GROUP = ALLDIRS ? D : 1;  // directions per phase
+  static constexpr int GROUP = G > 0 ? G : (ALLDIRS ? D : 1);
   static constexpr int WORK = GROUP * LINES * NPAIRS;
   static constexpr int THREADS = WORK < 512 ? ((WORK + 31) / 32) * 32 : 512;
   static constexpr int SMEM = (NC + NV + GROUP * NV) * P * 8 + WORK * NV * 8;
@@ -515,14 +516,18 @@ __device__ __forceinline__ void pp_line_of(int dir, int node, int& l, int& i) {
   }
 }
 
-template <int D, int N, int VF, bool FACES>
-__global__ void __launch_bounds__(FACES ? PairPar<D, N>::THREADS_F : PairPar<D, N>::THREADS)
-    volume_pp_kernel(double* u, double* __restrict__ du, const double* __restrict__ fs, Geom g,
-                     Tables<double> tb, unsigned* __restrict__ err, StageFuse fz, int sfk) {
-  using C = PairPar<D, N>;
+// The body for element e (every thread of the block calls it; it ends with a
+// barrier after its last shared-memory read, so a block may run it for one
+// element after another). smem: C::SMEM bytes (C::SMEM_F with FACES).
+template <int D, int N, int VF, bool FACES, int G>
+__device__ __forceinline__ void pp_element(double* u, double* __restrict__ du,
+                                           const double* __restrict__ fs, const Geom& g,
+                                           const Tables<double>& tb, unsigned* __restrict__ err,
+                                           const StageFuse& fz, int sfk, int e,
+                                           unsigned char* dg_smem) {
+  using C = PairPar<D, N, G>;
   constexpr int NP = C::NP, P = C::P, NV = C::NV, NC = C::NC, LINES = C::LINES,
                 NPAIRS = C::NPAIRS, GROUP = C::GROUP;
-  extern __shared__ __align__(16) unsigned char dg_smem[];
   double(*sp)[P] = reinterpret_cast<double(*)[P]>(dg_smem);                          // [NC][P]
   double(*sa)[P] = reinterpret_cast<double(*)[P]>(dg_smem + 8 * NC * P);             // [NV][P]
   double(*sd)[NV][P] = reinterpret_cast<double(*)[NV][P]>(dg_smem + 8 * (NC + NV) * P);
@@ -530,7 +535,6 @@ __global__ void __launch_bounds__(FACES ? PairPar<D, N>::THREADS_F : PairPar<D, 
   // FACES: [side][dir][c][l], side 0 the element's right face, 1 its left
   // face; c in normal-first order
   double* sfc = reinterpret_cast<double*>(dg_smem + C::SMEM);
-  const int e = blockIdx.x;
   const int nelem = (int)g.nelem;
   __shared__ int s_left[3];
   if (threadIdx.x < D) s_left[threadIdx.x] = neighbour32(g, e, threadIdx.x, -1);
@@ -685,6 +689,15 @@ __global__ void __launch_bounds__(FACES ? PairPar<D, N>::THREADS_F : PairPar<D, 
       du[i] = val;
     }
   }
+  __syncthreads();
+}
+
+template <int D, int N, int VF, bool FACES>
+__global__ void __launch_bounds__(FACES ? PairPar<D, N>::THREADS_F : PairPar<D, N>::THREADS)
+    volume_pp_kernel(double* u, double* __restrict__ du, const double* __restrict__ fs, Geom g,
+                     Tables<double> tb, unsigned* __restrict__ err, StageFuse fz, int sfk) {
+  extern __shared__ __align__(16) unsigned char dg_smem[];
+  pp_element<D, N, VF, FACES, 0>(u, du, fs, g, tb, err, fz, sfk, blockIdx.x, dg_smem);
 }
 
 }  // namespace dg

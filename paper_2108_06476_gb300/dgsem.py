@@ -38,7 +38,8 @@ EXPORTS = ("dg_mesh_create", "dg_mesh_create_curved", "dg_mesh_create_mhd",
            "dg_ensemble_stage", "dg_ensemble_step", "dg_ensemble_step_graph",
            "dg_ensemble_rk_reset", "dg_ensemble_check", "dg_ensemble_set_block",
            "dg_ensemble_get_block", "dg_ensemble_tune", "dg_measure_peaks",
-           "dg_selftest_arith", "dg_mesh_set_nodes", "dg_mesh_set_metric")
+           "dg_selftest_arith", "dg_mesh_set_nodes", "dg_mesh_set_metric",
+           "dg_ensemble_set_pair_parallel", "dg_ensemble_get_pair_parallel")
 
 
 class DGError(RuntimeError):
@@ -108,6 +109,8 @@ def load(path: str = SO_PATH):
     L.dg_ensemble_check.argtypes = [vp, ip]
     L.dg_ensemble_set_block.argtypes = [vp, ctypes.c_int, ctypes.c_int]
     L.dg_ensemble_get_block.argtypes = [vp, ip, ip, ip]
+    L.dg_ensemble_set_pair_parallel.argtypes = [vp, ctypes.c_int]
+    L.dg_ensemble_get_pair_parallel.argtypes = [vp, ip]
     L.dg_measure_peaks.argtypes = [dp, dp, ip, vp]
     L.dg_selftest_arith.argtypes = [ctypes.c_int, vp, vp, ctypes.c_longlong, vp]
     L.dg_mesh_set_nodes.argtypes = [vp, vp]
@@ -522,8 +525,24 @@ class Ensemble:
                                             ctypes.byref(g)), "dg_ensemble_get_block")
         return t.value, b.value, g.value
 
+    @property
+    def pair_parallel(self):
+        """Threads per line of the volume phase: False, one thread per line;
+        True (FP64 only), one thread per node pair (the same result)."""
+        on = ctypes.c_int()
+        _check(load().dg_ensemble_get_pair_parallel(self._h, ctypes.byref(on)),
+               "dg_ensemble_get_pair_parallel")
+        return bool(on.value)
+
+    @pair_parallel.setter
+    def pair_parallel(self, on):
+        _check(load().dg_ensemble_set_pair_parallel(self._h, int(bool(on))),
+               "dg_ensemble_set_pair_parallel")
+
     def tune(self, u, u_tmp):
-        """Autotune the CTA shape; returns (threads, ctas_per_sm, ms_per_stage)."""
+        """Autotune the CTA shape and (FP64) the threads per line; returns
+        (threads, ctas_per_sm, ms_per_stage); the chosen threads per line:
+        pair_parallel."""
         self._chk(u)
         self._chk(u_tmp)
         t, b, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_float()

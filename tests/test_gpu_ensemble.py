@@ -132,16 +132,48 @@ def test_graph_step_and_tuner_are_bitwise_consistent(orc):
         E.step(b, cfl=0.5, graph=True)
     torch.cuda.synchronize()
     assert torch.equal(a, b)
-    # every element is computed the same way whatever the CTA shape
+    # every element is computed the same way whatever the CTA shape and the
+    # threads per line
     threads, per_sm, ms = E.tune(a, tmp)
     assert threads in (64, 96, 128) and per_sm in (1, 2, 3, 4, 6) and ms > 0
     assert E.get_block()[:2] == (threads, per_sm)
+    print(f"tuned: {threads} threads, {per_sm} CTAs per SM, pair-parallel {E.pair_parallel}")
     E.rk_reset()
     c = torch.from_numpy(u0.copy()).cuda()
     for _ in range(2):
         E.step(c, cfl=0.5)
     torch.cuda.synchronize()
     assert torch.equal(a, c)
+
+
+@pytest.mark.parametrize("threads,per_sm", [(128, 3), (64, 2), (96, 1)])
+def test_pair_parallel_volume_phase_is_bitwise_the_line_owning_one(orc, threads, per_sm):
+    # threads per line: one thread per element line, or one per node pair
+    # with the line sums in the line-owning order; FP64 only
+    mem = small_members() + [W.EnsembleMember(3, 5, (5, 5, 5), 0.7, (0.1, 0.0, 0.2), 20.0)]
+    u0 = np.concatenate([W.random_state(3, m.N, m.n, seed=80 + s) for s, m in enumerate(mem)])
+    E = Ensemble([m.N for m in mem], [m.n[0] for m in mem])
+    E.set_block(threads, per_sm)
+    assert not E.pair_parallel
+    line = stage_rhs(E, u0)
+    E.pair_parallel = True
+    assert E.pair_parallel
+    pair = stage_rhs(E, u0)
+    for s, (a, b) in enumerate(zip(line, pair)):
+        assert np.array_equal(a, b), s
+    a = torch.from_numpy(u0.copy()).cuda()
+    E.rk_reset()
+    E.step(a, cfl=0.5, graph=True)
+    E.pair_parallel = False
+    b = torch.from_numpy(u0.copy()).cuda()
+    E.rk_reset()
+    E.step(b, cfl=0.5, graph=True)
+    torch.cuda.synchronize()
+    assert E.check() == 0
+    assert torch.equal(a, b)
+    F = Ensemble([3], [2], precision="fp32")
+    with pytest.raises(DGError):
+        F.pair_parallel = True
 
 
 def test_members_on_their_own_boxes(orc):
