@@ -198,7 +198,8 @@ __device__ void ens_volume_pp(const EnsArgs& a, const SimDesc& sd, const WorkIte
   double* u = const_cast<double*>(a.uin) + sd.off;
   const double* fs = static_cast<const double*>(a.fs) + sd.fsoff;
   for (int el = 0; el < w.count; ++el)
-    pp_element<3, N, kVRanocha, false, 1>(u, nullptr, fs, g, tb, a.err, fz, 0, w.e0 + el, smem);
+    pp_elements<3, N, kVRanocha, false, 1, 1>(u, nullptr, fs, g, tb, a.err, fz, 0, w.e0 + el, 1,
+                                              smem);
 }
 
 // one cooperative launch per stage: blocks walk the work list (largest

@@ -361,18 +361,28 @@ __device__ __forceinline__ void surface_nf(int sf, const Trace<R, D>& L, const T
 // the surface flux of face node l of element e's right face in direction
 // dir (the left element e, the right one its +dir neighbour), stored in
 // fs[dir][v][e][l]
+// a[k] of a D-vector for a runtime k in [0, D)
+template <int D>
+__device__ __forceinline__ double pick(const double* a, int k) {
+  if constexpr (D == 3) return k == 0 ? a[0] : (k == 1 ? a[1] : a[2]);
+  else return k == 0 ? a[0] : a[1];
+}
+
 // the surface flux of face node l of the right face (direction dir) of
 // element e, normal-first: f[0] mass, f[1] normal momentum, f[2..D]
-// tangential momenta (directions dir+1, dir+2), f[D+1] energy
-template <int D, int N, typename R, int dir>
-__device__ __forceinline__ void face_flux_nf(const double* __restrict__ u, const Geom& g, int sf,
-                                             int e, int l, R f[D + 2]) {
+// tangential momenta (directions dir+1, dir+2), f[D+1] energy. dir is a
+// value (the face kernel passes a constant, the one-launch small-mesh kernel
+// its thread's direction: the same arithmetic either way).
+template <int D, int N, typename R>
+__device__ __forceinline__ void face_flux_nf_dir(int dir, const double* __restrict__ u,
+                                                 const Geom& g, int sf, int e, int l,
+                                                 R f[D + 2]) {
   using S = Shape<D, N>;
   constexpr int NV = S::NV, P = S::P;
   const R gamma = R(g.gamma), gm1inv = R(g.gm1inv);
-  constexpr int t1 = (dir + 1) % D, t2 = (dir + 2) % D;
+  const int t1 = (dir + 1) % D, t2 = (dir + 2) % D;
   const int er = neighbour32(g, e, dir, +1);
-  const int nl = line_node<D, N, dir>(l, N), nr = line_node<D, N, dir>(l, 0);
+  const int nl = line_node_rt<D, N>(dir, l, N), nr = line_node_rt<D, N>(dir, l, 0);
   double cl[NV], cr[NV];
 #pragma unroll
   for (int v = 0; v < NV; ++v) {
@@ -391,26 +401,34 @@ __device__ __forceinline__ void face_flux_nf(const double* __restrict__ u, const
   Rt.rho = R(qr.rho);
   Rt.p = R(qr.p);
   Rt.ps = Rt.p;
-  L.vn = R(ql.v[dir]);
-  Rt.vn = R(qr.v[dir]);
-  L.vt[0] = R(ql.v[t1]);
-  Rt.vt[0] = R(qr.v[t1]);
+  // components picked by selects (no indexing of register arrays by a
+  // runtime direction)
+  L.vn = R(pick<D>(ql.v, dir));
+  Rt.vn = R(pick<D>(qr.v, dir));
+  L.vt[0] = R(pick<D>(ql.v, t1));
+  Rt.vt[0] = R(pick<D>(qr.v, t1));
   if (D == 3) {
-    L.vt[D - 2] = R(ql.v[t2]);
-    Rt.vt[D - 2] = R(qr.v[t2]);
+    L.vt[D - 2] = R(pick<D>(ql.v, t2));
+    Rt.vt[D - 2] = R(pick<D>(qr.v, t2));
   }
   const R dE = R(cr[NV - 1] - cl[NV - 1]);
-  L.mn = R(cl[1 + dir]);
-  Rt.mn = R(cr[1 + dir]);
-  L.mt[0] = R(cl[1 + t1]);
-  Rt.mt[0] = R(cr[1 + t1]);
+  L.mn = R(pick<D>(cl + 1, dir));
+  Rt.mn = R(pick<D>(cr + 1, dir));
+  L.mt[0] = R(pick<D>(cl + 1, t1));
+  Rt.mt[0] = R(pick<D>(cr + 1, t1));
   if (D == 3) {
-    L.mt[D - 2] = R(cl[1 + t2]);
-    Rt.mt[D - 2] = R(cr[1 + t2]);
+    L.mt[D - 2] = R(pick<D>(cl + 1, t2));
+    Rt.mt[D - 2] = R(pick<D>(cr + 1, t2));
   }
   L.E = R(cl[NV - 1]);
   Rt.E = R(cr[NV - 1]);
   surface_nf<R, D>(sf, L, Rt, dE, gamma, gm1inv, f);
+}
+
+template <int D, int N, typename R, int dir>
+__device__ __forceinline__ void face_flux_nf(const double* __restrict__ u, const Geom& g, int sf,
+                                             int e, int l, R f[D + 2]) {
+  face_flux_nf_dir<D, N, R>(dir, u, g, sf, e, l, f);
 }
 
 template <int D, int N, typename R, int dir>
@@ -448,42 +466,56 @@ __global__ void surface_kernel(const double* __restrict__ u, R* __restrict__ fs,
 }
 
 // ---- pair-parallel volume kernel for tiny meshes (FP64) ----
-// One element per CTA, one thread per (direction, line, node pair): every
-// pair flux is evaluated by its own thread (the line-owning kernel walks a
-// line's N(N+1)/2 pairs in one thread, and on a mesh of a few hundred
-// elements each SM holds one or two of those threads' warps, every FP64
-// instruction occupying the sub-partition's FP64 unit for the whole warp).
-// The fluxes go to shared memory; then one thread per (direction, node) sums
-// its pairs in the line-owning kernel's order (the other node's index
-// ascending, then the lifting), and the directions are added in order, so the
-// result is bitwise that of volume_kernel.
+// One thread per (direction, line, node pair): every pair flux is evaluated
+// by its own thread (the line-owning kernel walks a line's N(N+1)/2 pairs in
+// one thread; on a mesh of a few hundred elements each SM holds one or two of
+// those threads' warps). The fluxes go to shared memory; then one thread per
+// (direction, node) sums its pairs in the line-owning kernel's order (the
+// other node's index ascending, then the lifting), and the directions are
+// added in order, so the result is bitwise that of volume_kernel.
 //
-// With FACES the same launch also evaluates the surface fluxes its element
-// needs (both faces in every direction, in shared memory) in warps of their
-// own that run beside the prologue: a whole rhs, or a whole Runge-Kutta stage
-// that writes its new state to another buffer (neighbours read the input
-// state), in one launch. Each face is then evaluated by both of its elements,
-// with the same function and inputs as the face kernel, so the result is the
-// same as with the face kernel.
-// G: directions per phase (0: all of them when their pair fluxes fit in
-// 96 KB, else one)
-template <int D, int N, int G = 0>
+// On this GPU a warp's FP64 instruction occupies its sub-partition's FP64
+// unit for 64 cycles (half a lane per cycle) whatever its active lanes, so a
+// CTA takes EPB elements at once and every phase packs its work items into
+// full warps (2D N = 3: two elements per CTA).
+//
+// With FACES the same launch also evaluates the surface fluxes its elements
+// need (both faces in every direction, in shared memory) in warps of their
+// own that run beside the prologue and the first pair phase: a whole rhs, or
+// a whole Runge-Kutta stage that writes its new state to another buffer
+// (neighbours read the input state), in one launch. Each face is then
+// evaluated by both of its elements, with the face kernel's arithmetic, so the
+// result is the same as with the face kernel.
+//
+// G: directions per phase (0: all of them when one element's pair fluxes fit
+// in 96 KB, else one); EPB: elements per CTA.
+template <int D, int N, int G = 0, int EPB = 1>
 struct PairPar {
   static constexpr int NP = N + 1, P = Shape<D, N>::P, LINES = Shape<D, N>::LINES,
                        NV = D + 2, NC = 3 + 2 * D;
   static constexpr int NPAIRS = N * (N + 1) / 2;
   static constexpr bool ALLDIRS = D * LINES * NPAIRS * NV * 8 <= 98304;
   static constexpr int GROUP = G > 0 ? G : (ALLDIRS ? D : 1);
-  static constexpr int WORK = GROUP * LINES * NPAIRS;
-  static constexpr int THREADS = WORK < 512 ? ((WORK + 31) / 32) * 32 : 512;
-  static constexpr int SMEM = (NC + NV + GROUP * NV) * P * 8 + WORK * NV * 8;
-  // FACES: face warps after the THREADS volume threads; each direction has
-  // FSTRIDE slots for its 2 LINES face nodes (both sides)
-  static constexpr int FSTRIDE = ((2 * LINES + 31) / 32) * 32;
-  static constexpr int THREADS_F = THREADS + D * FSTRIDE;
+  static constexpr int WORK = GROUP * LINES * NPAIRS;  // pair items per element and phase
+  // volume threads: the pair items of the CTA's elements, at most 512
+  static constexpr int THREADS = EPB * WORK < 512 ? ((EPB * WORK + 31) / 32) * 32 : 512;
+  static constexpr int ELEM_SMEM = (NC + NV + GROUP * NV) * P * 8 + WORK * NV * 8;
+  static constexpr int SMEM = EPB * ELEM_SMEM;
+  // FACES: face warps after the volume threads, one thread per face node of
+  // the elements' 2 D faces
+  static constexpr int FITEMS = EPB * 2 * D * LINES;
+  static constexpr int THREADS_F = THREADS + ((FITEMS + 31) / 32) * 32;
   static_assert(THREADS_F <= 1024, "face warps do not fit the CTA");
-  static constexpr int SMEM_F = SMEM + 2 * D * NV * LINES * 8;
+  static constexpr int SMEM_F = SMEM + EPB * 2 * D * NV * LINES * 8;
 };
+
+// elements per CTA of the one-launch kernel: enough to fill a warp with the
+// face nodes of the elements (at most 4)
+template <int D, int N>
+constexpr int pp_epb() {
+  constexpr int per = 2 * D * Shape<D, N>::LINES;
+  return per >= 32 ? 1 : (32 / per > 4 ? 4 : 32 / per);
+}
 
 template <int N>
 __device__ __forceinline__ void pp_pair_of(int p, int& a, int& b) {
@@ -516,63 +548,83 @@ __device__ __forceinline__ void pp_line_of(int dir, int node, int& l, int& i) {
   }
 }
 
-// The body for element e (every thread of the block calls it; it ends with a
-// barrier after its last shared-memory read, so a block may run it for one
-// element after another). smem: C::SMEM bytes (C::SMEM_F with FACES).
-template <int D, int N, int VF, bool FACES, int G>
-__device__ __forceinline__ void pp_element(double* u, double* __restrict__ du,
-                                           const double* __restrict__ fs, const Geom& g,
-                                           const Tables<double>& tb, unsigned* __restrict__ err,
-                                           const StageFuse& fz, int sfk, int e,
-                                           unsigned char* dg_smem) {
-  using C = PairPar<D, N, G>;
+// The body for the `count` (<= EPB) elements from e0 (every thread of the
+// block calls it; it ends with a barrier after its last shared-memory read,
+// so a block may run it for one batch after another). smem: C::SMEM bytes
+// (C::SMEM_F with FACES).
+template <int D, int N, int VF, bool FACES, int G, int EPB>
+__device__ __forceinline__ void pp_elements(double* u, double* __restrict__ du,
+                                            const double* __restrict__ fs, const Geom& g,
+                                            const Tables<double>& tb, unsigned* __restrict__ err,
+                                            const StageFuse& fz, int sfk, int e0, int count,
+                                            unsigned char* dg_smem) {
+  using C = PairPar<D, N, G, EPB>;
   constexpr int NP = C::NP, P = C::P, NV = C::NV, NC = C::NC, LINES = C::LINES,
-                NPAIRS = C::NPAIRS, GROUP = C::GROUP;
-  double(*sp)[P] = reinterpret_cast<double(*)[P]>(dg_smem);                          // [NC][P]
-  double(*sa)[P] = reinterpret_cast<double(*)[P]>(dg_smem + 8 * NC * P);             // [NV][P]
-  double(*sd)[NV][P] = reinterpret_cast<double(*)[NV][P]>(dg_smem + 8 * (NC + NV) * P);
-  double* sf = reinterpret_cast<double*>(dg_smem + 8 * (NC + NV + GROUP * NV) * P);  // [WORK][NV]
-  // FACES: [side][dir][c][l], side 0 the element's right face, 1 its left
-  // face; c in normal-first order
+                NPAIRS = C::NPAIRS, GROUP = C::GROUP, WORK = C::WORK;
+  // per element el: slots sp[NC][P], accumulators sa[NV][P], direction
+  // parts sd[GROUP][NV][P], pair fluxes sf[WORK][NV]; FACES: sfc[el] =
+  // [side][dir][c][l], side 0 the element's right face, 1 its left face, c in
+  // normal-first order
+  auto sp = [&](int el) {
+    return reinterpret_cast<double(*)[P]>(dg_smem + el * C::ELEM_SMEM);
+  };
+  auto sa = [&](int el) {
+    return reinterpret_cast<double(*)[P]>(dg_smem + el * C::ELEM_SMEM + 8 * NC * P);
+  };
+  auto sd = [&](int el) {
+    return reinterpret_cast<double(*)[NV][P]>(dg_smem + el * C::ELEM_SMEM + 8 * (NC + NV) * P);
+  };
+  auto sf = [&](int el) {
+    return reinterpret_cast<double*>(dg_smem + el * C::ELEM_SMEM +
+                                     8 * (NC + NV + GROUP * NV) * P);
+  };
   double* sfc = reinterpret_cast<double*>(dg_smem + C::SMEM);
   const int nelem = (int)g.nelem;
-  __shared__ int s_left[3];
-  if (threadIdx.x < D) s_left[threadIdx.x] = neighbour32(g, e, threadIdx.x, -1);
+  __shared__ int s_left[EPB][3];
+  for (int t = threadIdx.x; t < EPB * D; t += blockDim.x)
+    s_left[t / D][t % D] = t / D < count ? neighbour32(g, e0 + t / D, t % D, -1) : 0;
   // FACES: the first THREADS threads (the volume threads) do the prologue and
   // the first pair phase, synchronised among themselves by barrier 1, while
-  // the face warps (one direction per warp) evaluate the surface fluxes; all
-  // meet at the barrier before the first line sums
+  // the face warps evaluate the surface fluxes; all meet at the barrier
+  // before the first line sums
   const int wt = FACES ? C::THREADS : (int)blockDim.x;
   if (FACES && (int)threadIdx.x >= C::THREADS) {
-    const int t = (int)threadIdx.x - C::THREADS;
-    const int dir = t / C::FSTRIDE, r = t % C::FSTRIDE;
-    if (r < 2 * LINES) {
-      const int side = r / LINES, l = r % LINES;
-      const int owner = side == 0 ? e : neighbour32(g, e, dir, -1);
-      double f[NV];
-      if (dir == 0) face_flux_nf<D, N, double, 0>(u, g, sfk, owner, l, f);
-      else if (dir == 1) face_flux_nf<D, N, double, 1>(u, g, sfk, owner, l, f);
-      else face_flux_nf<D, N, double, (D == 3 ? 2 : 1)>(u, g, sfk, owner, l, f);
+    constexpr int PER = 2 * D * LINES;  // face nodes per element
+    for (int t = (int)threadIdx.x - C::THREADS; t < C::FITEMS;
+         t += (int)blockDim.x - C::THREADS) {
+      const int el = t / PER, r = t % PER;
+      if (el < count) {
+        const int side = r / (D * LINES), dir = (r / LINES) % D, l = r % LINES;
+        const int e = e0 + el;
+        const int owner = side == 0 ? e : neighbour32(g, e, dir, -1);
+        double f[NV];
+        face_flux_nf_dir<D, N, double>(dir, u, g, sfk, owner, l, f);
+        double* dst = sfc + (long long)el * PER * NV + (side * D + dir) * NV * LINES + l;
 #pragma unroll
-      for (int c = 0; c < NV; ++c) sfc[((side * D + dir) * NV + c) * LINES + l] = f[c];
+        for (int c = 0; c < NV; ++c) dst[c * LINES] = f[c];
+      }
     }
   }
   unsigned bad = 0;
-  for (int node = threadIdx.x; node < P && (int)threadIdx.x < wt; node += wt) {
+  for (int t = threadIdx.x; t < EPB * P && (int)threadIdx.x < wt; t += wt) {
+    const int el = t / P, node = t % P;
+    if (el >= count) continue;
+    const int e = e0 + el;
     double c[NV], rr;
 #pragma unroll
     for (int v = 0; v < NV; ++v) c[v] = u[((long long)e * NV + v) * P + node];
     const Prim<double, D> q = prim_rcp<D>(c, g.gm1, rr);
     bad |= prim_check(q);
-    node_slots<VF, double>(q.rho, q.p, g.gm1, sp[0][node], sp[1][node]);
-    sp[2][node] = 0.5 * q.p;
+    double(*spe)[P] = sp(el);
+    node_slots<VF, double>(q.rho, q.p, g.gm1, spe[0][node], spe[1][node]);
+    spe[2][node] = 0.5 * q.p;
 #pragma unroll
     for (int k = 0; k < D; ++k) {
-      sp[3 + k][node] = q.v[k];
-      sp[3 + D + k][node] = 0.5 * q.v[k];
+      spe[3 + k][node] = q.v[k];
+      spe[3 + D + k][node] = 0.5 * q.v[k];
     }
 #pragma unroll
-    for (int v = 0; v < NV; ++v) sa[v][node] = 0.0;
+    for (int v = 0; v < NV; ++v) sa(el)[v][node] = 0.0;
   }
   if (bad) atomicOr(err, bad);
   if (FACES) {
@@ -585,7 +637,10 @@ __device__ __forceinline__ void pp_element(double* u, double* __restrict__ du,
 #pragma unroll 1
   for (int d0 = 0; d0 < D; d0 += GROUP) {
     // pair fluxes of the group's directions, normal-first (volume threads)
-    for (int w = threadIdx.x; w < C::WORK && (int)threadIdx.x < wt; w += wt) {
+    for (int t = threadIdx.x; t < EPB * WORK && (int)threadIdx.x < wt; t += wt) {
+      const int el = t / WORK, w = t % WORK;
+      if (el >= count) continue;
+      double(*spe)[P] = sp(el);
       const int dir = d0 + w / (LINES * NPAIRS);
       const int rem = w % (LINES * NPAIRS);
       const int l = rem / NPAIRS;
@@ -594,48 +649,53 @@ __device__ __forceinline__ void pp_element(double* u, double* __restrict__ du,
       const int na = line_node_rt<D, N>(dir, l, a), nb = line_node_rt<D, N>(dir, l, b);
       const int t1 = (dir + 1) % D, t2 = (dir + 2) % D;
       LinePrim<double, D> qa, qb;
-      qa.s0 = sp[0][na];
-      qa.s1 = sp[1][na];
-      qa.hp = sp[2][na];
-      qa.vn = sp[3 + dir][na];
-      qa.hvn = sp[3 + D + dir][na];
-      qa.vt[0] = sp[3 + t1][na];
-      qa.hvt[0] = sp[3 + D + t1][na];
-      qb.s0 = sp[0][nb];
-      qb.s1 = sp[1][nb];
-      qb.hp = sp[2][nb];
-      qb.vn = sp[3 + dir][nb];
-      qb.hvn = sp[3 + D + dir][nb];
-      qb.vt[0] = sp[3 + t1][nb];
-      qb.hvt[0] = sp[3 + D + t1][nb];
+      qa.s0 = spe[0][na];
+      qa.s1 = spe[1][na];
+      qa.hp = spe[2][na];
+      qa.vn = spe[3 + dir][na];
+      qa.hvn = spe[3 + D + dir][na];
+      qa.vt[0] = spe[3 + t1][na];
+      qa.hvt[0] = spe[3 + D + t1][na];
+      qb.s0 = spe[0][nb];
+      qb.s1 = spe[1][nb];
+      qb.hp = spe[2][nb];
+      qb.vn = spe[3 + dir][nb];
+      qb.hvn = spe[3 + D + dir][nb];
+      qb.vt[0] = spe[3 + t1][nb];
+      qb.hvt[0] = spe[3 + D + t1][nb];
       if (D == 3) {
-        qa.vt[D - 2] = sp[3 + t2][na];
-        qa.hvt[D - 2] = sp[3 + D + t2][na];
-        qb.vt[D - 2] = sp[3 + t2][nb];
-        qb.hvt[D - 2] = sp[3 + D + t2][nb];
+        qa.vt[D - 2] = spe[3 + t2][na];
+        qa.hvt[D - 2] = spe[3 + D + t2][na];
+        qb.vt[D - 2] = spe[3 + t2][nb];
+        qb.hvt[D - 2] = spe[3 + D + t2][nb];
       }
       double f[NV], an = 0.0;
       if (VF == kVRanocha) ranocha_nf<double, D>(qa, qb, f, an);
       else generic_nf<VF, double, D>(qa, qb, gm1inv, f);
+      double* sfe = sf(el);
 #pragma unroll
-      for (int v = 0; v < NV; ++v) sf[w * NV + v] = f[v];
+      for (int v = 0; v < NV; ++v) sfe[w * NV + v] = f[v];
     }
     __syncthreads();
-    // per (direction, node): the line sum in the line-owning order, then the
-    // lifting (normal-first components back to variables)
-    for (int t = threadIdx.x; t < GROUP * P; t += blockDim.x) {
-      const int gd = t / P, node = t % P, dir = d0 + gd;
+    // per (element, direction, node): the line sum in the line-owning order,
+    // then the lifting (normal-first components back to variables)
+    for (int t = threadIdx.x; t < EPB * GROUP * P; t += blockDim.x) {
+      const int el = t / (GROUP * P), r = t % (GROUP * P);
+      if (el >= count) continue;
+      const int gd = r / P, node = r % P, dir = d0 + gd;
+      const int e = e0 + el;
       const int t1 = (dir + 1) % D, t2 = (dir + 2) % D;
       int l, i;
       pp_line_of<D, N>(dir, node, l, i);
       double acc[NV];
 #pragma unroll
       for (int v = 0; v < NV; ++v) acc[v] = 0.0;
+      const double* sfe = sf(el);
       for (int j = 0; j < NP; ++j) {
         if (j == i) continue;
         const int p = j < i ? pp_pair_index<N>(j, i) : pp_pair_index<N>(i, j);
         const double dij = tb.Ds[dir][i][j];
-        const double* fp = sf + ((gd * LINES + l) * NPAIRS + p) * NV;
+        const double* fp = sfe + ((gd * LINES + l) * NPAIRS + p) * NV;
 #pragma unroll
         for (int v = 0; v < NV; ++v) acc[v] = fma(dij, fp[v], acc[v]);
       }
@@ -645,11 +705,12 @@ __device__ __forceinline__ void pp_element(double* u, double* __restrict__ du,
       comp[2] = 1 + t1;
       if (D == 3) comp[D] = 1 + t2;
       comp[D + 1] = D + 1;
+      const double* fce = sfc + (long long)el * 2 * D * LINES * NV;
       if (i == N) {
 #pragma unroll
         for (int c = 0; c < NV; ++c)
           acc[c] = fma(tb.liftR[dir],
-                       FACES ? sfc[((0 * D + dir) * NV + c) * LINES + l]
+                       FACES ? fce[((0 * D + dir) * NV + c) * LINES + l]
                              : fs[(long long)(dir * NV + comp[c]) * base + (long long)e * LINES + l],
                        acc[c]);
       }
@@ -657,29 +718,34 @@ __device__ __forceinline__ void pp_element(double* u, double* __restrict__ du,
 #pragma unroll
         for (int c = 0; c < NV; ++c)
           acc[c] = fma(tb.liftL[dir],
-                       FACES ? sfc[((1 * D + dir) * NV + c) * LINES + l]
+                       FACES ? fce[((1 * D + dir) * NV + c) * LINES + l]
                              : fs[(long long)(dir * NV + comp[c]) * base +
-                                  (long long)s_left[dir] * LINES + l],
+                                  (long long)s_left[el][dir] * LINES + l],
                        acc[c]);
       }
+      double(*sde)[NV][P] = sd(el);
 #pragma unroll
-      for (int c = 0; c < NV; ++c) sd[gd][comp[c]][node] = acc[c];
+      for (int c = 0; c < NV; ++c) sde[gd][comp[c]][node] = acc[c];
     }
     __syncthreads();
     // the directions added in order, as the line-owning kernel does
-    for (int t = threadIdx.x; t < NV * P; t += blockDim.x) {
-      const int v = t / P, node = t % P;
+    for (int t = threadIdx.x; t < EPB * NV * P; t += blockDim.x) {
+      const int el = t / (NV * P), r = t % (NV * P);
+      if (el >= count) continue;
+      const int v = r / P, node = r % P;
 #pragma unroll
-      for (int gd = 0; gd < GROUP; ++gd) sa[v][node] += sd[gd][v][node];
+      for (int gd = 0; gd < GROUP; ++gd) sa(el)[v][node] += sd(el)[gd][v][node];
     }
     __syncthreads();
   }
+  // epilogue: the CTA's elements are contiguous in the state
   const double dtv = fz.k ? *fz.dt : 0.0;
   double* const uo = fz.u_out ? fz.u_out : u;
-  for (int t = threadIdx.x; t < NV * P; t += blockDim.x) {
-    const int v = t / P, node = t % P;
-    const double val = sa[v][node];
-    const long long i = ((long long)e * NV + v) * P + node;
+  for (int t = threadIdx.x; t < count * NV * P; t += blockDim.x) {
+    const int el = t / (NV * P), r = t % (NV * P);
+    const int v = r / P, node = r % P;
+    const double val = sa(el)[v][node];
+    const long long i = (long long)e0 * NV * P + t;
     if (fz.k) {
       double kk = dtv * val;
       if (fz.a != 0.0) kk = fma(fz.a, fz.k[i], kk);
@@ -692,12 +758,16 @@ __device__ __forceinline__ void pp_element(double* u, double* __restrict__ du,
   __syncthreads();
 }
 
-template <int D, int N, int VF, bool FACES>
-__global__ void __launch_bounds__(FACES ? PairPar<D, N>::THREADS_F : PairPar<D, N>::THREADS)
+template <int D, int N, int VF, bool FACES, int EPB>
+__global__ void __launch_bounds__(FACES ? PairPar<D, N, 0, EPB>::THREADS_F
+                                        : PairPar<D, N, 0, EPB>::THREADS)
     volume_pp_kernel(double* u, double* __restrict__ du, const double* __restrict__ fs, Geom g,
                      Tables<double> tb, unsigned* __restrict__ err, StageFuse fz, int sfk) {
   extern __shared__ __align__(16) unsigned char dg_smem[];
-  pp_element<D, N, VF, FACES, 0>(u, du, fs, g, tb, err, fz, sfk, blockIdx.x, dg_smem);
+  const int e0 = blockIdx.x * EPB;
+  const int left = (int)g.nelem - e0;
+  pp_elements<D, N, VF, FACES, 0, EPB>(u, du, fs, g, tb, err, fz, sfk, e0,
+                                       left < EPB ? left : EPB, dg_smem);
 }
 
 }  // namespace dg
@@ -763,12 +833,14 @@ template <int D, int N, int VF, bool FACES>
 cudaError_t launch_volume_pp_vf(const double* u, double* du, double* fs, const Geom& g,
                                 const Tables<double>& tb, int sf, unsigned* err, cudaStream_t st,
                                 const StageFuse& fz) {
-  using C = PairPar<D, N>;
+  constexpr int EPB = FACES ? pp_epb<D, N>() : 1;
+  using C = PairPar<D, N, 0, EPB>;
   constexpr int threads = FACES ? C::THREADS_F : C::THREADS;
   constexpr int smem = FACES ? C::SMEM_F : C::SMEM;
   cudaError_t e;
-  if ((e = allow_smem(volume_pp_kernel<D, N, VF, FACES>, smem)) != cudaSuccess) return e;
-  volume_pp_kernel<D, N, VF, FACES><<<(unsigned)g.nelem, threads, smem, st>>>(
+  if ((e = allow_smem(volume_pp_kernel<D, N, VF, FACES, EPB>, smem)) != cudaSuccess) return e;
+  const unsigned grid = (unsigned)((g.nelem + EPB - 1) / EPB);
+  volume_pp_kernel<D, N, VF, FACES, EPB><<<grid, threads, smem, st>>>(
       const_cast<double*>(u), du, fs, g, tb, err, fz, sf);
   return cudaGetLastError();
 }
