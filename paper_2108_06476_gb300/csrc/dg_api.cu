@@ -282,19 +282,23 @@ __device__ __forceinline__ void speed_node(const double* c, int D, const Geom& g
 // mapped host buffer here once and continues on the device copy. dt
 // (optional): the last block to finish (a ticket in out[1]) also computes
 // dt = cfl 2 / ((N+1) worst) and clears out[0] and out[1], as dt_kernel does.
+// epw elements per warp (32 / P when P is 4, 8 or 16, else 1): each element
+// takes a segment of 32 / epw lanes, so that FP64 work fills the warps
 template <int D, typename R>
-__global__ void speed_kernel(const double* __restrict__ u, Geom g, int P, double s0, double s1,
-                             double s2, unsigned long long* out, unsigned* err,
+__global__ void speed_kernel(const double* __restrict__ u, Geom g, int P, int epw, double s0,
+                             double s1, double s2, unsigned long long* out, unsigned* err,
                              double* __restrict__ copy_to, int N, double cfl, double* dt) {
   constexpr int NV = D + 2;
   const int lane = threadIdx.x & 31;
+  const int seg = 32 / epw, sub = lane / seg;
   const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
   double best = 0.0;
   unsigned bad = 0;
-  for (long long e = warp; e < g.nelem; e += nwarps) {
+  for (long long eb = warp * epw; eb < g.nelem; eb += nwarps * epw) {
+    const long long e = eb + sub;
     R lamr[3] = {R(0), R(0), R(0)};
-    for (int node = lane; node < P; node += 32) {
+    for (int node = lane % seg; node < P && e < g.nelem; node += seg) {
       double c[NV];
 #pragma unroll
       for (int v = 0; v < NV; ++v) c[v] = u[(e * NV + v) * P + node];
@@ -308,7 +312,7 @@ __global__ void speed_kernel(const double* __restrict__ u, Geom g, int P, double
 #pragma unroll
     for (int k = 0; k < D; ++k) {
       lam[k] = (double)lamr[k];
-      for (int off = 16; off > 0; off >>= 1)
+      for (int off = seg / 2; off > 0; off >>= 1)
         lam[k] = fmax(lam[k], __shfl_xor_sync(0xffffffffu, lam[k], off));
     }
     double s = s0 * lam[0];
@@ -467,7 +471,7 @@ int launch_speed(dg_mesh* m, const double* u, double* copy_to = nullptr, double 
   // one warp per element; small meshes get one-warp blocks so that the FP64
   // work (2 lanes per clock per SM) spreads over more SMs
   const int threads = (m->nelem * 32 < 152LL * 4 * 256) ? 32 : 256;
-  const int grid = grid_for(m->nelem * 32, threads);
+  int grid = grid_for(m->nelem * 32, threads);
   if (m->mhd && m->curved) {
     DG_CUDA(dg::mhd_curved_speed_launch(u, m->Ja, m->invJ, m->geom, (int)m->P, m->speed, m->err,
                                         copy_to, grid, threads, m->stream),
@@ -490,22 +494,25 @@ int launch_speed(dg_mesh* m, const double* u, double* copy_to = nullptr, double 
   const double s0 = 2.0 / m->h[0], s1 = 2.0 / m->h[1], s2 = 2.0 / m->h[2];
   const bool f32 = m->opt.precision == DG_FP32;
   double* dt = cfl > 0.0 ? m->dt_dev : nullptr;
+  const int P = (int)m->P;
+  const int epw = (P == 4 || P == 8 || P == 16) ? 32 / P : 1;
+  if (epw > 1) grid = grid_for((m->nelem + epw - 1) / epw * 32, threads);
   if (m->d == 2) {
     if (f32)
-      speed_kernel<2, float><<<grid, threads, 0, m->stream>>>(u, m->geom, (int)m->P, s0, s1, s2,
+      speed_kernel<2, float><<<grid, threads, 0, m->stream>>>(u, m->geom, P, epw, s0, s1, s2,
                                                               m->speed, m->err, copy_to, m->N,
                                                               cfl, dt);
     else
-      speed_kernel<2, double><<<grid, threads, 0, m->stream>>>(u, m->geom, (int)m->P, s0, s1, s2,
+      speed_kernel<2, double><<<grid, threads, 0, m->stream>>>(u, m->geom, P, epw, s0, s1, s2,
                                                                m->speed, m->err, copy_to, m->N,
                                                                cfl, dt);
   } else {
     if (f32)
-      speed_kernel<3, float><<<grid, threads, 0, m->stream>>>(u, m->geom, (int)m->P, s0, s1, s2,
+      speed_kernel<3, float><<<grid, threads, 0, m->stream>>>(u, m->geom, P, epw, s0, s1, s2,
                                                               m->speed, m->err, copy_to, m->N,
                                                               cfl, dt);
     else
-      speed_kernel<3, double><<<grid, threads, 0, m->stream>>>(u, m->geom, (int)m->P, s0, s1, s2,
+      speed_kernel<3, double><<<grid, threads, 0, m->stream>>>(u, m->geom, P, epw, s0, s1, s2,
                                                                m->speed, m->err, copy_to, m->N,
                                                                cfl, dt);
   }
