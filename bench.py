@@ -59,6 +59,15 @@ def nominal_peaks(sms):
 PEAKS = {}
 
 
+def measured_hbm_gbs():
+    """The copy bandwidth of this machine's GPUs (MEASURED_PEAKS.json), or None."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["hbm_gbs"])
+    except (OSError, ValueError, KeyError, TypeError):
+        return None
+
+
 def measured_peaks():
     """FP64/FP32 FMA throughput and SM count, measured once per process."""
     if not PEAKS:
@@ -818,7 +827,7 @@ def run_ours(args, spec, world, rank, local):
         import torch.distributed as dist
         dist.init_process_group("nccl", init_method="env://")
     torch.cuda.set_device(local)
-    from paper_2108_06476_gb300 import Mesh, lgl_nodes, build as dgbuild
+    from paper_2108_06476_gb300 import Mesh, RK_A, RK_B, lgl_nodes, build as dgbuild
     dgbuild.build()
     d, N, ne = spec["d"], spec["N"], spec["ne"]
     n = (ne,) * d
@@ -828,6 +837,8 @@ def run_ours(args, spec, world, rank, local):
     peaks = measured_peaks()
     FP64_PEAK = peaks["fp64_tflops"]
     FP32_PEAK = peaks["fp32_tflops"]
+    from paper_2108_06476_gb300 import measure_fp64_issue
+    fp64_issue = measure_fp64_issue()
     mesh = Mesh(d, N, n, precision="fp64")
     u0 = torch.from_numpy(u_host).cuda()
     checks = []
@@ -863,7 +874,9 @@ def run_ours(args, spec, world, rank, local):
         ms = timed(lambda: run_steps(mesh, u, du, args.steps))
     mesh.check()
     value = job_value(M, 5, args.steps, world, ms)
-    launches_per_step = 2 + 5 * 2
+    # the wave-speed pass (it also writes dt) and five stages of a face and a
+    # volume kernel
+    launches_per_step = 1 + 5 * 2
 
     # ---- kernel timings (dominant kernel: volume) ----
     def kernel_ms(m, uu, dd, part, reps=10):
@@ -908,6 +921,35 @@ def run_ours(args, spec, world, rank, local):
         c_ach = counted_node * M / (vol_ms / 1e3) / 1e12
         counted = {"flops_per_node": counted_node, "achieved": c_ach,
                    "frac": c_ach / FP64_PEAK}
+
+    # ---- the memory-streaming kernels on the headline mesh ----
+    # stand-alone stage update (dg_rk_stage: u, k and du read, k and u
+    # written, 200 B per node; the step fuses it into the volume kernel) and
+    # the compensated integrals (u read, 40 B per node; double-double sums
+    # and two logarithms per node in FP64), against the measured copy
+    # bandwidth
+    streaming = None
+    if not args.no_streaming:
+        hbm = measured_hbm_gbs()
+        u2 = u.clone()
+        reps = 10
+        mesh.rk_reset()  # k = 0: the timed updates stay tiny (dt 1e-9)
+        mesh.rk_stage(u2, du, RK_A[1], RK_B[1], 1.0e-9)
+        ms_rk = timed(lambda: [mesh.rk_stage(u2, du, RK_A[1], RK_B[1], 1.0e-9)
+                               for _ in range(reps)]) / reps
+        mesh.rk_reset()
+        mesh.integrals(u2)
+        ms_int = timed(lambda: [mesh.integrals(u2) for _ in range(3)]) / 3
+        del u2
+        b_rk, b_int = 5 * (d + 2) * 8 * M, (d + 2) * 8 * M
+        streaming = {
+            "hbm_peak_gbs": hbm, "hbm_peak_source": "MEASURED_PEAKS.json (copy, read + write)",
+            "rk_stage": {"ms": ms_rk, "bytes": b_rk, "gbs": b_rk / ms_rk / 1e6,
+                         "frac": None if hbm is None else b_rk / ms_rk / 1e6 / hbm},
+            "integrals": {"ms": ms_int, "bytes": b_int, "gbs": b_int / ms_int / 1e6,
+                          "frac": None if hbm is None else b_int / ms_int / 1e6 / hbm,
+                          "note": "includes the host read of the 7 sums; FP64 arithmetic "
+                                  "(two logs and seven double-double sums per node)"}}
 
     # ---- FP32 kernels with FP64 state and RK accumulation ----
     fp32 = None
@@ -1006,10 +1048,14 @@ def run_ours(args, spec, world, rank, local):
                                       "square root one each") if oc else "hand count",
                      "flops_per_node_hand_count_rhs": flops_hand,
                      "kernel_ms": vol_ms,
-                     "counted": counted},
+                     "counted": counted,
+                     "fp64_issue_cycles": dict(fp64_issue, note=(
+                         "SM cycles per dependent FP64 FMA, one warp per SM, 32 active lanes "
+                         "and one (dg_measure_fp64_issue)"))},
         "kernels_ms": {"volume_fused_stage": vol_ms, "volume_rhs_only": rhs_vol_ms,
                        "surface": surf_ms},
         "rhs_only": rhs_only,
+        "streaming_kernels": streaming,
         "fp32": fp32,
         "ensemble": ensemble,
         "vjp": vjp,
@@ -1053,6 +1099,7 @@ def main():
                     help="MHD section: elements per dimension of the Alfven-wave mesh")
     ap.add_argument("--no-ensemble", action="store_true")
     ap.add_argument("--no-vjp", action="store_true")
+    ap.add_argument("--no-streaming", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -410,6 +410,15 @@ int dg_ensemble_tune(dg_ensemble *ens, const double *u, double *u_tmp, int *best
  * Errors: DG_ERR_CUDA, DG_ERR_ARG (a device of more than 256 SMs). */
 int dg_measure_peaks(double *fp64_tflops, double *fp32_tflops, int *sm_count, void *cuda_stream);
 
+/* Measurement helper behind the layout of the small-mesh kernels (no paper
+ * counterpart): the SM cycles per step of one dependent FP64 FMA chain run by
+ * one warp per SM with all 32 lanes active (cycles_full_warp) and with one
+ * lane active (cycles_one_lane), read with clock64 in the kernel. Equal
+ * values mean that a warp's FP64 instruction costs the same whatever its
+ * active lanes. Synchronous on cuda_stream; allocates nothing (a static
+ * device array of two counters). Errors: DG_ERR_CUDA. Outputs may be NULL. */
+int dg_measure_fp64_issue(double *cycles_full_warp, double *cycles_one_lane, void *cuda_stream);
+
 /* Self-check of the library's device arithmetic helpers (no paper
  * counterpart; for the test suite): y[i] = f(x[i]) for n device doubles,
  * evaluated by the same device functions the kernels use:

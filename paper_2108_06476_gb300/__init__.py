@@ -6,5 +6,6 @@ low-storage RK stage, as hand-written CUDA kernels for sm_103a behind the C
 ABI in include/dgsem.h. This package holds the in-tree build script, the
 ctypes binding and the seeded workload generators.
 """
-from .dgsem import Mesh, Ensemble, MeshSpec, DGError, lgl_nodes, load, measure_peaks, RK_A, RK_B, SO_PATH  # noqa: F401
+from .dgsem import (Mesh, Ensemble, MeshSpec, DGError, lgl_nodes, load, measure_peaks,  # noqa: F401
+                    measure_fp64_issue, RK_A, RK_B, SO_PATH)
 from . import workloads  # noqa: F401

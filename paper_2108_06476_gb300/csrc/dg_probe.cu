@@ -102,6 +102,47 @@ extern "C" int dg_measure_peaks(double* fp64_tflops, double* fp32_tflops, int* s
   return rc;
 }
 
+// ---- issue cost of one FP64 warp instruction ----
+namespace {
+
+__device__ long long g_probe_cycles[2];
+
+// one dependent DFMA chain per thread of `active` lanes (the others leave at
+// once); thread 0 of block 0 records the SM cycles of `iters` steps
+__global__ void dfma_chain_kernel(int iters, int active, int slot) {
+  if ((int)(threadIdx.x & 31) >= active) return;
+  double x = 1.0 + 1e-9 * threadIdx.x;
+  const long long t0 = clock64();
+  for (int i = 0; i < iters; ++i) x = fma(x, 0.9999999, 1e-7);
+  const long long t1 = clock64();
+  if (blockIdx.x == 0 && threadIdx.x == 0) g_probe_cycles[slot] = x == -1.0 ? 0 : t1 - t0;
+}
+
+}  // namespace
+
+extern "C" int dg_measure_fp64_issue(double* cycles_full_warp, double* cycles_one_lane,
+                                     void* cuda_stream) {
+  int dev = 0, nsm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return dg::set_last_error(DG_ERR_CUDA, "dg_measure_fp64_issue: device query failed");
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  const int iters = 4096;
+  // one warp per SM: 32 active lanes, then one
+  dfma_chain_kernel<<<nsm, 32, 0, st>>>(16, 32, 0);
+  dfma_chain_kernel<<<nsm, 32, 0, st>>>(iters, 32, 0);
+  dfma_chain_kernel<<<nsm, 32, 0, st>>>(iters, 1, 1);
+  long long c[2] = {0, 0};
+  if (cudaGetLastError() != cudaSuccess ||
+      cudaMemcpyFromSymbolAsync(c, g_probe_cycles, sizeof(c), 0, cudaMemcpyDeviceToHost, st) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return dg::set_last_error(DG_ERR_CUDA, "dg_measure_fp64_issue: probe failed");
+  if (cycles_full_warp) *cycles_full_warp = (double)c[0] / iters;
+  if (cycles_one_lane) *cycles_one_lane = (double)c[1] / iters;
+  return DG_OK;
+}
+
 // ---- self-check of the device arithmetic helpers ----
 #include "dg_f32.cuh"
 

@@ -39,7 +39,8 @@ EXPORTS = ("dg_mesh_create", "dg_mesh_create_curved", "dg_mesh_create_mhd",
            "dg_ensemble_rk_reset", "dg_ensemble_check", "dg_ensemble_set_block",
            "dg_ensemble_get_block", "dg_ensemble_tune", "dg_measure_peaks",
            "dg_selftest_arith", "dg_mesh_set_nodes", "dg_mesh_set_metric",
-           "dg_ensemble_set_pair_parallel", "dg_ensemble_get_pair_parallel")
+           "dg_ensemble_set_pair_parallel", "dg_ensemble_get_pair_parallel",
+           "dg_measure_fp64_issue")
 
 
 class DGError(RuntimeError):
@@ -112,6 +113,7 @@ def load(path: str = SO_PATH):
     L.dg_ensemble_set_pair_parallel.argtypes = [vp, ctypes.c_int]
     L.dg_ensemble_get_pair_parallel.argtypes = [vp, ip]
     L.dg_measure_peaks.argtypes = [dp, dp, ip, vp]
+    L.dg_measure_fp64_issue.argtypes = [dp, dp, vp]
     L.dg_selftest_arith.argtypes = [ctypes.c_int, vp, vp, ctypes.c_longlong, vp]
     L.dg_mesh_set_nodes.argtypes = [vp, vp]
     L.dg_mesh_set_metric.argtypes = [vp, vp, vp]
@@ -142,6 +144,17 @@ def measure_peaks(fp64=True, fp32=True, stream=None):
            "dg_measure_peaks")
     return {"fp64_tflops": a.value if fp64 else None, "fp32_tflops": b.value if fp32 else None,
             "sm_count": n.value}
+
+
+def measure_fp64_issue(stream=None):
+    """SM cycles per dependent FP64 FMA of one warp per SM with 32 active
+    lanes and with one (dg_measure_fp64_issue)."""
+    import torch
+    a, b = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    st = stream if stream is not None else torch.cuda.current_stream()
+    _check(load().dg_measure_fp64_issue(ctypes.byref(a), ctypes.byref(b),
+                                        ctypes.c_void_p(st.cuda_stream)), "dg_measure_fp64_issue")
+    return {"cycles_full_warp": a.value, "cycles_one_lane": b.value}
 
 
 def lgl_nodes(N: int):
