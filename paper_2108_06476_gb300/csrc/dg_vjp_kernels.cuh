@@ -478,15 +478,31 @@ __global__ void __launch_bounds__(EPB* Shape<D, N>::LINES)
   }
 }
 
+// elements per CTA of the VJP volume kernels (one thread per element line):
+// about 64 threads, unless their warps would leave more than a tenth of the
+// lanes idle (a warp's FP64 instruction costs the same whatever its active
+// lanes); then the count of at most 256 threads and 96 KB of shared memory
+// that fills the warps best
+template <int LINES, int PER>
+constexpr int vjp_epb() {
+  constexpr int byt = (64 / LINES) > 0 ? (64 / LINES) : 1;
+  constexpr int bys = (98304 / PER) > 0 ? (98304 / PER) : 1;
+  constexpr int base = byt < bys ? byt : bys;
+  auto fill = [](int t) { return (double)t / (32.0 * ((t + 31) / 32)); };
+  if (fill(base * LINES) >= 0.9) return base;
+  int best = base;
+  for (int e = 1; e * LINES <= 256 && e * PER <= 98304; ++e)
+    if (fill(e * LINES) > fill(best * LINES) + 0.01) best = e;
+  return best;
+}
+
 template <int D, int N, typename R>
 cudaError_t launch_vjp_dn(const double* u, const double* w, double* ubar, double* fb,
                           const Geom& g, const Tables<double>& tb, int vf, int sf,
                           cudaStream_t st) {
   using S = Shape<D, N>;
   constexpr int PER = 3 * S::NV * S::P * (int)sizeof(double);
-  constexpr int BYT = (64 / S::LINES) > 0 ? (64 / S::LINES) : 1;
-  constexpr int BYS = (98304 / PER) > 0 ? (98304 / PER) : 1;
-  constexpr int EPB = BYT < BYS ? BYT : BYS;
+  constexpr int EPB = vjp_epb<S::LINES, PER>();
   constexpr int SM = EPB * PER;
   {
     const long long total = g.nelem * S::LINES;
