@@ -18,6 +18,10 @@
 //    coalesced store of du, or the fused stage update k <- A k + dt du,
 //    u <- u + B k.
 //
+//  volume_pp_kernel (FP64 meshes under kPairParallelElems elements): one
+//    thread per node pair instead of per line; with FACES it also evaluates
+//    its elements' face fluxes, so that a whole rhs or stage is one launch.
+//
 // These templates are instantiated for FP64 meshes; FP32 meshes run the
 // perturbation-form kernels of dg_rhs32.cuh.
 #pragma once
@@ -908,11 +912,14 @@ cudaError_t launch_volume32_epb(const double* u, float* du, float* fs, const Geo
   return cudaGetLastError();
 }
 
-// Meshes with fewer elements than about two CTAs per SM run one element per
-// CTA (and the face kernel in 64-thread blocks), spreading the FP64 work (2
-// lanes per clock per SM) over more SMs; the arithmetic per node, and so the
-// result, is the same. FP32 meshes first write the per-element references
-// (part 1), which both flux kernels read.
+// FP64 meshes under kPairParallelElems elements run a whole rhs (parts = 3),
+// or a stage whose output buffer is not its input, as one launch of the
+// pair-parallel kernel with its face fluxes; the separate parts stay
+// available. Other meshes with fewer elements than about two CTAs per SM run
+// one element per CTA (and the face kernel in 64-thread blocks), spreading
+// the FP64 work (2 lanes per clock per SM) over more SMs; the arithmetic per
+// node, and so the result, is the same. FP32 meshes first write the
+// per-element references (part 1), which both flux kernels read.
 template <int D, int N, typename R>
 cudaError_t launch_rhs_dn(const double* u, R* du, R* fs, const Geom& g, const Tables<R>& tb,
                           int vf, int sf, unsigned* err, cudaStream_t st, int parts,
