@@ -179,6 +179,45 @@ __device__ __forceinline__ unsigned prim_check(const Prim<R, D>& q) {
   return bad;
 }
 
+// ---- FP64 <-> FP32 conversions on the integer pipe ----
+// The FP64 pipe (2 lanes per clock per SM on this part) also executes the
+// hardware conversions between double and float, which would otherwise take
+// a third of the FP64 work of the FP32 kernels (and the FP64 kernels'
+// polynomial tails below). These rebuild the IEEE 754
+// bit patterns instead (binary64: 1 sign, 11 exponent bits with bias 1023,
+// 52 fraction bits; binary32: 1, 8 with bias 127, 23): for results in the
+// normal range and for zeros; everything else (subnormals, overflow, inf,
+// NaN) takes the hardware conversion out of line.
+static __device__ __noinline__ float d2f_slow(double x) { return (float)x; }
+static __device__ __noinline__ double f2d_slow(float x) { return (double)x; }
+
+// double -> float, rounded to nearest (ties to even)
+__device__ __forceinline__ float d2f(double x) {
+  const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
+  const unsigned hi = (unsigned)(bits >> 32), lo = (unsigned)bits;
+  const unsigned e = (hi >> 20) & 0x7ffu;
+  if (e - 897u < 253u) {  // float exponent 1..253: no overflow after rounding
+    const unsigned m = ((hi & 0xfffffu) << 3) | (lo >> 29);  // top 23 fraction bits
+    const unsigned rest = lo & 0x1fffffffu;                   // the 29 dropped bits
+    unsigned f = (hi & 0x80000000u) | ((e - 896u) << 23) | m;
+    f += (rest > 0x10000000u) | ((rest == 0x10000000u) & (m & 1u));  // carries into e
+    return __uint_as_float(f);
+  }
+  if (((hi << 1) | lo) == 0u) return __uint_as_float(hi & 0x80000000u);  // +-0
+  return d2f_slow(x);
+}
+
+// float -> double (exact)
+__device__ __forceinline__ double f2d(float x) {
+  const unsigned b = __float_as_uint(x);
+  const unsigned fe = (b >> 23) & 0xffu;
+  if (fe - 1u < 254u)  // normal
+    return __hiloint2double((int)((b & 0x80000000u) | ((fe + 896u) << 20) | ((b & 0x7fffffu) >> 3)),
+                            (int)(b << 29));
+  if ((b << 1) == 0u) return __hiloint2double((int)(b & 0x80000000u), 0);  // +-0
+  return f2d_slow(x);
+}
+
 // ---- logarithmic mean ----
 // ln_mean(x, y) = (y - x) / ln(y / x). With s = x + y, t = (y - x)/s and
 // f2 = t^2, ln(y/x) = 2 atanh(t), so
@@ -219,6 +258,31 @@ __device__ __forceinline__ double s_short(double f2) {
   double r = 0.15791323599162152;
   r = fma(f2, r, 0.18177218144198024);
   r = fma(f2, r, 0.22222246134174709);
+  r = fma(f2, r, 0.28571428515311326);
+  r = fma(f2, r, 0.4000000000004813);
+  r = fma(f2, r, 0.6666666666666666);
+  return fma(f2, r, 2.0);
+}
+// q_short and s_short with the terms of high degree summed in FP32, the
+// rest by the same Horner scheme in FP64 (the FP64 kernels are bound by
+// their FP64 unit; the FP32 pipe has room): Q from f2^4 (|c_4| f2^4 <=
+// 3e-10 on [0, 1e-2], so the tail's FP32 rounding stays below 3e-17 of Q),
+// S from f2^5 (below 2e-18 of S). Same coefficients, the tail's rounded to
+// FP32.
+__device__ __forceinline__ double q_short_mixed(double f2) {
+  const float f = d2f(f2);
+  float t = -0.01719901874634888f;
+  t = fmaf(f, t, -0.021792151641765893f);
+  t = fmaf(f, t, -0.030194027707754922f);
+  double r = fma(f2, f2d(t), -0.0465608465041037);
+  r = fma(f2, r, -0.08888888888893755);
+  r = fma(f2, r, -0.3333333333333333);
+  return fma(f2, r, 1.0);
+}
+__device__ __forceinline__ double s_short_mixed(double f2) {
+  const float f = d2f(f2);
+  const float t = fmaf(f, 0.15791323599162152f, 0.18177218144198024f);
+  double r = fma(f2, f2d(t), 0.22222246134174709);
   r = fma(f2, r, 0.28571428515311326);
   r = fma(f2, r, 0.4000000000004813);
   r = fma(f2, r, 0.6666666666666666);
@@ -289,7 +353,7 @@ __device__ __forceinline__ double f2_of(float t) {
 __device__ __forceinline__ double q_of(double f2, double) {
   double q;
   if (in_short(f2))
-    q = q_short(f2);
+    q = q_short_mixed(f2);
   else
     q = q_long(f2);
   return q;
@@ -297,7 +361,7 @@ __device__ __forceinline__ double q_of(double f2, double) {
 __device__ __forceinline__ double s_of(double f2, double) {
   double S;
   if (in_short(f2))
-    S = s_short(f2);
+    S = s_short_mixed(f2);
   else
     S = s_long(f2);
   return S;

@@ -95,44 +95,6 @@ static __device__ __noinline__ float q_any32(float t) {
   return 2.0f * t / log1pf(2.0f * t / (1.0f - t));
 }
 
-// ---- FP64 <-> FP32 conversions on the integer pipe ----
-// The FP64 pipe (2 lanes per clock per SM on this part) also executes the
-// hardware conversions between double and float, which would otherwise take
-// a third of the FP64 work of the FP32 kernels. These rebuild the IEEE 754
-// bit patterns instead (binary64: 1 sign, 11 exponent bits with bias 1023,
-// 52 fraction bits; binary32: 1, 8 with bias 127, 23): for results in the
-// normal range and for zeros; everything else (subnormals, overflow, inf,
-// NaN) takes the hardware conversion out of line.
-static __device__ __noinline__ float d2f_slow(double x) { return (float)x; }
-static __device__ __noinline__ double f2d_slow(float x) { return (double)x; }
-
-// double -> float, rounded to nearest (ties to even)
-__device__ __forceinline__ float d2f(double x) {
-  const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
-  const unsigned hi = (unsigned)(bits >> 32), lo = (unsigned)bits;
-  const unsigned e = (hi >> 20) & 0x7ffu;
-  if (e - 897u < 253u) {  // float exponent 1..253: no overflow after rounding
-    const unsigned m = ((hi & 0xfffffu) << 3) | (lo >> 29);  // top 23 fraction bits
-    const unsigned rest = lo & 0x1fffffffu;                   // the 29 dropped bits
-    unsigned f = (hi & 0x80000000u) | ((e - 896u) << 23) | m;
-    f += (rest > 0x10000000u) | ((rest == 0x10000000u) & (m & 1u));  // carries into e
-    return __uint_as_float(f);
-  }
-  if (((hi << 1) | lo) == 0u) return __uint_as_float(hi & 0x80000000u);  // +-0
-  return d2f_slow(x);
-}
-
-// float -> double (exact)
-__device__ __forceinline__ double f2d(float x) {
-  const unsigned b = __float_as_uint(x);
-  const unsigned fe = (b >> 23) & 0xffu;
-  if (fe - 1u < 254u)  // normal
-    return __hiloint2double((int)((b & 0x80000000u) | ((fe + 896u) << 20) | ((b & 0x7fffffu) >> 3)),
-                            (int)(b << 29));
-  if ((b << 1) == 0u) return __hiloint2double((int)(b & 0x80000000u), 0);  // +-0
-  return f2d_slow(x);
-}
-
 // element reference in normal-first order for one direction
 template <int D>
 struct DRef {

@@ -142,3 +142,42 @@ def test_range_limits(header):
     # every polynomial covers the range that selects it
     for name, lim in (("q_short", 1e-2), ("s_short", 1e-2), ("q_long", 0.25), ("s_long", 0.25)):
         assert float(polynomial(header, "double", name)[1]) >= lim
+
+
+# The FP64 kernels evaluate the short-range polynomials with their tail in
+# FP32 (q_short_mixed from f2^4, s_short_mixed from f2^5): the same
+# coefficients, the tail's rounded to FP32, and the evaluation (FP32 Horner
+# tail, FP64 Horner head) within 3e-17 of Q and 2e-18 of S over [0, 1e-2],
+# emulated here with exact decimal arithmetic and FP32 rounding of every
+# tail operation.
+def _f32(x):
+    return Decimal(float(np.float32(float(x))))
+
+
+@pytest.mark.parametrize("name,mixed,split,ref,bound",
+                         [("q_short", "q_short_mixed", 4, Q_ref, 3e-17),
+                          ("s_short", "s_short_mixed", 5, S_ref, 2e-18)])
+def test_mixed_precision_short_polynomials(header, name, mixed, split, ref, bound):
+    coeffs = polynomial(header, "double", name)[0]
+    body = _body(header, f"double {mixed}(double f2)")
+    # the tail's literals carry the f suffix (rounded to FP32 by the
+    # compiler) and are the double coefficients as written; the head's are
+    # the double coefficients
+    flits = [float(x) for x in re.findall(r"(-?\d+\.\d*(?:e-?\d+)?)f[;),]", body)]
+    dlits = [float(x) for x in re.findall(r"(-?\d+\.\d*(?:e-?\d+)?)[;),]", body)]
+    assert sorted(flits) == sorted(coeffs[split:]), (flits, coeffs)
+    assert sorted(dlits) == sorted(coeffs[:split]), (dlits, coeffs)
+    tail = [float(np.float32(c)) for c in coeffs[split:]]
+    head = coeffs[:split]
+    worst = Decimal(0)
+    for k in range(401):
+        x = Decimal(1e-2) * k / 400
+        xf = _f32(x)
+        t = Decimal(tail[-1])
+        for c in reversed(tail[:-1]):
+            t = _f32(xf * t + Decimal(c))  # one FP32 fused multiply-add
+        p = t
+        for c in reversed(head):
+            p = p * x + Decimal(c)
+        worst = max(worst, abs(p / ref(x) - 1))
+    assert float(worst) <= bound, (mixed, float(worst))
