@@ -218,6 +218,22 @@ __device__ __forceinline__ double f2d(float x) {
   return f2d_slow(x);
 }
 
+// ---- halving ----
+// x / 2 of a double by decrementing its exponent field on the integer pipe:
+// exact, the same value as 0.5 * x, for normal x above the smallest
+// exponent; infinities, NaNs and zeros are their own halves; subnormal and
+// smallest-exponent values (never met in practice) take the multiplication
+// out of line. The FP64 kernels are bound by their FP64 unit.
+static __device__ __noinline__ double half_slow(double x) { return 0.5 * x; }
+__device__ __forceinline__ double half(double x) {
+  const long long b = __double_as_longlong(x);
+  const unsigned e = (unsigned)(b >> 52) & 0x7ffu;
+  if (e - 2u < 0x7fdu) return __longlong_as_double(b - (1LL << 52));
+  if (e == 0x7ffu || (b << 1) == 0) return x;
+  return half_slow(x);
+}
+__device__ __forceinline__ float half(float x) { return 0.5f * x; }
+
 // ---- logarithmic mean ----
 // ln_mean(x, y) = (y - x) / ln(y / x). With s = x + y, t = (y - x)/s and
 // f2 = t^2, ln(y/x) = 2 atanh(t), so

@@ -61,7 +61,7 @@ struct LinePrim {
 template <int VF, typename R>
 __device__ __forceinline__ void node_slots(R rho, R p, R gm1, R& s0, R& s1) {
   if (VF == kVRanocha) {
-    s0 = R(0.5) * rho;
+    s0 = half(rho);
     s1 = gm1 * rho * rcp(p);
   } else {
     s0 = rho;
@@ -226,11 +226,11 @@ __device__ __forceinline__ void volume_batch(double* u, R* __restrict__ du,
     bad |= prim_check(q);
     const R p = R(q.p);
     node_slots<VF, R>(R(q.rho), p, R(g.gm1), sp[el][0][node], sp[el][1][node]);
-    sp[el][2][node] = R(0.5) * p;
+    sp[el][2][node] = half(p);
 #pragma unroll
     for (int k = 0; k < D; ++k) {
       sp[el][3 + k][node] = R(q.v[k]);
-      sp[el][3 + D + k][node] = R(0.5) * R(q.v[k]);
+      sp[el][3 + D + k][node] = half(R(q.v[k]));
     }
 #pragma unroll
     for (int k = 0; k < NV; ++k) sa[el][k][node] = R(0);
@@ -295,18 +295,17 @@ __device__ __forceinline__ void surface_nf(int sf, const Trace<R, D>& L, const T
   if (sf == kSRanocha) {
     const R rho_ln = ln_mean(L.rho, Rt.rho);
     const R inv = inv_ln_mean(L.rho * Rt.p, Rt.rho * L.p);
-    const R an = R(0.5) * (L.vn + Rt.vn);
+    const R an = half(L.vn + Rt.vn);
     const R f0 = rho_ln * an;
     f[0] = f0;
-    f[1] = f0 * an + R(0.5) * (L.ps + Rt.ps);
+    f[1] = f0 * an + half(L.ps + Rt.ps);
     R vd = L.vn * Rt.vn;
 #pragma unroll
     for (int j = 0; j < D - 1; ++j) {
-      f[2 + j] = f0 * R(0.5) * (L.vt[j] + Rt.vt[j]);
+      f[2 + j] = f0 * half(L.vt[j] + Rt.vt[j]);
       vd += L.vt[j] * Rt.vt[j];
     }
-    f[D + 1] = f0 * (R(0.5) * vd + L.p * Rt.p * inv * gm1inv) +
-               R(0.5) * (L.p * Rt.vn + Rt.p * L.vn);
+    f[D + 1] = f0 * (half(vd) + L.p * Rt.p * inv * gm1inv) + half(L.p * Rt.vn + Rt.p * L.vn);
     return;
   }
   if (sf == kSChandrashekar) {
@@ -348,7 +347,9 @@ __device__ __forceinline__ void surface_nf(int sf, const Trace<R, D>& L, const T
     // correctly rounded)
     const R lam = fmax(fabs(L.vn), fabs(Rt.vn)) + sqrt(fmax(c2l, c2r));
 #pragma unroll
-    for (int v = 0; v < D + 2; ++v) f[v] = R(0.5) * (fl[v] + fr[v]) - R(0.5) * lam * dq[v];
+    const R hlam = half(lam);
+#pragma unroll
+    for (int v = 0; v < D + 2; ++v) f[v] = fma(-hlam, dq[v], half(fl[v] + fr[v]));
     return;
   }
   const R cl = sqrt(c2l), cr = sqrt(c2r);
@@ -621,11 +622,11 @@ __device__ __forceinline__ void pp_elements(double* u, double* __restrict__ du,
     bad |= prim_check(q);
     double(*spe)[P] = sp(el);
     node_slots<VF, double>(q.rho, q.p, g.gm1, spe[0][node], spe[1][node]);
-    spe[2][node] = 0.5 * q.p;
+    spe[2][node] = half(q.p);
 #pragma unroll
     for (int k = 0; k < D; ++k) {
       spe[3 + k][node] = q.v[k];
-      spe[3 + D + k][node] = 0.5 * q.v[k];
+      spe[3 + D + k][node] = half(q.v[k]);
     }
 #pragma unroll
     for (int v = 0; v < NV; ++v) sa(el)[v][node] = 0.0;
