@@ -251,12 +251,12 @@ __device__ __forceinline__ void speed_node(const double* c, int D, const Geom& g
     const dg::Prim<double, 2> q = dg::prim_rcp<2>(cc, g.gm1, rr);
     bad |= dg::prim_check(q);
     const double cs = sqrt(g.gamma * q.p * rr);
-    for (int k = 0; k < 2; ++k) lam[k] = fmax(lam[k], fabs(q.v[k]) + cs);
+    for (int k = 0; k < 2; ++k) lam[k] = dg::fmax_nn(lam[k], fabs(q.v[k]) + cs);
   } else {
     const dg::Prim<double, 3> q = dg::prim_rcp<3>(cc, g.gm1, rr);
     bad |= dg::prim_check(q);
     const double cs = sqrt(g.gamma * q.p * rr);
-    for (int k = 0; k < 3; ++k) lam[k] = fmax(lam[k], fabs(q.v[k]) + cs);
+    for (int k = 0; k < 3; ++k) lam[k] = dg::fmax_nn(lam[k], fabs(q.v[k]) + cs);
   }
 }
 // (FP32: the maxima stay in float and the state is converted on the integer

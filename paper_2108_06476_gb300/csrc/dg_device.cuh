@@ -234,6 +234,15 @@ __device__ __forceinline__ double half(double x) {
 }
 __device__ __forceinline__ float half(float x) { return 0.5f * x; }
 
+// max of two non-negative doubles (magnitudes, squared speeds) by their bit
+// patterns on the integer pipe: the order of non-negative IEEE values is
+// that of their bits, and a NaN (sign bit clear) exceeds every number, so it
+// is the result (fmax would drop it)
+__device__ __forceinline__ double fmax_nn(double a, double b) {
+  return __double_as_longlong(a) >= __double_as_longlong(b) ? a : b;
+}
+__device__ __forceinline__ float fmax_nn(float a, float b) { return fmaxf(a, b); }
+
 // ---- logarithmic mean ----
 // ln_mean(x, y) = (y - x) / ln(y / x). With s = x + y, t = (y - x)/s and
 // f2 = t^2, ln(y/x) = 2 atanh(t), so

@@ -176,14 +176,23 @@ __device__ __forceinline__ void volume_direction(int dir, R (*sp)[3 + 2 * D][Sha
       acc[0][c] = fma(ll, fs[row + oL], acc[0][c]);
     }
   }
+  // the first direction stores its contribution, the others add theirs
 #pragma unroll
   for (int a = 0; a < NP; ++a) {
     const int nd = node[a];
-    sa[el][0][nd] += acc[a][0];
-    sa[el][1 + dir][nd] += acc[a][1];
-    sa[el][1 + t1][nd] += acc[a][2];
-    if (D == 3) sa[el][1 + t2][nd] += acc[a][D];
-    sa[el][D + 1][nd] += acc[a][D + 1];
+    if (dir == 0) {
+      sa[el][0][nd] = acc[a][0];
+      sa[el][1 + dir][nd] = acc[a][1];
+      sa[el][1 + t1][nd] = acc[a][2];
+      if (D == 3) sa[el][1 + t2][nd] = acc[a][D];
+      sa[el][D + 1][nd] = acc[a][D + 1];
+    } else {
+      sa[el][0][nd] += acc[a][0];
+      sa[el][1 + dir][nd] += acc[a][1];
+      sa[el][1 + t1][nd] += acc[a][2];
+      if (D == 3) sa[el][1 + t2][nd] += acc[a][D];
+      sa[el][D + 1][nd] += acc[a][D + 1];
+    }
   }
 }
 
@@ -232,8 +241,6 @@ __device__ __forceinline__ void volume_batch(double* u, R* __restrict__ du,
       sp[el][3 + k][node] = R(q.v[k]);
       sp[el][3 + D + k][node] = half(R(q.v[k]));
     }
-#pragma unroll
-    for (int k = 0; k < NV; ++k) sa[el][k][node] = R(0);
   }
   if (bad) atomicOr(err, bad);
   __syncthreads();
@@ -345,7 +352,7 @@ __device__ __forceinline__ void surface_nf(int sf, const Trace<R, D>& L, const T
   if (sf == kSLLF) {
     // max(c_L, c_R) = sqrt(max(c_L^2, c_R^2)) exactly (sqrt is monotone and
     // correctly rounded)
-    const R lam = fmax(fabs(L.vn), fabs(Rt.vn)) + sqrt(fmax(c2l, c2r));
+    const R lam = fmax_nn(fabs(L.vn), fabs(Rt.vn)) + sqrt(fmax_nn(c2l, c2r));
 #pragma unroll
     const R hlam = half(lam);
 #pragma unroll
@@ -628,8 +635,6 @@ __device__ __forceinline__ void pp_elements(double* u, double* __restrict__ du,
       spe[3 + k][node] = q.v[k];
       spe[3 + D + k][node] = half(q.v[k]);
     }
-#pragma unroll
-    for (int v = 0; v < NV; ++v) sa(el)[v][node] = 0.0;
   }
   if (bad) atomicOr(err, bad);
   if (FACES) {
@@ -738,8 +743,11 @@ __device__ __forceinline__ void pp_elements(double* u, double* __restrict__ du,
       const int el = t / (NV * P), r = t % (NV * P);
       if (el >= count) continue;
       const int v = r / P, node = r % P;
+      // the first direction's part starts the sum, as in the line-owning kernel
+      double acc = d0 == 0 ? sd(el)[0][v][node] : sa(el)[v][node] + sd(el)[0][v][node];
 #pragma unroll
-      for (int gd = 0; gd < GROUP; ++gd) sa(el)[v][node] += sd(el)[gd][v][node];
+      for (int gd = 1; gd < GROUP; ++gd) acc += sd(el)[gd][v][node];
+      sa(el)[v][node] = acc;
     }
     __syncthreads();
   }
