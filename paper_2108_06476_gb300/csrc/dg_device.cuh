@@ -178,6 +178,18 @@ __device__ __forceinline__ unsigned prim_check(const Prim<R, D>& q) {
   if (!isfinite(q.rho) || !isfinite(q.p)) bad |= kErrNaN;
   return bad;
 }
+// the same tests of doubles on their bit patterns (integer pipe): x > 0
+// for 0 < bits <= bits of +inf, finite unless the exponent field is all ones
+template <int D>
+__device__ __forceinline__ unsigned prim_check(const Prim<double, D>& q) {
+  constexpr long long kInf = 0x7ff0000000000000LL;
+  const long long r = __double_as_longlong(q.rho), p = __double_as_longlong(q.p);
+  unsigned bad = 0;
+  if (!(r > 0 && r <= kInf)) bad |= kErrRho;
+  if (!(p > 0 && p <= kInf)) bad |= kErrP;
+  if ((r & kInf) == kInf || (p & kInf) == kInf) bad |= kErrNaN;
+  return bad;
+}
 
 // ---- FP64 <-> FP32 conversions on the integer pipe ----
 // The FP64 pipe (2 lanes per clock per SM on this part) also executes the
