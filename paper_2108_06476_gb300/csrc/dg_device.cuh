@@ -303,23 +303,41 @@ __device__ __forceinline__ double s_short(double f2) {
 // q_short and s_short with the terms of high degree summed in FP32, the
 // rest by the same Horner scheme in FP64 (the FP64 kernels are bound by
 // their FP64 unit; the FP32 pipe has room): Q from f2^4 (|c_4| f2^4 <=
-// 3e-10 on [0, 1e-2], so the tail's FP32 rounding stays below 3e-17 of Q),
+// 3e-10 on [0, 1e-2], so the tail's FP32 rounding, with f2 truncated to
+// FP32, stays below 3e-17 of Q),
 // S from f2^5 (below 2e-18 of S). Same coefficients, the tail's rounded to
 // FP32.
+// f2 >= 0 as a float, its bit pattern truncated (0 below the float range):
+// branch-free integer work, relative error below 2^-23 (the tail bound
+// above allows for it)
+__device__ __forceinline__ float f32_trunc_nonneg(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
+  const unsigned e = hi >> 20;  // sign bit clear
+  const unsigned f = ((e - 896u) << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29);
+  return e - 897u < 253u ? __uint_as_float(f) : 0.0f;
+}
+// a normal float as a double (exact; the tails are never zero or subnormal)
+__device__ __forceinline__ double f64_of_normal(float x) {
+  const unsigned b = __float_as_uint(x);
+  const unsigned fe = (b >> 23) & 0xffu;
+  return __hiloint2double((int)((b & 0x80000000u) | ((fe + 896u) << 20) | ((b & 0x7fffffu) >> 3)),
+                          (int)(b << 29));
+}
 __device__ __forceinline__ double q_short_mixed(double f2) {
-  const float f = d2f(f2);
+  const float f = f32_trunc_nonneg(f2);
   float t = -0.01719901874634888f;
   t = fmaf(f, t, -0.021792151641765893f);
   t = fmaf(f, t, -0.030194027707754922f);
-  double r = fma(f2, f2d(t), -0.0465608465041037);
+  double r = fma(f2, f64_of_normal(t), -0.0465608465041037);
   r = fma(f2, r, -0.08888888888893755);
   r = fma(f2, r, -0.3333333333333333);
   return fma(f2, r, 1.0);
 }
 __device__ __forceinline__ double s_short_mixed(double f2) {
-  const float f = d2f(f2);
+  const float f = f32_trunc_nonneg(f2);
   const float t = fmaf(f, 0.15791323599162152f, 0.18177218144198024f);
-  double r = fma(f2, f2d(t), 0.22222246134174709);
+  double r = fma(f2, f64_of_normal(t), 0.22222246134174709);
   r = fma(f2, r, 0.28571428515311326);
   r = fma(f2, r, 0.4000000000004813);
   r = fma(f2, r, 0.6666666666666666);
@@ -387,18 +405,23 @@ __device__ __forceinline__ double f2_of(float t) {
   const double td = t;
   return td * td;
 }
+// MIXED: the short range's tails in FP32 (the default); the line-owning
+// kernels of degree 6 and 7 take the FP64 polynomials, whose smaller code
+// suits their long unrolled line loops better
+template <bool MIXED = true>
 __device__ __forceinline__ double q_of(double f2, double) {
   double q;
   if (in_short(f2))
-    q = q_short_mixed(f2);
+    q = MIXED ? q_short_mixed(f2) : q_short(f2);
   else
     q = q_long(f2);
   return q;
 }
+template <bool MIXED = true>
 __device__ __forceinline__ double s_of(double f2, double) {
   double S;
   if (in_short(f2))
-    S = s_short_mixed(f2);
+    S = MIXED ? s_short_mixed(f2) : s_short(f2);
   else
     S = s_long(f2);
   return S;
@@ -409,7 +432,7 @@ __device__ __forceinline__ R ln_mean(R x, R y) {
   const R t = (y - x) * rcp(s);
   const double f2 = f2_of(t);
   if (!in_long(f2)) return ln_mean_far(x, y);
-  return R(0.5) * s * q_of(f2, R(0));
+  return R(0.5) * s * q_of<>(f2, R(0));
 }
 
 template <typename R>
@@ -418,29 +441,29 @@ __device__ __forceinline__ R inv_ln_mean(R x, R y) {
   const R t = (y - x) * rs;
   const double f2 = f2_of(t);
   if (!in_long(f2)) return inv_ln_mean_far(x, y);
-  return s_of(f2, R(0)) * rs;
+  return s_of<>(f2, R(0)) * rs;
 }
 
 // ln_mean(2 hx, 2 hy) from the halves: every step is the one of
 // ln_mean(x, y) scaled by an exact factor 2, so the result is bitwise
 // ln_mean(x, y), without the product (x + y)/2.
-template <typename R>
+template <typename R, bool MIXED = true>
 __device__ __forceinline__ R ln_mean_halves(R hx, R hy) {
   const R hs = hx + hy;
   const R t = (hy - hx) * rcp(hs);
   const double f2 = f2_of(t);
   if (!in_long(f2)) return R(2) * ln_mean_far(hx, hy);
-  return hs * q_of(f2, R(0));
+  return hs * q_of<MIXED>(f2, R(0));
 }
 
 // a + 1/ln_mean(x, y), the last product fused into the addition
-template <typename R>
+template <typename R, bool MIXED = true>
 __device__ __forceinline__ R add_inv_ln_mean(R x, R y, R a) {
   const R rs = rcp(x + y);
   const R t = (y - x) * rs;
   const double f2 = f2_of(t);
   if (!in_long(f2)) return a + inv_ln_mean_far(x, y);
-  return fma(s_of(f2, R(0)), rs, a);
+  return fma(s_of<MIXED>(f2, R(0)), rs, a);
 }
 
 // ---- two-point volume fluxes f#(L, R) in direction DIR ----

@@ -71,15 +71,15 @@ __device__ __forceinline__ void node_slots(R rho, R p, R gm1, R& s0, R& s1) {
 
 // Ranocha's EC/KEP flux in normal-first order. hp is p/2 (FP64) or p'/2
 // (FP32, then the P_e parts are handled by the caller); an = avg(v_n).
-template <typename R, int D>
+template <typename R, int D, bool MIXED = true>
 __device__ __forceinline__ void ranocha_nf(const LinePrim<R, D>& L, const LinePrim<R, D>& Rt,
                                            R f[D + 2], R& an) {
-  const R rho_ln = ln_mean_halves(L.s0, Rt.s0);
+  const R rho_ln = ln_mean_halves<R, MIXED>(L.s0, Rt.s0);
   R vd = L.hvn * Rt.vn;
 #pragma unroll
   for (int j = 0; j < D - 1; ++j) vd = fma(L.hvt[j], Rt.vt[j], vd);
   // v_L.v_R / 2 + 1 / ((gamma-1) ln_mean(rho/p))
-  const R ee = add_inv_ln_mean(L.s1, Rt.s1, vd);
+  const R ee = add_inv_ln_mean<R, MIXED>(L.s1, Rt.s1, vd);
   an = L.hvn + Rt.hvn;
   const R f0 = rho_ln * an;
   f[0] = f0;
@@ -145,7 +145,7 @@ __device__ __forceinline__ void volume_direction(int dir, R (*sp)[3 + 2 * D][Sha
 #pragma unroll
     for (int b = a + 1; b < NP; ++b) {
       R f[NV], an = R(0);
-      if (VF == kVRanocha) ranocha_nf<R, D>(q[a], q[b], f, an);
+      if (VF == kVRanocha) ranocha_nf<R, D, (N <= 5)>(q[a], q[b], f, an);
       else generic_nf<VF, R, D>(q[a], q[b], gm1inv, f);
       const R dab = tb.Ds[dir][a][b], dba = tb.Ds[dir][b][a];
 #pragma unroll

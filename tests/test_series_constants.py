@@ -146,12 +146,21 @@ def test_range_limits(header):
 
 # The FP64 kernels evaluate the short-range polynomials with their tail in
 # FP32 (q_short_mixed from f2^4, s_short_mixed from f2^5): the same
-# coefficients, the tail's rounded to FP32, and the evaluation (FP32 Horner
-# tail, FP64 Horner head) within 3e-17 of Q and 2e-18 of S over [0, 1e-2],
-# emulated here with exact decimal arithmetic and FP32 rounding of every
-# tail operation.
+# coefficients, the tail's rounded to FP32, and the evaluation (f2 truncated
+# to FP32, FP32 Horner tail, FP64 Horner head) within 3e-17 of Q and 2e-18
+# of S over [0, 1e-2], emulated here with exact decimal arithmetic and FP32
+# rounding of every tail operation.
 def _f32(x):
     return Decimal(float(np.float32(float(x))))
+
+
+def _f32_trunc(x):
+    """x >= 0 truncated to FP32 (the kernels' conversion of f2)."""
+    d = float(x)
+    f = np.float32(d)
+    if float(f) > d:
+        f = np.nextafter(f, np.float32(0))
+    return Decimal(float(f))
 
 
 @pytest.mark.parametrize("name,mixed,split,ref,bound",
@@ -172,7 +181,7 @@ def test_mixed_precision_short_polynomials(header, name, mixed, split, ref, boun
     worst = Decimal(0)
     for k in range(401):
         x = Decimal(1e-2) * k / 400
-        xf = _f32(x)
+        xf = _f32_trunc(x)
         t = Decimal(tail[-1])
         for c in reversed(tail[:-1]):
             t = _f32(xf * t + Decimal(c))  # one FP32 fused multiply-add
