@@ -426,7 +426,9 @@ int dg_measure_fp64_issue(double *cycles_full_warp, double *cycles_one_lane, voi
  *   op 1  the FP32 reciprocal of (float)x[i], widened,
  *   op 2  the double -> float conversion of the FP32 kernels (integer pipe,
  *         round to nearest even), widened,
- *   op 3  the float -> double conversion of (float)x[i].
+ *   op 3  the float -> double conversion of (float)x[i],
+ *   op 4  the FP64 square root of the wave-speed kernels (hardware
+ *         reciprocal-square-root approximation + Goldschmidt iteration).
  * Asynchronous on cuda_stream. Errors: DG_ERR_ARG, DG_ERR_CUDA. */
 int dg_selftest_arith(int op, const double *x, double *y, long long n, void *cuda_stream);
 

@@ -250,12 +250,12 @@ __device__ __forceinline__ void speed_node(const double* c, int D, const Geom& g
   if (D == 2) {
     const dg::Prim<double, 2> q = dg::prim_rcp<2>(cc, g.gm1, rr);
     bad |= dg::prim_check(q);
-    const double cs = sqrt(g.gamma * q.p * rr);
+    const double cs = dg::sqrt_pos(g.gamma * q.p * rr);
     for (int k = 0; k < 2; ++k) lam[k] = dg::fmax_nn(lam[k], fabs(q.v[k]) + cs);
   } else {
     const dg::Prim<double, 3> q = dg::prim_rcp<3>(cc, g.gm1, rr);
     bad |= dg::prim_check(q);
-    const double cs = sqrt(g.gamma * q.p * rr);
+    const double cs = dg::sqrt_pos(g.gamma * q.p * rr);
     for (int k = 0; k < 3; ++k) lam[k] = dg::fmax_nn(lam[k], fabs(q.v[k]) + cs);
   }
 }

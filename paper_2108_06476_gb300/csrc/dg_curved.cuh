@@ -305,11 +305,12 @@ __device__ __forceinline__ void curved_direction(int r, double (*sp)[9][(N + 1) 
       hg[a][k] = sg[el][k][nd];
     }
   }
+  // the line sums continue the running totals of the earlier directions
   double acc[NP][NV];
 #pragma unroll
   for (int a = 0; a < NP; ++a)
 #pragma unroll
-    for (int v = 0; v < NV; ++v) acc[a][v] = 0.0;
+    for (int v = 0; v < NV; ++v) acc[a][v] = sa[el][v][node[a]];
 #pragma unroll
   for (int a = 0; a < NP; ++a) {
 #pragma unroll
@@ -339,7 +340,7 @@ __device__ __forceinline__ void curved_direction(int r, double (*sp)[9][(N + 1) 
 #pragma unroll
   for (int a = 0; a < NP; ++a)
 #pragma unroll
-    for (int v = 0; v < NV; ++v) sa[el][v][node[a]] += acc[a][v];
+    for (int v = 0; v < NV; ++v) sa[el][v][node[a]] = acc[a][v];
 }
 
 // N = 3: three CTAs per SM (168 registers, the shared memory of three
@@ -549,9 +550,10 @@ __global__ void __launch_bounds__(CPairs<N>::THREADS)
     for (int node = threadIdx.x; node < P; node += blockDim.x) {
       int l, i;
       line_of<N>(r, node, l, i);
+      // continuing the running total, in the line-owning kernel's order
       double acc[NV];
 #pragma unroll
-      for (int v = 0; v < NV; ++v) acc[v] = 0.0;
+      for (int v = 0; v < NV; ++v) acc[v] = sa[v][node];
       for (int j = 0; j < NP; ++j) {
         if (j == i) continue;
         const int p = j < i ? pair_index<N>(j, i) : pair_index<N>(i, j);
@@ -571,7 +573,7 @@ __global__ void __launch_bounds__(CPairs<N>::THREADS)
                        acc[v]);
       }
 #pragma unroll
-      for (int v = 0; v < NV; ++v) sa[v][node] += acc[v];
+      for (int v = 0; v < NV; ++v) sa[v][node] = acc[v];
     }
     __syncthreads();
   }

@@ -255,6 +255,31 @@ __device__ __forceinline__ double fmax_nn(double a, double b) {
 }
 __device__ __forceinline__ float fmax_nn(float a, float b) { return fmaxf(a, b); }
 
+// ---- square root of a positive double (wave speeds) ----
+// Goldschmidt's coupled iteration for g = sqrt(x) and h = 1/(2 sqrt(x)), in
+// the form given by P. Markstein, "Software division and square root using
+// Goldschmidt's algorithms" (2004), from the hardware reciprocal square root
+// approximation y (rsqrt.approx.ftz.f64): g = x y, h = y/2; one step
+// r = 1/2 - g h, g += g r, h += h r squares the relative error, and the
+// correction g += (x - g^2) h squares it again, leaving the rounding of the
+// last FMA: within one ulp of the correctly rounded root, with six FP64
+// instructions. Positive normal arguments only; zero, negative, subnormal,
+// infinite and NaN arguments take the library square root out of line.
+static __device__ __noinline__ double sqrt_slow(double x) { return sqrt(x); }
+__device__ __forceinline__ double sqrt_pos(double x) {
+  const long long b = __double_as_longlong(x);
+  // positive normal: bits in [2^52, 0x7ff0000000000000)
+  if ((unsigned long long)(b - (1LL << 52)) >= 0x7fe0000000000000ULL) return sqrt_slow(x);
+  double y;
+  asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+  double g = x * y, h = half(y);
+  const double r = fma(-g, h, 0.5);
+  g = fma(g, r, g);
+  h = fma(h, r, h);
+  return fma(fma(-g, g, x), h, g);
+}
+__device__ __forceinline__ float sqrt_pos(float x) { return sqrtf(x); }
+
 // ---- logarithmic mean ----
 // ln_mean(x, y) = (y - x) / ln(y / x). With s = x + y, t = (y - x)/s and
 // f2 = t^2, ln(y/x) = 2 atanh(t), so

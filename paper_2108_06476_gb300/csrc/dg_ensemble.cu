@@ -198,7 +198,7 @@ __device__ void ens_volume_pp(const EnsArgs& a, const SimDesc& sd, const WorkIte
   double* u = const_cast<double*>(a.uin) + sd.off;
   const double* fs = static_cast<const double*>(a.fs) + sd.fsoff;
   for (int el = 0; el < w.count; ++el)
-    pp_elements<3, N, kVRanocha, false, 1, 1>(u, nullptr, fs, g, tb, a.err, fz, 0, w.e0 + el, 1,
+    pp_elements<3, N, kVRanocha, false, 1, 1, true>(u, nullptr, fs, g, tb, a.err, fz, 0, w.e0 + el, 1,
                                               smem);
 }
 
@@ -266,7 +266,7 @@ __global__ void ensemble_speed_kernel(const SimDesc* __restrict__ sims,
         double rr;
         const Prim<double, 3> q = prim_rcp<3>(c, gm1, rr);
         bad |= prim_check(q);
-        const double cs = sqrt(gamma * q.p * rr);
+        const double cs = dg::sqrt_pos(gamma * q.p * rr);
 #pragma unroll
         for (int k = 0; k < 3; ++k) lam[k] = fmax(lam[k], fabs(q.v[k]) + cs);
       }

@@ -407,9 +407,10 @@ __device__ __forceinline__ void mhd_ec_direction(const double (*sq)[(N + 1) * (N
   for (int node = threadIdx.x; node < P; node += blockDim.x) {
     int l, i;
     line_of<N>(DIR, node, l, i);
-    double acc[kMV], dn = 0.0;
+    // the line sums continue the running totals of the earlier directions
+    double acc[kMV], dn = sa[kMV][node];
 #pragma unroll
-    for (int v = 0; v < kMV; ++v) acc[v] = 0.0;
+    for (int v = 0; v < kMV; ++v) acc[v] = sa[v][node];
     const double bi = sq[5 + DIR][node];  // B_n / 2
     for (int j = 0; j < NP; ++j) {
       if (j == i) continue;
@@ -429,8 +430,8 @@ __device__ __forceinline__ void mhd_ec_direction(const double (*sq)[(N + 1) * (N
       dn = fma(lift, src[8 * base], dn);
     }
 #pragma unroll
-    for (int v = 0; v < kMV; ++v) sa[v][node] += acc[v];
-    sa[kMV][node] += dn;
+    for (int v = 0; v < kMV; ++v) sa[v][node] = acc[v];
+    sa[kMV][node] = dn;
   }
   __syncthreads();
 }

@@ -159,6 +159,7 @@ __global__ void arith_kernel(int op, const double* __restrict__ x, double* __res
       case 1: r = (double)dg::rcp((float)v); break;           // FP32 reciprocal
       case 2: r = (double)dg::d2f(v); break;                  // double -> float
       case 3: r = dg::f2d((float)v); break;                   // float -> double
+      case 4: r = dg::sqrt_pos(v); break;                     // FP64 square root
       default: r = 0.0;
     }
     y[i] = r;
@@ -169,7 +170,7 @@ __global__ void arith_kernel(int op, const double* __restrict__ x, double* __res
 
 extern "C" int dg_selftest_arith(int op, const double* x, double* y, long long n,
                                  void* cuda_stream) {
-  if (op < 0 || op > 3 || n < 0 || (n > 0 && (!x || !y)))
+  if (op < 0 || op > 4 || n < 0 || (n > 0 && (!x || !y)))
     return dg::set_last_error(DG_ERR_ARG, "dg_selftest_arith: bad argument");
   if (n == 0) return DG_OK;
   long long blocks = (n + 255) / 256;

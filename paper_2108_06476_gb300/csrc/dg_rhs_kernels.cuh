@@ -135,11 +135,21 @@ __device__ __forceinline__ void volume_direction(int dir, R (*sp)[3 + 2 * D][Sha
       q[a].hvt[D - 2] = sp[el][3 + D + t2][nd];
     }
   }
+  // the line sums continue the total of the earlier directions (the first
+  // starts from zero), so that no separate addition of the directions runs
+  // (one FP64 addition per node and variable for each direction after the
+  // first); the rounding then follows the running total
+  int comp[NV];
+  comp[0] = 0;
+  comp[1] = 1 + dir;
+  comp[2] = 1 + t1;
+  if (D == 3) comp[D] = 1 + t2;
+  comp[D + 1] = D + 1;
   R acc[NP][NV];
 #pragma unroll
   for (int a = 0; a < NP; ++a)
 #pragma unroll
-    for (int v = 0; v < NV; ++v) acc[a][v] = R(0);
+    for (int v = 0; v < NV; ++v) acc[a][v] = dir == 0 ? R(0) : sa[el][comp[v]][node[a]];
 #pragma unroll
   for (int a = 0; a < NP; ++a) {
 #pragma unroll
@@ -163,12 +173,6 @@ __device__ __forceinline__ void volume_direction(int dir, R (*sp)[3 + 2 * D][Sha
     const long long base = (long long)nelem * Shape<D, N>::LINES;
     const long long oR = (long long)e * Shape<D, N>::LINES + l;
     const long long oL = (long long)eleft * Shape<D, N>::LINES + l;
-    int comp[NV];
-    comp[0] = 0;
-    comp[1] = 1 + dir;
-    comp[2] = 1 + t1;
-    if (D == 3) comp[D] = 1 + t2;
-    comp[D + 1] = D + 1;
 #pragma unroll
     for (int c = 0; c < NV; ++c) {
       const long long row = (long long)(dir * NV + comp[c]) * base;
@@ -176,24 +180,11 @@ __device__ __forceinline__ void volume_direction(int dir, R (*sp)[3 + 2 * D][Sha
       acc[0][c] = fma(ll, fs[row + oL], acc[0][c]);
     }
   }
-  // the first direction stores its contribution, the others add theirs
+  // the running totals back to the line's nodes
 #pragma unroll
-  for (int a = 0; a < NP; ++a) {
-    const int nd = node[a];
-    if (dir == 0) {
-      sa[el][0][nd] = acc[a][0];
-      sa[el][1 + dir][nd] = acc[a][1];
-      sa[el][1 + t1][nd] = acc[a][2];
-      if (D == 3) sa[el][1 + t2][nd] = acc[a][D];
-      sa[el][D + 1][nd] = acc[a][D + 1];
-    } else {
-      sa[el][0][nd] += acc[a][0];
-      sa[el][1 + dir][nd] += acc[a][1];
-      sa[el][1 + t1][nd] += acc[a][2];
-      if (D == 3) sa[el][1 + t2][nd] += acc[a][D];
-      sa[el][D + 1][nd] += acc[a][D + 1];
-    }
-  }
+  for (int a = 0; a < NP; ++a)
+#pragma unroll
+    for (int c = 0; c < NV; ++c) sa[el][comp[c]][node[a]] = acc[a][c];
 }
 
 // One batch of `count` (<= MAXE) elements from e0: the prologue into shared
@@ -350,10 +341,9 @@ __device__ __forceinline__ void surface_nf(int sf, const Trace<R, D>& L, const T
   dq[D + 1] = dE;
   const R c2l = gamma * L.p * L.rr, c2r = gamma * Rt.p * Rt.rr;
   if (sf == kSLLF) {
-    // max(c_L, c_R) = sqrt(max(c_L^2, c_R^2)) exactly (sqrt is monotone and
-    // correctly rounded)
-    const R lam = fmax_nn(fabs(L.vn), fabs(Rt.vn)) + sqrt(fmax_nn(c2l, c2r));
-#pragma unroll
+    // max(c_L, c_R) as the root of max(c_L^2, c_R^2): one square root,
+    // within one ulp of the larger sound speed
+    const R lam = fmax_nn(fabs(L.vn), fabs(Rt.vn)) + sqrt_pos(fmax_nn(c2l, c2r));
     const R hlam = half(lam);
 #pragma unroll
     for (int v = 0; v < D + 2; ++v) f[v] = fma(-hlam, dq[v], half(fl[v] + fr[v]));
@@ -529,6 +519,15 @@ constexpr int pp_epb() {
   return per >= 32 ? 1 : (32 / per > 4 ? 4 : 32 / per);
 }
 
+// the normal-first component of variable v in direction dir: 0 mass, 1 the
+// normal momentum, 2 .. D the momenta of directions dir+1, dir+2, D+1 energy
+template <int D>
+__device__ __forceinline__ int nf_component(int v, int dir) {
+  if (v == 0 || v == D + 1) return v;
+  const int k = v - 1;
+  return k == dir ? 1 : (k == (dir + 1) % D ? 2 : D);
+}
+
 template <int N>
 __device__ __forceinline__ void pp_pair_of(int p, int& a, int& b) {
   a = 0;
@@ -564,7 +563,7 @@ __device__ __forceinline__ void pp_line_of(int dir, int node, int& l, int& i) {
 // block calls it; it ends with a barrier after its last shared-memory read,
 // so a block may run it for one batch after another). smem: C::SMEM bytes
 // (C::SMEM_F with FACES).
-template <int D, int N, int VF, bool FACES, int G, int EPB>
+template <int D, int N, int VF, bool FACES, int G, int EPB, bool CHAIN = false>
 __device__ __forceinline__ void pp_elements(double* u, double* __restrict__ du,
                                             const double* __restrict__ fs, const Geom& g,
                                             const Tables<double>& tb, unsigned* __restrict__ err,
@@ -574,7 +573,7 @@ __device__ __forceinline__ void pp_elements(double* u, double* __restrict__ du,
   constexpr int NP = C::NP, P = C::P, NV = C::NV, NC = C::NC, LINES = C::LINES,
                 NPAIRS = C::NPAIRS, GROUP = C::GROUP, WORK = C::WORK;
   // per element el: slots sp[NC][P], accumulators sa[NV][P], direction
-  // parts sd[GROUP][NV][P], pair fluxes sf[WORK][NV]; FACES: sfc[el] =
+  // parts sd[GROUP][NV][P] (unless CHAIN), pair fluxes sf[WORK][NV]; FACES: sfc[el] =
   // [side][dir][c][l], side 0 the element's right face, 1 its left face, c in
   // normal-first order
   auto sp = [&](int el) {
@@ -687,69 +686,110 @@ __device__ __forceinline__ void pp_elements(double* u, double* __restrict__ du,
       for (int v = 0; v < NV; ++v) sfe[w * NV + v] = f[v];
     }
     __syncthreads();
-    // per (element, direction, node): the line sum in the line-owning order,
-    // then the lifting (normal-first components back to variables)
-    for (int t = threadIdx.x; t < EPB * GROUP * P; t += blockDim.x) {
-      const int el = t / (GROUP * P), r = t % (GROUP * P);
-      if (el >= count) continue;
-      const int gd = r / P, node = r % P, dir = d0 + gd;
-      const int e = e0 + el;
-      const int t1 = (dir + 1) % D, t2 = (dir + 2) % D;
-      int l, i;
-      pp_line_of<D, N>(dir, node, l, i);
-      double acc[NV];
-#pragma unroll
-      for (int v = 0; v < NV; ++v) acc[v] = 0.0;
-      const double* sfe = sf(el);
-      for (int j = 0; j < NP; ++j) {
-        if (j == i) continue;
-        const int p = j < i ? pp_pair_index<N>(j, i) : pp_pair_index<N>(i, j);
-        const double dij = tb.Ds[dir][i][j];
-        const double* fp = sfe + ((gd * LINES + l) * NPAIRS + p) * NV;
-#pragma unroll
-        for (int v = 0; v < NV; ++v) acc[v] = fma(dij, fp[v], acc[v]);
+    if constexpr (CHAIN) {
+      // CHAIN: per (element, variable, node), the line sums of the group's
+      // directions in the line-owning kernel's order, each continuing the
+      // running total of the earlier directions, with the lifting at the line
+      // ends (face values in normal-first order)
+      for (int t = threadIdx.x; t < EPB * NV * P; t += blockDim.x) {
+        const int el = t / (NV * P), r = t % (NV * P);
+        if (el >= count) continue;
+        const int v = r / P, node = r % P;
+        const int e = e0 + el;
+        const double* sfe = sf(el);
+        const double* fce = sfc + (long long)el * 2 * D * LINES * NV;
+        double acc = d0 == 0 ? 0.0 : sa(el)[v][node];
+        for (int gd = 0; gd < GROUP; ++gd) {
+          const int dir = d0 + gd, c = nf_component<D>(v, dir);
+          int l, i;
+          pp_line_of<D, N>(dir, node, l, i);
+          for (int j = 0; j < NP; ++j) {
+            if (j == i) continue;
+            const int p = j < i ? pp_pair_index<N>(j, i) : pp_pair_index<N>(i, j);
+            acc = fma(tb.Ds[dir][i][j], sfe[((gd * LINES + l) * NPAIRS + p) * NV + c], acc);
+          }
+          if (i == N)
+            acc = fma(tb.liftR[dir],
+                      FACES ? fce[((0 * D + dir) * NV + c) * LINES + l]
+                            : fs[(long long)(dir * NV + v) * base + (long long)e * LINES + l],
+                      acc);
+          if (i == 0)
+            acc = fma(tb.liftL[dir],
+                      FACES ? fce[((1 * D + dir) * NV + c) * LINES + l]
+                            : fs[(long long)(dir * NV + v) * base +
+                                 (long long)s_left[el][dir] * LINES + l],
+                      acc);
+        }
+        sa(el)[v][node] = acc;
       }
-      int comp[NV];
-      comp[0] = 0;
-      comp[1] = 1 + dir;
-      comp[2] = 1 + t1;
-      if (D == 3) comp[D] = 1 + t2;
-      comp[D + 1] = D + 1;
-      const double* fce = sfc + (long long)el * 2 * D * LINES * NV;
-      if (i == N) {
+      __syncthreads();
+    } else {
+      // otherwise per (element, direction, node): the line sum on its own
+      // (in the same order of pairs), then the lifting (normal-first
+      // components back to variables); a direction whose terms cancel exactly
+      // keeps its exact zero
+      for (int t = threadIdx.x; t < EPB * GROUP * P; t += blockDim.x) {
+        const int el = t / (GROUP * P), r = t % (GROUP * P);
+        if (el >= count) continue;
+        const int gd = r / P, node = r % P, dir = d0 + gd;
+        const int e = e0 + el;
+        const int t1 = (dir + 1) % D, t2 = (dir + 2) % D;
+        int l, i;
+        pp_line_of<D, N>(dir, node, l, i);
+        double acc[NV];
 #pragma unroll
-        for (int c = 0; c < NV; ++c)
-          acc[c] = fma(tb.liftR[dir],
-                       FACES ? fce[((0 * D + dir) * NV + c) * LINES + l]
-                             : fs[(long long)(dir * NV + comp[c]) * base + (long long)e * LINES + l],
-                       acc[c]);
+        for (int v = 0; v < NV; ++v) acc[v] = 0.0;
+        const double* sfe = sf(el);
+        for (int j = 0; j < NP; ++j) {
+          if (j == i) continue;
+          const int p = j < i ? pp_pair_index<N>(j, i) : pp_pair_index<N>(i, j);
+          const double dij = tb.Ds[dir][i][j];
+          const double* fp = sfe + ((gd * LINES + l) * NPAIRS + p) * NV;
+#pragma unroll
+          for (int v = 0; v < NV; ++v) acc[v] = fma(dij, fp[v], acc[v]);
+        }
+        int comp[NV];
+        comp[0] = 0;
+        comp[1] = 1 + dir;
+        comp[2] = 1 + t1;
+        if (D == 3) comp[D] = 1 + t2;
+        comp[D + 1] = D + 1;
+        const double* fce = sfc + (long long)el * 2 * D * LINES * NV;
+        if (i == N) {
+#pragma unroll
+          for (int c = 0; c < NV; ++c)
+            acc[c] = fma(tb.liftR[dir],
+                         FACES ? fce[((0 * D + dir) * NV + c) * LINES + l]
+                               : fs[(long long)(dir * NV + comp[c]) * base + (long long)e * LINES + l],
+                         acc[c]);
+        }
+        if (i == 0) {
+#pragma unroll
+          for (int c = 0; c < NV; ++c)
+            acc[c] = fma(tb.liftL[dir],
+                         FACES ? fce[((1 * D + dir) * NV + c) * LINES + l]
+                               : fs[(long long)(dir * NV + comp[c]) * base +
+                                    (long long)s_left[el][dir] * LINES + l],
+                         acc[c]);
+        }
+        double(*sde)[NV][P] = sd(el);
+#pragma unroll
+        for (int c = 0; c < NV; ++c) sde[gd][comp[c]][node] = acc[c];
       }
-      if (i == 0) {
+      __syncthreads();
+      // the directions' sums added in order
+      for (int t = threadIdx.x; t < EPB * NV * P; t += blockDim.x) {
+        const int el = t / (NV * P), r = t % (NV * P);
+        if (el >= count) continue;
+        const int v = r / P, node = r % P;
+        // the first direction's part starts the sum
+        double acc = d0 == 0 ? sd(el)[0][v][node] : sa(el)[v][node] + sd(el)[0][v][node];
 #pragma unroll
-        for (int c = 0; c < NV; ++c)
-          acc[c] = fma(tb.liftL[dir],
-                       FACES ? fce[((1 * D + dir) * NV + c) * LINES + l]
-                             : fs[(long long)(dir * NV + comp[c]) * base +
-                                  (long long)s_left[el][dir] * LINES + l],
-                       acc[c]);
+        for (int gd = 1; gd < GROUP; ++gd) acc += sd(el)[gd][v][node];
+        sa(el)[v][node] = acc;
       }
-      double(*sde)[NV][P] = sd(el);
-#pragma unroll
-      for (int c = 0; c < NV; ++c) sde[gd][comp[c]][node] = acc[c];
+      __syncthreads();
     }
-    __syncthreads();
-    // the directions added in order, as the line-owning kernel does
-    for (int t = threadIdx.x; t < EPB * NV * P; t += blockDim.x) {
-      const int el = t / (NV * P), r = t % (NV * P);
-      if (el >= count) continue;
-      const int v = r / P, node = r % P;
-      // the first direction's part starts the sum, as in the line-owning kernel
-      double acc = d0 == 0 ? sd(el)[0][v][node] : sa(el)[v][node] + sd(el)[0][v][node];
-#pragma unroll
-      for (int gd = 1; gd < GROUP; ++gd) acc += sd(el)[gd][v][node];
-      sa(el)[v][node] = acc;
-    }
-    __syncthreads();
   }
   // epilogue: the CTA's elements are contiguous in the state
   const double dtv = fz.k ? *fz.dt : 0.0;

@@ -85,6 +85,38 @@ def test_fp32_reciprocal_within_one_ulp(lib):
     assert d.max() <= 1
 
 
+def test_fp64_square_root_within_one_ulp(lib):
+    # positive normal operands of every magnitude, powers of two (exact
+    # roots), the ends of the normal range and perfect squares: within one
+    # ulp of the correctly rounded IEEE root
+    rng = np.random.default_rng(5)
+    x = np.exp2(rng.uniform(-1022.0, 1023.9, 200000))
+    pow2 = np.exp2(np.arange(-1022, 1024, dtype=np.float64))
+    k = rng.integers(1, 2 ** 26, 20000).astype(np.float64)
+    edge = np.array([2.0 ** -1022 * (1 + j * 2.0 ** -52) for j in range(64)]
+                    + [np.finfo(np.float64).max * (1 - j * 2.0 ** -53) for j in range(64)]
+                    + [np.nextafter(1.0, 2.0), np.nextafter(1.0, 0.0), 2.0, 3.0, 0.1, 28.0])
+    x = np.concatenate([x, pow2, k * k, edge])
+    y = arith(lib, 4, x)
+    d = ulp_distance64(y, np.sqrt(x))
+    assert d.max() <= 1, (x[np.argmax(d)], d.max())
+    # even powers of two and perfect squares have exact roots
+    sq = np.concatenate([np.exp2(np.arange(-1022, 1024, 2, dtype=np.float64)), k * k])
+    assert np.array_equal(arith(lib, 4, sq), np.sqrt(sq))
+    # squared sound speeds of the kernels' states (gamma p / rho)
+    c2 = 1.4 * rng.uniform(1e-2, 1e2, 100000) / rng.uniform(1e-2, 2.0, 100000)
+    assert ulp_distance64(arith(lib, 4, c2), np.sqrt(c2)).max() <= 1
+    # everything else takes the library root: zeros, negative, subnormal,
+    # infinite and NaN arguments give the IEEE results
+    special = np.array([0.0, -0.0, -1.0, -np.inf, 5e-324, 1e-310, np.inf, np.nan])
+    with np.errstate(invalid="ignore"):
+        ref = np.sqrt(special)
+    got = arith(lib, 4, special)
+    assert np.array_equal(np.isnan(got), np.isnan(ref))
+    ok = ~np.isnan(ref)
+    assert np.array_equal(got[ok].view(np.int64), ref[ok].view(np.int64))
+
+
 def test_double_to_float_is_ieee_round_to_nearest_even(lib):
     rng = np.random.default_rng(3)
     x = np.exp2(rng.uniform(-130.0, 130.0, 200000)) * rng.choice([-1.0, 1.0], 200000)

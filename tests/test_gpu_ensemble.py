@@ -101,8 +101,14 @@ def test_in_place_stage_equals_out_of_place(orc, precision):
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 def test_member_equals_the_single_mesh_step(orc, precision):
     # the ensemble runs the single-mesh device functions with the member's
-    # own tables: a step with a given dt is bitwise the fused single-mesh step
-    mem = small_members()
+    # own tables: a step with a given dt is bitwise the fused single-mesh
+    # step. FP64 meshes under 608 elements run the pair-parallel one-launch
+    # kernel instead, which keeps each direction's line sums apart where the
+    # line-owning kernels continue one running total: those members agree to
+    # rounding
+    M = W.EnsembleMember
+    mem = small_members() + [M(3, 3, (9, 9, 9), 0.7, (0.1, 0.0, 0.2), 20.0),
+                             M(3, 5, (9, 9, 9), 0.98, (-0.2, 0.1, 0.3), 20.0)]
     u0 = W.ensemble_state(mem, lambda N: orc.lgl(N)[0])
     E = Ensemble([m.N for m in mem], [m.n[0] for m in mem], precision=precision)
     dt = 1.0e-3
@@ -115,7 +121,14 @@ def test_member_equals_the_single_mesh_step(orc, precision):
         us = torch.from_numpy(split(E, u0)[s].copy()).cuda()
         mesh.step_dt(us, dt)
         torch.cuda.synchronize()
-        assert np.array_equal(us.cpu().numpy(), got[s]), s
+        if precision == "fp64" and np.prod(m.n) < 608:
+            # the increments, with the rounding of u0 + increment allowed for
+            u0s = split(E, u0)[s]
+            inc = us.cpu().numpy() - u0s
+            bound = 1e-13 + 1e-15 * np.linalg.norm(u0s) / np.linalg.norm(inc)
+            assert rel(got[s] - u0s, inc) <= bound, s
+        else:
+            assert np.array_equal(us.cpu().numpy(), got[s]), s
 
 
 def test_graph_step_and_tuner_are_bitwise_consistent(orc):
