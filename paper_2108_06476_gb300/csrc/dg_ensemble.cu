@@ -222,10 +222,14 @@ __global__ void __launch_bounds__(kEnsMaxThreads, 3) ensemble_stage_kernel(EnsAr
     const WorkItem w = a.items[it];
     const SimDesc sd = a.sims[w.sim];
     {
+      // the member's coefficients; FP64 members take them times their dt
+      // (the fused stage's line sums are then dt du, as in the single-mesh
+      // kernel), FP32 members as they are
       const R* src = reinterpret_cast<const R*>(static_cast<const Tables<R>*>(a.tables) + w.sim);
       R* dst = reinterpret_cast<R*>(&s_tb);
+      const R sc = sizeof(R) == 8 ? R(a.dt[w.sim]) : R(1);
       for (int i = threadIdx.x; i < (int)(sizeof(Tables<R>) / sizeof(R)); i += blockDim.x)
-        dst[i] = src[i];
+        dst[i] = sc * src[i];
     }
     __syncthreads();
     if constexpr (sizeof(R) == 8) {

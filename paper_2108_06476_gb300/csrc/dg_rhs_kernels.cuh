@@ -187,12 +187,32 @@ __device__ __forceinline__ void volume_direction(int dir, R (*sp)[3 + 2 * D][Sha
     for (int c = 0; c < NV; ++c) sa[el][comp[c]][node[a]] = acc[a][c];
 }
 
+// The split-form and lifting coefficients of the dimension's directions,
+// times sc, into a shared copy (every thread of the block calls it; a
+// barrier must follow before use). A fused stage passes sc = dt, so that the
+// line sums are dt du itself and the epilogue needs no product by dt; the
+// rhs alone passes 1, which leaves every coefficient exact.
+template <int D, int N, typename R>
+__device__ __forceinline__ void stage_tables(Tables<R>& dst, const Tables<R>& tb, R sc) {
+  constexpr int NP = N + 1;
+  for (int t = threadIdx.x; t < D * NP * NP; t += blockDim.x) {
+    const int dir = t / (NP * NP), a = (t / NP) % NP, b = t % NP;
+    dst.Ds[dir][a][b] = sc * tb.Ds[dir][a][b];
+  }
+  if ((int)threadIdx.x < D) {
+    dst.liftR[threadIdx.x] = sc * tb.liftR[threadIdx.x];
+    dst.liftL[threadIdx.x] = sc * tb.liftL[threadIdx.x];
+  }
+}
+
 // One batch of `count` (<= MAXE) elements from e0: the prologue into shared
 // memory (smem: count x (3 + 2D) staged slots, then count x (D + 2)
 // accumulators), the D direction phases with one thread per element line,
 // and the epilogue. Every thread of the block calls it (it synchronises the
 // block); threads beyond count x LINES only help with the prologue and the
-// epilogue.
+// epilogue. In a fused stage (fz.k set) tb holds the coefficients times the
+// stage's dt (stage_tables), so that the sums are dt du; otherwise the
+// coefficients themselves.
 template <int D, int N, typename R, int VF, int MAXE>
 __device__ __forceinline__ void volume_batch(double* u, R* __restrict__ du,
                                              const R* __restrict__ fs, const Geom& g,
@@ -245,8 +265,7 @@ __device__ __forceinline__ void volume_batch(double* u, R* __restrict__ du,
                                           s_left[el][dir]);
     __syncthreads();
   }
-  // epilogue: the store (or the fused stage update)
-  const double dtv = fz.k ? *fz.dt : 0.0;
+  // epilogue: the store (or the fused stage update; the sums are dt du)
   double* const uo = fz.u_out ? fz.u_out : u;
   for (int t = threadIdx.x; t < count * P; t += blockDim.x) {
     const int ell = t / P, node = t % P;
@@ -257,7 +276,7 @@ __device__ __forceinline__ void volume_batch(double* u, R* __restrict__ du,
       const long long i = ((long long)e * NV + v) * P + node;
       if (fz.k) {
         // the first stage (A = 0) neither reads k nor lets stale k values in
-        double kk = dtv * (double)val;
+        double kk = (double)val;
         if (fz.a != 0.0) kk = fma(fz.a, fz.k[i], kk);
         fz.k[i] = kk;
         uo[i] = u[i] + fz.b * kk;
@@ -273,9 +292,12 @@ __global__ void __launch_bounds__(EPB* Shape<D, N>::LINES)
     volume_kernel(double* u, R* __restrict__ du, const R* __restrict__ fs, Geom g, Tables<R> tb,
                   unsigned* __restrict__ err, StageFuse fz) {
   extern __shared__ __align__(16) unsigned char dg_smem[];
+  __shared__ Tables<R> s_tab;  // volume_batch's first barrier follows
+  stage_tables<D, N, R>(s_tab, tb, fz.k ? R(*fz.dt) : R(1));
   const int e0 = blockIdx.x * EPB;
   const int left = (int)g.nelem - e0;
-  volume_batch<D, N, R, VF, EPB>(u, du, fs, g, tb, err, fz, e0, left < EPB ? left : EPB, dg_smem);
+  volume_batch<D, N, R, VF, EPB>(u, du, fs, g, s_tab, err, fz, e0, left < EPB ? left : EPB,
+                                 dg_smem);
 }
 
 // ---- surface ----
@@ -594,6 +616,7 @@ __device__ __forceinline__ void pp_elements(double* u, double* __restrict__ du,
   __shared__ int s_left[EPB][3];
   for (int t = threadIdx.x; t < EPB * D; t += blockDim.x)
     s_left[t / D][t % D] = t / D < count ? neighbour32(g, e0 + t / D, t % D, -1) : 0;
+
   // FACES: the first THREADS threads (the volume threads) do the prologue and
   // the first pair phase, synchronised among themselves by barrier 1, while
   // the face warps evaluate the surface fluxes; all meet at the barrier
@@ -792,7 +815,9 @@ __device__ __forceinline__ void pp_elements(double* u, double* __restrict__ du,
     }
   }
   // epilogue: the CTA's elements are contiguous in the state
-  const double dtv = fz.k ? *fz.dt : 0.0;
+  // (CHAIN: tb holds the coefficients times dt, as volume_batch's does, so
+  // the sums are already dt du)
+  const double dtv = fz.k ? (CHAIN ? 1.0 : *fz.dt) : 0.0;
   double* const uo = fz.u_out ? fz.u_out : u;
   for (int t = threadIdx.x; t < count * NV * P; t += blockDim.x) {
     const int el = t / (NV * P), r = t % (NV * P);
@@ -800,7 +825,7 @@ __device__ __forceinline__ void pp_elements(double* u, double* __restrict__ du,
     const double val = sa(el)[v][node];
     const long long i = (long long)e0 * NV * P + t;
     if (fz.k) {
-      double kk = dtv * val;
+      double kk = CHAIN ? val : dtv * val;
       if (fz.a != 0.0) kk = fma(fz.a, fz.k[i], kk);
       fz.k[i] = kk;
       uo[i] = u[i] + fz.b * kk;
