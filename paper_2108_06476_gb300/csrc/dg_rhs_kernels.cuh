@@ -187,24 +187,6 @@ __device__ __forceinline__ void volume_direction(int dir, R (*sp)[3 + 2 * D][Sha
     for (int c = 0; c < NV; ++c) sa[el][comp[c]][node[a]] = acc[a][c];
 }
 
-// The split-form and lifting coefficients of the dimension's directions,
-// times sc, into a shared copy (every thread of the block calls it; a
-// barrier must follow before use). A fused stage passes sc = dt, so that the
-// line sums are dt du itself and the epilogue needs no product by dt; the
-// rhs alone passes 1, which leaves every coefficient exact.
-template <int D, int N, typename R>
-__device__ __forceinline__ void stage_tables(Tables<R>& dst, const Tables<R>& tb, R sc) {
-  constexpr int NP = N + 1;
-  for (int t = threadIdx.x; t < D * NP * NP; t += blockDim.x) {
-    const int dir = t / (NP * NP), a = (t / NP) % NP, b = t % NP;
-    dst.Ds[dir][a][b] = sc * tb.Ds[dir][a][b];
-  }
-  if ((int)threadIdx.x < D) {
-    dst.liftR[threadIdx.x] = sc * tb.liftR[threadIdx.x];
-    dst.liftL[threadIdx.x] = sc * tb.liftL[threadIdx.x];
-  }
-}
-
 // One batch of `count` (<= MAXE) elements from e0: the prologue into shared
 // memory (smem: count x (3 + 2D) staged slots, then count x (D + 2)
 // accumulators), the D direction phases with one thread per element line,
