@@ -152,9 +152,9 @@ __device__ void ens_faces(const EnsArgs& a, const SimDesc& sd, const WorkItem& w
       else if (dir == 1) face_flux32<3, N, 1>(u, (float*)fs, g, a.sf, ref, refE, e, l);
       else face_flux32<3, N, 2>(u, (float*)fs, g, a.sf, ref, refE, e, l);
     } else {
-      if (dir == 0) face_flux<3, N, R, 0>(u, fs, g, a.sf, e, l);
-      else if (dir == 1) face_flux<3, N, R, 1>(u, fs, g, a.sf, e, l);
-      else face_flux<3, N, R, 2>(u, fs, g, a.sf, e, l);
+      // one instruction stream for the directions (items of degree 4 and 5
+      // put faces of two directions in one warp)
+      face_flux_rt<3, N, R>(dir, u, fs, g, a.sf, e, l);
     }
   }
 }

@@ -454,6 +454,26 @@ __device__ __forceinline__ void face_flux(const double* __restrict__ u, R* __res
   fs[(long long)(dir * NV + NV - 1) * base + off] = f[NV - 1];
 }
 
+// face_flux with the direction as a value: warps whose lanes hold faces of
+// different directions run one instruction stream (the same arithmetic)
+template <int D, int N, typename R>
+__device__ __forceinline__ void face_flux_rt(int dir, const double* __restrict__ u,
+                                             R* __restrict__ fs, const Geom& g, int sf, int e,
+                                             int l) {
+  constexpr int NV = D + 2, NF = Shape<D, N>::LINES;
+  const int t1 = (dir + 1) % D, t2 = (dir + 2) % D;
+  const int nelem = (int)g.nelem;
+  R f[NV];
+  face_flux_nf_dir<D, N, R>(dir, u, g, sf, e, l, f);
+  const long long base = (long long)nelem * NF;
+  const long long off = (long long)e * NF + l;
+  fs[(long long)(dir * NV + 0) * base + off] = f[0];
+  fs[(long long)(dir * NV + 1 + dir) * base + off] = f[1];
+  fs[(long long)(dir * NV + 1 + t1) * base + off] = f[2];
+  if (D == 3) fs[(long long)(dir * NV + 1 + t2) * base + off] = f[D];
+  fs[(long long)(dir * NV + NV - 1) * base + off] = f[NV - 1];
+}
+
 template <int D, int N, typename R, int dir>
 __device__ __forceinline__ void surface_body(const double* __restrict__ u, R* __restrict__ fs,
                                              const Geom& g, int sf) {
