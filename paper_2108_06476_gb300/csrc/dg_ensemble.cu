@@ -143,6 +143,9 @@ __device__ void ens_faces(const EnsArgs& a, const SimDesc& sd, const WorkItem& w
       element_ref<3>(u, ref, refE, w.e0 + el, N + 1, a.gm1, a.gm1inv);
     __syncthreads();
   }
+  // FP64: the direction is a value, so that warps holding faces of two
+  // directions (items of degree 4 and 5) issue one instruction stream (the
+  // FP32 face flux, mostly FP32 arithmetic, gained nothing from it)
   const int per_dir = w.count * LINES;
   for (int t = threadIdx.x; t < 3 * per_dir; t += blockDim.x) {
     const int dir = t / per_dir, r = t % per_dir;
@@ -152,8 +155,6 @@ __device__ void ens_faces(const EnsArgs& a, const SimDesc& sd, const WorkItem& w
       else if (dir == 1) face_flux32<3, N, 1>(u, (float*)fs, g, a.sf, ref, refE, e, l);
       else face_flux32<3, N, 2>(u, (float*)fs, g, a.sf, ref, refE, e, l);
     } else {
-      // one instruction stream for the directions (items of degree 4 and 5
-      // put faces of two directions in one warp)
       face_flux_rt<3, N, R>(dir, u, fs, g, a.sf, e, l);
     }
   }
