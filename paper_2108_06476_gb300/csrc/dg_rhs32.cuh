@@ -130,6 +130,132 @@ __device__ __forceinline__ void volume_direction32(int dir,
   }
 }
 
+// Degrees from kRows32FromN up: volume_direction32 with the row node a of
+// the pair loop as a loop value (one flux body per partner node b instead of
+// one per pair) and the partner's staged deviations read from shared memory
+// for each pair; the row's running sums and own flux are taken out of the
+// register arrays and put back, so every node's sum takes its terms in the
+// same order: bitwise the result of volume_direction32 (see
+// volume_direction_rows). On GB300 it raises the FP32 rhs of 3D N = 4, 5,
+// 6 and 7 by 8%, 12%, 23% and 25%; N = 3 keeps the line-held form.
+constexpr int kRows32FromN = 4;
+
+template <int D, int N, int VF>
+__device__ __forceinline__ void volume_direction32_rows(
+    int dir, float (*sp)[3 + 2 * D][Shape<D, N>::P], float (*sa)[D + 2][Shape<D, N>::P], int el,
+    int l, const Tables<float>& tb, float gm1inv, float ggm1, const float* __restrict__ fs,
+    int nelem, int e, int eleft, const float* rref, const float* dc) {
+  using S = Shape<D, N>;
+  constexpr int NP = S::NP, NV = S::NV;
+  const int t1 = (dir + 1) % D, t2 = (dir + 2) % D;
+  const int n0 = line_node_rt<D, N>(dir, l, 0);
+  const int ns = line_node_rt<D, N>(dir, l, 1) - n0;  // node stride along the line
+  auto stage = [&](int a) {
+    const int nd = n0 + a * ns;
+    DNode<D> q;
+    q.rho = sp[el][0][nd];
+    q.drho = sp[el][1][nd];
+    q.dp = sp[el][2][nd];
+    q.v[0] = sp[el][3 + dir][nd];
+    q.dv[0] = sp[el][3 + D + dir][nd];
+    q.v[1] = sp[el][3 + t1][nd];
+    q.dv[1] = sp[el][3 + D + t1][nd];
+    if (D == 3) {
+      q.v[D - 1] = sp[el][3 + t2][nd];
+      q.dv[D - 1] = sp[el][3 + D + t2][nd];
+    }
+    return q;
+  };
+  int comp[NV];
+  comp[0] = 0;
+  comp[1] = 1 + dir;
+  comp[2] = 1 + t1;
+  if (D == 3) comp[D] = 1 + t2;
+  comp[D + 1] = D + 1;
+  float fR[NV], fL[NV];
+  {
+    const long long base = (long long)nelem * S::LINES;
+    const long long oR = (long long)e * S::LINES + l;
+    const long long oL = (long long)eleft * S::LINES + l;
+#pragma unroll
+    for (int c = 0; c < NV; ++c) {
+      const long long row = (long long)(dir * NV + comp[c]) * base;
+      fR[c] = fs[row + oR];
+      fL[c] = fs[row + oL] + dc[comp[c]];
+    }
+  }
+  const DRef<D> rf = dir_ref<D>(rref[0], rref + 1, rref[D + 1], dir);
+  float Fn[NP][NV];
+#pragma unroll
+  for (int a = 0; a < NP; ++a) {
+    const DNode<D> q = stage(a);
+    delta_phys_flux<D>(q, rf, ggm1, Fn[a]);
+  }
+  float acc[NP][NV];
+#pragma unroll
+  for (int a = 0; a < NP; ++a)
+#pragma unroll
+    for (int v = 0; v < NV; ++v) acc[a][v] = 0.0f;
+#pragma unroll 1
+  for (int a = 0; a < NP - 1; ++a) {
+    const DNode<D> qa = stage(a);
+    float ra[NV], Fa[NV];
+#pragma unroll
+    for (int k = 0; k < NP - 1; ++k)
+      if (k == a)
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          ra[v] = acc[k][v];
+          Fa[v] = Fn[k][v];
+        }
+#pragma unroll
+    for (int b = 1; b < NP; ++b) {
+      if (b > a) {
+        const float dab = tb.Ds[dir][a][b], dba = tb.Ds[dir][b][a];
+        if (VF == kVCentral) {
+#pragma unroll
+          for (int v = 0; v < NV; ++v) {
+            const float h = 0.5f * (Fn[b][v] - Fa[v]);
+            ra[v] = fmaf(dab, h, ra[v]);
+            acc[b][v] = fmaf(-dba, h, acc[b][v]);
+          }
+        } else {
+          const DNode<D> qb = stage(b);
+          float f[NV];
+          delta_pair<VF, D>(qa, qb, rf, gm1inv, f);
+#pragma unroll
+          for (int v = 0; v < NV; ++v) {
+            ra[v] = fmaf(dab, f[v] - Fa[v], ra[v]);
+            acc[b][v] = fmaf(dba, f[v] - Fn[b][v], acc[b][v]);
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < NP - 1; ++k)
+      if (k == a)
+#pragma unroll
+        for (int v = 0; v < NV; ++v) acc[k][v] = ra[v];
+  }
+  {
+    const float lr = tb.liftR[dir], ll = tb.liftL[dir];
+#pragma unroll
+    for (int c = 0; c < NV; ++c) {
+      acc[N][c] = fmaf(lr, fR[c] - Fn[N][c], acc[N][c]);
+      acc[0][c] = fmaf(ll, fL[c] - Fn[0][c], acc[0][c]);
+    }
+  }
+#pragma unroll
+  for (int a = 0; a < NP; ++a) {
+    const int nd = n0 + a * ns;
+    sa[el][0][nd] += acc[a][0];
+    sa[el][1 + dir][nd] += acc[a][1];
+    sa[el][1 + t1][nd] += acc[a][2];
+    if (D == 3) sa[el][1 + t2][nd] += acc[a][D];
+    sa[el][D + 1][nd] += acc[a][D + 1];
+  }
+}
+
 // One batch of `count` (<= MAXE) elements from e0 (see volume_batch);
 // fz.ref holds the references of every element of the mesh. smem: count x
 // (3 + 2D) staged slots and count x (D + 2) accumulators (FP32), then, from
@@ -223,9 +349,14 @@ __device__ __forceinline__ void volume_batch32(double* u, float* __restrict__ du
   const float gm1inv = (float)g.gm1inv, ggm1 = (float)(g.gamma * g.gm1inv);
 #pragma unroll 1
   for (int dir = 0; dir < D; ++dir) {
-    if (active)
-      volume_direction32<D, N, VF>(dir, sp, sa, el, l, tb, gm1inv, ggm1, fs, nelem, e0 + el,
-                                   s_left[el][dir], s_ref[el], s_dc[el][dir]);
+    if (active) {
+      if constexpr (N >= kRows32FromN)
+        volume_direction32_rows<D, N, VF>(dir, sp, sa, el, l, tb, gm1inv, ggm1, fs, nelem,
+                                          e0 + el, s_left[el][dir], s_ref[el], s_dc[el][dir]);
+      else
+        volume_direction32<D, N, VF>(dir, sp, sa, el, l, tb, gm1inv, ggm1, fs, nelem, e0 + el,
+                                     s_left[el][dir], s_ref[el], s_dc[el][dir]);
+    }
     __syncthreads();
   }
   const double dtv = fz.k ? *fz.dt : 0.0;

@@ -187,6 +187,105 @@ __device__ __forceinline__ void volume_direction(int dir, R (*sp)[3 + 2 * D][Sha
     for (int c = 0; c < NV; ++c) sa[el][comp[c]][node[a]] = acc[a][c];
 }
 
+// Degrees from kRowsFromN up: the same direction phase with the row node a
+// of the pair loop as a loop value. The unrolled body is then one flux per
+// partner node b (b > a, a uniform branch) instead of one per pair, a
+// quarter of the code at N = 7, and the partner's staged values are read
+// from shared memory for each pair instead of being held for the whole line
+// (the line-held form needs every register of the thread at N = 7 and
+// spills). Row a takes its running total out of the accumulator array,
+// continues it over b > a and puts it back, so every node's sum takes its
+// terms in the order of volume_direction: the result is bitwise the same.
+// On GB300 the row loop takes 3D N = 7 from 0.58 to 0.73 G DOF/s per rhs and
+// N = 6 from 0.67 to 0.69; at N = 4 and 5 the two forms are within 1%.
+constexpr int kRowsFromN = 6;
+
+template <int D, int N, typename R, int VF, int EPB>
+__device__ __forceinline__ void volume_direction_rows(int dir, R (*sp)[3 + 2 * D][Shape<D, N>::P],
+                                                      R (*sa)[D + 2][Shape<D, N>::P], int el,
+                                                      int l, const Tables<R>& tb, R gm1inv,
+                                                      const R* __restrict__ fs, int nelem, int e,
+                                                      int eleft) {
+  using S = Shape<D, N>;
+  constexpr int NP = S::NP, NV = S::NV;
+  const int t1 = (dir + 1) % D, t2 = (dir + 2) % D;
+  const int n0 = line_node_rt<D, N>(dir, l, 0);
+  const int ns = line_node_rt<D, N>(dir, l, 1) - n0;  // node stride along the line
+  auto stage = [&](int a) {
+    const int nd = n0 + a * ns;
+    LinePrim<R, D> q;
+    q.s0 = sp[el][0][nd];
+    q.s1 = sp[el][1][nd];
+    q.hp = sp[el][2][nd];
+    q.vn = sp[el][3 + dir][nd];
+    q.hvn = sp[el][3 + D + dir][nd];
+    q.vt[0] = sp[el][3 + t1][nd];
+    q.hvt[0] = sp[el][3 + D + t1][nd];
+    if (D == 3) {
+      q.vt[D - 2] = sp[el][3 + t2][nd];
+      q.hvt[D - 2] = sp[el][3 + D + t2][nd];
+    }
+    return q;
+  };
+  int comp[NV];
+  comp[0] = 0;
+  comp[1] = 1 + dir;
+  comp[2] = 1 + t1;
+  if (D == 3) comp[D] = 1 + t2;
+  comp[D + 1] = D + 1;
+  R acc[NP][NV];
+#pragma unroll
+  for (int a = 0; a < NP; ++a)
+#pragma unroll
+    for (int v = 0; v < NV; ++v) acc[a][v] = dir == 0 ? R(0) : sa[el][comp[v]][n0 + a * ns];
+#pragma unroll 1
+  for (int a = 0; a < NP - 1; ++a) {
+    const LinePrim<R, D> qa = stage(a);
+    R ra[NV];
+#pragma unroll
+    for (int k = 0; k < NP - 1; ++k)
+      if (k == a)
+#pragma unroll
+        for (int v = 0; v < NV; ++v) ra[v] = acc[k][v];
+#pragma unroll
+    for (int b = 1; b < NP; ++b) {
+      if (b > a) {
+        const LinePrim<R, D> qb = stage(b);
+        R f[NV], an = R(0);
+        if (VF == kVRanocha) ranocha_nf<R, D, (N <= 5)>(qa, qb, f, an);
+        else generic_nf<VF, R, D>(qa, qb, gm1inv, f);
+        const R dab = tb.Ds[dir][a][b], dba = tb.Ds[dir][b][a];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          ra[v] = fma(dab, f[v], ra[v]);
+          acc[b][v] = fma(dba, f[v], acc[b][v]);
+        }
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < NP - 1; ++k)
+      if (k == a)
+#pragma unroll
+        for (int v = 0; v < NV; ++v) acc[k][v] = ra[v];
+  }
+  {
+    const R lr = tb.liftR[dir], ll = tb.liftL[dir];
+    const long long base = (long long)nelem * Shape<D, N>::LINES;
+    const long long oR = (long long)e * Shape<D, N>::LINES + l;
+    const long long oL = (long long)eleft * Shape<D, N>::LINES + l;
+#pragma unroll
+    for (int c = 0; c < NV; ++c) {
+      const long long row = (long long)(dir * NV + comp[c]) * base;
+      acc[N][c] = fma(lr, fs[row + oR], acc[N][c]);
+      acc[0][c] = fma(ll, fs[row + oL], acc[0][c]);
+    }
+  }
+#pragma unroll
+  for (int a = 0; a < NP; ++a)
+#pragma unroll
+    for (int c = 0; c < NV; ++c) sa[el][comp[c]][n0 + a * ns] = acc[a][c];
+}
+
 // One batch of `count` (<= MAXE) elements from e0: the prologue into shared
 // memory (smem: count x (3 + 2D) staged slots, then count x (D + 2)
 // accumulators), the D direction phases with one thread per element line,
@@ -242,9 +341,14 @@ __device__ __forceinline__ void volume_batch(double* u, R* __restrict__ du,
   const int nelem = (int)g.nelem;
 #pragma unroll 1
   for (int dir = 0; dir < D; ++dir) {
-    if (active)
-      volume_direction<D, N, R, VF, MAXE>(dir, sp, sa, el, l, tb, gm1inv, fs, nelem, e0 + el,
-                                          s_left[el][dir]);
+    if (active) {
+      if constexpr (N >= kRowsFromN)
+        volume_direction_rows<D, N, R, VF, MAXE>(dir, sp, sa, el, l, tb, gm1inv, fs, nelem,
+                                                 e0 + el, s_left[el][dir]);
+      else
+        volume_direction<D, N, R, VF, MAXE>(dir, sp, sa, el, l, tb, gm1inv, fs, nelem, e0 + el,
+                                            s_left[el][dir]);
+    }
     __syncthreads();
   }
   // epilogue: the store (or the fused stage update; the sums are dt du)
