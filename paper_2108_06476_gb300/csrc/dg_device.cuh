@@ -448,9 +448,8 @@ __device__ __forceinline__ double f2_of(float t) {
   const double td = t;
   return td * td;
 }
-// MIXED: the short range's tails in FP32 (the default); the line-owning
-// kernels of degree 6 and 7 take the FP64 polynomials, whose smaller code
-// suits their long unrolled line loops better
+// MIXED: the short range's tails in FP32 (the default, which every kernel
+// takes); false gives the FP64 polynomials of the same ranges
 template <bool MIXED = true>
 __device__ __forceinline__ double q_of(double f2, double) {
   double q;

@@ -155,7 +155,7 @@ __device__ __forceinline__ void volume_direction(int dir, R (*sp)[3 + 2 * D][Sha
 #pragma unroll
     for (int b = a + 1; b < NP; ++b) {
       R f[NV], an = R(0);
-      if (VF == kVRanocha) ranocha_nf<R, D, (N <= 5)>(q[a], q[b], f, an);
+      if (VF == kVRanocha) ranocha_nf<R, D>(q[a], q[b], f, an);
       else generic_nf<VF, R, D>(q[a], q[b], gm1inv, f);
       const R dab = tb.Ds[dir][a][b], dba = tb.Ds[dir][b][a];
 #pragma unroll
@@ -195,9 +195,12 @@ __device__ __forceinline__ void volume_direction(int dir, R (*sp)[3 + 2 * D][Sha
 // (the line-held form needs every register of the thread at N = 7 and
 // spills). Row a takes its running total out of the accumulator array,
 // continues it over b > a and puts it back, so every node's sum takes its
-// terms in the order of volume_direction: the result is bitwise the same.
-// On GB300 the row loop takes 3D N = 7 from 0.58 to 0.73 G DOF/s per rhs and
-// N = 6 from 0.67 to 0.69; at N = 4 and 5 the two forms are within 1%.
+// terms in the order of volume_direction. The log means take their FP32
+// polynomial tails as at the lower degrees (the line-held form at N = 6 and
+// 7 ran faster with the shorter code of the FP64 polynomials; the two differ
+// by about 1e-16 relative). On GB300 the row loop takes the 3D rhs at N = 7
+// from 0.58 to 0.75 G DOF/s and at N = 6 from 0.67 to 0.71; at N = 4 and 5
+// the two forms are within 1%.
 constexpr int kRowsFromN = 6;
 
 template <int D, int N, typename R, int VF, int EPB>
@@ -252,7 +255,7 @@ __device__ __forceinline__ void volume_direction_rows(int dir, R (*sp)[3 + 2 * D
       if (b > a) {
         const LinePrim<R, D> qb = stage(b);
         R f[NV], an = R(0);
-        if (VF == kVRanocha) ranocha_nf<R, D, (N <= 5)>(qa, qb, f, an);
+        if (VF == kVRanocha) ranocha_nf<R, D>(qa, qb, f, an);
         else generic_nf<VF, R, D>(qa, qb, gm1inv, f);
         const R dab = tb.Ds[dir][a][b], dba = tb.Ds[dir][b][a];
 #pragma unroll
