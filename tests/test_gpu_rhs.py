@@ -253,6 +253,36 @@ def test_rhs_fp32_small(orc, d, N, n, vf, sf):
     assert rel_l2(got, ref) <= TOL32, rel_l2(got, ref)
 
 
+# Meshes of 608 elements or more run the line-owning volume kernel, whose
+# direction phase is the row loop from N = 6 in FP64 and from N = 4 in FP32
+# (smaller FP64 meshes run the pair-parallel kernel, so the every-degree test
+# above does not reach it). Every volume flux through the row loop, 2D and
+# 3D, on anisotropic meshes; FP64 against the oracle on sampled elements
+# and FP32 on whole small meshes (FP32 meshes have no pair-parallel path),
+# random states.
+@pytest.mark.parametrize("vf,sf", [(0, 0), (1, 1), (2, 2), (0, 3)])
+@pytest.mark.parametrize("d,N,n", [(3, 6, (9, 9, 8)), (3, 7, (8, 8, 10)), (2, 7, (25, 26))])
+def test_rhs_fp64_row_loop_every_flux(orc, d, N, n, vf, sf):
+    dom = W.box(d)
+    u = W.random_state(d, N, n, seed=200 + 10 * N + vf)
+    elems = _sample_elements(n, 40, seed=N + vf)
+    P = (N + 1) ** d
+    ref = oracle_rhs(orc, d, N, n, dom, u, vf, sf, elems=elems).reshape(-1, d + 2, P)[elems]
+    got = gpu_rhs(d, N, n, dom, u, vf, sf).reshape(-1, d + 2, P)[elems]
+    assert rel_l2(got, ref) <= TOL64, rel_l2(got, ref)
+
+
+@pytest.mark.parametrize("vf,sf", [(0, 0), (1, 1), (2, 2), (0, 3)])
+@pytest.mark.parametrize("d,N,n", [(3, 4, (3, 2, 2)), (3, 6, (2, 2, 3)), (3, 7, (2, 1, 2)),
+                                   (2, 7, (4, 3))])
+def test_rhs_fp32_row_loop_every_flux(orc, d, N, n, vf, sf):
+    dom = W.box(d)
+    u = W.random_state(d, N, n, seed=300 + N)
+    ref = oracle_rhs(orc, d, N, n, dom, u, vf, sf)
+    got = gpu_rhs(d, N, n, dom, u, vf, sf, precision="fp32")
+    assert rel_l2(got, ref) <= TOL32, rel_l2(got, ref)
+
+
 # ---- fused step: device CFL time step, stage update inside the volume kernel ----
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 def test_fused_step_matches_unfused(orc, precision):
